@@ -1,0 +1,124 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module only generates inputs (geometry, receivers, frequencies); it holds
+none of the field method's arithmetic.  Both the CUDA library's callers and
+the FP64 oracle read the arrays it returns, so every coordinate is rounded to
+float32 once here and both sides see identical values.
+
+Workloads (the paper's Sec. III.C / IV describe rooms with PEC balls and a
+PEC-cylinder stand-in for people; its scenes are not published, so these
+stand in for them):
+  * ``sphere_ring``  -- PEC sphere a = 0.5 m at the origin, source at (3, 0, 0),
+    4096 receivers on the radius-2 m ring in z = 0, 2.4 GHz (Sec. IV.A's
+    analytical-sphere validation, at a fixed size).
+  * ``room``         -- 10 x 8 x 3 m box (6 PEC faces as 12 triangles) with N
+    PEC cylinders (radius U[0.15, 0.25] m, height 1.7 m, on the floor),
+    source at (1, 1, 2), receiver grid at z = 1.2 m.
+"""
+import numpy as np
+
+C0 = 299792458.0
+SEED_BASE = 2310101
+
+BODY_SPHERE = 0
+BODY_CYLINDER = 1
+
+
+class Scene:
+    """Plain container: float32 arrays, no behaviour."""
+
+    def __init__(self, tri, tri_face, bodies, tx, pol, freqs, rx, name, max_order=2):
+        self.tri = np.ascontiguousarray(tri, dtype=np.float32).reshape(-1, 3, 3)
+        self.tri_face = np.ascontiguousarray(tri_face, dtype=np.int32)
+        self.bodies = np.ascontiguousarray(bodies, dtype=np.float32).reshape(-1, 6)
+        self.tx = np.asarray(tx, dtype=np.float32).reshape(3)
+        self.pol = np.asarray(pol, dtype=np.float32).reshape(3)
+        self.freqs = np.asarray(freqs, dtype=np.float64).reshape(-1)
+        self.rx = np.ascontiguousarray(rx, dtype=np.float32).reshape(-1, 3)
+        self.name = name
+        self.max_order = int(max_order)
+
+    @property
+    def n_rx(self):
+        return self.rx.shape[0]
+
+    def rx_soa(self):
+        """Receivers as a [3][n_rx] float32 array (x row, y row, z row)."""
+        return np.ascontiguousarray(self.rx.T)
+
+    def subset(self, idx, name=None):
+        return Scene(self.tri, self.tri_face, self.bodies, self.tx, self.pol, self.freqs,
+                     self.rx[idx], name or self.name + "[sub]", self.max_order)
+
+
+def box_triangles(lx, ly, lz):
+    """Axis-aligned box [0,lx]x[0,ly]x[0,lz] as 12 triangles, 2 per face.
+    Face ids: 0 floor, 1 ceiling, 2 x=0, 3 x=lx, 4 y=0, 5 y=ly."""
+    quads = [
+        [(0, 0, 0), (lx, 0, 0), (lx, ly, 0), (0, ly, 0)],
+        [(0, 0, lz), (0, ly, lz), (lx, ly, lz), (lx, 0, lz)],
+        [(0, 0, 0), (0, ly, 0), (0, ly, lz), (0, 0, lz)],
+        [(lx, 0, 0), (lx, 0, lz), (lx, ly, lz), (lx, ly, 0)],
+        [(0, 0, 0), (0, 0, lz), (lx, 0, lz), (lx, 0, 0)],
+        [(0, ly, 0), (lx, ly, 0), (lx, ly, lz), (0, ly, lz)],
+    ]
+    tri, face = [], []
+    for f, q in enumerate(quads):
+        tri.append([q[0], q[1], q[2]]); face.append(f)
+        tri.append([q[0], q[2], q[3]]); face.append(f)
+    return np.asarray(tri, dtype=np.float32), np.asarray(face, dtype=np.int32)
+
+
+def sphere_ring(n_rx=4096, pol=(0.0, 0.0, 1.0), freq=2.4e9, radius=0.5, tx=(3.0, 0.0, 0.0), ring=2.0):
+    phi = 2.0 * np.pi * np.arange(n_rx) / n_rx
+    rx = np.stack([ring * np.cos(phi), ring * np.sin(phi), np.zeros(n_rx)], axis=1)
+    bodies = np.array([[BODY_SPHERE, 0.0, 0.0, 0.0, radius, 0.0]])
+    name = "sphere_ring(a=%.2f m, %d rx, pol=%s, %.2f GHz)" % (radius, n_rx, tuple(pol), freq / 1e9)
+    return Scene(np.zeros((0, 3, 3)), np.zeros(0), bodies, tx, pol, [freq], rx, name, max_order=0)
+
+
+def place_cylinders(n, lx, ly, rng, r_lo=0.15, r_hi=0.25, height=1.7, gap=0.05, avoid=None, max_tries=100000):
+    """Non-overlapping vertical cylinders on the floor (>= gap between surfaces
+    and >= gap from the walls).  ``avoid``: list of (x, y, clearance) points to
+    keep outside every footprint."""
+    out = []
+    tries = 0
+    while len(out) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place %d cylinders" % n)
+        r = np.float32(rng.uniform(r_lo, r_hi))
+        x = np.float32(rng.uniform(r + gap, lx - r - gap))
+        y = np.float32(rng.uniform(r + gap, ly - r - gap))
+        ok = True
+        for (cx, cy, cr) in out:
+            if np.hypot(x - cx, y - cy) < r + cr + gap:
+                ok = False
+                break
+        if ok and avoid:
+            for (px, py, cl) in avoid:
+                if np.hypot(x - px, y - py) < r + cl:
+                    ok = False
+                    break
+        if ok:
+            out.append((x, y, r))
+    return np.array([[BODY_CYLINDER, x, y, 0.0, r, height] for (x, y, r) in out], dtype=np.float32)
+
+
+def grid_receivers(nx, ny, lx, ly, z):
+    xs = (np.arange(nx) + 0.5) * (lx / nx)
+    ys = (np.arange(ny) + 0.5) * (ly / ny)
+    X, Y = np.meshgrid(xs, ys)          # row-major: y outer, x inner
+    return np.stack([X.ravel(), Y.ravel(), np.full(X.size, z)], axis=1)
+
+
+def room(n_cyl=20, nx=256, ny=256, freqs=(2.4e9, 5.8e9, 28e9), seed=SEED_BASE + 1,
+         size=(10.0, 8.0, 3.0), tx=(1.0, 1.0, 2.0), pol=(0.0, 0.0, 1.0), rx_z=1.2, max_order=2):
+    lx, ly, lz = size
+    rng = np.random.default_rng(seed)
+    tri, face = box_triangles(lx, ly, lz)
+    bodies = place_cylinders(n_cyl, lx, ly, rng, avoid=[(tx[0], tx[1], 0.3)])
+    rx = grid_receivers(nx, ny, lx, ly, rx_z)
+    name = "room(%gx%gx%g m, %d PEC cylinders, %dx%d rx, f=%s GHz, refl<=%d)" % (
+        lx, ly, lz, n_cyl, nx, ny, ",".join("%g" % (f / 1e9) for f in freqs), max_order)
+    return Scene(tri, face, bodies, tx, pol, freqs, rx, name, max_order=max_order)
