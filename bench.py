@@ -1,0 +1,337 @@
+"""Throughput of the creeping-wave field evaluator (one JSON line on stdout).
+
+Workload (one step): the 10 x 8 x 3 m room with 6 PEC faces (12 triangles)
+and 20 PEC cylinders standing in for people, source at (1, 1, 2) m, the
+256 x 256 receiver grid at z = 1.2 m, 2.4 / 5.8 / 28 GHz, planar reflections
+up to order 2, the first creeping ray each way round every cylinder, FP32
+bulk arithmetic: 65 536 receivers x 3 frequencies = 196 608 field samples.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+N > 1 runs under torch.distributed (one process per GPU): each rank evaluates
+its own receiver grid (shifted by a fraction of a cell) with no data-path
+collective; value = all ranks' samples / max-over-ranks time ("weak").
+--impl reference times the FP64 oracle (oracle/) on the host cores instead.
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "receiver field samples/s (GO+UTD creeping), error vs FP64 oracle (dB/rad)"
+UNIT = "samples/s"
+WORKLOAD = "room 10x8x3 m, 12 PEC triangles + 20 PEC cylinders, 256x256 rx at z=1.2 m, 2.4/5.8/28 GHz, refl<=2"
+
+# Algorithmic FP32 work per unit (FFMA = 2 flops), the work model of the
+# scope table: visibility tests, surface-ray geometry, image construction,
+# Fock evaluation and per-path phase/accumulation.
+UNIT_FLOPS = dict(seg_tri=30, seg_body=25, inside_tri=60, image_cand=60, body_refl=150, creep_geom=150,
+                  fock_evals=60, path_freq=30)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def make_scene(rank=0, world=1):
+    from paper_2310_10578_gb300 import scenes
+    sc = scenes.room()
+    if world > 1:
+        dx = (10.0 / 256) * rank / world
+        rx = sc.rx.copy()
+        rx[:, 0] = rx[:, 0] + dx
+        sc.rx = rx.astype(np.float32)
+    return sc
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if not self.samples:
+            return None
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for nm, v in zip(names, s[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def _kernel_source_hash():
+    p = os.path.join(ROOT, "paper_2310_10578_gb300", "csrc", "eval_fields.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def _profiled_traffic():
+    """DRAM bytes per launch of k_eval from the committed ncu summary, if it was
+    taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "k_eval_room20_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    kv = {}
+    for line in open(p):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("eval_fields.cu sha256[:16]") != _kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch_full_workload"])
+    except (KeyError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle
+    sc = make_scene()
+    rng = np.random.default_rng(12345)
+    oracle.build()
+    cores = os.cpu_count() or 1
+    # size one step: ~ a few seconds of oracle work
+    probe = sc.subset(rng.choice(sc.n_rx, 128, replace=False))
+    t0 = time.perf_counter()
+    oracle.evaluate(probe, want_paths=False)
+    rate = 128 / max(time.perf_counter() - t0, 1e-3)
+    per_step = int(np.clip(rate * 4.0, 64, sc.n_rx))
+    times = []
+    for it in range(args.warmup + args.steps):
+        sub = sc.subset(rng.choice(sc.n_rx, per_step, replace=False))
+        t0 = time.perf_counter()
+        oracle.evaluate(sub, want_paths=False)
+        dt = time.perf_counter() - t0
+        if it >= args.warmup:
+            times.append(dt)
+    samples = per_step * len(sc.freqs)
+    value = samples * len(times) / sum(times)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "step": "%d random receivers x %d frequencies" % (per_step, len(sc.freqs))},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d random receivers of the 256x256 grid per step" % per_step},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- CPU baseline + accuracy
+def cpu_baseline_and_accuracy(sc, E_gpu, target_s):
+    """Oracle (as it stands, all host cores) on a bounded random sample: its
+    throughput, the GPU error against it, and the work counters of the sample."""
+    from oracle import oracle
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from parity import compare_fields
+    oracle.build()
+    rng = np.random.default_rng(2024)
+    probe_n = 256
+    idx = rng.choice(sc.n_rx, probe_n, replace=False)
+    t0 = time.perf_counter()
+    oracle.evaluate(sc.subset(idx), want_paths=False)
+    rate = probe_n / max(time.perf_counter() - t0, 1e-3)
+    n = int(np.clip(rate * target_s, 512, sc.n_rx))
+    idx = np.sort(rng.choice(sc.n_rx, n, replace=False))
+    sub = sc.subset(idx)
+    t0 = time.perf_counter()
+    ref = oracle.evaluate(sub)
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    try:
+        st = compare_fields(E_gpu[:, :, idx], ref, flags=ref.flags, freqs=sc.freqs, db_tol=1e9, ph_tol=1e9)
+    except AssertionError as e:
+        st = {"error": str(e)[:200]}
+    base = {"value": n * len(sc.freqs) / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d random receivers of the 256x256 grid x %d freqs (%.1f s)" % (n, len(sc.freqs), dt)}
+    return base, st, ref.counters, n
+
+
+def algorithmic_flops(counters, n_sample, n_rx, n_f):
+    w = 0.0
+    for k, c in UNIT_FLOPS.items():
+        if k == "path_freq":
+            w += c * counters["paths"] * n_f
+        else:
+            w += c * counters[k]
+    return w * n_rx / n_sample
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_2310_10578_gb300 import build, creep
+    build.build()
+    sc = make_scene(rank, world)
+    S = creep.Scene.from_scene(sc)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    rx = torch.tensor(sc.rx_soa(), device=dev)
+    n_rx, n_f = sc.n_rx, len(sc.freqs)
+    out = torch.empty((n_f, 3, n_rx, 2), dtype=torch.float32, device=dev)
+    opts = creep.options(max_order=2)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(max(args.warmup, 3)):
+        S.evaluate(rx, out=out, opts=opts)
+    barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for i in range(args.steps):
+        flush.fill_(float(i))                        # evict L2 between timed steps
+        starts[i].record(stream)
+        S.evaluate(rx, out=out, opts=opts)
+        ends[i].record(stream)
+    barrier()
+    dev_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # ---- e2e: host buffers through rt_evaluate_host, copies inside the timed region
+    rx_host = torch.tensor(sc.rx_soa()).pin_memory()
+    out_host = torch.empty((n_f, 3, n_rx, 2), dtype=torch.float32).pin_memory()
+    lib = creep.load()
+    import ctypes
+    h = S._h
+
+    def e2e_once():
+        rc = lib.rt_evaluate_host(h, ctypes.c_void_p(rx_host.data_ptr()), n_rx, ctypes.c_void_p(out_host.data_ptr()),
+                                  None, ctypes.byref(opts), ctypes.c_void_p(stream.cuda_stream))
+        if rc != 0:
+            raise RuntimeError(lib.rt_last_error().decode())
+
+    for _ in range(3):
+        e2e_once()
+    barrier()
+    e2e_t = []
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_once()
+        e2e_t.append(time.perf_counter() - t0)
+    barrier()
+    clocks = sampler.stop() if sampler else None
+
+    ms = float(np.mean(dev_ms))
+    e2e_s = float(np.mean(e2e_t))
+    if world > 1:
+        t = torch.tensor([ms, e2e_s], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+    samples = n_rx * n_f
+    value = world * samples / (ms / 1e3)
+    e2e_value = world * samples / e2e_s
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    launches_per_step = (n_f + 3) // 4
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_rx": n_rx, "n_freq": n_f, "n_cylinders": int(sc.bodies.shape[0]),
+                       "n_triangles": int(sc.tri.shape[0]), "max_refl_order": 2, "precision": "fp32",
+                       "l2": "flushed between timed steps (256 MiB write)"},
+            "clocks": clocks,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * n_rx,
+                    "d2h_bytes_per_step": n_f * 3 * n_rx * 8},
+            "gpu_launches": launches_per_step * args.steps,
+            "roofline": None, "cpu_baseline": None}
+    stats = S.stats()
+    line["config"]["fp64_escalated_receivers"] = stats["escalated_receivers"]
+    if world == 1 and not args.no_cpu_baseline:
+        E_gpu = out.detach().cpu().numpy().astype(np.float64)
+        E_gpu = E_gpu[..., 0] + 1j * E_gpu[..., 1]
+        base, acc, counters, n_s = cpu_baseline_and_accuracy(sc, E_gpu, args.cpu_seconds)
+        line["cpu_baseline"] = base
+        line["accuracy_vs_fp64_oracle"] = dict(acc, sample_receivers=n_s)
+        flops = algorithmic_flops(counters, n_s, n_rx, n_f)
+        props = torch.cuda.get_device_properties(dev)
+        sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
+        peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12      # FP32 FFMA lanes x 2 x clock
+        achieved = flops / (ms / 1e3) / 1e12
+        line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                            "frac": achieved / peak, "traffic": _profiled_traffic(),
+                            "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived, FFMA)" %
+                                          (props.multi_processor_count, sm_max),
+                            "work_per_launch_flops": flops}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * creep.h -- C ABI of the GB300 creeping-wave (smooth-surface UTD) field
+ * evaluator.
+ *
+ * The operation (Wang, Audia, Manocha, "Indoor Wireless Signal Modeling with
+ * Smooth Surface Diffraction Effects", Sec. II.B, Eqs. 1-4 and Fig. 1): for
+ * one transmitter and every receiver P, sum coherently
+ *   E(P) = U^i E^i(P)                         direct ray           (Eq. 1)
+ *        + sum U^r E^r(P)                     specular reflections (Eqs. 1, 3)
+ *        + sum E^d(P)                         creeping rays        (Eqs. 2, 4)
+ * over: the direct ray; PEC image reflections off the scene's planar faces up
+ * to order 2; the first-order reflection off each convex body with the
+ * Fock-uniform reflection coefficient; and the first creeping (surface-
+ * diffracted) ray in each direction around each sphere or vertical cylinder,
+ * whose transfer function T uses the soft/hard Fock--Pekeris functions.  The
+ * visibility bits U are straight-segment tests against every triangle and
+ * body (Eqs. 1-2, "path validation", Sec. III.B).
+ *
+ * Conventions
+ *   - Units: metres, Hz.  Time convention e^{+j w t}: fields go as e^{-jks}.
+ *   - Source: isotropic, polarisation vector pol; on a ray leaving in
+ *     direction d the field is unit(pol - (pol.d) d) / r (|E| = 1/r).
+ *   - Every entry point returns an int status (RT_OK = 0 or an RT_ERR_*
+ *     code) and never throws; rt_last_error() gives a thread-local message.
+ *   - Device pointers are CUDA device addresses of the current device; host
+ *     pointers are ordinary host memory.  The caller owns every buffer it
+ *     passes; the library owns the scene (its device copies of geometry and
+ *     the Fock--Pekeris table) until rt_scene_destroy.
+ *   - Calls on one scene are not thread-safe; different scenes are
+ *     independent.  Kernels run on the caller's stream; rt_evaluate and
+ *     rt_paths return without synchronising.
+ */
+#ifndef CREEP_H
+#define CREEP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define RT_OK 0
+#define RT_ERR_ARG 1       /* null pointer, n < 0, NaN/Inf coordinate, a <= 0, bad enum */
+#define RT_ERR_GEOM 2      /* transmitter inside/on a body or on a face plane, overlapping bodies */
+#define RT_ERR_CUDA 3      /* a CUDA runtime call failed; message in rt_last_error() */
+#define RT_ERR_TIMEOUT 4   /* a bounded device wait gave up */
+#define RT_ERR_OVERFLOW 5  /* a size exceeds a library limit (faces, bodies, path cap) */
+#define RT_ERR_STATE 6     /* transmitter or frequencies not set */
+
+/* body types */
+#define RT_BODY_SPHERE 0   /* centre c, radius a */
+#define RT_BODY_CYLINDER 1 /* vertical (axis +z) finite cylinder: axis through (cx, cy), z in [cz, cz + h], radius a */
+
+/* contribution enable mask (rt_options.enable) */
+#define RT_EN_LOS 1u
+#define RT_EN_PLANAR 2u
+#define RT_EN_BODYREFL 4u
+#define RT_EN_CREEP_SOFT 8u
+#define RT_EN_CREEP_HARD 16u
+#define RT_EN_ALL 31u
+
+/* arithmetic of the geometry and field math (rt_options.precision) */
+#define RT_PREC_FP32 0     /* FP32 bulk, double-float path lengths, FP64 re-evaluation of uncertain decisions */
+#define RT_PREC_FP64 1     /* everything in FP64 */
+
+/* per-receiver flags (optional output) */
+#define RT_FLAG_INSIDE 1u     /* receiver inside or on a body: no field */
+#define RT_FLAG_CAUSTIC 2u    /* within half a wavelength of a sphere's axial caustic (k d_perp < pi) */
+#define RT_FLAG_ESCALATED 4u  /* at least one decision was re-evaluated in FP64 */
+#define RT_FLAG_OVERFLOW 8u   /* more paths than the rt_paths capacity */
+
+/* path type codes: a path is (type << 56) | (id1 << 28) | id2 */
+#define RT_PATH_LOS 0      /* direct */
+#define RT_PATH_R1 1       /* id1 = face */
+#define RT_PATH_R2 2       /* id1 = first face, id2 = second face */
+#define RT_PATH_RB 3       /* id1 = body: GO reflection off the body */
+#define RT_PATH_CP 4       /* id1 = body: creeping ray, short way round */
+#define RT_PATH_CM 5       /* id1 = body: creeping ray, long way round */
+
+/* library limits */
+#define RT_MAX_FACES 64
+#define RT_MAX_BODIES 1024
+#define RT_MAX_TRIS 4096
+#define RT_MAX_FREQS 64
+
+typedef struct rt_scene rt_scene;
+
+typedef struct {
+    int type;       /* RT_BODY_* */
+    float c[3];     /* sphere: centre; cylinder: (axis x, axis y, base z) */
+    float a;        /* radius, > 0 */
+    float h;        /* cylinder height, > 0 (ignored for spheres) */
+} rt_body;
+
+typedef struct {
+    int max_order;      /* planar reflection order 0, 1 or 2 */
+    unsigned enable;    /* RT_EN_* mask */
+    int precision;      /* RT_PREC_* */
+} rt_options;
+
+typedef struct {
+    unsigned long long escalated_receivers; /* receivers with RT_FLAG_ESCALATED in the last rt_evaluate/rt_paths */
+} rt_stats;
+
+/*
+ * Build a scene.  tri_xyz: host float [n_tri][3][3] (vertex-major xyz);
+ * tri_face: host int [n_tri], the planar face (coplanar triangle group that
+ * reflects as one polygon, Eq. 3) each triangle belongs to, ids 0..n_face-1;
+ * NULL makes every triangle its own face.  bodies: host [n_body].  The
+ * library copies everything to the current device and builds, once per
+ * device, the FP64 Fock--Pekeris table (see rt_fock_table).  *out
+ * receives the scene.  Errors: RT_ERR_ARG, RT_ERR_GEOM (overlapping bodies),
+ * RT_ERR_OVERFLOW (limits above), RT_ERR_CUDA.
+ */
+int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri,
+                    const rt_body *bodies, int n_body, rt_scene **out);
+
+/* Free a scene and its device memory (NULL is a no-op). */
+void rt_scene_destroy(rt_scene *scene);
+
+/*
+ * Transmitter position (host float[3]) and polarisation (host float[3],
+ * non-zero).  RT_ERR_GEOM if the point is inside or on a body or on the
+ * plane of a face (the off-surface assumption, Sec. II.B).
+ */
+int rt_set_tx(rt_scene *scene, const float tx[3], const float pol[3]);
+
+/* Frequencies (host double[n_f], Hz, > 0), 1 <= n_f <= RT_MAX_FREQS. */
+int rt_set_freqs(rt_scene *scene, const double *f_hz, int n_f);
+
+/*
+ * Field at n_rx receivers (Eqs. 1-4).
+ *   rx_soa  device float [3][n_rx]: x row, then y row, then z row.
+ *   e_out   device float [n_f][3][n_rx][2]: (re, im) of E_x, E_y, E_z per
+ *           frequency; caller-owned, fully overwritten.
+ *   flags   device uint32 [n_rx] (RT_FLAG_*), or NULL.
+ *   opt     NULL for {2, RT_EN_ALL, RT_PREC_FP32}.
+ *   stream  cudaStream_t (NULL = legacy default stream).
+ * n_rx = 0 is a no-op.  Asynchronous: returns after the launch.
+ */
+int rt_evaluate(rt_scene *scene, const float *rx_soa, int n_rx, float *e_out,
+                uint32_t *flags, const rt_options *opt, void *stream);
+
+/*
+ * Same evaluation from and to HOST buffers (rx_soa host [3][n_rx], e_out host
+ * [n_f][3][n_rx][2], flags host or NULL): copies in, evaluates, copies out,
+ * synchronises the stream.  Device scratch for the copies is allocated on the
+ * first call and kept with the scene.
+ */
+int rt_evaluate_host(rt_scene *scene, const float *rx_soa, int n_rx, float *e_out,
+                     uint32_t *flags, const rt_options *opt, void *stream);
+
+/*
+ * Path lists (the visibility decisions of Eqs. 1-2) instead of the field.
+ *   codes   device uint64 [n_rx][cap]: per receiver its paths in the
+ *           enumeration order LOS, R1(face), R2(face, face), then per body
+ *           RB, CP, CM; slots past the count are left untouched.
+ *   counts  device int32 [n_rx]: number of paths (may exceed cap; then
+ *           RT_FLAG_OVERFLOW is set and only cap codes are written).
+ *   flags   device uint32 [n_rx] or NULL.
+ */
+int rt_paths(rt_scene *scene, const float *rx_soa, int n_rx, uint64_t *codes,
+             int32_t *counts, int cap, uint32_t *flags, const rt_options *opt, void *stream);
+
+/* Counters of the last rt_evaluate / rt_paths on this scene (synchronises its stream). */
+int rt_get_stats(rt_scene *scene, rt_stats *out);
+
+/*
+ * Copy the device's Fock--Pekeris table to host memory for inspection:
+ * xi_lo, step, n nodes; G[kind][n] with kind 0 soft, 1 hard, of
+ * G(xi) = phat(xi) e^{-j xi^3/12}, phat = P + c/xi, and dG/dxi; each complex as
+ * (re, im) doubles.  Buffers: g host double [2][n][2], dg host double [2][n][2];
+ * pass NULL to query n only.  res: host double [4][8] = alpha_n, 1/Ai'(-alpha_n)^2,
+ * beta_n, 1/(beta_n Ai(-beta_n)^2) (residue-series constants), or NULL.
+ */
+int rt_fock_table(double *xi_lo, double *step, int *n, double *g, double *dg, double *res);
+
+/* Thread-local description of the last error (never NULL). */
+const char *rt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CREEP_H */

@@ -308,6 +308,7 @@ static inline uint64_t pcode(int type, int id1, int id2) {
 /* ------------------------------------------------------------ per-receiver */
 typedef struct {
     c3 *E;             /* [n_f] accumulated field */
+    double *Sabs;      /* [n_f] sum over paths of |E_path| (conditioning of the coherent sum) */
     uint64_t *paths; int n_paths, cap;
     unsigned flags;
     counters ct;
@@ -322,6 +323,16 @@ static void add_path(rx_state *st, uint64_t code) {
 
 static double kwave(double f) { return TWO_PI * f / C0_LIGHT; }
 
+static inline double c3_norm(c3 v) {
+    return sqrt(creal(v.x) * creal(v.x) + cimag(v.x) * cimag(v.x) + creal(v.y) * creal(v.y) + cimag(v.y) * cimag(v.y) +
+                creal(v.z) * creal(v.z) + cimag(v.z) * cimag(v.z));
+}
+/* add one path's field at frequency f */
+static inline void accum(rx_state *st, int f, c3 v) {
+    st->E[f] = c3_add(st->E[f], v);
+    st->Sabs[f] += c3_norm(v);
+}
+
 /* LOS and planar image paths (order 1 and 2); PEC faces. */
 static void planar_paths(const scene *s, v3 P, rx_state *st) {
     v3 S = s->tx;
@@ -332,7 +343,7 @@ static void planar_paths(const scene *s, v3 P, rx_state *st) {
             v3 e = source_pol(s, unit(sub(P, S)));
             for (int f = 0; f < s->n_f; ++f) {
                 double k = kwave(s->freq[f]);
-                st->E[f] = c3_add(st->E[f], rscl(e, cexp(-I * k * R) / R));
+                accum(st, f, rscl(e, cexp(-I * k * R) / R));
             }
         }
     }
@@ -355,7 +366,7 @@ static void planar_paths(const scene *s, v3 P, rx_state *st) {
             c3 e = pec_mirror(c3_from(source_pol(s, unit(sub(Q, S)))), Fi->n);
             for (int f = 0; f < s->n_f; ++f) {
                 double k = kwave(s->freq[f]);
-                st->E[f] = c3_add(st->E[f], c3_scl(e, cexp(-I * k * L) / L));
+                accum(st, f, c3_scl(e, cexp(-I * k * L) / L));
             }
         }
     }
@@ -386,7 +397,7 @@ static void planar_paths(const scene *s, v3 P, rx_state *st) {
                 c3 e = pec_mirror(pec_mirror(c3_from(source_pol(s, unit(sub(Q1, S)))), Fi->n), Fj->n);
                 for (int f = 0; f < s->n_f; ++f) {
                     double k = kwave(s->freq[f]);
-                    st->E[f] = c3_add(st->E[f], c3_scl(e, cexp(-I * k * L) / L));
+                    accum(st, f, c3_scl(e, cexp(-I * k * L) / L));
                 }
             }
         }
@@ -607,7 +618,7 @@ static void add_body_reflection(const scene *s, const refl_geom *G, v3 P, rx_sta
         }
         cplx ph = A * cexp(-I * k * (si + sr)) / si;
         c3 Er = c3_add(rscl(eperp, Rs * Es * ph), rscl(epar_r, Rh * Eh * ph));
-        st->E[f] = c3_add(st->E[f], Er);
+        accum(st, f, Er);
     }
 }
 
@@ -635,7 +646,7 @@ static void add_creeping(const scene *s, const creep_geom *G, v3 P, rx_state *st
         cplx Th = (s->enable & EN_CREEP_HARD) ? Tpre * Bh : 0.0;
         cplx ph = caus * G->amp * cexp(-I * k * (G->sp + G->sq));
         c3 Ed = c3_add(rscl(b2, Ts * Es * ph), rscl(G->n2, Th * Eh * ph));
-        st->E[f] = c3_add(st->E[f], Ed);
+        accum(st, f, Ed);
     }
 }
 
@@ -704,7 +715,7 @@ static int build_faces(scene *s) {
  *   tx[3], pol[3], freq [n_f] (Hz)
  *   rx [n_rx][3]
  *   E_out [n_f][3][n_rx][2] (re, im), path_codes [n_rx][cap], path_count [n_rx],
- *   flags [n_rx], counters_out[8] (summed)
+ *   flags [n_rx], counters_out[8] (summed), sabs_out [n_f][n_rx] (sum of |E_path|, or NULL)
  * Returns 0.
  */
 int oracle_eval(const double *tri, const int *tri_face, int n_tri,
@@ -721,7 +732,7 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
                 double xi_lo, double xi_hi,
                 int max_order, int enable,
                 double *E_out, uint64_t *path_codes, int *path_count, int cap,
-                unsigned *flags_out, long long *counters_out, int n_threads) {
+                unsigned *flags_out, long long *counters_out, int n_threads, double *sabs_out) {
     fock_rule R = {tau_re, tau_im, ws_re, ws_im, wh_re, wh_im, offsets, n_buckets,
                    res_alpha, res_cs, res_beta, res_ch, n_res, xi_lo, xi_hi};
     scene s;
@@ -752,11 +763,14 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
 #pragma omp parallel for schedule(dynamic, 16) reduction(+ : c0, c1, c2, c3v, c4, c5, c6, c7)
     for (int r = 0; r < n_rx; ++r) {
         c3 Eacc[64];
+        double Sacc[64];
         c3 *E = (n_f <= 64) ? Eacc : (c3 *)malloc(sizeof(c3) * n_f);
-        for (int f = 0; f < n_f; ++f) E[f] = CV(0, 0, 0);
+        double *Sa = (n_f <= 64) ? Sacc : (double *)malloc(sizeof(double) * n_f);
+        for (int f = 0; f < n_f; ++f) { E[f] = CV(0, 0, 0); Sa[f] = 0.0; }
         rx_state st;
         memset(&st, 0, sizeof(st));
         st.E = E;
+        st.Sabs = Sa;
         st.paths = path_codes ? path_codes + (size_t)r * cap : NULL;
         st.cap = path_codes ? cap : 0;
         v3 P = V(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
@@ -779,7 +793,10 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
         if (flags_out) flags_out[r] = st.flags;
         c0 += st.ct.seg_tri; c1 += st.ct.seg_body; c2 += st.ct.inside_tri; c3v += st.ct.image_cand;
         c4 += st.ct.body_refl; c5 += st.ct.creep_geom; c6 += st.ct.paths; c7 += st.ct.fock_evals;
+        if (sabs_out)
+            for (int f = 0; f < n_f; ++f) sabs_out[(size_t)f * n_rx + r] = Sa[f];
         if (E != Eacc) free(E);
+        if (Sa != Sacc) free(Sa);
     }
     if (counters_out) {
         counters_out[0] = c0; counters_out[1] = c1; counters_out[2] = c2; counters_out[3] = c3v;

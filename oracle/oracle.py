@@ -36,7 +36,9 @@ def build(force=False):
     os.makedirs(BUILD, exist_ok=True)
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fopenmp", "-fPIC", "-shared",
+        # -ffp-contract=off: every operation rounds as written (no fused
+        # multiply-add), so results do not depend on the host ISA.
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
                                "-o", tmp, SRC, "-lm"])
         os.replace(tmp, LIB)
     return LIB
@@ -52,7 +54,7 @@ def _load():
         d = ctypes.c_double
         _lib.oracle_eval.argtypes = [P, P, i, P, i, P, P, P, i, P, i,
                                      P, P, P, P, P, P, P, i, P, P, P, P, i, d, d,
-                                     i, i, P, P, P, i, P, P, i]
+                                     i, i, P, P, P, i, P, P, i, P]
         _lib.oracle_eval.restype = i
         _lib.oracle_transition_F.argtypes = [P, i, P]
         _lib.oracle_fock_bracket.argtypes = [P, P, P, P, P, P, P, i, P, P, P, P, i, d, d, P, P, i, P]
@@ -94,8 +96,9 @@ class Result:
 def evaluate(scene, rx=None, enable=EN_ALL, cap=256, threads=0, want_paths=True):
     """FP64 field of ``scene`` at its receivers (or at ``rx`` [n,3]).
 
-    Returns an object with E [n_f][3][n_rx] complex128, paths (list of sorted
-    uint64 arrays), flags [n_rx] uint32, counters dict and seconds."""
+    Returns an object with E [n_f][3][n_rx] complex128, sabs [n_f][n_rx] (sum of
+    |E_path|), paths (list of sorted uint64 arrays), flags [n_rx] uint32,
+    counters dict and seconds."""
     lib = _load()
     rx = scene.rx if rx is None else rx
     rx64 = np.ascontiguousarray(np.asarray(rx, dtype=np.float32).astype(np.float64))
@@ -112,16 +115,18 @@ def evaluate(scene, rx=None, enable=EN_ALL, cap=256, threads=0, want_paths=True)
     counts = np.zeros(n_rx, dtype=np.int32)
     flags = np.zeros(n_rx, dtype=np.uint32)
     ctr = np.zeros(8, dtype=np.int64)
+    sabs = np.zeros((n_f, n_rx), dtype=np.float64)
     t0 = time.perf_counter()
     lib.oracle_eval(_p(tri), _p(tf), scene.tri.shape[0], _p(bodies), scene.bodies.shape[0],
                     _p(tx), _p(pol), _p(fr), n_f, _p(rx64), n_rx, *_fock_args(),
                     scene.max_order, enable, _p(E),
                     _p(codes) if want_paths else None, _p(counts), cap if want_paths else 0,
-                    _p(flags), _p(ctr), threads)
+                    _p(flags), _p(ctr), threads, _p(sabs))
     res = Result()
     res.seconds = time.perf_counter() - t0
     res.E = E[..., 0] + 1j * E[..., 1]
     res.flags = flags
+    res.sabs = sabs
     res.counts = counts
     if want_paths:
         res.paths = [np.sort(codes[r, :min(counts[r], cap)]) for r in range(n_rx)]

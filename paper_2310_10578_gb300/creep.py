@@ -1,0 +1,203 @@
+"""Python binding of the C ABI in include/creep.h (argument marshalling only).
+
+Every step of the field evaluation runs in the CUDA library libcreep.so; this
+module loads it with ctypes and passes pointers.  PyTorch provides device
+memory and streams.  There is no CPU fallback: if the library is missing or
+no CUDA device is present, the calls raise.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+RT_OK, RT_ERR_ARG, RT_ERR_GEOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_OVERFLOW, RT_ERR_STATE = range(7)
+RT_BODY_SPHERE, RT_BODY_CYLINDER = 0, 1
+RT_EN_LOS, RT_EN_PLANAR, RT_EN_BODYREFL, RT_EN_CREEP_SOFT, RT_EN_CREEP_HARD = 1, 2, 4, 8, 16
+RT_EN_ALL = 31
+RT_PREC_FP32, RT_PREC_FP64 = 0, 1
+RT_FLAG_INSIDE, RT_FLAG_CAUSTIC, RT_FLAG_ESCALATED, RT_FLAG_OVERFLOW = 1, 2, 4, 8
+RT_PATH_LOS, RT_PATH_R1, RT_PATH_R2, RT_PATH_RB, RT_PATH_CP, RT_PATH_CM = range(6)
+FOCK_NRES = 8
+
+EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "rt_evaluate",
+           "rt_evaluate_host", "rt_paths", "rt_get_stats", "rt_fock_table", "rt_last_error")
+
+
+class CreepError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("creep error %d: %s" % (code, msg))
+        self.code = code
+
+
+class rt_body(ctypes.Structure):
+    _fields_ = [("type", ctypes.c_int), ("c", ctypes.c_float * 3), ("a", ctypes.c_float), ("h", ctypes.c_float)]
+
+
+class rt_options(ctypes.Structure):
+    _fields_ = [("max_order", ctypes.c_int), ("enable", ctypes.c_uint), ("precision", ctypes.c_int)]
+
+
+class rt_stats(ctypes.Structure):
+    _fields_ = [("escalated_receivers", ctypes.c_ulonglong)]
+
+
+_lib = None
+
+
+def load(build_if_missing=True):
+    """Load libcreep.so (building it in-tree first if it is absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise OSError("libcreep.so not built: run paper_2310_10578_gb300.build.build()")
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P, I, U = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint
+    lib.rt_scene_create.argtypes = [P, P, I, P, I, ctypes.POINTER(P)]
+    lib.rt_scene_destroy.argtypes = [P]
+    lib.rt_scene_destroy.restype = None
+    lib.rt_set_tx.argtypes = [P, P, P]
+    lib.rt_set_freqs.argtypes = [P, P, I]
+    lib.rt_evaluate.argtypes = [P, P, I, P, P, P, P]
+    lib.rt_evaluate_host.argtypes = [P, P, I, P, P, P, P]
+    lib.rt_paths.argtypes = [P, P, I, P, P, I, P, P, P]
+    lib.rt_get_stats.argtypes = [P, P]
+    lib.rt_fock_table.argtypes = [P, P, P, P, P, P]
+    lib.rt_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code != RT_OK:
+        raise CreepError(code, _lib.rt_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(ctypes.c_void_p)
+    return ctypes.c_void_p(a.data_ptr())
+
+
+def options(max_order=2, enable=RT_EN_ALL, precision=RT_PREC_FP32):
+    return rt_options(max_order, enable, precision)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Scene:
+    """A scene on the current CUDA device: planar faces (triangles grouped into
+    coplanar reflecting faces) and convex PEC bodies (spheres, vertical
+    cylinders), one transmitter and a frequency list."""
+
+    def __init__(self, tri, tri_face, bodies):
+        lib = load()
+        tri = np.ascontiguousarray(np.asarray(tri, dtype=np.float32).reshape(-1, 9))
+        n_tri = tri.shape[0]
+        tf = None if tri_face is None else np.ascontiguousarray(np.asarray(tri_face, dtype=np.int32))
+        bodies = np.asarray(bodies, dtype=np.float64).reshape(-1, 6)
+        arr = (rt_body * max(1, len(bodies)))()
+        for i, b in enumerate(bodies):
+            arr[i].type = int(b[0])
+            arr[i].c[0], arr[i].c[1], arr[i].c[2] = float(b[1]), float(b[2]), float(b[3])
+            arr[i].a, arr[i].h = float(b[4]), float(b[5])
+        self._h = ctypes.c_void_p()
+        _check(lib.rt_scene_create(_ptr(tri) if n_tri else None, _ptr(tf), n_tri, ctypes.cast(arr, ctypes.c_void_p),
+                                   len(bodies), ctypes.byref(self._h)))
+        self.n_f = 0
+
+    @classmethod
+    def from_scene(cls, sc):
+        """Build from a paper_2310_10578_gb300.scenes.Scene (also sets Tx and frequencies)."""
+        s = cls(sc.tri, sc.tri_face, sc.bodies)
+        s.set_tx(sc.tx, sc.pol)
+        s.set_freqs(sc.freqs)
+        return s
+
+    def close(self):
+        if self._h:
+            _lib.rt_scene_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_tx(self, tx, pol):
+        tx = np.ascontiguousarray(np.asarray(tx, dtype=np.float32).reshape(3))
+        pol = np.ascontiguousarray(np.asarray(pol, dtype=np.float32).reshape(3))
+        _check(_lib.rt_set_tx(self._h, _ptr(tx), _ptr(pol)))
+
+    def set_freqs(self, freqs):
+        f = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64).reshape(-1))
+        _check(_lib.rt_set_freqs(self._h, _ptr(f), len(f)))
+        self.n_f = len(f)
+
+    def evaluate(self, rx_soa, out=None, flags=None, opts=None, stream=None):
+        """Field at receivers. rx_soa: CUDA float32 tensor [3, n]; returns (and
+        fills) out: CUDA float32 tensor [n_f, 3, n, 2]."""
+        import torch
+        n = rx_soa.shape[1]
+        assert rx_soa.is_cuda and rx_soa.dtype == torch.float32 and rx_soa.is_contiguous()
+        if out is None:
+            out = torch.empty((self.n_f, 3, n, 2), dtype=torch.float32, device=rx_soa.device)
+        _check(_lib.rt_evaluate(self._h, _ptr(rx_soa), n, _ptr(out), _ptr(flags),
+                                ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
+        return out
+
+    def evaluate_host(self, rx_soa, flags=False, opts=None, stream=None):
+        """Same from/to host memory (numpy): copies inside the call."""
+        rx_soa = np.ascontiguousarray(np.asarray(rx_soa, dtype=np.float32))
+        n = rx_soa.shape[1]
+        out = np.empty((self.n_f, 3, n, 2), dtype=np.float32)
+        fl = np.empty(n, dtype=np.uint32) if flags else None
+        _check(_lib.rt_evaluate_host(self._h, _ptr(rx_soa), n, _ptr(out), _ptr(fl),
+                                     ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
+        return (out, fl) if flags else out
+
+    def paths(self, rx_soa, cap=256, opts=None, stream=None):
+        """Path lists: (codes [n, cap] int64 tensor, counts [n] int32, flags [n] int32)."""
+        import torch
+        n = rx_soa.shape[1]
+        codes = torch.zeros((n, cap), dtype=torch.int64, device=rx_soa.device)
+        counts = torch.zeros(n, dtype=torch.int32, device=rx_soa.device)
+        fl = torch.zeros(n, dtype=torch.int32, device=rx_soa.device)
+        _check(_lib.rt_paths(self._h, _ptr(rx_soa), n, _ptr(codes), _ptr(counts), cap, _ptr(fl),
+                             ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
+        return codes, counts, fl
+
+    def stats(self):
+        st = rt_stats()
+        _check(_lib.rt_get_stats(self._h, ctypes.byref(st)))
+        return {"escalated_receivers": int(st.escalated_receivers)}
+
+
+def fock_table():
+    """The device's Fock--Pekeris table: (xi_lo, step, G [2, n] complex, dG [2, n], res [4, 8])."""
+    lib = load()
+    xi_lo, step, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+    _check(lib.rt_fock_table(ctypes.byref(xi_lo), ctypes.byref(step), ctypes.byref(n), None, None, None))
+    g = np.zeros((2, n.value, 2))
+    dg = np.zeros((2, n.value, 2))
+    res = np.zeros((4, FOCK_NRES))
+    _check(lib.rt_fock_table(None, None, None, _ptr(g), _ptr(dg), _ptr(res)))
+    return xi_lo.value, step.value, g[..., 0] + 1j * g[..., 1], dg[..., 0] + 1j * dg[..., 1], res
+
+
+def decode(code):
+    code = int(code) & 0xFFFFFFFFFFFFFFFF
+    return (code >> 56) & 0xFF, (code >> 28) & 0xFFFFFFF, code & 0xFFFFFFF

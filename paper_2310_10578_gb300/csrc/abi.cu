@@ -1,0 +1,506 @@
+// abi.cu -- the C ABI (include/creep.h): scene management, argument checks,
+// per-device Fock--Pekeris table cache, launches.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace creep {
+
+static thread_local std::string g_err = "no error";
+void set_error(const std::string &msg) { g_err = msg; }
+
+// ---------------------------------------------------------------- table cache
+struct DevTable {
+    float4 *fock32 = nullptr;
+    double2 *fock64 = nullptr;
+    float4 *res32 = nullptr;
+    dq4 *res64 = nullptr;
+    float *weid = nullptr;
+    double *weid64 = nullptr;
+    float weid_L = 0.f;
+    FockHost host;
+};
+static std::mutex g_table_mu;
+static std::map<int, DevTable> g_tables;
+
+// Weideman (1994) coefficients of w(z): a_n = (1/2M) sum_k f(t_k) cos(n k pi/M),
+// t_k = L tan(k pi / 2M), f(t) = e^{-t^2} (L^2 + t^2), M = 2N, L = (N / sqrt 2)^{1/2}.
+static void weideman(std::vector<double> &a, double *L) {
+    const int N = WEIDEMAN_N, M = 2 * N;
+    *L = sqrt(N / sqrt(2.0));
+    a.assign(N, 0.0);
+    for (int n = 1; n <= N; ++n) {
+        double s = 0.0;
+        for (int k = -M + 1; k <= M - 1; ++k) {
+            double t = *L * tan(k * M_PI / (2.0 * M));
+            s += exp(-t * t) * (*L * *L + t * t) * cos(n * k * M_PI / M);
+        }
+        a[n - 1] = s / (2.0 * M);
+    }
+}
+
+static int get_table(DevTable **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { set_error(std::string("cudaGetDevice: ") + cudaGetErrorString(e)); return RT_ERR_CUDA; }
+    std::lock_guard<std::mutex> lk(g_table_mu);
+    auto it = g_tables.find(dev);
+    if (it != g_tables.end()) { *out = &it->second; return RT_OK; }
+    DevTable T;
+    int rc = build_fock_table(&T.host);
+    if (rc != RT_OK) return rc;
+    std::vector<float4> f32(FOCK_N * 2);
+    std::vector<double2> f64(FOCK_N * 4);
+    for (int j = 0; j < FOCK_N; ++j)
+        for (int k = 0; k < 2; ++k) {
+            const double *q = &T.host.tab[(j * 2 + k) * 4];
+            f32[j * 2 + k] = make_float4((float)q[0], (float)q[1], (float)(q[2] * XI_STEP), (float)(q[3] * XI_STEP));
+            f64[(j * 2 + k) * 2] = make_double2(q[0], q[1]);
+            f64[(j * 2 + k) * 2 + 1] = make_double2(q[2], q[3]);
+        }
+    std::vector<float4> r32(FOCK_NRES * 2);
+    std::vector<dq4> r64(FOCK_NRES * 2);
+    const double s3 = sqrt(3.0) / 2.0;
+    for (int n = 0; n < FOCK_NRES; ++n) {
+        double al = T.host.res[n], cs = T.host.res[FOCK_NRES + n], be = T.host.res[2 * FOCK_NRES + n],
+               ch = T.host.res[3 * FOCK_NRES + n];
+        r32[2 * n] = make_float4((float)(al * s3), (float)(al / 2), (float)cs, 0.f);
+        r32[2 * n + 1] = make_float4((float)(be * s3), (float)(be / 2), (float)ch, 0.f);
+        r64[2 * n] = make_dq4(al * s3, al / 2, cs, 0.0);
+        r64[2 * n + 1] = make_dq4(be * s3, be / 2, ch, 0.0);
+    }
+    std::vector<double> wa;
+    double L;
+    weideman(wa, &L);
+    std::vector<float> wf(wa.begin(), wa.end());
+    T.weid_L = (float)L;
+#define CKT(x)                                                                         \
+    do {                                                                               \
+        cudaError_t e_ = (x);                                                          \
+        if (e_ != cudaSuccess) { set_error(std::string(#x) + ": " + cudaGetErrorString(e_)); return RT_ERR_CUDA; } \
+    } while (0)
+    CKT(cudaMalloc(&T.fock32, sizeof(float4) * f32.size()));
+    CKT(cudaMalloc(&T.fock64, sizeof(double2) * f64.size()));
+    CKT(cudaMalloc(&T.res32, sizeof(float4) * r32.size()));
+    CKT(cudaMalloc(&T.res64, sizeof(dq4) * r64.size()));
+    CKT(cudaMalloc(&T.weid, sizeof(float) * WEIDEMAN_N));
+    CKT(cudaMalloc(&T.weid64, sizeof(double) * WEIDEMAN_N));
+    CKT(cudaMemcpy(T.fock32, f32.data(), sizeof(float4) * f32.size(), cudaMemcpyHostToDevice));
+    CKT(cudaMemcpy(T.fock64, f64.data(), sizeof(double2) * f64.size(), cudaMemcpyHostToDevice));
+    CKT(cudaMemcpy(T.res32, r32.data(), sizeof(float4) * r32.size(), cudaMemcpyHostToDevice));
+    CKT(cudaMemcpy(T.res64, r64.data(), sizeof(dq4) * r64.size(), cudaMemcpyHostToDevice));
+    CKT(cudaMemcpy(T.weid, wf.data(), sizeof(float) * WEIDEMAN_N, cudaMemcpyHostToDevice));
+    CKT(cudaMemcpy(T.weid64, wa.data(), sizeof(double) * WEIDEMAN_N, cudaMemcpyHostToDevice));
+    g_tables[dev] = T;
+    *out = &g_tables[dev];
+    return RT_OK;
+}
+
+}  // namespace creep
+
+using namespace creep;
+
+struct rt_scene {
+    int device = 0;
+    int n_tri = 0, n_face = 0, n_body = 0;
+    std::vector<float> tri;             // [n_tri][9]
+    std::vector<int> tri_face;
+    std::vector<FaceHost> faces;
+    std::vector<rt_body> bodies;
+    // device copies
+    float4 *d_tri = nullptr, *d_aux = nullptr, *d_face32 = nullptr, *d_body = nullptr;
+    dq4 *d_face64 = nullptr;
+    int2 *d_face_rng = nullptr;
+    int *d_face_tris = nullptr;
+    double *d_freq = nullptr;
+    float4 *d_img = nullptr;            // source images, see DevScene::img
+    unsigned long long *d_esc = nullptr;
+    DevTable *table = nullptr;
+    // state
+    bool tx_set = false, f_set = false;
+    float tx[3], pol[3];
+    std::vector<double> freqs;
+    float band_len = 0.f;
+    // host-io scratch (rt_evaluate_host)
+    float *io_rx = nullptr, *io_e = nullptr;
+    uint32_t *io_fl = nullptr;
+    size_t io_cap = 0;
+    cudaStream_t last_stream = nullptr;
+};
+
+#define CK(x)                                                                              \
+    do {                                                                                   \
+        cudaError_t e_ = (x);                                                              \
+        if (e_ != cudaSuccess) {                                                           \
+            set_error(std::string(#x) + ": " + cudaGetErrorString(e_));                    \
+            return RT_ERR_CUDA;                                                            \
+        }                                                                                  \
+    } while (0)
+
+static bool fin32(float x) { return isfinite(x); }
+
+static int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    set_error(buf);
+    return code;
+}
+
+static void free_scene(rt_scene *s) {
+    cudaFree(s->d_tri); cudaFree(s->d_aux); cudaFree(s->d_face32); cudaFree(s->d_body);
+    cudaFree(s->d_face64); cudaFree(s->d_face_rng); cudaFree(s->d_face_tris); cudaFree(s->d_freq);
+    cudaFree(s->d_esc); cudaFree(s->io_rx); cudaFree(s->io_e); cudaFree(s->io_fl); cudaFree(s->d_img);
+}
+
+// distance from point p to the solid of body b (0 if inside)
+static double dist_to_body(const double p[3], const rt_body &b) {
+    if (b.type == RT_BODY_SPHERE) {
+        double d = sqrt((p[0] - b.c[0]) * (p[0] - b.c[0]) + (p[1] - b.c[1]) * (p[1] - b.c[1]) + (p[2] - b.c[2]) * (p[2] - b.c[2]));
+        return d > b.a ? d - b.a : 0.0;
+    }
+    double rho = sqrt((p[0] - b.c[0]) * (p[0] - b.c[0]) + (p[1] - b.c[1]) * (p[1] - b.c[1]));
+    double dr = rho > b.a ? rho - b.a : 0.0;
+    double dz = p[2] < b.c[2] ? b.c[2] - p[2] : (p[2] > b.c[2] + b.h ? p[2] - b.c[2] - b.h : 0.0);
+    return sqrt(dr * dr + dz * dz);
+}
+
+static bool bodies_overlap(const rt_body &A, const rt_body &B) {
+    if (A.type == RT_BODY_SPHERE && B.type == RT_BODY_SPHERE) {
+        double c[3] = {A.c[0], A.c[1], A.c[2]};
+        return dist_to_body(c, B) < A.a;
+    }
+    if (A.type == RT_BODY_SPHERE || B.type == RT_BODY_SPHERE) {
+        const rt_body &S = A.type == RT_BODY_SPHERE ? A : B, &C = A.type == RT_BODY_SPHERE ? B : A;
+        double c[3] = {S.c[0], S.c[1], S.c[2]};
+        return dist_to_body(c, C) < S.a;
+    }
+    double dh = sqrt((A.c[0] - B.c[0]) * (A.c[0] - B.c[0]) + (A.c[1] - B.c[1]) * (A.c[1] - B.c[1]));
+    bool zo = !(A.c[2] + A.h < B.c[2] || B.c[2] + B.h < A.c[2]);
+    return zo && dh < (double)A.a + B.a;
+}
+
+extern "C" {
+
+const char *rt_last_error(void) { return g_err.c_str(); }
+
+int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const rt_body *bodies, int n_body,
+                    rt_scene **out) {
+    if (!out) return fail(RT_ERR_ARG, "rt_scene_create: out is NULL");
+    *out = nullptr;
+    if (n_tri < 0 || n_body < 0) return fail(RT_ERR_ARG, "rt_scene_create: negative count");
+    if ((n_tri > 0 && !tri_xyz) || (n_body > 0 && !bodies)) return fail(RT_ERR_ARG, "rt_scene_create: NULL array");
+    if (n_tri > RT_MAX_TRIS) return fail(RT_ERR_OVERFLOW, "rt_scene_create: %d triangles > %d", n_tri, RT_MAX_TRIS);
+    if (n_body > RT_MAX_BODIES) return fail(RT_ERR_OVERFLOW, "rt_scene_create: %d bodies > %d", n_body, RT_MAX_BODIES);
+    rt_scene *s = new rt_scene();
+    cudaGetDevice(&s->device);
+    s->n_tri = n_tri;
+    s->n_body = n_body;
+    s->tri.assign(tri_xyz, tri_xyz + 9 * (size_t)n_tri);
+    for (size_t i = 0; i < s->tri.size(); ++i)
+        if (!fin32(s->tri[i])) { delete s; return fail(RT_ERR_ARG, "rt_scene_create: non-finite vertex"); }
+    s->tri_face.resize(n_tri);
+    int nf = 0;
+    for (int t = 0; t < n_tri; ++t) {
+        int f = tri_face ? tri_face[t] : t;
+        if (f < 0) { delete s; return fail(RT_ERR_ARG, "rt_scene_create: negative face id"); }
+        s->tri_face[t] = f;
+        if (f + 1 > nf) nf = f + 1;
+    }
+    if (nf > RT_MAX_FACES) { delete s; return fail(RT_ERR_OVERFLOW, "rt_scene_create: %d faces > %d", nf, RT_MAX_FACES); }
+    s->n_face = nf;
+    s->faces.assign(nf, FaceHost());
+    std::vector<int> cnt(nf, 0);
+    for (int t = 0; t < n_tri; ++t) cnt[s->tri_face[t]]++;
+    int acc = 0;
+    for (int f = 0; f < nf; ++f) {
+        if (cnt[f] == 0) { delete s; return fail(RT_ERR_ARG, "rt_scene_create: face %d has no triangle", f); }
+        s->faces[f].first = acc; s->faces[f].count = 0; acc += cnt[f];
+    }
+    std::vector<int> face_tris(n_tri > 0 ? n_tri : 1);
+    std::vector<float4> htri(3 * (size_t)n_tri), haux(3 * (size_t)n_tri);
+    for (int t = 0; t < n_tri; ++t) {
+        const float *v = &s->tri[9 * (size_t)t];
+        double v0[3] = {v[0], v[1], v[2]}, v1[3] = {v[3], v[4], v[5]}, v2[3] = {v[6], v[7], v[8]};
+        double e1[3] = {v1[0] - v0[0], v1[1] - v0[1], v1[2] - v0[2]}, e2[3] = {v2[0] - v0[0], v2[1] - v0[1], v2[2] - v0[2]};
+        double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+        double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(nn > 0.0)) { delete s; return fail(RT_ERR_ARG, "rt_scene_create: triangle %d is degenerate", t); }
+        double u[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+        double off = u[0] * v0[0] + u[1] * v0[1] + u[2] * v0[2];
+        auto len = [](const double *a, const double *b) {
+            return sqrt((a[0] - b[0]) * (a[0] - b[0]) + (a[1] - b[1]) * (a[1] - b[1]) + (a[2] - b[2]) * (a[2] - b[2]));
+        };
+        double l01 = len(v0, v1), l12 = len(v1, v2), l20 = len(v2, v0);
+        // altitudes: h0 of v0 over edge v1v2 = |n| / l12, etc.
+        double h0 = nn / l12, h1 = nn / l20, h2 = nn / l01;
+        int f = s->tri_face[t];
+        FaceHost &F = s->faces[f];
+        if (F.count == 0) {
+            F.n[0] = u[0]; F.n[1] = u[1]; F.n[2] = u[2]; F.d = off;
+        }
+        face_tris[F.first + F.count++] = t;
+        int fbits;
+        memcpy(&fbits, &f, sizeof(int));
+        float fw;
+        memcpy(&fw, &fbits, sizeof(float));
+        htri[3 * t] = make_float4(v[0], v[1], v[2], fw);
+        htri[3 * t + 1] = make_float4(v[3], v[4], v[5], 0.f);
+        htri[3 * t + 2] = make_float4(v[6], v[7], v[8], 0.f);
+        haux[3 * t] = make_float4((float)u[0], (float)u[1], (float)u[2], (float)off);
+        haux[3 * t + 1] = make_float4((float)h0, (float)h1, (float)h2, 0.f);
+        haux[3 * t + 2] = make_float4((float)(1.0 / l01), (float)(1.0 / l12), (float)(1.0 / l20), 0.f);
+    }
+    // bodies
+    s->bodies.assign(bodies, bodies + n_body);
+    std::vector<float4> hb(2 * (size_t)n_body);
+    double scale = 1.0;
+    for (int b = 0; b < n_body; ++b) {
+        const rt_body &B = s->bodies[b];
+        if (B.type != RT_BODY_SPHERE && B.type != RT_BODY_CYLINDER) { delete s; return fail(RT_ERR_ARG, "body %d: bad type", b); }
+        if (!fin32(B.c[0]) || !fin32(B.c[1]) || !fin32(B.c[2]) || !fin32(B.a) || !fin32(B.h) || !(B.a > 0.f) ||
+            (B.type == RT_BODY_CYLINDER && !(B.h > 0.f))) {
+            delete s;
+            return fail(RT_ERR_ARG, "body %d: non-finite or non-positive size", b);
+        }
+        for (int q = 0; q < b; ++q)
+            if (bodies_overlap(s->bodies[q], B)) { delete s; return fail(RT_ERR_GEOM, "bodies %d and %d overlap", q, b); }
+        hb[2 * b] = make_float4(B.c[0], B.c[1], B.c[2], B.a);
+        hb[2 * b + 1] = make_float4(B.type == RT_BODY_CYLINDER ? B.h : 0.f, (float)B.type, 0.f, 0.f);
+        for (int k = 0; k < 3; ++k) scale = fmax(scale, fabs((double)B.c[k]) + B.a + B.h);
+    }
+    for (size_t i = 0; i < s->tri.size(); ++i) scale = fmax(scale, fabs((double)s->tri[i]));
+    // FP32 decision band: bounds the FP32 error of a margin (metres) built from
+    // a few dozen roundings of coordinates of magnitude <= scale: 32 ulp.
+    s->band_len = (float)(scale * 32.0 * 5.96e-8);
+    std::vector<float4> hf32(nf > 0 ? nf : 1);
+    std::vector<dq4> hf64(nf > 0 ? nf : 1);
+    std::vector<int2> hr(nf > 0 ? nf : 1);
+    for (int f = 0; f < nf; ++f) {
+        const FaceHost &F = s->faces[f];
+        hf32[f] = make_float4((float)F.n[0], (float)F.n[1], (float)F.n[2], (float)F.d);
+        hf64[f] = make_dq4(F.n[0], F.n[1], F.n[2], F.d);
+        hr[f] = make_int2(F.first, F.count);
+    }
+    int rc = get_table(&s->table);
+    if (rc != RT_OK) { delete s; return rc; }
+#define CKS(x)                                                                  \
+    do {                                                                        \
+        cudaError_t e_ = (x);                                                   \
+        if (e_ != cudaSuccess) {                                                \
+            set_error(std::string(#x) + ": " + cudaGetErrorString(e_));         \
+            free_scene(s); delete s; return RT_ERR_CUDA;                        \
+        }                                                                       \
+    } while (0)
+    size_t ntr = n_tri > 0 ? n_tri : 1, nbd = n_body > 0 ? n_body : 1, nfc = nf > 0 ? nf : 1;
+    CKS(cudaMalloc(&s->d_tri, sizeof(float4) * 3 * ntr));
+    CKS(cudaMalloc(&s->d_aux, sizeof(float4) * 3 * ntr));
+    CKS(cudaMalloc(&s->d_face32, sizeof(float4) * nfc));
+    CKS(cudaMalloc(&s->d_face64, sizeof(dq4) * nfc));
+    CKS(cudaMalloc(&s->d_face_rng, sizeof(int2) * nfc));
+    CKS(cudaMalloc(&s->d_face_tris, sizeof(int) * ntr));
+    CKS(cudaMalloc(&s->d_body, sizeof(float4) * 2 * nbd));
+    CKS(cudaMalloc(&s->d_freq, sizeof(double) * RT_MAX_FREQS));
+    CKS(cudaMalloc(&s->d_esc, sizeof(unsigned long long)));
+    CKS(cudaMalloc(&s->d_img, sizeof(float4) * 2 * (nfc + nfc * nfc)));
+    if (n_tri > 0) {
+        CKS(cudaMemcpy(s->d_tri, htri.data(), sizeof(float4) * 3 * n_tri, cudaMemcpyHostToDevice));
+        CKS(cudaMemcpy(s->d_aux, haux.data(), sizeof(float4) * 3 * n_tri, cudaMemcpyHostToDevice));
+        CKS(cudaMemcpy(s->d_face_tris, face_tris.data(), sizeof(int) * n_tri, cudaMemcpyHostToDevice));
+    }
+    if (nf > 0) {
+        CKS(cudaMemcpy(s->d_face32, hf32.data(), sizeof(float4) * nf, cudaMemcpyHostToDevice));
+        CKS(cudaMemcpy(s->d_face64, hf64.data(), sizeof(dq4) * nf, cudaMemcpyHostToDevice));
+        CKS(cudaMemcpy(s->d_face_rng, hr.data(), sizeof(int2) * nf, cudaMemcpyHostToDevice));
+    }
+    if (n_body > 0) CKS(cudaMemcpy(s->d_body, hb.data(), sizeof(float4) * 2 * n_body, cudaMemcpyHostToDevice));
+    CKS(cudaMemset(s->d_esc, 0, sizeof(unsigned long long)));
+    *out = s;
+    return RT_OK;
+}
+
+void rt_scene_destroy(rt_scene *s) {
+    if (!s) return;
+    free_scene(s);
+    delete s;
+}
+
+int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
+    if (!s || !tx || !pol) return fail(RT_ERR_ARG, "rt_set_tx: NULL argument");
+    for (int k = 0; k < 3; ++k)
+        if (!fin32(tx[k]) || !fin32(pol[k])) return fail(RT_ERR_ARG, "rt_set_tx: non-finite value");
+    if (pol[0] == 0.f && pol[1] == 0.f && pol[2] == 0.f) return fail(RT_ERR_ARG, "rt_set_tx: zero polarisation");
+    double p[3] = {tx[0], tx[1], tx[2]};
+    for (int b = 0; b < s->n_body; ++b)
+        if (dist_to_body(p, s->bodies[b]) <= 0.0) return fail(RT_ERR_GEOM, "rt_set_tx: transmitter inside or on body %d", b);
+    for (int f = 0; f < s->n_face; ++f) {
+        const FaceHost &F = s->faces[f];
+        if (F.n[0] * p[0] + F.n[1] * p[1] + F.n[2] * p[2] - F.d == 0.0)
+            return fail(RT_ERR_GEOM, "rt_set_tx: transmitter on the plane of face %d", f);
+    }
+    memcpy(s->tx, tx, sizeof(s->tx));
+    memcpy(s->pol, pol, sizeof(s->pol));
+    // source images in every face and every ordered face pair (FP64), split
+    // into float hi + lo: the planar path length is |P - image| (Eq. 3, image
+    // method), exact to ~1e-14 for any receiver
+    int nf = s->n_face;
+    std::vector<float4> img(2 * (size_t)(nf + nf * nf));
+    auto mirror = [&](const double X[3], int f, double Y[3]) {
+        const FaceHost &F = s->faces[f];
+        double dist = F.n[0] * X[0] + F.n[1] * X[1] + F.n[2] * X[2] - F.d;
+        for (int k = 0; k < 3; ++k) Y[k] = X[k] - F.n[k] * (2.0 * dist);
+    };
+    auto put = [&](size_t slot, const double Y[3]) {
+        float h[3], l[3];
+        for (int k = 0; k < 3; ++k) { h[k] = (float)Y[k]; l[k] = (float)(Y[k] - (double)h[k]); }
+        img[2 * slot] = make_float4(h[0], h[1], h[2], 0.f);
+        img[2 * slot + 1] = make_float4(l[0], l[1], l[2], 0.f);
+    };
+    for (int i = 0; i < nf; ++i) {
+        double S1[3];
+        mirror(p, i, S1);
+        put(i, S1);
+        for (int j = 0; j < nf; ++j) {
+            double S2[3];
+            mirror(S1, j, S2);
+            put(nf + (size_t)i * nf + j, S2);
+        }
+    }
+    if (nf > 0) CK(cudaMemcpy(s->d_img, img.data(), sizeof(float4) * img.size(), cudaMemcpyHostToDevice));
+    s->tx_set = true;
+    return RT_OK;
+}
+
+int rt_set_freqs(rt_scene *s, const double *f_hz, int n_f) {
+    if (!s || !f_hz) return fail(RT_ERR_ARG, "rt_set_freqs: NULL argument");
+    if (n_f < 1 || n_f > RT_MAX_FREQS) return fail(RT_ERR_ARG, "rt_set_freqs: n_f = %d out of [1, %d]", n_f, RT_MAX_FREQS);
+    for (int i = 0; i < n_f; ++i)
+        if (!(f_hz[i] > 0.0) || !isfinite(f_hz[i])) return fail(RT_ERR_ARG, "rt_set_freqs: bad frequency");
+    s->freqs.assign(f_hz, f_hz + n_f);
+    CK(cudaMemcpy(s->d_freq, f_hz, sizeof(double) * n_f, cudaMemcpyHostToDevice));
+    s->f_set = true;
+    return RT_OK;
+}
+
+static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec) {
+    rt_options o = {2, RT_EN_ALL, RT_PREC_FP32};
+    if (opt) o = *opt;
+    if (o.max_order < 0 || o.max_order > 2) return fail(RT_ERR_ARG, "max_order %d not in [0, 2]", o.max_order);
+    if (o.precision != RT_PREC_FP32 && o.precision != RT_PREC_FP64) return fail(RT_ERR_ARG, "bad precision %d", o.precision);
+    if (o.enable & ~RT_EN_ALL) return fail(RT_ERR_ARG, "bad enable mask 0x%x", o.enable);
+    if (!s->tx_set || !s->f_set) return fail(RT_ERR_STATE, "transmitter or frequencies not set");
+    memset(&D, 0, sizeof(D));
+    D.n_tri = s->n_tri; D.n_face = s->n_face; D.n_body = s->n_body; D.n_f = (int)s->freqs.size();
+    D.tri = s->d_tri; D.tri_alt = s->d_aux; D.tri_nrm = s->d_aux;
+    D.face32 = s->d_face32; D.face64 = s->d_face64; D.face_rng = s->d_face_rng; D.face_tris = s->d_face_tris;
+    D.body = s->d_body;
+    D.fock32 = s->table->fock32; D.fock64 = s->table->fock64;
+    D.res32 = s->table->res32; D.res64 = s->table->res64;
+    D.weid = s->table->weid; D.weid64 = s->table->weid64; D.weid_L = s->table->weid_L;
+    D.freq = s->freqs.data();   // host pointer: read by the launcher only
+    D.img = s->d_img;
+    memcpy(D.tx, s->tx, sizeof(D.tx));
+    memcpy(D.pol, s->pol, sizeof(D.pol));
+    D.band_len = s->band_len;
+    D.max_order = o.max_order;
+    D.enable = o.enable;
+    *prec = o.precision;
+    return RT_OK;
+}
+
+int rt_evaluate(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags, const rt_options *opt,
+                void *stream) {
+    if (!s) return fail(RT_ERR_ARG, "rt_evaluate: NULL scene");
+    if (n_rx < 0) return fail(RT_ERR_ARG, "rt_evaluate: n_rx < 0");
+    DevScene D;
+    int prec;
+    int rc = make_dev(s, opt, D, &prec);
+    if (rc != RT_OK) return rc;
+    if (n_rx > 0 && (!rx_soa || !e_out)) return fail(RT_ERR_ARG, "rt_evaluate: NULL buffer");
+    if (n_rx == 0) return RT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(s->d_esc, 0, sizeof(unsigned long long), st));
+    s->last_stream = st;
+    return launch_eval(D, rx_soa, n_rx, e_out, flags, nullptr, nullptr, 0, prec, s->d_esc, st);
+}
+
+int rt_paths(rt_scene *s, const float *rx_soa, int n_rx, uint64_t *codes, int32_t *counts, int cap, uint32_t *flags,
+             const rt_options *opt, void *stream) {
+    if (!s) return fail(RT_ERR_ARG, "rt_paths: NULL scene");
+    if (n_rx < 0 || cap < 1) return fail(RT_ERR_ARG, "rt_paths: n_rx < 0 or cap < 1");
+    DevScene D;
+    int prec;
+    int rc = make_dev(s, opt, D, &prec);
+    if (rc != RT_OK) return rc;
+    if (n_rx > 0 && (!rx_soa || !codes || !counts)) return fail(RT_ERR_ARG, "rt_paths: NULL buffer");
+    if (n_rx == 0) return RT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(s->d_esc, 0, sizeof(unsigned long long), st));
+    s->last_stream = st;
+    return launch_eval(D, rx_soa, n_rx, nullptr, flags, codes, counts, cap, prec, s->d_esc, st);
+}
+
+int rt_evaluate_host(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags, const rt_options *opt,
+                     void *stream) {
+    if (!s) return fail(RT_ERR_ARG, "rt_evaluate_host: NULL scene");
+    if (n_rx < 0) return fail(RT_ERR_ARG, "rt_evaluate_host: n_rx < 0");
+    if (n_rx == 0) return RT_OK;
+    if (!rx_soa || !e_out) return fail(RT_ERR_ARG, "rt_evaluate_host: NULL buffer");
+    if (!s->f_set) return fail(RT_ERR_STATE, "frequencies not set");
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t nf = s->freqs.size();
+    if ((size_t)n_rx > s->io_cap) {
+        cudaFree(s->io_rx); cudaFree(s->io_e); cudaFree(s->io_fl);
+        s->io_rx = nullptr; s->io_e = nullptr; s->io_fl = nullptr; s->io_cap = 0;
+        CK(cudaMalloc(&s->io_rx, sizeof(float) * 3 * (size_t)n_rx));
+        CK(cudaMalloc(&s->io_e, sizeof(float) * 2 * 3 * RT_MAX_FREQS * (size_t)n_rx));
+        CK(cudaMalloc(&s->io_fl, sizeof(uint32_t) * (size_t)n_rx));
+        s->io_cap = n_rx;
+    }
+    CK(cudaMemcpyAsync(s->io_rx, rx_soa, sizeof(float) * 3 * (size_t)n_rx, cudaMemcpyHostToDevice, st));
+    int rc = rt_evaluate(s, s->io_rx, n_rx, s->io_e, flags ? s->io_fl : nullptr, opt, stream);
+    if (rc != RT_OK) return rc;
+    CK(cudaMemcpyAsync(e_out, s->io_e, sizeof(float) * 2 * 3 * nf * (size_t)n_rx, cudaMemcpyDeviceToHost, st));
+    if (flags) CK(cudaMemcpyAsync(flags, s->io_fl, sizeof(uint32_t) * (size_t)n_rx, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return RT_OK;
+}
+
+int rt_get_stats(rt_scene *s, rt_stats *out) {
+    if (!s || !out) return fail(RT_ERR_ARG, "rt_get_stats: NULL argument");
+    CK(cudaStreamSynchronize(s->last_stream));
+    unsigned long long v = 0;
+    CK(cudaMemcpy(&v, s->d_esc, sizeof(v), cudaMemcpyDeviceToHost));
+    out->escalated_receivers = v;
+    return RT_OK;
+}
+
+int rt_fock_table(double *xi_lo, double *step, int *n, double *g, double *dg, double *res) {
+    DevTable *T = nullptr;
+    int rc = get_table(&T);
+    if (rc != RT_OK) return rc;
+    if (xi_lo) *xi_lo = XI_LO;
+    if (step) *step = XI_STEP;
+    if (n) *n = FOCK_N;
+    for (int j = 0; j < FOCK_N; ++j)
+        for (int k = 0; k < 2; ++k) {
+            const double *q = &T->host.tab[(j * 2 + k) * 4];
+            if (g) { g[(k * FOCK_N + j) * 2] = q[0]; g[(k * FOCK_N + j) * 2 + 1] = q[1]; }
+            if (dg) { dg[(k * FOCK_N + j) * 2] = q[2]; dg[(k * FOCK_N + j) * 2 + 1] = q[3]; }
+        }
+    if (res) memcpy(res, T->host.res.data(), sizeof(double) * 4 * FOCK_NRES);
+    return RT_OK;
+}
+
+}  // extern "C"

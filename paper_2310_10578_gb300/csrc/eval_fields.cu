@@ -1,0 +1,1318 @@
+// eval_fields.cu -- the per-receiver field kernel (sm_103a).
+//
+// One thread evaluates one receiver P: it enumerates the candidate ray paths
+// (direct; planar image reflections of order 1 and 2; per convex body the
+// GO reflection and the creeping ray each way round), decides each path's
+// existence and visibility, and sums the coherent field of the valid ones
+// over the frequencies of the launch (Eqs. 1-4 of the paper; the surface-ray
+// geometry of Fig. 1).  Scene geometry and the Fock--Pekeris table are
+// staged in shared memory per block.
+//
+// Precision (RT_PREC_FP32): geometry and field math in FP32; every
+// existence/visibility decision is computed with a margin in metres and is
+// taken in FP32 only when the margin exceeds a band that bounds the FP32
+// error; otherwise the whole candidate is re-evaluated in FP64 with exactly
+// the decision rules of the FP64 definition (ties: triangles and face
+// membership inclusive, bodies strict).  Path lengths are accumulated as
+// double-float so that the phase 2 pi frac(L / lambda) keeps ~1e-7 rad at
+// 28 GHz over tens of metres.  Reflection points near grazing incidence are
+// refined in FP64.  RT_PREC_FP64 runs everything in FP64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "devmath.cuh"
+#include "internal.h"
+
+namespace creep {
+
+#define EPS_TRIM 1e-6
+enum { D_NO = 0, D_YES = 1, D_UNSURE = 2 };
+enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5 };
+
+constexpr int NFC = 4;                 // frequencies per launch (accumulators in registers)
+constexpr int BLOCK = 128;
+constexpr int SMEM_TRI_MAX = 256;
+constexpr int SMEM_BODY_MAX = 256;
+
+__device__ __forceinline__ uint64_t pcode(int type, int a, int b) {
+    return ((uint64_t)type << 56) | ((uint64_t)a << 28) | (uint64_t)b;
+}
+
+// "m > 0" with an uncertainty band (band == 0: exact, ties -> tie)
+template <typename T>
+__device__ __forceinline__ int decide(T m, T band, int tie) {
+    if (m > band) return D_YES;
+    if (m < -band) return D_NO;
+    if (band > T(0)) return D_UNSURE;
+    return (m > T(0)) ? D_YES : ((m < T(0)) ? D_NO : tie);
+}
+
+// per-frequency constants of one launch
+struct FreqC {
+    float k[NFC], kh[NFC];       // wavenumber, (k/2)^{1/3}
+    float il_hi[NFC], il_lo[NFC];// 1/lambda as double-float
+    double kd[NFC], fc[NFC];     // FP64: wavenumber, f/c
+    int nf;
+};
+
+// scene view (pointers into shared or global memory)
+struct Ctx {
+    const float4 *tri, *tri_aux, *face32, *body;
+    const dq4 *face64;
+    const int2 *face_rng;
+    const int *face_tris;
+    int n_tri, n_face, n_body;
+    float band;
+    v3t<float> S, pol;
+    const float4 *fock;          // [FOCK_N][2]
+    const float4 *res;           // [FOCK_NRES][2]
+    const float *weid;
+    float weid_L;
+    const double2 *fock64;
+    const dq4 *res64;
+    const double *weid64;
+    const float4 *img;           // source images (double-float), see DevScene
+};
+
+template <typename T>
+__device__ __forceinline__ v3t<T> ld3(float4 q) { return mk3<T>(T((double)q.x), T((double)q.y), T((double)q.z)); }
+template <>
+__device__ __forceinline__ v3t<float> ld3<float>(float4 q) { return mk3<float>(q.x, q.y, q.z); }
+
+// ------------------------------------------------------------------ visibility
+// Segment A->B (t in [EPS, 1-EPS]) against a closed triangle.
+__device__ int seg_tri(const Ctx &c, int t, v3t<float> A, v3t<float> B, float band) {
+    float4 nq = c.tri_aux[3 * t];
+    v3t<float> n = mk3(nq.x, nq.y, nq.z);
+    float sA = dot3(n, A) - nq.w, sB = dot3(n, B) - nq.w;
+    if ((sA > band && sB > band) || (sA < -band && sB < -band)) return D_NO;
+    if (!((sA > band && sB < -band) || (sA < -band && sB > band))) return D_UNSURE;
+    v3t<float> v0 = ld3<float>(c.tri[3 * t]), v1 = ld3<float>(c.tri[3 * t + 1]), v2 = ld3<float>(c.tri[3 * t + 2]);
+    v3t<float> D = B - A, e1 = v1 - v0, e2 = v2 - v0;
+    v3t<float> pv = cross3(D, e2);
+    float inv = 1.0f / dot3(e1, pv);
+    v3t<float> tv = A - v0;
+    float u = dot3(tv, pv) * inv;
+    v3t<float> qv = cross3(tv, e1);
+    float v = dot3(D, qv) * inv;
+    float tt = dot3(e2, qv) * inv;
+    float4 alt = c.tri_aux[3 * t + 1];
+    float Dl = norm3(D);
+    float m = fminf(fminf(u * alt.y, v * alt.z), (1.0f - u - v) * alt.x);
+    m = fminf(m, fminf((tt - (float)EPS_TRIM) * Dl, (1.0f - (float)EPS_TRIM - tt) * Dl));
+    return decide(m, band, D_YES);
+}
+__device__ int seg_tri(const Ctx &c, int t, v3t<dx> A, v3t<dx> B, dx) {
+    v3t<dx> v0 = ld3<dx>(c.tri[3 * t]), v1 = ld3<dx>(c.tri[3 * t + 1]), v2 = ld3<dx>(c.tri[3 * t + 2]);
+    v3t<dx> D = B - A, e1 = v1 - v0, e2 = v2 - v0;
+    v3t<dx> pv = cross3(D, e2);
+    dx det = dot3(e1, pv);
+    if (det == dx(0.0)) return D_NO;
+    dx inv = dx(1.0) / det;
+    v3t<dx> tv = A - v0;
+    dx u = dot3(tv, pv) * inv;
+    if (u < dx(0.0) || u > dx(1.0)) return D_NO;
+    v3t<dx> qv = cross3(tv, e1);
+    dx v = dot3(D, qv) * inv;
+    if (v < dx(0.0) || u + v > dx(1.0)) return D_NO;
+    dx tt = dot3(e2, qv) * inv;
+    return (tt >= dx(EPS_TRIM) && tt <= dx(1.0) - dx(EPS_TRIM)) ? D_YES : D_NO;
+}
+
+// Segment vs open solid body (tangent touch does not obstruct)
+__device__ int seg_body(const Ctx &c, int b, v3t<float> A, v3t<float> B, float band) {
+    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
+    v3t<float> D = B - A;
+    if (q1.y == 0.0f) {   // sphere
+        v3t<float> w = mk3(q0.x - A.x, q0.y - A.y, q0.z - A.z);
+        float t = dot3(w, D) / dot3(D, D);
+        t = fminf(fmaxf(t, (float)EPS_TRIM), 1.0f - (float)EPS_TRIM);
+        v3t<float> q = D * t - w;
+        return decide(q0.w - norm3(q), band, D_NO);
+    }
+    float ox = A.x - q0.x, oy = A.y - q0.y;
+    float qa = D.x * D.x + D.y * D.y;
+    float od = ox * D.x + oy * D.y;
+    float tc = (qa > 0.0f) ? fminf(fmaxf(-od / qa, (float)EPS_TRIM), 1.0f - (float)EPS_TRIM) : (float)EPS_TRIM;
+    float hx = ox + tc * D.x, hy = oy + tc * D.y;
+    float m2 = q0.w - sqrtf(hx * hx + hy * hy);
+    if (m2 < -band) return D_NO;
+    if (m2 <= band) return D_UNSURE;
+    float t1 = -1e30f, t2 = 1e30f;
+    if (qa > 0.0f) {
+        float cr = ox * D.y - oy * D.x;
+        float half = sqrtf(fmaxf(q0.w * q0.w - cr * cr / qa, 0.0f)) / sqrtf(qa);
+        float tm = -od / qa;
+        t1 = tm - half; t2 = tm + half;
+    }
+    float t3 = -1e30f, t4 = 1e30f;
+    if (D.z == 0.0f) {
+        float mz = fminf(A.z - q0.z, q0.z + q1.x - A.z);
+        if (mz < -band) return D_NO;
+        if (mz <= band) return D_UNSURE;
+    } else {
+        float ta = (q0.z - A.z) / D.z, tb = (q0.z + q1.x - A.z) / D.z;
+        t3 = fminf(ta, tb); t4 = fmaxf(ta, tb);
+    }
+    float lo = fmaxf(fmaxf(t1, t3), (float)EPS_TRIM), hi = fminf(fminf(t2, t4), 1.0f - (float)EPS_TRIM);
+    return decide((hi - lo) * norm3(D), band, D_NO);
+}
+__device__ int seg_body(const Ctx &c, int b, v3t<dx> A, v3t<dx> B, dx) {
+    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
+    v3t<dx> D = B - A;
+    dx a = (double)q0.w;
+    if (q1.y == 0.0f) {
+        v3t<dx> w = mk3<dx>((double)q0.x, (double)q0.y, (double)q0.z) - A;
+        dx t = dot3(w, D) / dot3(D, D);
+        if (t < dx(EPS_TRIM)) t = dx(EPS_TRIM);
+        if (t > dx(1.0) - dx(EPS_TRIM)) t = dx(1.0) - dx(EPS_TRIM);
+        v3t<dx> q = (A + D * t) - mk3<dx>((double)q0.x, (double)q0.y, (double)q0.z);
+        return (dot3(q, q) < a * a) ? D_YES : D_NO;
+    }
+    dx lo = dx(EPS_TRIM), hi = dx(1.0) - dx(EPS_TRIM);
+    dx ox = A.x - dx((double)q0.x), oy = A.y - dx((double)q0.y);
+    dx qa = D.x * D.x + D.y * D.y, qb = dx(2.0) * (ox * D.x + oy * D.y), qc = ox * ox + oy * oy - a * a;
+    dx t1, t2;
+    if (qa == dx(0.0)) {
+        if (!(qc < dx(0.0))) return D_NO;
+        t1 = dx(-INFINITY); t2 = dx(INFINITY);
+    } else {
+        dx disc = qb * qb - dx(4.0) * qa * qc;
+        if (!(disc > dx(0.0))) return D_NO;
+        dx sq = Sqrt(disc);
+        t1 = (-qb - sq) / (dx(2.0) * qa);
+        t2 = (-qb + sq) / (dx(2.0) * qa);
+    }
+    dx cz = (double)q0.z, h = (double)q1.x;
+    dx t3, t4;
+    if (D.z == dx(0.0)) {
+        if (!(A.z > cz && A.z < cz + h)) return D_NO;
+        t3 = dx(-INFINITY); t4 = dx(INFINITY);
+    } else {
+        dx ta = (cz - A.z) / D.z, tb = (cz + h - A.z) / D.z;
+        t3 = Fmin(ta, tb); t4 = Fmax(ta, tb);
+    }
+    dx olo = Fmax(t1, t3), ohi = Fmin(t2, t4);
+    if (!(olo < ohi)) return D_NO;
+    return (olo < hi && ohi > lo) ? D_YES : D_NO;
+}
+
+// 0 visible, 1 blocked, 2 unsure.  Faces sf1/sf2 and body sb are skipped.
+template <typename T>
+__device__ int blocked(const Ctx &c, v3t<T> A, v3t<T> B, int sf1, int sf2, int sb, T band) {
+    int uns = 0;
+    for (int t = 0; t < c.n_tri; ++t) {
+        int f = __float_as_int(c.tri[3 * t].w);
+        if (f == sf1 || f == sf2) continue;
+        int r = seg_tri(c, t, A, B, band);
+        if (r == D_YES) return D_YES;
+        uns |= (r == D_UNSURE);
+    }
+    for (int b = 0; b < c.n_body; ++b) {
+        if (b == sb) continue;
+        int r = seg_body(c, b, A, B, band);
+        if (r == D_YES) return D_YES;
+        uns |= (r == D_UNSURE);
+    }
+    return uns ? D_UNSURE : D_NO;
+}
+
+// point (on the triangle's plane) inside the closed triangle
+__device__ int in_tri(const Ctx &c, int t, v3t<float> Q, float band) {
+    float4 nq = c.tri_aux[3 * t], il = c.tri_aux[3 * t + 2];
+    v3t<float> n = mk3(nq.x, nq.y, nq.z);
+    v3t<float> v0 = ld3<float>(c.tri[3 * t]), v1 = ld3<float>(c.tri[3 * t + 1]), v2 = ld3<float>(c.tri[3 * t + 2]);
+    float m0 = dot3(cross3(v1 - v0, Q - v0), n) * il.x;
+    float m1 = dot3(cross3(v2 - v1, Q - v1), n) * il.y;
+    float m2 = dot3(cross3(v0 - v2, Q - v2), n) * il.z;
+    return decide(fminf(fminf(m0, m1), m2), band, D_YES);
+}
+__device__ int in_tri(const Ctx &c, int t, v3t<dx> Q, dx) {
+    v3t<dx> v0 = ld3<dx>(c.tri[3 * t]), v1 = ld3<dx>(c.tri[3 * t + 1]), v2 = ld3<dx>(c.tri[3 * t + 2]);
+    v3t<dx> n = cross3(v1 - v0, v2 - v0);
+    if (dot3(cross3(v1 - v0, Q - v0), n) < dx(0.0)) return D_NO;
+    if (dot3(cross3(v2 - v1, Q - v1), n) < dx(0.0)) return D_NO;
+    if (dot3(cross3(v0 - v2, Q - v2), n) < dx(0.0)) return D_NO;
+    return D_YES;
+}
+template <typename T>
+__device__ int in_face(const Ctx &c, int f, v3t<T> Q, T band) {
+    int2 r = c.face_rng[f];
+    int uns = 0;
+    for (int i = 0; i < r.y; ++i) {
+        int d = in_tri(c, c.face_tris[r.x + i], Q, band);
+        if (d == D_YES) return D_YES;
+        uns |= (d == D_UNSURE);
+    }
+    return uns ? D_UNSURE : D_NO;
+}
+
+template <typename T> __device__ __forceinline__ void face_plane(const Ctx &c, int f, v3t<T> *n, T *d);
+template <> __device__ __forceinline__ void face_plane<float>(const Ctx &c, int f, v3t<float> *n, float *d) {
+    float4 q = c.face32[f]; *n = mk3(q.x, q.y, q.z); *d = q.w;
+}
+template <> __device__ __forceinline__ void face_plane<dx>(const Ctx &c, int f, v3t<dx> *n, dx *d) {
+    dq4 q = c.face64[f]; *n = mk3<dx>(q.x, q.y, q.z); *d = dx(q.w);
+}
+
+// combine a new decision into a running conjunction; returns false to stop (definite NO)
+__device__ __forceinline__ bool conj(int &acc, int d) {
+    if (d == D_NO) { acc = D_NO; return false; }
+    if (d == D_UNSURE) acc = D_UNSURE;
+    return true;
+}
+__device__ __forceinline__ int vis_to_dec(int blk) { return blk == D_NO ? D_YES : (blk == D_YES ? D_NO : D_UNSURE); }
+
+// ------------------------------------------------------------------ candidate geometry
+template <typename T>
+struct Geo {
+    v3t<T> Q1, Q2, n1, n2;
+    T sp, t, sq, amp, rho_g, inv_f1, inv_f2, dperp;
+    int caus;
+    dfl Lf;          // FP32 mode: total path length as double-float (reflection off a body)
+};
+
+template <typename T>
+__device__ __forceinline__ v3t<T> mirror_pt(v3t<T> X, v3t<T> n, T d) {
+    T dist = dot3(n, X) - d;
+    return X - n * (T(2) * dist);
+}
+
+// signs of a and b strictly equal (want_same) or strictly opposite
+template <typename T>
+__device__ __forceinline__ int side_dec(T a, T b, T band, bool want_same) {
+    if (band > T(0)) {
+        if (Fabs(a) <= band || Fabs(b) <= band) return D_UNSURE;
+        bool same = (a > 0) == (b > 0);
+        return (same == want_same) ? D_YES : D_NO;
+    }
+    T p = a * b;
+    return want_same ? (p > T(0) ? D_YES : D_NO) : (p < T(0) ? D_YES : D_NO);
+}
+
+template <typename T>
+__device__ int cand_los(const Ctx &c, v3t<T> S, v3t<T> P, T band) {
+    return vis_to_dec(blocked(c, S, P, -1, -1, -1, band));
+}
+
+template <typename T>
+__device__ int cand_r1(const Ctx &c, int i, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
+    v3t<T> n; T d;
+    face_plane<T>(c, i, &n, &d);
+    T dS = dot3(n, S) - d, dP = dot3(n, P) - d;
+    int acc = D_YES;
+    if (!conj(acc, side_dec(dS, dP, band, true))) return D_NO;
+    v3t<T> S1 = mirror_pt(S, n, d);
+    T d1 = dot3(n, S1) - d;
+    T t = d1 / (d1 - dP);
+    v3t<T> Q = S1 + (P - S1) * t;
+    if (!conj(acc, in_face(c, i, Q, band))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, S, Q, i, -1, -1, band)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, Q, P, i, -1, -1, band)))) return D_NO;
+    g.Q1 = Q;
+    return acc;
+}
+
+template <typename T>
+__device__ int cand_r2(const Ctx &c, int i, int j, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
+    v3t<T> ni, nj; T di, dj;
+    face_plane<T>(c, i, &ni, &di);
+    face_plane<T>(c, j, &nj, &dj);
+    v3t<T> S1 = mirror_pt(S, ni, di);
+    v3t<T> S2 = mirror_pt(S1, nj, dj);
+    T d2 = dot3(nj, S2) - dj, dP = dot3(nj, P) - dj;
+    int acc = D_YES;
+    if (!conj(acc, side_dec(d2, dP, band, false))) return D_NO;
+    T t2 = d2 / (d2 - dP);
+    v3t<T> Q2 = S2 + (P - S2) * t2;
+    if (!conj(acc, in_face(c, j, Q2, band))) return D_NO;
+    T e1 = dot3(ni, S1) - di, eq = dot3(ni, Q2) - di;
+    if (!conj(acc, side_dec(e1, eq, band, false))) return D_NO;
+    T t1 = e1 / (e1 - eq);
+    v3t<T> Q1 = S1 + (Q2 - S1) * t1;
+    if (!conj(acc, in_face(c, i, Q1, band))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, S, Q1, i, -1, -1, band)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, Q1, Q2, i, j, -1, band)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, Q2, P, j, -1, -1, band)))) return D_NO;
+    g.Q1 = Q1; g.Q2 = Q2;
+    return acc;
+}
+
+// frame of the (S, c, P) problem: u towards S, v towards P (sphere: 3-D; cylinder: horizontal)
+template <typename T>
+struct Frame {
+    v3t<T> u, v;
+    T ds, dp, gam, bs, bp, pu, pv;
+    bool axis_ok;   // v well conditioned (P not near the S-c axis)
+};
+
+template <typename T>
+__device__ void sphere_frame(v3t<T> S, v3t<T> P, v3t<T> cc, T a, Frame<T> &F, T band) {
+    v3t<T> ws = S - cc, wp = P - cc;
+    F.ds = norm3(ws); F.dp = norm3(wp);
+    F.u = ws * (T(1) / F.ds);
+    F.gam = Atan2(norm3(cross3(ws, wp)), dot3(ws, wp));
+    v3t<T> vp = wp - F.u * dot3(wp, F.u);
+    T nv = norm3(vp);
+    F.axis_ok = (band > T(0)) ? (nv > T(1e-3) * F.dp) : true;
+    if (nv == T(0)) {
+        v3t<T> tmp = (Fabs(F.u.x) < T(0.9)) ? mk3<T>(1, 0, 0) : mk3<T>(0, 1, 0);
+        F.v = unit3(cross3(F.u, tmp));
+    } else {
+        F.v = vp * (T(1) / nv);
+    }
+    F.bs = Acos(a / F.ds); F.bp = Acos(a / F.dp);
+    F.pu = dot3(wp, F.u); F.pv = dot3(wp, F.v);
+}
+
+template <typename T>
+__device__ void cyl_frame(v3t<T> S, v3t<T> P, T cx, T cy, T a, Frame<T> &F, T band) {
+    T sx = S.x - cx, sy = S.y - cy, px = P.x - cx, py = P.y - cy;
+    F.ds = Sqrt(sx * sx + sy * sy); F.dp = Sqrt(px * px + py * py);
+    F.u = mk3<T>(sx / F.ds, sy / F.ds, T(0));
+    F.gam = Atan2(Fabs(sx * py - sy * px), sx * px + sy * py);
+    T pd = px * F.u.x + py * F.u.y;
+    T wx = px - pd * F.u.x, wy = py - pd * F.u.y;
+    T nw = Sqrt(wx * wx + wy * wy);
+    F.axis_ok = (band > T(0)) ? (nw > T(1e-3) * F.dp) : true;
+    F.v = (nw == T(0)) ? mk3<T>(-F.u.y, F.u.x, T(0)) : mk3<T>(wx / nw, wy / nw, T(0));
+    F.bs = Acos(a / F.ds); F.bp = Acos(a / F.dp);
+    F.pu = px * F.u.x + py * F.u.y; F.pv = px * F.v.x + py * F.v.y;
+}
+
+// 2-D reflection point psi on the circle of radius a, S = (ds, 0), P = (pu, pv):
+// root of dL/dpsi in (0, gam).  FP32: safeguarded Newton; FP64: bisection to
+// double resolution.
+__device__ float refl_psi(float a, float ds, float pu, float pv, float gam, float *err_est) {
+    float lo = 0.0f, hi = gam;
+    float gmag = 0.0f, curv = 1.0f;
+    // start at the direction of u_S + u_P
+    float dpn = sqrtf(pu * pu + pv * pv);
+    float psi = atan2f(pv / dpn, 1.0f + pu / dpn);
+    for (int it = 0; it < 24; ++it) {
+        float sn, cs;
+        sincosf(psi, &sn, &cs);
+        float qx = a * cs, qy = a * sn, tx = -a * sn, ty = a * cs;
+        float sx = qx - ds, sy = qy, rx = qx - pu, ry = qy - pv;
+        float fs = sqrtf(sx * sx + sy * sy), fr = sqrtf(rx * rx + ry * ry);
+        float gs = (sx * tx + sy * ty) / fs, gr = (rx * tx + ry * ty) / fr;
+        float g = gs + gr;
+        // d2L/dpsi2 = sum (X.Q - f'^2)/f
+        float g2 = (ds * qx - gs * gs) / fs + (pu * qx + pv * qy - gr * gr) / fr;
+        gmag = fabsf(gs) + fabsf(gr) + a;
+        curv = g2;
+        if (g == 0.0f) break;
+        if (g < 0.0f) lo = psi; else hi = psi;
+        float nx = psi - g / g2;
+        if (!(g2 > 0.0f) || nx < lo || nx > hi) nx = 0.5f * (lo + hi);
+        if (fabsf(nx - psi) <= 2e-7f * fmaxf(fabsf(psi), 1e-3f)) { psi = nx; break; }
+        psi = nx;
+    }
+    // FP32 root error: rounding noise of dL/dpsi over its slope
+    *err_est = (curv > 0.0f) ? 8.0f * 1.2e-7f * gmag / curv + 2e-7f * fabsf(psi) : 1.0f;
+    return psi;
+}
+__device__ dx refl_psi(dx a, dx ds, dx pu, dx pv, dx gam) {
+    dx lo = dx(0.0), hi = gam;
+    for (int it = 0; it < 200; ++it) {
+        dx mid = dx(0.5) * (lo + hi);
+        if (!(mid > lo && mid < hi)) break;
+        dx sn, cs;
+        SinCos(mid, &sn, &cs);
+        dx qx = a * cs, qy = a * sn, tx = -(a * sn), ty = a * cs;
+        dx sx = qx - ds, sy = qy, rx = qx - pu, ry = qy - pv;
+        dx g = (sx * tx + sy * ty) / Sqrt(sx * sx + sy * sy) + (rx * tx + ry * ty) / Sqrt(rx * rx + ry * ry);
+        if (g < dx(0.0)) lo = mid; else hi = mid;
+    }
+    return dx(0.5) * (lo + hi);
+}
+// FP64 Newton polish of an FP32 root (near-grazing reflection points)
+__device__ float refl_psi_polish(float a, float ds, float pu, float pv, float gam, float psi0) {
+    double lo = 0.0, hi = gam, psi = psi0;
+    for (int it = 0; it < 12; ++it) {
+        double sn, cs;
+        sincos(psi, &sn, &cs);
+        double qx = a * cs, qy = a * sn, tx = -a * sn, ty = a * cs;
+        double sx = qx - ds, sy = qy, rx = qx - pu, ry = qy - pv;
+        double fs = sqrt(sx * sx + sy * sy), fr = sqrt(rx * rx + ry * ry);
+        double gs = (sx * tx + sy * ty) / fs, gr = (rx * tx + ry * ty) / fr;
+        double g = gs + gr;
+        if (g == 0.0) break;
+        if (g < 0.0) lo = psi; else hi = psi;
+        double g2 = ((double)ds * qx - gs * gs) / fs + ((double)pu * qx + (double)pv * qy - gr * gr) / fr;
+        double nx = psi - g / g2;
+        if (!(g2 > 0.0) || nx < lo || nx > hi) nx = 0.5 * (lo + hi);
+        if (fabs(nx - psi) <= 1e-15 * fabs(psi)) { psi = nx; break; }
+        psi = nx;
+    }
+    return (float)psi;
+}
+
+// body reflection candidate (sphere or vertical cylinder)
+template <typename T>
+__device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
+    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
+    T a = q0.w;
+    Frame<T> F;
+    int acc = D_YES;
+    bool sphere = (q1.y == 0.0f);
+    if (sphere) {
+        sphere_frame(S, P, mk3<T>(q0.x, q0.y, q0.z), a, F, band);
+    } else {
+        T rs = Sqrt((S.x - (T)q0.x) * (S.x - (T)q0.x) + (S.y - (T)q0.y) * (S.y - (T)q0.y));
+        if (!conj(acc, decide(rs - a, band, D_NO))) return D_NO;
+        T rp = Sqrt((P.x - (T)q0.x) * (P.x - (T)q0.x) + (P.y - (T)q0.y) * (P.y - (T)q0.y));
+        if (!conj(acc, decide(rp - a, band, D_NO))) return D_NO;
+        cyl_frame(S, P, (T)q0.x, (T)q0.y, a, F, band);
+    }
+    if (!F.axis_ok) return D_UNSURE;       // frame ill-conditioned: decide in FP64
+    T dplus = F.gam - F.bs - F.bp;
+    if (!conj(acc, decide(-dplus * a, band, D_NO))) return D_NO;      // strictly lit
+    T psi;
+    float psi_err = 0.0f;
+    if constexpr (sizeof(T) == 4) psi = refl_psi(a, F.ds, F.pu, F.pv, F.gam, &psi_err);
+    else psi = refl_psi(a, F.ds, F.pu, F.pv, F.gam);
+    T sn, cs;
+    SinCos(psi, &sn, &cs);
+    if constexpr (sizeof(T) == 4) {
+        // incidence cosine (2-D, horizontal for cylinders): refine the root in FP64
+        // when its FP32 error would exceed 1e-6 of cos(theta_i) (near grazing)
+        float c2 = (F.ds * cs - a) / sqrtf((a * cs - F.ds) * (a * cs - F.ds) + a * a * sn * sn);
+        if (psi_err > 1e-6f * fmaxf(c2, 0.0f)) {
+            psi = refl_psi_polish(a, F.ds, F.pu, F.pv, F.gam, psi);
+            SinCos(psi, &sn, &cs);
+        }
+    }
+    v3t<T> n = F.u * cs + F.v * sn;
+    v3t<T> Q;
+    if (sphere) {
+        Q = mk3<T>(T((double)q0.x), T((double)q0.y), T((double)q0.z)) + n * a;
+    } else {
+        T qx = a * cs, qy = a * sn;
+        T l1 = Sqrt((qx - F.ds) * (qx - F.ds) + qy * qy);
+        T l2 = Sqrt((qx - F.pu) * (qx - F.pu) + (qy - F.pv) * (qy - F.pv));
+        T zq = S.z + (P.z - S.z) * l1 / (l1 + l2);
+        if (!conj(acc, decide(zq - T((double)q0.z), band, D_YES))) return D_NO;
+        if (!conj(acc, decide(T((double)q0.z) + T((double)q1.x) - zq, band, D_YES))) return D_NO;
+        Q = mk3<T>(T((double)q0.x) + a * n.x, T((double)q0.y) + a * n.y, zq);
+    }
+    v3t<T> shi = unit3(Q - S);
+    T cth = -dot3(shi, n);
+    if constexpr (sizeof(T) == 4) {
+        // total length s^i + s^r from the body-centred frame (stationary in psi,
+        // so the FP32 root error enters at second order; the large squares are
+        // exact double-float): |X - Q|^2 = |X - c|^2 + a^2 - 2 a (X - c).n
+        dfl a2 = two_prod(a, a);
+        float cpsi = cs, spsi = sn;
+        if (sphere) {
+            dfl ds2 = df_add(df_add(df_sq_diff(S.x, q0.x), df_sq_diff(S.y, q0.y)), df_sq_diff(S.z, q0.z));
+            dfl dp2 = df_add(df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y)), df_sq_diff(P.z, q0.z));
+            dfl si = df_sqrt(df_addf(df_add(ds2, a2), -2.0f * a * F.ds * cpsi));
+            dfl sr = df_sqrt(df_addf(df_add(dp2, a2), -2.0f * a * (F.pu * cpsi + F.pv * spsi)));
+            g.Lf = df_add(si, sr);
+        } else {
+            dfl ds2 = df_add(df_sq_diff(S.x, q0.x), df_sq_diff(S.y, q0.y));
+            dfl dp2 = df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y));
+            dfl l1 = df_sqrt(df_addf(df_add(ds2, a2), -2.0f * a * F.ds * cpsi));
+            dfl l2 = df_sqrt(df_addf(df_add(dp2, a2), -2.0f * a * (F.pu * cpsi + F.pv * spsi)));
+            dfl H = df_add(l1, l2);
+            g.Lf = df_sqrt(df_add(df_mul(H, H), df_sq_diff(P.z, S.z)));
+        }
+    }
+    if (!conj(acc, vis_to_dec(blocked(c, S, Q, -1, -1, b, band)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, Q, P, -1, -1, b, band)))) return D_NO;
+    g.Q1 = Q; g.n1 = n;
+    if (sphere) {
+        g.inv_f1 = T(2) / (a * cth);
+        g.inv_f2 = T(2) * cth / a;
+        g.rho_g = a;
+    } else {
+        g.inv_f1 = T(2) * (T(1) - shi.z * shi.z) / (a * cth);
+        g.inv_f2 = T(0);
+        T sphi = -shi.x * n.y + shi.y * n.x;     // s_i . phi_hat, phi_hat = z x n
+        g.rho_g = (sphi == T(0)) ? T(INFINITY) : a * (T(1) - cth * cth) / (sphi * sphi);
+    }
+    return acc;
+}
+
+// creeping candidate, dir 0 short way, 1 long way
+template <typename T>
+__device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
+    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
+    T a = q0.w;
+    bool sphere = (q1.y == 0.0f);
+    Frame<T> F;
+    int acc = D_YES;
+    if (sphere) {
+        sphere_frame(S, P, mk3<T>(q0.x, q0.y, q0.z), a, F, band);
+    } else {
+        T rs = Sqrt((S.x - (T)q0.x) * (S.x - (T)q0.x) + (S.y - (T)q0.y) * (S.y - (T)q0.y));
+        if (!conj(acc, decide(rs - a, band, D_NO))) return D_NO;
+        T rp = Sqrt((P.x - (T)q0.x) * (P.x - (T)q0.x) + (P.y - (T)q0.y) * (P.y - (T)q0.y));
+        if (!conj(acc, decide(rp - a, band, D_NO))) return D_NO;
+        cyl_frame(S, P, (T)q0.x, (T)q0.y, a, F, band);
+    }
+    if (!F.axis_ok) return D_UNSURE;       // frame ill-conditioned: decide in FP64
+    const T TWO_PI_T = T(6.283185307179586476925286766559);
+    T dpsi = (dir == 0) ? (F.gam - F.bs - F.bp) : (TWO_PI_T - F.gam - F.bs - F.bp);
+    if (!conj(acc, decide(dpsi * a, band, D_NO))) return D_NO;
+    T psi1 = (dir == 0) ? F.bs : -F.bs;
+    T psi2 = (dir == 0) ? F.gam - F.bp : F.gam + F.bp;
+    T s1, c1, s2, c2;
+    SinCos(psi1, &s1, &c1);
+    SinCos(psi2, &s2, &c2);
+    g.n1 = F.u * c1 + F.v * s1;
+    g.n2 = F.u * c2 + F.v * s2;
+    if (sphere) {
+        v3t<T> cc = mk3<T>(q0.x, q0.y, q0.z);
+        g.Q1 = cc + g.n1 * a;
+        g.Q2 = cc + g.n2 * a;
+        g.sp = Sqrt(F.ds * F.ds - a * a);
+        g.sq = Sqrt(F.dp * F.dp - a * a);
+        g.t = a * dpsi;
+        g.rho_g = a;
+        g.caus = (dir == 1);
+        if (band > T(0)) {
+            g.dperp = F.pv;                      // distance of P from the S-c axis
+        } else {
+            T sg, cg; SinCos(F.gam, &sg, &cg);
+            g.dperp = F.dp * sg;
+        }
+        T dq1 = a * Sqrt(Fmax(T(0), T(1) - (a / F.ds) * (a / F.ds)));   // a sin(beta_s)
+        if (band == T(0)) { T sb, cb; SinCos(F.bs, &sb, &cb); dq1 = a * sb; }
+        g.amp = (g.dperp > T(0)) ? Sqrt(dq1 / g.dperp) / Sqrt(g.sq) / g.sp : T(0);
+    } else {
+        T ds_ = Sqrt(F.ds * F.ds - a * a), dp_ = Sqrt(F.dp * F.dp - a * a);
+        T dz = P.z - S.z;
+        T H = ds_ + a * dpsi + dp_;
+        T ell = Sqrt(H * H + dz * dz);
+        T sin0 = H / ell;
+        T z1 = S.z + dz * ds_ / H, z2 = S.z + dz * (ds_ + a * dpsi) / H;
+        T cz = q0.z, top = (T)q0.z + (T)q1.x;
+        if (!conj(acc, decide(z1 - cz, band, D_YES))) return D_NO;
+        if (!conj(acc, decide(top - z1, band, D_YES))) return D_NO;
+        if (!conj(acc, decide(z2 - cz, band, D_YES))) return D_NO;
+        if (!conj(acc, decide(top - z2, band, D_YES))) return D_NO;
+        g.Q1 = mk3<T>((T)q0.x + a * g.n1.x, (T)q0.y + a * g.n1.y, z1);
+        g.Q2 = mk3<T>((T)q0.x + a * g.n2.x, (T)q0.y + a * g.n2.y, z2);
+        g.sp = ds_ / sin0; g.t = a * dpsi / sin0; g.sq = dp_ / sin0;
+        g.rho_g = a / (sin0 * sin0);
+        g.caus = 0;
+        g.dperp = T(0);
+        g.amp = T(1) / Sqrt(g.sp * g.sq * (g.sp + g.t + g.sq));
+    }
+    if (!conj(acc, vis_to_dec(blocked(c, S, g.Q1, -1, -1, b, band)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, g.Q2, P, -1, -1, b, band)))) return D_NO;
+    return acc;
+}
+
+// ------------------------------------------------------------------ Fock functions
+// Weideman's rational approximation of w(z) = e^{-z^2} erfc(-jz), Im z > 0:
+// w ~ 2 p(Z)/(L - jz)^2 + 1/(sqrt(pi) (L - jz)), Z = (L + jz)/(L - jz).
+template <typename T>
+__device__ cpx<T> faddeeva(const Ctx &c, cpx<T> z);
+template <>
+__device__ cpx<float> faddeeva<float>(const Ctx &c, cpx<float> z) {
+    float L = c.weid_L;
+    cpx<float> lm = mkc(L + z.im, -z.re), lp = mkc(L - z.im, z.re);
+    cpx<float> Z = cdiv(lp, lm);
+    cpx<float> p = mkc(c.weid[WEIDEMAN_N - 1], 0.0f);
+    for (int n = WEIDEMAN_N - 2; n >= 0; --n) p = p * Z + mkc(c.weid[n], 0.0f);
+    cpx<float> r = cdiv(p * 2.0f, lm * lm) + cdiv(mkc(0.56418958354775628f, 0.0f), lm);
+    return r;
+}
+// Fock--Pekeris functions at xi >= XI_LO.  regular = true returns phat = P + c/xi,
+// false returns P itself (each computed without cancellation in its domain).
+__device__ void pekeris(const Ctx &c, float xi, cpx<float> &ps, cpx<float> &ph, bool regular) {
+    const float ci = 0.19947114f / xi;                 // c/xi = e^{-j pi/4}/(2 sqrt(pi) xi) = (ci, -ci)
+    if (xi > (float)XI_HI) {
+        cpx<float> ss = mkc(0.f, 0.f), sh = mkc(0.f, 0.f);
+        for (int n = 0; n < FOCK_NRES; ++n) {
+            float4 rs = c.res[2 * n], rh = c.res[2 * n + 1];
+            float sn, cs;
+            sincosf(xi * rs.y, &sn, &cs);
+            float e = expf(-xi * rs.x) * rs.z;
+            ss = ss + mkc(e * cs, -e * sn);
+            sincosf(xi * rh.y, &sn, &cs);
+            e = expf(-xi * rh.x) * rh.z;
+            sh = sh + mkc(e * cs, -e * sn);
+        }
+        const cpx<float> pre = mkc(-0.27248264483602590f, 0.07301150463530957f);   // -e^{-j pi/12}/(2 sqrt(pi))
+        ps = pre * ss;
+        ph = pre * sh;
+        if (regular) { ps = ps + mkc(ci, -ci); ph = ph + mkc(ci, -ci); }
+        return;
+    }
+    float u = (xi - (float)XI_LO) * (float)(1.0 / XI_STEP);
+    int j = min(max((int)u, 0), FOCK_N - 2);
+    float t = u - (float)j;
+    float t2 = t * t, omt = 1.0f - t;
+    float h00 = (1.0f + 2.0f * t) * omt * omt, h10 = t * omt * omt, h01 = t2 * (3.0f - 2.0f * t), h11 = t2 * (t - 1.0f);
+    float4 a0 = c.fock[2 * j], a1 = c.fock[2 * j + 2];
+    float4 b0 = c.fock[2 * j + 1], b1 = c.fock[2 * j + 3];
+    cpx<float> Gs = mkc(h00 * a0.x + h10 * a0.z + h01 * a1.x + h11 * a1.z, h00 * a0.y + h10 * a0.w + h01 * a1.y + h11 * a1.w);
+    cpx<float> Gh = mkc(h00 * b0.x + h10 * b0.z + h01 * b1.x + h11 * b1.z, h00 * b0.y + h10 * b0.w + h01 * b1.y + h11 * b1.w);
+    float sn, cs;
+    sincosf(xi * xi * xi * (1.0f / 12.0f), &sn, &cs);   // e^{+j xi^3/12}
+    cpx<float> rot = mkc(cs, sn);
+    ps = Gs * rot;
+    ph = Gh * rot;
+    if (!regular) { ps = ps - mkc(ci, -ci); ph = ph - mkc(ci, -ci); }
+}
+__device__ void pekeris(const Ctx &c, dx xid, cpx<dx> &psd, cpx<dx> &phd, bool regular) {
+    double xi = xid.v;
+    const double ci = (0.5 / sqrt(M_PI)) * cos(M_PI / 4.0) / xi;
+    cpx<double> ps, ph;
+    if (xi > XI_HI) {
+        cpx<double> ss = mkc(0.0, 0.0), sh = mkc(0.0, 0.0);
+        for (int n = 0; n < FOCK_NRES; ++n) {
+            dq4 rs = c.res64[2 * n], rh = c.res64[2 * n + 1];
+            double sn, cs;
+            sincos(xi * rs.y, &sn, &cs);
+            double e = exp(-xi * rs.x) * rs.z;
+            ss = ss + mkc(e * cs, -e * sn);
+            sincos(xi * rh.y, &sn, &cs);
+            e = exp(-xi * rh.x) * rh.z;
+            sh = sh + mkc(e * cs, -e * sn);
+        }
+        cpx<double> pre = mkc(-cos(M_PI / 12.0), sin(M_PI / 12.0)) * (0.5 / sqrt(M_PI));
+        ps = pre * ss;
+        ph = pre * sh;
+        if (regular) { ps = ps + mkc(ci, -ci); ph = ph + mkc(ci, -ci); }
+    } else {
+        double u = (xi - XI_LO) / XI_STEP;
+        int j = min(max((int)u, 0), FOCK_N - 2);
+        double t = u - j, t2 = t * t, omt = 1.0 - t;
+        double h00 = (1 + 2 * t) * omt * omt, h10 = t * omt * omt * XI_STEP, h01 = t2 * (3 - 2 * t), h11 = t2 * (t - 1) * XI_STEP;
+        cpx<double> G[2];
+        for (int k = 0; k < 2; ++k) {
+            double2 g0 = c.fock64[(j * 2 + k) * 2], d0 = c.fock64[(j * 2 + k) * 2 + 1];
+            double2 g1 = c.fock64[((j + 1) * 2 + k) * 2], d1 = c.fock64[((j + 1) * 2 + k) * 2 + 1];
+            G[k] = mkc(h00 * g0.x + h10 * d0.x + h01 * g1.x + h11 * d1.x, h00 * g0.y + h10 * d0.y + h01 * g1.y + h11 * d1.y);
+        }
+        double sn, cs;
+        sincos(xi * xi * xi / 12.0, &sn, &cs);
+        ps = G[0] * mkc(cs, sn);
+        ph = G[1] * mkc(cs, sn);
+        if (!regular) { ps = ps - mkc(ci, -ci); ph = ph - mkc(ci, -ci); }
+    }
+    psd = mkc<dx>(ps.re, ps.im);
+    phd = mkc<dx>(ph.re, ph.im);
+}
+
+__device__ __forceinline__ cpx<dx> faddeeva_dx(const Ctx &c, cpx<dx> zd) {
+    cpx<double> z = mkc(zd.re.v, zd.im.v);
+    double L = c.weid_L;
+    cpx<double> lm = mkc(L + z.im, -z.re), lp = mkc(L - z.im, z.re);
+    cpx<double> Z = cdiv(lp, lm);
+    cpx<double> p = mkc(c.weid64[WEIDEMAN_N - 1], 0.0);
+    for (int n = WEIDEMAN_N - 2; n >= 0; --n) p = p * Z + mkc(c.weid64[n], 0.0);
+    cpx<double> r = cdiv(p * 2.0, lm * lm) + cdiv(mkc(0.56418958354775628, 0.0), lm);
+    return mkc<dx>(r.re, r.im);
+}
+__device__ __forceinline__ cpx<float> faddeeva_t(const Ctx &c, cpx<float> z) { return faddeeva<float>(c, z); }
+__device__ __forceinline__ cpx<dx> faddeeva_t(const Ctx &c, cpx<dx> z) { return faddeeva_dx(c, z); }
+
+// Fock bracket B = P + (c/xi)(1 - F(X)) = phat - c F(X)/xi with sqrt(X) = K |xi|.
+// X <= 4: phat - c F/xi, F/xi = sgn(xi) sqrt(pi) K e^{j pi/4} w(e^{j 3pi/4} K |xi|).
+// X > 4: P + (c/xi)(1 - F), 1 - F from w (X < 30) or from the asymptotic series
+// 1 - F ~ -sum_{n>=1} (2n-1)!! (j/(2X))^n (X >= 30, 8 terms): no cancellation
+// between two O(c/xi) terms.
+template <typename T>
+__device__ void fock_bracket(const Ctx &c, T xi, T K, cpx<T> &Bs, cpx<T> &Bh) {
+    const T r2 = T(0.70710678118654752440), spi = T(1.7724538509055160273), cc = T(0.19947114020071633897);
+    T sx = K * Fabs(xi);
+    T X = sx * sx;
+    cpx<T> ps, ph;
+    if (!(X > T(4))) {
+        pekeris(c, xi, ps, ph, true);
+        cpx<T> w = faddeeva_t(c, mkc<T>(-(sx * r2), sx * r2));
+        T s = (xi >= T(0) ? T(1) : T(-1)) * spi * K * r2;
+        cpx<T> fx = w * mkc<T>(s, s);                      // F/xi
+        cpx<T> cf = mkc<T>(cc * (fx.re + fx.im), cc * (fx.im - fx.re));   // (1 - j) cc * fx
+        Bs = ps - cf;
+        Bh = ph - cf;
+        return;
+    }
+    pekeris(c, xi, ps, ph, false);
+    cpx<T> omf;                                            // 1 - F(X)
+    if (X >= T(30)) {
+        T u = T(0.5) / X;                                  // j/(2X) = j u
+        cpx<T> acc = mkc<T>(T(1), T(0));
+        for (int n = 8; n >= 2; --n) {                     // 1 + (2n-1) j u (...)
+            T f = T(2 * n - 1) * u;
+            acc = mkc<T>(T(1) - f * acc.im, f * acc.re);
+        }
+        omf = mkc<T>(u * acc.im, -(u * acc.re));           // -(j u) acc
+    } else {
+        cpx<T> w = faddeeva_t(c, mkc<T>(-(sx * r2), sx * r2));
+        T s = Sqrt(T(3.14159265358979323846) * X) * r2;   // sqrt(pi X) e^{j pi/4}
+        cpx<T> F = w * mkc<T>(s, s);
+        omf = mkc<T>(T(1) - F.re, -F.im);
+    }
+    T ci = cc / xi;
+    cpx<T> cterm = mkc<T>(ci * (omf.re + omf.im), ci * (omf.im - omf.re));   // (1 - j) ci (1 - F)
+    Bs = ps + cterm;
+    Bh = ph + cterm;
+}
+
+// ------------------------------------------------------------------ field accumulation
+template <typename T>
+struct Acc {
+    cpx<T> E[NFC][3];
+};
+
+template <typename T>
+__device__ __forceinline__ v3t<T> src_pol(const Ctx &c, v3t<T> d) {
+    v3t<T> p = mk3<T>(c.pol.x, c.pol.y, c.pol.z);
+    v3t<T> pt = p - d * dot3(p, d);
+    T n = norm3(pt);
+    return (n > T(0)) ? pt * (T(1) / n) : mk3<T>(0, 0, 0);
+}
+template <typename T>
+__device__ __forceinline__ v3t<T> pec_mirror(v3t<T> e, v3t<T> n) {
+    return n * (T(2) * dot3(n, e)) - e;
+}
+
+// path length representation: FP32 mode carries double-float
+struct LenF { dfl L; };
+struct LenD { dx L; };
+
+__device__ __forceinline__ cpx<float> phasor(const FreqC &fq, int f, dfl L) {
+    dfl il; il.hi = fq.il_hi[f]; il.lo = fq.il_lo[f];
+    dfl cyc = df_mul(L, il);
+    float n = floorf(cyc.hi);
+    float fr = (cyc.hi - n) + cyc.lo;
+    fr -= floorf(fr);
+    float s, co;
+    sincospif(2.0f * fr, &s, &co);
+    return mkc(co, -s);
+}
+__device__ __forceinline__ cpx<dx> phasor(const FreqC &fq, int f, dx Ld) {
+    double L = Ld.v;
+    double cyc = L * fq.fc[f];
+    double fr = cyc - floor(cyc);
+    double s, co;
+    sincospi(2.0 * fr, &s, &co);
+    return mkc<dx>(co, -s);
+}
+__device__ __forceinline__ float len_val(dfl L) { return L.hi + L.lo; }
+__device__ __forceinline__ dx len_val(dx L) { return L; }
+__device__ __forceinline__ float kof(const FreqC &fq, int f, float) { return fq.k[f]; }
+__device__ __forceinline__ dx kof(const FreqC &fq, int f, dx) { return dx(fq.kd[f]); }
+__device__ __forceinline__ float khof(const FreqC &fq, int f, float) { return fq.kh[f]; }
+__device__ __forceinline__ dx khof(const FreqC &fq, int f, dx) { return dx(cbrt(fq.kd[f] * 0.5)); }
+
+// segment length helpers
+__device__ __forceinline__ dfl seglen(v3t<float> a, v3t<float> b) { return df_dist(a, b); }
+__device__ __forceinline__ dx seglen(v3t<dx> a, v3t<dx> b) { return norm3(b - a); }
+__device__ __forceinline__ dfl ladd(dfl a, dfl b) { return df_add(a, b); }
+__device__ __forceinline__ dx ladd(dx a, dx b) { return a + b; }
+__device__ __forceinline__ dfl laddf(dfl a, float b) { return df_addf(a, b); }
+__device__ __forceinline__ dx laddf(dx a, dx b) { return a + b; }
+__device__ __forceinline__ dfl lsqrt_diff_sq(float d, float a) {    // sqrt(d^2 - a^2)
+    dfl s = two_prod(d, d), t = two_prod(a, a);
+    t.hi = -t.hi; t.lo = -t.lo;
+    return df_sqrt(df_add(s, t));
+}
+__device__ __forceinline__ dx lsqrt_diff_sq(dx d, dx a) { return Sqrt(d * d - a * a); }
+
+template <typename T, typename L>
+__device__ __forceinline__ void add_ray(Acc<T> &acc, const FreqC &fq, v3t<T> e, T amp, L len) {
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+        if (f < fq.nf) {
+            cpx<T> ph = phasor(fq, f, len) * amp;
+            acc.E[f][0] = acc.E[f][0] + ph * e.x;
+            acc.E[f][1] = acc.E[f][1] + ph * e.y;
+            acc.E[f][2] = acc.E[f][2] + ph * e.z;
+        }
+    }
+}
+
+template <typename T, typename L>
+__device__ void field_body_refl(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S, v3t<T> P, const Geo<T> &g, L len) {
+    v3t<T> Q = g.Q1, n = g.n1;
+    v3t<T> di = Q - S, dr = P - Q;
+    T si = norm3(di), sr = norm3(dr);
+    v3t<T> shi = di * (T(1) / si), shr = dr * (T(1) / sr);
+    T cth = -dot3(shi, n);
+    v3t<T> ep = cross3(n, shi);
+    T ne = norm3(ep);
+    if (ne == T(0)) {
+        v3t<T> tmp = (Fabs(n.x) < T(0.9)) ? mk3<T>(1, 0, 0) : mk3<T>(0, 1, 0);
+        ep = unit3(cross3(n, tmp));
+    } else {
+        ep = ep * (T(1) / ne);
+    }
+    v3t<T> epi = cross3(ep, shi), epr = cross3(ep, shr);
+    v3t<T> e0 = src_pol(c, shi);
+    T Es = dot3(e0, ep), Eh = dot3(e0, epi);
+    T rho1 = T(1) / (T(1) / si + g.inv_f1), rho2 = T(1) / (T(1) / si + g.inv_f2);
+    T A = Sqrt(rho1 * rho2 / ((rho1 + sr) * (rho2 + sr))) / si;
+    T Lp = si * sr / (si + sr);
+    T rcb = Cbrt(g.rho_g);
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+        if (f < fq.nf) {
+            T k = kof(fq, f, T(0));
+            T m = khof(fq, f, T(0)) * rcb;
+            T xi = T(-2) * m * cth;
+            cpx<T> Rs, Rh;
+            if (!(xi >= T(XI_LO))) {
+                Rs = mkc<T>(-1, 0); Rh = mkc<T>(1, 0);
+            } else {
+                cpx<T> Bs, Bh;
+                fock_bracket<T>(c, xi, Sqrt(k * Lp / (T(2) * m * m)), Bs, Bh);
+                T sn, cs;
+                SinCos(-xi * xi * xi / T(12), &sn, &cs);
+                cpx<T> pre = mkc<T>(cs, sn) * (-Sqrt(T(-4) / xi));
+                Rs = pre * Bs; Rh = pre * Bh;
+            }
+            cpx<T> ph = phasor(fq, f, len) * A;
+            cpx<T> as = Rs * ph * Es, ah = Rh * ph * Eh;
+            acc.E[f][0] = acc.E[f][0] + as * ep.x + ah * epr.x;
+            acc.E[f][1] = acc.E[f][1] + as * ep.y + ah * epr.y;
+            acc.E[f][2] = acc.E[f][2] + as * ep.z + ah * epr.z;
+        }
+    }
+}
+
+template <typename T, typename L>
+__device__ void field_creep(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S, v3t<T> P, const Geo<T> &g,
+                            L len, unsigned enable) {
+    v3t<T> t1 = unit3(g.Q1 - S), t2 = unit3(P - g.Q2);
+    v3t<T> b1 = cross3(t1, g.n1), b2 = cross3(t2, g.n2);
+    v3t<T> e0 = src_pol(c, t1);
+    T Es = dot3(e0, b1), Eh = dot3(e0, g.n1);
+    if (!(enable & RT_EN_CREEP_SOFT)) Es = T(0);
+    if (!(enable & RT_EN_CREEP_HARD)) Eh = T(0);
+    T Lp = g.sp * g.sq / (g.sp + g.sq);
+    T rcb = Cbrt(g.rho_g);
+    T tr = g.t / g.rho_g;
+#pragma unroll
+    for (int f = 0; f < NFC; ++f) {
+        if (f < fq.nf) {
+            T k = kof(fq, f, T(0));
+            T m = khof(fq, f, T(0)) * rcb;
+            T xi = m * tr;
+            cpx<T> Bs, Bh;
+            fock_bracket<T>(c, xi, Sqrt(k * Lp / (T(2) * m * m)), Bs, Bh);
+            // T = -m sqrt(2/k) B e^{-jkt}; e^{-jkt} is inside the path phasor (len includes t)
+            T pre = -m * Sqrt(T(2) / k) * g.amp;
+            cpx<T> ph = phasor(fq, f, len) * pre;
+            if (g.caus) ph = mkc<T>(-ph.im, ph.re);          // x (+j)
+            cpx<T> as = Bs * ph * Es, ah = Bh * ph * Eh;
+            acc.E[f][0] = acc.E[f][0] + as * b2.x + ah * g.n2.x;
+            acc.E[f][1] = acc.E[f][1] + as * b2.y + ah * g.n2.y;
+            acc.E[f][2] = acc.E[f][2] + as * b2.z + ah * g.n2.z;
+        }
+    }
+}
+
+// total creeping path length s' + t + s
+__device__ __forceinline__ dfl creep_len(const Ctx &c, int b, v3t<float> S, v3t<float> P, const Geo<float> &g) {
+    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
+    if (q1.y == 0.0f) {
+        dfl ds2 = df_add(df_add(df_sq_diff(S.x, q0.x), df_sq_diff(S.y, q0.y)), df_sq_diff(S.z, q0.z));
+        dfl dp2 = df_add(df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y)), df_sq_diff(P.z, q0.z));
+        dfl a2 = two_prod(q0.w, q0.w);
+        a2.hi = -a2.hi; a2.lo = -a2.lo;
+        dfl sp = df_sqrt(df_add(ds2, a2)), sq = df_sqrt(df_add(dp2, a2));
+        return df_addf(df_add(sp, sq), g.t);
+    }
+    // cylinder: unrolled straight line, sqrt(H^2 + dz^2), H = d_s + a dphi + d_p
+    dfl rs2 = df_add(df_sq_diff(S.x, q0.x), df_sq_diff(S.y, q0.y));
+    dfl rp2 = df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y));
+    dfl a2 = two_prod(q0.w, q0.w);
+    a2.hi = -a2.hi; a2.lo = -a2.lo;
+    dfl ds_ = df_sqrt(df_add(rs2, a2)), dp_ = df_sqrt(df_add(rp2, a2));
+    // a dphi = t sin(theta0), sin(theta0) = d_s / s'
+    float adphi = g.t * (len_val(ds_) / g.sp);
+    dfl H = df_addf(df_add(ds_, dp_), adphi);
+    dfl dz2 = df_sq_diff(P.z, S.z);
+    dfl H2 = df_mul(H, H);
+    return df_sqrt(df_add(H2, dz2));
+}
+__device__ __forceinline__ dx creep_len(const Ctx &, int, v3t<dx>, v3t<dx>, const Geo<dx> &g) {
+    return g.sp + g.t + g.sq;
+}
+
+__device__ __forceinline__ void len_from(double x, dfl *L) { L->hi = (float)x; L->lo = (float)(x - (double)L->hi); }
+__device__ __forceinline__ void len_from(double x, dx *L) { *L = dx(x); }
+
+template <typename T> struct LenOf;
+template <> struct LenOf<float> { typedef dfl type; };
+template <> struct LenOf<dx> { typedef dx type; };
+
+// FP64 geometry -> FP32 (escalated candidates feed the FP32 field code)
+__device__ __forceinline__ v3t<float> to_f3(v3t<dx> a) { return mk3<float>(to_float(a.x), to_float(a.y), to_float(a.z)); }
+__device__ __forceinline__ Geo<float> to_f(const Geo<dx> &d) {
+    Geo<float> g;
+    g.Q1 = to_f3(d.Q1); g.Q2 = to_f3(d.Q2); g.n1 = to_f3(d.n1); g.n2 = to_f3(d.n2);
+    g.sp = to_float(d.sp); g.t = to_float(d.t); g.sq = to_float(d.sq); g.amp = to_float(d.amp);
+    g.rho_g = to_float(d.rho_g); g.inv_f1 = to_float(d.inv_f1); g.inv_f2 = to_float(d.inv_f2);
+    g.dperp = to_float(d.dperp); g.caus = d.caus;
+    return g;
+}
+__device__ __forceinline__ dfl to_df(double x) {
+    dfl r;
+    r.hi = (float)x;
+    r.lo = (float)(x - (double)r.hi);
+    return r;
+}
+
+__device__ __forceinline__ void acc_add(Acc<float> &a, const Acc<dx> &b, int nf) {
+#pragma unroll
+    for (int f = 0; f < NFC; ++f)
+        if (f < nf)
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                a.E[f][q] = a.E[f][q] + mkc<float>(to_float(b.E[f][q].re), to_float(b.E[f][q].im));
+}
+__device__ __forceinline__ void acc_zero(Acc<dx> &a) {
+#pragma unroll
+    for (int f = 0; f < NFC; ++f)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) a.E[f][q] = mkc<dx>(0.0, 0.0);
+}
+
+// ------------------------------------------------------------------ kernel
+template <typename T, bool PATHS>
+__global__ void __launch_bounds__(BLOCK) k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e_out,
+                                               uint32_t *__restrict__ flags_out, uint64_t *__restrict__ codes,
+                                               int32_t *__restrict__ counts, int cap, int f0, FreqC fq,
+                                               double half_lambda_max, unsigned long long *esc_counter) {
+    extern __shared__ float4 smem[];
+    // stage scene and table
+    float4 *s_fock = smem;                                   // FOCK_N * 2
+    float4 *s_res = s_fock + FOCK_N * 2;                     // FOCK_NRES * 2
+    float4 *s_face = s_res + FOCK_NRES * 2;                  // n_face
+    float4 *s_body = s_face + S.n_face;                      // n_body * 2 (if staged)
+    bool body_sm = S.n_body <= SMEM_BODY_MAX;
+    float4 *s_tri = s_body + (body_sm ? 2 * S.n_body : 0);   // n_tri * 3 (if staged)
+    bool tri_sm = S.n_tri <= SMEM_TRI_MAX;
+    float4 *s_aux = s_tri + (tri_sm ? 3 * S.n_tri : 0);      // n_tri * 3 (if staged)
+    float *s_weid = (float *)(s_aux + (tri_sm ? 3 * S.n_tri : 0));
+    for (int i = threadIdx.x; i < FOCK_N * 2; i += blockDim.x) s_fock[i] = S.fock32[i];
+    for (int i = threadIdx.x; i < FOCK_NRES * 2; i += blockDim.x) s_res[i] = S.res32[i];
+    for (int i = threadIdx.x; i < S.n_face; i += blockDim.x) s_face[i] = S.face32[i];
+    if (body_sm)
+        for (int i = threadIdx.x; i < 2 * S.n_body; i += blockDim.x) s_body[i] = S.body[i];
+    if (tri_sm)
+        for (int i = threadIdx.x; i < 3 * S.n_tri; i += blockDim.x) {
+            s_tri[i] = S.tri[i];
+            s_aux[i] = S.tri_alt[i];
+        }
+    for (int i = threadIdx.x; i < WEIDEMAN_N; i += blockDim.x) s_weid[i] = S.weid[i];
+    __syncthreads();
+
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_rx) return;
+
+    Ctx c;
+    c.tri = tri_sm ? s_tri : S.tri;
+    c.tri_aux = tri_sm ? s_aux : S.tri_alt;
+    c.face32 = s_face;
+    c.face64 = S.face64;
+    c.face_rng = S.face_rng;
+    c.face_tris = S.face_tris;
+    c.body = body_sm ? s_body : S.body;
+    c.n_tri = S.n_tri; c.n_face = S.n_face; c.n_body = S.n_body;
+    c.band = S.band_len;
+    c.S = mk3(S.tx[0], S.tx[1], S.tx[2]);
+    c.pol = mk3(S.pol[0], S.pol[1], S.pol[2]);
+    c.fock = s_fock; c.res = s_res; c.weid = s_weid; c.weid_L = S.weid_L;
+    c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
+    c.img = S.img;
+
+    const T band = (sizeof(T) == 4) ? (T)S.band_len : T(0);
+    v3t<float> Pf = mk3(rx[r], rx[n_rx + r], rx[2 * n_rx + r]);
+    v3t<T> P = mk3<T>(Pf.x, Pf.y, Pf.z);
+    v3t<T> Sx = mk3<T>(c.S.x, c.S.y, c.S.z);
+    uint32_t fl = 0;
+    int npath = 0;
+    Acc<T> acc;
+#pragma unroll
+    for (int f = 0; f < NFC; ++f)
+        for (int q = 0; q < 3; ++q) acc.E[f][q] = mkc<T>(0, 0);
+
+    auto emit = [&](int type, int a, int b) {
+        if (PATHS) {
+            if (npath < cap) codes[(size_t)r * cap + npath] = pcode(type, a, b);
+            else fl |= RT_FLAG_OVERFLOW;
+        }
+        ++npath;
+    };
+
+    // receiver inside a body?
+    int inside = 0;
+    for (int b = 0; b < S.n_body && !inside; ++b) {
+        float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
+        int d;
+        if (q1.y == 0.0f) {
+            T ex = P.x - (T)q0.x, ey = P.y - (T)q0.y, ez = P.z - (T)q0.z;
+            if (band > T(0)) d = decide((T)q0.w - Sqrt(ex * ex + ey * ey + ez * ez), band, D_YES);
+            else d = (ex * ex + ey * ey + ez * ez <= (T)q0.w * (T)q0.w) ? D_YES : D_NO;
+        } else {
+            T ex = P.x - (T)q0.x, ey = P.y - (T)q0.y;
+            if (band > T(0)) {
+                T m = Fmin(Fmin((T)q0.w - Sqrt(ex * ex + ey * ey), P.z - (T)q0.z), (T)q0.z + (T)q1.x - P.z);
+                d = decide(m, band, D_YES);
+            } else {
+                d = (ex * ex + ey * ey <= (T)q0.w * (T)q0.w && P.z >= (T)q0.z && P.z <= (T)q0.z + (T)q1.x) ? D_YES : D_NO;
+            }
+        }
+        if (d == D_UNSURE) {
+            fl |= RT_FLAG_ESCALATED;
+            dx ex = dx((double)Pf.x) - dx((double)q0.x), ey = dx((double)Pf.y) - dx((double)q0.y),
+               ez = dx((double)Pf.z) - dx((double)q0.z), a = dx((double)q0.w);
+            if (q1.y == 0.0f) d = (ex * ex + ey * ey + ez * ez <= a * a) ? D_YES : D_NO;
+            else d = (ex * ex + ey * ey <= a * a && dx((double)Pf.z) >= dx((double)q0.z) &&
+                      dx((double)Pf.z) <= dx((double)q0.z) + dx((double)q1.x)) ? D_YES : D_NO;
+        }
+        inside = (d == D_YES);
+    }
+    typedef typename LenOf<T>::type LT;
+    v3t<dx> Pd = mk3<dx>((double)Pf.x, (double)Pf.y, (double)Pf.z), Sd = mk3<dx>((double)c.S.x, (double)c.S.y, (double)c.S.z);
+    const dx zero_band = dx(0.0);
+
+    if (inside) {
+        fl |= RT_FLAG_INSIDE;
+    } else {
+        // ---- direct ray
+        if (S.enable & RT_EN_LOS) {
+            int d = cand_los<T>(c, Sx, P, band);
+            if (d == D_UNSURE) { fl |= RT_FLAG_ESCALATED; d = cand_los<dx>(c, Sd, Pd, zero_band); }
+            if (d == D_YES) {
+                emit(PT_LOS, 0, 0);
+                if (!PATHS) {
+                    LT L = seglen(Sx, P);
+                    add_ray(acc, fq, src_pol(c, unit3(P - Sx)), T(1) / (T)len_val(L), L);
+                }
+            }
+        }
+        // ---- planar image reflections
+        if ((S.enable & RT_EN_PLANAR) && S.max_order >= 1) {
+            for (int i = 0; i < S.n_face; ++i) {
+                Geo<T> g;
+                int d = cand_r1<T>(c, i, Sx, P, band, g);
+                if (d == D_UNSURE) {
+                    fl |= RT_FLAG_ESCALATED;
+                    Geo<dx> gd;
+                    d = cand_r1<dx>(c, i, Sd, Pd, zero_band, gd);
+                    if constexpr (sizeof(T) == 4) g.Q1 = to_f3(gd.Q1);
+                }
+                if (d == D_YES) {
+                    emit(PT_R1, i, 0);
+                    if (!PATHS) {
+                        v3t<T> ni; T di;
+                        face_plane<T>(c, i, &ni, &di);
+                        LT L;
+                        if constexpr (sizeof(T) == 4) L = df_dist_df(c.img[2 * i], c.img[2 * i + 1], Pf);
+                        else L = ladd(seglen(Sx, g.Q1), seglen(g.Q1, P));
+                        add_ray(acc, fq, pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni), T(1) / (T)len_val(L), L);
+                    }
+                }
+            }
+        }
+        if ((S.enable & RT_EN_PLANAR) && S.max_order >= 2) {
+            for (int i = 0; i < S.n_face; ++i) {
+                for (int j = 0; j < S.n_face; ++j) {
+                    if (j == i) continue;
+                    Geo<T> g;
+                    int d = cand_r2<T>(c, i, j, Sx, P, band, g);
+                    if (d == D_UNSURE) {
+                        fl |= RT_FLAG_ESCALATED;
+                        Geo<dx> gd;
+                        d = cand_r2<dx>(c, i, j, Sd, Pd, zero_band, gd);
+                        if constexpr (sizeof(T) == 4) { g.Q1 = to_f3(gd.Q1); g.Q2 = to_f3(gd.Q2); }
+                    }
+                    if (d == D_YES) {
+                        emit(PT_R2, i, j);
+                        if (!PATHS) {
+                            v3t<T> ni, nj; T di, dj;
+                            face_plane<T>(c, i, &ni, &di);
+                            face_plane<T>(c, j, &nj, &dj);
+                            LT L;
+                            if constexpr (sizeof(T) == 4) {
+                                int slot = S.n_face + i * S.n_face + j;
+                                L = df_dist_df(c.img[2 * slot], c.img[2 * slot + 1], Pf);
+                            } else {
+                                L = ladd(ladd(seglen(Sx, g.Q1), seglen(g.Q1, g.Q2)), seglen(g.Q2, P));
+                            }
+                            v3t<T> e = pec_mirror(pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni), nj);
+                            add_ray(acc, fq, e, T(1) / (T)len_val(L), L);
+                        }
+                    }
+                }
+            }
+        }
+        // ---- curved bodies
+        for (int b = 0; b < S.n_body; ++b) {
+            if (S.enable & RT_EN_BODYREFL) {
+                Geo<T> g;
+                int d = cand_rb<T>(c, b, Sx, P, band, g);
+                if constexpr (sizeof(T) == 4) {
+                    if (d == D_UNSURE) {
+                        // decided in FP64; its field too (the geometry may be
+                        // ill-conditioned in FP32, e.g. a receiver at a surface)
+                        fl |= RT_FLAG_ESCALATED;
+                        Geo<dx> gd;
+                        d = cand_rb<dx>(c, b, Sd, Pd, zero_band, gd);
+                        if (d == D_YES) {
+                            emit(PT_RB, b, 0);
+                            if (!PATHS) {
+                                Acc<dx> a2;
+                                acc_zero(a2);
+                                field_body_refl<dx>(c, a2, fq, Sd, Pd, gd, seglen(Sd, gd.Q1) + seglen(gd.Q1, Pd));
+                                acc_add(acc, a2, fq.nf);
+                            }
+                        }
+                        d = D_NO;
+                    }
+                }
+                if (d == D_YES) {
+                    emit(PT_RB, b, 0);
+                    if (!PATHS) {
+                        LT L;
+                        if constexpr (sizeof(T) == 4) L = g.Lf;
+                        else L = ladd(seglen(Sx, g.Q1), seglen(g.Q1, P));
+                        field_body_refl<T>(c, acc, fq, Sx, P, g, L);
+                    }
+                }
+            }
+            if (S.enable & (RT_EN_CREEP_SOFT | RT_EN_CREEP_HARD)) {
+                for (int dir = 0; dir < 2; ++dir) {
+                    Geo<T> g;
+                    int d = cand_creep<T>(c, b, dir, Sx, P, band, g);
+                    bool esc = false;
+                    Geo<dx> gd = {};
+                    if constexpr (sizeof(T) == 4) {
+                        if (d == D_UNSURE) {
+                            fl |= RT_FLAG_ESCALATED;
+                            esc = true;
+                            d = cand_creep<dx>(c, b, dir, Sd, Pd, zero_band, gd);
+                            if (d == D_YES) g = to_f(gd);
+                        }
+                    }
+                    if (d != D_YES) continue;
+                    emit(dir == 0 ? PT_CP : PT_CM, b, 0);
+                    if (c.body[2 * b + 1].y == 0.0f) {
+                        // axial caustic flag: k d_perp < pi for some frequency, i.e. d_perp < lambda_max / 2
+                        int cd;
+                        if constexpr (sizeof(T) == 8) {
+                            cd = (half_lambda_max > to_double(g.dperp)) ? D_YES : D_NO;
+                        } else {
+                            cd = esc ? ((half_lambda_max > gd.dperp.v) ? D_YES : D_NO)
+                                     : decide((T)half_lambda_max - g.dperp, band, D_NO);
+                            if (cd == D_UNSURE) {
+                                fl |= RT_FLAG_ESCALATED;
+                                cand_creep<dx>(c, b, dir, Sd, Pd, zero_band, gd);
+                                cd = (half_lambda_max > gd.dperp.v) ? D_YES : D_NO;
+                            }
+                        }
+                        if (cd == D_YES) fl |= RT_FLAG_CAUSTIC;
+                        if (!(g.dperp > T(0))) continue;
+                    }
+                    if (!PATHS) {
+                        if constexpr (sizeof(T) == 4) {
+                            if (esc) {
+                                Acc<dx> a2;
+                                acc_zero(a2);
+                                field_creep<dx>(c, a2, fq, Sd, Pd, gd, gd.sp + gd.t + gd.sq, S.enable);
+                                acc_add(acc, a2, fq.nf);
+                                continue;
+                            }
+                        }
+                        LT L = creep_len(c, b, Sx, P, g);
+                        field_creep<T>(c, acc, fq, Sx, P, g, L, S.enable);
+                    }
+                }
+            }
+        }
+    }
+    if (PATHS) {
+        counts[r] = npath;
+    } else {
+#pragma unroll
+        for (int f = 0; f < NFC; ++f) {
+            if (f < fq.nf) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    size_t idx = ((size_t)(f0 + f) * 3 + q) * n_rx + r;
+                    float2 v;
+                    v.x = to_float(acc.E[f][q].re);
+                    v.y = to_float(acc.E[f][q].im);
+                    reinterpret_cast<float2 *>(e_out)[idx] = v;
+                }
+            }
+        }
+    }
+    if (flags_out && (f0 == 0)) flags_out[r] = fl;
+    if (esc_counter && (fl & RT_FLAG_ESCALATED) && f0 == 0) atomicAdd(esc_counter, 1ull);
+}
+
+static size_t smem_bytes(const DevScene &S) {
+    size_t n = FOCK_N * 2 + FOCK_NRES * 2 + S.n_face;
+    if (S.n_body <= SMEM_BODY_MAX) n += 2 * S.n_body;
+    if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;
+    return n * sizeof(float4) + WEIDEMAN_N * sizeof(float) + 16;
+}
+
+int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
+                uint64_t *codes, int32_t *counts, int cap, int precision, unsigned long long *esc_counter,
+                cudaStream_t stream) {
+    if (n_rx <= 0) return RT_OK;
+    size_t sm = smem_bytes(S);
+    int grid = (n_rx + BLOCK - 1) / BLOCK;
+    double hl = 0.0;
+    for (int f = 0; f < S.n_f; ++f) {
+        double lam = 299792458.0 / S.freq[f];
+        if (lam / 2.0 > hl) hl = lam / 2.0;
+    }
+    bool paths = codes != nullptr;
+    int nchunks = paths ? 1 : (S.n_f + NFC - 1) / NFC;
+    for (int ch = 0; ch < nchunks; ++ch) {
+        FreqC fq;
+        fq.nf = paths ? 0 : ((S.n_f - ch * NFC) < NFC ? (S.n_f - ch * NFC) : NFC);
+        for (int f = 0; f < NFC; ++f) {
+            double fr = (f < fq.nf) ? S.freq[ch * NFC + f] : S.freq[0];
+            double k = 2.0 * M_PI * fr / 299792458.0;
+            double il = fr / 299792458.0;
+            fq.k[f] = (float)k;
+            fq.kh[f] = (float)cbrt(k / 2.0);
+            fq.il_hi[f] = (float)il;
+            fq.il_lo[f] = (float)(il - (double)fq.il_hi[f]);
+            fq.kd[f] = k;
+            fq.fc[f] = il;
+        }
+        int f0 = ch * NFC;
+        cudaError_t e;
+        if (precision == RT_PREC_FP64) {
+            if (paths) {
+                cudaFuncSetAttribute(k_eval<dx, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                k_eval<dx, true><<<grid, BLOCK, sm, stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, esc_counter);
+            } else {
+                cudaFuncSetAttribute(k_eval<dx, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                k_eval<dx, false><<<grid, BLOCK, sm, stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, esc_counter);
+            }
+        } else {
+            if (paths) {
+                cudaFuncSetAttribute(k_eval<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                k_eval<float, true><<<grid, BLOCK, sm, stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, esc_counter);
+            } else {
+                cudaFuncSetAttribute(k_eval<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                k_eval<float, false><<<grid, BLOCK, sm, stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, esc_counter);
+            }
+        }
+        e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            set_error(std::string("k_eval launch: ") + cudaGetErrorString(e));
+            return RT_ERR_CUDA;
+        }
+    }
+    return RT_OK;
+}
+
+}  // namespace creep

@@ -1,0 +1,76 @@
+// internal.h -- declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/creep.h"
+
+namespace creep {
+
+// 4 doubles (the CUDA vector type of that shape is deprecated in CUDA 13)
+struct __align__(16) dq4 {
+    double x, y, z, w;
+};
+inline dq4 make_dq4(double x, double y, double z, double w) { dq4 r; r.x = x; r.y = y; r.z = z; r.w = w; return r; }
+
+// Fock--Pekeris table domain (smooth-surface UTD coefficients).  Below XI_LO
+// the reflection coefficients take their GO values -1 / +1; above XI_HI the
+// residue (creeping-mode) series is summed instead of the table.
+constexpr double XI_LO = -10.0;
+constexpr double XI_HI = 1.5;
+constexpr double XI_STEP = 1.0 / 64.0;
+constexpr int FOCK_N = 737;            // (XI_HI - XI_LO) / XI_STEP + 1
+constexpr int FOCK_NBUCKET = 11;       // quadrature buckets: [0, XI_HI], [-1, 0), ..., [-10, -9)
+constexpr int FOCK_NRES = 8;           // residue-series terms
+constexpr int WEIDEMAN_N = 16;         // terms of the rational approximation of w(z)
+
+struct FockHost {
+    std::vector<double> tab;   // [FOCK_N][2][4]: G.re, G.im, G'.re, G'.im (soft, hard)
+    std::vector<double> res;   // [4][FOCK_NRES]: alpha, 1/Ai'(-alpha)^2, beta, 1/(beta Ai(-beta)^2)
+    int n_nodes = 0;
+};
+
+void set_error(const std::string &msg);
+int build_fock_table(FockHost *T);
+
+// Face (planar reflector) data
+struct FaceHost {
+    double n[3], d;            // unit normal and offset, from the face's first triangle
+    int first, count;          // range in the face -> triangle index list
+};
+
+// Device-side scene description passed to the field kernel by value.
+struct DevScene {
+    int n_tri, n_face, n_body, n_f;
+    const float4 *tri;         // [n_tri][3]: v0 (w: face id bits), v1 (w: altitude over edge v1v2... see tri_alt), v2
+    const float4 *tri_alt;     // [n_tri]: altitudes h0 (v0 over v1v2), h1, h2 and unit-normal inverse scale
+    const float4 *tri_nrm;     // [n_tri]: unit normal (xyz), offset n.v0 (w)
+    const float4 *face32;      // [n_face]: unit normal, offset (FP32)
+    const dq4 *face64;     // [n_face]: unit normal, offset (FP64)
+    const int2 *face_rng;      // [n_face]: first, count in face_tris
+    const int *face_tris;      // [n_tri]
+    const float4 *body;        // [n_body][2]: (cx, cy, cz, a), (h, type, 0, 0)
+    const float4 *fock32;      // [FOCK_N][2]: (G.re, G.im, h G'.re, h G'.im) soft, hard
+    const double2 *fock64;     // [FOCK_N][2][2]: G, G' (soft, hard)
+    const float4 *res32;       // [FOCK_NRES][2]: (alpha sqrt3/2, alpha/2, coef, 0) soft, hard
+    const dq4 *res64;      // [FOCK_NRES][2]
+    const float *weid;         // [WEIDEMAN_N]
+    const double *weid64;      // [WEIDEMAN_N]
+    float weid_L;
+    const float4 *img;         // [n_face + n_face^2][2]: source images (hi, lo) as double-float:
+                               // [f] mirror of Tx in face f; [n_face + i n_face + j] in i then j
+    const double *freq;        // [n_f] Hz (host copy, read by the launcher)
+    float tx[3], pol[3];
+    float band_len;            // FP32 decision band (m)
+    int max_order;
+    unsigned enable;
+};
+
+int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
+                uint64_t *codes, int32_t *counts, int cap, int precision, unsigned long long *esc_counter,
+                cudaStream_t stream);
+
+}  // namespace creep

@@ -1,0 +1,183 @@
+"""GPU path (libcreep.so through the C ABI) against the FP64 oracle.
+
+Bit-exact: path lists (which direct, reflected and creeping rays exist and are
+visible, Eqs. 1-2) and the semantic receiver flags.  Fields: the bound of
+tests/parity.py (derived from the FP32 arithmetic) on every receiver, and
+|E| within 0.05 dB, phase within 1e-3 rad where the coherent sum is well
+conditioned.
+"""
+import numpy as np
+import pytest
+
+from parity import compare_fields, compare_paths, gpu_fields
+from paper_2310_10578_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def creep():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_10578_gb300 import creep as c
+    c.load()
+    return c
+
+
+def _run(creep, sc, opts=None, cap=256):
+    S = creep.Scene.from_scene(sc)
+    rx = torch.tensor(sc.rx_soa(), device="cuda")
+    n = sc.n_rx
+    fl = torch.zeros(n, dtype=torch.int32, device="cuda")
+    if opts is None:
+        opts = creep.options(max_order=sc.max_order)
+    E = S.evaluate(rx, flags=fl, opts=opts)
+    codes, counts, fl2 = S.paths(rx, cap=cap, opts=opts)
+    torch.cuda.synchronize()
+    return S, gpu_fields(E), codes, counts, fl.cpu().numpy().astype(np.uint32), fl2.cpu().numpy().astype(np.uint32)
+
+
+def _flags_equal(fl, ref):
+    sem = 1 | 2
+    assert np.array_equal(fl & sem, ref.flags & sem), np.where((fl & sem) != (ref.flags & sem))[0][:10]
+
+
+def test_fock_table_matches_oracle(creep):
+    from scipy.special import ai_zeros
+    from oracle import fock
+    xi_lo, step, G, dG, res = creep.fock_table()
+    n = G.shape[1]
+    xi = xi_lo + step * np.arange(n)
+    assert abs(xi[-1] - fock.XI_HI) < 1e-12 and xi_lo == fock.XI_LO
+    for k, hard in ((0, False), (1, True)):
+        ph = np.array([fock.phat(x, hard) for x in xi])
+        ref = ph * np.exp(-1j * xi ** 3 / 12)
+        assert np.max(np.abs(G[k] - ref)) < 1e-10
+        h = 1e-5
+        xs = xi[5:-5:7]
+        num = (np.array([fock.phat(x + h, hard) * np.exp(-1j * (x + h) ** 3 / 12) for x in xs]) -
+               np.array([fock.phat(x - h, hard) * np.exp(-1j * (x - h) ** 3 / 12) for x in xs])) / (2 * h)
+        assert np.max(np.abs(dG[k][5:-5:7] - num)) < 1e-6
+    a, ap, ai, aip = ai_zeros(8)
+    assert np.allclose(res[0], -a, rtol=1e-13) and np.allclose(res[2], -ap, rtol=1e-13)
+    assert np.allclose(res[1], 1 / aip ** 2, rtol=1e-11) and np.allclose(res[3], 1 / (-ap * ai ** 2), rtol=1e-11)
+
+
+@pytest.mark.parametrize("pol", [(0, 0, 1.0), (0, 1.0, 0)])
+def test_sphere_ring_parity(creep, oracle_mod, pol):
+    sc = scenes.sphere_ring(n_rx=4096, pol=pol)
+    S, Eg, codes, counts, fl, fl2 = _run(creep, sc)
+    ref = oracle_mod.evaluate(sc)
+    compare_paths(codes, counts, ref)
+    _flags_equal(fl, ref)
+    _flags_equal(fl2, ref)
+    st = compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs)
+    assert st["n_cmp"] > 2500
+
+
+def test_room_parity_small(creep, oracle_mod):
+    # 20 cylinders, 61 x 47 receivers (ragged last block), three frequencies
+    sc = scenes.room(n_cyl=20, nx=61, ny=47)
+    S, Eg, codes, counts, fl, fl2 = _run(creep, sc)
+    ref = oracle_mod.evaluate(sc)
+    npaths = compare_paths(codes, counts, ref)
+    assert npaths > 20 * sc.n_rx
+    _flags_equal(fl, ref)
+    compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs)
+
+
+def test_room_parity_full_size_sampled(creep, oracle_mod):
+    """The 256 x 256 grid evaluated in one launch on the GPU, compared at a
+    sample of receivers the oracle computes one by one."""
+    sc = scenes.room()
+    S, Eg, codes, counts, fl, _ = _run(creep, sc)
+    rng = np.random.default_rng(3)
+    idx = np.unique(np.concatenate([rng.choice(sc.n_rx, 1500, replace=False),
+                                    [0, 127, 128, sc.n_rx - 129, sc.n_rx - 1]]))
+    sub = sc.subset(idx)
+    ref = oracle_mod.evaluate(sub)
+    compare_paths(codes[torch.tensor(idx, device="cuda")], counts[torch.tensor(idx, device="cuda")], ref)
+    assert np.array_equal(fl[idx] & 3, ref.flags & 3)
+    compare_fields(Eg[:, :, idx], ref, flags=ref.flags, freqs=sc.freqs)
+
+
+def test_fp64_mode(creep, oracle_mod):
+    sc = scenes.room(n_cyl=12, nx=23, ny=19, seed=77)
+    opts = creep.options(precision=creep.RT_PREC_FP64)
+    S, Eg, codes, counts, fl, _ = _run(creep, sc, opts=opts)
+    ref = oracle_mod.evaluate(sc)
+    compare_paths(codes, counts, ref)
+    err = np.linalg.norm(Eg - ref.E, axis=1)
+    assert np.all(err <= 2e-6 * ref.sabs + 1e-13), float(np.max(err / (ref.sabs + 1e-30)))
+
+
+def test_many_frequencies_and_masks(creep, oracle_mod):
+    # five frequencies (two launches of the 4-frequency kernel); contributions
+    # switched on one class at a time.  The hard creeping term of a z-polarised
+    # source vanishes identically on these cylinders (E^i has no normal
+    # component at a tangent point), so the hard-only case uses a y source.
+    sc = scenes.room(n_cyl=8, nx=17, ny=13, freqs=(2.0e9, 2.4e9, 5.8e9, 12e9, 28e9), seed=5)
+    for enable, order in ((creep.RT_EN_ALL, 1), (creep.RT_EN_CREEP_SOFT, 2), (creep.RT_EN_CREEP_HARD | creep.RT_EN_LOS, 0),
+                          (creep.RT_EN_BODYREFL | creep.RT_EN_PLANAR, 2)):
+        sc.max_order = order
+        sc.pol = np.array([0, 1.0, 0] if enable & creep.RT_EN_CREEP_HARD and not enable & creep.RT_EN_CREEP_SOFT
+                          else [0, 0, 1.0], dtype=np.float32)
+        opts = creep.options(max_order=order, enable=enable)
+        S, Eg, codes, counts, fl, _ = _run(creep, sc, opts=opts)
+        ref = oracle_mod.evaluate(sc, enable=enable)
+        compare_paths(codes, counts, ref)
+        compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs)
+
+
+def test_receivers_inside_bodies_and_on_axes(creep, oracle_mod):
+    sc = scenes.room(n_cyl=10, nx=4, ny=4, seed=9)
+    b = sc.bodies
+    pts = [[b[0, 1], b[0, 2], 1.0], [b[1, 1] + b[1, 4], b[1, 2], 1.0],      # centre, exactly on the surface
+           [b[2, 1], b[2, 2], 1.75], [5.0, 4.0, 1.2], [sc.tx[0], sc.tx[1], 1.2]]
+    sc2 = sc.subset(np.arange(len(pts)))
+    sc2.rx = np.asarray(pts, dtype=np.float32)
+    S, Eg, codes, counts, fl, _ = _run(creep, sc2)
+    ref = oracle_mod.evaluate(sc2)
+    compare_paths(codes, counts, ref)
+    _flags_equal(fl, ref)
+    assert fl[0] & 1 and not (fl[2] & 1)              # centre inside; above the top outside
+    assert np.all(Eg[:, :, 0] == 0)
+    compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs)
+
+
+def test_empty_and_error_paths(creep):
+    sc = scenes.room(n_cyl=3, nx=2, ny=2)
+    S = creep.Scene.from_scene(sc)
+    rx = torch.zeros((3, 0), dtype=torch.float32, device="cuda")
+    out = S.evaluate(rx)
+    assert out.shape == (3, 3, 0, 2)
+    with pytest.raises(creep.CreepError) as e:
+        S.set_tx((sc.bodies[0, 1], sc.bodies[0, 2], 1.0), (0, 0, 1))
+    assert e.value.code == creep.RT_ERR_GEOM
+    with pytest.raises(creep.CreepError) as e:
+        S.set_tx((np.nan, 1, 1), (0, 0, 1))
+    assert e.value.code == creep.RT_ERR_ARG
+    with pytest.raises(creep.CreepError) as e:
+        S.set_freqs([])
+    assert e.value.code == creep.RT_ERR_ARG
+    S2 = creep.Scene(sc.tri, sc.tri_face, sc.bodies)
+    with pytest.raises(creep.CreepError) as e:
+        S2.evaluate(torch.zeros((3, 4), dtype=torch.float32, device="cuda"))
+    assert e.value.code == creep.RT_ERR_STATE
+    bad = np.array([[1, 1.0, 1.0, 0.0, 0.3, 1.7], [1, 1.2, 1.0, 0.0, 0.3, 1.7]])
+    with pytest.raises(creep.CreepError) as e:
+        creep.Scene(sc.tri, sc.tri_face, bad)
+    assert e.value.code == creep.RT_ERR_GEOM
+    with pytest.raises(creep.CreepError) as e:
+        S.evaluate(torch.zeros((3, 4), dtype=torch.float32, device="cuda"), opts=creep.options(max_order=3))
+    assert e.value.code == creep.RT_ERR_ARG
+
+
+def test_host_entry_point_matches_device(creep):
+    sc = scenes.room(n_cyl=10, nx=40, ny=33, seed=4)
+    S = creep.Scene.from_scene(sc)
+    rx = torch.tensor(sc.rx_soa(), device="cuda")
+    E = S.evaluate(rx).cpu().numpy()
+    Eh, flh = S.evaluate_host(sc.rx_soa(), flags=True)
+    assert np.array_equal(E, Eh)
