@@ -31,6 +31,9 @@ enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5 };
 
 constexpr int NFC = 4;                 // frequencies per launch (accumulators in registers)
 constexpr int BLOCK = 128;
+#ifndef CREEP_MIN_BLOCKS
+#define CREEP_MIN_BLOCKS 2             // resident blocks per SM the register budget is sized for
+#endif
 constexpr int SMEM_TRI_MAX = 256;
 constexpr int SMEM_BODY_MAX = 256;
 
@@ -199,14 +202,44 @@ __device__ int seg_body(const Ctx &c, int b, v3t<dx> A, v3t<dx> B, dx) {
 
 // 0 visible, 1 blocked, 2 unsure.  Faces sf1/sf2 and body sb are skipped.
 template <typename T>
-__device__ int blocked(const Ctx &c, v3t<T> A, v3t<T> B, int sf1, int sf2, int sb, T band) {
+__device__ __forceinline__ int blocked_impl(const Ctx &c, v3t<T> A, v3t<T> B, int sf1, int sf2, int sb, T band) {
     int uns = 0;
-    for (int t = 0; t < c.n_tri; ++t) {
-        int f = __float_as_int(c.tri[3 * t].w);
-        if (f == sf1 || f == sf2) continue;
-        int r = seg_tri(c, t, A, B, band);
-        if (r == D_YES) return D_YES;
-        uns |= (r == D_UNSURE);
+    if constexpr (sizeof(T) == 4) {
+        // faces first: both ends clearly on one side of a face's plane => none of
+        // its triangles can be hit
+        for (int f = 0; f < c.n_face; ++f) {
+            if (f == sf1 || f == sf2) continue;
+            float4 q = c.face32[f];
+            float sA = q.x * A.x + q.y * A.y + q.z * A.z - q.w, sB = q.x * B.x + q.y * B.y + q.z * B.z - q.w;
+            if ((sA > band && sB > band) || (sA < -band && sB < -band)) continue;
+            int2 rg = c.face_rng[f];
+            for (int i = 0; i < rg.y; ++i) {
+                int r = seg_tri(c, c.face_tris[rg.x + i], A, B, band);
+                if (r == D_YES) return D_YES;
+                uns |= (r == D_UNSURE);
+            }
+        }
+    } else {
+        // exact decisions, FP32-filtered: each primitive is first tested in FP32
+        // on the rounded endpoints with the FP32 error band (which also covers
+        // the rounding of the endpoints); only an uncertain one is tested in FP64
+        v3t<float> Af = mk3<float>(to_float(A.x), to_float(A.y), to_float(A.z));
+        v3t<float> Bf = mk3<float>(to_float(B.x), to_float(B.y), to_float(B.z));
+        for (int t = 0; t < c.n_tri; ++t) {
+            int f = __float_as_int(c.tri[3 * t].w);
+            if (f == sf1 || f == sf2) continue;
+            int r = seg_tri(c, t, Af, Bf, c.band);
+            if (r == D_UNSURE) r = seg_tri(c, t, A, B, band);
+            if (r == D_YES) return D_YES;
+        }
+#pragma unroll 1
+        for (int b = 0; b < c.n_body; ++b) {
+            if (b == sb) continue;
+            int r = seg_body(c, b, Af, Bf, c.band);
+            if (r == D_UNSURE) r = seg_body(c, b, A, B, band);
+            if (r == D_YES) return D_YES;
+        }
+        return D_NO;
     }
     for (int b = 0; b < c.n_body; ++b) {
         if (b == sb) continue;
@@ -215,6 +248,14 @@ __device__ int blocked(const Ctx &c, v3t<T> A, v3t<T> B, int sf1, int sf2, int s
         uns |= (r == D_UNSURE);
     }
     return uns ? D_UNSURE : D_NO;
+}
+// One out-of-line copy per precision: the visibility loop is called from ten
+// places per receiver; inlining it everywhere overflows the instruction cache.
+__device__ __noinline__ int blocked(const Ctx &c, v3t<float> A, v3t<float> B, int sf1, int sf2, int sb, float band) {
+    return blocked_impl(c, A, B, sf1, sf2, sb, band);
+}
+__device__ __noinline__ int blocked(const Ctx &c, v3t<dx> A, v3t<dx> B, int sf1, int sf2, int sb, dx band) {
+    return blocked_impl(c, A, B, sf1, sf2, sb, band);
 }
 
 // point (on the triangle's plane) inside the closed triangle
@@ -240,7 +281,13 @@ __device__ int in_face(const Ctx &c, int f, v3t<T> Q, T band) {
     int2 r = c.face_rng[f];
     int uns = 0;
     for (int i = 0; i < r.y; ++i) {
-        int d = in_tri(c, c.face_tris[r.x + i], Q, band);
+        int d;
+        if constexpr (sizeof(T) == 4) {
+            d = in_tri(c, c.face_tris[r.x + i], Q, band);
+        } else {
+            d = in_tri(c, c.face_tris[r.x + i], mk3<float>(to_float(Q.x), to_float(Q.y), to_float(Q.z)), c.band);
+            if (d == D_UNSURE) d = in_tri(c, c.face_tris[r.x + i], Q, band);
+        }
         if (d == D_YES) return D_YES;
         uns |= (d == D_UNSURE);
     }
@@ -371,11 +418,19 @@ __device__ void cyl_frame(v3t<T> S, v3t<T> P, T cx, T cy, T a, Frame<T> &F, T ba
     F.ds = Sqrt(sx * sx + sy * sy); F.dp = Sqrt(px * px + py * py);
     F.u = mk3<T>(sx / F.ds, sy / F.ds, T(0));
     F.gam = Atan2(Fabs(sx * py - sy * px), sx * px + sy * py);
-    T pd = px * F.u.x + py * F.u.y;
-    T wx = px - pd * F.u.x, wy = py - pd * F.u.y;
-    T nw = Sqrt(wx * wx + wy * wy);
-    F.axis_ok = (band > T(0)) ? (nw > T(1e-3) * F.dp) : true;
-    F.v = (nw == T(0)) ? mk3<T>(-F.u.y, F.u.x, T(0)) : mk3<T>(wx / nw, wy / nw, T(0));
+    if constexpr (sizeof(T) == 4) {
+        // in the horizontal plane v is +-(z x u); only its sign depends on P, and
+        // that sign is uncertain only for P within FP32 rounding of the S-c line
+        T side = F.u.x * py - F.u.y * px;                 // (z x u).(P - c)
+        F.axis_ok = Fabs(side) > T(4e-6) * F.dp;
+        F.v = (side < T(0)) ? mk3<T>(F.u.y, -F.u.x, T(0)) : mk3<T>(-F.u.y, F.u.x, T(0));
+    } else {
+        T pd = px * F.u.x + py * F.u.y;
+        T wx = px - pd * F.u.x, wy = py - pd * F.u.y;
+        T nw = Sqrt(wx * wx + wy * wy);
+        F.axis_ok = true;
+        F.v = (nw == T(0)) ? mk3<T>(-F.u.y, F.u.x, T(0)) : mk3<T>(wx / nw, wy / nw, T(0));
+    }
     F.bs = Acos(a / F.ds); F.bp = Acos(a / F.dp);
     F.pu = px * F.u.x + py * F.u.y; F.pv = px * F.v.x + py * F.v.y;
 }
@@ -476,9 +531,10 @@ __device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, Geo<T> &
     SinCos(psi, &sn, &cs);
     if constexpr (sizeof(T) == 4) {
         // incidence cosine (2-D, horizontal for cylinders): refine the root in FP64
-        // when its FP32 error would exceed 1e-6 of cos(theta_i) (near grazing)
+        // when its FP32 error would exceed 1e-5 of cos(theta_i) (near grazing),
+        // the amplitude budget of the FP32 path
         float c2 = (F.ds * cs - a) / sqrtf((a * cs - F.ds) * (a * cs - F.ds) + a * a * sn * sn);
-        if (psi_err > 1e-6f * fmaxf(c2, 0.0f)) {
+        if (psi_err > 1e-5f * fmaxf(c2, 0.0f)) {
             psi = refl_psi_polish(a, F.ds, F.pu, F.pv, F.gam, psi);
             SinCos(psi, &sn, &cs);
         }
@@ -719,7 +775,7 @@ __device__ __forceinline__ cpx<dx> faddeeva_t(const Ctx &c, cpx<dx> z) { return 
 // 1 - F ~ -sum_{n>=1} (2n-1)!! (j/(2X))^n (X >= 30, 8 terms): no cancellation
 // between two O(c/xi) terms.
 template <typename T>
-__device__ void fock_bracket(const Ctx &c, T xi, T K, cpx<T> &Bs, cpx<T> &Bh) {
+__device__ __forceinline__ void fock_bracket_impl(const Ctx &c, T xi, T K, cpx<T> &Bs, cpx<T> &Bh) {
     const T r2 = T(0.70710678118654752440), spi = T(1.7724538509055160273), cc = T(0.19947114020071633897);
     T sx = K * Fabs(xi);
     T X = sx * sx;
@@ -754,6 +810,24 @@ __device__ void fock_bracket(const Ctx &c, T xi, T K, cpx<T> &Bs, cpx<T> &Bh) {
     cpx<T> cterm = mkc<T>(ci * (omf.re + omf.im), ci * (omf.im - omf.re));   // (1 - j) ci (1 - F)
     Bs = ps + cterm;
     Bh = ph + cterm;
+}
+
+struct Bpair {
+    cpx<float> s, h;
+};
+__device__ __noinline__ Bpair fock_bracket_f(const Ctx &c, float xi, float K) {
+    Bpair b;
+    fock_bracket_impl<float>(c, xi, K, b.s, b.h);
+    return b;
+}
+template <typename T>
+__device__ __forceinline__ void fock_bracket(const Ctx &c, T xi, T K, cpx<T> &Bs, cpx<T> &Bh) {
+    if constexpr (sizeof(T) == 4) {
+        Bpair b = fock_bracket_f(c, xi, K);
+        Bs = b.s; Bh = b.h;
+    } else {
+        fock_bracket_impl<T>(c, xi, K, Bs, Bh);
+    }
 }
 
 // ------------------------------------------------------------------ field accumulation
@@ -817,16 +891,25 @@ __device__ __forceinline__ dfl lsqrt_diff_sq(float d, float a) {    // sqrt(d^2 
 }
 __device__ __forceinline__ dx lsqrt_diff_sq(dx d, dx a) { return Sqrt(d * d - a * a); }
 
+// acc.E[f] += (x, y, z) for a runtime f (registers stay registers)
+template <typename T>
+__device__ __forceinline__ void acc_put(Acc<T> &acc, int f, cpx<T> x, cpx<T> y, cpx<T> z) {
+#pragma unroll
+    for (int ff = 0; ff < NFC; ++ff) {
+        if (ff == f) {
+            acc.E[ff][0] = acc.E[ff][0] + x;
+            acc.E[ff][1] = acc.E[ff][1] + y;
+            acc.E[ff][2] = acc.E[ff][2] + z;
+        }
+    }
+}
+
 template <typename T, typename L>
 __device__ __forceinline__ void add_ray(Acc<T> &acc, const FreqC &fq, v3t<T> e, T amp, L len) {
-#pragma unroll
-    for (int f = 0; f < NFC; ++f) {
-        if (f < fq.nf) {
-            cpx<T> ph = phasor(fq, f, len) * amp;
-            acc.E[f][0] = acc.E[f][0] + ph * e.x;
-            acc.E[f][1] = acc.E[f][1] + ph * e.y;
-            acc.E[f][2] = acc.E[f][2] + ph * e.z;
-        }
+#pragma unroll 1
+    for (int f = 0; f < fq.nf; ++f) {
+        cpx<T> ph = phasor(fq, f, len) * amp;
+        acc_put(acc, f, ph * e.x, ph * e.y, ph * e.z);
     }
 }
 
@@ -852,9 +935,9 @@ __device__ void field_body_refl(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<
     T A = Sqrt(rho1 * rho2 / ((rho1 + sr) * (rho2 + sr))) / si;
     T Lp = si * sr / (si + sr);
     T rcb = Cbrt(g.rho_g);
-#pragma unroll
-    for (int f = 0; f < NFC; ++f) {
-        if (f < fq.nf) {
+#pragma unroll 1
+    for (int f = 0; f < fq.nf; ++f) {
+        {
             T k = kof(fq, f, T(0));
             T m = khof(fq, f, T(0)) * rcb;
             T xi = T(-2) * m * cth;
@@ -871,9 +954,7 @@ __device__ void field_body_refl(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<
             }
             cpx<T> ph = phasor(fq, f, len) * A;
             cpx<T> as = Rs * ph * Es, ah = Rh * ph * Eh;
-            acc.E[f][0] = acc.E[f][0] + as * ep.x + ah * epr.x;
-            acc.E[f][1] = acc.E[f][1] + as * ep.y + ah * epr.y;
-            acc.E[f][2] = acc.E[f][2] + as * ep.z + ah * epr.z;
+            acc_put(acc, f, as * ep.x + ah * epr.x, as * ep.y + ah * epr.y, as * ep.z + ah * epr.z);
         }
     }
 }
@@ -890,9 +971,9 @@ __device__ void field_creep(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S
     T Lp = g.sp * g.sq / (g.sp + g.sq);
     T rcb = Cbrt(g.rho_g);
     T tr = g.t / g.rho_g;
-#pragma unroll
-    for (int f = 0; f < NFC; ++f) {
-        if (f < fq.nf) {
+#pragma unroll 1
+    for (int f = 0; f < fq.nf; ++f) {
+        {
             T k = kof(fq, f, T(0));
             T m = khof(fq, f, T(0)) * rcb;
             T xi = m * tr;
@@ -903,9 +984,7 @@ __device__ void field_creep(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S
             cpx<T> ph = phasor(fq, f, len) * pre;
             if (g.caus) ph = mkc<T>(-ph.im, ph.re);          // x (+j)
             cpx<T> as = Bs * ph * Es, ah = Bh * ph * Eh;
-            acc.E[f][0] = acc.E[f][0] + as * b2.x + ah * g.n2.x;
-            acc.E[f][1] = acc.E[f][1] + as * b2.y + ah * g.n2.y;
-            acc.E[f][2] = acc.E[f][2] + as * b2.z + ah * g.n2.z;
+            acc_put(acc, f, as * b2.x + ah * g.n2.x, as * b2.y + ah * g.n2.y, as * b2.z + ah * g.n2.z);
         }
     }
 }
@@ -962,13 +1041,24 @@ __device__ __forceinline__ dfl to_df(double x) {
     return r;
 }
 
-__device__ __forceinline__ void acc_add(Acc<float> &a, const Acc<dx> &b, int nf) {
+// ------------------------------------------------------------------ FP64 re-evaluation
+// Out of line: these run for the few candidates whose FP32 margins fall inside
+// the error band; keeping them out of the kernel body keeps the hot loop small.
+struct Contrib {
+    cpx<float> E[NFC][3];
+};
+__device__ __forceinline__ void contrib_from(Contrib *o, const Acc<dx> &a) {
+#pragma unroll
+    for (int f = 0; f < NFC; ++f)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) o->E[f][q] = mkc<float>(to_float(a.E[f][q].re), to_float(a.E[f][q].im));
+}
+__device__ __forceinline__ void acc_add(Acc<float> &a, const Contrib &b, int nf) {
 #pragma unroll
     for (int f = 0; f < NFC; ++f)
         if (f < nf)
 #pragma unroll
-            for (int q = 0; q < 3; ++q)
-                a.E[f][q] = a.E[f][q] + mkc<float>(to_float(b.E[f][q].re), to_float(b.E[f][q].im));
+            for (int q = 0; q < 3; ++q) a.E[f][q] = a.E[f][q] + b.E[f][q];
 }
 __device__ __forceinline__ void acc_zero(Acc<dx> &a) {
 #pragma unroll
@@ -976,22 +1066,83 @@ __device__ __forceinline__ void acc_zero(Acc<dx> &a) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) a.E[f][q] = mkc<dx>(0.0, 0.0);
 }
+__device__ __forceinline__ v3t<dx> dxv(v3t<float> a) { return mk3<dx>((double)a.x, (double)a.y, (double)a.z); }
+
+__device__ __noinline__ int esc_inside(const Ctx &c, int b, v3t<float> Pf) {
+    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
+    dx ex = dx((double)Pf.x) - dx((double)q0.x), ey = dx((double)Pf.y) - dx((double)q0.y),
+       ez = dx((double)Pf.z) - dx((double)q0.z), a = dx((double)q0.w);
+    if (q1.y == 0.0f) return (ex * ex + ey * ey + ez * ez <= a * a) ? D_YES : D_NO;
+    return (ex * ex + ey * ey <= a * a && dx((double)Pf.z) >= dx((double)q0.z) &&
+            dx((double)Pf.z) <= dx((double)q0.z) + dx((double)q1.x)) ? D_YES : D_NO;
+}
+__device__ __noinline__ int esc_los(const Ctx &c, v3t<float> Pf) {
+    return cand_los<dx>(c, dxv(c.S), dxv(Pf), dx(0.0));
+}
+__device__ __noinline__ int esc_r1(const Ctx &c, int i, v3t<float> Pf, v3t<float> *Q) {
+    Geo<dx> g;
+    int d = cand_r1<dx>(c, i, dxv(c.S), dxv(Pf), dx(0.0), g);
+    if (d == D_YES) *Q = to_f3(g.Q1);
+    return d;
+}
+__device__ __noinline__ int esc_r2(const Ctx &c, int i, int j, v3t<float> Pf, v3t<float> *Q1, v3t<float> *Q2) {
+    Geo<dx> g;
+    int d = cand_r2<dx>(c, i, j, dxv(c.S), dxv(Pf), dx(0.0), g);
+    if (d == D_YES) { *Q1 = to_f3(g.Q1); *Q2 = to_f3(g.Q2); }
+    return d;
+}
+// body reflection decided and (field = true) evaluated in FP64
+__device__ __noinline__ int esc_rb(const Ctx &c, int b, v3t<float> Pf, const FreqC &fq, bool field, Contrib *out) {
+    Geo<dx> g;
+    v3t<dx> Sd = dxv(c.S), Pd = dxv(Pf);
+    int d = cand_rb<dx>(c, b, Sd, Pd, dx(0.0), g);
+    if (d == D_YES && field) {
+        Acc<dx> a;
+        acc_zero(a);
+        field_body_refl<dx>(c, a, fq, Sd, Pd, g, seglen(Sd, g.Q1) + seglen(g.Q1, Pd));
+        contrib_from(out, a);
+    }
+    return d;
+}
+// creeping ray decided, its caustic flag taken, and (field) evaluated in FP64
+__device__ __noinline__ int esc_creep(const Ctx &c, int b, int dir, v3t<float> Pf, const FreqC &fq, bool field,
+                                      double half_lambda_max, unsigned enable, Contrib *out, int *caustic) {
+    Geo<dx> g;
+    v3t<dx> Sd = dxv(c.S), Pd = dxv(Pf);
+    int d = cand_creep<dx>(c, b, dir, Sd, Pd, dx(0.0), g);
+    *caustic = 0;
+    if (d != D_YES) return d;
+    bool sphere = c.body[2 * b + 1].y == 0.0f;
+    if (sphere) {
+        *caustic = half_lambda_max > g.dperp.v;
+        if (!(g.dperp > dx(0.0))) field = false;     // exactly on the axis: no finite ray field
+    }
+    if (field) {
+        Acc<dx> a;
+        acc_zero(a);
+        field_creep<dx>(c, a, fq, Sd, Pd, g, g.sp + g.t + g.sq, enable);
+        contrib_from(out, a);
+    }
+    return d;
+}
 
 // ------------------------------------------------------------------ kernel
 template <typename T, bool PATHS>
-__global__ void __launch_bounds__(BLOCK) k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e_out,
+__global__ void __launch_bounds__(BLOCK, CREEP_MIN_BLOCKS) k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e_out,
                                                uint32_t *__restrict__ flags_out, uint64_t *__restrict__ codes,
-                                               int32_t *__restrict__ counts, int cap, int f0, FreqC fq,
+                                               int32_t *__restrict__ counts, int cap, int f0, FreqC fq_in,
                                                double half_lambda_max, unsigned long long *esc_counter) {
     extern __shared__ float4 smem[];
+    __shared__ Ctx s_ctx;
+    __shared__ FreqC s_fq;
     // stage scene and table
     float4 *s_fock = smem;                                   // FOCK_N * 2
     float4 *s_res = s_fock + FOCK_N * 2;                     // FOCK_NRES * 2
     float4 *s_face = s_res + FOCK_NRES * 2;                  // n_face
-    float4 *s_body = s_face + S.n_face;                      // n_body * 2 (if staged)
     bool body_sm = S.n_body <= SMEM_BODY_MAX;
-    float4 *s_tri = s_body + (body_sm ? 2 * S.n_body : 0);   // n_tri * 3 (if staged)
+    float4 *s_body = s_face + S.n_face;                      // n_body * 2 (if staged)
     bool tri_sm = S.n_tri <= SMEM_TRI_MAX;
+    float4 *s_tri = s_body + (body_sm ? 2 * S.n_body : 0);   // n_tri * 3 (if staged)
     float4 *s_aux = s_tri + (tri_sm ? 3 * S.n_tri : 0);      // n_tri * 3 (if staged)
     float *s_weid = (float *)(s_aux + (tri_sm ? 3 * S.n_tri : 0));
     for (int i = threadIdx.x; i < FOCK_N * 2; i += blockDim.x) s_fock[i] = S.fock32[i];
@@ -1005,37 +1156,44 @@ __global__ void __launch_bounds__(BLOCK) k_eval(DevScene S, const float *__restr
             s_aux[i] = S.tri_alt[i];
         }
     for (int i = threadIdx.x; i < WEIDEMAN_N; i += blockDim.x) s_weid[i] = S.weid[i];
+    if (threadIdx.x == 0) {
+        Ctx &c = s_ctx;
+        c.tri = tri_sm ? s_tri : S.tri;
+        c.tri_aux = tri_sm ? s_aux : S.tri_alt;
+        c.face32 = s_face;
+        c.face64 = S.face64;
+        c.face_rng = S.face_rng;
+        c.face_tris = S.face_tris;
+        c.body = body_sm ? s_body : S.body;
+        c.n_tri = S.n_tri; c.n_face = S.n_face; c.n_body = S.n_body;
+        c.band = S.band_len;
+        c.S = mk3(S.tx[0], S.tx[1], S.tx[2]);
+        c.pol = mk3(S.pol[0], S.pol[1], S.pol[2]);
+        c.fock = s_fock; c.res = s_res; c.weid = s_weid; c.weid_L = S.weid_L;
+        c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
+        c.img = S.img;
+        s_fq = fq_in;
+    }
     __syncthreads();
 
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_rx) return;
-
-    Ctx c;
-    c.tri = tri_sm ? s_tri : S.tri;
-    c.tri_aux = tri_sm ? s_aux : S.tri_alt;
-    c.face32 = s_face;
-    c.face64 = S.face64;
-    c.face_rng = S.face_rng;
-    c.face_tris = S.face_tris;
-    c.body = body_sm ? s_body : S.body;
-    c.n_tri = S.n_tri; c.n_face = S.n_face; c.n_body = S.n_body;
-    c.band = S.band_len;
-    c.S = mk3(S.tx[0], S.tx[1], S.tx[2]);
-    c.pol = mk3(S.pol[0], S.pol[1], S.pol[2]);
-    c.fock = s_fock; c.res = s_res; c.weid = s_weid; c.weid_L = S.weid_L;
-    c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
-    c.img = S.img;
-
-    const T band = (sizeof(T) == 4) ? (T)S.band_len : T(0);
+    const Ctx &c = s_ctx;
+    const FreqC &fq = s_fq;
+    const bool fp32 = sizeof(T) == 4;
+    const T band = fp32 ? T(c.band) : T(0);
+    const int nf = fq.nf;
     v3t<float> Pf = mk3(rx[r], rx[n_rx + r], rx[2 * n_rx + r]);
-    v3t<T> P = mk3<T>(Pf.x, Pf.y, Pf.z);
-    v3t<T> Sx = mk3<T>(c.S.x, c.S.y, c.S.z);
+    v3t<T> P = mk3<T>(T((double)Pf.x), T((double)Pf.y), T((double)Pf.z));
+    v3t<T> Sx = mk3<T>(T((double)c.S.x), T((double)c.S.y), T((double)c.S.z));
     uint32_t fl = 0;
     int npath = 0;
     Acc<T> acc;
 #pragma unroll
     for (int f = 0; f < NFC; ++f)
-        for (int q = 0; q < 3; ++q) acc.E[f][q] = mkc<T>(0, 0);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc.E[f][q] = mkc<T>(T(0.0), T(0.0));
+    typedef typename LenOf<T>::type LT;
 
     auto emit = [&](int type, int a, int b) {
         if (PATHS) {
@@ -1045,37 +1203,23 @@ __global__ void __launch_bounds__(BLOCK) k_eval(DevScene S, const float *__restr
         ++npath;
     };
 
-    // receiver inside a body?
+    // receiver inside (or on) a body?
     int inside = 0;
-    for (int b = 0; b < S.n_body && !inside; ++b) {
+    for (int b = 0; b < c.n_body && !inside; ++b) {
         float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
         int d;
-        if (q1.y == 0.0f) {
-            T ex = P.x - (T)q0.x, ey = P.y - (T)q0.y, ez = P.z - (T)q0.z;
-            if (band > T(0)) d = decide((T)q0.w - Sqrt(ex * ex + ey * ey + ez * ez), band, D_YES);
-            else d = (ex * ex + ey * ey + ez * ez <= (T)q0.w * (T)q0.w) ? D_YES : D_NO;
+        T ex = P.x - T((double)q0.x), ey = P.y - T((double)q0.y), ez = P.z - T((double)q0.z), a = T((double)q0.w);
+        if (fp32) {
+            T m = (q1.y == 0.0f) ? a - Sqrt(ex * ex + ey * ey + ez * ez)
+                                 : Fmin(Fmin(a - Sqrt(ex * ex + ey * ey), P.z - T((double)q0.z)),
+                                        T((double)q0.z) + T((double)q1.x) - P.z);
+            d = decide(m, band, D_YES);
+            if (d == D_UNSURE) { fl |= RT_FLAG_ESCALATED; d = esc_inside(c, b, Pf); }
         } else {
-            T ex = P.x - (T)q0.x, ey = P.y - (T)q0.y;
-            if (band > T(0)) {
-                T m = Fmin(Fmin((T)q0.w - Sqrt(ex * ex + ey * ey), P.z - (T)q0.z), (T)q0.z + (T)q1.x - P.z);
-                d = decide(m, band, D_YES);
-            } else {
-                d = (ex * ex + ey * ey <= (T)q0.w * (T)q0.w && P.z >= (T)q0.z && P.z <= (T)q0.z + (T)q1.x) ? D_YES : D_NO;
-            }
-        }
-        if (d == D_UNSURE) {
-            fl |= RT_FLAG_ESCALATED;
-            dx ex = dx((double)Pf.x) - dx((double)q0.x), ey = dx((double)Pf.y) - dx((double)q0.y),
-               ez = dx((double)Pf.z) - dx((double)q0.z), a = dx((double)q0.w);
-            if (q1.y == 0.0f) d = (ex * ex + ey * ey + ez * ez <= a * a) ? D_YES : D_NO;
-            else d = (ex * ex + ey * ey <= a * a && dx((double)Pf.z) >= dx((double)q0.z) &&
-                      dx((double)Pf.z) <= dx((double)q0.z) + dx((double)q1.x)) ? D_YES : D_NO;
+            d = esc_inside(c, b, Pf);
         }
         inside = (d == D_YES);
     }
-    typedef typename LenOf<T>::type LT;
-    v3t<dx> Pd = mk3<dx>((double)Pf.x, (double)Pf.y, (double)Pf.z), Sd = mk3<dx>((double)c.S.x, (double)c.S.y, (double)c.S.z);
-    const dx zero_band = dx(0.0);
 
     if (inside) {
         fl |= RT_FLAG_INSIDE;
@@ -1083,7 +1227,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval(DevScene S, const float *__restr
         // ---- direct ray
         if (S.enable & RT_EN_LOS) {
             int d = cand_los<T>(c, Sx, P, band);
-            if (d == D_UNSURE) { fl |= RT_FLAG_ESCALATED; d = cand_los<dx>(c, Sd, Pd, zero_band); }
+            if (d == D_UNSURE) { fl |= RT_FLAG_ESCALATED; d = esc_los(c, Pf); }
             if (d == D_YES) {
                 emit(PT_LOS, 0, 0);
                 if (!PATHS) {
@@ -1094,14 +1238,12 @@ __global__ void __launch_bounds__(BLOCK) k_eval(DevScene S, const float *__restr
         }
         // ---- planar image reflections
         if ((S.enable & RT_EN_PLANAR) && S.max_order >= 1) {
-            for (int i = 0; i < S.n_face; ++i) {
+#pragma unroll 1
+            for (int i = 0; i < c.n_face; ++i) {
                 Geo<T> g;
                 int d = cand_r1<T>(c, i, Sx, P, band, g);
-                if (d == D_UNSURE) {
-                    fl |= RT_FLAG_ESCALATED;
-                    Geo<dx> gd;
-                    d = cand_r1<dx>(c, i, Sd, Pd, zero_band, gd);
-                    if constexpr (sizeof(T) == 4) g.Q1 = to_f3(gd.Q1);
+                if constexpr (sizeof(T) == 4) {
+                    if (d == D_UNSURE) { fl |= RT_FLAG_ESCALATED; d = esc_r1(c, i, Pf, &g.Q1); }
                 }
                 if (d == D_YES) {
                     emit(PT_R1, i, 0);
@@ -1117,16 +1259,15 @@ __global__ void __launch_bounds__(BLOCK) k_eval(DevScene S, const float *__restr
             }
         }
         if ((S.enable & RT_EN_PLANAR) && S.max_order >= 2) {
-            for (int i = 0; i < S.n_face; ++i) {
-                for (int j = 0; j < S.n_face; ++j) {
+#pragma unroll 1
+            for (int i = 0; i < c.n_face; ++i) {
+#pragma unroll 1
+                for (int j = 0; j < c.n_face; ++j) {
                     if (j == i) continue;
                     Geo<T> g;
                     int d = cand_r2<T>(c, i, j, Sx, P, band, g);
-                    if (d == D_UNSURE) {
-                        fl |= RT_FLAG_ESCALATED;
-                        Geo<dx> gd;
-                        d = cand_r2<dx>(c, i, j, Sd, Pd, zero_band, gd);
-                        if constexpr (sizeof(T) == 4) { g.Q1 = to_f3(gd.Q1); g.Q2 = to_f3(gd.Q2); }
+                    if constexpr (sizeof(T) == 4) {
+                        if (d == D_UNSURE) { fl |= RT_FLAG_ESCALATED; d = esc_r2(c, i, j, Pf, &g.Q1, &g.Q2); }
                     }
                     if (d == D_YES) {
                         emit(PT_R2, i, j);
@@ -1136,7 +1277,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval(DevScene S, const float *__restr
                             face_plane<T>(c, j, &nj, &dj);
                             LT L;
                             if constexpr (sizeof(T) == 4) {
-                                int slot = S.n_face + i * S.n_face + j;
+                                int slot = c.n_face + i * c.n_face + j;
                                 L = df_dist_df(c.img[2 * slot], c.img[2 * slot + 1], Pf);
                             } else {
                                 L = ladd(ladd(seglen(Sx, g.Q1), seglen(g.Q1, g.Q2)), seglen(g.Q2, P));
@@ -1149,25 +1290,21 @@ __global__ void __launch_bounds__(BLOCK) k_eval(DevScene S, const float *__restr
             }
         }
         // ---- curved bodies
-        for (int b = 0; b < S.n_body; ++b) {
+#pragma unroll 1
+        for (int b = 0; b < c.n_body; ++b) {
             if (S.enable & RT_EN_BODYREFL) {
                 Geo<T> g;
                 int d = cand_rb<T>(c, b, Sx, P, band, g);
                 if constexpr (sizeof(T) == 4) {
                     if (d == D_UNSURE) {
-                        // decided in FP64; its field too (the geometry may be
+                        // decided in FP64, and its field too (the geometry may be
                         // ill-conditioned in FP32, e.g. a receiver at a surface)
                         fl |= RT_FLAG_ESCALATED;
-                        Geo<dx> gd;
-                        d = cand_rb<dx>(c, b, Sd, Pd, zero_band, gd);
+                        Contrib ct;
+                        d = esc_rb(c, b, Pf, fq, !PATHS, &ct);
                         if (d == D_YES) {
                             emit(PT_RB, b, 0);
-                            if (!PATHS) {
-                                Acc<dx> a2;
-                                acc_zero(a2);
-                                field_body_refl<dx>(c, a2, fq, Sd, Pd, gd, seglen(Sd, gd.Q1) + seglen(gd.Q1, Pd));
-                                acc_add(acc, a2, fq.nf);
-                            }
+                            if (!PATHS) acc_add(acc, ct, nf);
                         }
                         d = D_NO;
                     }
@@ -1183,48 +1320,38 @@ __global__ void __launch_bounds__(BLOCK) k_eval(DevScene S, const float *__restr
                 }
             }
             if (S.enable & (RT_EN_CREEP_SOFT | RT_EN_CREEP_HARD)) {
+                bool sphere = c.body[2 * b + 1].y == 0.0f;
+#pragma unroll 1
                 for (int dir = 0; dir < 2; ++dir) {
                     Geo<T> g;
                     int d = cand_creep<T>(c, b, dir, Sx, P, band, g);
-                    bool esc = false;
-                    Geo<dx> gd = {};
+                    int cd = D_NO;
+                    if (d == D_YES && sphere) {
+                        // axial caustic flag: k d_perp < pi for some frequency, i.e. d_perp < lambda_max / 2
+                        if constexpr (sizeof(T) == 8) cd = (half_lambda_max > to_double(g.dperp)) ? D_YES : D_NO;
+                        else cd = decide((T)half_lambda_max - g.dperp, band, D_NO);
+                    }
                     if constexpr (sizeof(T) == 4) {
-                        if (d == D_UNSURE) {
+                        if (d == D_UNSURE || cd == D_UNSURE) {
                             fl |= RT_FLAG_ESCALATED;
-                            esc = true;
-                            d = cand_creep<dx>(c, b, dir, Sd, Pd, zero_band, gd);
-                            if (d == D_YES) g = to_f(gd);
+                            Contrib ct;
+                            int caus = 0;
+                            d = esc_creep(c, b, dir, Pf, fq, !PATHS, half_lambda_max, S.enable, &ct, &caus);
+                            if (d == D_YES) {
+                                emit(dir == 0 ? PT_CP : PT_CM, b, 0);
+                                if (caus) fl |= RT_FLAG_CAUSTIC;
+                                if (!PATHS) acc_add(acc, ct, nf);
+                            }
+                            continue;
                         }
                     }
                     if (d != D_YES) continue;
                     emit(dir == 0 ? PT_CP : PT_CM, b, 0);
-                    if (c.body[2 * b + 1].y == 0.0f) {
-                        // axial caustic flag: k d_perp < pi for some frequency, i.e. d_perp < lambda_max / 2
-                        int cd;
-                        if constexpr (sizeof(T) == 8) {
-                            cd = (half_lambda_max > to_double(g.dperp)) ? D_YES : D_NO;
-                        } else {
-                            cd = esc ? ((half_lambda_max > gd.dperp.v) ? D_YES : D_NO)
-                                     : decide((T)half_lambda_max - g.dperp, band, D_NO);
-                            if (cd == D_UNSURE) {
-                                fl |= RT_FLAG_ESCALATED;
-                                cand_creep<dx>(c, b, dir, Sd, Pd, zero_band, gd);
-                                cd = (half_lambda_max > gd.dperp.v) ? D_YES : D_NO;
-                            }
-                        }
+                    if (sphere) {
                         if (cd == D_YES) fl |= RT_FLAG_CAUSTIC;
-                        if (!(g.dperp > T(0))) continue;
+                        if (!(g.dperp > T(0.0))) continue;        // exactly on the axis: no finite ray field
                     }
                     if (!PATHS) {
-                        if constexpr (sizeof(T) == 4) {
-                            if (esc) {
-                                Acc<dx> a2;
-                                acc_zero(a2);
-                                field_creep<dx>(c, a2, fq, Sd, Pd, gd, gd.sp + gd.t + gd.sq, S.enable);
-                                acc_add(acc, a2, fq.nf);
-                                continue;
-                            }
-                        }
                         LT L = creep_len(c, b, Sx, P, g);
                         field_creep<T>(c, acc, fq, Sx, P, g, L, S.enable);
                     }
@@ -1237,7 +1364,7 @@ __global__ void __launch_bounds__(BLOCK) k_eval(DevScene S, const float *__restr
     } else {
 #pragma unroll
         for (int f = 0; f < NFC; ++f) {
-            if (f < fq.nf) {
+            if (f < nf) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
                     size_t idx = ((size_t)(f0 + f) * 3 + q) * n_rx + r;
