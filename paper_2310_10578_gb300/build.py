@@ -17,8 +17,10 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcreep.so")
 SOURCES = ["abi.cu", "eval_fields.cu", "fock_table.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# host code: -ffp-contract=off so that host-side FP64 decisions (per-transmitter
+# precomputation) round as written on every host ISA
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr"]
+         "-Xcompiler", "-ffp-contract=off", "--expt-relaxed-constexpr"]
 
 
 def nvcc():

@@ -123,6 +123,7 @@ struct rt_scene {
     int *d_face_tris = nullptr;
     double *d_freq = nullptr;
     float4 *d_img = nullptr;            // source images, see DevScene::img
+    float4 *d_txb = nullptr;            // source-side body frames, see DevScene::txb
     unsigned long long *d_esc = nullptr;
     DevTable *table = nullptr;
     // state
@@ -161,7 +162,7 @@ static int fail(int code, const char *fmt, ...) {
 static void free_scene(rt_scene *s) {
     cudaFree(s->d_tri); cudaFree(s->d_aux); cudaFree(s->d_face32); cudaFree(s->d_body);
     cudaFree(s->d_face64); cudaFree(s->d_face_rng); cudaFree(s->d_face_tris); cudaFree(s->d_freq);
-    cudaFree(s->d_esc); cudaFree(s->io_rx); cudaFree(s->io_e); cudaFree(s->io_fl); cudaFree(s->d_img);
+    cudaFree(s->d_esc); cudaFree(s->io_rx); cudaFree(s->io_e); cudaFree(s->io_fl); cudaFree(s->d_img); cudaFree(s->d_txb);
 }
 
 // distance from point p to the solid of body b (0 if inside)
@@ -314,6 +315,7 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
     CKS(cudaMalloc(&s->d_freq, sizeof(double) * RT_MAX_FREQS));
     CKS(cudaMalloc(&s->d_esc, sizeof(unsigned long long)));
     CKS(cudaMalloc(&s->d_img, sizeof(float4) * 2 * (nfc + nfc * nfc)));
+    CKS(cudaMalloc(&s->d_txb, sizeof(float4) * 2 * nbd));
     if (n_tri > 0) {
         CKS(cudaMemcpy(s->d_tri, htri.data(), sizeof(float4) * 3 * n_tri, cudaMemcpyHostToDevice));
         CKS(cudaMemcpy(s->d_aux, haux.data(), sizeof(float4) * 3 * n_tri, cudaMemcpyHostToDevice));
@@ -378,6 +380,25 @@ int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
         }
     }
     if (nf > 0) CK(cudaMemcpy(s->d_img, img.data(), sizeof(float4) * img.size(), cudaMemcpyHostToDevice));
+    // per body, the source side of the (S, c, P) frame: the same for every receiver
+    std::vector<float4> txb(2 * (size_t)(s->n_body > 0 ? s->n_body : 1));
+    for (int b = 0; b < s->n_body; ++b) {
+        const rt_body &B = s->bodies[b];
+        double w[3] = {p[0] - B.c[0], p[1] - B.c[1], B.type == RT_BODY_SPHERE ? p[2] - B.c[2] : 0.0};
+        double a = B.a;
+        double ds = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        bool ok = ds > a;                      // cylinder: a source over the footprint has no lateral paths
+        double u[3] = {0, 0, 0}, bs = 0, q = 0;
+        if (ok) {
+            for (int k = 0; k < 3; ++k) u[k] = w[k] / ds;
+            bs = acos(a / ds);
+            q = sqrt(ds * ds - a * a);
+        }
+        float qh = (float)q;
+        txb[2 * b] = make_float4((float)u[0], (float)u[1], (float)u[2], (float)ds);
+        txb[2 * b + 1] = make_float4((float)bs, qh, (float)(q - (double)qh), ok ? 1.f : 0.f);
+    }
+    if (s->n_body > 0) CK(cudaMemcpy(s->d_txb, txb.data(), sizeof(float4) * 2 * s->n_body, cudaMemcpyHostToDevice));
     s->tx_set = true;
     return RT_OK;
 }
@@ -410,6 +431,7 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec) 
     D.weid = s->table->weid; D.weid64 = s->table->weid64; D.weid_L = s->table->weid_L;
     D.freq = s->freqs.data();   // host pointer: read by the launcher only
     D.img = s->d_img;
+    D.txb = s->d_txb;
     memcpy(D.tx, s->tx, sizeof(D.tx));
     memcpy(D.pol, s->pol, sizeof(D.pol));
     D.band_len = s->band_len;

@@ -75,6 +75,7 @@ struct Ctx {
     const dq4 *res64;
     const double *weid64;
     const float4 *img;           // source images (double-float), see DevScene
+    const float4 *txb;           // [n_body][2] source-side body frame, see DevScene
 };
 
 template <typename T>
@@ -391,6 +392,8 @@ struct Frame {
     v3t<T> u, v;
     T ds, dp, gam, bs, bp, pu, pv;
     bool axis_ok;   // v well conditioned (P not near the S-c axis)
+    int dec;        // D_YES: lateral paths possible; D_NO: source or receiver over a cylinder's footprint
+    dfl dsq;        // FP32 mode: sqrt(ds^2 - a^2) as double-float (from the FP64 source precomputation)
 };
 
 template <typename T>
@@ -433,6 +436,57 @@ __device__ void cyl_frame(v3t<T> S, v3t<T> P, T cx, T cy, T a, Frame<T> &F, T ba
     }
     F.bs = Acos(a / F.ds); F.bp = Acos(a / F.dp);
     F.pu = px * F.u.x + py * F.u.y; F.pv = px * F.v.x + py * F.v.y;
+}
+
+// The (S, c, P) frame of body b, shared by its reflection and both creeping
+// rays.  FP32: the source-only quantities (u, |S - c|, beta_s, s' or d_s, and
+// whether the source is over a cylinder's footprint) come precomputed in FP64
+// per transmitter (Ctx::txb); FP64: computed here as the definition does.
+__device__ void body_frame(const Ctx &c, int b, v3t<float> S, v3t<float> P, float band, Frame<float> &F) {
+    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1], t0 = c.txb[2 * b], t1 = c.txb[2 * b + 1];
+    float a = q0.w;
+    F.dec = D_YES;
+    F.axis_ok = true;
+    if (t1.w == 0.0f) { F.dec = D_NO; return; }      // source over the cylinder's footprint
+    F.u = mk3(t0.x, t0.y, t0.z);
+    F.ds = t0.w;
+    F.bs = t1.x;
+    F.dsq.hi = t1.y; F.dsq.lo = t1.z;
+    if (q1.y == 0.0f) {
+        v3t<float> wp = mk3(P.x - q0.x, P.y - q0.y, P.z - q0.z);
+        F.pu = dot3(F.u, wp);
+        v3t<float> cr = cross3(F.u, wp);
+        F.pv = norm3(cr);
+        F.dp = norm3(wp);
+        F.axis_ok = F.pv > 1e-3f * F.dp;
+        F.v = (F.pv > 0.0f) ? (wp - F.u * F.pu) * (1.0f / F.pv) : mk3(0.f, 0.f, 0.f);
+    } else {
+        float px = P.x - q0.x, py = P.y - q0.y;
+        F.dp = sqrtf(px * px + py * py);
+        int d = decide(F.dp - a, band, D_NO);
+        if (d == D_NO) { F.dec = D_NO; return; }
+        F.dec = d;
+        F.pu = F.u.x * px + F.u.y * py;
+        float side = F.u.x * py - F.u.y * px;             // (z x u).(P - c)
+        F.pv = fabsf(side);
+        F.axis_ok = F.pv > 4e-6f * F.dp;
+        F.v = (side < 0.0f) ? mk3(F.u.y, -F.u.x, 0.0f) : mk3(-F.u.y, F.u.x, 0.0f);
+    }
+    F.gam = atan2f(F.pv, F.pu);
+    F.bp = acosf(a / F.dp);
+}
+__device__ void body_frame(const Ctx &c, int b, v3t<dx> S, v3t<dx> P, dx band, Frame<dx> &F) {
+    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
+    dx a = (double)q0.w;
+    F.dec = D_YES;
+    if (q1.y == 0.0f) {
+        sphere_frame(S, P, mk3<dx>((double)q0.x, (double)q0.y, (double)q0.z), a, F, band);
+        return;
+    }
+    dx rs = Sqrt((S.x - dx((double)q0.x)) * (S.x - dx((double)q0.x)) + (S.y - dx((double)q0.y)) * (S.y - dx((double)q0.y)));
+    dx rp = Sqrt((P.x - dx((double)q0.x)) * (P.x - dx((double)q0.x)) + (P.y - dx((double)q0.y)) * (P.y - dx((double)q0.y)));
+    if (!(rs > a) || !(rp > a)) { F.dec = D_NO; return; }
+    cyl_frame(S, P, dx((double)q0.x), dx((double)q0.y), a, F, band);
 }
 
 // 2-D reflection point psi on the circle of radius a, S = (ds, 0), P = (pu, pv):
@@ -505,21 +559,12 @@ __device__ float refl_psi_polish(float a, float ds, float pu, float pv, float ga
 
 // body reflection candidate (sphere or vertical cylinder)
 template <typename T>
-__device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
+__device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Frame<T> &F, Geo<T> &g) {
     float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
     T a = q0.w;
-    Frame<T> F;
-    int acc = D_YES;
+    int acc = F.dec;
     bool sphere = (q1.y == 0.0f);
-    if (sphere) {
-        sphere_frame(S, P, mk3<T>(q0.x, q0.y, q0.z), a, F, band);
-    } else {
-        T rs = Sqrt((S.x - (T)q0.x) * (S.x - (T)q0.x) + (S.y - (T)q0.y) * (S.y - (T)q0.y));
-        if (!conj(acc, decide(rs - a, band, D_NO))) return D_NO;
-        T rp = Sqrt((P.x - (T)q0.x) * (P.x - (T)q0.x) + (P.y - (T)q0.y) * (P.y - (T)q0.y));
-        if (!conj(acc, decide(rp - a, band, D_NO))) return D_NO;
-        cyl_frame(S, P, (T)q0.x, (T)q0.y, a, F, band);
-    }
+    if (acc == D_NO) return D_NO;
     if (!F.axis_ok) return D_UNSURE;       // frame ill-conditioned: decide in FP64
     T dplus = F.gam - F.bs - F.bp;
     if (!conj(acc, decide(-dplus * a, band, D_NO))) return D_NO;      // strictly lit
@@ -593,21 +638,12 @@ __device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, Geo<T> &
 
 // creeping candidate, dir 0 short way, 1 long way
 template <typename T>
-__device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
+__device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T band, const Frame<T> &F, Geo<T> &g) {
     float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
     T a = q0.w;
     bool sphere = (q1.y == 0.0f);
-    Frame<T> F;
-    int acc = D_YES;
-    if (sphere) {
-        sphere_frame(S, P, mk3<T>(q0.x, q0.y, q0.z), a, F, band);
-    } else {
-        T rs = Sqrt((S.x - (T)q0.x) * (S.x - (T)q0.x) + (S.y - (T)q0.y) * (S.y - (T)q0.y));
-        if (!conj(acc, decide(rs - a, band, D_NO))) return D_NO;
-        T rp = Sqrt((P.x - (T)q0.x) * (P.x - (T)q0.x) + (P.y - (T)q0.y) * (P.y - (T)q0.y));
-        if (!conj(acc, decide(rp - a, band, D_NO))) return D_NO;
-        cyl_frame(S, P, (T)q0.x, (T)q0.y, a, F, band);
-    }
+    int acc = F.dec;
+    if (acc == D_NO) return D_NO;
     if (!F.axis_ok) return D_UNSURE;       // frame ill-conditioned: decide in FP64
     const T TWO_PI_T = T(6.283185307179586476925286766559);
     T dpsi = (dir == 0) ? (F.gam - F.bs - F.bp) : (TWO_PI_T - F.gam - F.bs - F.bp);
@@ -990,22 +1026,19 @@ __device__ void field_creep(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S
 }
 
 // total creeping path length s' + t + s
-__device__ __forceinline__ dfl creep_len(const Ctx &c, int b, v3t<float> S, v3t<float> P, const Geo<float> &g) {
+__device__ __forceinline__ dfl creep_len(const Ctx &c, int b, v3t<float> S, v3t<float> P, const Geo<float> &g,
+                                         const Frame<float> &F) {
     float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
-    if (q1.y == 0.0f) {
-        dfl ds2 = df_add(df_add(df_sq_diff(S.x, q0.x), df_sq_diff(S.y, q0.y)), df_sq_diff(S.z, q0.z));
-        dfl dp2 = df_add(df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y)), df_sq_diff(P.z, q0.z));
-        dfl a2 = two_prod(q0.w, q0.w);
-        a2.hi = -a2.hi; a2.lo = -a2.lo;
-        dfl sp = df_sqrt(df_add(ds2, a2)), sq = df_sqrt(df_add(dp2, a2));
-        return df_addf(df_add(sp, sq), g.t);
-    }
-    // cylinder: unrolled straight line, sqrt(H^2 + dz^2), H = d_s + a dphi + d_p
-    dfl rs2 = df_add(df_sq_diff(S.x, q0.x), df_sq_diff(S.y, q0.y));
-    dfl rp2 = df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y));
     dfl a2 = two_prod(q0.w, q0.w);
     a2.hi = -a2.hi; a2.lo = -a2.lo;
-    dfl ds_ = df_sqrt(df_add(rs2, a2)), dp_ = df_sqrt(df_add(rp2, a2));
+    if (q1.y == 0.0f) {
+        dfl dp2 = df_add(df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y)), df_sq_diff(P.z, q0.z));
+        dfl sq = df_sqrt(df_add(dp2, a2));
+        return df_addf(df_add(F.dsq, sq), g.t);
+    }
+    // cylinder: unrolled straight line, sqrt(H^2 + dz^2), H = d_s + a dphi + d_p
+    dfl rp2 = df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y));
+    dfl ds_ = F.dsq, dp_ = df_sqrt(df_add(rp2, a2));
     // a dphi = t sin(theta0), sin(theta0) = d_s / s'
     float adphi = g.t * (len_val(ds_) / g.sp);
     dfl H = df_addf(df_add(ds_, dp_), adphi);
@@ -1013,7 +1046,7 @@ __device__ __forceinline__ dfl creep_len(const Ctx &c, int b, v3t<float> S, v3t<
     dfl H2 = df_mul(H, H);
     return df_sqrt(df_add(H2, dz2));
 }
-__device__ __forceinline__ dx creep_len(const Ctx &, int, v3t<dx>, v3t<dx>, const Geo<dx> &g) {
+__device__ __forceinline__ dx creep_len(const Ctx &, int, v3t<dx>, v3t<dx>, const Geo<dx> &g, const Frame<dx> &) {
     return g.sp + g.t + g.sq;
 }
 
@@ -1095,7 +1128,9 @@ __device__ __noinline__ int esc_r2(const Ctx &c, int i, int j, v3t<float> Pf, v3
 __device__ __noinline__ int esc_rb(const Ctx &c, int b, v3t<float> Pf, const FreqC &fq, bool field, Contrib *out) {
     Geo<dx> g;
     v3t<dx> Sd = dxv(c.S), Pd = dxv(Pf);
-    int d = cand_rb<dx>(c, b, Sd, Pd, dx(0.0), g);
+    Frame<dx> F;
+    body_frame(c, b, Sd, Pd, dx(0.0), F);
+    int d = cand_rb<dx>(c, b, Sd, Pd, dx(0.0), F, g);
     if (d == D_YES && field) {
         Acc<dx> a;
         acc_zero(a);
@@ -1109,7 +1144,9 @@ __device__ __noinline__ int esc_creep(const Ctx &c, int b, int dir, v3t<float> P
                                       double half_lambda_max, unsigned enable, Contrib *out, int *caustic) {
     Geo<dx> g;
     v3t<dx> Sd = dxv(c.S), Pd = dxv(Pf);
-    int d = cand_creep<dx>(c, b, dir, Sd, Pd, dx(0.0), g);
+    Frame<dx> F;
+    body_frame(c, b, Sd, Pd, dx(0.0), F);
+    int d = cand_creep<dx>(c, b, dir, Sd, Pd, dx(0.0), F, g);
     *caustic = 0;
     if (d != D_YES) return d;
     bool sphere = c.body[2 * b + 1].y == 0.0f;
@@ -1144,12 +1181,16 @@ __global__ void __launch_bounds__(BLOCK, CREEP_MIN_BLOCKS) k_eval(DevScene S, co
     bool tri_sm = S.n_tri <= SMEM_TRI_MAX;
     float4 *s_tri = s_body + (body_sm ? 2 * S.n_body : 0);   // n_tri * 3 (if staged)
     float4 *s_aux = s_tri + (tri_sm ? 3 * S.n_tri : 0);      // n_tri * 3 (if staged)
-    float *s_weid = (float *)(s_aux + (tri_sm ? 3 * S.n_tri : 0));
+    float4 *s_txb = s_aux + (tri_sm ? 3 * S.n_tri : 0);       // n_body * 2 (if staged)
+    float *s_weid = (float *)(s_txb + (body_sm ? 2 * S.n_body : 0));
     for (int i = threadIdx.x; i < FOCK_N * 2; i += blockDim.x) s_fock[i] = S.fock32[i];
     for (int i = threadIdx.x; i < FOCK_NRES * 2; i += blockDim.x) s_res[i] = S.res32[i];
     for (int i = threadIdx.x; i < S.n_face; i += blockDim.x) s_face[i] = S.face32[i];
     if (body_sm)
-        for (int i = threadIdx.x; i < 2 * S.n_body; i += blockDim.x) s_body[i] = S.body[i];
+        for (int i = threadIdx.x; i < 2 * S.n_body; i += blockDim.x) {
+            s_body[i] = S.body[i];
+            s_txb[i] = S.txb[i];
+        }
     if (tri_sm)
         for (int i = threadIdx.x; i < 3 * S.n_tri; i += blockDim.x) {
             s_tri[i] = S.tri[i];
@@ -1172,6 +1213,7 @@ __global__ void __launch_bounds__(BLOCK, CREEP_MIN_BLOCKS) k_eval(DevScene S, co
         c.fock = s_fock; c.res = s_res; c.weid = s_weid; c.weid_L = S.weid_L;
         c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
         c.img = S.img;
+        c.txb = body_sm ? s_txb : S.txb;
         s_fq = fq_in;
     }
     __syncthreads();
@@ -1292,9 +1334,11 @@ __global__ void __launch_bounds__(BLOCK, CREEP_MIN_BLOCKS) k_eval(DevScene S, co
         // ---- curved bodies
 #pragma unroll 1
         for (int b = 0; b < c.n_body; ++b) {
+            Frame<T> F;
+            body_frame(c, b, Sx, P, band, F);
             if (S.enable & RT_EN_BODYREFL) {
                 Geo<T> g;
-                int d = cand_rb<T>(c, b, Sx, P, band, g);
+                int d = cand_rb<T>(c, b, Sx, P, band, F, g);
                 if constexpr (sizeof(T) == 4) {
                     if (d == D_UNSURE) {
                         // decided in FP64, and its field too (the geometry may be
@@ -1324,7 +1368,7 @@ __global__ void __launch_bounds__(BLOCK, CREEP_MIN_BLOCKS) k_eval(DevScene S, co
 #pragma unroll 1
                 for (int dir = 0; dir < 2; ++dir) {
                     Geo<T> g;
-                    int d = cand_creep<T>(c, b, dir, Sx, P, band, g);
+                    int d = cand_creep<T>(c, b, dir, Sx, P, band, F, g);
                     int cd = D_NO;
                     if (d == D_YES && sphere) {
                         // axial caustic flag: k d_perp < pi for some frequency, i.e. d_perp < lambda_max / 2
@@ -1352,7 +1396,7 @@ __global__ void __launch_bounds__(BLOCK, CREEP_MIN_BLOCKS) k_eval(DevScene S, co
                         if (!(g.dperp > T(0.0))) continue;        // exactly on the axis: no finite ray field
                     }
                     if (!PATHS) {
-                        LT L = creep_len(c, b, Sx, P, g);
+                        LT L = creep_len(c, b, Sx, P, g, F);
                         field_creep<T>(c, acc, fq, Sx, P, g, L, S.enable);
                     }
                 }
@@ -1382,7 +1426,7 @@ __global__ void __launch_bounds__(BLOCK, CREEP_MIN_BLOCKS) k_eval(DevScene S, co
 
 static size_t smem_bytes(const DevScene &S) {
     size_t n = FOCK_N * 2 + FOCK_NRES * 2 + S.n_face;
-    if (S.n_body <= SMEM_BODY_MAX) n += 2 * S.n_body;
+    if (S.n_body <= SMEM_BODY_MAX) n += 4 * S.n_body;
     if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;
     return n * sizeof(float4) + WEIDEMAN_N * sizeof(float) + 16;
 }
