@@ -242,11 +242,13 @@ __device__ __forceinline__ int blocked_impl(const Ctx &c, v3t<T> A, v3t<T> B, in
         }
         return D_NO;
     }
-    for (int b = 0; b < c.n_body; ++b) {
-        if (b == sb) continue;
-        int r = seg_body(c, b, A, B, band);
-        if (r == D_YES) return D_YES;
-        uns |= (r == D_UNSURE);
+    if constexpr (sizeof(T) == 4) {
+        for (int b = 0; b < c.n_body; ++b) {
+            if (b == sb) continue;
+            int r = seg_body(c, b, A, B, band);
+            if (r == D_YES) return D_YES;
+            uns |= (r == D_UNSURE);
+        }
     }
     return uns ? D_UNSURE : D_NO;
 }
