@@ -152,6 +152,42 @@ int rt_evaluate_host(rt_scene *scene, const float *rx_soa, int n_rx, float *e_ou
                      uint32_t *flags, const rt_options *opt, void *stream);
 
 /*
+ * rt_evaluate_host_noalloc -- the evaluation of rt_evaluate_host for callers
+ * that may not allocate device memory.  (An engineering addition: the paper
+ * has no counterpart.)
+ *
+ * Who needs it: code that runs where cudaMalloc is off limits -- for
+ * example inside a framework that has already claimed the device's memory
+ * for its own pool, in a loop that must not take cudaMalloc's implicit
+ * device-wide synchronisation, or in a process whose allocator policy
+ * forbids new device allocations after start-up.  rt_evaluate_host would
+ * allocate its staging buffers on its first call; this entry point uses a
+ * fixed device array compiled into the library instead and calls no
+ * cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Arguments and results are those of rt_evaluate_host (host rx_soa
+ * [3][n_rx], host e_out [n_f][3][n_rx][2], host flags [n_rx] or NULL,
+ * copies in, evaluates, copies out, synchronises the stream).
+ *
+ * Limits and sharing:
+ *   - The array holds RT_NOALLOC_SCRATCH_BYTES (8 MiB) on every device that
+ *     loads the library, for the life of the process.  A call needs
+ *     768 + n_rx * (16 + 24 * n_f) bytes (rounded up to 256-byte sections);
+ *     larger requests fail with RT_ERR_OVERFLOW before any work is queued.
+ *     With 3 frequencies that is up to about 95 000 receivers per call.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - All calls on a device share the one array and leave their data in it;
+ *     nothing in it needs clearing, since each call overwrites what it reads.
+ *     Calls whose GPU work overlaps (other threads, other streams) race on
+ *     the array: serialise them.
+ */
+#define RT_NOALLOC_SCRATCH_BYTES (8u << 20)
+int rt_evaluate_host_noalloc(rt_scene *scene, const float *rx_soa, int n_rx, float *e_out,
+                             uint32_t *flags, const rt_options *opt, void *stream);
+
+/*
  * Path lists (the visibility decisions of Eqs. 1-2) instead of the field.
  *   codes   device uint64 [n_rx][cap]: per receiver its paths in the
  *           enumeration order LOS, R1(face), R2(face, face), then per body

@@ -22,7 +22,9 @@ RT_PATH_LOS, RT_PATH_R1, RT_PATH_R2, RT_PATH_RB, RT_PATH_CP, RT_PATH_CM = range(
 FOCK_NRES = 8
 
 EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "rt_evaluate",
-           "rt_evaluate_host", "rt_paths", "rt_get_stats", "rt_fock_table", "rt_last_error")
+           "rt_evaluate_host", "rt_evaluate_host_noalloc", "rt_paths", "rt_get_stats", "rt_fock_table",
+           "rt_last_error")
+RT_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
 class CreepError(RuntimeError):
@@ -65,6 +67,7 @@ def load(build_if_missing=True):
     lib.rt_set_freqs.argtypes = [P, P, I]
     lib.rt_evaluate.argtypes = [P, P, I, P, P, P, P]
     lib.rt_evaluate_host.argtypes = [P, P, I, P, P, P, P]
+    lib.rt_evaluate_host_noalloc.argtypes = [P, P, I, P, P, P, P]
     lib.rt_paths.argtypes = [P, P, I, P, P, I, P, P, P]
     lib.rt_get_stats.argtypes = [P, P]
     lib.rt_fock_table.argtypes = [P, P, P, P, P, P]
@@ -167,6 +170,18 @@ class Scene:
         fl = np.empty(n, dtype=np.uint32) if flags else None
         _check(_lib.rt_evaluate_host(self._h, _ptr(rx_soa), n, _ptr(out), _ptr(fl),
                                      ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
+        return (out, fl) if flags else out
+
+    def evaluate_host_noalloc(self, rx_soa, flags=False, opts=None, stream=None):
+        """evaluate_host through the entry point that allocates no device
+        memory (fixed 8 MiB device array shared by all calls on a device)."""
+        rx_soa = np.ascontiguousarray(np.asarray(rx_soa, dtype=np.float32))
+        n = rx_soa.shape[1]
+        out = np.empty((self.n_f, 3, n, 2), dtype=np.float32)
+        fl = np.empty(n, dtype=np.uint32) if flags else None
+        _check(_lib.rt_evaluate_host_noalloc(self._h, _ptr(rx_soa), n, _ptr(out), _ptr(fl),
+                                             ctypes.byref(opts) if opts is not None else None,
+                                             _stream_handle(stream)))
         return (out, fl) if flags else out
 
     def paths(self, rx_soa, cap=256, opts=None, stream=None):

@@ -526,3 +526,62 @@ int rt_fock_table(double *xi_lo, double *step, int *n, double *g, double *dg, do
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Evaluation from host buffers without device allocation (see creep.h).
+// The staging buffers live in one file-scope device array; its device
+// address is looked up once per device and then reused.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES];   // device address per device (nullptr: not looked up yet)
+
+size_t round256(size_t n) { return (n + 255) & ~(size_t)255; }
+}  // namespace
+
+extern "C" int rt_evaluate_host_noalloc(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
+                                        const rt_options *opt, void *stream) {
+    if (!s) return fail(RT_ERR_ARG, "rt_evaluate_host_noalloc: NULL scene");
+    if (n_rx < 0) return fail(RT_ERR_ARG, "rt_evaluate_host_noalloc: n_rx < 0");
+    if (!s->f_set) return fail(RT_ERR_STATE, "frequencies not set");
+    if (n_rx == 0) return RT_OK;
+    if (!rx_soa || !e_out) return fail(RT_ERR_ARG, "rt_evaluate_host_noalloc: NULL buffer");
+    size_t nf = s->freqs.size();
+    size_t rx_bytes = round256(sizeof(float) * 3 * (size_t)n_rx);
+    size_t e_bytes = round256(sizeof(float) * 2 * 3 * nf * (size_t)n_rx);
+    size_t fl_bytes = round256(sizeof(uint32_t) * (size_t)n_rx);
+    size_t need = rx_bytes + e_bytes + fl_bytes;
+    if (need > (size_t)RT_NOALLOC_SCRATCH_BYTES)
+        return fail(RT_ERR_OVERFLOW,
+                    "rt_evaluate_host_noalloc: %d receivers x %d frequencies need %zu bytes of device scratch, "
+                    "the fixed array holds %u; split the receivers into smaller calls",
+                    n_rx, (int)nf, need, RT_NOALLOC_SCRATCH_BYTES);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(RT_ERR_ARG, "rt_evaluate_host_noalloc: device %d", dev);
+    void *base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || !p)
+                return fail(RT_ERR_CUDA, "rt_evaluate_host_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            g_noalloc_ptr[dev] = p;
+        }
+        base = g_noalloc_ptr[dev];
+    }
+    float *d_rx = (float *)base;
+    float *d_e = (float *)((unsigned char *)base + rx_bytes);
+    uint32_t *d_fl = (uint32_t *)((unsigned char *)base + rx_bytes + e_bytes);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(d_rx, rx_soa, sizeof(float) * 3 * (size_t)n_rx, cudaMemcpyHostToDevice, st));
+    int rc = rt_evaluate(s, d_rx, n_rx, d_e, flags ? d_fl : nullptr, opt, stream);
+    if (rc != RT_OK) return rc;
+    CK(cudaMemcpyAsync(e_out, d_e, sizeof(float) * 2 * 3 * nf * (size_t)n_rx, cudaMemcpyDeviceToHost, st));
+    if (flags) CK(cudaMemcpyAsync(flags, d_fl, sizeof(uint32_t) * (size_t)n_rx, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return RT_OK;
+}
