@@ -457,7 +457,13 @@ static void sphere_frame(const body *B, v3 S, v3 P, body_frame *F) {
     if (nv == 0.0) {
         v3 tmp = fabs(F->u.x) < 0.9 ? V(1, 0, 0) : V(0, 1, 0);
         F->v = unit(cross(F->u, tmp));
-    } else F->v = scl(vperp, 1.0 / nv);
+    } else {
+        /* a second Gram-Schmidt pass: when P lies on (or within rounding of)
+           the S-c axis, vperp is rounding noise and its normalisation alone
+           need not be perpendicular to u */
+        F->v = scl(vperp, 1.0 / nv);
+        F->v = unit(sub(F->v, scl(F->u, dot(F->v, F->u))));
+    }
     F->bs = acos(B->a / F->ds); F->bp = acos(B->a / F->dp);
     F->pu = dot(wp, F->u); F->pv = dot(wp, F->v);
 }
@@ -469,9 +475,12 @@ static int cylinder_frame(const body *B, v3 S, v3 P, body_frame *F) {
     if (!(F->ds > B->a) || !(F->dp > B->a)) return 0;
     F->u = V(sx / F->ds, sy / F->ds, 0.0);
     F->gam = atan2(fabs(sx * py - sy * px), sx * px + sy * py);
-    double wx = px - (px * F->u.x + py * F->u.y) * F->u.x, wy = py - (px * F->u.x + py * F->u.y) * F->u.y;
-    double nw = sqrt(wx * wx + wy * wy);
-    F->v = (nw == 0.0) ? V(-F->u.y, F->u.x, 0.0) : V(wx / nw, wy / nw, 0.0);
+    /* v = +-(z x u), the horizontal unit vector normal to u, turned toward P;
+       side = (z x u).(P - c) >= 0 selects +.  (Normalising p - (p.u)u instead
+       gives a v that is not normal to u when P lies on the S-c line in
+       projection, where that vector is rounding noise.) */
+    double side = F->u.x * py - F->u.y * px;
+    F->v = (side < 0.0) ? V(F->u.y, -F->u.x, 0.0) : V(-F->u.y, F->u.x, 0.0);
     F->bs = acos(B->a / F->ds); F->bp = acos(B->a / F->dp);
     F->pu = px * F->u.x + py * F->u.y; F->pv = px * F->v.x + py * F->v.y;
     return 1;

@@ -147,6 +147,46 @@ def test_reflection_point_law_of_reflection(oracle_mod, trial):
     assert si @ n > 0 and sr @ n > 0
 
 
+@pytest.mark.parametrize("trial", range(8))
+def test_reflection_with_receiver_on_the_source_axis(oracle_mod, trial):
+    """Degenerate frames: a receiver straight below the source (the same x, y,
+    so on the S-c line of every vertical cylinder in projection) and a receiver
+    on a sphere's S-c axis.  The reflection is then a retro-reflection in
+    projection: the law of reflection still holds, the reflection point lies on
+    the surface, and for the cylinder it sits half way down (equal horizontal
+    runs).  Float inputs, as the scenes hold them."""
+    rng = np.random.default_rng(700 + trial)
+    c = np.array([rng.uniform(-3, 3), rng.uniform(-3, 3), 0.0], dtype=np.float32).astype(np.float64)
+    a = float(np.float32(rng.uniform(0.15, 0.3)))
+    S = np.array([1.0, 1.0, 2.0])
+    if trial % 2 == 0:
+        body = np.array([BODY_CYLINDER, *c, a, 1.9])
+        P = np.array([S[0], S[1], float(np.float32(rng.uniform(0.3, 1.7)))])
+    else:
+        body = np.array([BODY_SPHERE, *c, a, 0.0])
+        u = (S - c) / np.linalg.norm(S - c)
+        P = (c + u * float(rng.uniform(1.5, 3.0)) * a).astype(np.float32).astype(np.float64)
+    g = oracle_mod.body_reflection(body, S, P)
+    assert g is not None
+    Q, n = g["Q"], g["n"]
+    si, sr = (S - Q) / np.linalg.norm(S - Q), (P - Q) / np.linalg.norm(P - Q)
+    assert abs(si @ n - sr @ n) < 1e-9
+    assert abs(np.cross(si, sr) @ n) < 1e-9            # coplanar with the normal
+    if body[0] == BODY_CYLINDER:
+        assert abs(np.hypot(*(Q - c)[:2]) - a) < 1e-12 and n[2] == 0.0
+        assert abs(Q[2] - 0.5 * (S[2] + P[2])) < 1e-9
+    else:
+        assert abs(np.linalg.norm(Q - c) - a) < 1e-12
+    # the creeping rays' frame stays orthonormal: both surface points on the body
+    for direction in (0, 1):
+        cg = oracle_mod.body_creeping(body, S, P, direction)
+        if cg is None:
+            continue
+        for key in ("Q1", "Q2"):
+            rr = np.hypot(*(cg[key] - c)[:2]) if body[0] == BODY_CYLINDER else np.linalg.norm(cg[key] - c)
+            assert abs(rr - a) < 1e-12
+
+
 def _ray_body(S, d, body):
     """First intersection of the ray S + tau d with the body surface (brute force)."""
     c, a = body[1:4], body[4]
