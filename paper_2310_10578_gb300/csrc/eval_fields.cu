@@ -320,6 +320,7 @@ struct Geo {
     T sp, t, sq, amp, rho_g, inv_f1, inv_f2, dperp;
     int caus;
     dfl Lf;          // FP32 mode: total path length as double-float (reflection off a body)
+    v3t<T> dr;       // reflection off a body: P - Q1, free of cancellation near the surface
 };
 
 template <typename T>
@@ -393,9 +394,11 @@ template <typename T>
 struct Frame {
     v3t<T> u, v;
     T ds, dp, gam, bs, bp, pu, pv;
+    T sps, sqp;     // tangent lengths sqrt(ds^2 - a^2), sqrt(dp^2 - a^2) (horizontal for cylinders)
     bool axis_ok;   // v well conditioned (P not near the S-c axis)
     int dec;        // D_YES: lateral paths possible; D_NO: source or receiver over a cylinder's footprint
     dfl dsq;        // FP32 mode: sqrt(ds^2 - a^2) as double-float (from the FP64 source precomputation)
+    dfl dpq;        // FP32 mode: sqrt(dp^2 - a^2) as double-float
 };
 
 template <typename T>
@@ -411,9 +414,12 @@ __device__ void sphere_frame(v3t<T> S, v3t<T> P, v3t<T> cc, T a, Frame<T> &F, T 
         v3t<T> tmp = (Fabs(F.u.x) < T(0.9)) ? mk3<T>(1, 0, 0) : mk3<T>(0, 1, 0);
         F.v = unit3(cross3(F.u, tmp));
     } else {
+        // second Gram-Schmidt pass: vp is rounding noise for P on the S-c axis
         F.v = vp * (T(1) / nv);
+        F.v = unit3(F.v - F.u * dot3(F.v, F.u));
     }
     F.bs = Acos(a / F.ds); F.bp = Acos(a / F.dp);
+    F.sps = Sqrt(F.ds * F.ds - a * a); F.sqp = Sqrt(F.dp * F.dp - a * a);
     F.pu = dot3(wp, F.u); F.pv = dot3(wp, F.v);
 }
 
@@ -423,20 +429,14 @@ __device__ void cyl_frame(v3t<T> S, v3t<T> P, T cx, T cy, T a, Frame<T> &F, T ba
     F.ds = Sqrt(sx * sx + sy * sy); F.dp = Sqrt(px * px + py * py);
     F.u = mk3<T>(sx / F.ds, sy / F.ds, T(0));
     F.gam = Atan2(Fabs(sx * py - sy * px), sx * px + sy * py);
-    if constexpr (sizeof(T) == 4) {
-        // in the horizontal plane v is +-(z x u); only its sign depends on P, and
-        // that sign is uncertain only for P within FP32 rounding of the S-c line
-        T side = F.u.x * py - F.u.y * px;                 // (z x u).(P - c)
-        F.axis_ok = Fabs(side) > T(4e-6) * F.dp;
-        F.v = (side < T(0)) ? mk3<T>(F.u.y, -F.u.x, T(0)) : mk3<T>(-F.u.y, F.u.x, T(0));
-    } else {
-        T pd = px * F.u.x + py * F.u.y;
-        T wx = px - pd * F.u.x, wy = py - pd * F.u.y;
-        T nw = Sqrt(wx * wx + wy * wy);
-        F.axis_ok = true;
-        F.v = (nw == T(0)) ? mk3<T>(-F.u.y, F.u.x, T(0)) : mk3<T>(wx / nw, wy / nw, T(0));
-    }
+    // in the horizontal plane v is +-(z x u), turned toward P; in FP32 its sign
+    // is uncertain only for P within rounding of the S-c line
+    T side = F.u.x * py - F.u.y * px;                 // (z x u).(P - c)
+    F.v = (side < T(0)) ? mk3<T>(F.u.y, -F.u.x, T(0)) : mk3<T>(-F.u.y, F.u.x, T(0));
+    if constexpr (sizeof(T) == 4) F.axis_ok = Fabs(side) > T(4e-6) * F.dp;
+    else F.axis_ok = true;
     F.bs = Acos(a / F.ds); F.bp = Acos(a / F.dp);
+    F.sps = Sqrt(F.ds * F.ds - a * a); F.sqp = Sqrt(F.dp * F.dp - a * a);
     F.pu = px * F.u.x + py * F.u.y; F.pv = px * F.v.x + py * F.v.y;
 }
 
@@ -475,7 +475,23 @@ __device__ void body_frame(const Ctx &c, int b, v3t<float> S, v3t<float> P, floa
         F.v = (side < 0.0f) ? mk3(F.u.y, -F.u.x, 0.0f) : mk3(-F.u.y, F.u.x, 0.0f);
     }
     F.gam = atan2f(F.pv, F.pu);
-    F.bp = acosf(a / F.dp);
+    // receiver tangent length and angle from d_p^2 - a^2 formed exactly in
+    // double-float (X - c and a^2 are exact): well conditioned also for a
+    // receiver within a few ulp of the surface, where acos(a / d_p) and
+    // d_p^2 - a^2 in FP32 lose most of their digits
+    dfl q2 = df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y));
+    if (q1.y == 0.0f) q2 = df_add(q2, df_sq_diff(P.z, q0.z));
+    dfl a2 = two_prod(a, a);
+    a2.hi = -a2.hi; a2.lo = -a2.lo;
+    q2 = df_add(q2, a2);
+    if (q2.hi > 0.0f) {
+        F.dpq = df_sqrt(q2);
+    } else {
+        F.dpq.hi = 0.0f; F.dpq.lo = 0.0f;
+    }
+    F.sqp = F.dpq.hi;
+    F.sps = F.dsq.hi;
+    F.bp = atan2f(F.sqp, a);
 }
 __device__ void body_frame(const Ctx &c, int b, v3t<dx> S, v3t<dx> P, dx band, Frame<dx> &F) {
     float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
@@ -559,6 +575,28 @@ __device__ float refl_psi_polish(float a, float ds, float pu, float pv, float ga
     return (float)psi;
 }
 
+// X - (c + a n) per component as double-float, for FP32 X, c, n and radius a:
+// X - c is exact, a n is exact, so the vector (and its length) is that of the
+// FP32 surface point c + a n itself, also when X lies within a wavelength of
+// the surface, where |X - c|^2 + a^2 - 2 a (X - c).n would cancel.  horiz:
+// horizontal components only (vertical cylinders), z returned as zero.
+__device__ __forceinline__ void df_to_surface(v3t<float> X, float4 c, float a, v3t<float> n, bool horiz, dfl w[3]) {
+    dfl m;
+    m = two_prod(a, n.x); m.hi = -m.hi; m.lo = -m.lo;
+    w[0] = df_add(two_sum(X.x, -c.x), m);
+    m = two_prod(a, n.y); m.hi = -m.hi; m.lo = -m.lo;
+    w[1] = df_add(two_sum(X.y, -c.y), m);
+    if (horiz) {
+        w[2].hi = 0.0f; w[2].lo = 0.0f;
+    } else {
+        m = two_prod(a, n.z); m.hi = -m.hi; m.lo = -m.lo;
+        w[2] = df_add(two_sum(X.z, -c.z), m);
+    }
+}
+__device__ __forceinline__ dfl df_norm3(const dfl w[3]) {
+    return df_sqrt(df_add(df_add(df_sq(w[0]), df_sq(w[1])), df_sq(w[2])));
+}
+
 // body reflection candidate (sphere or vertical cylinder)
 template <typename T>
 __device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Frame<T> &F, Geo<T> &g) {
@@ -601,29 +639,30 @@ __device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Fr
     }
     v3t<T> shi = unit3(Q - S);
     T cth = -dot3(shi, n);
-    if constexpr (sizeof(T) == 4) {
-        // total length s^i + s^r from the body-centred frame (stationary in psi,
-        // so the FP32 root error enters at second order; the large squares are
-        // exact double-float): |X - Q|^2 = |X - c|^2 + a^2 - 2 a (X - c).n
-        dfl a2 = two_prod(a, a);
-        float cpsi = cs, spsi = sn;
-        if (sphere) {
-            dfl ds2 = df_add(df_add(df_sq_diff(S.x, q0.x), df_sq_diff(S.y, q0.y)), df_sq_diff(S.z, q0.z));
-            dfl dp2 = df_add(df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y)), df_sq_diff(P.z, q0.z));
-            dfl si = df_sqrt(df_addf(df_add(ds2, a2), -2.0f * a * F.ds * cpsi));
-            dfl sr = df_sqrt(df_addf(df_add(dp2, a2), -2.0f * a * (F.pu * cpsi + F.pv * spsi)));
-            g.Lf = df_add(si, sr);
-        } else {
-            dfl ds2 = df_add(df_sq_diff(S.x, q0.x), df_sq_diff(S.y, q0.y));
-            dfl dp2 = df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y));
-            dfl l1 = df_sqrt(df_addf(df_add(ds2, a2), -2.0f * a * F.ds * cpsi));
-            dfl l2 = df_sqrt(df_addf(df_add(dp2, a2), -2.0f * a * (F.pu * cpsi + F.pv * spsi)));
-            dfl H = df_add(l1, l2);
-            g.Lf = df_sqrt(df_add(df_mul(H, H), df_sq_diff(P.z, S.z)));
-        }
-    }
     if (!conj(acc, vis_to_dec(blocked(c, S, Q, -1, -1, b, band)))) return D_NO;
     if (!conj(acc, vis_to_dec(blocked(c, Q, P, -1, -1, b, band)))) return D_NO;
+    if constexpr (sizeof(T) == 4) {
+        // total length s^i + s^r to the FP32 surface point c + a n, each leg in
+        // double-float (the length is stationary in psi, so the FP32 root and
+        // the rounding of n enter at second order along the surface and by
+        // about a ulp of a across it)
+        dfl ws[3], wp[3];
+        df_to_surface(S, q0, a, n, !sphere, ws);
+        df_to_surface(P, q0, a, n, !sphere, wp);
+        dfl si = df_norm3(ws), sr = df_norm3(wp);
+        if (sphere) {
+            g.Lf = df_add(si, sr);
+            g.dr = mk3<T>(wp[0].hi + wp[0].lo, wp[1].hi + wp[1].lo, wp[2].hi + wp[2].lo);
+        } else {
+            // unrolled: horizontal run l1 + l2, vertical rise P.z - S.z
+            dfl H = df_add(si, sr);
+            g.Lf = df_sqrt(df_add(df_mul(H, H), df_sq_diff(P.z, S.z)));
+            float l1 = si.hi, l2 = sr.hi;
+            g.dr = mk3<T>(wp[0].hi + wp[0].lo, wp[1].hi + wp[1].lo, (P.z - S.z) * (l2 / (l1 + l2)));
+        }
+    } else {
+        g.dr = P - Q;
+    }
     g.Q1 = Q; g.n1 = n;
     if (sphere) {
         g.inv_f1 = T(2) / (a * cth);
@@ -661,8 +700,8 @@ __device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T ba
         v3t<T> cc = mk3<T>(q0.x, q0.y, q0.z);
         g.Q1 = cc + g.n1 * a;
         g.Q2 = cc + g.n2 * a;
-        g.sp = Sqrt(F.ds * F.ds - a * a);
-        g.sq = Sqrt(F.dp * F.dp - a * a);
+        g.sp = F.sps;
+        g.sq = F.sqp;
         g.t = a * dpsi;
         g.rho_g = a;
         g.caus = (dir == 1);
@@ -676,7 +715,7 @@ __device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T ba
         if (band == T(0)) { T sb, cb; SinCos(F.bs, &sb, &cb); dq1 = a * sb; }
         g.amp = (g.dperp > T(0)) ? Sqrt(dq1 / g.dperp) / Sqrt(g.sq) / g.sp : T(0);
     } else {
-        T ds_ = Sqrt(F.ds * F.ds - a * a), dp_ = Sqrt(F.dp * F.dp - a * a);
+        T ds_ = F.sps, dp_ = F.sqp;
         T dz = P.z - S.z;
         T H = ds_ + a * dpsi + dp_;
         T ell = Sqrt(H * H + dz * dz);
@@ -954,10 +993,14 @@ __device__ __forceinline__ void add_ray(Acc<T> &acc, const FreqC &fq, v3t<T> e, 
 template <typename T, typename L>
 __device__ void field_body_refl(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S, v3t<T> P, const Geo<T> &g, L len) {
     v3t<T> Q = g.Q1, n = g.n1;
-    v3t<T> di = Q - S, dr = P - Q;
-    T si = norm3(di), sr = norm3(dr);
-    v3t<T> shi = di * (T(1) / si), shr = dr * (T(1) / sr);
+    v3t<T> di = Q - S;
+    T si = norm3(di), sr = norm3(g.dr);
+    v3t<T> shi = di * (T(1) / si);
     T cth = -dot3(shi, n);
+    // reflected direction by the law of reflection: unlike (P - Q) / |P - Q|
+    // it does not turn with a rounding-size shift of Q along the surface,
+    // which matters when the receiver is within a wavelength of the body
+    v3t<T> shr = unit3(shi + n * (T(2) * cth));
     v3t<T> ep = cross3(n, shi);
     T ne = norm3(ep);
     if (ne == T(0)) {
@@ -1030,17 +1073,10 @@ __device__ void field_creep(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S
 // total creeping path length s' + t + s
 __device__ __forceinline__ dfl creep_len(const Ctx &c, int b, v3t<float> S, v3t<float> P, const Geo<float> &g,
                                          const Frame<float> &F) {
-    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
-    dfl a2 = two_prod(q0.w, q0.w);
-    a2.hi = -a2.hi; a2.lo = -a2.lo;
-    if (q1.y == 0.0f) {
-        dfl dp2 = df_add(df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y)), df_sq_diff(P.z, q0.z));
-        dfl sq = df_sqrt(df_add(dp2, a2));
-        return df_addf(df_add(F.dsq, sq), g.t);
-    }
+    float4 q1 = c.body[2 * b + 1];
+    if (q1.y == 0.0f) return df_addf(df_add(F.dsq, F.dpq), g.t);
     // cylinder: unrolled straight line, sqrt(H^2 + dz^2), H = d_s + a dphi + d_p
-    dfl rp2 = df_add(df_sq_diff(P.x, q0.x), df_sq_diff(P.y, q0.y));
-    dfl ds_ = F.dsq, dp_ = df_sqrt(df_add(rp2, a2));
+    dfl ds_ = F.dsq, dp_ = F.dpq;
     // a dphi = t sin(theta0), sin(theta0) = d_s / s'
     float adphi = g.t * (len_val(ds_) / g.sp);
     dfl H = df_addf(df_add(ds_, dp_), adphi);

@@ -1,0 +1,71 @@
+"""The N > 1 host logic of bench.py on CPU, two gloo ranks.
+
+Receivers are independent (Eqs. 1-4 per receiver), so the evaluation shards
+across ranks with no data-path exchange: each rank owns a distinct receiver
+grid of the same size, the job's time is the slowest rank's, and the job's
+throughput is all ranks' samples over that time.  No GPU is used here.
+"""
+import os
+import socket
+import sys
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import bench
+        sc = bench.make_scene(rank, world)
+        # a rank-dependent "time": the reduction must return the slowest rank's
+        ms, e2e = bench.max_over_ranks([1.0 + rank, 10.0 - rank])
+        grids = [None] * world
+        dist.all_gather_object(grids, sc.rx[:64].copy())
+        # the reference arm runs on rank 0 only; other ranks return without work
+        rc = bench.run_reference(None) if rank != 0 else 0
+        q.put((rank, ms, e2e, sc.n_rx, len(sc.freqs), [g.tolist() for g in grids], rc))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_shard_without_exchange():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=240) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for rank, ms, e2e, n_rx, n_f, grids, rc in res:
+        assert ms == 2.0 and e2e == 10.0          # max over ranks, on every rank
+        assert n_rx == 65536 and n_f == 3          # same per-rank work (weak scaling)
+        assert rc == 0
+    g0, g1 = (np.asarray(g) for g in res[0][5])
+    assert not np.any(np.all(np.isclose(g0[:, None, :], g1[None, :, :], atol=1e-6), axis=2))   # distinct receivers
+    assert np.allclose(g1[:, 1:], g0[:, 1:]) and np.allclose(g1[:, 0] - g0[:, 0], 10.0 / 256 / 2, atol=1e-5)
+
+
+def test_single_process_reduction_and_throughput():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks([3.0, 4.5]) == [3.0, 4.5]
+    assert bench.job_throughput(196608, 4, 0.5) == pytest.approx(4 * 196608 / 0.5)
