@@ -100,7 +100,13 @@ typedef struct {
 } rt_options;
 
 typedef struct {
-    unsigned long long escalated_receivers; /* receivers with RT_FLAG_ESCALATED in the last rt_evaluate/rt_paths */
+    /* candidate decisions of the last rt_evaluate / rt_paths on this scene
+       that were taken in FP64 (RT_PREC_FP32 only; a receiver with at least
+       one carries RT_FLAG_ESCALATED) */
+    unsigned long long escalated_candidates;
+    /* kernel launches the last rt_evaluate / rt_paths queued (the path
+       classes run as separate kernels, per chunk of 4 frequencies) */
+    unsigned long long kernel_launches;
 } rt_stats;
 
 /*

@@ -42,7 +42,7 @@ class rt_options(ctypes.Structure):
 
 
 class rt_stats(ctypes.Structure):
-    _fields_ = [("escalated_receivers", ctypes.c_ulonglong)]
+    _fields_ = [("escalated_candidates", ctypes.c_ulonglong), ("kernel_launches", ctypes.c_ulonglong)]
 
 
 _lib = None
@@ -198,7 +198,7 @@ class Scene:
     def stats(self):
         st = rt_stats()
         _check(_lib.rt_get_stats(self._h, ctypes.byref(st)))
-        return {"escalated_receivers": int(st.escalated_receivers)}
+        return {"escalated_candidates": int(st.escalated_candidates), "kernel_launches": int(st.kernel_launches)}
 
 
 def fock_table():

@@ -124,7 +124,7 @@ struct rt_scene {
     double *d_freq = nullptr;
     float4 *d_img = nullptr;            // source images, see DevScene::img
     float4 *d_txb = nullptr;            // source-side body frames, see DevScene::txb
-    unsigned long long *d_esc = nullptr;
+    unsigned long long *d_esc = nullptr;   // [CTR_N]: FP64-decided candidates, then one work queue per launch
     DevTable *table = nullptr;
     // state
     bool tx_set = false, f_set = false;
@@ -136,6 +136,7 @@ struct rt_scene {
     uint32_t *io_fl = nullptr;
     size_t io_cap = 0;
     cudaStream_t last_stream = nullptr;
+    int last_launches = 0;
 };
 
 #define CK(x)                                                                              \
@@ -313,7 +314,7 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
     CKS(cudaMalloc(&s->d_face_tris, sizeof(int) * ntr));
     CKS(cudaMalloc(&s->d_body, sizeof(float4) * 2 * nbd));
     CKS(cudaMalloc(&s->d_freq, sizeof(double) * RT_MAX_FREQS));
-    CKS(cudaMalloc(&s->d_esc, sizeof(unsigned long long)));
+    CKS(cudaMalloc(&s->d_esc, sizeof(unsigned long long) * CTR_N));
     CKS(cudaMalloc(&s->d_img, sizeof(float4) * 2 * (nfc + nfc * nfc)));
     CKS(cudaMalloc(&s->d_txb, sizeof(float4) * 2 * nbd));
     if (n_tri > 0) {
@@ -327,7 +328,7 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
         CKS(cudaMemcpy(s->d_face_rng, hr.data(), sizeof(int2) * nf, cudaMemcpyHostToDevice));
     }
     if (n_body > 0) CKS(cudaMemcpy(s->d_body, hb.data(), sizeof(float4) * 2 * n_body, cudaMemcpyHostToDevice));
-    CKS(cudaMemset(s->d_esc, 0, sizeof(unsigned long long)));
+    CKS(cudaMemset(s->d_esc, 0, sizeof(unsigned long long) * CTR_N));
     *out = s;
     return RT_OK;
 }
@@ -452,9 +453,9 @@ int rt_evaluate(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint32
     if (n_rx > 0 && (!rx_soa || !e_out)) return fail(RT_ERR_ARG, "rt_evaluate: NULL buffer");
     if (n_rx == 0) return RT_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    CK(cudaMemsetAsync(s->d_esc, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(s->d_esc, 0, sizeof(unsigned long long) * CTR_N, st));
     s->last_stream = st;
-    return launch_eval(D, rx_soa, n_rx, e_out, flags, nullptr, nullptr, 0, prec, s->d_esc, st);
+    return launch_eval(D, rx_soa, n_rx, e_out, flags, nullptr, nullptr, 0, prec, s->d_esc, st, &s->last_launches);
 }
 
 int rt_paths(rt_scene *s, const float *rx_soa, int n_rx, uint64_t *codes, int32_t *counts, int cap, uint32_t *flags,
@@ -468,9 +469,9 @@ int rt_paths(rt_scene *s, const float *rx_soa, int n_rx, uint64_t *codes, int32_
     if (n_rx > 0 && (!rx_soa || !codes || !counts)) return fail(RT_ERR_ARG, "rt_paths: NULL buffer");
     if (n_rx == 0) return RT_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    CK(cudaMemsetAsync(s->d_esc, 0, sizeof(unsigned long long), st));
+    CK(cudaMemsetAsync(s->d_esc, 0, sizeof(unsigned long long) * CTR_N, st));
     s->last_stream = st;
-    return launch_eval(D, rx_soa, n_rx, nullptr, flags, codes, counts, cap, prec, s->d_esc, st);
+    return launch_eval(D, rx_soa, n_rx, nullptr, flags, codes, counts, cap, prec, s->d_esc, st, &s->last_launches);
 }
 
 int rt_evaluate_host(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags, const rt_options *opt,
@@ -504,7 +505,8 @@ int rt_get_stats(rt_scene *s, rt_stats *out) {
     CK(cudaStreamSynchronize(s->last_stream));
     unsigned long long v = 0;
     CK(cudaMemcpy(&v, s->d_esc, sizeof(v), cudaMemcpyDeviceToHost));
-    out->escalated_receivers = v;
+    out->escalated_candidates = v;
+    out->kernel_launches = (unsigned long long)s->last_launches;
     return RT_OK;
 }
 

@@ -31,9 +31,6 @@ enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5 };
 
 constexpr int NFC = 4;                 // frequencies per launch (accumulators in registers)
 constexpr int BLOCK = 128;
-#ifndef CREEP_MIN_BLOCKS
-#define CREEP_MIN_BLOCKS 2             // resident blocks per SM the register budget is sized for
-#endif
 constexpr int SMEM_TRI_MAX = 256;
 constexpr int SMEM_BODY_MAX = 256;
 
@@ -553,26 +550,77 @@ __device__ dx refl_psi(dx a, dx ds, dx pu, dx pv, dx gam) {
     }
     return dx(0.5) * (lo + hi);
 }
-// FP64 Newton polish of an FP32 root (near-grazing reflection points)
-__device__ float refl_psi_polish(float a, float ds, float pu, float pv, float gam, float psi0) {
-    double lo = 0.0, hi = gam, psi = psi0;
-    for (int it = 0; it < 12; ++it) {
-        double sn, cs;
-        sincos(psi, &sn, &cs);
-        double qx = a * cs, qy = a * sn, tx = -a * sn, ty = a * cs;
-        double sx = qx - ds, sy = qy, rx = qx - pu, ry = qy - pv;
-        double fs = sqrt(sx * sx + sy * sy), fr = sqrt(rx * rx + ry * ry);
-        double gs = (sx * tx + sy * ty) / fs, gr = (rx * tx + ry * ty) / fr;
+// FP64 Newton steps for the reflection point, on the unit vector
+// n = (cos psi, sin psi) itself and without trigonometric calls: for Q = a n
+// on the circle, (Q - S).t = a ds sin(psi) and (Q - P).t = a (pu sin(psi) -
+// pv cos(psi)), t the unit tangent, so
+//   dL/dpsi   = a [ds s / |Q - S| + (pu s - pv c) / |Q - P|],
+//   d2L/dpsi2 = (X.Q - (dL/dpsi)_X^2) / |Q - X| summed over X = S, P,
+// and n is rotated by each step d with cos d, sin d from their Taylor series
+// (|d| <= 1e-3).  Returns false (no result) if a step is too large or the
+// curvature not positive; the caller then brackets.
+__device__ bool refl_newton64(double A, double Ds, double Pu, double Pv, double *c_io, double *s_io) {
+    double c = *c_io, s = *s_io;
+    const double dp2 = Pu * Pu + Pv * Pv;
+    for (int it = 0; it < 6; ++it) {
+        double fs = sqrt(A * A + Ds * Ds - 2.0 * A * Ds * c);
+        double fr = sqrt(A * A + dp2 - 2.0 * A * (Pu * c + Pv * s));
+        double gs = A * Ds * s / fs, gr = A * (Pu * s - Pv * c) / fr;
         double g = gs + gr;
-        if (g == 0.0) break;
-        if (g < 0.0) lo = psi; else hi = psi;
-        double g2 = ((double)ds * qx - gs * gs) / fs + ((double)pu * qx + (double)pv * qy - gr * gr) / fr;
-        double nx = psi - g / g2;
-        if (!(g2 > 0.0) || nx < lo || nx > hi) nx = 0.5 * (lo + hi);
-        if (fabs(nx - psi) <= 1e-15 * fabs(psi)) { psi = nx; break; }
-        psi = nx;
+        double g2 = (Ds * A * c - gs * gs) / fs + (A * (Pu * c + Pv * s) - gr * gr) / fr;
+        if (!(g2 > 0.0)) return false;
+        double d = -g / g2;
+        if (!(fabs(d) <= 1e-3)) return false;
+        double d2 = d * d;
+        double cd = 1.0 - d2 * (0.5 - d2 * (1.0 / 24.0));
+        double sd = d * (1.0 - d2 * ((1.0 / 6.0) - d2 * (1.0 / 120.0)));
+        double cn = c * cd - s * sd, sn = s * cd + c * sd;
+        c = cn; s = sn;
+        if (fabs(d) <= 1e-13) {
+            *c_io = c; *s_io = s;
+            return true;
+        }
     }
-    return (float)psi;
+    return false;
+}
+
+// FP64 refinement of an FP32 reflection point (near-grazing incidence, where
+// the FP32 root of dL/dpsi is too coarse for cos(theta_i)); FP64 bisection
+// when Newton does not converge.  Returns (cos psi, sin psi) in FP32.
+__device__ __noinline__ void refl_polish(float a, float ds, float pu, float pv, float gam, float psi0,
+                                         float *cs_out, float *sn_out) {
+    float c0f, s0f;
+    sincosf(psi0, &s0f, &c0f);
+    double c = c0f, s = s0f;
+    double r = 1.0 / sqrt(c * c + s * s);
+    c *= r; s *= r;
+    if (!refl_newton64(a, ds, pu, pv, &c, &s)) {
+        dx psi = refl_psi(dx((double)a), dx((double)ds), dx((double)pu), dx((double)pv), dx((double)gam));
+        sincos(psi.v, &s, &c);
+    }
+    *cs_out = (float)c;
+    *sn_out = (float)s;
+}
+
+// FP64 reflection point: the FP32 root refined by FP64 Newton steps (to
+// ~1e-15 of the bisection root of the definition); bisection when Newton
+// does not converge.
+__device__ __noinline__ void refl_root(dx a, dx ds, dx pu, dx pv, dx gam, dx *cs_out, dx *sn_out) {
+    float err;
+    float psi0 = refl_psi(to_float(a), to_float(ds), to_float(pu), to_float(pv), to_float(gam), &err);
+    float c0f, s0f;
+    sincosf(psi0, &s0f, &c0f);
+    double c = c0f, s = s0f;
+    double r = 1.0 / sqrt(c * c + s * s);
+    c *= r; s *= r;
+    if (!refl_newton64(a.v, ds.v, pu.v, pv.v, &c, &s)) {
+        dx psi = refl_psi(a, ds, pu, pv, gam);
+        dx sn, cs;
+        SinCos(psi, &sn, &cs);
+        c = cs.v; s = sn.v;
+    }
+    *cs_out = dx(c);
+    *sn_out = dx(s);
 }
 
 // X - (c + a n) per component as double-float, for FP32 X, c, n and radius a:
@@ -608,21 +656,18 @@ __device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Fr
     if (!F.axis_ok) return D_UNSURE;       // frame ill-conditioned: decide in FP64
     T dplus = F.gam - F.bs - F.bp;
     if (!conj(acc, decide(-dplus * a, band, D_NO))) return D_NO;      // strictly lit
-    T psi;
-    float psi_err = 0.0f;
-    if constexpr (sizeof(T) == 4) psi = refl_psi(a, F.ds, F.pu, F.pv, F.gam, &psi_err);
-    else psi = refl_psi(a, F.ds, F.pu, F.pv, F.gam);
     T sn, cs;
-    SinCos(psi, &sn, &cs);
     if constexpr (sizeof(T) == 4) {
+        float psi_err = 0.0f;
+        float psi = refl_psi(a, F.ds, F.pu, F.pv, F.gam, &psi_err);
+        SinCos(psi, &sn, &cs);
         // incidence cosine (2-D, horizontal for cylinders): refine the root in FP64
         // when its FP32 error would exceed 1e-5 of cos(theta_i) (near grazing),
         // the amplitude budget of the FP32 path
         float c2 = (F.ds * cs - a) / sqrtf((a * cs - F.ds) * (a * cs - F.ds) + a * a * sn * sn);
-        if (psi_err > 1e-5f * fmaxf(c2, 0.0f)) {
-            psi = refl_psi_polish(a, F.ds, F.pu, F.pv, F.gam, psi);
-            SinCos(psi, &sn, &cs);
-        }
+        if (psi_err > 1e-5f * fmaxf(c2, 0.0f)) refl_polish(a, F.ds, F.pu, F.pv, F.gam, psi, &cs, &sn);
+    } else {
+        refl_root(a, F.ds, F.pu, F.pv, F.gam, &cs, &sn);
     }
     v3t<T> n = F.u * cs + F.v * sn;
     v3t<T> Q;
@@ -897,11 +942,18 @@ __device__ __noinline__ Bpair fock_bracket_f(const Ctx &c, float xi, float K) {
     fock_bracket_impl<float>(c, xi, K, b.s, b.h);
     return b;
 }
-template <typename T>
+// F32FOCK: evaluate the bracket in FP32 also for FP64 geometry (candidates
+// re-decided in FP64: the bracket is a smooth function of xi and X, and its
+// FP32 evaluation is accurate to ~1e-6, inside the FP32 path's budget)
+template <typename T, bool F32FOCK = false>
 __device__ __forceinline__ void fock_bracket(const Ctx &c, T xi, T K, cpx<T> &Bs, cpx<T> &Bh) {
     if constexpr (sizeof(T) == 4) {
         Bpair b = fock_bracket_f(c, xi, K);
         Bs = b.s; Bh = b.h;
+    } else if constexpr (F32FOCK) {
+        Bpair b = fock_bracket_f(c, to_float(xi), to_float(K));
+        Bs = mkc<T>(T((double)b.s.re), T((double)b.s.im));
+        Bh = mkc<T>(T((double)b.h.re), T((double)b.h.im));
     } else {
         fock_bracket_impl<T>(c, xi, K, Bs, Bh);
     }
@@ -990,7 +1042,7 @@ __device__ __forceinline__ void add_ray(Acc<T> &acc, const FreqC &fq, v3t<T> e, 
     }
 }
 
-template <typename T, typename L>
+template <typename T, typename L, bool F32FOCK = false>
 __device__ void field_body_refl(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S, v3t<T> P, const Geo<T> &g, L len) {
     v3t<T> Q = g.Q1, n = g.n1;
     v3t<T> di = Q - S;
@@ -1027,7 +1079,7 @@ __device__ void field_body_refl(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<
                 Rs = mkc<T>(-1, 0); Rh = mkc<T>(1, 0);
             } else {
                 cpx<T> Bs, Bh;
-                fock_bracket<T>(c, xi, Sqrt(k * Lp / (T(2) * m * m)), Bs, Bh);
+                fock_bracket<T, F32FOCK>(c, xi, Sqrt(k * Lp / (T(2) * m * m)), Bs, Bh);
                 T sn, cs;
                 SinCos(-xi * xi * xi / T(12), &sn, &cs);
                 cpx<T> pre = mkc<T>(cs, sn) * (-Sqrt(T(-4) / xi));
@@ -1040,7 +1092,7 @@ __device__ void field_body_refl(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<
     }
 }
 
-template <typename T, typename L>
+template <typename T, typename L, bool F32FOCK = false>
 __device__ void field_creep(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S, v3t<T> P, const Geo<T> &g,
                             L len, unsigned enable) {
     v3t<T> t1 = unit3(g.Q1 - S), t2 = unit3(P - g.Q2);
@@ -1059,7 +1111,7 @@ __device__ void field_creep(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S
             T m = khof(fq, f, T(0)) * rcb;
             T xi = m * tr;
             cpx<T> Bs, Bh;
-            fock_bracket<T>(c, xi, Sqrt(k * Lp / (T(2) * m * m)), Bs, Bh);
+            fock_bracket<T, F32FOCK>(c, xi, Sqrt(k * Lp / (T(2) * m * m)), Bs, Bh);
             // T = -m sqrt(2/k) B e^{-jkt}; e^{-jkt} is inside the path phasor (len includes t)
             T pre = -m * Sqrt(T(2) / k) * g.amp;
             cpx<T> ph = phasor(fq, f, len) * pre;
@@ -1172,7 +1224,7 @@ __device__ __noinline__ int esc_rb(const Ctx &c, int b, v3t<float> Pf, const Fre
     if (d == D_YES && field) {
         Acc<dx> a;
         acc_zero(a);
-        field_body_refl<dx>(c, a, fq, Sd, Pd, g, seglen(Sd, g.Q1) + seglen(g.Q1, Pd));
+        field_body_refl<dx, dx, true>(c, a, fq, Sd, Pd, g, seglen(Sd, g.Q1) + seglen(g.Q1, Pd));
         contrib_from(out, a);
     }
     return d;
@@ -1195,34 +1247,280 @@ __device__ __noinline__ int esc_creep(const Ctx &c, int b, int dir, v3t<float> P
     if (field) {
         Acc<dx> a;
         acc_zero(a);
-        field_creep<dx>(c, a, fq, Sd, Pd, g, g.sp + g.t + g.sq, enable);
+        field_creep<dx, dx, true>(c, a, fq, Sd, Pd, g, g.sp + g.t + g.sq, enable);
         contrib_from(out, a);
     }
     return d;
 }
 
 // ------------------------------------------------------------------ kernel
-template <typename T, bool PATHS>
-__global__ void __launch_bounds__(BLOCK, CREEP_MIN_BLOCKS) k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e_out,
-                                               uint32_t *__restrict__ flags_out, uint64_t *__restrict__ codes,
-                                               int32_t *__restrict__ counts, int cap, int f0, FreqC fq_in,
-                                               double half_lambda_max, unsigned long long *esc_counter) {
+// Path classes; one launch evaluates the classes of its CLS mask, so that each
+// kernel carries only the code (and the live registers) of its classes.
+enum { CLS_PLANAR = 1,        // direct ray and planar image reflections
+       CLS_BODYREFL = 2,      // GO reflection off each curved body
+       CLS_CREEP = 4 };       // creeping rays round each curved body
+#ifndef CREEP_SPLIT
+#define CREEP_SPLIT 3          // 1: one kernel; 2: planar | bodies; 3: planar | reflection | creeping
+#endif
+constexpr int min_blocks(int cls) {
+    return cls == CLS_PLANAR ? 4 : (cls == (CLS_PLANAR | CLS_BODYREFL | CLS_CREEP) ? 2 : 3);
+}
+
+// One receiver P = rx[r]: the paths of the classes in CLS, their field (or
+// their codes), the receiver's flags.
+template <typename T, bool PATHS, int CLS>
+__device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, unsigned enable, int max_order,
+                                              const float *__restrict__ rx, int n_rx, int r, float *__restrict__ e_out,
+                                              uint32_t *__restrict__ flags_out, uint64_t *__restrict__ codes,
+                                              int32_t *__restrict__ counts, int cap, int f0, double half_lambda_max,
+                                              int accumulate, unsigned long long *esc_counter) {
+    constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
+    const bool fp32 = sizeof(T) == 4;
+    const T band = fp32 ? T(c.band) : T(0);
+    const int nf = fq.nf;
+    v3t<float> Pf = mk3(rx[r], rx[n_rx + r], rx[2 * n_rx + r]);
+    v3t<T> P = mk3<T>(T((double)Pf.x), T((double)Pf.y), T((double)Pf.z));
+    v3t<T> Sx = mk3<T>(T((double)c.S.x), T((double)c.S.y), T((double)c.S.z));
+    uint32_t fl = 0;
+    unsigned nesc = 0;                       // candidates decided in FP64
+    int npath = (PATHS && accumulate) ? counts[r] : 0;
+    Acc<T> acc;
+#pragma unroll
+    for (int f = 0; f < NFC; ++f)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc.E[f][q] = mkc<T>(T(0.0), T(0.0));
+    typedef typename LenOf<T>::type LT;
+
+    auto emit = [&](int type, int a, int b) {
+        if (PATHS) {
+            if (npath < cap) codes[(size_t)r * cap + npath] = pcode(type, a, b);
+            else fl |= RT_FLAG_OVERFLOW;
+        }
+        ++npath;
+    };
+    auto escalated = [&]() {
+        fl |= RT_FLAG_ESCALATED;
+        ++nesc;
+    };
+
+    // receiver inside (or on) a body?  (every class kernel takes this decision
+    // itself; it is the same in each)
+    int inside = 0;
+    for (int b = 0; b < c.n_body && !inside; ++b) {
+        float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
+        int d;
+        T ex = P.x - T((double)q0.x), ey = P.y - T((double)q0.y), ez = P.z - T((double)q0.z), a = T((double)q0.w);
+        if (fp32) {
+            T m = (q1.y == 0.0f) ? a - Sqrt(ex * ex + ey * ey + ez * ez)
+                                 : Fmin(Fmin(a - Sqrt(ex * ex + ey * ey), P.z - T((double)q0.z)),
+                                        T((double)q0.z) + T((double)q1.x) - P.z);
+            d = decide(m, band, D_YES);
+            if (d == D_UNSURE) { escalated(); d = esc_inside(c, b, Pf); }
+        } else {
+            d = esc_inside(c, b, Pf);
+        }
+        inside = (d == D_YES);
+    }
+
+    if (inside) {
+        fl |= RT_FLAG_INSIDE;
+    } else {
+        if constexpr ((CLS & CLS_PLANAR) != 0) {
+            // ---- direct ray
+            if (enable & RT_EN_LOS) {
+                int d = cand_los<T>(c, Sx, P, band);
+                if (d == D_UNSURE) { escalated(); d = esc_los(c, Pf); }
+                if (d == D_YES) {
+                    emit(PT_LOS, 0, 0);
+                    if (!PATHS) {
+                        LT L = seglen(Sx, P);
+                        add_ray(acc, fq, src_pol(c, unit3(P - Sx)), T(1) / (T)len_val(L), L);
+                    }
+                }
+            }
+            // ---- planar image reflections
+            if ((enable & RT_EN_PLANAR) && max_order >= 1) {
+#pragma unroll 1
+                for (int i = 0; i < c.n_face; ++i) {
+                    Geo<T> g;
+                    int d = cand_r1<T>(c, i, Sx, P, band, g);
+                    if constexpr (sizeof(T) == 4) {
+                        if (d == D_UNSURE) { escalated(); d = esc_r1(c, i, Pf, &g.Q1); }
+                    }
+                    if (d == D_YES) {
+                        emit(PT_R1, i, 0);
+                        if (!PATHS) {
+                            v3t<T> ni; T di;
+                            face_plane<T>(c, i, &ni, &di);
+                            LT L;
+                            if constexpr (sizeof(T) == 4) L = df_dist_df(c.img[2 * i], c.img[2 * i + 1], Pf);
+                            else L = ladd(seglen(Sx, g.Q1), seglen(g.Q1, P));
+                            add_ray(acc, fq, pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni), T(1) / (T)len_val(L), L);
+                        }
+                    }
+                }
+            }
+            if ((enable & RT_EN_PLANAR) && max_order >= 2) {
+#pragma unroll 1
+                for (int i = 0; i < c.n_face; ++i) {
+#pragma unroll 1
+                    for (int j = 0; j < c.n_face; ++j) {
+                        if (j == i) continue;
+                        Geo<T> g;
+                        int d = cand_r2<T>(c, i, j, Sx, P, band, g);
+                        if constexpr (sizeof(T) == 4) {
+                            if (d == D_UNSURE) { escalated(); d = esc_r2(c, i, j, Pf, &g.Q1, &g.Q2); }
+                        }
+                        if (d == D_YES) {
+                            emit(PT_R2, i, j);
+                            if (!PATHS) {
+                                v3t<T> ni, nj; T di, dj;
+                                face_plane<T>(c, i, &ni, &di);
+                                face_plane<T>(c, j, &nj, &dj);
+                                LT L;
+                                if constexpr (sizeof(T) == 4) {
+                                    int slot = c.n_face + i * c.n_face + j;
+                                    L = df_dist_df(c.img[2 * slot], c.img[2 * slot + 1], Pf);
+                                } else {
+                                    L = ladd(ladd(seglen(Sx, g.Q1), seglen(g.Q1, g.Q2)), seglen(g.Q2, P));
+                                }
+                                v3t<T> e = pec_mirror(pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni), nj);
+                                add_ray(acc, fq, e, T(1) / (T)len_val(L), L);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        // ---- curved bodies
+        if constexpr (BODIES) {
+#pragma unroll 1
+            for (int b = 0; b < c.n_body; ++b) {
+                Frame<T> F;
+                body_frame(c, b, Sx, P, band, F);
+                if constexpr ((CLS & CLS_BODYREFL) != 0) {
+                    if (enable & RT_EN_BODYREFL) {
+                        Geo<T> g;
+                        int d = cand_rb<T>(c, b, Sx, P, band, F, g);
+                        if constexpr (sizeof(T) == 4) {
+                            if (d == D_UNSURE) {
+                                // decided in FP64, and its geometry, length and amplitude
+                                // too (they may be ill-conditioned in FP32, e.g. for a
+                                // receiver at a surface); the Fock bracket stays FP32
+                                escalated();
+                                Contrib ct;
+                                d = esc_rb(c, b, Pf, fq, !PATHS, &ct);
+                                if (d == D_YES) {
+                                    emit(PT_RB, b, 0);
+                                    if (!PATHS) acc_add(acc, ct, nf);
+                                }
+                                d = D_NO;
+                            }
+                        }
+                        if (d == D_YES) {
+                            emit(PT_RB, b, 0);
+                            if (!PATHS) {
+                                LT L;
+                                if constexpr (sizeof(T) == 4) L = g.Lf;
+                                else L = ladd(seglen(Sx, g.Q1), seglen(g.Q1, P));
+                                field_body_refl<T>(c, acc, fq, Sx, P, g, L);
+                            }
+                        }
+                    }
+                }
+                if constexpr ((CLS & CLS_CREEP) != 0) {
+                    if (enable & (RT_EN_CREEP_SOFT | RT_EN_CREEP_HARD)) {
+                        bool sphere = c.body[2 * b + 1].y == 0.0f;
+#pragma unroll 1
+                        for (int dir = 0; dir < 2; ++dir) {
+                            Geo<T> g;
+                            int d = cand_creep<T>(c, b, dir, Sx, P, band, F, g);
+                            int cd = D_NO;
+                            if (d == D_YES && sphere) {
+                                // axial caustic flag: k d_perp < pi for some frequency, i.e. d_perp < lambda_max / 2
+                                if constexpr (sizeof(T) == 8) cd = (half_lambda_max > to_double(g.dperp)) ? D_YES : D_NO;
+                                else cd = decide((T)half_lambda_max - g.dperp, band, D_NO);
+                            }
+                            if constexpr (sizeof(T) == 4) {
+                                if (d == D_UNSURE || cd == D_UNSURE) {
+                                    escalated();
+                                    Contrib ct;
+                                    int caus = 0;
+                                    d = esc_creep(c, b, dir, Pf, fq, !PATHS, half_lambda_max, enable, &ct, &caus);
+                                    if (d == D_YES) {
+                                        emit(dir == 0 ? PT_CP : PT_CM, b, 0);
+                                        if (caus) fl |= RT_FLAG_CAUSTIC;
+                                        if (!PATHS) acc_add(acc, ct, nf);
+                                    }
+                                    continue;
+                                }
+                            }
+                            if (d != D_YES) continue;
+                            emit(dir == 0 ? PT_CP : PT_CM, b, 0);
+                            if (sphere) {
+                                if (cd == D_YES) fl |= RT_FLAG_CAUSTIC;
+                                if (!(g.dperp > T(0.0))) continue;        // exactly on the axis: no finite ray field
+                            }
+                            if (!PATHS) {
+                                LT L = creep_len(c, b, Sx, P, g, F);
+                                field_creep<T>(c, acc, fq, Sx, P, g, L, enable);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (PATHS) {
+        counts[r] = npath;
+    } else {
+#pragma unroll
+        for (int f = 0; f < NFC; ++f) {
+            if (f < nf) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    size_t idx = ((size_t)(f0 + f) * 3 + q) * n_rx + r;
+                    float2 v;
+                    v.x = to_float(acc.E[f][q].re);
+                    v.y = to_float(acc.E[f][q].im);
+                    if (accumulate) {
+                        float2 o = reinterpret_cast<float2 *>(e_out)[idx];
+                        v.x += o.x;
+                        v.y += o.y;
+                    }
+                    reinterpret_cast<float2 *>(e_out)[idx] = v;
+                }
+            }
+        }
+    }
+    if (flags_out && f0 == 0) flags_out[r] = accumulate ? (flags_out[r] | fl) : fl;
+    if (esc_counter && nesc && f0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
+}
+
+
+template <typename T, bool PATHS, int CLS>
+__global__ void __launch_bounds__(BLOCK, min_blocks(CLS))
+k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e_out, uint32_t *__restrict__ flags_out,
+       uint64_t *__restrict__ codes, int32_t *__restrict__ counts, int cap, int f0, FreqC fq_in, double half_lambda_max,
+       int accumulate, unsigned long long *esc_counter, unsigned long long *queue) {
+    constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     extern __shared__ float4 smem[];
     __shared__ Ctx s_ctx;
     __shared__ FreqC s_fq;
-    // stage scene and table
-    float4 *s_fock = smem;                                   // FOCK_N * 2
-    float4 *s_res = s_fock + FOCK_N * 2;                     // FOCK_NRES * 2
-    float4 *s_face = s_res + FOCK_NRES * 2;                  // n_face
+    // stage scene (and, for the body classes, the Fock--Pekeris table)
+    const int n_fock = BODIES ? FOCK_N * 2 : 0, n_res = BODIES ? FOCK_NRES * 2 : 0;
+    float4 *s_fock = smem;                                   // n_fock
+    float4 *s_res = s_fock + n_fock;                         // n_res
+    float4 *s_face = s_res + n_res;                          // n_face
     bool body_sm = S.n_body <= SMEM_BODY_MAX;
     float4 *s_body = s_face + S.n_face;                      // n_body * 2 (if staged)
     bool tri_sm = S.n_tri <= SMEM_TRI_MAX;
     float4 *s_tri = s_body + (body_sm ? 2 * S.n_body : 0);   // n_tri * 3 (if staged)
     float4 *s_aux = s_tri + (tri_sm ? 3 * S.n_tri : 0);      // n_tri * 3 (if staged)
-    float4 *s_txb = s_aux + (tri_sm ? 3 * S.n_tri : 0);       // n_body * 2 (if staged)
+    float4 *s_txb = s_aux + (tri_sm ? 3 * S.n_tri : 0);      // n_body * 2 (if staged)
     float *s_weid = (float *)(s_txb + (body_sm ? 2 * S.n_body : 0));
-    for (int i = threadIdx.x; i < FOCK_N * 2; i += blockDim.x) s_fock[i] = S.fock32[i];
-    for (int i = threadIdx.x; i < FOCK_NRES * 2; i += blockDim.x) s_res[i] = S.res32[i];
+    for (int i = threadIdx.x; i < n_fock; i += blockDim.x) s_fock[i] = S.fock32[i];
+    for (int i = threadIdx.x; i < n_res; i += blockDim.x) s_res[i] = S.res32[i];
     for (int i = threadIdx.x; i < S.n_face; i += blockDim.x) s_face[i] = S.face32[i];
     if (body_sm)
         for (int i = threadIdx.x; i < 2 * S.n_body; i += blockDim.x) {
@@ -1234,7 +1532,8 @@ __global__ void __launch_bounds__(BLOCK, CREEP_MIN_BLOCKS) k_eval(DevScene S, co
             s_tri[i] = S.tri[i];
             s_aux[i] = S.tri_alt[i];
         }
-    for (int i = threadIdx.x; i < WEIDEMAN_N; i += blockDim.x) s_weid[i] = S.weid[i];
+    if (BODIES)
+        for (int i = threadIdx.x; i < WEIDEMAN_N; i += blockDim.x) s_weid[i] = S.weid[i];
     if (threadIdx.x == 0) {
         Ctx &c = s_ctx;
         c.tri = tri_sm ? s_tri : S.tri;
@@ -1256,225 +1555,95 @@ __global__ void __launch_bounds__(BLOCK, CREEP_MIN_BLOCKS) k_eval(DevScene S, co
     }
     __syncthreads();
 
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_rx) return;
+    // persistent blocks: each warp takes tiles of 32 consecutive receivers
+    // from the launch's queue until none is left (balances the very uneven
+    // per-receiver cost and avoids a partial last wave)
     const Ctx &c = s_ctx;
     const FreqC &fq = s_fq;
-    const bool fp32 = sizeof(T) == 4;
-    const T band = fp32 ? T(c.band) : T(0);
-    const int nf = fq.nf;
-    v3t<float> Pf = mk3(rx[r], rx[n_rx + r], rx[2 * n_rx + r]);
-    v3t<T> P = mk3<T>(T((double)Pf.x), T((double)Pf.y), T((double)Pf.z));
-    v3t<T> Sx = mk3<T>(T((double)c.S.x), T((double)c.S.y), T((double)c.S.z));
-    uint32_t fl = 0;
-    int npath = 0;
-    Acc<T> acc;
-#pragma unroll
-    for (int f = 0; f < NFC; ++f)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) acc.E[f][q] = mkc<T>(T(0.0), T(0.0));
-    typedef typename LenOf<T>::type LT;
-
-    auto emit = [&](int type, int a, int b) {
-        if (PATHS) {
-            if (npath < cap) codes[(size_t)r * cap + npath] = pcode(type, a, b);
-            else fl |= RT_FLAG_OVERFLOW;
-        }
-        ++npath;
-    };
-
-    // receiver inside (or on) a body?
-    int inside = 0;
-    for (int b = 0; b < c.n_body && !inside; ++b) {
-        float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
-        int d;
-        T ex = P.x - T((double)q0.x), ey = P.y - T((double)q0.y), ez = P.z - T((double)q0.z), a = T((double)q0.w);
-        if (fp32) {
-            T m = (q1.y == 0.0f) ? a - Sqrt(ex * ex + ey * ey + ez * ez)
-                                 : Fmin(Fmin(a - Sqrt(ex * ex + ey * ey), P.z - T((double)q0.z)),
-                                        T((double)q0.z) + T((double)q1.x) - P.z);
-            d = decide(m, band, D_YES);
-            if (d == D_UNSURE) { fl |= RT_FLAG_ESCALATED; d = esc_inside(c, b, Pf); }
-        } else {
-            d = esc_inside(c, b, Pf);
-        }
-        inside = (d == D_YES);
+    const int lane = threadIdx.x & 31;
+    const unsigned long long ntiles = ((unsigned long long)n_rx + 31ull) >> 5;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0) t = atomicAdd(queue, 1ull);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        if (t >= ntiles) break;
+        int r = (int)(t * 32ull) + lane;
+        if (r < n_rx)
+            eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, e_out, flags_out, codes, counts, cap,
+                                         f0, half_lambda_max, accumulate, esc_counter);
     }
-
-    if (inside) {
-        fl |= RT_FLAG_INSIDE;
-    } else {
-        // ---- direct ray
-        if (S.enable & RT_EN_LOS) {
-            int d = cand_los<T>(c, Sx, P, band);
-            if (d == D_UNSURE) { fl |= RT_FLAG_ESCALATED; d = esc_los(c, Pf); }
-            if (d == D_YES) {
-                emit(PT_LOS, 0, 0);
-                if (!PATHS) {
-                    LT L = seglen(Sx, P);
-                    add_ray(acc, fq, src_pol(c, unit3(P - Sx)), T(1) / (T)len_val(L), L);
-                }
-            }
-        }
-        // ---- planar image reflections
-        if ((S.enable & RT_EN_PLANAR) && S.max_order >= 1) {
-#pragma unroll 1
-            for (int i = 0; i < c.n_face; ++i) {
-                Geo<T> g;
-                int d = cand_r1<T>(c, i, Sx, P, band, g);
-                if constexpr (sizeof(T) == 4) {
-                    if (d == D_UNSURE) { fl |= RT_FLAG_ESCALATED; d = esc_r1(c, i, Pf, &g.Q1); }
-                }
-                if (d == D_YES) {
-                    emit(PT_R1, i, 0);
-                    if (!PATHS) {
-                        v3t<T> ni; T di;
-                        face_plane<T>(c, i, &ni, &di);
-                        LT L;
-                        if constexpr (sizeof(T) == 4) L = df_dist_df(c.img[2 * i], c.img[2 * i + 1], Pf);
-                        else L = ladd(seglen(Sx, g.Q1), seglen(g.Q1, P));
-                        add_ray(acc, fq, pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni), T(1) / (T)len_val(L), L);
-                    }
-                }
-            }
-        }
-        if ((S.enable & RT_EN_PLANAR) && S.max_order >= 2) {
-#pragma unroll 1
-            for (int i = 0; i < c.n_face; ++i) {
-#pragma unroll 1
-                for (int j = 0; j < c.n_face; ++j) {
-                    if (j == i) continue;
-                    Geo<T> g;
-                    int d = cand_r2<T>(c, i, j, Sx, P, band, g);
-                    if constexpr (sizeof(T) == 4) {
-                        if (d == D_UNSURE) { fl |= RT_FLAG_ESCALATED; d = esc_r2(c, i, j, Pf, &g.Q1, &g.Q2); }
-                    }
-                    if (d == D_YES) {
-                        emit(PT_R2, i, j);
-                        if (!PATHS) {
-                            v3t<T> ni, nj; T di, dj;
-                            face_plane<T>(c, i, &ni, &di);
-                            face_plane<T>(c, j, &nj, &dj);
-                            LT L;
-                            if constexpr (sizeof(T) == 4) {
-                                int slot = c.n_face + i * c.n_face + j;
-                                L = df_dist_df(c.img[2 * slot], c.img[2 * slot + 1], Pf);
-                            } else {
-                                L = ladd(ladd(seglen(Sx, g.Q1), seglen(g.Q1, g.Q2)), seglen(g.Q2, P));
-                            }
-                            v3t<T> e = pec_mirror(pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni), nj);
-                            add_ray(acc, fq, e, T(1) / (T)len_val(L), L);
-                        }
-                    }
-                }
-            }
-        }
-        // ---- curved bodies
-#pragma unroll 1
-        for (int b = 0; b < c.n_body; ++b) {
-            Frame<T> F;
-            body_frame(c, b, Sx, P, band, F);
-            if (S.enable & RT_EN_BODYREFL) {
-                Geo<T> g;
-                int d = cand_rb<T>(c, b, Sx, P, band, F, g);
-                if constexpr (sizeof(T) == 4) {
-                    if (d == D_UNSURE) {
-                        // decided in FP64, and its field too (the geometry may be
-                        // ill-conditioned in FP32, e.g. a receiver at a surface)
-                        fl |= RT_FLAG_ESCALATED;
-                        Contrib ct;
-                        d = esc_rb(c, b, Pf, fq, !PATHS, &ct);
-                        if (d == D_YES) {
-                            emit(PT_RB, b, 0);
-                            if (!PATHS) acc_add(acc, ct, nf);
-                        }
-                        d = D_NO;
-                    }
-                }
-                if (d == D_YES) {
-                    emit(PT_RB, b, 0);
-                    if (!PATHS) {
-                        LT L;
-                        if constexpr (sizeof(T) == 4) L = g.Lf;
-                        else L = ladd(seglen(Sx, g.Q1), seglen(g.Q1, P));
-                        field_body_refl<T>(c, acc, fq, Sx, P, g, L);
-                    }
-                }
-            }
-            if (S.enable & (RT_EN_CREEP_SOFT | RT_EN_CREEP_HARD)) {
-                bool sphere = c.body[2 * b + 1].y == 0.0f;
-#pragma unroll 1
-                for (int dir = 0; dir < 2; ++dir) {
-                    Geo<T> g;
-                    int d = cand_creep<T>(c, b, dir, Sx, P, band, F, g);
-                    int cd = D_NO;
-                    if (d == D_YES && sphere) {
-                        // axial caustic flag: k d_perp < pi for some frequency, i.e. d_perp < lambda_max / 2
-                        if constexpr (sizeof(T) == 8) cd = (half_lambda_max > to_double(g.dperp)) ? D_YES : D_NO;
-                        else cd = decide((T)half_lambda_max - g.dperp, band, D_NO);
-                    }
-                    if constexpr (sizeof(T) == 4) {
-                        if (d == D_UNSURE || cd == D_UNSURE) {
-                            fl |= RT_FLAG_ESCALATED;
-                            Contrib ct;
-                            int caus = 0;
-                            d = esc_creep(c, b, dir, Pf, fq, !PATHS, half_lambda_max, S.enable, &ct, &caus);
-                            if (d == D_YES) {
-                                emit(dir == 0 ? PT_CP : PT_CM, b, 0);
-                                if (caus) fl |= RT_FLAG_CAUSTIC;
-                                if (!PATHS) acc_add(acc, ct, nf);
-                            }
-                            continue;
-                        }
-                    }
-                    if (d != D_YES) continue;
-                    emit(dir == 0 ? PT_CP : PT_CM, b, 0);
-                    if (sphere) {
-                        if (cd == D_YES) fl |= RT_FLAG_CAUSTIC;
-                        if (!(g.dperp > T(0.0))) continue;        // exactly on the axis: no finite ray field
-                    }
-                    if (!PATHS) {
-                        LT L = creep_len(c, b, Sx, P, g, F);
-                        field_creep<T>(c, acc, fq, Sx, P, g, L, S.enable);
-                    }
-                }
-            }
-        }
-    }
-    if (PATHS) {
-        counts[r] = npath;
-    } else {
-#pragma unroll
-        for (int f = 0; f < NFC; ++f) {
-            if (f < nf) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    size_t idx = ((size_t)(f0 + f) * 3 + q) * n_rx + r;
-                    float2 v;
-                    v.x = to_float(acc.E[f][q].re);
-                    v.y = to_float(acc.E[f][q].im);
-                    reinterpret_cast<float2 *>(e_out)[idx] = v;
-                }
-            }
-        }
-    }
-    if (flags_out && (f0 == 0)) flags_out[r] = fl;
-    if (esc_counter && (fl & RT_FLAG_ESCALATED) && f0 == 0) atomicAdd(esc_counter, 1ull);
 }
 
-static size_t smem_bytes(const DevScene &S) {
-    size_t n = FOCK_N * 2 + FOCK_NRES * 2 + S.n_face;
+static size_t smem_bytes(const DevScene &S, bool bodies) {
+    size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + S.n_face;
     if (S.n_body <= SMEM_BODY_MAX) n += 4 * S.n_body;
     if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;
     return n * sizeof(float4) + WEIDEMAN_N * sizeof(float) + 16;
 }
 
+// Launch state of one evaluation: the counters (escalations, one work queue
+// per launch) and the launches queued so far.
+struct LaunchCtx {
+    unsigned long long *ctr;
+    int n;
+    cudaStream_t stream;
+};
+
+template <typename T, bool PATHS, int CLS>
+static cudaError_t launch_one(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
+                              uint64_t *codes, int32_t *counts, int cap, int f0, const FreqC &fq, double hl,
+                              int accumulate, LaunchCtx &L) {
+    if (L.n >= CTR_QUEUES) return cudaErrorInvalidValue;
+    size_t sm = smem_bytes(S, (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0);
+    cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    // persistent grid: the blocks that fit on the device at once
+    int dev = 0, nsm = 0, occ = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<T, PATHS, CLS>, BLOCK, sm)) != cudaSuccess) return e;
+    long long need = ((long long)n_rx + BLOCK - 1) / BLOCK;
+    long long cap_blocks = (long long)nsm * (occ > 0 ? occ : 1);
+    int grid = (int)(need < cap_blocks ? need : cap_blocks);
+    k_eval<T, PATHS, CLS><<<grid, BLOCK, sm, L.stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl,
+                                                         accumulate, L.ctr, L.ctr + 1 + L.n);
+    ++L.n;
+    return cudaGetLastError();
+}
+
+// the class kernels of one frequency chunk, in order; the first writes the
+// outputs, the others add to them
+template <typename T, bool PATHS>
+static cudaError_t launch_classes(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
+                                  uint64_t *codes, int32_t *counts, int cap, int f0, const FreqC &fq, double hl,
+                                  LaunchCtx &L) {
+    cudaError_t e;
+#if CREEP_SPLIT == 1
+    e = launch_one<T, PATHS, CLS_PLANAR | CLS_BODYREFL | CLS_CREEP>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap,
+                                                                     f0, fq, hl, 0, L);
+#elif CREEP_SPLIT == 2
+    e = launch_one<T, PATHS, CLS_PLANAR>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, 0, L);
+    if (e == cudaSuccess)
+        e = launch_one<T, PATHS, CLS_BODYREFL | CLS_CREEP>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, 1,
+                                                           L);
+#else
+    e = launch_one<T, PATHS, CLS_PLANAR>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, 0, L);
+    if (e == cudaSuccess)
+        e = launch_one<T, PATHS, CLS_BODYREFL>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, 1,
+                                               L);
+    if (e == cudaSuccess)
+        e = launch_one<T, PATHS, CLS_CREEP>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, 1,
+                                            L);
+#endif
+    return e;
+}
+
 int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
-                uint64_t *codes, int32_t *counts, int cap, int precision, unsigned long long *esc_counter,
-                cudaStream_t stream) {
+                uint64_t *codes, int32_t *counts, int cap, int precision, unsigned long long *ctr,
+                cudaStream_t stream, int *n_launches) {
+    *n_launches = 0;
     if (n_rx <= 0) return RT_OK;
-    size_t sm = smem_bytes(S);
-    int grid = (n_rx + BLOCK - 1) / BLOCK;
+    LaunchCtx L{ctr, 0, stream};
     double hl = 0.0;
     for (int f = 0; f < S.n_f; ++f) {
         double lam = 299792458.0 / S.freq[f];
@@ -1499,27 +1668,17 @@ int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, 
         int f0 = ch * NFC;
         cudaError_t e;
         if (precision == RT_PREC_FP64) {
-            if (paths) {
-                cudaFuncSetAttribute(k_eval<dx, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                k_eval<dx, true><<<grid, BLOCK, sm, stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, esc_counter);
-            } else {
-                cudaFuncSetAttribute(k_eval<dx, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                k_eval<dx, false><<<grid, BLOCK, sm, stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, esc_counter);
-            }
+            e = paths ? launch_classes<dx, true>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, L)
+                      : launch_classes<dx, false>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, L);
         } else {
-            if (paths) {
-                cudaFuncSetAttribute(k_eval<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                k_eval<float, true><<<grid, BLOCK, sm, stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, esc_counter);
-            } else {
-                cudaFuncSetAttribute(k_eval<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-                k_eval<float, false><<<grid, BLOCK, sm, stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, esc_counter);
-            }
+            e = paths ? launch_classes<float, true>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, L)
+                      : launch_classes<float, false>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, L);
         }
-        e = cudaGetLastError();
         if (e != cudaSuccess) {
             set_error(std::string("k_eval launch: ") + cudaGetErrorString(e));
             return RT_ERR_CUDA;
         }
+        *n_launches = L.n;
     }
     return RT_OK;
 }

@@ -71,8 +71,15 @@ struct DevScene {
     unsigned enable;
 };
 
+// Device counters of one evaluation: [0] candidates decided in FP64, [1 + i]
+// the work queue of launch i.  Zeroed by the caller before launch_eval.
+constexpr int CTR_QUEUES = 64;
+constexpr int CTR_N = 1 + CTR_QUEUES;
+
+// Evaluate (codes == nullptr) or list paths; *n_launches receives the number
+// of kernel launches queued.
 int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
-                uint64_t *codes, int32_t *counts, int cap, int precision, unsigned long long *esc_counter,
-                cudaStream_t stream);
+                uint64_t *codes, int32_t *counts, int cap, int precision, unsigned long long *ctr,
+                cudaStream_t stream, int *n_launches);
 
 }  // namespace creep
