@@ -240,8 +240,34 @@ __device__ __forceinline__ int blocked_impl(const Ctx &c, v3t<T> A, v3t<T> B, in
         return D_NO;
     }
     if constexpr (sizeof(T) == 4) {
+        // bodies: a squared-distance test against the segment's closest point
+        // to the centre (cylinders: to the axis, in projection) rejects the
+        // bodies that are clearly apart -- distance above a + band, so the
+        // margin of the full test would be below -band -- in a few FMAs with
+        // the per-segment constants; the rest get the full test
+        const v3t<float> D = B - A;
+        const float qa = D.x * D.x + D.y * D.y;
+        const float iqa = (qa > 0.0f) ? 1.0f / qa : 0.0f;
+        const float idd = 1.0f / (qa + D.z * D.z);
+        const float tlo = (float)EPS_TRIM, thi = 1.0f - (float)EPS_TRIM;
+#pragma unroll 2
         for (int b = 0; b < c.n_body; ++b) {
             if (b == sb) continue;
+            const float4 q0 = c.body[2 * b];
+            const float wx = q0.x - A.x, wy = q0.y - A.y;
+            float d2;
+            if (c.body[2 * b + 1].y == 0.0f) {          // sphere: closest point of the segment to c
+                const float wz = q0.z - A.z;
+                const float t = fminf(fmaxf((wx * D.x + wy * D.y + wz * D.z) * idd, tlo), thi);
+                const float hx = D.x * t - wx, hy = D.y * t - wy, hz = D.z * t - wz;
+                d2 = hx * hx + hy * hy + hz * hz;
+            } else {                                     // cylinder: closest point to the axis
+                const float t = (qa > 0.0f) ? fminf(fmaxf((wx * D.x + wy * D.y) * iqa, tlo), thi) : tlo;
+                const float hx = D.x * t - wx, hy = D.y * t - wy;
+                d2 = hx * hx + hy * hy;
+            }
+            const float ab = q0.w + band;
+            if (d2 > ab * ab) continue;
             int r = seg_body(c, b, A, B, band);
             if (r == D_YES) return D_YES;
             uns |= (r == D_UNSURE);
@@ -557,17 +583,18 @@ __device__ dx refl_psi(dx a, dx ds, dx pu, dx pv, dx gam) {
 //   dL/dpsi   = a [ds s / |Q - S| + (pu s - pv c) / |Q - P|],
 //   d2L/dpsi2 = (X.Q - (dL/dpsi)_X^2) / |Q - X| summed over X = S, P,
 // and n is rotated by each step d with cos d, sin d from their Taylor series
-// (|d| <= 1e-3).  Returns false (no result) if a step is too large or the
-// curvature not positive; the caller then brackets.
-__device__ bool refl_newton64(double A, double Ds, double Pu, double Pv, double *c_io, double *s_io) {
+// (|d| <= 1e-3), until a step is below tol (quadratic convergence: the next
+// one would be of order tol^2).  Returns false (no result) if a step is too
+// large or the curvature not positive; the caller then brackets.
+__device__ bool refl_newton64(double A, double Ds, double Pu, double Pv, double *c_io, double *s_io, double tol) {
     double c = *c_io, s = *s_io;
     const double dp2 = Pu * Pu + Pv * Pv;
     for (int it = 0; it < 6; ++it) {
-        double fs = sqrt(A * A + Ds * Ds - 2.0 * A * Ds * c);
-        double fr = sqrt(A * A + dp2 - 2.0 * A * (Pu * c + Pv * s));
-        double gs = A * Ds * s / fs, gr = A * (Pu * s - Pv * c) / fr;
+        double ifs = rsqrt(A * A + Ds * Ds - 2.0 * A * Ds * c);
+        double ifr = rsqrt(A * A + dp2 - 2.0 * A * (Pu * c + Pv * s));
+        double gs = A * Ds * s * ifs, gr = A * (Pu * s - Pv * c) * ifr;
         double g = gs + gr;
-        double g2 = (Ds * A * c - gs * gs) / fs + (A * (Pu * c + Pv * s) - gr * gr) / fr;
+        double g2 = (Ds * A * c - gs * gs) * ifs + (A * (Pu * c + Pv * s) - gr * gr) * ifr;
         if (!(g2 > 0.0)) return false;
         double d = -g / g2;
         if (!(fabs(d) <= 1e-3)) return false;
@@ -576,7 +603,7 @@ __device__ bool refl_newton64(double A, double Ds, double Pu, double Pv, double 
         double sd = d * (1.0 - d2 * ((1.0 / 6.0) - d2 * (1.0 / 120.0)));
         double cn = c * cd - s * sd, sn = s * cd + c * sd;
         c = cn; s = sn;
-        if (fabs(d) <= 1e-13) {
+        if (fabs(d) <= tol) {
             *c_io = c; *s_io = s;
             return true;
         }
@@ -594,7 +621,7 @@ __device__ __noinline__ void refl_polish(float a, float ds, float pu, float pv, 
     double c = c0f, s = s0f;
     double r = 1.0 / sqrt(c * c + s * s);
     c *= r; s *= r;
-    if (!refl_newton64(a, ds, pu, pv, &c, &s)) {
+    if (!refl_newton64(a, ds, pu, pv, &c, &s, 1e-9)) {        // the result is rounded to FP32
         dx psi = refl_psi(dx((double)a), dx((double)ds), dx((double)pu), dx((double)pv), dx((double)gam));
         sincos(psi.v, &s, &c);
     }
@@ -613,7 +640,7 @@ __device__ __noinline__ void refl_root(dx a, dx ds, dx pu, dx pv, dx gam, dx *cs
     double c = c0f, s = s0f;
     double r = 1.0 / sqrt(c * c + s * s);
     c *= r; s *= r;
-    if (!refl_newton64(a.v, ds.v, pu.v, pv.v, &c, &s)) {
+    if (!refl_newton64(a.v, ds.v, pu.v, pv.v, &c, &s, 1e-13)) {
         dx psi = refl_psi(a, ds, pu, pv, gam);
         dx sn, cs;
         SinCos(psi, &sn, &cs);
@@ -804,15 +831,28 @@ __device__ cpx<float> faddeeva<float>(const Ctx &c, cpx<float> z) {
 __device__ void pekeris(const Ctx &c, float xi, cpx<float> &ps, cpx<float> &ph, bool regular) {
     const float ci = 0.19947114f / xi;                 // c/xi = e^{-j pi/4}/(2 sqrt(pi) xi) = (ci, -ci)
     if (xi > (float)XI_HI) {
+        // residue series: term n decays as exp(-xi rs.x); the terms are summed
+        // until one falls below 1e-8 of the first (exp2 and sincospi with the
+        // constants scaled by log2(e) and 1/pi: no large-argument reduction)
+        const float LOG2E = 1.4426950408889634f, INV_PI = 0.31830988618379067f;
         cpx<float> ss = mkc(0.f, 0.f), sh = mkc(0.f, 0.f);
+        const float x0s = xi * c.res[0].x, x0h = xi * c.res[1].x;
         for (int n = 0; n < FOCK_NRES; ++n) {
-            float4 rs = c.res[2 * n], rh = c.res[2 * n + 1];
+            float4 rs = c.res[2 * n];
+            float xs = xi * rs.x;
+            if (xs - x0s > 18.5f) break;
             float sn, cs;
-            sincosf(xi * rs.y, &sn, &cs);
-            float e = expf(-xi * rs.x) * rs.z;
+            sincospif(xi * (rs.y * INV_PI), &sn, &cs);
+            float e = exp2f(-xs * LOG2E) * rs.z;
             ss = ss + mkc(e * cs, -e * sn);
-            sincosf(xi * rh.y, &sn, &cs);
-            e = expf(-xi * rh.x) * rh.z;
+        }
+        for (int n = 0; n < FOCK_NRES; ++n) {
+            float4 rh = c.res[2 * n + 1];
+            float xh = xi * rh.x;
+            if (xh - x0h > 18.5f) break;
+            float sn, cs;
+            sincospif(xi * (rh.y * INV_PI), &sn, &cs);
+            float e = exp2f(-xh * LOG2E) * rh.z;
             sh = sh + mkc(e * cs, -e * sn);
         }
         const cpx<float> pre = mkc(-0.27248264483602590f, 0.07301150463530957f);   // -e^{-j pi/12}/(2 sqrt(pi))
@@ -831,7 +871,7 @@ __device__ void pekeris(const Ctx &c, float xi, cpx<float> &ps, cpx<float> &ph, 
     cpx<float> Gs = mkc(h00 * a0.x + h10 * a0.z + h01 * a1.x + h11 * a1.z, h00 * a0.y + h10 * a0.w + h01 * a1.y + h11 * a1.w);
     cpx<float> Gh = mkc(h00 * b0.x + h10 * b0.z + h01 * b1.x + h11 * b1.z, h00 * b0.y + h10 * b0.w + h01 * b1.y + h11 * b1.w);
     float sn, cs;
-    sincosf(xi * xi * xi * (1.0f / 12.0f), &sn, &cs);   // e^{+j xi^3/12}
+    sincospif(xi * xi * xi * (float)(1.0 / (12.0 * M_PI)), &sn, &cs);   // e^{+j xi^3/12}
     cpx<float> rot = mkc(cs, sn);
     ps = Gs * rot;
     ph = Gh * rot;
@@ -937,7 +977,7 @@ __device__ __forceinline__ void fock_bracket_impl(const Ctx &c, T xi, T K, cpx<T
 struct Bpair {
     cpx<float> s, h;
 };
-__device__ __noinline__ Bpair fock_bracket_f(const Ctx &c, float xi, float K) {
+__device__ __forceinline__ Bpair fock_bracket_f(const Ctx &c, float xi, float K) {
     Bpair b;
     fock_bracket_impl<float>(c, xi, K, b.s, b.h);
     return b;
@@ -1081,7 +1121,8 @@ __device__ void field_body_refl(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<
                 cpx<T> Bs, Bh;
                 fock_bracket<T, F32FOCK>(c, xi, Sqrt(k * Lp / (T(2) * m * m)), Bs, Bh);
                 T sn, cs;
-                SinCos(-xi * xi * xi / T(12), &sn, &cs);
+                if constexpr (sizeof(T) == 4) sincospif(-xi * xi * xi * (float)(1.0 / (12.0 * M_PI)), &sn, &cs);
+                else SinCos(-xi * xi * xi / T(12), &sn, &cs);
                 cpx<T> pre = mkc<T>(cs, sn) * (-Sqrt(T(-4) / xi));
                 Rs = pre * Bs; Rh = pre * Bh;
             }
@@ -1266,14 +1307,18 @@ constexpr int min_blocks(int cls) {
     return cls == CLS_PLANAR ? 4 : (cls == (CLS_PLANAR | CLS_BODYREFL | CLS_CREEP) ? 2 : 3);
 }
 
-// One receiver P = rx[r]: the paths of the classes in CLS, their field (or
-// their codes), the receiver's flags.
+// One receiver P = rx[r]: the paths of the classes in CLS among the
+// candidates of share `part` of `nparts` -- the direct ray to share 0, the
+// reflection off face i to share (1 + i) mod nparts, off faces (i, j) to
+// share (1 + i n_face + j) mod nparts, the paths of body b to share
+// b mod nparts -- summed into acc; the receiver's flags, the count of FP64
+// re-decisions and (PATHS) the path codes from slot npath on.
 template <typename T, bool PATHS, int CLS>
 __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, unsigned enable, int max_order,
-                                              const float *__restrict__ rx, int n_rx, int r, float *__restrict__ e_out,
-                                              uint32_t *__restrict__ flags_out, uint64_t *__restrict__ codes,
-                                              int32_t *__restrict__ counts, int cap, int f0, double half_lambda_max,
-                                              int accumulate, unsigned long long *esc_counter) {
+                                              const float *__restrict__ rx, int n_rx, int r,
+                                              uint64_t *__restrict__ codes, int cap, double half_lambda_max,
+                                              int part, int nparts, Acc<T> &acc, uint32_t &fl, unsigned &nesc,
+                                              int &npath) {
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     const bool fp32 = sizeof(T) == 4;
     const T band = fp32 ? T(c.band) : T(0);
@@ -1281,10 +1326,8 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
     v3t<float> Pf = mk3(rx[r], rx[n_rx + r], rx[2 * n_rx + r]);
     v3t<T> P = mk3<T>(T((double)Pf.x), T((double)Pf.y), T((double)Pf.z));
     v3t<T> Sx = mk3<T>(T((double)c.S.x), T((double)c.S.y), T((double)c.S.z));
-    uint32_t fl = 0;
-    unsigned nesc = 0;                       // candidates decided in FP64
-    int npath = (PATHS && accumulate) ? counts[r] : 0;
-    Acc<T> acc;
+    fl = 0;
+    nesc = 0;
 #pragma unroll
     for (int f = 0; f < NFC; ++f)
 #pragma unroll
@@ -1315,7 +1358,11 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                                  : Fmin(Fmin(a - Sqrt(ex * ex + ey * ey), P.z - T((double)q0.z)),
                                         T((double)q0.z) + T((double)q1.x) - P.z);
             d = decide(m, band, D_YES);
-            if (d == D_UNSURE) { escalated(); d = esc_inside(c, b, Pf); }
+            if (d == D_UNSURE) {
+                if (part == 0) escalated();              // every share takes it; one counts it
+                else fl |= RT_FLAG_ESCALATED;
+                d = esc_inside(c, b, Pf);
+            }
         } else {
             d = esc_inside(c, b, Pf);
         }
@@ -1326,8 +1373,8 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
         fl |= RT_FLAG_INSIDE;
     } else {
         if constexpr ((CLS & CLS_PLANAR) != 0) {
-            // ---- direct ray
-            if (enable & RT_EN_LOS) {
+            // ---- direct ray (candidate 0)
+            if ((enable & RT_EN_LOS) && part == 0) {
                 int d = cand_los<T>(c, Sx, P, band);
                 if (d == D_UNSURE) { escalated(); d = esc_los(c, Pf); }
                 if (d == D_YES) {
@@ -1342,6 +1389,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
             if ((enable & RT_EN_PLANAR) && max_order >= 1) {
 #pragma unroll 1
                 for (int i = 0; i < c.n_face; ++i) {
+                    if ((1 + i) % nparts != part) continue;      // candidates 1 .. n_face
                     Geo<T> g;
                     int d = cand_r1<T>(c, i, Sx, P, band, g);
                     if constexpr (sizeof(T) == 4) {
@@ -1366,6 +1414,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
 #pragma unroll 1
                     for (int j = 0; j < c.n_face; ++j) {
                         if (j == i) continue;
+                        if ((1 + i * c.n_face + j) % nparts != part) continue;   // then the ordered pairs
                         Geo<T> g;
                         int d = cand_r2<T>(c, i, j, Sx, P, band, g);
                         if constexpr (sizeof(T) == 4) {
@@ -1395,7 +1444,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
         // ---- curved bodies
         if constexpr (BODIES) {
 #pragma unroll 1
-            for (int b = 0; b < c.n_body; ++b) {
+            for (int b = part; b < c.n_body; b += nparts) {
                 Frame<T> F;
                 body_frame(c, b, Sx, P, band, F);
                 if constexpr ((CLS & CLS_BODYREFL) != 0) {
@@ -1471,30 +1520,6 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
             }
         }
     }
-    if (PATHS) {
-        counts[r] = npath;
-    } else {
-#pragma unroll
-        for (int f = 0; f < NFC; ++f) {
-            if (f < nf) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    size_t idx = ((size_t)(f0 + f) * 3 + q) * n_rx + r;
-                    float2 v;
-                    v.x = to_float(acc.E[f][q].re);
-                    v.y = to_float(acc.E[f][q].im);
-                    if (accumulate) {
-                        float2 o = reinterpret_cast<float2 *>(e_out)[idx];
-                        v.x += o.x;
-                        v.y += o.y;
-                    }
-                    reinterpret_cast<float2 *>(e_out)[idx] = v;
-                }
-            }
-        }
-    }
-    if (flags_out && f0 == 0) flags_out[r] = accumulate ? (flags_out[r] | fl) : fl;
-    if (esc_counter && nesc && f0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
 }
 
 
@@ -1555,22 +1580,95 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
     }
     __syncthreads();
 
-    // persistent blocks: each warp takes tiles of 32 consecutive receivers
-    // from the launch's queue until none is left (balances the very uneven
-    // per-receiver cost and avoids a partial last wave)
     const Ctx &c = s_ctx;
     const FreqC &fq = s_fq;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = BLOCK / 32;
     const unsigned long long ntiles = ((unsigned long long)n_rx + 31ull) >> 5;
-    for (;;) {
-        unsigned long long t = 0;
-        if (lane == 0) t = atomicAdd(queue, 1ull);
-        t = __shfl_sync(0xffffffffu, t, 0);
-        if (t >= ntiles) break;
-        int r = (int)(t * 32ull) + lane;
-        if (r < n_rx)
-            eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, e_out, flags_out, codes, counts, cap,
-                                         f0, half_lambda_max, accumulate, esc_counter);
+    if constexpr (PATHS) {
+        // path lists: each warp takes tiles of 32 consecutive receivers from
+        // the launch's queue and lists every candidate itself (codes in the
+        // canonical order)
+        for (;;) {
+            unsigned long long t = 0;
+            if (lane == 0) t = atomicAdd(queue, 1ull);
+            t = __shfl_sync(0xffffffffu, t, 0);
+            if (t >= ntiles) break;
+            int r = (int)(t * 32ull) + lane;
+            if (r < n_rx) {
+                Acc<T> acc;
+                uint32_t fl;
+                unsigned nesc;
+                int npath = accumulate ? counts[r] : 0;
+                eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap, half_lambda_max,
+                                             0, 1, acc, fl, nesc, npath);
+                counts[r] = npath;
+                if (flags_out) flags_out[r] = accumulate ? (flags_out[r] | fl) : fl;
+                if (nesc) atomicAdd(esc_counter, (unsigned long long)nesc);
+            }
+        }
+    } else {
+        // fields: persistent blocks take tiles of 32 consecutive receivers
+        // from the launch's queue; the block's warps share each tile's
+        // candidates (warp w takes share w) and the partial fields are summed
+        // in shared memory in warp order, so the result does not depend on
+        // timing.  Sharing a tile among the warps shortens it, so the last
+        // tiles of the launch leave little of the GPU idle.
+        __shared__ T s_part[NW][NFC * 6][32];
+        __shared__ uint32_t s_fl[NW][32];
+        __shared__ unsigned long long s_tile;
+        for (;;) {
+            if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1ull);
+            __syncthreads();
+            const unsigned long long t = s_tile;
+            if (t >= ntiles) break;
+            const int r = (int)(t * 32ull) + lane;
+            Acc<T> acc;
+            uint32_t fl = 0;
+            unsigned nesc = 0;
+            int npath = 0;
+            if (r < n_rx)
+                eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap, half_lambda_max,
+                                             warp, NW, acc, fl, nesc, npath);
+#pragma unroll
+            for (int f = 0; f < NFC; ++f)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    s_part[warp][(f * 3 + q) * 2][lane] = acc.E[f][q].re;
+                    s_part[warp][(f * 3 + q) * 2 + 1][lane] = acc.E[f][q].im;
+                }
+            s_fl[warp][lane] = fl;
+            if (nesc && f0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
+            __syncthreads();
+            // reduce: warp w writes the (frequency, component) pairs j = w, w + NW, ...
+            if (r < n_rx) {
+                for (int j = warp; j < fq.nf * 3; j += NW) {
+                    T re = s_part[0][2 * j][lane], im = s_part[0][2 * j + 1][lane];
+#pragma unroll
+                    for (int w = 1; w < NW; ++w) {
+                        re = re + s_part[w][2 * j][lane];
+                        im = im + s_part[w][2 * j + 1][lane];
+                    }
+                    size_t idx = ((size_t)(f0 + j / 3) * 3 + (j % 3)) * n_rx + r;
+                    float2 v;
+                    v.x = to_float(re);
+                    v.y = to_float(im);
+                    if (accumulate) {
+                        float2 o = reinterpret_cast<float2 *>(e_out)[idx];
+                        v.x += o.x;
+                        v.y += o.y;
+                    }
+                    reinterpret_cast<float2 *>(e_out)[idx] = v;
+                }
+                if (warp == 0 && flags_out && f0 == 0) {
+                    uint32_t f_all = 0;
+#pragma unroll
+                    for (int w = 0; w < NW; ++w) f_all |= s_fl[w][lane];
+                    flags_out[r] = accumulate ? (flags_out[r] | f_all) : f_all;
+                }
+            }
+            __syncthreads();
+        }
     }
 }
 
