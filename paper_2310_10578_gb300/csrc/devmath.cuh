@@ -172,6 +172,23 @@ __device__ __forceinline__ dfl df_sqrt(dfl a) {
     float r = ((a.hi - ss.hi) - ss.lo + a.lo) / (2.0f * s);
     return quick_two_sum(s, r);
 }
+__device__ __forceinline__ dfl df_neg(dfl a) {
+    dfl r;
+    r.hi = -a.hi; r.lo = -a.lo;
+    return r;
+}
+// double-float times float
+__device__ __forceinline__ dfl df_mulf(dfl a, float b) {
+    dfl p = two_prod(a.hi, b);
+    return quick_two_sum(p.hi, fmaf(a.lo, b, p.lo));
+}
+// double-float quotient (two correction terms of the FP32 quotient)
+__device__ __forceinline__ dfl df_div(dfl a, dfl b) {
+    float q1 = a.hi / b.hi;
+    dfl r = df_add(a, df_neg(df_mulf(b, q1)));
+    float q2 = r.hi / b.hi;
+    return quick_two_sum(q1, q2);
+}
 // square of an exact float difference b - a, as double-float
 __device__ __forceinline__ dfl df_sq_diff(float b, float a) {
     dfl d = two_sum(b, -a);

@@ -611,9 +611,54 @@ __device__ bool refl_newton64(double A, double Ds, double Pu, double Pv, double 
     return false;
 }
 
-// FP64 refinement of an FP32 reflection point (near-grazing incidence, where
-// the FP32 root of dL/dpsi is too coarse for cos(theta_i)); FP64 bisection
-// when Newton does not converge.  Returns (cos psi, sin psi) in FP32.
+// Double-float refinement of an FP32 reflection point (near-grazing
+// incidence, where the FP32 root of dL/dpsi is too coarse for cos(theta_i)).
+// At n0 = (c0, s0) = sincos(psi0) normalised exactly (1/|n0| = 1 - delta/2,
+// delta = |n0|^2 - 1 formed exactly), dL/dpsi of the closed form above is
+// evaluated in double-float -- its two terms cancel at the root, which is
+// what limits the FP32 root -- and Newton steps rotate n; the FP32 slope is
+// enough for the step.  Returns false if a step exceeds 1e-4 or the slope is
+// not positive.
+__device__ bool refl_polish_df(float a, float ds, float pu, float pv, float psi0, float *cs_out, float *sn_out) {
+    float c0, s0;
+    sincosf(psi0, &s0, &c0);
+    for (int it = 0; it < 3; ++it) {
+        dfl r2 = df_add(two_prod(c0, c0), two_prod(s0, s0));
+        float delta = (r2.hi - 1.0f) + r2.lo;
+        dfl c, s;
+        c.hi = c0; c.lo = -0.5f * delta * c0;
+        s.hi = s0; s.lo = -0.5f * delta * s0;
+        // |Q - S|^2 = a^2 + ds^2 - 2 a ds c,  |Q - P|^2 = a^2 + pu^2 + pv^2 - 2 a (pu c + pv s)
+        dfl a2 = two_prod(a, a);
+        dfl fs2 = df_add(df_add(a2, two_prod(ds, ds)), df_neg(df_mul(c, two_prod(2.0f * a, ds))));
+        dfl ps = df_add(df_mulf(c, pu), df_mulf(s, pv));
+        dfl fr2 = df_add(df_add(a2, df_add(two_prod(pu, pu), two_prod(pv, pv))), df_neg(df_mulf(ps, 2.0f * a)));
+        dfl fs = df_sqrt(fs2), fr = df_sqrt(fr2);
+        dfl t1 = df_div(df_mulf(s, ds), fs);
+        dfl t2 = df_div(df_add(df_mulf(s, pu), df_neg(df_mulf(c, pv))), fr);
+        dfl g = df_add(t1, t2);                               // (dL/dpsi) / a
+        // slope d2L/dpsi2 = a sum_X (u - a)(|X|^2 - a u) / |Q - X|^3, u = X.n: a
+        // product form (the difference form cancels near grazing)
+        float uS = ds * c0, uP = ps.hi;
+        float g2 = a * ((uS - a) * (ds * ds - a * uS) / (fs.hi * fs.hi * fs.hi) +
+                        (uP - a) * (pu * pu + pv * pv - a * uP) / (fr.hi * fr.hi * fr.hi));
+        if (!(g2 > 0.0f)) return false;
+        float d = -(a * (g.hi + g.lo)) / g2;
+        if (!(fabsf(d) <= 1e-4f)) return false;
+        // rotate by d (cos d = 1 - d^2/2, sin d = d at this size), one rounding
+        float cn = c0 + (c.lo - s0 * d - 0.5f * c0 * d * d);
+        float sn = s0 + (s.lo + c0 * d - 0.5f * s0 * d * d);
+        c0 = cn; s0 = sn;
+        if (fabsf(d) <= 1e-9f) break;
+    }
+    *cs_out = c0;
+    *sn_out = s0;
+    return true;
+}
+
+// FP64 refinement of an FP32 reflection point, for the cases the
+// double-float step does not take; FP64 bisection when Newton does not
+// converge.  Returns (cos psi, sin psi) in FP32.
 __device__ __noinline__ void refl_polish(float a, float ds, float pu, float pv, float gam, float psi0,
                                          float *cs_out, float *sn_out) {
     float c0f, s0f;
@@ -692,7 +737,10 @@ __device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Fr
         // when its FP32 error would exceed 1e-5 of cos(theta_i) (near grazing),
         // the amplitude budget of the FP32 path
         float c2 = (F.ds * cs - a) / sqrtf((a * cs - F.ds) * (a * cs - F.ds) + a * a * sn * sn);
-        if (psi_err > 1e-5f * fmaxf(c2, 0.0f)) refl_polish(a, F.ds, F.pu, F.pv, F.gam, psi, &cs, &sn);
+        if (psi_err > 1e-5f * fmaxf(c2, 0.0f)) {
+            if (!refl_polish_df(a, F.ds, F.pu, F.pv, psi, &cs, &sn))
+                refl_polish(a, F.ds, F.pu, F.pv, F.gam, psi, &cs, &sn);
+        }
     } else {
         refl_root(a, F.ds, F.pu, F.pv, F.gam, &cs, &sn);
     }
