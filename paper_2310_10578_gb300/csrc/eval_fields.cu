@@ -204,17 +204,27 @@ __device__ __forceinline__ int blocked_impl(const Ctx &c, v3t<T> A, v3t<T> B, in
     int uns = 0;
     if constexpr (sizeof(T) == 4) {
         // faces first: both ends clearly on one side of a face's plane => none of
-        // its triangles can be hit
-        for (int f = 0; f < c.n_face; ++f) {
-            if (f == sf1 || f == sf2) continue;
-            float4 q = c.face32[f];
-            float sA = q.x * A.x + q.y * A.y + q.z * A.z - q.w, sB = q.x * B.x + q.y * B.y + q.z * B.z - q.w;
-            if ((sA > band && sB > band) || (sA < -band && sB < -band)) continue;
-            int2 rg = c.face_rng[f];
-            for (int i = 0; i < rg.y; ++i) {
-                int r = seg_tri(c, c.face_tris[rg.x + i], A, B, band);
-                if (r == D_YES) return D_YES;
-                uns |= (r == D_UNSURE);
+        // its triangles can be hit (the plane tests of all faces are made
+        // branch-free; only the faces left over are looked at)
+        for (int f0 = 0; f0 < c.n_face; f0 += 32) {
+            unsigned keep = 0;
+            const int nfc = min(32, c.n_face - f0);
+#pragma unroll 4
+            for (int k = 0; k < nfc; ++k) {
+                float4 q = c.face32[f0 + k];
+                float sA = q.x * A.x + q.y * A.y + q.z * A.z - q.w, sB = q.x * B.x + q.y * B.y + q.z * B.z - q.w;
+                bool cull = (sA > band && sB > band) || (sA < -band && sB < -band) || f0 + k == sf1 || f0 + k == sf2;
+                keep |= cull ? 0u : (1u << k);
+            }
+            while (keep) {
+                const int f = f0 + __ffs(keep) - 1;
+                keep &= keep - 1;
+                int2 rg = c.face_rng[f];
+                for (int i = 0; i < rg.y; ++i) {
+                    int r = seg_tri(c, c.face_tris[rg.x + i], A, B, band);
+                    if (r == D_YES) return D_YES;
+                    uns |= (r == D_UNSURE);
+                }
             }
         }
     } else {
@@ -243,34 +253,37 @@ __device__ __forceinline__ int blocked_impl(const Ctx &c, v3t<T> A, v3t<T> B, in
         // bodies: a squared-distance test against the segment's closest point
         // to the centre (cylinders: to the axis, in projection) rejects the
         // bodies that are clearly apart -- distance above a + band, so the
-        // margin of the full test would be below -band -- in a few FMAs with
-        // the per-segment constants; the rest get the full test
+        // margin of the full test would be below -band.  Four bodies at a
+        // time without branches (sphere and cylinder differ by a select), so
+        // their dependent chains overlap; the full test only for the rest.
         const v3t<float> D = B - A;
         const float qa = D.x * D.x + D.y * D.y;
         const float iqa = (qa > 0.0f) ? 1.0f / qa : 0.0f;
         const float idd = 1.0f / (qa + D.z * D.z);
         const float tlo = (float)EPS_TRIM, thi = 1.0f - (float)EPS_TRIM;
-#pragma unroll 2
-        for (int b = 0; b < c.n_body; ++b) {
-            if (b == sb) continue;
-            const float4 q0 = c.body[2 * b];
-            const float wx = q0.x - A.x, wy = q0.y - A.y;
-            float d2;
-            if (c.body[2 * b + 1].y == 0.0f) {          // sphere: closest point of the segment to c
-                const float wz = q0.z - A.z;
-                const float t = fminf(fmaxf((wx * D.x + wy * D.y + wz * D.z) * idd, tlo), thi);
-                const float hx = D.x * t - wx, hy = D.y * t - wy, hz = D.z * t - wz;
-                d2 = hx * hx + hy * hy + hz * hz;
-            } else {                                     // cylinder: closest point to the axis
-                const float t = (qa > 0.0f) ? fminf(fmaxf((wx * D.x + wy * D.y) * iqa, tlo), thi) : tlo;
-                const float hx = D.x * t - wx, hy = D.y * t - wy;
-                d2 = hx * hx + hy * hy;
+        const int nb = c.n_body;
+        for (int b0 = 0; b0 < nb; b0 += 4) {
+            unsigned near = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int b = min(b0 + k, nb - 1);
+                const float4 q0 = c.body[2 * b];
+                const bool sph = c.body[2 * b + 1].y == 0.0f;
+                const float wx = q0.x - A.x, wy = q0.y - A.y, wz = sph ? q0.z - A.z : 0.0f;
+                const float dz = sph ? D.z : 0.0f;
+                const float t = fminf(fmaxf((wx * D.x + wy * D.y + wz * dz) * (sph ? idd : iqa), tlo), thi);
+                const float hx = D.x * t - wx, hy = D.y * t - wy, hz = dz * t - wz;
+                const float ab = q0.w + band;
+                const bool n = (b0 + k < nb) && (b0 + k != sb) && (hx * hx + hy * hy + hz * hz <= ab * ab);
+                near |= n ? (1u << k) : 0u;
             }
-            const float ab = q0.w + band;
-            if (d2 > ab * ab) continue;
-            int r = seg_body(c, b, A, B, band);
-            if (r == D_YES) return D_YES;
-            uns |= (r == D_UNSURE);
+            while (near) {
+                const int b = b0 + __ffs(near) - 1;
+                near &= near - 1;
+                int r = seg_body(c, b, A, B, band);
+                if (r == D_YES) return D_YES;
+                uns |= (r == D_UNSURE);
+            }
         }
     }
     return uns ? D_UNSURE : D_NO;
