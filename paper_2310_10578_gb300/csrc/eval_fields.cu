@@ -1065,6 +1065,14 @@ template <typename T>
 struct Acc {
     cpx<T> E[NFC][3];
 };
+// The same sums kept in shared memory (the kernel's per-warp partial-field
+// array; entry j of this lane at p[32 j], j = 6 f + 2 q + {0: re, 1: im}):
+// the receiver's sums are then not live registers across the calls of the
+// candidate loop.
+template <typename T>
+struct AccS {
+    T *p;
+};
 
 template <typename T>
 __device__ __forceinline__ v3t<T> src_pol(const Ctx &c, v3t<T> d) {
@@ -1134,8 +1142,21 @@ __device__ __forceinline__ void acc_put(Acc<T> &acc, int f, cpx<T> x, cpx<T> y, 
     }
 }
 
-template <typename T, typename L>
-__device__ __forceinline__ void add_ray(Acc<T> &acc, const FreqC &fq, v3t<T> e, T amp, L len) {
+template <typename T>
+__device__ __forceinline__ void acc_put(AccS<T> &acc, int f, cpx<T> x, cpx<T> y, cpx<T> z) {
+    T *q = acc.p + f * 6 * 32;
+    q[0] = q[0] + x.re; q[32] = q[32] + x.im;
+    q[64] = q[64] + y.re; q[96] = q[96] + y.im;
+    q[128] = q[128] + z.re; q[160] = q[160] + z.im;
+}
+template <typename T>
+__device__ __forceinline__ void acc_zero(AccS<T> &acc) {
+#pragma unroll
+    for (int j = 0; j < NFC * 6; ++j) acc.p[32 * j] = T(0.0);
+}
+
+template <typename T, typename L, typename ACC>
+__device__ __forceinline__ void add_ray(ACC &acc, const FreqC &fq, v3t<T> e, T amp, L len) {
 #pragma unroll 1
     for (int f = 0; f < fq.nf; ++f) {
         cpx<T> ph = phasor(fq, f, len) * amp;
@@ -1143,8 +1164,8 @@ __device__ __forceinline__ void add_ray(Acc<T> &acc, const FreqC &fq, v3t<T> e, 
     }
 }
 
-template <typename T, typename L, bool F32FOCK = false>
-__device__ void field_body_refl(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S, v3t<T> P, const Geo<T> &g, L len) {
+template <typename T, typename L, bool F32FOCK = false, typename ACC = Acc<T>>
+__device__ void field_body_refl(const Ctx &c, ACC &acc, const FreqC &fq, v3t<T> S, v3t<T> P, const Geo<T> &g, L len) {
     v3t<T> Q = g.Q1, n = g.n1;
     v3t<T> di = Q - S;
     T si = norm3(di), sr = norm3(g.dr);
@@ -1194,8 +1215,8 @@ __device__ void field_body_refl(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<
     }
 }
 
-template <typename T, typename L, bool F32FOCK = false>
-__device__ void field_creep(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S, v3t<T> P, const Geo<T> &g,
+template <typename T, typename L, bool F32FOCK = false, typename ACC = Acc<T>>
+__device__ void field_creep(const Ctx &c, ACC &acc, const FreqC &fq, v3t<T> S, v3t<T> P, const Geo<T> &g,
                             L len, unsigned enable) {
     v3t<T> t1 = unit3(g.Q1 - S), t2 = unit3(P - g.Q2);
     v3t<T> b1 = cross3(t1, g.n1), b2 = cross3(t2, g.n2);
@@ -1221,6 +1242,105 @@ __device__ void field_creep(const Ctx &c, Acc<T> &acc, const FreqC &fq, v3t<T> S
             cpx<T> as = Bs * ph * Es, ah = Bh * ph * Eh;
             acc_put(acc, f, as * b2.x + ah * g.n2.x, as * b2.y + ah * g.n2.y, as * b2.z + ah * g.n2.z);
         }
+    }
+}
+
+// ---- path records (FP32): the frequency-independent factors of one path's
+// field, written by the geometry pass and turned into fields, frequency by
+// frequency, by the field pass; the two passes are separate loops so that
+// each one's code stays in the instruction cache.  14 floats, entry j of a
+// lane at rec[32 j]:
+//   0 Es, 1 Eh, 2-4 e1, 5-7 e2, 8 A (creeping: amplitude, negative for the
+//   ray through the caustic), 9 L' (transition distance), 10 rho_g^(1/3),
+//   11 cos(theta_i) (reflection) or t / rho_g (creeping), 12-13 path length.
+constexpr int REC_N = 14;
+constexpr int REC_CAP = 5;             // records per lane between field passes
+
+__device__ __forceinline__ void rec_put(float *r, float Es, float Eh, v3t<float> e1, v3t<float> e2, float A,
+                                        float Lp, float rcb, float x, dfl len) {
+    r[0] = Es; r[32] = Eh;
+    r[64] = e1.x; r[96] = e1.y; r[128] = e1.z;
+    r[160] = e2.x; r[192] = e2.y; r[224] = e2.z;
+    r[256] = A; r[288] = Lp; r[320] = rcb; r[352] = x; r[384] = len.hi; r[416] = len.lo;
+}
+
+// reflection off a body: as field_body_refl, up to the frequency loop
+__device__ __forceinline__ void rb_prep(const Ctx &c, float *r, v3t<float> S, const Geo<float> &g, dfl len) {
+    v3t<float> Q = g.Q1, n = g.n1;
+    v3t<float> di = Q - S;
+    float si = norm3(di), sr = norm3(g.dr);
+    v3t<float> shi = di * (1.0f / si);
+    float cth = -dot3(shi, n);
+    v3t<float> shr = unit3(shi + n * (2.0f * cth));
+    v3t<float> ep = cross3(n, shi);
+    float ne = norm3(ep);
+    if (ne == 0.0f) {
+        v3t<float> tmp = (fabsf(n.x) < 0.9f) ? mk3<float>(1, 0, 0) : mk3<float>(0, 1, 0);
+        ep = unit3(cross3(n, tmp));
+    } else {
+        ep = ep * (1.0f / ne);
+    }
+    v3t<float> epi = cross3(ep, shi), epr = cross3(ep, shr);
+    v3t<float> e0 = src_pol(c, shi);
+    float rho1 = 1.0f / (1.0f / si + g.inv_f1), rho2 = 1.0f / (1.0f / si + g.inv_f2);
+    float A = sqrtf(rho1 * rho2 / ((rho1 + sr) * (rho2 + sr))) / si;
+    rec_put(r, dot3(e0, ep), dot3(e0, epi), ep, epr, A, si * sr / (si + sr), cbrtf(g.rho_g), cth, len);
+}
+__device__ __forceinline__ void rb_apply(const Ctx &c, AccS<float> &acc, const FreqC &fq, const float *r) {
+    const float Es = r[0], Eh = r[32], A = r[256], Lp = r[288], rcb = r[320], cth = r[352];
+    dfl len;
+    len.hi = r[384]; len.lo = r[416];
+#pragma unroll 1
+    for (int f = 0; f < fq.nf; ++f) {
+        float k = fq.k[f];
+        float m = fq.kh[f] * rcb;
+        float xi = -2.0f * m * cth;
+        cpx<float> Rs, Rh;
+        if (!(xi >= (float)XI_LO)) {
+            Rs = mkc<float>(-1, 0); Rh = mkc<float>(1, 0);
+        } else {
+            cpx<float> Bs, Bh;
+            fock_bracket<float>(c, xi, sqrtf(k * Lp / (2.0f * m * m)), Bs, Bh);
+            float sn, cs;
+            sincospif(-xi * xi * xi * (float)(1.0 / (12.0 * M_PI)), &sn, &cs);
+            cpx<float> pre = mkc<float>(cs, sn) * (-sqrtf(-4.0f / xi));
+            Rs = pre * Bs; Rh = pre * Bh;
+        }
+        cpx<float> ph = phasor(fq, f, len) * A;
+        cpx<float> as = Rs * ph * Es, ah = Rh * ph * Eh;
+        acc_put(acc, f, as * r[64] + ah * r[160], as * r[96] + ah * r[192], as * r[128] + ah * r[224]);
+    }
+}
+
+// creeping ray: as field_creep, up to the frequency loop
+__device__ __forceinline__ void creep_prep(const Ctx &c, float *r, v3t<float> S, v3t<float> P, const Geo<float> &g,
+                                           dfl len, unsigned enable) {
+    v3t<float> t1 = unit3(g.Q1 - S), t2 = unit3(P - g.Q2);
+    v3t<float> b1 = cross3(t1, g.n1), b2 = cross3(t2, g.n2);
+    v3t<float> e0 = src_pol(c, t1);
+    float Es = (enable & RT_EN_CREEP_SOFT) ? dot3(e0, b1) : 0.0f;
+    float Eh = (enable & RT_EN_CREEP_HARD) ? dot3(e0, g.n1) : 0.0f;
+    rec_put(r, Es, Eh, b2, g.n2, g.caus ? -g.amp : g.amp, g.sp * g.sq / (g.sp + g.sq), cbrtf(g.rho_g),
+            g.t / g.rho_g, len);
+}
+__device__ __forceinline__ void creep_apply(const Ctx &c, AccS<float> &acc, const FreqC &fq, const float *r) {
+    const float Es = r[0], Eh = r[32], Lp = r[288], rcb = r[320], tr = r[352];
+    const float amp = fabsf(r[256]);
+    const bool caus = r[256] < 0.0f;
+    dfl len;
+    len.hi = r[384]; len.lo = r[416];
+#pragma unroll 1
+    for (int f = 0; f < fq.nf; ++f) {
+        float k = fq.k[f];
+        float m = fq.kh[f] * rcb;
+        float xi = m * tr;
+        cpx<float> Bs, Bh;
+        fock_bracket<float>(c, xi, sqrtf(k * Lp / (2.0f * m * m)), Bs, Bh);
+        float pre = -m * sqrtf(2.0f / k) * amp;
+        cpx<float> ph = phasor(fq, f, len) * pre;
+        if (caus) ph = mkc<float>(-ph.im, ph.re);          // x (+j)
+        cpx<float> as = Bs * ph * Es, ah = Bh * ph * Eh;
+        acc_put(acc, f, as * r[64] + ah * r[160], as * r[96] + ah * r[192], as * r[128] + ah * r[224]);
     }
 }
 
@@ -1278,12 +1398,8 @@ __device__ __forceinline__ void contrib_from(Contrib *o, const Acc<dx> &a) {
 #pragma unroll
         for (int q = 0; q < 3; ++q) o->E[f][q] = mkc<float>(to_float(a.E[f][q].re), to_float(a.E[f][q].im));
 }
-__device__ __forceinline__ void acc_add(Acc<float> &a, const Contrib &b, int nf) {
-#pragma unroll
-    for (int f = 0; f < NFC; ++f)
-        if (f < nf)
-#pragma unroll
-            for (int q = 0; q < 3; ++q) a.E[f][q] = a.E[f][q] + b.E[f][q];
+__device__ __forceinline__ void acc_add(AccS<float> &a, const Contrib &b, int nf) {
+    for (int f = 0; f < nf; ++f) acc_put(a, f, b.E[f][0], b.E[f][1], b.E[f][2]);
 }
 __device__ __forceinline__ void acc_zero(Acc<dx> &a) {
 #pragma unroll
@@ -1378,7 +1494,7 @@ template <typename T, bool PATHS, int CLS>
 __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, unsigned enable, int max_order,
                                               const float *__restrict__ rx, int n_rx, int r,
                                               uint64_t *__restrict__ codes, int cap, double half_lambda_max,
-                                              int part, int nparts, Acc<T> &acc, uint32_t &fl, unsigned &nesc,
+                                              int part, int nparts, AccS<T> acc, float *rec, uint32_t &fl, unsigned &nesc,
                                               int &npath) {
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     const bool fp32 = sizeof(T) == 4;
@@ -1389,10 +1505,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
     v3t<T> Sx = mk3<T>(T((double)c.S.x), T((double)c.S.y), T((double)c.S.z));
     fl = 0;
     nesc = 0;
-#pragma unroll
-    for (int f = 0; f < NFC; ++f)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) acc.E[f][q] = mkc<T>(T(0.0), T(0.0));
+    if (!PATHS) acc_zero(acc);
     typedef typename LenOf<T>::type LT;
 
     auto emit = [&](int type, int a, int b) {
@@ -1504,8 +1617,30 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
         }
         // ---- curved bodies
         if constexpr (BODIES) {
+            // FP32 fields: the geometry pass writes a record per valid path,
+            // the field pass (one place in the loop) turns the records into
+            // fields when the buffer could overflow and at the end
+            constexpr bool RECS = (sizeof(T) == 4) && !PATHS;
+            constexpr int PER = ((CLS & CLS_CREEP) ? 2 : 0) + ((CLS & CLS_BODYREFL) ? 1 : 0);
+            int nrec = 0;
+            int b = part;
 #pragma unroll 1
-            for (int b = part; b < c.n_body; b += nparts) {
+            for (;;) {
+                const bool done = b >= c.n_body;
+                if constexpr (RECS) {
+                    if (done || nrec > REC_CAP - PER) {
+#pragma unroll 1
+                        for (int j = 0; j < nrec; ++j) {
+                            const float *r = rec + j * REC_N * 32;
+                            if constexpr (CLS == CLS_BODYREFL) rb_apply(c, acc, fq, r);
+                            else if constexpr (CLS == CLS_CREEP) creep_apply(c, acc, fq, r);
+                            else if (r[288] < 0.0f) creep_apply(c, acc, fq, r);   // creeping records: L' < 0
+                            else rb_apply(c, acc, fq, r);
+                        }
+                        nrec = 0;
+                    }
+                }
+                if (done) break;
                 Frame<T> F;
                 body_frame(c, b, Sx, P, band, F);
                 if constexpr ((CLS & CLS_BODYREFL) != 0) {
@@ -1529,11 +1664,11 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                         }
                         if (d == D_YES) {
                             emit(PT_RB, b, 0);
-                            if (!PATHS) {
-                                LT L;
-                                if constexpr (sizeof(T) == 4) L = g.Lf;
-                                else L = ladd(seglen(Sx, g.Q1), seglen(g.Q1, P));
-                                field_body_refl<T>(c, acc, fq, Sx, P, g, L);
+                            if constexpr (RECS) {
+                                rb_prep(c, rec + nrec * REC_N * 32, Sx, g, g.Lf);
+                                ++nrec;
+                            } else if constexpr (!PATHS) {
+                                field_body_refl<T>(c, acc, fq, Sx, P, g, ladd(seglen(Sx, g.Q1), seglen(g.Q1, P)));
                             }
                         }
                     }
@@ -1571,13 +1706,18 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                                 if (cd == D_YES) fl |= RT_FLAG_CAUSTIC;
                                 if (!(g.dperp > T(0.0))) continue;        // exactly on the axis: no finite ray field
                             }
-                            if (!PATHS) {
-                                LT L = creep_len(c, b, Sx, P, g, F);
-                                field_creep<T>(c, acc, fq, Sx, P, g, L, enable);
+                            if constexpr (RECS) {
+                                float *r = rec + nrec * REC_N * 32;
+                                creep_prep(c, r, Sx, P, g, creep_len(c, b, Sx, P, g, F), enable);
+                                if constexpr (CLS != CLS_CREEP) r[288] = -r[288];   // mark as creeping
+                                ++nrec;
+                            } else if constexpr (!PATHS) {
+                                field_creep<T>(c, acc, fq, Sx, P, g, creep_len(c, b, Sx, P, g, F), enable);
                             }
                         }
                     }
                 }
+                b += nparts;
             }
         }
     }
@@ -1605,6 +1745,7 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
     float4 *s_aux = s_tri + (tri_sm ? 3 * S.n_tri : 0);      // n_tri * 3 (if staged)
     float4 *s_txb = s_aux + (tri_sm ? 3 * S.n_tri : 0);      // n_body * 2 (if staged)
     float *s_weid = (float *)(s_txb + (body_sm ? 2 * S.n_body : 0));
+    float *s_rec = s_weid + WEIDEMAN_N;                      // path records (FP32 fields of the body classes)
     for (int i = threadIdx.x; i < n_fock; i += blockDim.x) s_fock[i] = S.fock32[i];
     for (int i = threadIdx.x; i < n_res; i += blockDim.x) s_res[i] = S.res32[i];
     for (int i = threadIdx.x; i < S.n_face; i += blockDim.x) s_face[i] = S.face32[i];
@@ -1657,12 +1798,12 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
             if (t >= ntiles) break;
             int r = (int)(t * 32ull) + lane;
             if (r < n_rx) {
-                Acc<T> acc;
+                AccS<T> acc{nullptr};                // no fields in this mode
                 uint32_t fl;
                 unsigned nesc;
                 int npath = accumulate ? counts[r] : 0;
                 eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap, half_lambda_max,
-                                             0, 1, acc, fl, nesc, npath);
+                                             0, 1, acc, nullptr, fl, nesc, npath);
                 counts[r] = npath;
                 if (flags_out) flags_out[r] = accumulate ? (flags_out[r] | fl) : fl;
                 if (nesc) atomicAdd(esc_counter, (unsigned long long)nesc);
@@ -1684,20 +1825,14 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
             const unsigned long long t = s_tile;
             if (t >= ntiles) break;
             const int r = (int)(t * 32ull) + lane;
-            Acc<T> acc;
+            AccS<T> acc{&s_part[warp][0][lane]};     // the warp's partial sums, summed in place
             uint32_t fl = 0;
             unsigned nesc = 0;
             int npath = 0;
             if (r < n_rx)
                 eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap, half_lambda_max,
-                                             warp, NW, acc, fl, nesc, npath);
-#pragma unroll
-            for (int f = 0; f < NFC; ++f)
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    s_part[warp][(f * 3 + q) * 2][lane] = acc.E[f][q].re;
-                    s_part[warp][(f * 3 + q) * 2 + 1][lane] = acc.E[f][q].im;
-                }
+                                             warp, NW, acc, s_rec + warp * (REC_CAP * REC_N * 32) + lane, fl, nesc,
+                                             npath);
             s_fl[warp][lane] = fl;
             if (nesc && f0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
             __syncthreads();
@@ -1733,11 +1868,12 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
     }
 }
 
-static size_t smem_bytes(const DevScene &S, bool bodies) {
+static size_t smem_bytes(const DevScene &S, bool bodies, bool records) {
     size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + S.n_face;
     if (S.n_body <= SMEM_BODY_MAX) n += 4 * S.n_body;
     if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;
-    return n * sizeof(float4) + WEIDEMAN_N * sizeof(float) + 16;
+    return n * sizeof(float4) + WEIDEMAN_N * sizeof(float) + 16 +
+           (records ? sizeof(float) * (BLOCK / 32) * REC_CAP * REC_N * 32 : 0);
 }
 
 // Launch state of one evaluation: the counters (escalations, one work queue
@@ -1753,7 +1889,8 @@ static cudaError_t launch_one(const DevScene &S, const float *rx_soa, int n_rx, 
                               uint64_t *codes, int32_t *counts, int cap, int f0, const FreqC &fq, double hl,
                               int accumulate, LaunchCtx &L) {
     if (L.n >= CTR_QUEUES) return cudaErrorInvalidValue;
-    size_t sm = smem_bytes(S, (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0);
+    constexpr bool bodies = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
+    size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS);
     cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     // persistent grid: the blocks that fit on the device at once
