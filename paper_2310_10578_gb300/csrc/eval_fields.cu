@@ -1480,9 +1480,16 @@ enum { CLS_PLANAR = 1,        // direct ray and planar image reflections
 #ifndef CREEP_SPLIT
 #define CREEP_SPLIT 3          // 1: one kernel; 2: planar | bodies; 3: planar | reflection | creeping
 #endif
-constexpr int min_blocks(int cls) {
-    return cls == CLS_PLANAR ? 4 : (cls == (CLS_PLANAR | CLS_BODYREFL | CLS_CREEP) ? 2 : 3);
+// Block shape.  The body classes run one block of 12 warps per SM: three
+// tiles at a time, four warps per tile; a block barrier between the geometry
+// pass and the field pass keeps all warps of the SM in the same pass, so the
+// instruction cache holds one pass's code at a time.  The planar class, and
+// the FP64 path, run 4-warp blocks, several per SM.
+constexpr int blk_of(int cls, bool fp32) { return ((cls & (CLS_BODYREFL | CLS_CREEP)) && fp32) ? 384 : BLOCK; }
+constexpr int min_blocks(int cls, bool fp32) {
+    return ((cls & (CLS_BODYREFL | CLS_CREEP)) && fp32) ? 1 : (cls == CLS_PLANAR ? 4 : 3);
 }
+constexpr int WARPS_PER_TILE = 4;
 
 // One receiver P = rx[r]: the paths of the classes in CLS among the
 // candidates of share `part` of `nparts` -- the direct ray to share 0, the
@@ -1495,7 +1502,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                                               const float *__restrict__ rx, int n_rx, int r,
                                               uint64_t *__restrict__ codes, int cap, double half_lambda_max,
                                               int part, int nparts, AccS<T> acc, float *rec, uint32_t &fl, unsigned &nesc,
-                                              int &npath) {
+                                              int &npath, int &nrec_out) {
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     const bool fp32 = sizeof(T) == 4;
     const T band = fp32 ? T(c.band) : T(0);
@@ -1505,6 +1512,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
     v3t<T> Sx = mk3<T>(T((double)c.S.x), T((double)c.S.y), T((double)c.S.z));
     fl = 0;
     nesc = 0;
+    nrec_out = 0;
     if (!PATHS) acc_zero(acc);
     typedef typename LenOf<T>::type LT;
 
@@ -1617,9 +1625,10 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
         }
         // ---- curved bodies
         if constexpr (BODIES) {
-            // FP32 fields: the geometry pass writes a record per valid path,
-            // the field pass (one place in the loop) turns the records into
-            // fields when the buffer could overflow and at the end
+            // FP32 fields: the geometry pass writes a record per valid path;
+            // the records left at the end are turned into fields by the
+            // caller's field pass, after a block barrier (here only when the
+            // buffer could overflow)
             constexpr bool RECS = (sizeof(T) == 4) && !PATHS;
             constexpr int PER = ((CLS & CLS_CREEP) ? 2 : 0) + ((CLS & CLS_BODYREFL) ? 1 : 0);
             int nrec = 0;
@@ -1628,7 +1637,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
             for (;;) {
                 const bool done = b >= c.n_body;
                 if constexpr (RECS) {
-                    if (done || nrec > REC_CAP - PER) {
+                    if (!done && nrec > REC_CAP - PER) {
 #pragma unroll 1
                         for (int j = 0; j < nrec; ++j) {
                             const float *r = rec + j * REC_N * 32;
@@ -1719,13 +1728,14 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                 }
                 b += nparts;
             }
+            nrec_out = nrec;
         }
     }
 }
 
 
 template <typename T, bool PATHS, int CLS>
-__global__ void __launch_bounds__(BLOCK, min_blocks(CLS))
+__global__ void __launch_bounds__(blk_of(CLS, sizeof(T) == 4), min_blocks(CLS, sizeof(T) == 4))
 k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e_out, uint32_t *__restrict__ flags_out,
        uint64_t *__restrict__ codes, int32_t *__restrict__ counts, int cap, int f0, FreqC fq_in, double half_lambda_max,
        int accumulate, unsigned long long *esc_counter, unsigned long long *queue) {
@@ -1785,7 +1795,7 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
     const Ctx &c = s_ctx;
     const FreqC &fq = s_fq;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int NW = BLOCK / 32;
+    constexpr int NW = blk_of(CLS, sizeof(T) == 4) / 32;
     const unsigned long long ntiles = ((unsigned long long)n_rx + 31ull) >> 5;
     if constexpr (PATHS) {
         // path lists: each warp takes tiles of 32 consecutive receivers from
@@ -1802,8 +1812,9 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
                 uint32_t fl;
                 unsigned nesc;
                 int npath = accumulate ? counts[r] : 0;
+                int nrec;
                 eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap, half_lambda_max,
-                                             0, 1, acc, nullptr, fl, nesc, npath);
+                                             0, 1, acc, nullptr, fl, nesc, npath, nrec);
                 counts[r] = npath;
                 if (flags_out) flags_out[r] = accumulate ? (flags_out[r] | fl) : fl;
                 if (nesc) atomicAdd(esc_counter, (unsigned long long)nesc);
@@ -1811,39 +1822,59 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
         }
     } else {
         // fields: persistent blocks take tiles of 32 consecutive receivers
-        // from the launch's queue; the block's warps share each tile's
-        // candidates (warp w takes share w) and the partial fields are summed
-        // in shared memory in warp order, so the result does not depend on
-        // timing.  Sharing a tile among the warps shortens it, so the last
-        // tiles of the launch leave little of the GPU idle.
+        // from the launch's queue, TPB tiles per step; the NWT warps of a
+        // tile share its candidates (warp part p takes share p) and the
+        // partial fields are summed in shared memory in warp order, so the
+        // result does not depend on timing.  Sharing a tile among warps
+        // shortens it, so the last tiles of the launch leave little of the GPU
+        // idle.  Body classes: all warps finish the geometry pass (records)
+        // before any starts the field pass.
+        constexpr int NWT = BODIES ? WARPS_PER_TILE : NW;
+        constexpr int TPB = NW / NWT;
+        constexpr bool RECS = BODIES && sizeof(T) == 4;
+        const int grp = warp / NWT, part = warp % NWT;
         __shared__ T s_part[NW][NFC * 6][32];
         __shared__ uint32_t s_fl[NW][32];
         __shared__ unsigned long long s_tile;
         for (;;) {
-            if (threadIdx.x == 0) s_tile = atomicAdd(queue, 1ull);
+            if (threadIdx.x == 0) s_tile = atomicAdd(queue, (unsigned long long)TPB);
             __syncthreads();
-            const unsigned long long t = s_tile;
-            if (t >= ntiles) break;
+            const unsigned long long t = s_tile + grp;
+            if (s_tile >= ntiles) break;
             const int r = (int)(t * 32ull) + lane;
+            const bool rok = t < ntiles && r < n_rx;
             AccS<T> acc{&s_part[warp][0][lane]};     // the warp's partial sums, summed in place
+            float *rec = s_rec + warp * (REC_CAP * REC_N * 32) + lane;
             uint32_t fl = 0;
             unsigned nesc = 0;
-            int npath = 0;
-            if (r < n_rx)
+            int npath = 0, nrec = 0;
+            if (rok)
                 eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap, half_lambda_max,
-                                             warp, NW, acc, s_rec + warp * (REC_CAP * REC_N * 32) + lane, fl, nesc,
-                                             npath);
+                                             part, NWT, acc, rec, fl, nesc, npath, nrec);
+            if constexpr (RECS) {
+                __syncthreads();                      // every warp has done its geometry pass
+#pragma unroll 1
+                for (int j = 0; j < nrec; ++j) {
+                    const float *rj = rec + j * REC_N * 32;
+                    if constexpr (CLS == CLS_BODYREFL) rb_apply(c, acc, fq, rj);
+                    else if constexpr (CLS == CLS_CREEP) creep_apply(c, acc, fq, rj);
+                    else if (rj[288] < 0.0f) creep_apply(c, acc, fq, rj);
+                    else rb_apply(c, acc, fq, rj);
+                }
+            }
             s_fl[warp][lane] = fl;
             if (nesc && f0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
             __syncthreads();
-            // reduce: warp w writes the (frequency, component) pairs j = w, w + NW, ...
-            if (r < n_rx) {
-                for (int j = warp; j < fq.nf * 3; j += NW) {
-                    T re = s_part[0][2 * j][lane], im = s_part[0][2 * j + 1][lane];
+            // reduce the tile's NWT partials: part p writes the (frequency,
+            // component) pairs j = p, p + NWT, ...
+            if (rok) {
+                const int w0 = grp * NWT;
+                for (int j = part; j < fq.nf * 3; j += NWT) {
+                    T re = s_part[w0][2 * j][lane], im = s_part[w0][2 * j + 1][lane];
 #pragma unroll
-                    for (int w = 1; w < NW; ++w) {
-                        re = re + s_part[w][2 * j][lane];
-                        im = im + s_part[w][2 * j + 1][lane];
+                    for (int w = 1; w < NWT; ++w) {
+                        re = re + s_part[w0 + w][2 * j][lane];
+                        im = im + s_part[w0 + w][2 * j + 1][lane];
                     }
                     size_t idx = ((size_t)(f0 + j / 3) * 3 + (j % 3)) * n_rx + r;
                     float2 v;
@@ -1856,10 +1887,10 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
                     }
                     reinterpret_cast<float2 *>(e_out)[idx] = v;
                 }
-                if (warp == 0 && flags_out && f0 == 0) {
+                if (part == 0 && flags_out && f0 == 0) {
                     uint32_t f_all = 0;
 #pragma unroll
-                    for (int w = 0; w < NW; ++w) f_all |= s_fl[w][lane];
+                    for (int w = 0; w < NWT; ++w) f_all |= s_fl[w0 + w][lane];
                     flags_out[r] = accumulate ? (flags_out[r] | f_all) : f_all;
                 }
             }
@@ -1868,12 +1899,12 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
     }
 }
 
-static size_t smem_bytes(const DevScene &S, bool bodies, bool records) {
+static size_t smem_bytes(const DevScene &S, bool bodies, bool records, int blk) {
     size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + S.n_face;
     if (S.n_body <= SMEM_BODY_MAX) n += 4 * S.n_body;
     if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;
     return n * sizeof(float4) + WEIDEMAN_N * sizeof(float) + 16 +
-           (records ? sizeof(float) * (BLOCK / 32) * REC_CAP * REC_N * 32 : 0);
+           (records ? sizeof(float) * (blk / 32) * REC_CAP * REC_N * 32 : 0);
 }
 
 // Launch state of one evaluation: the counters (escalations, one work queue
@@ -1890,18 +1921,19 @@ static cudaError_t launch_one(const DevScene &S, const float *rx_soa, int n_rx, 
                               int accumulate, LaunchCtx &L) {
     if (L.n >= CTR_QUEUES) return cudaErrorInvalidValue;
     constexpr bool bodies = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
-    size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS);
+    constexpr int blk = blk_of(CLS, sizeof(T) == 4);
+    size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk);
     cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     // persistent grid: the blocks that fit on the device at once
     int dev = 0, nsm = 0, occ = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<T, PATHS, CLS>, BLOCK, sm)) != cudaSuccess) return e;
-    long long need = ((long long)n_rx + BLOCK - 1) / BLOCK;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<T, PATHS, CLS>, blk, sm)) != cudaSuccess) return e;
+    long long need = ((long long)n_rx + blk - 1) / blk;
     long long cap_blocks = (long long)nsm * (occ > 0 ? occ : 1);
     int grid = (int)(need < cap_blocks ? need : cap_blocks);
-    k_eval<T, PATHS, CLS><<<grid, BLOCK, sm, L.stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl,
+    k_eval<T, PATHS, CLS><<<grid, blk, sm, L.stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl,
                                                          accumulate, L.ctr, L.ctr + 1 + L.n);
     ++L.n;
     return cudaGetLastError();
