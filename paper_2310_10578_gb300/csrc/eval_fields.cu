@@ -1791,6 +1791,10 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
         s_fq = fq_in;
     }
     __syncthreads();
+    // the next class kernel (launched as a programmatic dependent) may start
+    // on SMs this grid leaves idle; it waits for this grid to complete before
+    // it first touches the outputs (griddepcontrol.wait below)
+    asm volatile("griddepcontrol.launch_dependents;");
 
     const Ctx &c = s_ctx;
     const FreqC &fq = s_fq;
@@ -1798,6 +1802,7 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
     constexpr int NW = blk_of(CLS, sizeof(T) == 4) / 32;
     const unsigned long long ntiles = ((unsigned long long)n_rx + 31ull) >> 5;
     if constexpr (PATHS) {
+        asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous class kernel's lists are complete
         // path lists: each warp takes tiles of 32 consecutive receivers from
         // the launch's queue and lists every candidate itself (codes in the
         // canonical order)
@@ -1864,6 +1869,10 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
             }
             s_fl[warp][lane] = fl;
             if (nesc && f0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
+            // the previous class kernel's fields and flags are complete (a
+            // no-op when this grid was not launched as a dependent, and after
+            // its first return)
+            asm volatile("griddepcontrol.wait;" ::: "memory");
             __syncthreads();
             // reduce the tile's NWT partials: part p writes the (frequency,
             // component) pairs j = p, p + NWT, ...
@@ -1933,10 +1942,22 @@ static cudaError_t launch_one(const DevScene &S, const float *rx_soa, int n_rx, 
     long long need = ((long long)n_rx + blk - 1) / blk;
     long long cap_blocks = (long long)nsm * (occ > 0 ? occ : 1);
     int grid = (int)(need < cap_blocks ? need : cap_blocks);
-    k_eval<T, PATHS, CLS><<<grid, blk, sm, L.stream>>>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl,
-                                                         accumulate, L.ctr, L.ctr + 1 + L.n);
+    // every launch after the first of the evaluation is a programmatic
+    // dependent of the one before: it may start while that one finishes
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(blk);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = L.stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = L.n > 0 ? 1 : 0;
+    e = cudaLaunchKernelEx(&cfg, k_eval<T, PATHS, CLS>, S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl,
+                           accumulate, L.ctr, L.ctr + 1 + L.n);
     ++L.n;
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // the class kernels of one frequency chunk, in order; the first writes the
