@@ -134,8 +134,9 @@ def _kernel_source_hash():
 
 
 def _profiled_traffic():
-    """DRAM bytes per launch of k_eval from the committed ncu summary, if it was
-    taken on the current kernel source; else None."""
+    """DRAM bytes of one evaluation (the three class kernels) from the
+    committed ncu summary, if it was taken on the current kernel source; else
+    None."""
     p = os.path.join(ROOT, "profiles", "k_eval_room20_traffic.txt")
     if not os.path.exists(p):
         return None
@@ -147,7 +148,7 @@ def _profiled_traffic():
     if kv.get("eval_fields.cu sha256[:16]") != _kernel_source_hash():
         return None
     try:
-        return float(kv["dram_bytes_per_launch_full_workload"])
+        return float(kv["dram_bytes_per_evaluation_full_workload"])
     except (KeyError, ValueError):
         return None
 
@@ -352,11 +353,16 @@ def main():
         sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
         peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12      # FP32 FFMA lanes x 2 x clock
         achieved = flops / (ms / 1e3) / 1e12
+        # the unit timed is one evaluation: the three class kernels, which
+        # overlap through programmatic dependent launch (their durations are
+        # not separable with events); per-kernel shares are in the ncu launch
+        # list under profiles/
         line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                             "frac": achieved / peak, "traffic": _profiled_traffic(),
                             "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived, FFMA)" %
                                           (props.multi_processor_count, sm_max),
-                            "work_per_launch_flops": flops}
+                            "kernel": "evaluation: k_eval<float, false, 1|2|4> (planar, body reflection, creeping)",
+                            "work_per_evaluation_flops": flops}
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
