@@ -122,6 +122,7 @@ struct rt_scene {
     int2 *d_face_rng = nullptr;
     int *d_face_tris = nullptr;
     double *d_freq = nullptr;
+    FreqC *d_fqc = nullptr;            // [RT_MAX_FREQS / NFC] per-chunk frequency constants
     float4 *d_img = nullptr;            // source images, see DevScene::img
     float4 *d_txb = nullptr;            // source-side body frames, see DevScene::txb
     unsigned long long *d_esc = nullptr;   // [CTR_N]: FP64-decided candidates, then one work queue per launch
@@ -162,7 +163,7 @@ static int fail(int code, const char *fmt, ...) {
 
 static void free_scene(rt_scene *s) {
     cudaFree(s->d_tri); cudaFree(s->d_aux); cudaFree(s->d_face32); cudaFree(s->d_body);
-    cudaFree(s->d_face64); cudaFree(s->d_face_rng); cudaFree(s->d_face_tris); cudaFree(s->d_freq);
+    cudaFree(s->d_face64); cudaFree(s->d_face_rng); cudaFree(s->d_face_tris); cudaFree(s->d_freq); cudaFree(s->d_fqc);
     cudaFree(s->d_esc); cudaFree(s->io_rx); cudaFree(s->io_e); cudaFree(s->io_fl); cudaFree(s->d_img); cudaFree(s->d_txb);
 }
 
@@ -314,6 +315,7 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
     CKS(cudaMalloc(&s->d_face_tris, sizeof(int) * ntr));
     CKS(cudaMalloc(&s->d_body, sizeof(float4) * 2 * nbd));
     CKS(cudaMalloc(&s->d_freq, sizeof(double) * RT_MAX_FREQS));
+    CKS(cudaMalloc(&s->d_fqc, sizeof(FreqC) * ((RT_MAX_FREQS + NFC - 1) / NFC)));
     CKS(cudaMalloc(&s->d_esc, sizeof(unsigned long long) * CTR_N));
     CKS(cudaMalloc(&s->d_img, sizeof(float4) * 2 * (nfc + nfc * nfc)));
     CKS(cudaMalloc(&s->d_txb, sizeof(float4) * 2 * nbd));
@@ -411,6 +413,25 @@ int rt_set_freqs(rt_scene *s, const double *f_hz, int n_f) {
         if (!(f_hz[i] > 0.0) || !isfinite(f_hz[i])) return fail(RT_ERR_ARG, "rt_set_freqs: bad frequency");
     s->freqs.assign(f_hz, f_hz + n_f);
     CK(cudaMemcpy(s->d_freq, f_hz, sizeof(double) * n_f, cudaMemcpyHostToDevice));
+    // per-chunk constants: k, (k/2)^{1/3}, 1/lambda (double-float), FP64 k and f/c
+    int nch = (n_f + NFC - 1) / NFC;
+    std::vector<FreqC> fq(nch);
+    for (int ch = 0; ch < nch; ++ch) {
+        FreqC &q = fq[ch];
+        q.nf = (n_f - ch * NFC) < NFC ? (n_f - ch * NFC) : NFC;
+        for (int f = 0; f < NFC; ++f) {
+            double fr = (f < q.nf) ? f_hz[ch * NFC + f] : f_hz[0];
+            double k = 2.0 * M_PI * fr / 299792458.0;
+            double il = fr / 299792458.0;
+            q.k[f] = (float)k;
+            q.kh[f] = (float)cbrt(k / 2.0);
+            q.il_hi[f] = (float)il;
+            q.il_lo[f] = (float)(il - (double)q.il_hi[f]);
+            q.kd[f] = k;
+            q.fc[f] = il;
+        }
+    }
+    CK(cudaMemcpy(s->d_fqc, fq.data(), sizeof(FreqC) * nch, cudaMemcpyHostToDevice));
     s->f_set = true;
     return RT_OK;
 }
@@ -431,6 +452,7 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec) 
     D.res32 = s->table->res32; D.res64 = s->table->res64;
     D.weid = s->table->weid; D.weid64 = s->table->weid64; D.weid_L = s->table->weid_L;
     D.freq = s->freqs.data();   // host pointer: read by the launcher only
+    D.fqc = s->d_fqc;
     D.img = s->d_img;
     D.txb = s->d_txb;
     memcpy(D.tx, s->tx, sizeof(D.tx));

@@ -29,7 +29,6 @@ namespace creep {
 enum { D_NO = 0, D_YES = 1, D_UNSURE = 2 };
 enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5 };
 
-constexpr int NFC = 4;                 // frequencies per launch (accumulators in registers)
 constexpr int BLOCK = 128;
 constexpr int SMEM_TRI_MAX = 256;
 constexpr int SMEM_BODY_MAX = 256;
@@ -47,13 +46,6 @@ __device__ __forceinline__ int decide(T m, T band, int tie) {
     return (m > T(0)) ? D_YES : ((m < T(0)) ? D_NO : tie);
 }
 
-// per-frequency constants of one launch
-struct FreqC {
-    float k[NFC], kh[NFC];       // wavenumber, (k/2)^{1/3}
-    float il_hi[NFC], il_lo[NFC];// 1/lambda as double-float
-    double kd[NFC], fc[NFC];     // FP64: wavenumber, f/c
-    int nf;
-};
 
 // scene view (pointers into shared or global memory)
 struct Ctx {
@@ -1248,13 +1240,22 @@ __device__ void field_creep(const Ctx &c, ACC &acc, const FreqC &fq, v3t<T> S, v
 // ---- path records (FP32): the frequency-independent factors of one path's
 // field, written by the geometry pass and turned into fields, frequency by
 // frequency, by the field pass; the two passes are separate loops so that
-// each one's code stays in the instruction cache.  14 floats, entry j of a
-// lane at rec[32 j]:
+// each one's code stays in the instruction cache, and so that the geometry
+// is reused for every frequency chunk.  14 floats, entry j of a lane at
+// rec[32 j]:
 //   0 Es, 1 Eh, 2-4 e1, 5-7 e2, 8 A (creeping: amplitude, negative for the
-//   ray through the caustic), 9 L' (transition distance), 10 rho_g^(1/3),
-//   11 cos(theta_i) (reflection) or t / rho_g (creeping), 12-13 path length.
+//   ray through the caustic), 9 L' (transition distance; its sign tells the
+//   kind: > 0 reflection, < 0 creeping), 10 rho_g^(1/3), 11 cos(theta_i)
+//   (reflection) or t / rho_g (creeping), 12-13 path length.
+// A candidate decided in FP64 whose field is deferred to the field passes
+// (several frequency chunks) has L' = 0 and entry 0 holds, as int bits,
+// kind | dir << 2 | body << 3 (kind REC_ESC_RB or REC_ESC_CREEP).
 constexpr int REC_N = 14;
-constexpr int REC_CAP = 5;             // records per lane between field passes
+enum { REC_ESC_RB = 2, REC_ESC_CREEP = 3 };
+__device__ __forceinline__ void rec_esc(float *r, int kind, int dir, int b) {
+    r[0] = __int_as_float(kind | (dir << 2) | (b << 3));
+    r[288] = 0.0f;
+}
 
 __device__ __forceinline__ void rec_put(float *r, float Es, float Eh, v3t<float> e1, v3t<float> e2, float A,
                                         float Lp, float rcb, float x, dfl len) {
@@ -1320,11 +1321,11 @@ __device__ __forceinline__ void creep_prep(const Ctx &c, float *r, v3t<float> S,
     v3t<float> e0 = src_pol(c, t1);
     float Es = (enable & RT_EN_CREEP_SOFT) ? dot3(e0, b1) : 0.0f;
     float Eh = (enable & RT_EN_CREEP_HARD) ? dot3(e0, g.n1) : 0.0f;
-    rec_put(r, Es, Eh, b2, g.n2, g.caus ? -g.amp : g.amp, g.sp * g.sq / (g.sp + g.sq), cbrtf(g.rho_g),
+    rec_put(r, Es, Eh, b2, g.n2, g.caus ? -g.amp : g.amp, -(g.sp * g.sq / (g.sp + g.sq)), cbrtf(g.rho_g),
             g.t / g.rho_g, len);
 }
 __device__ __forceinline__ void creep_apply(const Ctx &c, AccS<float> &acc, const FreqC &fq, const float *r) {
-    const float Es = r[0], Eh = r[32], Lp = r[288], rcb = r[320], tr = r[352];
+    const float Es = r[0], Eh = r[32], Lp = -r[288], rcb = r[320], tr = r[352];
     const float amp = fabsf(r[256]);
     const bool caus = r[256] < 0.0f;
     dfl len;
@@ -1477,9 +1478,6 @@ __device__ __noinline__ int esc_creep(const Ctx &c, int b, int dir, v3t<float> P
 enum { CLS_PLANAR = 1,        // direct ray and planar image reflections
        CLS_BODYREFL = 2,      // GO reflection off each curved body
        CLS_CREEP = 4 };       // creeping rays round each curved body
-#ifndef CREEP_SPLIT
-#define CREEP_SPLIT 3          // 1: one kernel; 2: planar | bodies; 3: planar | reflection | creeping
-#endif
 // Block shape.  The body classes run one block of 12 warps per SM: three
 // tiles at a time, four warps per tile; a block barrier between the geometry
 // pass and the field pass keeps all warps of the SM in the same pass, so the
@@ -1491,6 +1489,31 @@ constexpr int min_blocks(int cls, bool fp32) {
 }
 constexpr int WARPS_PER_TILE = 4;
 
+// Field pass over one lane's records for the frequency chunk fq; a candidate
+// decided in FP64 is re-evaluated in FP64 out of line.
+__device__ __noinline__ void apply_esc_record(const Ctx &c, AccS<float> &acc, const FreqC &fq, int tag, v3t<float> Pf,
+                                              double half_lambda_max, unsigned enable) {
+    const int kind = tag & 3, dir = (tag >> 2) & 1, b = tag >> 3;
+    Contrib ct;
+    int caus = 0;
+    int d = (kind == REC_ESC_RB) ? esc_rb(c, b, Pf, fq, true, &ct)
+                                 : esc_creep(c, b, dir, Pf, fq, true, half_lambda_max, enable, &ct, &caus);
+    if (d == D_YES) acc_add(acc, ct, fq.nf);
+}
+template <int CLS>
+__device__ __forceinline__ void apply_records(const Ctx &c, AccS<float> &acc, const FreqC &fq, const float *rec,
+                                              int nrec, v3t<float> Pf, double half_lambda_max, unsigned enable) {
+    constexpr bool RB = (CLS & CLS_BODYREFL) != 0, CP = (CLS & CLS_CREEP) != 0;
+#pragma unroll 1
+    for (int j = 0; j < nrec; ++j) {
+        const float *r = rec + j * REC_N * 32;
+        const float Lp = r[288];
+        if (RB && Lp > 0.0f) rb_apply(c, acc, fq, r);
+        else if (CP && Lp < 0.0f) creep_apply(c, acc, fq, r);
+        else apply_esc_record(c, acc, fq, __float_as_int(r[0]), Pf, half_lambda_max, enable);
+    }
+}
+
 // One receiver P = rx[r]: the paths of the classes in CLS among the
 // candidates of share `part` of `nparts` -- the direct ray to share 0, the
 // reflection off face i to share (1 + i) mod nparts, off faces (i, j) to
@@ -1501,8 +1524,10 @@ template <typename T, bool PATHS, int CLS>
 __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, unsigned enable, int max_order,
                                               const float *__restrict__ rx, int n_rx, int r,
                                               uint64_t *__restrict__ codes, int cap, double half_lambda_max,
-                                              int part, int nparts, AccS<T> acc, float *rec, uint32_t &fl, unsigned &nesc,
-                                              int &npath, int &nrec_out) {
+                                              int b_begin, int b_end, bool first_chunk, bool may_flush, int rcap,
+                                              int part, int nparts,
+                                              AccS<T> acc, float *rec, uint32_t &fl, unsigned &nesc, int &npath,
+                                              int &nrec_out) {
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     const bool fp32 = sizeof(T) == 4;
     const T band = fp32 ? T(c.band) : T(0);
@@ -1541,7 +1566,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                                         T((double)q0.z) + T((double)q1.x) - P.z);
             d = decide(m, band, D_YES);
             if (d == D_UNSURE) {
-                if (part == 0) escalated();              // every share takes it; one counts it
+                if (part == 0 && first_chunk) escalated();   // every share and chunk takes it; one counts it
                 else fl |= RT_FLAG_ESCALATED;
                 d = esc_inside(c, b, Pf);
             }
@@ -1623,33 +1648,26 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                 }
             }
         }
-        // ---- curved bodies
+        // ---- curved bodies b_begin .. b_end - 1 (this share: every nparts-th)
         if constexpr (BODIES) {
-            // FP32 fields: the geometry pass writes a record per valid path;
-            // the records left at the end are turned into fields by the
-            // caller's field pass, after a block barrier (here only when the
-            // buffer could overflow)
+            // FP32 fields: the geometry pass writes a record per valid path
+            // (candidates decided in FP64 as tagged records too); the caller
+            // turns them into fields, frequency chunk by frequency chunk, after
+            // a block barrier.  The body range is sized so that the records fit.
             constexpr bool RECS = (sizeof(T) == 4) && !PATHS;
             constexpr int PER = ((CLS & CLS_CREEP) ? 2 : 0) + ((CLS & CLS_BODYREFL) ? 1 : 0);
             int nrec = 0;
-            int b = part;
 #pragma unroll 1
-            for (;;) {
-                const bool done = b >= c.n_body;
+            for (int b = b_begin + part; b < b_end; b += nparts) {
                 if constexpr (RECS) {
-                    if (!done && nrec > REC_CAP - PER) {
-#pragma unroll 1
-                        for (int j = 0; j < nrec; ++j) {
-                            const float *r = rec + j * REC_N * 32;
-                            if constexpr (CLS == CLS_BODYREFL) rb_apply(c, acc, fq, r);
-                            else if constexpr (CLS == CLS_CREEP) creep_apply(c, acc, fq, r);
-                            else if (r[288] < 0.0f) creep_apply(c, acc, fq, r);   // creeping records: L' < 0
-                            else rb_apply(c, acc, fq, r);
-                        }
+                    // one frequency chunk: records that could overflow are turned
+                    // into fields here (with several chunks the caller sizes the
+                    // body range so that they cannot)
+                    if (may_flush && nrec > rcap - PER) {
+                        apply_records<CLS>(c, acc, fq, rec, nrec, Pf, half_lambda_max, enable);
                         nrec = 0;
                     }
                 }
-                if (done) break;
                 Frame<T> F;
                 body_frame(c, b, Sx, P, band, F);
                 if constexpr ((CLS & CLS_BODYREFL) != 0) {
@@ -1663,10 +1681,14 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                                 // receiver at a surface); the Fock bracket stays FP32
                                 escalated();
                                 Contrib ct;
-                                d = esc_rb(c, b, Pf, fq, !PATHS, &ct);
+                                // (with several frequency chunks its field is deferred to
+                                // the field passes as a tagged record)
+                                const bool defer = RECS && !may_flush;
+                                d = esc_rb(c, b, Pf, fq, !PATHS && !defer, &ct);
                                 if (d == D_YES) {
                                     emit(PT_RB, b, 0);
-                                    if (!PATHS) acc_add(acc, ct, nf);
+                                    if (defer) rec_esc(rec + (nrec++) * REC_N * 32, REC_ESC_RB, 0, b);
+                                    else if (!PATHS) acc_add(acc, ct, nf);
                                 }
                                 d = D_NO;
                             }
@@ -1674,8 +1696,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                         if (d == D_YES) {
                             emit(PT_RB, b, 0);
                             if constexpr (RECS) {
-                                rb_prep(c, rec + nrec * REC_N * 32, Sx, g, g.Lf);
-                                ++nrec;
+                                rb_prep(c, rec + (nrec++) * REC_N * 32, Sx, g, g.Lf);
                             } else if constexpr (!PATHS) {
                                 field_body_refl<T>(c, acc, fq, Sx, P, g, ladd(seglen(Sx, g.Q1), seglen(g.Q1, P)));
                             }
@@ -1700,11 +1721,14 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                                     escalated();
                                     Contrib ct;
                                     int caus = 0;
-                                    d = esc_creep(c, b, dir, Pf, fq, !PATHS, half_lambda_max, enable, &ct, &caus);
+                                    const bool defer = RECS && !may_flush;
+                                    d = esc_creep(c, b, dir, Pf, fq, !PATHS && !defer, half_lambda_max, enable, &ct,
+                                                  &caus);
                                     if (d == D_YES) {
                                         emit(dir == 0 ? PT_CP : PT_CM, b, 0);
                                         if (caus) fl |= RT_FLAG_CAUSTIC;
-                                        if (!PATHS) acc_add(acc, ct, nf);
+                                        if (defer) rec_esc(rec + (nrec++) * REC_N * 32, REC_ESC_CREEP, dir, b);
+                                        else if (!PATHS) acc_add(acc, ct, nf);
                                     }
                                     continue;
                                 }
@@ -1716,29 +1740,24 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                                 if (!(g.dperp > T(0.0))) continue;        // exactly on the axis: no finite ray field
                             }
                             if constexpr (RECS) {
-                                float *r = rec + nrec * REC_N * 32;
-                                creep_prep(c, r, Sx, P, g, creep_len(c, b, Sx, P, g, F), enable);
-                                if constexpr (CLS != CLS_CREEP) r[288] = -r[288];   // mark as creeping
-                                ++nrec;
+                                creep_prep(c, rec + (nrec++) * REC_N * 32, Sx, P, g, creep_len(c, b, Sx, P, g, F), enable);
                             } else if constexpr (!PATHS) {
                                 field_creep<T>(c, acc, fq, Sx, P, g, creep_len(c, b, Sx, P, g, F), enable);
                             }
                         }
                     }
                 }
-                b += nparts;
             }
             nrec_out = nrec;
         }
     }
 }
 
-
 template <typename T, bool PATHS, int CLS>
 __global__ void __launch_bounds__(blk_of(CLS, sizeof(T) == 4), min_blocks(CLS, sizeof(T) == 4))
 k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e_out, uint32_t *__restrict__ flags_out,
-       uint64_t *__restrict__ codes, int32_t *__restrict__ counts, int cap, int f0, FreqC fq_in, double half_lambda_max,
-       int accumulate, unsigned long long *esc_counter, unsigned long long *queue) {
+       uint64_t *__restrict__ codes, int32_t *__restrict__ counts, int cap, int ch0, int nch, int rcap,
+       double half_lambda_max, int accumulate, unsigned long long *esc_counter, unsigned long long *queue) {
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     extern __shared__ float4 smem[];
     __shared__ Ctx s_ctx;
@@ -1788,7 +1807,7 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
         c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
         c.img = S.img;
         c.txb = body_sm ? s_txb : S.txb;
-        s_fq = fq_in;
+        s_fq = S.fqc[ch0];
     }
     __syncthreads();
     // the next class kernel (launched as a programmatic dependent) may start
@@ -1819,7 +1838,7 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
                 int npath = accumulate ? counts[r] : 0;
                 int nrec;
                 eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap, half_lambda_max,
-                                             0, 1, acc, nullptr, fl, nesc, npath, nrec);
+                                             0, c.n_body, true, false, 0, 0, 1, acc, nullptr, fl, nesc, npath, nrec);
                 counts[r] = npath;
                 if (flags_out) flags_out[r] = accumulate ? (flags_out[r] | fl) : fl;
                 if (nesc) atomicAdd(esc_counter, (unsigned long long)nesc);
@@ -1832,11 +1851,18 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
         // partial fields are summed in shared memory in warp order, so the
         // result does not depend on timing.  Sharing a tile among warps
         // shortens it, so the last tiles of the launch leave little of the GPU
-        // idle.  Body classes: all warps finish the geometry pass (records)
-        // before any starts the field pass.
+        // idle.  Body classes (FP32): the bodies go in chunks sized for the
+        // record buffer; per chunk all warps finish the geometry pass before
+        // any starts the field pass, which runs once per frequency chunk on
+        // the same records and adds its rows to the outputs.
         constexpr int NWT = BODIES ? WARPS_PER_TILE : NW;
         constexpr int TPB = NW / NWT;
         constexpr bool RECS = BODIES && sizeof(T) == 4;
+        constexpr int PER = ((CLS & CLS_CREEP) ? 2 : 0) + ((CLS & CLS_BODYREFL) ? 1 : 0);
+        const int n_b = BODIES ? c.n_body : 0;
+        // bodies per geometry pass: all of them with one frequency chunk (full
+        // record buffers are flushed on the way), else as many as the buffer holds
+        const int bc = (RECS && nch > 1) ? NWT * (rcap / PER) : (n_b > 0 ? n_b : 1);
         const int grp = warp / NWT, part = warp % NWT;
         __shared__ T s_part[NW][NFC * 6][32];
         __shared__ uint32_t s_fl[NW][32];
@@ -1849,71 +1875,80 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
             const int r = (int)(t * 32ull) + lane;
             const bool rok = t < ntiles && r < n_rx;
             AccS<T> acc{&s_part[warp][0][lane]};     // the warp's partial sums, summed in place
-            float *rec = s_rec + warp * (REC_CAP * REC_N * 32) + lane;
-            uint32_t fl = 0;
-            unsigned nesc = 0;
-            int npath = 0, nrec = 0;
-            if (rok)
-                eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap, half_lambda_max,
-                                             part, NWT, acc, rec, fl, nesc, npath, nrec);
-            if constexpr (RECS) {
-                __syncthreads();                      // every warp has done its geometry pass
+            float *rec = s_rec + warp * (rcap * REC_N * 32) + lane;
 #pragma unroll 1
-                for (int j = 0; j < nrec; ++j) {
-                    const float *rj = rec + j * REC_N * 32;
-                    if constexpr (CLS == CLS_BODYREFL) rb_apply(c, acc, fq, rj);
-                    else if constexpr (CLS == CLS_CREEP) creep_apply(c, acc, fq, rj);
-                    else if (rj[288] < 0.0f) creep_apply(c, acc, fq, rj);
-                    else rb_apply(c, acc, fq, rj);
-                }
-            }
-            s_fl[warp][lane] = fl;
-            if (nesc && f0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
-            // the previous class kernel's fields and flags are complete (a
-            // no-op when this grid was not launched as a dependent, and after
-            // its first return)
-            asm volatile("griddepcontrol.wait;" ::: "memory");
-            __syncthreads();
-            // reduce the tile's NWT partials: part p writes the (frequency,
-            // component) pairs j = p, p + NWT, ...
-            if (rok) {
-                const int w0 = grp * NWT;
-                for (int j = part; j < fq.nf * 3; j += NWT) {
-                    T re = s_part[w0][2 * j][lane], im = s_part[w0][2 * j + 1][lane];
-#pragma unroll
-                    for (int w = 1; w < NWT; ++w) {
-                        re = re + s_part[w0 + w][2 * j][lane];
-                        im = im + s_part[w0 + w][2 * j + 1][lane];
+            for (int b0 = 0; b0 < (n_b > 0 ? n_b : 1); b0 += bc) {
+                uint32_t fl = 0;
+                unsigned nesc = 0;
+                int npath = 0, nrec = 0;
+                if (rok)
+                    eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap,
+                                                 half_lambda_max, b0, min(b0 + bc, n_b), b0 == 0, nch == 1, rcap, part,
+                                                 NWT, acc, rec, fl, nesc, npath, nrec);
+                s_fl[warp][lane] = fl;
+                if (nesc && ch0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
+#pragma unroll 1
+                for (int ch = ch0; ch < ch0 + nch; ++ch) {
+                    if constexpr (RECS) {
+                        __syncthreads();              // geometry pass / previous reduction done
+                        if (nch > 1) {                // (one chunk: staged at the start)
+                            if (threadIdx.x == 0) s_fq = S.fqc[ch];
+                            __syncthreads();
+                        }
+                        if (rok) {
+                            if (ch > ch0) acc_zero(acc);      // the geometry pass zeroed it for the first chunk
+                            apply_records<CLS>(c, acc, fq, rec, nrec, mk3(rx[r], rx[n_rx + r], rx[2 * n_rx + r]),
+                                          half_lambda_max, S.enable);
+                        }
                     }
-                    size_t idx = ((size_t)(f0 + j / 3) * 3 + (j % 3)) * n_rx + r;
-                    float2 v;
-                    v.x = to_float(re);
-                    v.y = to_float(im);
-                    if (accumulate) {
-                        float2 o = reinterpret_cast<float2 *>(e_out)[idx];
-                        v.x += o.x;
-                        v.y += o.y;
-                    }
-                    reinterpret_cast<float2 *>(e_out)[idx] = v;
-                }
-                if (part == 0 && flags_out && f0 == 0) {
-                    uint32_t f_all = 0;
+                    // the previous class kernel's fields and flags are complete (a
+                    // no-op when this grid was not launched as a dependent, and
+                    // after its first return)
+                    asm volatile("griddepcontrol.wait;" ::: "memory");
+                    __syncthreads();
+                    // reduce the tile's NWT partials: part p writes the
+                    // (frequency, component) pairs j = p, p + NWT, ... of chunk ch
+                    if (rok) {
+                        const int w0 = grp * NWT, f0 = ch * NFC;
+                        const bool add = accumulate || b0 > 0;
+                        for (int j = part; j < fq.nf * 3; j += NWT) {
+                            T re = s_part[w0][2 * j][lane], im = s_part[w0][2 * j + 1][lane];
 #pragma unroll
-                    for (int w = 0; w < NWT; ++w) f_all |= s_fl[w0 + w][lane];
-                    flags_out[r] = accumulate ? (flags_out[r] | f_all) : f_all;
+                            for (int w = 1; w < NWT; ++w) {
+                                re = re + s_part[w0 + w][2 * j][lane];
+                                im = im + s_part[w0 + w][2 * j + 1][lane];
+                            }
+                            size_t idx = ((size_t)(f0 + j / 3) * 3 + (j % 3)) * n_rx + r;
+                            float2 v;
+                            v.x = to_float(re);
+                            v.y = to_float(im);
+                            if (add) {
+                                float2 o = reinterpret_cast<float2 *>(e_out)[idx];
+                                v.x += o.x;
+                                v.y += o.y;
+                            }
+                            reinterpret_cast<float2 *>(e_out)[idx] = v;
+                        }
+                        if (ch == 0 && part == 0 && flags_out) {
+                            uint32_t f_all = 0;
+#pragma unroll
+                            for (int w = 0; w < NWT; ++w) f_all |= s_fl[w0 + w][lane];
+                            flags_out[r] = add ? (flags_out[r] | f_all) : f_all;
+                        }
+                    }
                 }
+                __syncthreads();                      // before the next geometry pass or tile
             }
-            __syncthreads();
         }
     }
 }
 
-static size_t smem_bytes(const DevScene &S, bool bodies, bool records, int blk) {
+static size_t smem_bytes(const DevScene &S, bool bodies, bool records, int blk, int rcap) {
     size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + S.n_face;
     if (S.n_body <= SMEM_BODY_MAX) n += 4 * S.n_body;
     if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;
     return n * sizeof(float4) + WEIDEMAN_N * sizeof(float) + 16 +
-           (records ? sizeof(float) * (blk / 32) * REC_CAP * REC_N * 32 : 0);
+           (records ? sizeof(float) * (blk / 32) * rcap * REC_N * 32 : 0);
 }
 
 // Launch state of one evaluation: the counters (escalations, one work queue
@@ -1926,12 +1961,15 @@ struct LaunchCtx {
 
 template <typename T, bool PATHS, int CLS>
 static cudaError_t launch_one(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
-                              uint64_t *codes, int32_t *counts, int cap, int f0, const FreqC &fq, double hl,
+                              uint64_t *codes, int32_t *counts, int cap, int ch0, int nch, double hl,
                               int accumulate, LaunchCtx &L) {
     if (L.n >= CTR_QUEUES) return cudaErrorInvalidValue;
     constexpr bool bodies = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     constexpr int blk = blk_of(CLS, sizeof(T) == 4);
-    size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk);
+    // records per lane: one frequency chunk flushes full buffers on the way
+    // (5 is enough); several chunks size the body range by the capacity
+    const int rcap = (nch > 1) ? 6 : 5;
+    size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk, rcap);
     cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     // persistent grid: the blocks that fit on the device at once
@@ -1954,36 +1992,32 @@ static cudaError_t launch_one(const DevScene &S, const float *rx_soa, int n_rx, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = L.n > 0 ? 1 : 0;
-    e = cudaLaunchKernelEx(&cfg, k_eval<T, PATHS, CLS>, S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl,
-                           accumulate, L.ctr, L.ctr + 1 + L.n);
+    e = cudaLaunchKernelEx(&cfg, k_eval<T, PATHS, CLS>, S, rx_soa, n_rx, e_out, flags, codes, counts, cap, ch0, nch,
+                           rcap, hl, accumulate, L.ctr, L.ctr + 1 + L.n);
     ++L.n;
     return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-// the class kernels of one frequency chunk, in order; the first writes the
-// outputs, the others add to them
+// The class kernels of one evaluation.  Path lists and FP64 fields: the
+// three classes per frequency chunk.  FP32 fields: the planar kernel per
+// chunk, then each body kernel once for all chunks (its geometry is reused).
+// The first launch writes the outputs, the later ones add to them.
 template <typename T, bool PATHS>
-static cudaError_t launch_classes(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
-                                  uint64_t *codes, int32_t *counts, int cap, int f0, const FreqC &fq, double hl,
-                                  LaunchCtx &L) {
-    cudaError_t e;
-#if CREEP_SPLIT == 1
-    e = launch_one<T, PATHS, CLS_PLANAR | CLS_BODYREFL | CLS_CREEP>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap,
-                                                                     f0, fq, hl, 0, L);
-#elif CREEP_SPLIT == 2
-    e = launch_one<T, PATHS, CLS_PLANAR>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, 0, L);
-    if (e == cudaSuccess)
-        e = launch_one<T, PATHS, CLS_BODYREFL | CLS_CREEP>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, 1,
-                                                           L);
-#else
-    e = launch_one<T, PATHS, CLS_PLANAR>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, 0, L);
-    if (e == cudaSuccess)
-        e = launch_one<T, PATHS, CLS_BODYREFL>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, 1,
-                                               L);
-    if (e == cudaSuccess)
-        e = launch_one<T, PATHS, CLS_CREEP>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, 1,
-                                            L);
-#endif
+static cudaError_t launch_all(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
+                              uint64_t *codes, int32_t *counts, int cap, int nchunks, double hl, LaunchCtx &L) {
+    cudaError_t e = cudaSuccess;
+    const bool chunked_bodies = PATHS || sizeof(T) != 4;
+    for (int ch = 0; ch < nchunks && e == cudaSuccess; ++ch) {
+        e = launch_one<T, PATHS, CLS_PLANAR>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, ch, 1, hl, 0, L);
+        if (chunked_bodies && e == cudaSuccess)
+            e = launch_one<T, PATHS, CLS_BODYREFL>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, ch, 1, hl, 1, L);
+        if (chunked_bodies && e == cudaSuccess)
+            e = launch_one<T, PATHS, CLS_CREEP>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, ch, 1, hl, 1, L);
+    }
+    if (!chunked_bodies && e == cudaSuccess)
+        e = launch_one<T, PATHS, CLS_BODYREFL>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, 0, nchunks, hl, 1, L);
+    if (!chunked_bodies && e == cudaSuccess)
+        e = launch_one<T, PATHS, CLS_CREEP>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, 0, nchunks, hl, 1, L);
     return e;
 }
 
@@ -1998,36 +2032,19 @@ int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, 
         double lam = 299792458.0 / S.freq[f];
         if (lam / 2.0 > hl) hl = lam / 2.0;
     }
-    bool paths = codes != nullptr;
-    int nchunks = paths ? 1 : (S.n_f + NFC - 1) / NFC;
-    for (int ch = 0; ch < nchunks; ++ch) {
-        FreqC fq;
-        fq.nf = paths ? 0 : ((S.n_f - ch * NFC) < NFC ? (S.n_f - ch * NFC) : NFC);
-        for (int f = 0; f < NFC; ++f) {
-            double fr = (f < fq.nf) ? S.freq[ch * NFC + f] : S.freq[0];
-            double k = 2.0 * M_PI * fr / 299792458.0;
-            double il = fr / 299792458.0;
-            fq.k[f] = (float)k;
-            fq.kh[f] = (float)cbrt(k / 2.0);
-            fq.il_hi[f] = (float)il;
-            fq.il_lo[f] = (float)(il - (double)fq.il_hi[f]);
-            fq.kd[f] = k;
-            fq.fc[f] = il;
-        }
-        int f0 = ch * NFC;
-        cudaError_t e;
-        if (precision == RT_PREC_FP64) {
-            e = paths ? launch_classes<dx, true>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, L)
-                      : launch_classes<dx, false>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, L);
-        } else {
-            e = paths ? launch_classes<float, true>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, L)
-                      : launch_classes<float, false>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, f0, fq, hl, L);
-        }
-        if (e != cudaSuccess) {
-            set_error(std::string("k_eval launch: ") + cudaGetErrorString(e));
-            return RT_ERR_CUDA;
-        }
-        *n_launches = L.n;
+    const bool paths = codes != nullptr;
+    const int nchunks = paths ? 1 : (S.n_f + NFC - 1) / NFC;
+    cudaError_t e;
+    if (precision == RT_PREC_FP64)
+        e = paths ? launch_all<dx, true>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, nchunks, hl, L)
+                  : launch_all<dx, false>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, nchunks, hl, L);
+    else
+        e = paths ? launch_all<float, true>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, nchunks, hl, L)
+                  : launch_all<float, false>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, nchunks, hl, L);
+    *n_launches = L.n;
+    if (e != cudaSuccess) {
+        set_error(std::string("k_eval launch: ") + cudaGetErrorString(e));
+        return RT_ERR_CUDA;
     }
     return RT_OK;
 }

@@ -42,6 +42,16 @@ struct FaceHost {
     int first, count;          // range in the face -> triangle index list
 };
 
+// Frequencies are evaluated in chunks of NFC (one accumulator set each).
+constexpr int NFC = 4;
+// Per-chunk frequency constants (built on the host at rt_set_freqs).
+struct FreqC {
+    float k[NFC], kh[NFC];       // wavenumber, (k/2)^{1/3}
+    float il_hi[NFC], il_lo[NFC];// 1/lambda as double-float
+    double kd[NFC], fc[NFC];     // FP64: wavenumber, f/c
+    int nf;                      // frequencies in this chunk (0 for path lists)
+};
+
 // Device-side scene description passed to the field kernel by value.
 struct DevScene {
     int n_tri, n_face, n_body, n_f;
@@ -65,6 +75,7 @@ struct DevScene {
     const float4 *txb;         // [n_body][2] per transmitter, FP64-computed: (u, |S - c|), (beta_s, sqrt(|S-c|^2 - a^2) hi, lo,
                                // lateral paths possible ? 1 : 0); cylinders use horizontal distances
     const double *freq;        // [n_f] Hz (host copy, read by the launcher)
+    const FreqC *fqc;          // [ceil(n_f / NFC)] per-chunk frequency constants (device)
     float tx[3], pol[3];
     float band_len;            // FP32 decision band (m)
     int max_order;
