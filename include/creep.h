@@ -205,6 +205,75 @@ int rt_evaluate_host_noalloc(rt_scene *scene, const float *rx_soa, int n_rx, flo
 int rt_paths(rt_scene *scene, const float *rx_soa, int n_rx, uint64_t *codes,
              int32_t *counts, int cap, uint32_t *flags, const rt_options *opt, void *stream);
 
+/*
+ * Batched frames: the evaluation of rt_evaluate (Eqs. 1-4) for n_frames
+ * frames of one scene at once -- the dynamic-scene use of Sec. III (people
+ * moving through a fixed room, one frame per time step).  Every frame shares
+ * the scene's triangles, transmitter and polarisation; each has its own
+ * curved bodies (which replace the scene's own bodies), its own n_f
+ * frequencies (the same count in every frame) and its own number of
+ * receivers.  All frames' receivers are one work queue of one launch per
+ * path class, so uneven frames keep the GPU busy.
+ *
+ * Layout (rx_offset(f) = n_rx[0] + ... + n_rx[f - 1]):
+ *   rx_soa  device float: frame f's [3][n_rx[f]] block (x row, y row, z
+ *           row) at rx_soa + 3 rx_offset(f).
+ *   e_out   device float: frame f's [n_f][3][n_rx[f]][2] block (as
+ *           rt_evaluate) at e_out + 6 n_f rx_offset(f); fully overwritten.
+ *   flags   device uint32: frame f's [n_rx[f]] at flags + rx_offset(f), or NULL.
+ * A frame's fields equal those of rt_evaluate on a scene with the same
+ * triangles and that frame's bodies, transmitter and frequencies.
+ */
+typedef struct rt_batch rt_batch;
+
+/*
+ * Create a batch of n_frames >= 1 frames on scene (which must outlive it):
+ * n_rx host int32 [n_frames] (>= 0; zero is allowed), n_f in
+ * [1, RT_MAX_FREQS] frequencies per frame, and max_body, the most bodies any
+ * frame will hold (<= RT_MAX_BODIES).  Device memory for the frames' data
+ * is allocated here.  Errors: RT_ERR_ARG, RT_ERR_OVERFLOW, RT_ERR_CUDA.
+ */
+int rt_batch_create(rt_scene *scene, int n_frames, const int32_t *n_rx, int n_f, int max_body,
+                    rt_batch **out);
+
+/* Free a batch (NULL is a no-op). */
+void rt_batch_destroy(rt_batch *batch);
+
+/*
+ * Set frame `frame`: its bodies (host [n_body], n_body <= max_body, checked
+ * as in rt_scene_create, and the scene's transmitter must lie outside them)
+ * and its frequencies (host double [n_f], Hz).  Copies to the device and
+ * synchronises; do not call while an evaluation of this batch is in flight.
+ * The scene's transmitter must be set first; after a later rt_set_tx every
+ * frame must be set again (RT_ERR_STATE otherwise).  A captured graph
+ * (rt_batch_capture) reads the frames when it runs, so frames set between
+ * replays take effect without a new capture.
+ */
+int rt_batch_set_frame(rt_batch *batch, int frame, const rt_body *bodies, int n_body,
+                       const double *f_hz);
+
+/*
+ * Evaluate every frame (layout above) on `stream`; returns after the launch.
+ * opt as for rt_evaluate.  RT_ERR_STATE if a frame has not been set.
+ */
+int rt_batch_evaluate(rt_batch *batch, const float *rx_soa, float *e_out, uint32_t *flags,
+                      const rt_options *opt, void *stream);
+
+/*
+ * Capture rt_batch_evaluate(batch, rx_soa, e_out, flags, opt, stream) into a
+ * CUDA graph kept with the batch (replacing an earlier one); nothing runs.
+ * stream must not be the legacy default stream (NULL).  The buffers must
+ * stay valid for every replay.
+ */
+int rt_batch_capture(rt_batch *batch, const float *rx_soa, float *e_out, uint32_t *flags,
+                     const rt_options *opt, void *stream);
+
+/* Launch the captured graph on `stream` (RT_ERR_STATE if none). */
+int rt_batch_replay(rt_batch *batch, void *stream);
+
+/* Counters of the batch's last evaluation or replay (synchronises its stream). */
+int rt_batch_get_stats(rt_batch *batch, rt_stats *out);
+
 /* Counters of the last rt_evaluate / rt_paths on this scene (synchronises its stream). */
 int rt_get_stats(rt_scene *scene, rt_stats *out);
 

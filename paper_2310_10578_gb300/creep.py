@@ -23,7 +23,8 @@ FOCK_NRES = 8
 
 EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "rt_evaluate",
            "rt_evaluate_host", "rt_evaluate_host_noalloc", "rt_paths", "rt_get_stats", "rt_fock_table",
-           "rt_last_error")
+           "rt_last_error", "rt_batch_create", "rt_batch_destroy", "rt_batch_set_frame", "rt_batch_evaluate",
+           "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats")
 RT_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -72,6 +73,14 @@ def load(build_if_missing=True):
     lib.rt_get_stats.argtypes = [P, P]
     lib.rt_fock_table.argtypes = [P, P, P, P, P, P]
     lib.rt_last_error.restype = ctypes.c_char_p
+    lib.rt_batch_create.argtypes = [P, I, P, I, I, ctypes.POINTER(P)]
+    lib.rt_batch_destroy.argtypes = [P]
+    lib.rt_batch_destroy.restype = None
+    lib.rt_batch_set_frame.argtypes = [P, I, P, I, P]
+    lib.rt_batch_evaluate.argtypes = [P, P, P, P, P, P]
+    lib.rt_batch_capture.argtypes = [P, P, P, P, P, P]
+    lib.rt_batch_replay.argtypes = [P, P]
+    lib.rt_batch_get_stats.argtypes = [P, P]
     _lib = lib
     return lib
 
@@ -100,6 +109,16 @@ def _stream_handle(stream):
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _bodies_arr(bodies):
+    bodies = np.asarray(bodies, dtype=np.float64).reshape(-1, 6)
+    arr = (rt_body * max(1, len(bodies)))()
+    for i, b in enumerate(bodies):
+        arr[i].type = int(b[0])
+        arr[i].c[0], arr[i].c[1], arr[i].c[2] = float(b[1]), float(b[2]), float(b[3])
+        arr[i].a, arr[i].h = float(b[4]), float(b[5])
+    return arr, len(bodies)
+
+
 class Scene:
     """A scene on the current CUDA device: planar faces (triangles grouped into
     coplanar reflecting faces) and convex PEC bodies (spheres, vertical
@@ -110,15 +129,10 @@ class Scene:
         tri = np.ascontiguousarray(np.asarray(tri, dtype=np.float32).reshape(-1, 9))
         n_tri = tri.shape[0]
         tf = None if tri_face is None else np.ascontiguousarray(np.asarray(tri_face, dtype=np.int32))
-        bodies = np.asarray(bodies, dtype=np.float64).reshape(-1, 6)
-        arr = (rt_body * max(1, len(bodies)))()
-        for i, b in enumerate(bodies):
-            arr[i].type = int(b[0])
-            arr[i].c[0], arr[i].c[1], arr[i].c[2] = float(b[1]), float(b[2]), float(b[3])
-            arr[i].a, arr[i].h = float(b[4]), float(b[5])
+        arr, nb = _bodies_arr(bodies)
         self._h = ctypes.c_void_p()
         _check(lib.rt_scene_create(_ptr(tri) if n_tri else None, _ptr(tf), n_tri, ctypes.cast(arr, ctypes.c_void_p),
-                                   len(bodies), ctypes.byref(self._h)))
+                                   nb, ctypes.byref(self._h)))
         self.n_f = 0
 
     @classmethod
@@ -198,6 +212,82 @@ class Scene:
     def stats(self):
         st = rt_stats()
         _check(_lib.rt_get_stats(self._h, ctypes.byref(st)))
+        return {"escalated_candidates": int(st.escalated_candidates), "kernel_launches": int(st.kernel_launches)}
+
+
+class Batch:
+    """Frames of one scene evaluated together (rt_batch_*): each frame has its
+    own bodies, n_f frequencies and receivers; the triangles and transmitter
+    are the scene's.  Receivers of all frames are one [3, sum n_rx] tensor of
+    per-frame [3, n_rx[f]] blocks (see rx_pack); fields one flat tensor of
+    per-frame [n_f, 3, n_rx[f], 2] blocks (see frame_fields)."""
+
+    def __init__(self, scene, n_rx, n_f, max_body):
+        self.scene = scene                  # keeps the scene alive
+        self.n_rx = [int(n) for n in n_rx]
+        self.n_f = int(n_f)
+        self.rx_off = np.concatenate([[0], np.cumsum(self.n_rx)]).astype(np.int64)
+        n = np.ascontiguousarray(np.asarray(self.n_rx, dtype=np.int32))
+        self._h = ctypes.c_void_p()
+        _check(_lib.rt_batch_create(scene._h, len(self.n_rx), _ptr(n), self.n_f, int(max_body),
+                                    ctypes.byref(self._h)))
+
+    @property
+    def n_frames(self):
+        return len(self.n_rx)
+
+    @property
+    def total_rx(self):
+        return int(self.rx_off[-1])
+
+    def close(self):
+        if self._h:
+            _lib.rt_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_frame(self, frame, bodies, freqs):
+        arr, nb = _bodies_arr(bodies)
+        f = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64).reshape(-1))
+        if len(f) != self.n_f:
+            raise ValueError("frame %d: %d frequencies, the batch has %d" % (frame, len(f), self.n_f))
+        _check(_lib.rt_batch_set_frame(self._h, int(frame), ctypes.cast(arr, ctypes.c_void_p), nb, _ptr(f)))
+
+    def rx_pack(self, rx_per_frame):
+        """Per-frame [3, n_rx[f]] float32 arrays -> one flat float32 array."""
+        return np.concatenate([np.ascontiguousarray(r, dtype=np.float32).reshape(3, n).ravel()
+                               for r, n in zip(rx_per_frame, self.n_rx)] or [np.zeros(0, np.float32)])
+
+    def frame_fields(self, out, frame):
+        """View of frame's [n_f, 3, n_rx, 2] block in the flat output."""
+        a, n = int(self.rx_off[frame]), self.n_rx[frame]
+        return out[6 * self.n_f * a: 6 * self.n_f * (a + n)].reshape(self.n_f, 3, n, 2)
+
+    def evaluate(self, rx_flat, out=None, flags=None, opts=None, stream=None):
+        import torch
+        assert rx_flat.is_cuda and rx_flat.dtype == torch.float32 and rx_flat.is_contiguous()
+        assert rx_flat.numel() == 3 * self.total_rx
+        if out is None:
+            out = torch.empty(6 * self.n_f * self.total_rx, dtype=torch.float32, device=rx_flat.device)
+        _check(_lib.rt_batch_evaluate(self._h, _ptr(rx_flat), _ptr(out), _ptr(flags),
+                                      ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
+        return out
+
+    def capture(self, rx_flat, out, flags=None, opts=None, stream=None):
+        _check(_lib.rt_batch_capture(self._h, _ptr(rx_flat), _ptr(out), _ptr(flags),
+                                     ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
+
+    def replay(self, stream=None):
+        _check(_lib.rt_batch_replay(self._h, _stream_handle(stream)))
+
+    def stats(self):
+        st = rt_stats()
+        _check(_lib.rt_batch_get_stats(self._h, ctypes.byref(st)))
         return {"escalated_candidates": int(st.escalated_candidates), "kernel_launches": int(st.kernel_launches)}
 
 

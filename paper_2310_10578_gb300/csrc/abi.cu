@@ -129,6 +129,8 @@ struct rt_scene {
     DevTable *table = nullptr;
     // state
     bool tx_set = false, f_set = false;
+    unsigned tx_version = 0;            // incremented by every rt_set_tx
+    double tri_scale = 1.0;             // largest |coordinate| of the triangles (at least 1)
     float tx[3], pol[3];
     std::vector<double> freqs;
     float band_len = 0.f;
@@ -192,6 +194,86 @@ static bool bodies_overlap(const rt_body &A, const rt_body &B) {
     double dh = sqrt((A.c[0] - B.c[0]) * (A.c[0] - B.c[0]) + (A.c[1] - B.c[1]) * (A.c[1] - B.c[1]));
     bool zo = !(A.c[2] + A.h < B.c[2] || B.c[2] + B.h < A.c[2]);
     return zo && dh < (double)A.a + B.a;
+}
+
+// Check bodies (type, finite positive sizes, no two overlapping) and write
+// their device form hb[2 n_body]; scale grows to cover them.
+static int prep_bodies(const rt_body *bodies, int n_body, std::vector<float4> &hb, double &scale) {
+    hb.assign(2 * (size_t)(n_body > 0 ? n_body : 1), make_float4(0.f, 0.f, 0.f, 0.f));
+    for (int b = 0; b < n_body; ++b) {
+        const rt_body &B = bodies[b];
+        if (B.type != RT_BODY_SPHERE && B.type != RT_BODY_CYLINDER) return fail(RT_ERR_ARG, "body %d: bad type", b);
+        if (!fin32(B.c[0]) || !fin32(B.c[1]) || !fin32(B.c[2]) || !fin32(B.a) || !fin32(B.h) || !(B.a > 0.f) ||
+            (B.type == RT_BODY_CYLINDER && !(B.h > 0.f)))
+            return fail(RT_ERR_ARG, "body %d: non-finite or non-positive size", b);
+        for (int q = 0; q < b; ++q)
+            if (bodies_overlap(bodies[q], B)) return fail(RT_ERR_GEOM, "bodies %d and %d overlap", q, b);
+        hb[2 * b] = make_float4(B.c[0], B.c[1], B.c[2], B.a);
+        hb[2 * b + 1] = make_float4(B.type == RT_BODY_CYLINDER ? B.h : 0.f, (float)B.type, 0.f, 0.f);
+        for (int k = 0; k < 3; ++k) scale = fmax(scale, fabs((double)B.c[k]) + B.a + B.h);
+    }
+    return RT_OK;
+}
+
+// FP32 decision band: bounds the FP32 error of a margin (metres) built from
+// a few dozen roundings of coordinates of magnitude <= scale: 32 ulp.
+static float band_of(double scale) { return (float)(scale * 32.0 * 5.96e-8); }
+
+// The transmitter p must lie outside every body.
+static int check_tx_outside(const double p[3], const rt_body *bodies, int n_body, const char *who) {
+    for (int b = 0; b < n_body; ++b)
+        if (dist_to_body(p, bodies[b]) <= 0.0) return fail(RT_ERR_GEOM, "%s: transmitter inside or on body %d", who, b);
+    return RT_OK;
+}
+
+// Per body, the source side of the (S, c, P) frame: the same for every
+// receiver (FP64, rounded once).  txb[2 n_body].
+static void prep_txb(const double p[3], const rt_body *bodies, int n_body, float4 *txb) {
+    for (int b = 0; b < n_body; ++b) {
+        const rt_body &B = bodies[b];
+        double w[3] = {p[0] - B.c[0], p[1] - B.c[1], B.type == RT_BODY_SPHERE ? p[2] - B.c[2] : 0.0};
+        double a = B.a;
+        double ds = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+        bool ok = ds > a;                      // cylinder: a source over the footprint has no lateral paths
+        double u[3] = {0, 0, 0}, bs = 0, q = 0;
+        if (ok) {
+            for (int k = 0; k < 3; ++k) u[k] = w[k] / ds;
+            bs = acos(a / ds);
+            q = sqrt(ds * ds - a * a);
+        }
+        float qh = (float)q;
+        txb[2 * b] = make_float4((float)u[0], (float)u[1], (float)u[2], (float)ds);
+        txb[2 * b + 1] = make_float4((float)bs, qh, (float)(q - (double)qh), ok ? 1.f : 0.f);
+    }
+}
+
+// Check n_f frequencies (Hz); fill the per-chunk constants fq[ceil(n_f /
+// NFC)]: k, (k/2)^{1/3}, 1/lambda (double-float), FP64 k and f/c; and *hl,
+// half the longest wavelength.
+static int prep_freqs(const double *f_hz, int n_f, FreqC *fq, double *hl, const char *who) {
+    if (n_f < 1 || n_f > RT_MAX_FREQS) return fail(RT_ERR_ARG, "%s: n_f = %d out of [1, %d]", who, n_f, RT_MAX_FREQS);
+    for (int i = 0; i < n_f; ++i)
+        if (!(f_hz[i] > 0.0) || !isfinite(f_hz[i])) return fail(RT_ERR_ARG, "%s: bad frequency", who);
+    int nch = (n_f + NFC - 1) / NFC;
+    for (int ch = 0; ch < nch; ++ch) {
+        FreqC &q = fq[ch];
+        memset(&q, 0, sizeof(q));
+        q.nf = (n_f - ch * NFC) < NFC ? (n_f - ch * NFC) : NFC;
+        for (int f = 0; f < NFC; ++f) {
+            double fr = (f < q.nf) ? f_hz[ch * NFC + f] : f_hz[0];
+            double k = 2.0 * M_PI * fr / 299792458.0;
+            double il = fr / 299792458.0;
+            q.k[f] = (float)k;
+            q.kh[f] = (float)cbrt(k / 2.0);
+            q.il_hi[f] = (float)il;
+            q.il_lo[f] = (float)(il - (double)q.il_hi[f]);
+            q.kd[f] = k;
+            q.fc[f] = il;
+        }
+    }
+    *hl = 0.0;
+    for (int i = 0; i < n_f; ++i) *hl = fmax(*hl, 299792458.0 / f_hz[i] / 2.0);
+    return RT_OK;
 }
 
 extern "C" {
@@ -267,26 +349,13 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
     }
     // bodies
     s->bodies.assign(bodies, bodies + n_body);
-    std::vector<float4> hb(2 * (size_t)n_body);
+    std::vector<float4> hb;
     double scale = 1.0;
-    for (int b = 0; b < n_body; ++b) {
-        const rt_body &B = s->bodies[b];
-        if (B.type != RT_BODY_SPHERE && B.type != RT_BODY_CYLINDER) { delete s; return fail(RT_ERR_ARG, "body %d: bad type", b); }
-        if (!fin32(B.c[0]) || !fin32(B.c[1]) || !fin32(B.c[2]) || !fin32(B.a) || !fin32(B.h) || !(B.a > 0.f) ||
-            (B.type == RT_BODY_CYLINDER && !(B.h > 0.f))) {
-            delete s;
-            return fail(RT_ERR_ARG, "body %d: non-finite or non-positive size", b);
-        }
-        for (int q = 0; q < b; ++q)
-            if (bodies_overlap(s->bodies[q], B)) { delete s; return fail(RT_ERR_GEOM, "bodies %d and %d overlap", q, b); }
-        hb[2 * b] = make_float4(B.c[0], B.c[1], B.c[2], B.a);
-        hb[2 * b + 1] = make_float4(B.type == RT_BODY_CYLINDER ? B.h : 0.f, (float)B.type, 0.f, 0.f);
-        for (int k = 0; k < 3; ++k) scale = fmax(scale, fabs((double)B.c[k]) + B.a + B.h);
-    }
     for (size_t i = 0; i < s->tri.size(); ++i) scale = fmax(scale, fabs((double)s->tri[i]));
-    // FP32 decision band: bounds the FP32 error of a margin (metres) built from
-    // a few dozen roundings of coordinates of magnitude <= scale: 32 ulp.
-    s->band_len = (float)(scale * 32.0 * 5.96e-8);
+    s->tri_scale = scale;
+    int rcb = prep_bodies(s->bodies.data(), n_body, hb, scale);
+    if (rcb != RT_OK) { delete s; return rcb; }
+    s->band_len = band_of(scale);
     std::vector<float4> hf32(nf > 0 ? nf : 1);
     std::vector<dq4> hf64(nf > 0 ? nf : 1);
     std::vector<int2> hr(nf > 0 ? nf : 1);
@@ -347,8 +416,8 @@ int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
         if (!fin32(tx[k]) || !fin32(pol[k])) return fail(RT_ERR_ARG, "rt_set_tx: non-finite value");
     if (pol[0] == 0.f && pol[1] == 0.f && pol[2] == 0.f) return fail(RT_ERR_ARG, "rt_set_tx: zero polarisation");
     double p[3] = {tx[0], tx[1], tx[2]};
-    for (int b = 0; b < s->n_body; ++b)
-        if (dist_to_body(p, s->bodies[b]) <= 0.0) return fail(RT_ERR_GEOM, "rt_set_tx: transmitter inside or on body %d", b);
+    int rc = check_tx_outside(p, s->bodies.data(), s->n_body, "rt_set_tx");
+    if (rc != RT_OK) return rc;
     for (int f = 0; f < s->n_face; ++f) {
         const FaceHost &F = s->faces[f];
         if (F.n[0] * p[0] + F.n[1] * p[1] + F.n[2] * p[2] - F.d == 0.0)
@@ -385,64 +454,34 @@ int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
     if (nf > 0) CK(cudaMemcpy(s->d_img, img.data(), sizeof(float4) * img.size(), cudaMemcpyHostToDevice));
     // per body, the source side of the (S, c, P) frame: the same for every receiver
     std::vector<float4> txb(2 * (size_t)(s->n_body > 0 ? s->n_body : 1));
-    for (int b = 0; b < s->n_body; ++b) {
-        const rt_body &B = s->bodies[b];
-        double w[3] = {p[0] - B.c[0], p[1] - B.c[1], B.type == RT_BODY_SPHERE ? p[2] - B.c[2] : 0.0};
-        double a = B.a;
-        double ds = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-        bool ok = ds > a;                      // cylinder: a source over the footprint has no lateral paths
-        double u[3] = {0, 0, 0}, bs = 0, q = 0;
-        if (ok) {
-            for (int k = 0; k < 3; ++k) u[k] = w[k] / ds;
-            bs = acos(a / ds);
-            q = sqrt(ds * ds - a * a);
-        }
-        float qh = (float)q;
-        txb[2 * b] = make_float4((float)u[0], (float)u[1], (float)u[2], (float)ds);
-        txb[2 * b + 1] = make_float4((float)bs, qh, (float)(q - (double)qh), ok ? 1.f : 0.f);
-    }
+    prep_txb(p, s->bodies.data(), s->n_body, txb.data());
     if (s->n_body > 0) CK(cudaMemcpy(s->d_txb, txb.data(), sizeof(float4) * 2 * s->n_body, cudaMemcpyHostToDevice));
     s->tx_set = true;
+    ++s->tx_version;
     return RT_OK;
 }
 
 int rt_set_freqs(rt_scene *s, const double *f_hz, int n_f) {
     if (!s || !f_hz) return fail(RT_ERR_ARG, "rt_set_freqs: NULL argument");
-    if (n_f < 1 || n_f > RT_MAX_FREQS) return fail(RT_ERR_ARG, "rt_set_freqs: n_f = %d out of [1, %d]", n_f, RT_MAX_FREQS);
-    for (int i = 0; i < n_f; ++i)
-        if (!(f_hz[i] > 0.0) || !isfinite(f_hz[i])) return fail(RT_ERR_ARG, "rt_set_freqs: bad frequency");
+    std::vector<FreqC> fq((RT_MAX_FREQS + NFC - 1) / NFC);
+    double hl;
+    int rc = prep_freqs(f_hz, n_f, fq.data(), &hl, "rt_set_freqs");
+    if (rc != RT_OK) return rc;
     s->freqs.assign(f_hz, f_hz + n_f);
     CK(cudaMemcpy(s->d_freq, f_hz, sizeof(double) * n_f, cudaMemcpyHostToDevice));
-    // per-chunk constants: k, (k/2)^{1/3}, 1/lambda (double-float), FP64 k and f/c
     int nch = (n_f + NFC - 1) / NFC;
-    std::vector<FreqC> fq(nch);
-    for (int ch = 0; ch < nch; ++ch) {
-        FreqC &q = fq[ch];
-        q.nf = (n_f - ch * NFC) < NFC ? (n_f - ch * NFC) : NFC;
-        for (int f = 0; f < NFC; ++f) {
-            double fr = (f < q.nf) ? f_hz[ch * NFC + f] : f_hz[0];
-            double k = 2.0 * M_PI * fr / 299792458.0;
-            double il = fr / 299792458.0;
-            q.k[f] = (float)k;
-            q.kh[f] = (float)cbrt(k / 2.0);
-            q.il_hi[f] = (float)il;
-            q.il_lo[f] = (float)(il - (double)q.il_hi[f]);
-            q.kd[f] = k;
-            q.fc[f] = il;
-        }
-    }
     CK(cudaMemcpy(s->d_fqc, fq.data(), sizeof(FreqC) * nch, cudaMemcpyHostToDevice));
     s->f_set = true;
     return RT_OK;
 }
 
-static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec) {
+static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, bool need_freqs = true) {
     rt_options o = {2, RT_EN_ALL, RT_PREC_FP32};
     if (opt) o = *opt;
     if (o.max_order < 0 || o.max_order > 2) return fail(RT_ERR_ARG, "max_order %d not in [0, 2]", o.max_order);
     if (o.precision != RT_PREC_FP32 && o.precision != RT_PREC_FP64) return fail(RT_ERR_ARG, "bad precision %d", o.precision);
     if (o.enable & ~RT_EN_ALL) return fail(RT_ERR_ARG, "bad enable mask 0x%x", o.enable);
-    if (!s->tx_set || !s->f_set) return fail(RT_ERR_STATE, "transmitter or frequencies not set");
+    if (!s->tx_set || (need_freqs && !s->f_set)) return fail(RT_ERR_STATE, "transmitter or frequencies not set");
     memset(&D, 0, sizeof(D));
     D.n_tri = s->n_tri; D.n_face = s->n_face; D.n_body = s->n_body; D.n_f = (int)s->freqs.size();
     D.tri = s->d_tri; D.tri_alt = s->d_aux; D.tri_nrm = s->d_aux;
@@ -546,6 +585,207 @@ int rt_fock_table(double *xi_lo, double *step, int *n, double *g, double *dg, do
             if (dg) { dg[(k * FOCK_N + j) * 2] = q[2]; dg[(k * FOCK_N + j) * 2 + 1] = q[3]; }
         }
     if (res) memcpy(res, T->host.res.data(), sizeof(double) * 4 * FOCK_NRES);
+    return RT_OK;
+}
+
+// ---- batched frames
+
+}  // extern "C"
+
+struct rt_batch {
+    rt_scene *s = nullptr;
+    int n_frames = 0, n_f = 0, max_body = 0, nch = 0;
+    std::vector<FrameDev> fr;           // host copy of the device frame table
+    std::vector<unsigned> fr_tx;        // scene transmitter version each frame was set with (0: never set)
+    unsigned long long n_tiles = 0;
+    float4 *d_body = nullptr, *d_txb = nullptr;   // [n_frames][max_body][2]
+    FreqC *d_fqc = nullptr;                       // [n_frames][nch]
+    FrameDev *d_frames = nullptr;                 // [n_frames]
+    unsigned long long *d_ctr = nullptr;          // [CTR_N]
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t last_stream = nullptr;
+    int last_launches = 0;
+};
+
+static void free_batch(rt_batch *b) {
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    cudaFree(b->d_body); cudaFree(b->d_txb); cudaFree(b->d_fqc); cudaFree(b->d_frames); cudaFree(b->d_ctr);
+}
+
+// queue one evaluation of the batch on st (no synchronisation)
+static int batch_queue(rt_batch *b, const float *rx_soa, float *e_out, uint32_t *flags, const rt_options *opt,
+                       cudaStream_t st) {
+    rt_scene *s = b->s;
+    for (int f = 0; f < b->n_frames; ++f)
+        if (b->fr_tx[f] != s->tx_version)
+            return fail(RT_ERR_STATE, "rt_batch: frame %d not set since the transmitter was last set", f);
+    DevScene D;
+    int prec;
+    int rc = make_dev(s, opt, D, &prec, false);
+    if (rc != RT_OK) return rc;
+    if (b->n_tiles > 0 && (!rx_soa || !e_out)) return fail(RT_ERR_ARG, "rt_batch: NULL buffer");
+    D.n_body = b->max_body;
+    D.n_f = b->n_f;
+    D.body = b->d_body; D.txb = b->d_txb; D.fqc = b->d_fqc;
+    D.freq = nullptr;
+    b->last_stream = st;
+    b->last_launches = 0;
+    if (b->n_tiles == 0) return RT_OK;
+    CK(cudaMemsetAsync(b->d_ctr, 0, sizeof(unsigned long long) * CTR_N, st));
+    return launch_eval_batch(D, b->d_frames, b->fr.data(), b->n_frames, b->n_tiles, rx_soa, e_out, flags, prec,
+                             b->d_ctr, st, &b->last_launches);
+}
+
+extern "C" {
+
+int rt_batch_create(rt_scene *s, int n_frames, const int32_t *n_rx, int n_f, int max_body, rt_batch **out) {
+    if (!out) return fail(RT_ERR_ARG, "rt_batch_create: out is NULL");
+    *out = nullptr;
+    if (!s || !n_rx) return fail(RT_ERR_ARG, "rt_batch_create: NULL argument");
+    if (n_frames < 1) return fail(RT_ERR_ARG, "rt_batch_create: n_frames = %d < 1", n_frames);
+    if (n_f < 1 || n_f > RT_MAX_FREQS) return fail(RT_ERR_ARG, "rt_batch_create: n_f = %d out of [1, %d]", n_f, RT_MAX_FREQS);
+    if (max_body < 0) return fail(RT_ERR_ARG, "rt_batch_create: max_body < 0");
+    if (max_body > RT_MAX_BODIES) return fail(RT_ERR_OVERFLOW, "rt_batch_create: max_body %d > %d", max_body, RT_MAX_BODIES);
+    rt_batch *b = new rt_batch();
+    b->s = s;
+    b->n_frames = n_frames;
+    b->n_f = n_f;
+    b->max_body = max_body;
+    b->nch = (n_f + NFC - 1) / NFC;
+    b->fr.assign(n_frames, FrameDev());
+    b->fr_tx.assign(n_frames, 0u);
+    long long rx_off = 0;
+    unsigned long long tile = 0;
+    for (int f = 0; f < n_frames; ++f) {
+        if (n_rx[f] < 0) { delete b; return fail(RT_ERR_ARG, "rt_batch_create: n_rx[%d] < 0", f); }
+        FrameDev &F = b->fr[f];
+        F.rx_off = rx_off;
+        F.e_off = 6 * (long long)n_f * rx_off;
+        F.tile0 = tile;
+        F.n_rx = n_rx[f];
+        F.n_body = 0;
+        F.band = band_of(s->tri_scale);
+        unsigned long long nt = ((unsigned long long)n_rx[f] + 31ull) >> 5;
+        tile += (nt + TILE_ALIGN - 1) / TILE_ALIGN * TILE_ALIGN;
+        rx_off += n_rx[f];
+    }
+    b->n_tiles = tile;
+    size_t nb = (size_t)n_frames * 2 * (max_body > 0 ? max_body : 1);
+#define CKB(x)                                                                  \
+    do {                                                                        \
+        cudaError_t e_ = (x);                                                   \
+        if (e_ != cudaSuccess) {                                                \
+            set_error(std::string(#x) + ": " + cudaGetErrorString(e_));         \
+            free_batch(b); delete b; return RT_ERR_CUDA;                        \
+        }                                                                       \
+    } while (0)
+    CKB(cudaMalloc(&b->d_body, sizeof(float4) * nb));
+    CKB(cudaMalloc(&b->d_txb, sizeof(float4) * nb));
+    CKB(cudaMalloc(&b->d_fqc, sizeof(FreqC) * (size_t)n_frames * b->nch));
+    CKB(cudaMalloc(&b->d_frames, sizeof(FrameDev) * (size_t)n_frames));
+    CKB(cudaMalloc(&b->d_ctr, sizeof(unsigned long long) * CTR_N));
+    for (int f = 0; f < n_frames; ++f) {
+        FrameDev &F = b->fr[f];
+        F.body = b->d_body + (size_t)f * 2 * (max_body > 0 ? max_body : 1);
+        F.txb = b->d_txb + (size_t)f * 2 * (max_body > 0 ? max_body : 1);
+        F.fqc = b->d_fqc + (size_t)f * b->nch;
+    }
+    CKB(cudaMemcpy(b->d_frames, b->fr.data(), sizeof(FrameDev) * (size_t)n_frames, cudaMemcpyHostToDevice));
+    CKB(cudaMemset(b->d_ctr, 0, sizeof(unsigned long long) * CTR_N));
+#undef CKB
+    *out = b;
+    return RT_OK;
+}
+
+void rt_batch_destroy(rt_batch *b) {
+    if (!b) return;
+    free_batch(b);
+    delete b;
+}
+
+int rt_batch_set_frame(rt_batch *b, int frame, const rt_body *bodies, int n_body, const double *f_hz) {
+    if (!b || !f_hz || (n_body > 0 && !bodies)) return fail(RT_ERR_ARG, "rt_batch_set_frame: NULL argument");
+    if (frame < 0 || frame >= b->n_frames) return fail(RT_ERR_ARG, "rt_batch_set_frame: frame %d out of range", frame);
+    if (n_body < 0) return fail(RT_ERR_ARG, "rt_batch_set_frame: n_body < 0");
+    if (n_body > b->max_body)
+        return fail(RT_ERR_OVERFLOW, "rt_batch_set_frame: %d bodies > max_body %d", n_body, b->max_body);
+    rt_scene *s = b->s;
+    if (!s->tx_set) return fail(RT_ERR_STATE, "rt_batch_set_frame: transmitter not set");
+    std::vector<float4> hb;
+    double scale = s->tri_scale;
+    int rc = prep_bodies(bodies, n_body, hb, scale);
+    if (rc != RT_OK) return rc;
+    double p[3] = {s->tx[0], s->tx[1], s->tx[2]};
+    rc = check_tx_outside(p, bodies, n_body, "rt_batch_set_frame");
+    if (rc != RT_OK) return rc;
+    std::vector<float4> txb(hb.size());
+    prep_txb(p, bodies, n_body, txb.data());
+    std::vector<FreqC> fq(b->nch);
+    double hl;
+    rc = prep_freqs(f_hz, b->n_f, fq.data(), &hl, "rt_batch_set_frame");
+    if (rc != RT_OK) return rc;
+    FrameDev &F = b->fr[frame];
+    F.n_body = n_body;
+    F.hl = hl;
+    F.band = band_of(scale);
+    if (n_body > 0) {
+        CK(cudaMemcpy((void *)F.body, hb.data(), sizeof(float4) * 2 * n_body, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy((void *)F.txb, txb.data(), sizeof(float4) * 2 * n_body, cudaMemcpyHostToDevice));
+    }
+    CK(cudaMemcpy((void *)F.fqc, fq.data(), sizeof(FreqC) * b->nch, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_frames + frame, &F, sizeof(FrameDev), cudaMemcpyHostToDevice));
+    b->fr_tx[frame] = s->tx_version;
+    return RT_OK;
+}
+
+int rt_batch_evaluate(rt_batch *b, const float *rx_soa, float *e_out, uint32_t *flags, const rt_options *opt,
+                      void *stream) {
+    if (!b) return fail(RT_ERR_ARG, "rt_batch_evaluate: NULL batch");
+    return batch_queue(b, rx_soa, e_out, flags, opt, (cudaStream_t)stream);
+}
+
+int rt_batch_capture(rt_batch *b, const float *rx_soa, float *e_out, uint32_t *flags, const rt_options *opt,
+                     void *stream) {
+    if (!b) return fail(RT_ERR_ARG, "rt_batch_capture: NULL batch");
+    if (!stream) return fail(RT_ERR_ARG, "rt_batch_capture: capture needs a stream other than the legacy default stream");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (b->gexec) { cudaGraphExecDestroy(b->gexec); b->gexec = nullptr; }
+    if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    int rc = batch_queue(b, rx_soa, e_out, flags, opt, st);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc != RT_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    if (e != cudaSuccess) return fail(RT_ERR_CUDA, "rt_batch_capture: cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    b->graph = g;
+    CK(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+    return RT_OK;
+}
+
+int rt_batch_replay(rt_batch *b, void *stream) {
+    if (!b) return fail(RT_ERR_ARG, "rt_batch_replay: NULL batch");
+    if (!b->gexec) return fail(RT_ERR_STATE, "rt_batch_replay: nothing captured");
+    for (int f = 0; f < b->n_frames; ++f)
+        if (b->fr_tx[f] != b->s->tx_version)
+            return fail(RT_ERR_STATE, "rt_batch_replay: frame %d not set since the transmitter was last set", f);
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaGraphLaunch(b->gexec, st));
+    b->last_stream = st;
+    return RT_OK;
+}
+
+int rt_batch_get_stats(rt_batch *b, rt_stats *out) {
+    if (!b || !out) return fail(RT_ERR_ARG, "rt_batch_get_stats: NULL argument");
+    CK(cudaStreamSynchronize(b->last_stream));
+    unsigned long long v = 0;
+    CK(cudaMemcpy(&v, b->d_ctr, sizeof(v), cudaMemcpyDeviceToHost));
+    out->escalated_candidates = v;
+    out->kernel_launches = (unsigned long long)b->last_launches;
     return RT_OK;
 }
 

@@ -1755,9 +1755,10 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
 
 template <typename T, bool PATHS, int CLS>
 __global__ void __launch_bounds__(blk_of(CLS, sizeof(T) == 4), min_blocks(CLS, sizeof(T) == 4))
-k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e_out, uint32_t *__restrict__ flags_out,
+k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frames, unsigned long long n_tiles,
+       const float *__restrict__ rx_base, float *__restrict__ e_base, uint32_t *__restrict__ fl_base,
        uint64_t *__restrict__ codes, int32_t *__restrict__ counts, int cap, int ch0, int nch, int rcap,
-       double half_lambda_max, int accumulate, unsigned long long *esc_counter, unsigned long long *queue) {
+       int accumulate, unsigned long long *esc_counter, unsigned long long *queue) {
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     extern __shared__ float4 smem[];
     __shared__ Ctx s_ctx;
@@ -1778,10 +1779,13 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
     for (int i = threadIdx.x; i < n_fock; i += blockDim.x) s_fock[i] = S.fock32[i];
     for (int i = threadIdx.x; i < n_res; i += blockDim.x) s_res[i] = S.res32[i];
     for (int i = threadIdx.x; i < S.n_face; i += blockDim.x) s_face[i] = S.face32[i];
-    if (body_sm)
-        for (int i = threadIdx.x; i < 2 * S.n_body; i += blockDim.x) {
-            s_body[i] = S.body[i];
-            s_txb[i] = S.txb[i];
+    // the frame's bodies and source-side body frames (one frame: F1; a
+    // batch: staged again whenever the block's next work unit is in another
+    // frame)
+    if (body_sm && !frames)
+        for (int i = threadIdx.x; i < 2 * F1.n_body; i += blockDim.x) {
+            s_body[i] = F1.body[i];
+            s_txb[i] = F1.txb[i];
         }
     if (tri_sm)
         for (int i = threadIdx.x; i < 3 * S.n_tri; i += blockDim.x) {
@@ -1798,16 +1802,16 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
         c.face64 = S.face64;
         c.face_rng = S.face_rng;
         c.face_tris = S.face_tris;
-        c.body = body_sm ? s_body : S.body;
-        c.n_tri = S.n_tri; c.n_face = S.n_face; c.n_body = S.n_body;
+        c.body = body_sm ? s_body : F1.body;
+        c.n_tri = S.n_tri; c.n_face = S.n_face; c.n_body = frames ? 0 : F1.n_body;
         c.band = S.band_len;
         c.S = mk3(S.tx[0], S.tx[1], S.tx[2]);
         c.pol = mk3(S.pol[0], S.pol[1], S.pol[2]);
         c.fock = s_fock; c.res = s_res; c.weid = s_weid; c.weid_L = S.weid_L;
         c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
         c.img = S.img;
-        c.txb = body_sm ? s_txb : S.txb;
-        s_fq = S.fqc[ch0];
+        c.txb = body_sm ? s_txb : F1.txb;
+        if (!frames) s_fq = F1.fqc[ch0];
     }
     __syncthreads();
     // the next class kernel (launched as a programmatic dependent) may start
@@ -1819,8 +1823,11 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
     const FreqC &fq = s_fq;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = blk_of(CLS, sizeof(T) == 4) / 32;
-    const unsigned long long ntiles = ((unsigned long long)n_rx + 31ull) >> 5;
     if constexpr (PATHS) {
+        // (one frame only)
+        const float *rx = rx_base;
+        const int n_rx = F1.n_rx;
+        const unsigned long long ntiles = ((unsigned long long)n_rx + 31ull) >> 5;
         asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous class kernel's lists are complete
         // path lists: each warp takes tiles of 32 consecutive receivers from
         // the launch's queue and lists every candidate itself (codes in the
@@ -1837,10 +1844,10 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
                 unsigned nesc;
                 int npath = accumulate ? counts[r] : 0;
                 int nrec;
-                eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap, half_lambda_max,
+                eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap, F1.hl,
                                              0, c.n_body, true, false, 0, 0, 1, acc, nullptr, fl, nesc, npath, nrec);
                 counts[r] = npath;
-                if (flags_out) flags_out[r] = accumulate ? (flags_out[r] | fl) : fl;
+                if (fl_base) fl_base[r] = accumulate ? (fl_base[r] | fl) : fl;
                 if (nesc) atomicAdd(esc_counter, (unsigned long long)nesc);
             }
         }
@@ -1855,25 +1862,71 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
         // record buffer; per chunk all warps finish the geometry pass before
         // any starts the field pass, which runs once per frequency chunk on
         // the same records and adds its rows to the outputs.
+        //   A work unit is TPB tiles of one frame; a batch's frames start at
+        // tile indices that are multiples of TILE_ALIGN (every class's TPB
+        // divides it), so unit u covers tiles u TPB .. u TPB + TPB - 1.  A
+        // block's units come in increasing order, so its frame only moves on.
         constexpr int NWT = BODIES ? WARPS_PER_TILE : NW;
         constexpr int TPB = NW / NWT;
+        static_assert(TILE_ALIGN % TPB == 0, "frame alignment");
         constexpr bool RECS = BODIES && sizeof(T) == 4;
         constexpr int PER = ((CLS & CLS_CREEP) ? 2 : 0) + ((CLS & CLS_BODYREFL) ? 1 : 0);
-        const int n_b = BODIES ? c.n_body : 0;
-        // bodies per geometry pass: all of them with one frequency chunk (full
-        // record buffers are flushed on the way), else as many as the buffer holds
-        const int bc = (RECS && nch > 1) ? NWT * (rcap / PER) : (n_b > 0 ? n_b : 1);
+        const unsigned long long n_units = (n_tiles + TPB - 1) / TPB;
         const int grp = warp / NWT, part = warp % NWT;
         __shared__ T s_part[NW][NFC * 6][32];
         __shared__ uint32_t s_fl[NW][32];
-        __shared__ unsigned long long s_tile;
+        __shared__ unsigned long long s_unit;
+        __shared__ int s_fi, s_new;
+        __shared__ FrameDev s_fr;
+        if (threadIdx.x == 0) {
+            s_fi = -1;
+            if (!frames) s_fr = F1;
+        }
         for (;;) {
-            if (threadIdx.x == 0) s_tile = atomicAdd(queue, (unsigned long long)TPB);
+            if (threadIdx.x == 0) {
+                const unsigned long long u = atomicAdd(queue, 1ull);
+                int fi = 0, nw = 0;
+                if (frames && u < n_units) {
+                    fi = s_fi < 0 ? 0 : s_fi;
+                    while (fi + 1 < n_frames && u * TPB >= frames[fi + 1].tile0) ++fi;
+                    nw = fi != s_fi;
+                    if (nw) s_fr = frames[fi];
+                }
+                s_unit = u;
+                s_fi = fi;
+                s_new = nw;
+            }
             __syncthreads();
-            const unsigned long long t = s_tile + grp;
-            if (s_tile >= ntiles) break;
-            const int r = (int)(t * 32ull) + lane;
-            const bool rok = t < ntiles && r < n_rx;
+            if (s_unit >= n_units) break;
+            if (s_new) {
+                // this unit is the block's first in frame s_fi: stage its data
+                if (body_sm)
+                    for (int i = threadIdx.x; i < 2 * s_fr.n_body; i += blockDim.x) {
+                        s_body[i] = s_fr.body[i];
+                        s_txb[i] = s_fr.txb[i];
+                    }
+                if (threadIdx.x == 0) {
+                    s_ctx.body = body_sm ? s_body : s_fr.body;
+                    s_ctx.txb = body_sm ? s_txb : s_fr.txb;
+                    s_ctx.n_body = s_fr.n_body;
+                    s_ctx.band = s_fr.band;
+                    s_fq = s_fr.fqc[ch0];
+                }
+                __syncthreads();
+            }
+            const FrameDev &Fr = s_fr;
+            const int n_rx = Fr.n_rx;
+            const float *rx = rx_base + 3 * Fr.rx_off;
+            float *e_out = e_base + Fr.e_off;
+            uint32_t *flags_out = fl_base ? fl_base + Fr.rx_off : nullptr;
+            const int n_b = BODIES ? c.n_body : 0;
+            // bodies per geometry pass: all of them with one frequency chunk (full
+            // record buffers are flushed on the way), else as many as the buffer holds
+            const int bc = (RECS && nch > 1) ? NWT * (rcap / PER) : (n_b > 0 ? n_b : 1);
+            const unsigned long long t = s_unit * TPB - Fr.tile0 + grp;   // tile within the frame
+            const long long r0 = (long long)(t * 32ull);
+            const int r = r0 < n_rx ? (int)r0 + lane : n_rx;
+            const bool rok = r < n_rx;
             AccS<T> acc{&s_part[warp][0][lane]};     // the warp's partial sums, summed in place
             float *rec = s_rec + warp * (rcap * REC_N * 32) + lane;
 #pragma unroll 1
@@ -1883,7 +1936,7 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
                 int npath = 0, nrec = 0;
                 if (rok)
                     eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap,
-                                                 half_lambda_max, b0, min(b0 + bc, n_b), b0 == 0, nch == 1, rcap, part,
+                                                 Fr.hl, b0, min(b0 + bc, n_b), b0 == 0, nch == 1, rcap, part,
                                                  NWT, acc, rec, fl, nesc, npath, nrec);
                 s_fl[warp][lane] = fl;
                 if (nesc && ch0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
@@ -1891,14 +1944,14 @@ k_eval(DevScene S, const float *__restrict__ rx, int n_rx, float *__restrict__ e
                 for (int ch = ch0; ch < ch0 + nch; ++ch) {
                     if constexpr (RECS) {
                         __syncthreads();              // geometry pass / previous reduction done
-                        if (nch > 1) {                // (one chunk: staged at the start)
-                            if (threadIdx.x == 0) s_fq = S.fqc[ch];
+                        if (nch > 1) {                // (one chunk: staged with the frame)
+                            if (threadIdx.x == 0) s_fq = Fr.fqc[ch];
                             __syncthreads();
                         }
                         if (rok) {
                             if (ch > ch0) acc_zero(acc);      // the geometry pass zeroed it for the first chunk
                             apply_records<CLS>(c, acc, fq, rec, nrec, mk3(rx[r], rx[n_rx + r], rx[2 * n_rx + r]),
-                                          half_lambda_max, S.enable);
+                                               Fr.hl, S.enable);
                         }
                     }
                     // the previous class kernel's fields and flags are complete (a
@@ -1959,10 +2012,23 @@ struct LaunchCtx {
     cudaStream_t stream;
 };
 
+// What one evaluation covers: one frame (F1, frames == nullptr) or a batch
+// of frames, and where its inputs and outputs are.
+struct Work {
+    FrameDev F1;
+    const FrameDev *frames;
+    int n_frames;
+    unsigned long long n_tiles;
+    const float *rx;
+    float *e;
+    uint32_t *fl;
+    uint64_t *codes;
+    int32_t *counts;
+    int cap;
+};
+
 template <typename T, bool PATHS, int CLS>
-static cudaError_t launch_one(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
-                              uint64_t *codes, int32_t *counts, int cap, int ch0, int nch, double hl,
-                              int accumulate, LaunchCtx &L) {
+static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch, int accumulate, LaunchCtx &L) {
     if (L.n >= CTR_QUEUES) return cudaErrorInvalidValue;
     constexpr bool bodies = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     constexpr int blk = blk_of(CLS, sizeof(T) == 4);
@@ -1972,14 +2038,17 @@ static cudaError_t launch_one(const DevScene &S, const float *rx_soa, int n_rx, 
     size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk, rcap);
     cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    // persistent grid: the blocks that fit on the device at once
+    // persistent grid: the blocks that fit on the device at once, at most
+    // one per work unit
     int dev = 0, nsm = 0, occ = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<T, PATHS, CLS>, blk, sm)) != cudaSuccess) return e;
-    long long need = ((long long)n_rx + blk - 1) / blk;
+    constexpr int tiles_per_unit = PATHS ? blk / 32 : (bodies ? blk / 32 / WARPS_PER_TILE : 1);
+    long long need = (long long)((W.n_tiles + tiles_per_unit - 1) / tiles_per_unit);
     long long cap_blocks = (long long)nsm * (occ > 0 ? occ : 1);
     int grid = (int)(need < cap_blocks ? need : cap_blocks);
+    if (grid < 1) grid = 1;
     // every launch after the first of the evaluation is a programmatic
     // dependent of the one before: it may start while that one finishes
     cudaLaunchConfig_t cfg = {};
@@ -1992,8 +2061,8 @@ static cudaError_t launch_one(const DevScene &S, const float *rx_soa, int n_rx, 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = L.n > 0 ? 1 : 0;
-    e = cudaLaunchKernelEx(&cfg, k_eval<T, PATHS, CLS>, S, rx_soa, n_rx, e_out, flags, codes, counts, cap, ch0, nch,
-                           rcap, hl, accumulate, L.ctr, L.ctr + 1 + L.n);
+    e = cudaLaunchKernelEx(&cfg, k_eval<T, PATHS, CLS>, S, W.F1, W.frames, W.n_frames, W.n_tiles, W.rx, W.e, W.fl,
+                           W.codes, W.counts, W.cap, ch0, nch, rcap, accumulate, L.ctr, L.ctr + 1 + L.n);
     ++L.n;
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -2003,22 +2072,34 @@ static cudaError_t launch_one(const DevScene &S, const float *rx_soa, int n_rx, 
 // chunk, then each body kernel once for all chunks (its geometry is reused).
 // The first launch writes the outputs, the later ones add to them.
 template <typename T, bool PATHS>
-static cudaError_t launch_all(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
-                              uint64_t *codes, int32_t *counts, int cap, int nchunks, double hl, LaunchCtx &L) {
+static cudaError_t launch_all(const DevScene &S, const Work &W, int nchunks, LaunchCtx &L) {
     cudaError_t e = cudaSuccess;
     const bool chunked_bodies = PATHS || sizeof(T) != 4;
     for (int ch = 0; ch < nchunks && e == cudaSuccess; ++ch) {
-        e = launch_one<T, PATHS, CLS_PLANAR>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, ch, 1, hl, 0, L);
-        if (chunked_bodies && e == cudaSuccess)
-            e = launch_one<T, PATHS, CLS_BODYREFL>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, ch, 1, hl, 1, L);
-        if (chunked_bodies && e == cudaSuccess)
-            e = launch_one<T, PATHS, CLS_CREEP>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, ch, 1, hl, 1, L);
+        e = launch_one<T, PATHS, CLS_PLANAR>(S, W, ch, 1, 0, L);
+        if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL>(S, W, ch, 1, 1, L);
+        if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_CREEP>(S, W, ch, 1, 1, L);
     }
-    if (!chunked_bodies && e == cudaSuccess)
-        e = launch_one<T, PATHS, CLS_BODYREFL>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, 0, nchunks, hl, 1, L);
-    if (!chunked_bodies && e == cudaSuccess)
-        e = launch_one<T, PATHS, CLS_CREEP>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, 0, nchunks, hl, 1, L);
+    if (!chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL>(S, W, 0, nchunks, 1, L);
+    if (!chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_CREEP>(S, W, 0, nchunks, 1, L);
     return e;
+}
+
+static int run(const DevScene &S, const Work &W, int precision, bool paths, unsigned long long *ctr,
+               cudaStream_t stream, int *n_launches) {
+    LaunchCtx L{ctr, 0, stream};
+    const int nchunks = paths ? 1 : (S.n_f + NFC - 1) / NFC;
+    cudaError_t e;
+    if (precision == RT_PREC_FP64)
+        e = paths ? launch_all<dx, true>(S, W, nchunks, L) : launch_all<dx, false>(S, W, nchunks, L);
+    else
+        e = paths ? launch_all<float, true>(S, W, nchunks, L) : launch_all<float, false>(S, W, nchunks, L);
+    *n_launches = L.n;
+    if (e != cudaSuccess) {
+        set_error(std::string("k_eval launch: ") + cudaGetErrorString(e));
+        return RT_ERR_CUDA;
+    }
+    return RT_OK;
 }
 
 int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
@@ -2026,27 +2107,37 @@ int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, 
                 cudaStream_t stream, int *n_launches) {
     *n_launches = 0;
     if (n_rx <= 0) return RT_OK;
-    LaunchCtx L{ctr, 0, stream};
-    double hl = 0.0;
+    Work W = {};
+    W.F1.body = S.body;
+    W.F1.txb = S.txb;
+    W.F1.fqc = S.fqc;
+    W.F1.n_rx = n_rx;
+    W.F1.n_body = S.n_body;
+    W.F1.band = S.band_len;
     for (int f = 0; f < S.n_f; ++f) {
         double lam = 299792458.0 / S.freq[f];
-        if (lam / 2.0 > hl) hl = lam / 2.0;
+        if (lam / 2.0 > W.F1.hl) W.F1.hl = lam / 2.0;
     }
-    const bool paths = codes != nullptr;
-    const int nchunks = paths ? 1 : (S.n_f + NFC - 1) / NFC;
-    cudaError_t e;
-    if (precision == RT_PREC_FP64)
-        e = paths ? launch_all<dx, true>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, nchunks, hl, L)
-                  : launch_all<dx, false>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, nchunks, hl, L);
-    else
-        e = paths ? launch_all<float, true>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, nchunks, hl, L)
-                  : launch_all<float, false>(S, rx_soa, n_rx, e_out, flags, codes, counts, cap, nchunks, hl, L);
-    *n_launches = L.n;
-    if (e != cudaSuccess) {
-        set_error(std::string("k_eval launch: ") + cudaGetErrorString(e));
-        return RT_ERR_CUDA;
-    }
-    return RT_OK;
+    W.frames = nullptr;
+    W.n_frames = 1;
+    W.n_tiles = ((unsigned long long)n_rx + 31ull) >> 5;
+    W.rx = rx_soa; W.e = e_out; W.fl = flags;
+    W.codes = codes; W.counts = counts; W.cap = cap;
+    return run(S, W, precision, codes != nullptr, ctr, stream, n_launches);
+}
+
+int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const FrameDev *frames_host, int n_frames,
+                      unsigned long long n_tiles, const float *rx_soa, float *e_out, uint32_t *flags, int precision,
+                      unsigned long long *ctr, cudaStream_t stream, int *n_launches) {
+    *n_launches = 0;
+    if (n_frames <= 0 || n_tiles == 0) return RT_OK;
+    Work W = {};
+    W.F1 = frames_host[0];      // (unused by the kernels when frames is set)
+    W.frames = frames_dev;
+    W.n_frames = n_frames;
+    W.n_tiles = n_tiles;
+    W.rx = rx_soa; W.e = e_out; W.fl = flags;
+    return run(S, W, precision, false, ctr, stream, n_launches);
 }
 
 }  // namespace creep

@@ -82,6 +82,24 @@ struct DevScene {
     unsigned enable;
 };
 
+// One frame of an evaluation: its curved bodies, frequencies and receivers
+// (the triangles and the transmitter belong to the scene).  A plain
+// evaluation is one frame passed by value; a batch is a device array of them.
+// Each frame's first tile index (32 receivers a tile) is a multiple of
+// TILE_ALIGN, so that a work unit of any class kernel lies in one frame.
+constexpr int TILE_ALIGN = 3;
+struct FrameDev {
+    const float4 *body;        // [n_body][2], as DevScene::body
+    const float4 *txb;         // [n_body][2], as DevScene::txb
+    const FreqC *fqc;          // [ceil(n_f / NFC)] frequency constants
+    long long rx_off;          // first receiver: SoA block at rx + 3 rx_off, flags at flags + rx_off
+    long long e_off;           // first output float
+    unsigned long long tile0;  // first tile of the batch's tile range
+    double hl;                 // half the longest wavelength (caustic flag threshold)
+    int n_rx, n_body;
+    float band;                // FP32 decision band (m) of the frame's geometry
+};
+
 // Device counters of one evaluation: [0] candidates decided in FP64, [1 + i]
 // the work queue of launch i.  Zeroed by the caller before launch_eval.
 constexpr int CTR_QUEUES = 64;
@@ -92,5 +110,12 @@ constexpr int CTR_N = 1 + CTR_QUEUES;
 int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
                 uint64_t *codes, int32_t *counts, int cap, int precision, unsigned long long *ctr,
                 cudaStream_t stream, int *n_launches);
+
+// Evaluate the n_frames frames of frames_dev (device copy of frames_host):
+// every frame has S.n_f frequencies and at most S.n_body bodies; n_tiles is
+// the end of the last frame's tile range.
+int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const FrameDev *frames_host, int n_frames,
+                      unsigned long long n_tiles, const float *rx_soa, float *e_out, uint32_t *flags, int precision,
+                      unsigned long long *ctr, cudaStream_t stream, int *n_launches);
 
 }  // namespace creep

@@ -14,6 +14,12 @@ stand in for them):
   * ``room``         -- 10 x 8 x 3 m box (6 PEC faces as 12 triangles) with N
     PEC cylinders (radius U[0.15, 0.25] m, height 1.7 m, on the floor),
     source at (1, 1, 2), receiver grid at z = 1.2 m.
+  * ``crowd``        -- frames of that room in which the cylinders (people)
+    walk: every 0.1 s each takes a 0.14 m step (1.4 m/s) in a random
+    direction, kept inside the room, clear of the source and of each other
+    (Sec. III's dynamic scenes); per frame its own frequencies (uniform in a
+    band) and an uneven receiver count (log-uniform), receivers uniform over
+    the floor plan at z = 1.2 m.
 """
 import numpy as np
 
@@ -122,3 +128,84 @@ def room(n_cyl=20, nx=256, ny=256, freqs=(2.4e9, 5.8e9, 28e9), seed=SEED_BASE + 
     name = "room(%gx%gx%g m, %d PEC cylinders, %dx%d rx, f=%s GHz, refl<=%d)" % (
         lx, ly, lz, n_cyl, nx, ny, ",".join("%g" % (f / 1e9) for f in freqs), max_order)
     return Scene(tri, face, bodies, tx, pol, freqs, rx, name, max_order=max_order)
+
+
+class Crowd:
+    """Frames of one room: shared triangles, source and polarisation; per
+    frame its bodies, frequencies and receivers (float32 arrays)."""
+
+    def __init__(self, tri, tri_face, tx, pol, bodies, freqs, rx, name, max_order=2):
+        self.tri, self.tri_face = tri, tri_face
+        self.tx = np.asarray(tx, dtype=np.float32).reshape(3)
+        self.pol = np.asarray(pol, dtype=np.float32).reshape(3)
+        self.bodies = bodies          # list of [n_body, 6] float32
+        self.freqs = freqs            # list of [n_f] float64
+        self.rx = rx                  # list of [n_rx, 3] float32
+        self.name = name
+        self.max_order = int(max_order)
+
+    @property
+    def n_frames(self):
+        return len(self.rx)
+
+    @property
+    def n_rx(self):
+        return [r.shape[0] for r in self.rx]
+
+    def frame(self, i, idx=None):
+        """Frame i (or the receivers idx of it) as a single Scene."""
+        rx = self.rx[i] if idx is None else self.rx[i][idx]
+        return Scene(self.tri, self.tri_face, self.bodies[i], self.tx, self.pol, self.freqs[i], rx,
+                     "%s[frame %d]" % (self.name, i), self.max_order)
+
+
+def walk_step(bodies, lx, ly, rng, step, avoid, gap=0.05, tries=16):
+    """One random-walk step of every cylinder (in order): a move of length
+    `step` in a uniform random direction, redrawn up to `tries` times while
+    it would leave the room (gap), overlap another cylinder (gap) or come
+    within clearance of a point in `avoid`; a cylinder with no free move stays."""
+    out = bodies.copy()
+    for i in range(len(out)):
+        r = float(out[i, 4])
+        for _ in range(tries):
+            th = rng.uniform(0.0, 2.0 * np.pi)
+            x = np.float32(out[i, 1] + step * np.cos(th))
+            y = np.float32(out[i, 2] + step * np.sin(th))
+            if not (r + gap <= x <= lx - r - gap and r + gap <= y <= ly - r - gap):
+                continue
+            ok = True
+            for j in range(len(out)):
+                if j != i and np.hypot(x - out[j, 1], y - out[j, 2]) < r + out[j, 4] + gap:
+                    ok = False
+                    break
+            if ok:
+                for (px, py, cl) in avoid:
+                    if np.hypot(x - px, y - py) < r + cl:
+                        ok = False
+                        break
+            if ok:
+                out[i, 1], out[i, 2] = x, y
+                break
+    return out
+
+
+def crowd(n_frames=64, n_cyl=50, n_freq=16, band=(24e9, 30e9), rx_range=(1000, 65536), speed=1.4, dt=0.1,
+          seed=SEED_BASE + 3, size=(10.0, 8.0, 3.0), tx=(1.0, 1.0, 2.0), pol=(0.0, 0.0, 1.0), rx_z=1.2,
+          max_order=2):
+    lx, ly, lz = size
+    rng = np.random.default_rng(seed)
+    tri, face = box_triangles(lx, ly, lz)
+    avoid = [(tx[0], tx[1], 0.3)]
+    b = place_cylinders(n_cyl, lx, ly, rng, avoid=avoid)
+    bodies, freqs, rxs = [], [], []
+    for f in range(n_frames):
+        if f > 0:
+            b = walk_step(b, lx, ly, rng, speed * dt, avoid)
+        bodies.append(b.copy())
+        freqs.append(rng.uniform(band[0], band[1], n_freq))
+        n = int(round(np.exp(rng.uniform(np.log(rx_range[0]), np.log(rx_range[1])))))
+        rx = np.stack([rng.uniform(0.0, lx, n), rng.uniform(0.0, ly, n), np.full(n, rx_z)], axis=1)
+        rxs.append(np.ascontiguousarray(rx, dtype=np.float32))
+    name = "crowd(%d frames, %gx%gx%g m, %d walking PEC cylinders, %d freqs in %g-%g GHz, rx %d-%d log-uniform)" % (
+        n_frames, lx, ly, lz, n_cyl, n_freq, band[0] / 1e9, band[1] / 1e9, rx_range[0], rx_range[1])
+    return Crowd(tri, face, tx, pol, bodies, freqs, rxs, name, max_order=max_order)
