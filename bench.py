@@ -8,6 +8,11 @@ bulk arithmetic: 65 536 receivers x 3 frequencies = 196 608 field samples.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
+At N = 1 the line also carries "batched": the batched form on 64 crowd frames
+(50 walking PEC cylinders, 16 frequencies in 24-30 GHz per frame, 1k-64k
+receivers per frame, 1.12 M receivers in all) replayed from a captured CUDA
+graph, with its own roofline and oracle comparison (--no-batched skips it).
+
 N > 1 runs under torch.distributed (one process per GPU): each rank evaluates
 its own receiver grid (shifted by a fraction of a cell) with no data-path
 collective; value = all ranks' samples / max-over-ranks time ("weak").
@@ -45,6 +50,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched crowd-frames measurement")
+    ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -114,6 +121,10 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        return self.clocks_now()
+
+    def clocks_now(self):
+        """Summary of the samples taken so far (None if none)."""
         if not self.samples:
             return None
         sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
@@ -239,6 +250,95 @@ def algorithmic_flops(counters, n_sample, n_rx, n_f):
     return w * n_rx / n_sample
 
 
+# ---------------------------------------------------------------- batched crowd frames
+def batched_crowd(args, creep, dev, flush, peak_fn):
+    """The batched form: 64 crowd frames in one launch per path class,
+    replayed from a captured graph; throughput, roofline and accuracy on
+    sampled receivers of eight frames against the oracle."""
+    import torch
+    from paper_2310_10578_gb300 import scenes
+    cw = scenes.crowd()
+    n_f = len(cw.freqs[0])
+    S = creep.Scene(cw.tri, cw.tri_face, np.zeros((0, 6)))
+    S.set_tx(cw.tx, cw.pol)
+    B = creep.Batch(S, cw.n_rx, n_f, max(len(b) for b in cw.bodies))
+    for i in range(cw.n_frames):
+        B.set_frame(i, cw.bodies[i], cw.freqs[i])
+    rx = torch.tensor(B.rx_pack([r.T for r in cw.rx]), device=dev)
+    out = torch.empty(6 * n_f * B.total_rx, dtype=torch.float32, device=dev)
+    opts = creep.options(max_order=2)
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream())
+    B.capture(rx, out, opts=opts, stream=side)
+    for _ in range(3):
+        B.replay(stream=side)
+    side.synchronize()
+    st, en = [], []
+    for i in range(args.batched_steps):
+        with torch.cuda.stream(side):
+            flush.fill_(float(i))
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(side)
+            B.replay(stream=side)
+            b.record(side)
+        st.append(a)
+        en.append(b)
+    side.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in zip(st, en)]))
+    samples = B.total_rx * n_f
+    stats = B.stats()
+    res = {"workload": cw.name, "value": samples / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "steps": args.batched_steps, "frames": cw.n_frames, "n_rx_total": B.total_rx, "n_freq": n_f,
+           "launch": "captured CUDA graph: counter reset + 6 kernels (4 planar chunks, body reflection, creeping)",
+           "gpu_launches_per_step": stats["kernel_launches"],
+           "fp64_escalated_candidates": stats["escalated_candidates"],
+           "l2": "flushed between timed steps (256 MiB write)"}
+    if not args.no_cpu_baseline:
+        from oracle import oracle
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from parity import compare_fields
+        oracle.build()
+        rng = np.random.default_rng(77)
+        flat = out.detach().cpu().numpy().astype(np.float64)
+        flops_frames = 0.0          # algorithmic work of the sampled frames (scaled to their receivers)
+        rx_frames = 0
+        n_s = 0
+        worst = {}
+        t_cpu = 0.0
+        for fr in rng.choice(cw.n_frames, 8, replace=False):
+            idx = np.sort(rng.choice(cw.n_rx[fr], 256, replace=False))
+            t0 = time.perf_counter()
+            ref = oracle.evaluate(cw.frame(fr, idx))
+            t_cpu += time.perf_counter() - t0
+            a = int(B.rx_off[fr])
+            n = cw.n_rx[fr]
+            Eg = flat[6 * n_f * a: 6 * n_f * (a + n)].reshape(n_f, 3, n, 2)
+            Eg = (Eg[..., 0] + 1j * Eg[..., 1])[:, :, idx]
+            acc = compare_fields(Eg, ref, flags=ref.flags, freqs=cw.freqs[fr], check=False)
+            for k, v in acc.items():
+                if k.startswith("n_"):
+                    worst[k] = worst.get(k, 0) + v
+                elif isinstance(v, (int, float)):
+                    worst[k] = max(worst.get(k, v), v)
+            flops_frames += algorithmic_flops(ref.counters, len(idx), n, n_f)
+            rx_frames += n
+            n_s += len(idx)
+        # the sampled frames stand for all 64, in proportion to receivers
+        flops = flops_frames * B.total_rx / rx_frames
+        peak, basis = peak_fn()
+        achieved = flops / (ms / 1e3) / 1e12
+        res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                           "frac": achieved / peak, "traffic": None, "peak_basis": basis,
+                           "kernel": "evaluation: k_eval<float, false, 1|2|4> over all frames",
+                           "work_per_evaluation_flops": flops}
+        res["accuracy_vs_fp64_oracle"] = dict(worst, sample_receivers=n_s,
+                                              sample="256 random receivers of each of 8 random frames")
+        res["cpu_baseline"] = {"value": n_s * n_f / t_cpu, "unit": UNIT, "cores": os.cpu_count() or 1,
+                               "kind": "oracle", "sample": "the accuracy sample (%.1f s)" % t_cpu}
+    return res
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -311,6 +411,15 @@ def main():
         e2e_once()
         e2e_t.append(time.perf_counter() - t0)
     barrier()
+    props = torch.cuda.get_device_properties(dev)
+    batched = None
+    if world == 1 and not args.no_batched:
+        def peak_fn():
+            c = (sampler.clocks_now() if sampler else None) or {}
+            sm_max = c.get("sm_max_mhz") or 2070.0
+            return (props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12,
+                    "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived, FFMA)" % (props.multi_processor_count, sm_max))
+        batched = batched_crowd(args, creep, dev, flush, peak_fn)
     clocks = sampler.stop() if sampler else None
 
     ms, e2e_s = max_over_ranks([np.mean(dev_ms), np.mean(e2e_t)], device=dev)
@@ -349,7 +458,6 @@ def main():
         line["cpu_baseline"] = base
         line["accuracy_vs_fp64_oracle"] = dict(acc, sample_receivers=n_s)
         flops = algorithmic_flops(counters, n_s, n_rx, n_f)
-        props = torch.cuda.get_device_properties(dev)
         sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
         peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12      # FP32 FFMA lanes x 2 x clock
         achieved = flops / (ms / 1e3) / 1e12
@@ -363,6 +471,8 @@ def main():
                                           (props.multi_processor_count, sm_max),
                             "kernel": "evaluation: k_eval<float, false, 1|2|4> (planar, body reflection, creeping)",
                             "work_per_evaluation_flops": flops}
+    if batched is not None:
+        line["batched"] = batched
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -1247,15 +1247,9 @@ __device__ void field_creep(const Ctx &c, ACC &acc, const FreqC &fq, v3t<T> S, v
 //   ray through the caustic), 9 L' (transition distance; its sign tells the
 //   kind: > 0 reflection, < 0 creeping), 10 rho_g^(1/3), 11 cos(theta_i)
 //   (reflection) or t / rho_g (creeping), 12-13 path length.
-// A candidate decided in FP64 whose field is deferred to the field passes
-// (several frequency chunks) has L' = 0 and entry 0 holds, as int bits,
-// kind | dir << 2 | body << 3 (kind REC_ESC_RB or REC_ESC_CREEP).
+// A candidate decided in FP64 gets the record of its FP64 geometry when its
+// field goes through the records (several frequency chunks).
 constexpr int REC_N = 14;
-enum { REC_ESC_RB = 2, REC_ESC_CREEP = 3 };
-__device__ __forceinline__ void rec_esc(float *r, int kind, int dir, int b) {
-    r[0] = __int_as_float(kind | (dir << 2) | (b << 3));
-    r[288] = 0.0f;
-}
 
 __device__ __forceinline__ void rec_put(float *r, float Es, float Eh, v3t<float> e1, v3t<float> e2, float A,
                                         float Lp, float rcb, float x, dfl len) {
@@ -1378,6 +1372,7 @@ __device__ __forceinline__ Geo<float> to_f(const Geo<dx> &d) {
     g.sp = to_float(d.sp); g.t = to_float(d.t); g.sq = to_float(d.sq); g.amp = to_float(d.amp);
     g.rho_g = to_float(d.rho_g); g.inv_f1 = to_float(d.inv_f1); g.inv_f2 = to_float(d.inv_f2);
     g.dperp = to_float(d.dperp); g.caus = d.caus;
+    g.dr = to_f3(d.dr);
     return g;
 }
 __device__ __forceinline__ dfl to_df(double x) {
@@ -1434,13 +1429,18 @@ __device__ __noinline__ int esc_r2(const Ctx &c, int i, int j, v3t<float> Pf, v3
     return d;
 }
 // body reflection decided and (field = true) evaluated in FP64
-__device__ __noinline__ int esc_rb(const Ctx &c, int b, v3t<float> Pf, const FreqC &fq, bool field, Contrib *out) {
+__device__ __noinline__ int esc_rb(const Ctx &c, int b, v3t<float> Pf, const FreqC &fq, bool field, Contrib *out,
+                                   float *rec) {
     Geo<dx> g;
     v3t<dx> Sd = dxv(c.S), Pd = dxv(Pf);
     Frame<dx> F;
     body_frame(c, b, Sd, Pd, dx(0.0), F);
     int d = cand_rb<dx>(c, b, Sd, Pd, dx(0.0), F, g);
-    if (d == D_YES && field) {
+    if (d == D_YES && rec) {
+        // the path record of the FP64 geometry (its field is summed with the
+        // FP32 records, frequency chunk by frequency chunk)
+        rb_prep(c, rec, c.S, to_f(g), to_df(to_double(seglen(Sd, g.Q1) + seglen(g.Q1, Pd))));
+    } else if (d == D_YES && field) {
         Acc<dx> a;
         acc_zero(a);
         field_body_refl<dx, dx, true>(c, a, fq, Sd, Pd, g, seglen(Sd, g.Q1) + seglen(g.Q1, Pd));
@@ -1450,7 +1450,8 @@ __device__ __noinline__ int esc_rb(const Ctx &c, int b, v3t<float> Pf, const Fre
 }
 // creeping ray decided, its caustic flag taken, and (field) evaluated in FP64
 __device__ __noinline__ int esc_creep(const Ctx &c, int b, int dir, v3t<float> Pf, const FreqC &fq, bool field,
-                                      double half_lambda_max, unsigned enable, Contrib *out, int *caustic) {
+                                      double half_lambda_max, unsigned enable, Contrib *out, int *caustic,
+                                      float *rec = nullptr, int *n_rec = nullptr) {
     Geo<dx> g;
     v3t<dx> Sd = dxv(c.S), Pd = dxv(Pf);
     Frame<dx> F;
@@ -1461,9 +1462,12 @@ __device__ __noinline__ int esc_creep(const Ctx &c, int b, int dir, v3t<float> P
     bool sphere = c.body[2 * b + 1].y == 0.0f;
     if (sphere) {
         *caustic = half_lambda_max > g.dperp.v;
-        if (!(g.dperp > dx(0.0))) field = false;     // exactly on the axis: no finite ray field
+        if (!(g.dperp > dx(0.0))) return d;          // exactly on the axis: no finite ray field
     }
-    if (field) {
+    if (rec) {
+        creep_prep(c, rec, c.S, Pf, to_f(g), to_df(to_double(g.sp + g.t + g.sq)), enable);
+        *n_rec = 1;
+    } else if (field) {
         Acc<dx> a;
         acc_zero(a);
         field_creep<dx, dx, true>(c, a, fq, Sd, Pd, g, g.sp + g.t + g.sq, enable);
@@ -1489,28 +1493,16 @@ constexpr int min_blocks(int cls, bool fp32) {
 }
 constexpr int WARPS_PER_TILE = 4;
 
-// Field pass over one lane's records for the frequency chunk fq; a candidate
-// decided in FP64 is re-evaluated in FP64 out of line.
-__device__ __noinline__ void apply_esc_record(const Ctx &c, AccS<float> &acc, const FreqC &fq, int tag, v3t<float> Pf,
-                                              double half_lambda_max, unsigned enable) {
-    const int kind = tag & 3, dir = (tag >> 2) & 1, b = tag >> 3;
-    Contrib ct;
-    int caus = 0;
-    int d = (kind == REC_ESC_RB) ? esc_rb(c, b, Pf, fq, true, &ct)
-                                 : esc_creep(c, b, dir, Pf, fq, true, half_lambda_max, enable, &ct, &caus);
-    if (d == D_YES) acc_add(acc, ct, fq.nf);
-}
+// Field pass over one lane's records for the frequency chunk fq.
 template <int CLS>
 __device__ __forceinline__ void apply_records(const Ctx &c, AccS<float> &acc, const FreqC &fq, const float *rec,
-                                              int nrec, v3t<float> Pf, double half_lambda_max, unsigned enable) {
+                                              int nrec) {
     constexpr bool RB = (CLS & CLS_BODYREFL) != 0, CP = (CLS & CLS_CREEP) != 0;
 #pragma unroll 1
     for (int j = 0; j < nrec; ++j) {
         const float *r = rec + j * REC_N * 32;
-        const float Lp = r[288];
-        if (RB && Lp > 0.0f) rb_apply(c, acc, fq, r);
-        else if (CP && Lp < 0.0f) creep_apply(c, acc, fq, r);
-        else apply_esc_record(c, acc, fq, __float_as_int(r[0]), Pf, half_lambda_max, enable);
+        if (RB && (!CP || r[288] > 0.0f)) rb_apply(c, acc, fq, r);
+        else if (CP) creep_apply(c, acc, fq, r);
     }
 }
 
@@ -1664,7 +1656,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                     // into fields here (with several chunks the caller sizes the
                     // body range so that they cannot)
                     if (may_flush && nrec > rcap - PER) {
-                        apply_records<CLS>(c, acc, fq, rec, nrec, Pf, half_lambda_max, enable);
+                        apply_records<CLS>(c, acc, fq, rec, nrec);
                         nrec = 0;
                     }
                 }
@@ -1681,13 +1673,14 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                                 // receiver at a surface); the Fock bracket stays FP32
                                 escalated();
                                 Contrib ct;
-                                // (with several frequency chunks its field is deferred to
-                                // the field passes as a tagged record)
+                                // (with several frequency chunks its field goes through a
+                                // record, as the FP32 candidates' do)
                                 const bool defer = RECS && !may_flush;
-                                d = esc_rb(c, b, Pf, fq, !PATHS && !defer, &ct);
+                                d = esc_rb(c, b, Pf, fq, !PATHS && !defer, &ct,
+                                           defer ? rec + nrec * REC_N * 32 : nullptr);
                                 if (d == D_YES) {
                                     emit(PT_RB, b, 0);
-                                    if (defer) rec_esc(rec + (nrec++) * REC_N * 32, REC_ESC_RB, 0, b);
+                                    if (defer) ++nrec;
                                     else if (!PATHS) acc_add(acc, ct, nf);
                                 }
                                 d = D_NO;
@@ -1722,12 +1715,13 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                                     Contrib ct;
                                     int caus = 0;
                                     const bool defer = RECS && !may_flush;
+                                    int added = 0;
                                     d = esc_creep(c, b, dir, Pf, fq, !PATHS && !defer, half_lambda_max, enable, &ct,
-                                                  &caus);
+                                                  &caus, defer ? rec + nrec * REC_N * 32 : nullptr, &added);
                                     if (d == D_YES) {
                                         emit(dir == 0 ? PT_CP : PT_CM, b, 0);
                                         if (caus) fl |= RT_FLAG_CAUSTIC;
-                                        if (defer) rec_esc(rec + (nrec++) * REC_N * 32, REC_ESC_CREEP, dir, b);
+                                        if (defer) nrec += added;
                                         else if (!PATHS) acc_add(acc, ct, nf);
                                     }
                                     continue;
@@ -1950,8 +1944,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                         }
                         if (rok) {
                             if (ch > ch0) acc_zero(acc);      // the geometry pass zeroed it for the first chunk
-                            apply_records<CLS>(c, acc, fq, rec, nrec, mk3(rx[r], rx[n_rx + r], rx[2 * n_rx + r]),
-                                               Fr.hl, S.enable);
+                            apply_records<CLS>(c, acc, fq, rec, nrec);
                         }
                     }
                     // the previous class kernel's fields and flags are complete (a
