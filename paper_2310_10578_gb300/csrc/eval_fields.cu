@@ -1155,6 +1155,21 @@ __device__ __forceinline__ void add_ray(ACC &acc, const FreqC &fq, v3t<T> e, T a
         acc_put(acc, f, ph * e.x, ph * e.y, ph * e.z);
     }
 }
+// the same ray for nfq frequency chunks fqs[0 .. nfq - 1], whose partial sums
+// follow one another (NFC * 6 rows each)
+template <typename T, typename L>
+__device__ __forceinline__ void add_ray_chunks(AccS<T> &acc, const FreqC *fqs, int nfq, v3t<T> e, T amp, L len) {
+#pragma unroll 1
+    for (int k = 0; k < nfq; ++k) {
+        AccS<T> a{acc.p + k * (NFC * 6 * 32)};
+        add_ray(a, fqs[k], e, amp, len);
+    }
+}
+template <typename T>
+__device__ __forceinline__ void acc_zero_rows(AccS<T> &acc, int rows) {
+#pragma unroll 4
+    for (int j = 0; j < rows; ++j) acc.p[32 * j] = T(0.0);
+}
 
 template <typename T, typename L, bool F32FOCK = false, typename ACC = Acc<T>>
 __device__ void field_body_refl(const Ctx &c, ACC &acc, const FreqC &fq, v3t<T> S, v3t<T> P, const Geo<T> &g, L len) {
@@ -1492,6 +1507,8 @@ constexpr int min_blocks(int cls, bool fp32) {
     return ((cls & (CLS_BODYREFL | CLS_CREEP)) && fp32) ? 1 : (cls == CLS_PLANAR ? 4 : 3);
 }
 constexpr int WARPS_PER_TILE = 4;
+constexpr int MAX_CHUNKS = (RT_MAX_FREQS + NFC - 1) / NFC;
+constexpr int PLANAR_CHUNKS = 4;       // frequency chunks per planar launch (FP32 fields)
 
 // Field pass over one lane's records for the frequency chunk fq.
 template <int CLS>
@@ -1513,7 +1530,7 @@ __device__ __forceinline__ void apply_records(const Ctx &c, AccS<float> &acc, co
 // b mod nparts -- summed into acc; the receiver's flags, the count of FP64
 // re-decisions and (PATHS) the path codes from slot npath on.
 template <typename T, bool PATHS, int CLS>
-__device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, unsigned enable, int max_order,
+__device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, int nfq, unsigned enable, int max_order,
                                               const float *__restrict__ rx, int n_rx, int r,
                                               uint64_t *__restrict__ codes, int cap, double half_lambda_max,
                                               int b_begin, int b_end, bool first_chunk, bool may_flush, int rcap,
@@ -1523,6 +1540,9 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     const bool fp32 = sizeof(T) == 4;
     const T band = fp32 ? T(c.band) : T(0);
+    // fqs[0]: the frequency chunk of the body classes' fields; the planar
+    // rays take all nfq chunks (each with its own partial sums)
+    const FreqC &fq = fqs[0];
     const int nf = fq.nf;
     v3t<float> Pf = mk3(rx[r], rx[n_rx + r], rx[2 * n_rx + r]);
     v3t<T> P = mk3<T>(T((double)Pf.x), T((double)Pf.y), T((double)Pf.z));
@@ -1530,7 +1550,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
     fl = 0;
     nesc = 0;
     nrec_out = 0;
-    if (!PATHS) acc_zero(acc);
+    if (!PATHS) acc_zero_rows(acc, nfq * NFC * 6);
     typedef typename LenOf<T>::type LT;
 
     auto emit = [&](int type, int a, int b) {
@@ -1580,7 +1600,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                     emit(PT_LOS, 0, 0);
                     if (!PATHS) {
                         LT L = seglen(Sx, P);
-                        add_ray(acc, fq, src_pol(c, unit3(P - Sx)), T(1) / (T)len_val(L), L);
+                        add_ray_chunks(acc, fqs, nfq, src_pol(c, unit3(P - Sx)), T(1) / (T)len_val(L), L);
                     }
                 }
             }
@@ -1602,7 +1622,8 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                             LT L;
                             if constexpr (sizeof(T) == 4) L = df_dist_df(c.img[2 * i], c.img[2 * i + 1], Pf);
                             else L = ladd(seglen(Sx, g.Q1), seglen(g.Q1, P));
-                            add_ray(acc, fq, pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni), T(1) / (T)len_val(L), L);
+                            add_ray_chunks(acc, fqs, nfq, pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni),
+                                           T(1) / (T)len_val(L), L);
                         }
                     }
                 }
@@ -1633,7 +1654,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
                                     L = ladd(ladd(seglen(Sx, g.Q1), seglen(g.Q1, g.Q2)), seglen(g.Q2, P));
                                 }
                                 v3t<T> e = pec_mirror(pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni), nj);
-                                add_ray(acc, fq, e, T(1) / (T)len_val(L), L);
+                                add_ray_chunks(acc, fqs, nfq, e, T(1) / (T)len_val(L), L);
                             }
                         }
                     }
@@ -1747,6 +1768,12 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC &fq, uns
     }
 }
 
+// copy n bytes (a multiple of 4) from global to shared memory, all threads
+__device__ __forceinline__ void stage_words(void *dst, const void *src, int n) {
+    for (int i = threadIdx.x; i < n / 4; i += blockDim.x)
+        static_cast<uint32_t *>(dst)[i] = static_cast<const uint32_t *>(src)[i];
+}
+
 template <typename T, bool PATHS, int CLS>
 __global__ void __launch_bounds__(blk_of(CLS, sizeof(T) == 4), min_blocks(CLS, sizeof(T) == 4))
 k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frames, unsigned long long n_tiles,
@@ -1756,7 +1783,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     extern __shared__ float4 smem[];
     __shared__ Ctx s_ctx;
-    __shared__ FreqC s_fq;
+    __shared__ FreqC s_fqs[MAX_CHUNKS];        // frequency chunks ch0 .. ch0 + nch - 1
     // stage scene (and, for the body classes, the Fock--Pekeris table)
     const int n_fock = BODIES ? FOCK_N * 2 : 0, n_res = BODIES ? FOCK_NRES * 2 : 0;
     float4 *s_fock = smem;                                   // n_fock
@@ -1773,9 +1800,10 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
     for (int i = threadIdx.x; i < n_fock; i += blockDim.x) s_fock[i] = S.fock32[i];
     for (int i = threadIdx.x; i < n_res; i += blockDim.x) s_res[i] = S.res32[i];
     for (int i = threadIdx.x; i < S.n_face; i += blockDim.x) s_face[i] = S.face32[i];
-    // the frame's bodies and source-side body frames (one frame: F1; a
-    // batch: staged again whenever the block's next work unit is in another
-    // frame)
+    // the frame's bodies, source-side body frames and frequency chunks (one
+    // frame: F1; a batch: staged again whenever the block's next work unit is
+    // in another frame)
+    if (!frames) stage_words(s_fqs, F1.fqc + ch0, nch * sizeof(FreqC));
     if (body_sm && !frames)
         for (int i = threadIdx.x; i < 2 * F1.n_body; i += blockDim.x) {
             s_body[i] = F1.body[i];
@@ -1805,7 +1833,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
         c.img = S.img;
         c.txb = body_sm ? s_txb : F1.txb;
-        if (!frames) s_fq = F1.fqc[ch0];
+
     }
     __syncthreads();
     // the next class kernel (launched as a programmatic dependent) may start
@@ -1814,7 +1842,6 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
     asm volatile("griddepcontrol.launch_dependents;");
 
     const Ctx &c = s_ctx;
-    const FreqC &fq = s_fq;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int NW = blk_of(CLS, sizeof(T) == 4) / 32;
     if constexpr (PATHS) {
@@ -1838,7 +1865,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                 unsigned nesc;
                 int npath = accumulate ? counts[r] : 0;
                 int nrec;
-                eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap, F1.hl,
+                eval_receiver<T, PATHS, CLS>(c, s_fqs, 1, S.enable, S.max_order, rx, n_rx, r, codes, cap, F1.hl,
                                              0, c.n_body, true, false, 0, 0, 1, acc, nullptr, fl, nesc, npath, nrec);
                 counts[r] = npath;
                 if (fl_base) fl_base[r] = accumulate ? (fl_base[r] | fl) : fl;
@@ -1867,7 +1894,14 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         constexpr int PER = ((CLS & CLS_CREEP) ? 2 : 0) + ((CLS & CLS_BODYREFL) ? 1 : 0);
         const unsigned long long n_units = (n_tiles + TPB - 1) / TPB;
         const int grp = warp / NWT, part = warp % NWT;
-        __shared__ T s_part[NW][NFC * 6][32];
+        // partial sums of each warp: NFC * 6 rows of 32 lanes; the FP32
+        // planar kernel ("wide") keeps the rows of all nch chunks at once in
+        // the dynamic region (it has no path records), so one geometry pass
+        // serves every chunk
+        constexpr bool WIDE = (CLS == CLS_PLANAR) && sizeof(T) == 4;
+        __shared__ T s_part_st[NW][WIDE ? 1 : NFC * 6][32];
+        const int prow = WIDE ? nch * NFC * 6 : NFC * 6;
+        T *s_part = WIDE ? reinterpret_cast<T *>(s_rec) : &s_part_st[0][0][0];
         __shared__ uint32_t s_fl[NW][32];
         __shared__ unsigned long long s_unit;
         __shared__ int s_fi, s_new;
@@ -1899,12 +1933,12 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                         s_body[i] = s_fr.body[i];
                         s_txb[i] = s_fr.txb[i];
                     }
+                stage_words(s_fqs, s_fr.fqc + ch0, nch * sizeof(FreqC));
                 if (threadIdx.x == 0) {
                     s_ctx.body = body_sm ? s_body : s_fr.body;
                     s_ctx.txb = body_sm ? s_txb : s_fr.txb;
                     s_ctx.n_body = s_fr.n_body;
                     s_ctx.band = s_fr.band;
-                    s_fq = s_fr.fqc[ch0];
                 }
                 __syncthreads();
             }
@@ -1921,7 +1955,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
             const long long r0 = (long long)(t * 32ull);
             const int r = r0 < n_rx ? (int)r0 + lane : n_rx;
             const bool rok = r < n_rx;
-            AccS<T> acc{&s_part[warp][0][lane]};     // the warp's partial sums, summed in place
+            AccS<T> acc{s_part + warp * prow * 32 + lane};     // the warp's partial sums, summed in place
             float *rec = s_rec + warp * (rcap * REC_N * 32) + lane;
 #pragma unroll 1
             for (int b0 = 0; b0 < (n_b > 0 ? n_b : 1); b0 += bc) {
@@ -1929,22 +1963,19 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                 unsigned nesc = 0;
                 int npath = 0, nrec = 0;
                 if (rok)
-                    eval_receiver<T, PATHS, CLS>(c, fq, S.enable, S.max_order, rx, n_rx, r, codes, cap,
+                    eval_receiver<T, PATHS, CLS>(c, s_fqs, WIDE ? nch : 1, S.enable, S.max_order, rx, n_rx, r, codes, cap,
                                                  Fr.hl, b0, min(b0 + bc, n_b), b0 == 0, nch == 1, rcap, part,
                                                  NWT, acc, rec, fl, nesc, npath, nrec);
                 s_fl[warp][lane] = fl;
                 if (nesc && ch0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
 #pragma unroll 1
                 for (int ch = ch0; ch < ch0 + nch; ++ch) {
+                    const FreqC &fqc = s_fqs[ch - ch0];
                     if constexpr (RECS) {
                         __syncthreads();              // geometry pass / previous reduction done
-                        if (nch > 1) {                // (one chunk: staged with the frame)
-                            if (threadIdx.x == 0) s_fq = Fr.fqc[ch];
-                            __syncthreads();
-                        }
                         if (rok) {
                             if (ch > ch0) acc_zero(acc);      // the geometry pass zeroed it for the first chunk
-                            apply_records<CLS>(c, acc, fq, rec, nrec);
+                            apply_records<CLS>(c, acc, fqc, rec, nrec);
                         }
                     }
                     // the previous class kernel's fields and flags are complete (a
@@ -1957,12 +1988,13 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                     if (rok) {
                         const int w0 = grp * NWT, f0 = ch * NFC;
                         const bool add = accumulate || b0 > 0;
-                        for (int j = part; j < fq.nf * 3; j += NWT) {
-                            T re = s_part[w0][2 * j][lane], im = s_part[w0][2 * j + 1][lane];
+                        const T *pp = s_part + (WIDE ? (ch - ch0) * NFC * 6 * 32 : 0) + lane;
+                        for (int j = part; j < fqc.nf * 3; j += NWT) {
+                            T re = pp[(w0 * prow + 2 * j) * 32], im = pp[(w0 * prow + 2 * j + 1) * 32];
 #pragma unroll
                             for (int w = 1; w < NWT; ++w) {
-                                re = re + s_part[w0 + w][2 * j][lane];
-                                im = im + s_part[w0 + w][2 * j + 1][lane];
+                                re = re + pp[((w0 + w) * prow + 2 * j) * 32];
+                                im = im + pp[((w0 + w) * prow + 2 * j + 1) * 32];
                             }
                             size_t idx = ((size_t)(f0 + j / 3) * 3 + (j % 3)) * n_rx + r;
                             float2 v;
@@ -1989,12 +2021,15 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
     }
 }
 
-static size_t smem_bytes(const DevScene &S, bool bodies, bool records, int blk, int rcap) {
+// dynamic shared memory of a launch: scene, tables, then the path records
+// (body classes) or the wide partial sums of wide_chunks chunks (planar)
+static size_t smem_bytes(const DevScene &S, bool bodies, bool records, int blk, int rcap, int wide_chunks) {
     size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + S.n_face;
     if (S.n_body <= SMEM_BODY_MAX) n += 4 * S.n_body;
     if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;
     return n * sizeof(float4) + WEIDEMAN_N * sizeof(float) + 16 +
-           (records ? sizeof(float) * (blk / 32) * rcap * REC_N * 32 : 0);
+           (records ? sizeof(float) * (blk / 32) * rcap * REC_N * 32 : 0) +
+           sizeof(float) * (blk / 32) * wide_chunks * NFC * 6 * 32;
 }
 
 // Launch state of one evaluation: the counters (escalations, one work queue
@@ -2028,7 +2063,9 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     // records per lane: one frequency chunk flushes full buffers on the way
     // (5 is enough); several chunks size the body range by the capacity
     const int rcap = (nch > 1) ? 6 : 5;
-    size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk, rcap);
+    const bool wide = CLS == CLS_PLANAR && sizeof(T) == 4 && !PATHS;
+    if (nch < 1 || nch > MAX_CHUNKS || (!wide && !bodies && nch != 1)) return cudaErrorInvalidValue;
+    size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk, rcap, wide ? nch : 0);
     cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     // persistent grid: the blocks that fit on the device at once, at most
@@ -2062,14 +2099,19 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
 
 // The class kernels of one evaluation.  Path lists and FP64 fields: the
 // three classes per frequency chunk.  FP32 fields: the planar kernel per
-// chunk, then each body kernel once for all chunks (its geometry is reused).
+// PLANAR_CHUNKS chunks, then each body kernel once for all chunks (the
+// geometry of a pass serves every chunk it covers).
 // The first launch writes the outputs, the later ones add to them.
 template <typename T, bool PATHS>
 static cudaError_t launch_all(const DevScene &S, const Work &W, int nchunks, LaunchCtx &L) {
     cudaError_t e = cudaSuccess;
     const bool chunked_bodies = PATHS || sizeof(T) != 4;
-    for (int ch = 0; ch < nchunks && e == cudaSuccess; ++ch) {
-        e = launch_one<T, PATHS, CLS_PLANAR>(S, W, ch, 1, 0, L);
+    // FP32 fields: each planar launch takes up to PLANAR_CHUNKS chunks in one
+    // geometry pass
+    const int pstep = chunked_bodies ? 1 : PLANAR_CHUNKS;
+    for (int ch = 0; ch < nchunks && e == cudaSuccess; ch += pstep) {
+        const int n = nchunks - ch < pstep ? nchunks - ch : pstep;
+        e = launch_one<T, PATHS, CLS_PLANAR>(S, W, ch, n, 0, L);
         if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL>(S, W, ch, 1, 1, L);
         if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_CREEP>(S, W, ch, 1, 1, L);
     }
