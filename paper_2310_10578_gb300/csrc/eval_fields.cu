@@ -65,6 +65,11 @@ struct Ctx {
     const double *weid64;
     const float4 *img;           // source images (double-float), see DevScene
     const float4 *txb;           // [n_body][2] source-side body frame, see DevScene
+    // occluder masks (FP32 body kernels): occ_w words per body; word w of
+    // body b's source-side mask has bit j set if body j may block a segment
+    // from the source to a point of body b (occ_w = 0: no masks)
+    const uint32_t *occ_src;
+    int occ_w;
 };
 
 template <typename T>
@@ -285,8 +290,74 @@ __device__ __forceinline__ int blocked_impl(const Ctx &c, v3t<T> A, v3t<T> B, in
 __device__ __noinline__ int blocked(const Ctx &c, v3t<float> A, v3t<float> B, int sf1, int sf2, int sb, float band) {
     return blocked_impl(c, A, B, sf1, sf2, sb, band);
 }
+// A leg between a point of body sb and the source or a receiver (FP32): the
+// faces as in blocked; the bodies are those of the occluder mask occ (a
+// superset of the bodies that can pass the distance test), or all.
+__device__ __noinline__ int blocked_occ(const Ctx &c, v3t<float> A, v3t<float> B, int sb, float band,
+                                        const uint32_t *occ) {
+    if (!occ) return blocked_impl(c, A, B, -1, -1, sb, band);
+    int uns = 0;
+    for (int f0 = 0; f0 < c.n_face; f0 += 32) {
+        unsigned keep = 0;
+        const int nfc = min(32, c.n_face - f0);
+#pragma unroll 4
+        for (int k = 0; k < nfc; ++k) {
+            float4 q = c.face32[f0 + k];
+            float sA = q.x * A.x + q.y * A.y + q.z * A.z - q.w, sB = q.x * B.x + q.y * B.y + q.z * B.z - q.w;
+            bool cull = (sA > band && sB > band) || (sA < -band && sB < -band);
+            keep |= cull ? 0u : (1u << k);
+        }
+        while (keep) {
+            const int f = f0 + __ffs(keep) - 1;
+            keep &= keep - 1;
+            int2 rg = c.face_rng[f];
+            for (int i = 0; i < rg.y; ++i) {
+                int r = seg_tri(c, c.face_tris[rg.x + i], A, B, band);
+                if (r == D_YES) return D_YES;
+                uns |= (r == D_UNSURE);
+            }
+        }
+    }
+    const v3t<float> D = B - A;
+    const float qa = D.x * D.x + D.y * D.y;
+    const float iqa = (qa > 0.0f) ? 1.0f / qa : 0.0f;
+    const float idd = 1.0f / (qa + D.z * D.z);
+    const float tlo = (float)EPS_TRIM, thi = 1.0f - (float)EPS_TRIM;
+#pragma unroll 1
+    for (int w = 0; w < c.occ_w; ++w) {
+        unsigned cand = occ[w];
+        if (sb >> 5 == w) cand &= ~(1u << (sb & 31));
+        while (cand) {
+            const int b = 32 * w + __ffs(cand) - 1;
+            cand &= cand - 1;
+            const float4 q0 = c.body[2 * b];
+            const bool sph = c.body[2 * b + 1].y == 0.0f;
+            const float wx = q0.x - A.x, wy = q0.y - A.y, wz = sph ? q0.z - A.z : 0.0f;
+            const float dz = sph ? D.z : 0.0f;
+            const float t = fminf(fmaxf((wx * D.x + wy * D.y + wz * dz) * (sph ? idd : iqa), tlo), thi);
+            const float hx = D.x * t - wx, hy = D.y * t - wy, hz = dz * t - wz;
+            const float ab = q0.w + band;
+            if (hx * hx + hy * hy + hz * hz <= ab * ab) {
+                int r = seg_body(c, b, A, B, band);
+                if (r == D_YES) return D_YES;
+                uns |= (r == D_UNSURE);
+            }
+        }
+    }
+    return uns ? D_UNSURE : D_NO;
+}
 __device__ __noinline__ int blocked(const Ctx &c, v3t<dx> A, v3t<dx> B, int sf1, int sf2, int sb, dx band) {
     return blocked_impl(c, A, B, sf1, sf2, sb, band);
+}
+// a leg from or to a point of body b; FP32 legs take the occluder mask occ
+// (nullptr: every body)
+template <typename T>
+__device__ __forceinline__ int blocked_leg(const Ctx &c, v3t<T> A, v3t<T> B, int b, T band, const uint32_t *occ) {
+    if constexpr (sizeof(T) == 4) return blocked_occ(c, A, B, b, band, occ);
+    else return blocked(c, A, B, -1, -1, b, band);
+}
+__device__ __forceinline__ const uint32_t *occ_of(const Ctx &c, const uint32_t *masks, int b) {
+    return (masks && c.occ_w) ? masks + b * c.occ_w : nullptr;
 }
 
 // point (on the triangle's plane) inside the closed triangle
@@ -724,7 +795,8 @@ __device__ __forceinline__ dfl df_norm3(const dfl w[3]) {
 
 // body reflection candidate (sphere or vertical cylinder)
 template <typename T>
-__device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Frame<T> &F, Geo<T> &g) {
+__device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Frame<T> &F, Geo<T> &g,
+                       const uint32_t *occ_rx = nullptr) {
     float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
     T a = q0.w;
     int acc = F.dec;
@@ -764,8 +836,8 @@ __device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Fr
     }
     v3t<T> shi = unit3(Q - S);
     T cth = -dot3(shi, n);
-    if (!conj(acc, vis_to_dec(blocked(c, S, Q, -1, -1, b, band)))) return D_NO;
-    if (!conj(acc, vis_to_dec(blocked(c, Q, P, -1, -1, b, band)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked_leg(c, S, Q, b, band, occ_of(c, c.occ_src, b))))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked_leg(c, Q, P, b, band, occ_of(c, occ_rx, b))))) return D_NO;
     if constexpr (sizeof(T) == 4) {
         // total length s^i + s^r to the FP32 surface point c + a n, each leg in
         // double-float (the length is stationary in psi, so the FP32 root and
@@ -804,7 +876,8 @@ __device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Fr
 
 // creeping candidate, dir 0 short way, 1 long way
 template <typename T>
-__device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T band, const Frame<T> &F, Geo<T> &g) {
+__device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T band, const Frame<T> &F, Geo<T> &g,
+                          const uint32_t *occ_rx = nullptr) {
     float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
     T a = q0.w;
     bool sphere = (q1.y == 0.0f);
@@ -859,8 +932,8 @@ __device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T ba
         g.dperp = T(0);
         g.amp = T(1) / Sqrt(g.sp * g.sq * (g.sp + g.t + g.sq));
     }
-    if (!conj(acc, vis_to_dec(blocked(c, S, g.Q1, -1, -1, b, band)))) return D_NO;
-    if (!conj(acc, vis_to_dec(blocked(c, g.Q2, P, -1, -1, b, band)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked_leg(c, S, g.Q1, b, band, occ_of(c, c.occ_src, b))))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked_leg(c, g.Q2, P, b, band, occ_of(c, occ_rx, b))))) return D_NO;
     return acc;
 }
 
@@ -1509,6 +1582,7 @@ constexpr int min_blocks(int cls, bool fp32) {
 constexpr int WARPS_PER_TILE = 4;
 constexpr int MAX_CHUNKS = (RT_MAX_FREQS + NFC - 1) / NFC;
 constexpr int PLANAR_CHUNKS = 4;       // frequency chunks per planar launch (FP32 fields)
+constexpr int OCC_MAX_BODIES = 256;    // occluder masks up to this many bodies (FP32 body kernels)
 
 // Field pass over one lane's records for the frequency chunk fq.
 template <int CLS>
@@ -1534,7 +1608,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                                               const float *__restrict__ rx, int n_rx, int r,
                                               uint64_t *__restrict__ codes, int cap, double half_lambda_max,
                                               int b_begin, int b_end, bool first_chunk, bool may_flush, int rcap,
-                                              int part, int nparts,
+                                              const uint32_t *occ_rx, int part, int nparts,
                                               AccS<T> acc, float *rec, uint32_t &fl, unsigned &nesc, int &npath,
                                               int &nrec_out) {
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
@@ -1686,7 +1760,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                 if constexpr ((CLS & CLS_BODYREFL) != 0) {
                     if (enable & RT_EN_BODYREFL) {
                         Geo<T> g;
-                        int d = cand_rb<T>(c, b, Sx, P, band, F, g);
+                        int d = cand_rb<T>(c, b, Sx, P, band, F, g, occ_rx);
                         if constexpr (sizeof(T) == 4) {
                             if (d == D_UNSURE) {
                                 // decided in FP64, and its geometry, length and amplitude
@@ -1723,7 +1797,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
 #pragma unroll 1
                         for (int dir = 0; dir < 2; ++dir) {
                             Geo<T> g;
-                            int d = cand_creep<T>(c, b, dir, Sx, P, band, F, g);
+                            int d = cand_creep<T>(c, b, dir, Sx, P, band, F, g, occ_rx);
                             int cd = D_NO;
                             if (d == D_YES && sphere) {
                                 // axial caustic flag: k d_perp < pi for some frequency, i.e. d_perp < lambda_max / 2
@@ -1764,6 +1838,57 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                 }
             }
             nrec_out = nrec;
+        }
+    }
+}
+
+// ---- occluder masks.  A leg of a body path runs between a point of body b
+// and the source or a receiver; in projection on the floor it lies in the
+// convex hull of body b's disk (centre c_b, radius a_b) and of that end's
+// region R, here a disk of radius rr round a segment T0 T1.  That hull lies
+// within the triangle (T0, T1, c_b) grown by max(rr, a_b), so a body j whose
+// disk (grown by the band and a margin for the FP32 arithmetic of this test)
+// misses it cannot pass the distance test of the visibility loop for any
+// such leg (projection shortens distances), and is left out of the mask.
+__device__ __forceinline__ float seg_d2(float px, float py, float ax, float ay, float bx, float by) {
+    const float dx = bx - ax, dy = by - ay, wx = px - ax, wy = py - ay;
+    const float dd = dx * dx + dy * dy;
+    const float t = dd > 0.0f ? fminf(fmaxf((wx * dx + wy * dy) / dd, 0.0f), 1.0f) : 0.0f;
+    const float hx = wx - t * dx, hy = wy - t * dy;
+    return hx * hx + hy * hy;
+}
+// squared distance from p to the triangle (a, b, c); 0 inside or degenerate
+__device__ __forceinline__ float tri_d2(float px, float py, float ax, float ay, float bx, float by, float cx,
+                                        float cy) {
+    const float d1 = (bx - ax) * (py - ay) - (by - ay) * (px - ax);
+    const float d2 = (cx - bx) * (py - by) - (cy - by) * (px - bx);
+    const float d3 = (ax - cx) * (py - cy) - (ay - cy) * (px - cx);
+    const bool neg = d1 < 0.0f || d2 < 0.0f || d3 < 0.0f, pos = d1 > 0.0f || d2 > 0.0f || d3 > 0.0f;
+    if (!(neg && pos)) return 0.0f;
+    return fminf(seg_d2(px, py, ax, ay, bx, by), fminf(seg_d2(px, py, bx, by, cx, cy), seg_d2(px, py, cx, cy, ax, ay)));
+}
+// masks of every body for the region (T0, T1, rr): out[b * occ_w + w]; the
+// calling warp (index wi of nwarps that share the work) takes bodies wi,
+// wi + nwarps, ...; every lane of the warp takes part
+__device__ __noinline__ void occ_masks(const Ctx &c, float t0x, float t0y, float t1x, float t1y, float rr, uint32_t *out, int wi,
+                          int nwarps) {
+    const int lane = threadIdx.x & 31, nb = c.n_body;
+    const float margin = 1e-3f + 8.0f * c.band;
+#pragma unroll 1
+    for (int b = wi; b < nb; b += nwarps) {
+        const float4 qb = c.body[2 * b];
+        const float rad = fmaxf(rr, qb.w) + c.band + margin;
+#pragma unroll 1
+        for (int w = 0; w < c.occ_w; ++w) {
+            const int j = 32 * w + lane;
+            bool hit = false;
+            if (j < nb && j != b) {
+                const float4 qj = c.body[2 * j];
+                const float lim = rad + qj.w;
+                hit = tri_d2(qj.x, qj.y, t0x, t0y, t1x, t1y, qb.x, qb.y) <= lim * lim;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, hit);
+            if (lane == 0) out[b * c.occ_w + w] = m;
         }
     }
 }
@@ -1833,6 +1958,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
         c.img = S.img;
         c.txb = body_sm ? s_txb : F1.txb;
+        c.occ_src = nullptr;
+        c.occ_w = 0;
 
     }
     __syncthreads();
@@ -1866,7 +1993,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                 int npath = accumulate ? counts[r] : 0;
                 int nrec;
                 eval_receiver<T, PATHS, CLS>(c, s_fqs, 1, S.enable, S.max_order, rx, n_rx, r, codes, cap, F1.hl,
-                                             0, c.n_body, true, false, 0, 0, 1, acc, nullptr, fl, nesc, npath, nrec);
+                                             0, c.n_body, true, false, 0, nullptr, 0, 1, acc, nullptr, fl, nesc, npath,
+                                             nrec);
                 counts[r] = npath;
                 if (fl_base) fl_base[r] = accumulate ? (fl_base[r] | fl) : fl;
                 if (nesc) atomicAdd(esc_counter, (unsigned long long)nesc);
@@ -1906,10 +2034,21 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         __shared__ unsigned long long s_unit;
         __shared__ int s_fi, s_new;
         __shared__ FrameDev s_fr;
+        // occluder masks (FP32 body kernels): the source side per frame, the
+        // receiver side per tile, after the path records
+        constexpr bool OCC = BODIES && sizeof(T) == 4;
+        const bool occ_on = OCC && S.n_body > 0 && S.n_body <= OCC_MAX_BODIES;
+        const int occ_w = occ_on ? (S.n_body + 31) >> 5 : 0;
+        uint32_t *s_occ_src = reinterpret_cast<uint32_t *>(s_rec + (RECS ? NW * rcap * REC_N * 32 : 0));
+        uint32_t *s_occ_rx = s_occ_src + S.n_body * occ_w;
         if (threadIdx.x == 0) {
             s_fi = -1;
             if (!frames) s_fr = F1;
+            s_ctx.occ_src = occ_on ? s_occ_src : nullptr;
+            s_ctx.occ_w = occ_w;
         }
+        __syncthreads();
+        if (occ_on && !frames) occ_masks(c, c.S.x, c.S.y, c.S.x, c.S.y, 0.0f, s_occ_src, warp, NW);
         for (;;) {
             if (threadIdx.x == 0) {
                 const unsigned long long u = atomicAdd(queue, 1ull);
@@ -1941,6 +2080,10 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                     s_ctx.band = s_fr.band;
                 }
                 __syncthreads();
+                if (occ_on) {
+                    occ_masks(c, c.S.x, c.S.y, c.S.x, c.S.y, 0.0f, s_occ_src, warp, NW);
+                    __syncthreads();
+                }
             }
             const FrameDev &Fr = s_fr;
             const int n_rx = Fr.n_rx;
@@ -1955,6 +2098,30 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
             const long long r0 = (long long)(t * 32ull);
             const int r = r0 < n_rx ? (int)r0 + lane : n_rx;
             const bool rok = r < n_rx;
+            if (occ_on) {
+                // the tile's region: its receivers' bounding box, as a disk of
+                // radius rr round the box's longer midline T0 T1.  Each warp
+                // makes the masks of the bodies of its own share (b = part
+                // mod NWT), so no other warp waits for them.
+                float x0 = rok ? rx[r] : INFINITY, y0 = rok ? rx[n_rx + r] : INFINITY;
+                float x1 = rok ? x0 : -INFINITY, y1 = rok ? y0 : -INFINITY;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+                    y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+                    x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+                    y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+                }
+                if (x0 <= x1) {
+                    const float xm = 0.5f * (x0 + x1), ym = 0.5f * (y0 + y1);
+                    const bool along_x = (x1 - x0) >= (y1 - y0);
+                    // (half the shorter side, rounded up by a relative 1e-6 for the midpoint's rounding)
+                    const float rr = (along_x ? 0.5f * (y1 - y0) : 0.5f * (x1 - x0)) * 1.000001f;
+                    occ_masks(c, along_x ? x0 : xm, along_x ? ym : y0, along_x ? x1 : xm, along_x ? ym : y1, rr,
+                              s_occ_rx + grp * S.n_body * occ_w, part, NWT);
+                }
+                __syncwarp();
+            }
             AccS<T> acc{s_part + warp * prow * 32 + lane};     // the warp's partial sums, summed in place
             float *rec = s_rec + warp * (rcap * REC_N * 32) + lane;
 #pragma unroll 1
@@ -1964,7 +2131,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                 int npath = 0, nrec = 0;
                 if (rok)
                     eval_receiver<T, PATHS, CLS>(c, s_fqs, WIDE ? nch : 1, S.enable, S.max_order, rx, n_rx, r, codes, cap,
-                                                 Fr.hl, b0, min(b0 + bc, n_b), b0 == 0, nch == 1, rcap, part,
+                                                 Fr.hl, b0, min(b0 + bc, n_b), b0 == 0, nch == 1, rcap,
+                                                 occ_on ? s_occ_rx + grp * S.n_body * occ_w : nullptr, part,
                                                  NWT, acc, rec, fl, nesc, npath, nrec);
                 s_fl[warp][lane] = fl;
                 if (nesc && ch0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
@@ -2027,9 +2195,12 @@ static size_t smem_bytes(const DevScene &S, bool bodies, bool records, int blk, 
     size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + S.n_face;
     if (S.n_body <= SMEM_BODY_MAX) n += 4 * S.n_body;
     if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;
+    const int occ_w = (records && S.n_body > 0 && S.n_body <= OCC_MAX_BODIES) ? (S.n_body + 31) >> 5 : 0;
+    const int tpb = (blk / 32) / WARPS_PER_TILE;
     return n * sizeof(float4) + WEIDEMAN_N * sizeof(float) + 16 +
            (records ? sizeof(float) * (blk / 32) * rcap * REC_N * 32 : 0) +
-           sizeof(float) * (blk / 32) * wide_chunks * NFC * 6 * 32;
+           sizeof(float) * (blk / 32) * wide_chunks * NFC * 6 * 32 +
+           sizeof(uint32_t) * (size_t)S.n_body * occ_w * (1 + tpb);
 }
 
 // Launch state of one evaluation: the counters (escalations, one work queue
