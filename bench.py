@@ -290,8 +290,8 @@ def batched_crowd(args, creep, dev, flush, peak_fn):
     stats = B.stats()
     res = {"workload": cw.name, "value": samples / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
            "steps": args.batched_steps, "frames": cw.n_frames, "n_rx_total": B.total_rx, "n_freq": n_f,
-           "launch": "captured CUDA graph: counter reset + %d kernels (planar, body reflection, creeping)"
-                     % stats["kernel_launches"],
+           "launch": "captured CUDA graph: counter resets + %d kernels (receiver spatial order: 3; planar, body "
+                     "reflection, creeping)" % stats["kernel_launches"],
            "gpu_launches_per_step": stats["kernel_launches"],
            "fp64_escalated_candidates": stats["escalated_candidates"],
            "l2": "flushed between timed steps (256 MiB write)"}

@@ -131,6 +131,7 @@ struct rt_scene {
     bool tx_set = false, f_set = false;
     unsigned tx_version = 0;            // incremented by every rt_set_tx
     double tri_scale = 1.0;             // largest |coordinate| of the triangles (at least 1)
+    float plan[4] = {0.f, 0.f, 0.f, 0.f};   // floor plan of the triangles: x min, x max, y min, y max
     float tx[3], pol[3];
     std::vector<double> freqs;
     float band_len = 0.f;
@@ -353,6 +354,14 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
     double scale = 1.0;
     for (size_t i = 0; i < s->tri.size(); ++i) scale = fmax(scale, fabs((double)s->tri[i]));
     s->tri_scale = scale;
+    if (n_tri > 0) {
+        float bx0 = INFINITY, bx1 = -INFINITY, by0 = INFINITY, by1 = -INFINITY;
+        for (int t = 0; t < 3 * n_tri; ++t) {
+            bx0 = fminf(bx0, s->tri[3 * t]); bx1 = fmaxf(bx1, s->tri[3 * t]);
+            by0 = fminf(by0, s->tri[3 * t + 1]); by1 = fmaxf(by1, s->tri[3 * t + 1]);
+        }
+        s->plan[0] = bx0; s->plan[1] = bx1; s->plan[2] = by0; s->plan[3] = by1;
+    }
     int rcb = prep_bodies(s->bodies.data(), n_body, hb, scale);
     if (rcb != RT_OK) { delete s; return rcb; }
     s->band_len = band_of(scale);
@@ -602,6 +611,13 @@ struct rt_batch {
     FreqC *d_fqc = nullptr;                       // [n_frames][nch]
     FrameDev *d_frames = nullptr;                 // [n_frames]
     unsigned long long *d_ctr = nullptr;          // [CTR_N]
+    // spatial ordering of the receivers: cell counts [n_frames][RX_CELLS],
+    // ranks, the sorted receivers and the permutation [total receivers]
+    uint32_t *d_cnt = nullptr, *d_rank = nullptr;
+    float *d_rxs = nullptr;
+    int32_t *d_perm = nullptr;
+    long long total_rx = 0;
+    int max_rx = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t last_stream = nullptr;
@@ -612,6 +628,7 @@ static void free_batch(rt_batch *b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->graph) cudaGraphDestroy(b->graph);
     cudaFree(b->d_body); cudaFree(b->d_txb); cudaFree(b->d_fqc); cudaFree(b->d_frames); cudaFree(b->d_ctr);
+    cudaFree(b->d_cnt); cudaFree(b->d_rank); cudaFree(b->d_rxs); cudaFree(b->d_perm);
 }
 
 // queue one evaluation of the batch on st (no synchronisation)
@@ -634,8 +651,18 @@ static int batch_queue(rt_batch *b, const float *rx_soa, float *e_out, uint32_t 
     b->last_launches = 0;
     if (b->n_tiles == 0) return RT_OK;
     CK(cudaMemsetAsync(b->d_ctr, 0, sizeof(unsigned long long) * CTR_N, st));
-    return launch_eval_batch(D, b->d_frames, b->fr.data(), b->n_frames, b->n_tiles, rx_soa, e_out, flags, prec,
-                             b->d_ctr, st, &b->last_launches);
+    // receivers in a spatial order (grid over the floor plan of the scene's
+    // triangles, else a 100 m square round the origin), results in theirs
+    float x0 = s->plan[0], x1 = s->plan[1], y0 = s->plan[2], y1 = s->plan[3];
+    if (!(x1 > x0) || !(y1 > y0)) { x0 = -50.f; x1 = 50.f; y0 = -50.f; y1 = 50.f; }
+    float4 grid = make_float4(x0, y0, (float)RX_GRID / (x1 - x0), (float)RX_GRID / (y1 - y0));
+    rc = launch_rx_order(b->d_frames, b->n_frames, b->max_rx, rx_soa, grid, b->d_cnt, b->d_rank, b->d_rxs,
+                         b->d_perm, st);
+    if (rc != RT_OK) return rc;
+    rc = launch_eval_batch(D, b->d_frames, b->fr.data(), b->n_frames, b->n_tiles, b->d_rxs, b->d_perm, e_out, flags,
+                           prec, b->d_ctr, st, &b->last_launches);
+    if (rc == RT_OK) b->last_launches += 3;          // the ordering kernels
+    return rc;
 }
 
 extern "C" {
@@ -670,8 +697,10 @@ int rt_batch_create(rt_scene *s, int n_frames, const int32_t *n_rx, int n_f, int
         unsigned long long nt = ((unsigned long long)n_rx[f] + 31ull) >> 5;
         tile += (nt + TILE_ALIGN - 1) / TILE_ALIGN * TILE_ALIGN;
         rx_off += n_rx[f];
+        if (n_rx[f] > b->max_rx) b->max_rx = n_rx[f];
     }
     b->n_tiles = tile;
+    b->total_rx = rx_off;
     size_t nb = (size_t)n_frames * 2 * (max_body > 0 ? max_body : 1);
 #define CKB(x)                                                                  \
     do {                                                                        \
@@ -686,6 +715,13 @@ int rt_batch_create(rt_scene *s, int n_frames, const int32_t *n_rx, int n_f, int
     CKB(cudaMalloc(&b->d_fqc, sizeof(FreqC) * (size_t)n_frames * b->nch));
     CKB(cudaMalloc(&b->d_frames, sizeof(FrameDev) * (size_t)n_frames));
     CKB(cudaMalloc(&b->d_ctr, sizeof(unsigned long long) * CTR_N));
+    {
+        const size_t nr = (size_t)(rx_off > 0 ? rx_off : 1);
+        CKB(cudaMalloc(&b->d_cnt, sizeof(uint32_t) * (size_t)n_frames * RX_CELLS));
+        CKB(cudaMalloc(&b->d_rank, sizeof(uint32_t) * nr));
+        CKB(cudaMalloc(&b->d_rxs, sizeof(float) * 3 * nr));
+        CKB(cudaMalloc(&b->d_perm, sizeof(int32_t) * nr));
+    }
     for (int f = 0; f < n_frames; ++f) {
         FrameDev &F = b->fr[f];
         F.body = b->d_body + (size_t)f * 2 * (max_body > 0 ? max_body : 1);

@@ -1902,7 +1902,8 @@ __device__ __forceinline__ void stage_words(void *dst, const void *src, int n) {
 template <typename T, bool PATHS, int CLS>
 __global__ void __launch_bounds__(blk_of(CLS, sizeof(T) == 4), min_blocks(CLS, sizeof(T) == 4))
 k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frames, unsigned long long n_tiles,
-       const float *__restrict__ rx_base, float *__restrict__ e_base, uint32_t *__restrict__ fl_base,
+       const float *__restrict__ rx_base, const int32_t *__restrict__ perm, float *__restrict__ e_base,
+       uint32_t *__restrict__ fl_base,
        uint64_t *__restrict__ codes, int32_t *__restrict__ counts, int cap, int ch0, int nch, int rcap,
        int accumulate, unsigned long long *esc_counter, unsigned long long *queue) {
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
@@ -2155,6 +2156,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                     // (frequency, component) pairs j = p, p + NWT, ... of chunk ch
                     if (rok) {
                         const int w0 = grp * NWT, f0 = ch * NFC;
+                        const int ro = perm ? perm[Fr.rx_off + r] : r;       // the receiver's output slot
                         const bool add = accumulate || b0 > 0;
                         const T *pp = s_part + (WIDE ? (ch - ch0) * NFC * 6 * 32 : 0) + lane;
                         for (int j = part; j < fqc.nf * 3; j += NWT) {
@@ -2164,7 +2166,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                                 re = re + pp[((w0 + w) * prow + 2 * j) * 32];
                                 im = im + pp[((w0 + w) * prow + 2 * j + 1) * 32];
                             }
-                            size_t idx = ((size_t)(f0 + j / 3) * 3 + (j % 3)) * n_rx + r;
+                            size_t idx = ((size_t)(f0 + j / 3) * 3 + (j % 3)) * n_rx + ro;
                             float2 v;
                             v.x = to_float(re);
                             v.y = to_float(im);
@@ -2179,7 +2181,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                             uint32_t f_all = 0;
 #pragma unroll
                             for (int w = 0; w < NWT; ++w) f_all |= s_fl[w0 + w][lane];
-                            flags_out[r] = add ? (flags_out[r] | f_all) : f_all;
+                            flags_out[ro] = add ? (flags_out[ro] | f_all) : f_all;
                         }
                     }
                 }
@@ -2219,6 +2221,7 @@ struct Work {
     int n_frames;
     unsigned long long n_tiles;
     const float *rx;
+    const int32_t *perm;
     float *e;
     uint32_t *fl;
     uint64_t *codes;
@@ -2262,7 +2265,7 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = L.n > 0 ? 1 : 0;
-    e = cudaLaunchKernelEx(&cfg, k_eval<T, PATHS, CLS>, S, W.F1, W.frames, W.n_frames, W.n_tiles, W.rx, W.e, W.fl,
+    e = cudaLaunchKernelEx(&cfg, k_eval<T, PATHS, CLS>, S, W.F1, W.frames, W.n_frames, W.n_tiles, W.rx, W.perm, W.e, W.fl,
                            W.codes, W.counts, W.cap, ch0, nch, rcap, accumulate, L.ctr, L.ctr + 1 + L.n);
     ++L.n;
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -2333,8 +2336,8 @@ int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, 
 }
 
 int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const FrameDev *frames_host, int n_frames,
-                      unsigned long long n_tiles, const float *rx_soa, float *e_out, uint32_t *flags, int precision,
-                      unsigned long long *ctr, cudaStream_t stream, int *n_launches) {
+                      unsigned long long n_tiles, const float *rx_soa, const int32_t *perm, float *e_out,
+                      uint32_t *flags, int precision, unsigned long long *ctr, cudaStream_t stream, int *n_launches) {
     *n_launches = 0;
     if (n_frames <= 0 || n_tiles == 0) return RT_OK;
     Work W = {};
@@ -2342,7 +2345,7 @@ int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const Frame
     W.frames = frames_dev;
     W.n_frames = n_frames;
     W.n_tiles = n_tiles;
-    W.rx = rx_soa; W.e = e_out; W.fl = flags;
+    W.rx = rx_soa; W.perm = perm; W.e = e_out; W.fl = flags;
     return run(S, W, precision, false, ctr, stream, n_launches);
 }
 

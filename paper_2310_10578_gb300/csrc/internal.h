@@ -113,9 +113,21 @@ int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, 
 
 // Evaluate the n_frames frames of frames_dev (device copy of frames_host):
 // every frame has S.n_f frequencies and at most S.n_body bodies; n_tiles is
-// the end of the last frame's tile range.
+// the end of the last frame's tile range.  perm (or nullptr): the receivers
+// in rx_soa are in a reordered sequence; sorted position rx_off + p of a
+// frame holds its receiver perm[rx_off + p], where that receiver's outputs go.
 int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const FrameDev *frames_host, int n_frames,
-                      unsigned long long n_tiles, const float *rx_soa, float *e_out, uint32_t *flags, int precision,
-                      unsigned long long *ctr, cudaStream_t stream, int *n_launches);
+                      unsigned long long n_tiles, const float *rx_soa, const int32_t *perm, float *e_out,
+                      uint32_t *flags, int precision, unsigned long long *ctr, cudaStream_t stream, int *n_launches);
+
+// Spatial ordering of a batch's receivers (rx_order.cu): a counting sort per
+// frame on the RX_GRID x RX_GRID cells (Morton order) of the rectangle grid
+// = (x0, y0, cells per metre in x, in y).  Scratch: cnt [n_frames][RX_CELLS],
+// rank [total receivers]; results: rx_sorted (SoA per frame, as rx) and perm
+// (see launch_eval_batch).  max_rx: the largest frame.
+constexpr int RX_GRID = 128;
+constexpr int RX_CELLS = RX_GRID * RX_GRID;
+int launch_rx_order(const FrameDev *frames_dev, int n_frames, int max_rx, const float *rx, float4 grid,
+                    uint32_t *cnt, uint32_t *rank, float *rx_sorted, int32_t *perm, cudaStream_t st);
 
 }  // namespace creep

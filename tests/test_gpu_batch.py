@@ -80,8 +80,9 @@ def test_batch_small_parity_and_single_equality(creep, oracle_mod, precision):
         assert np.array_equal(fb & 3, ref.flags & 3)
         compare_fields(gpu_fields(B.frame_fields(out, i)), ref, flags=ref.flags, freqs=cw.freqs[i])
     st = B.stats()
-    # FP32: one planar launch for both chunks, one per body class; FP64: three per chunk
-    assert st["kernel_launches"] == (3 if precision == "fp32" else 6)
+    # three for the receivers' spatial order; FP32: one planar launch for both
+    # chunks, one per body class; FP64: three per chunk
+    assert st["kernel_launches"] == 3 + (3 if precision == "fp32" else 6)
 
 
 def test_batch_full_size_crowd(creep, oracle_mod):
@@ -95,7 +96,7 @@ def test_batch_full_size_crowd(creep, oracle_mod):
     fl = torch.zeros(B.total_rx, dtype=torch.int32, device="cuda")
     out = B.evaluate(rx, flags=fl, opts=opts)
     torch.cuda.synchronize()
-    assert B.stats()["kernel_launches"] == 3
+    assert B.stats()["kernel_launches"] == 6
     flags = fl.cpu().numpy().astype(np.uint32)
     for i in range(cw.n_frames):
         Es, fs = _single(creep, cw, i, opts)
