@@ -309,6 +309,8 @@ static inline uint64_t pcode(int type, int id1, int id2) {
 typedef struct {
     c3 *E;             /* [n_f] accumulated field */
     double *Sabs;      /* [n_f] sum over paths of |E_path| (conditioning of the coherent sum) */
+    double *pathE;     /* or NULL: [cap][n_f][3][2] each listed path's own field */
+    int n_f;
     uint64_t *paths; int n_paths, cap;
     unsigned flags;
     counters ct;
@@ -331,6 +333,13 @@ static inline double c3_norm(c3 v) {
 static inline void accum(rx_state *st, int f, c3 v) {
     st->E[f] = c3_add(st->E[f], v);
     st->Sabs[f] += c3_norm(v);
+    int idx = st->n_paths - 1;                 /* the path just listed */
+    if (st->pathE && idx >= 0 && idx < st->cap) {
+        double *o = st->pathE + ((size_t)idx * st->n_f + f) * 6;
+        o[0] += creal(v.x); o[1] += cimag(v.x);
+        o[2] += creal(v.y); o[3] += cimag(v.y);
+        o[4] += creal(v.z); o[5] += cimag(v.z);
+    }
 }
 
 /* LOS and planar image paths (order 1 and 2); PEC faces. */
@@ -741,7 +750,8 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
                 double xi_lo, double xi_hi,
                 int max_order, int enable,
                 double *E_out, uint64_t *path_codes, int *path_count, int cap,
-                unsigned *flags_out, long long *counters_out, int n_threads, double *sabs_out) {
+                unsigned *flags_out, long long *counters_out, int n_threads, double *sabs_out,
+                double *path_E_out) {
     fock_rule R = {tau_re, tau_im, ws_re, ws_im, wh_re, wh_im, offsets, n_buckets,
                    res_alpha, res_cs, res_beta, res_ch, n_res, xi_lo, xi_hi};
     scene s;
@@ -782,6 +792,8 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
         st.Sabs = Sa;
         st.paths = path_codes ? path_codes + (size_t)r * cap : NULL;
         st.cap = path_codes ? cap : 0;
+        st.n_f = n_f;
+        st.pathE = (path_codes && path_E_out) ? path_E_out + (size_t)r * cap * n_f * 6 : NULL;
         v3 P = V(rx[3 * r], rx[3 * r + 1], rx[3 * r + 2]);
         int inside = 0;
         for (int b = 0; b < n_body; ++b) if (inside_body(P, &s.bodies[b])) inside = 1;

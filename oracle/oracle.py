@@ -54,7 +54,7 @@ def _load():
         d = ctypes.c_double
         _lib.oracle_eval.argtypes = [P, P, i, P, i, P, P, P, i, P, i,
                                      P, P, P, P, P, P, P, i, P, P, P, P, i, d, d,
-                                     i, i, P, P, P, i, P, P, i, P]
+                                     i, i, P, P, P, i, P, P, i, P, P]
         _lib.oracle_eval.restype = i
         _lib.oracle_transition_F.argtypes = [P, i, P]
         _lib.oracle_fock_bracket.argtypes = [P, P, P, P, P, P, P, i, P, P, P, P, i, d, d, P, P, i, P]
@@ -93,12 +93,15 @@ class Result:
     pass
 
 
-def evaluate(scene, rx=None, enable=EN_ALL, cap=256, threads=0, want_paths=True):
+def evaluate(scene, rx=None, enable=EN_ALL, cap=256, threads=0, want_paths=True, path_fields=False):
     """FP64 field of ``scene`` at its receivers (or at ``rx`` [n,3]).
 
     Returns an object with E [n_f][3][n_rx] complex128, sabs [n_f][n_rx] (sum of
     |E_path|), paths (list of sorted uint64 arrays), flags [n_rx] uint32,
-    counters dict and seconds."""
+    counters dict and seconds; with path_fields, also codes [n_rx][cap]
+    (enumeration order), counts [n_rx] and path_E [n_rx][cap][n_f][3]
+    complex128, each listed path's own field.  The scene's arrays are read as
+    float64 (pass float64 arrays for coordinates finer than float32)."""
     lib = _load()
     rx = scene.rx if rx is None else rx
     rx64 = np.ascontiguousarray(np.asarray(rx, dtype=np.float32).astype(np.float64))
@@ -116,12 +119,13 @@ def evaluate(scene, rx=None, enable=EN_ALL, cap=256, threads=0, want_paths=True)
     flags = np.zeros(n_rx, dtype=np.uint32)
     ctr = np.zeros(8, dtype=np.int64)
     sabs = np.zeros((n_f, n_rx), dtype=np.float64)
+    pE = np.zeros((n_rx, cap, n_f, 3, 2), dtype=np.float64) if (path_fields and want_paths) else None
     t0 = time.perf_counter()
     lib.oracle_eval(_p(tri), _p(tf), scene.tri.shape[0], _p(bodies), scene.bodies.shape[0],
                     _p(tx), _p(pol), _p(fr), n_f, _p(rx64), n_rx, *_fock_args(),
                     scene.max_order, enable, _p(E),
                     _p(codes) if want_paths else None, _p(counts), cap if want_paths else 0,
-                    _p(flags), _p(ctr), threads, _p(sabs))
+                    _p(flags), _p(ctr), threads, _p(sabs), _p(pE) if pE is not None else None)
     res = Result()
     res.seconds = time.perf_counter() - t0
     res.E = E[..., 0] + 1j * E[..., 1]
@@ -130,6 +134,9 @@ def evaluate(scene, rx=None, enable=EN_ALL, cap=256, threads=0, want_paths=True)
     res.counts = counts
     if want_paths:
         res.paths = [np.sort(codes[r, :min(counts[r], cap)]) for r in range(n_rx)]
+    if pE is not None:
+        res.codes = codes
+        res.path_E = pE[..., 0] + 1j * pE[..., 1]
     res.counters = dict(zip(COUNTER_NAMES, (int(c) for c in ctr)))
     return res
 
