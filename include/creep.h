@@ -274,6 +274,30 @@ int rt_batch_replay(rt_batch *batch, void *stream);
 /* Counters of the batch's last evaluation or replay (synchronises its stream). */
 int rt_batch_get_stats(rt_batch *batch, rt_stats *out);
 
+/*
+ * rt_backward -- gradient of a real loss through the fields (the adjoint of
+ * rt_evaluate: its vector-Jacobian product) with respect to every body's
+ * centre and radius, the transmitter position and every frequency, with
+ * visibility held fixed: the paths are those listed by rt_paths for the same
+ * receivers and options, and each one's geometry and field (Eqs. 1-4) are
+ * recomputed in FP64 dual numbers, nothing per path being stored.
+ *   rx_soa, n_rx          device, as rt_evaluate.
+ *   codes, counts, cap    device, as rt_paths wrote them (a receiver with more
+ *                         than cap paths contributes its first cap).
+ *   grad_e                device float [n_f][3][n_rx][2]: dLoss/dRe E and
+ *                         dLoss/dIm E, the layout of rt_evaluate's e_out.
+ *   grad_bodies           device double [n_body][4]: dLoss/d(cx, cy, cz, a)
+ *                         (cz has no effect on a cylinder: 0).
+ *   grad_tx               device double [3]; grad_freqs device double [n_f]
+ *                         (per Hz).  All three are overwritten.
+ *   opt                   as for rt_evaluate (its enable mask weighs the soft
+ *                         and hard creeping fields; precision is ignored).
+ * Asynchronous on `stream`.  Errors: RT_ERR_ARG, RT_ERR_STATE, RT_ERR_CUDA.
+ */
+int rt_backward(rt_scene *scene, const float *rx_soa, int n_rx, const uint64_t *codes,
+                const int32_t *counts, int cap, const float *grad_e, double *grad_bodies,
+                double *grad_tx, double *grad_freqs, const rt_options *opt, void *stream);
+
 /* Counters of the last rt_evaluate / rt_paths on this scene (synchronises its stream). */
 int rt_get_stats(rt_scene *scene, rt_stats *out);
 

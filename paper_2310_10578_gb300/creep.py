@@ -24,7 +24,7 @@ FOCK_NRES = 8
 EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "rt_evaluate",
            "rt_evaluate_host", "rt_evaluate_host_noalloc", "rt_paths", "rt_get_stats", "rt_fock_table",
            "rt_last_error", "rt_batch_create", "rt_batch_destroy", "rt_batch_set_frame", "rt_batch_evaluate",
-           "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats")
+           "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats", "rt_backward")
 RT_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -81,6 +81,7 @@ def load(build_if_missing=True):
     lib.rt_batch_capture.argtypes = [P, P, P, P, P, P]
     lib.rt_batch_replay.argtypes = [P, P]
     lib.rt_batch_get_stats.argtypes = [P, P]
+    lib.rt_backward.argtypes = [P, P, I, P, P, I, P, P, P, P, P, P]
     _lib = lib
     return lib
 
@@ -133,6 +134,7 @@ class Scene:
         self._h = ctypes.c_void_p()
         _check(lib.rt_scene_create(_ptr(tri) if n_tri else None, _ptr(tf), n_tri, ctypes.cast(arr, ctypes.c_void_p),
                                    nb, ctypes.byref(self._h)))
+        self.n_body = nb
         self.n_f = 0
 
     @classmethod
@@ -208,6 +210,23 @@ class Scene:
         _check(_lib.rt_paths(self._h, _ptr(rx_soa), n, _ptr(codes), _ptr(counts), cap, _ptr(fl),
                              ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
         return codes, counts, fl
+
+    def backward(self, rx_soa, codes, counts, grad_e, opts=None, stream=None):
+        """Adjoint of evaluate (rt_backward): dLoss/d(body centres and radii
+        [n_body, 4], transmitter [3], frequencies [n_f]) as float64 CUDA
+        tensors, from grad_e = dLoss/dE [n_f, 3, n, 2] and the path list
+        (codes [n, cap], counts [n]) of the same receivers."""
+        import torch
+        n = rx_soa.shape[1]
+        dev = rx_soa.device
+        gb = torch.zeros((max(self.n_body, 1), 4), dtype=torch.float64, device=dev)
+        gt = torch.zeros(3, dtype=torch.float64, device=dev)
+        gf = torch.zeros(self.n_f, dtype=torch.float64, device=dev)
+        ge = grad_e.contiguous().to(torch.float32)
+        _check(_lib.rt_backward(self._h, _ptr(rx_soa), n, _ptr(codes), _ptr(counts), codes.shape[1], _ptr(ge),
+                                _ptr(gb), _ptr(gt), _ptr(gf), ctypes.byref(opts) if opts is not None else None,
+                                _stream_handle(stream)))
+        return gb[:self.n_body], gt, gf
 
     def stats(self):
         st = rt_stats()

@@ -544,6 +544,25 @@ int rt_paths(rt_scene *s, const float *rx_soa, int n_rx, uint64_t *codes, int32_
     return launch_eval(D, rx_soa, n_rx, nullptr, flags, codes, counts, cap, prec, s->d_esc, st, &s->last_launches);
 }
 
+int rt_backward(rt_scene *s, const float *rx_soa, int n_rx, const uint64_t *codes, const int32_t *counts, int cap,
+                const float *grad_e, double *grad_bodies, double *grad_tx, double *grad_freqs, const rt_options *opt,
+                void *stream) {
+    if (!s) return fail(RT_ERR_ARG, "rt_backward: NULL scene");
+    if (n_rx < 0 || cap < 1) return fail(RT_ERR_ARG, "rt_backward: n_rx < 0 or cap < 1");
+    if (!grad_tx || !grad_freqs || (s->n_body > 0 && !grad_bodies))
+        return fail(RT_ERR_ARG, "rt_backward: NULL gradient buffer");
+    if (n_rx > 0 && (!rx_soa || !codes || !counts || !grad_e)) return fail(RT_ERR_ARG, "rt_backward: NULL buffer");
+    DevScene D;
+    int prec;
+    int rc = make_dev(s, opt, D, &prec);
+    if (rc != RT_OK) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    s->last_stream = st;
+    s->last_launches = n_rx > 0 ? 1 : 0;
+    return launch_adjoint(D, rx_soa, n_rx, codes, counts, cap, grad_e, grad_bodies, grad_tx, grad_freqs, s->d_esc + 1,
+                          st);
+}
+
 int rt_evaluate_host(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags, const rt_options *opt,
                      void *stream) {
     if (!s) return fail(RT_ERR_ARG, "rt_evaluate_host: NULL scene");

@@ -21,6 +21,7 @@
 #include <stdint.h>
 
 #include "devmath.cuh"
+#include "dual.cuh"
 #include "internal.h"
 
 namespace creep {
@@ -1550,7 +1551,13 @@ __device__ __noinline__ int esc_creep(const Ctx &c, int b, int dir, v3t<float> P
     bool sphere = c.body[2 * b + 1].y == 0.0f;
     if (sphere) {
         *caustic = half_lambda_max > g.dperp.v;
-        if (!(g.dperp > dx(0.0))) return d;          // exactly on the axis: no finite ray field
+        if (!(g.dperp > dx(0.0))) {                  // exactly on the axis: no finite ray field
+            if (field) {
+                for (int f = 0; f < NFC; ++f)
+                    for (int q = 0; q < 3; ++q) out->E[f][q] = mkc(0.0f, 0.0f);
+            }
+            return d;
+        }
     }
     if (rec) {
         creep_prep(c, rec, c.S, Pf, to_f(g), to_df(to_double(g.sp + g.t + g.sq)), enable);
@@ -2347,6 +2354,377 @@ int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const Frame
     W.n_tiles = n_tiles;
     W.rx = rx_soa; W.perm = perm; W.e = e_out; W.fl = flags;
     return run(S, W, precision, false, ctr, stream, n_launches);
+}
+
+// ============================================================== adjoint
+// Gradient of a scalar loss through the fields (the vector-Jacobian product
+// of the evaluation): given dLoss/dE (real and imaginary parts) at every
+// receiver and frequency, the sums over the listed paths of each path's
+// field derivative with respect to its body's centre and radius, the
+// transmitter position and the frequency.  Visibility is held fixed: the
+// paths are those of the forward path list (rt_paths), and each one's
+// geometry and field are recomputed here in FP64 dual numbers (D8), by the
+// same construction as the forward FP64 path: image points for planar
+// reflections (Eq. 3), the specular point on the body (its derivative from
+// one Newton step in dual arithmetic at the FP64 root, which is the
+// implicit-function derivative), the tangent points and geodesic of the
+// creeping ray (Eq. 4, Fig. 1), the Fock--Pekeris functions (table
+// derivative from the cubic Hermite interpolant, residue series term by
+// term), the transition function through w'(z) = -2 z w(z) + 2j/sqrt(pi).
+
+template <> __device__ __forceinline__ void face_plane<D8>(const Ctx &c, int f, v3t<D8> *n, D8 *d) {
+    dq4 q = c.face64[f]; *n = mk3<D8>(q.x, q.y, q.z); *d = D8(q.w);
+}
+
+__device__ void pekeris(const Ctx &c, const D8 &xi, cpx<D8> &ps, cpx<D8> &ph, bool regular) {
+    const double cc = (0.5 / sqrt(M_PI)) * cos(M_PI / 4.0);
+    const D8 ci = D8(cc) / xi;
+    if (xi.v > XI_HI) {
+        cpx<D8> ss = mkc<D8>(0.0, 0.0), sh = mkc<D8>(0.0, 0.0);
+        for (int n = 0; n < FOCK_NRES; ++n) {
+            dq4 rs = c.res64[2 * n], rh = c.res64[2 * n + 1];
+            D8 sn, cs;
+            SinCos(xi * D8(rs.y), &sn, &cs);
+            D8 e = Exp(-(xi * D8(rs.x))) * D8(rs.z);
+            ss = ss + mkc<D8>(e * cs, -(e * sn));
+            SinCos(xi * D8(rh.y), &sn, &cs);
+            e = Exp(-(xi * D8(rh.x))) * D8(rh.z);
+            sh = sh + mkc<D8>(e * cs, -(e * sn));
+        }
+        const cpx<D8> pre = mkc<D8>(-cos(M_PI / 12.0) * (0.5 / sqrt(M_PI)), sin(M_PI / 12.0) * (0.5 / sqrt(M_PI)));
+        ps = pre * ss;
+        ph = pre * sh;
+        if (regular) { ps = ps + mkc<D8>(ci, -ci); ph = ph + mkc<D8>(ci, -ci); }
+        return;
+    }
+    // cubic Hermite interpolant of G and its derivative in xi
+    const double u = (xi.v - XI_LO) / XI_STEP;
+    const int j = min(max((int)u, 0), FOCK_N - 2);
+    const double t = u - j, t2 = t * t, omt = 1.0 - t;
+    const double h00 = (1 + 2 * t) * omt * omt, h10 = t * omt * omt * XI_STEP, h01 = t2 * (3 - 2 * t),
+                 h11 = t2 * (t - 1) * XI_STEP;
+    // d/dxi = (d/dt) / XI_STEP
+    const double d00 = (6 * t2 - 6 * t) / XI_STEP, d10 = 1 - 4 * t + 3 * t2, d01 = (6 * t - 6 * t2) / XI_STEP,
+                 d11 = 3 * t2 - 2 * t;
+    cpx<D8> G[2];
+    for (int k = 0; k < 2; ++k) {
+        double2 g0 = c.fock64[(j * 2 + k) * 2], q0 = c.fock64[(j * 2 + k) * 2 + 1];
+        double2 g1 = c.fock64[((j + 1) * 2 + k) * 2], q1 = c.fock64[((j + 1) * 2 + k) * 2 + 1];
+        const double gr = h00 * g0.x + h10 * q0.x + h01 * g1.x + h11 * q1.x;
+        const double gi = h00 * g0.y + h10 * q0.y + h01 * g1.y + h11 * q1.y;
+        const double dr = d00 * g0.x + d10 * q0.x + d01 * g1.x + d11 * q1.x;
+        const double di = d00 * g0.y + d10 * q0.y + d01 * g1.y + d11 * q1.y;
+        G[k] = mkc<D8>(dchain(gr, dr, xi), dchain(gi, di, xi));
+    }
+    const cpx<D8> rot = cexpi(xi * xi * xi / D8(12.0));
+    ps = G[0] * rot;
+    ph = G[1] * rot;
+    if (!regular) { ps = ps - mkc<D8>(ci, -ci); ph = ph - mkc<D8>(ci, -ci); }
+}
+
+__device__ cpx<D8> faddeeva_t(const Ctx &c, const cpx<D8> &zd) {
+    cpx<double> z = mkc(zd.re.v, zd.im.v);
+    const double L = c.weid_L;
+    cpx<double> lm = mkc(L + z.im, -z.re), lp = mkc(L - z.im, z.re);
+    cpx<double> Z = cdiv(lp, lm);
+    cpx<double> p = mkc(c.weid64[WEIDEMAN_N - 1], 0.0);
+    for (int n = WEIDEMAN_N - 2; n >= 0; --n) p = p * Z + mkc(c.weid64[n], 0.0);
+    cpx<double> w = cdiv(p * 2.0, lm * lm) + cdiv(mkc(0.56418958354775628, 0.0), lm);
+    // w'(z) = -2 z w + 2j / sqrt(pi)
+    cpx<double> wp = z * w * -2.0 + mkc(0.0, 1.1283791670955126);
+    cpx<D8> r;
+    r.re.v = w.re; r.im.v = w.im;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) {
+        r.re.d[k] = wp.re * zd.re.d[k] - wp.im * zd.im.d[k];
+        r.im.d[k] = wp.re * zd.im.d[k] + wp.im * zd.re.d[k];
+    }
+    return r;
+}
+
+// wavenumber, (k/2)^{1/3} and the path phasor with the frequency as slot DS_F
+__device__ __forceinline__ D8 kof(const FreqC &fq, int f, const D8 &) {
+    D8 k(fq.kd[f]);
+    k.d[DS_F] = 2.0 * M_PI / 299792458.0;
+    return k;
+}
+__device__ __forceinline__ D8 khof(const FreqC &fq, int f, const D8 &x) { return Cbrt(kof(fq, f, x) * D8(0.5)); }
+__device__ __forceinline__ cpx<D8> phasor(const FreqC &fq, int f, const D8 &L) {
+    D8 fc(fq.fc[f]);
+    fc.d[DS_F] = 1.0 / 299792458.0;
+    D8 cyc = L * fc;
+    cyc.v -= floor(cyc.v);                      // the integer cycles (no derivative)
+    D8 s, co;
+    SinCosPi(cyc * D8(2.0), &s, &co);
+    return mkc<D8>(co, -s);
+}
+__device__ __forceinline__ D8 len_val(const D8 &L) { return L; }
+
+// contracts each path field's tangents with dLoss/dE of its receiver
+struct AccAdj {
+    const float *gE;        // [n_f][3][n_rx][2]
+    int n_rx, r, f0;
+    double g[ND - 1];       // body and transmitter slots
+    double gf[NFC];         // frequency slot, per frequency of the chunk
+};
+__device__ __forceinline__ void acc_put(AccAdj &a, int f, const cpx<D8> &x, const cpx<D8> &y, const cpx<D8> &z) {
+    const cpx<D8> *e[3] = {&x, &y, &z};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const size_t idx = ((size_t)(a.f0 + f) * 3 + q) * a.n_rx + a.r;
+        const float gr = a.gE[2 * idx], gi = a.gE[2 * idx + 1];
+#pragma unroll
+        for (int k = 0; k < ND - 1; ++k) a.g[k] += gr * e[q]->re.d[k] + gi * e[q]->im.d[k];
+        a.gf[f] += gr * e[q]->re.d[DS_F] + gi * e[q]->im.d[DS_F];
+    }
+}
+
+// body b's centre and radius as parameters (slots 0-3)
+__device__ __forceinline__ void adj_body(const Ctx &c, int b, v3t<D8> &cc, D8 &a, bool &sphere) {
+    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
+    cc = mk3<D8>(dvar(q0.x, DS_CX), dvar(q0.y, DS_CY), dvar(q0.z, DS_CZ));
+    a = dvar(q0.w, DS_A);
+    sphere = q1.y == 0.0f;
+}
+
+__device__ __noinline__ void adj_refl_root(const D8 &a, const D8 &ds, const D8 &pu, const D8 &pv, const D8 &gam,
+                                           D8 *cs, D8 *sn) {
+    dx c0, s0;
+    refl_root(dx(a.v), dx(ds.v), dx(pu.v), dx(pv.v), dx(gam.v), &c0, &s0);
+    // one Newton step on dL/dpsi = 0 in dual arithmetic at the root
+    const D8 psi(atan2(s0.v, c0.v));
+    D8 s, c;
+    SinCos(psi, &s, &c);
+    const D8 qx = a * c, qy = a * s;
+    const D8 lS = Sqrt((qx - ds) * (qx - ds) + qy * qy);
+    const D8 lP = Sqrt((qx - pu) * (qx - pu) + (qy - pv) * (qy - pv));
+    const D8 gS = a * ds * s / lS, gP = a * (pu * s - pv * c) / lP;
+    const D8 h = (ds * qx - gS * gS) / lS + (pu * qx + pv * qy - gP * gP) / lP;
+    SinCos(psi - (gS + gP) / h, sn, cs);
+}
+
+// reflection off body b (the forward FP64 construction, without decisions)
+__device__ __noinline__ void adj_rb(const Ctx &c, int b, v3t<D8> S, v3t<D8> P, const FreqC &fq, AccAdj &acc) {
+    v3t<D8> cc;
+    D8 a;
+    bool sphere;
+    adj_body(c, b, cc, a, sphere);
+    Frame<D8> F;
+    if (sphere) sphere_frame(S, P, cc, a, F, D8(0.0));
+    else cyl_frame(S, P, cc.x, cc.y, a, F, D8(0.0));
+    D8 cs, sn;
+    adj_refl_root(a, F.ds, F.pu, F.pv, F.gam, &cs, &sn);
+    v3t<D8> n = F.u * cs + F.v * sn;
+    v3t<D8> Q;
+    if (sphere) {
+        Q = cc + n * a;
+    } else {
+        D8 qx = a * cs, qy = a * sn;
+        D8 l1 = Sqrt((qx - F.ds) * (qx - F.ds) + qy * qy);
+        D8 l2 = Sqrt((qx - F.pu) * (qx - F.pu) + (qy - F.pv) * (qy - F.pv));
+        D8 zq = S.z + (P.z - S.z) * l1 / (l1 + l2);
+        Q = mk3<D8>(cc.x + a * n.x, cc.y + a * n.y, zq);
+    }
+    Geo<D8> g;
+    v3t<D8> shi = unit3(Q - S);
+    D8 cth = -dot3(shi, n);
+    g.dr = P - Q;
+    g.Q1 = Q;
+    g.n1 = n;
+    if (sphere) {
+        g.inv_f1 = D8(2.0) / (a * cth);
+        g.inv_f2 = D8(2.0) * cth / a;
+        g.rho_g = a;
+    } else {
+        g.inv_f1 = D8(2.0) * (D8(1.0) - shi.z * shi.z) / (a * cth);
+        g.inv_f2 = D8(0.0);
+        D8 sphi = -(shi.x * n.y) + shi.y * n.x;
+        g.rho_g = (sphi == D8(0.0)) ? D8(INFINITY) : a * (D8(1.0) - cth * cth) / (sphi * sphi);
+    }
+    field_body_refl<D8, D8, false, AccAdj>(c, acc, fq, S, P, g, norm3(Q - S) + norm3(P - Q));
+}
+
+// creeping ray round body b, dir 0 short way, 1 long way; false: no finite field
+__device__ __noinline__ bool adj_creep(const Ctx &c, int b, int dir, v3t<D8> S, v3t<D8> P, const FreqC &fq,
+                                       unsigned enable, AccAdj &acc) {
+    v3t<D8> cc;
+    D8 a;
+    bool sphere;
+    adj_body(c, b, cc, a, sphere);
+    Frame<D8> F;
+    if (sphere) sphere_frame(S, P, cc, a, F, D8(0.0));
+    else cyl_frame(S, P, cc.x, cc.y, a, F, D8(0.0));
+    const D8 TWO_PI(6.283185307179586476925286766559);
+    D8 dpsi = (dir == 0) ? (F.gam - F.bs - F.bp) : (TWO_PI - F.gam - F.bs - F.bp);
+    D8 psi1 = (dir == 0) ? F.bs : -F.bs;
+    D8 psi2 = (dir == 0) ? F.gam - F.bp : F.gam + F.bp;
+    D8 s1, c1, s2, c2;
+    SinCos(psi1, &s1, &c1);
+    SinCos(psi2, &s2, &c2);
+    Geo<D8> g;
+    g.n1 = F.u * c1 + F.v * s1;
+    g.n2 = F.u * c2 + F.v * s2;
+    if (sphere) {
+        g.Q1 = cc + g.n1 * a;
+        g.Q2 = cc + g.n2 * a;
+        g.sp = F.sps;
+        g.sq = F.sqp;
+        g.t = a * dpsi;
+        g.rho_g = a;
+        g.caus = (dir == 1);
+        D8 sg, cg;
+        SinCos(F.gam, &sg, &cg);
+        g.dperp = F.dp * sg;
+        if (!(g.dperp > D8(0.0))) return false;
+        D8 sb, cb;
+        SinCos(F.bs, &sb, &cb);
+        g.amp = Sqrt(a * sb / g.dperp) / Sqrt(g.sq) / g.sp;
+    } else {
+        D8 ds_ = F.sps, dp_ = F.sqp;
+        D8 dz = P.z - S.z;
+        D8 H = ds_ + a * dpsi + dp_;
+        D8 ell = Sqrt(H * H + dz * dz);
+        D8 sin0 = H / ell;
+        D8 z1 = S.z + dz * ds_ / H, z2 = S.z + dz * (ds_ + a * dpsi) / H;
+        g.Q1 = mk3<D8>(cc.x + a * g.n1.x, cc.y + a * g.n1.y, z1);
+        g.Q2 = mk3<D8>(cc.x + a * g.n2.x, cc.y + a * g.n2.y, z2);
+        g.sp = ds_ / sin0;
+        g.t = a * dpsi / sin0;
+        g.sq = dp_ / sin0;
+        g.rho_g = a / (sin0 * sin0);
+        g.caus = 0;
+        g.dperp = D8(0.0);
+        g.amp = D8(1.0) / Sqrt(g.sp * g.sq * (g.sp + g.t + g.sq));
+    }
+    field_creep<D8, D8, false, AccAdj>(c, acc, fq, S, P, g, g.sp + g.t + g.sq, enable);
+    return true;
+}
+
+// direct ray and planar image paths (faces i, j; -1: none)
+__device__ __noinline__ void adj_planar(const Ctx &c, int order, int i, int j, v3t<D8> S, v3t<D8> P,
+                                        const FreqC &fq, AccAdj &acc) {
+    if (order == 0) {
+        v3t<D8> d = P - S;
+        D8 L = norm3(d);
+        add_ray(acc, fq, src_pol(c, d * (D8(1.0) / L)), D8(1.0) / L, L);
+        return;
+    }
+    v3t<D8> ni, nj;
+    D8 di, dj;
+    face_plane<D8>(c, i, &ni, &di);
+    v3t<D8> S1 = mirror_pt(S, ni, di);
+    if (order == 1) {
+        D8 d1 = dot3(ni, S1) - di, dP = dot3(ni, P) - di;
+        v3t<D8> Q = S1 + (P - S1) * (d1 / (d1 - dP));
+        D8 L = norm3(Q - S) + norm3(P - Q);
+        add_ray(acc, fq, pec_mirror(src_pol(c, unit3(Q - S)), ni), D8(1.0) / L, L);
+        return;
+    }
+    face_plane<D8>(c, j, &nj, &dj);
+    v3t<D8> S2 = mirror_pt(S1, nj, dj);
+    D8 d2 = dot3(nj, S2) - dj, dP = dot3(nj, P) - dj;
+    v3t<D8> Q2 = S2 + (P - S2) * (d2 / (d2 - dP));
+    D8 e1 = dot3(ni, S1) - di, eq = dot3(ni, Q2) - di;
+    v3t<D8> Q1 = S1 + (Q2 - S1) * (e1 / (e1 - eq));
+    D8 L = norm3(Q1 - S) + norm3(Q2 - Q1) + norm3(P - Q2);
+    add_ray(acc, fq, pec_mirror(pec_mirror(src_pol(c, unit3(Q1 - S)), ni), nj), D8(1.0) / L, L);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One warp per receiver (persistent, from a queue), its lanes over the
+// receiver's listed paths.  Body gradients by atomics per path; transmitter
+// and frequency gradients summed over the warp first.
+__global__ void __launch_bounds__(128) k_adjoint(DevScene S, const float *__restrict__ rx, int n_rx,
+                                                 const uint64_t *__restrict__ codes,
+                                                 const int32_t *__restrict__ counts, int cap,
+                                                 const float *__restrict__ gE, double *g_body, double *g_tx,
+                                                 double *g_f, unsigned long long *queue) {
+    Ctx c;
+    c.tri = S.tri; c.tri_aux = S.tri_alt; c.face32 = S.face32; c.face64 = S.face64;
+    c.face_rng = S.face_rng; c.face_tris = S.face_tris; c.body = S.body;
+    c.n_tri = S.n_tri; c.n_face = S.n_face; c.n_body = S.n_body;
+    c.band = 0.0f;
+    c.S = mk3(S.tx[0], S.tx[1], S.tx[2]);
+    c.pol = mk3(S.pol[0], S.pol[1], S.pol[2]);
+    c.fock = nullptr; c.res = nullptr; c.weid = nullptr; c.weid_L = S.weid_L;
+    c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
+    c.img = S.img; c.txb = S.txb; c.occ_src = nullptr; c.occ_w = 0;
+    const int lane = threadIdx.x & 31;
+    const int nch = (S.n_f + NFC - 1) / NFC;
+    const v3t<D8> Sd = mk3<D8>(dvar(c.S.x, DS_SX), dvar(c.S.y, DS_SY), dvar(c.S.z, DS_SZ));
+    double gtx[3] = {0.0, 0.0, 0.0};
+    for (;;) {
+        unsigned long long q = 0;
+        if (lane == 0) q = atomicAdd(queue, 1ull);
+        q = __shfl_sync(0xffffffffu, q, 0);
+        if (q >= (unsigned long long)n_rx) break;
+        const int r = (int)q;
+        const int np = min(counts[r], cap);
+        const v3t<D8> Pd = mk3<D8>(rx[r], rx[n_rx + r], rx[2 * n_rx + r]);
+        for (int j0 = 0; j0 < np; j0 += 32) {
+            const int jj = j0 + lane;
+            for (int ch = 0; ch < nch; ++ch) {
+                const FreqC &fq = S.fqc[ch];
+                AccAdj acc;
+                acc.gE = gE; acc.n_rx = n_rx; acc.r = r; acc.f0 = ch * NFC;
+                for (int k = 0; k < ND - 1; ++k) acc.g[k] = 0.0;
+                for (int k = 0; k < NFC; ++k) acc.gf[k] = 0.0;
+                int body = -1;
+                if (jj < np) {
+                    const uint64_t code = codes[(size_t)r * cap + jj];
+                    const int type = (int)(code >> 56), id1 = (int)((code >> 28) & 0xFFFFFFFu),
+                              id2 = (int)(code & 0xFFFFFFFu);
+                    if (type == PT_LOS) adj_planar(c, 0, -1, -1, Sd, Pd, fq, acc);
+                    else if (type == PT_R1) adj_planar(c, 1, id1, -1, Sd, Pd, fq, acc);
+                    else if (type == PT_R2) adj_planar(c, 2, id1, id2, Sd, Pd, fq, acc);
+                    else if (type == PT_RB) { adj_rb(c, id1, Sd, Pd, fq, acc); body = id1; }
+                    else if (type == PT_CP || type == PT_CM) {
+                        if (adj_creep(c, id1, type == PT_CM, Sd, Pd, fq, S.enable, acc)) body = id1;
+                    }
+                }
+                if (body >= 0)
+                    for (int k = 0; k < 4; ++k)
+                        if (acc.g[k] != 0.0) atomicAdd(&g_body[4 * body + k], acc.g[k]);
+                for (int k = 0; k < 3; ++k) gtx[k] += acc.g[DS_SX + k];
+                for (int f = 0; f < fq.nf; ++f) {
+                    const double v = warp_sum(acc.gf[f]);
+                    if (lane == 0 && v != 0.0) atomicAdd(&g_f[ch * NFC + f], v);
+                }
+            }
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double v = warp_sum(gtx[k]);
+        if (lane == 0 && v != 0.0) atomicAdd(&g_tx[k], v);
+    }
+}
+
+int launch_adjoint(const DevScene &S, const float *rx_soa, int n_rx, const uint64_t *codes, const int32_t *counts,
+                   int cap, const float *grad_e, double *g_body, double *g_tx, double *g_f,
+                   unsigned long long *queue, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess && S.n_body > 0) e = cudaMemsetAsync(g_body, 0, sizeof(double) * 4 * S.n_body, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_tx, 0, sizeof(double) * 3, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g_f, 0, sizeof(double) * S.n_f, st);
+    if (e == cudaSuccess && n_rx > 0) {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        long long need = ((long long)n_rx + 3) / 4;
+        int grid = (int)(need < 4LL * nsm ? need : 4LL * nsm);
+        k_adjoint<<<grid, 128, 0, st>>>(S, rx_soa, n_rx, codes, counts, cap, grad_e, g_body, g_tx, g_f, queue);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) {
+        set_error(std::string("adjoint: ") + cudaGetErrorString(e));
+        return RT_ERR_CUDA;
+    }
+    return RT_OK;
 }
 
 }  // namespace creep

@@ -120,6 +120,15 @@ int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const Frame
                       unsigned long long n_tiles, const float *rx_soa, const int32_t *perm, float *e_out,
                       uint32_t *flags, int precision, unsigned long long *ctr, cudaStream_t stream, int *n_launches);
 
+// Gradient of a loss through the fields (adjoint pass, eval_fields.cu): for
+// the n_rx receivers' listed paths (codes/counts/cap as rt_paths wrote
+// them), the sums of dLoss/dE (grad_e, as the fields) times each path's
+// field derivative: g_body [n_body][4] (centre x, y, z, radius), g_tx [3],
+// g_f [n_f]; all zeroed first.  queue: one device counter.
+int launch_adjoint(const DevScene &S, const float *rx_soa, int n_rx, const uint64_t *codes, const int32_t *counts,
+                   int cap, const float *grad_e, double *g_body, double *g_tx, double *g_f,
+                   unsigned long long *queue, cudaStream_t st);
+
 // Spatial ordering of a batch's receivers (rx_order.cu): a counting sort per
 // frame on the RX_GRID x RX_GRID cells (Morton order) of the rectangle grid
 // = (x0, y0, cells per metre in x, in y).  Scratch: cnt [n_frames][RX_CELLS],
