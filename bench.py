@@ -11,7 +11,9 @@ bulk arithmetic: 65 536 receivers x 3 frequencies = 196 608 field samples.
 At N = 1 the line also carries "batched": the batched form on 64 crowd frames
 (50 walking PEC cylinders, 16 frequencies in 24-30 GHz per frame, 1k-64k
 receivers per frame, 1.12 M receivers in all) replayed from a captured CUDA
-graph, with its own roofline and oracle comparison (--no-batched skips it).
+graph, with its own roofline and oracle comparison (--no-batched skips it),
+and "adjoint": one gradient step (fields, path list, rt_backward) on the room
+with 200 PEC cylinders at 28 GHz, 64 x 64 receivers (--no-adjoint skips it).
 
 N > 1 runs under torch.distributed (one process per GPU): each rank evaluates
 its own receiver grid (shifted by a fraction of a cell) with no data-path
@@ -52,6 +54,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched crowd-frames measurement")
     ap.add_argument("--batched-steps", type=int, default=10)
+    ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) measurement")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -340,6 +343,61 @@ def batched_crowd(args, creep, dev, flush, peak_fn):
     return res
 
 
+# ---------------------------------------------------------------- adjoint
+def adjoint_room200(args, creep, dev, flush):
+    """The adjoint form: the room with 200 PEC cylinders, 28 GHz, 64 x 64
+    receivers; one gradient step = forward fields (rt_evaluate), the path
+    list (rt_paths) and the adjoint (rt_backward) with a dB-power loss seed."""
+    import torch
+    from paper_2310_10578_gb300 import scenes
+    sc = scenes.room(n_cyl=200, nx=64, ny=64, freqs=(28e9,))
+    S = creep.Scene.from_scene(sc)
+    rx = torch.tensor(sc.rx_soa(), device=dev)
+    opts = creep.options(max_order=2)
+    n = sc.n_rx
+    E = torch.empty((1, 3, n, 2), dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream()
+
+    def step():
+        S.evaluate(rx, out=E, opts=opts)
+        codes, counts, _ = S.paths(rx, cap=64, opts=opts)
+        p = (E.double() ** 2).sum(dim=(0, 1, 3))
+        g = torch.where(p > 0, 20.0 / np.log(10.0) / torch.clamp(p, min=1e-300), torch.zeros_like(p))
+        gE = (E.double() * g[None, None, :, None]).float()
+        return S.backward(rx, codes, counts, gE, opts=opts)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    marks = []
+    for i in range(args.batched_steps):
+        flush.fill_(float(i))
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(st)
+        S.evaluate(rx, out=E, opts=opts)
+        ev[1].record(st)
+        codes, counts, _ = S.paths(rx, cap=64, opts=opts)
+        ev[2].record(st)
+        p = (E.double() ** 2).sum(dim=(0, 1, 3))
+        g = torch.where(p > 0, 20.0 / np.log(10.0) / torch.clamp(p, min=1e-300), torch.zeros_like(p))
+        gE = (E.double() * g[None, None, :, None]).float()
+        gb, gt, gf = S.backward(rx, codes, counts, gE, opts=opts)
+        ev[3].record(st)
+        marks.append(ev)
+    torch.cuda.synchronize()
+    t = np.array([[m[k].elapsed_time(m[k + 1]) for k in range(3)] for m in marks])
+    fwd, paths, bwd = (float(np.mean(t[:, k])) for k in range(3))
+    total = float(np.mean([m[0].elapsed_time(m[3]) for m in marks]))
+    n_paths = int(counts.sum())
+    return {"workload": "room 10x8x3 m, 12 PEC triangles + 200 PEC cylinders, 64x64 rx at z=1.2 m, 28 GHz, refl<=2",
+            "loss": "sum over receivers of received power in dB (seed dLoss/dE = 20/ln10 E/|E|^2)",
+            "ms_forward": fwd, "ms_path_list": paths, "ms_backward_incl_seed": bwd, "ms_step": total,
+            "value": n / (total / 1e3), "unit": "receiver gradients/s (forward + path list + adjoint)",
+            "paths": n_paths, "steps": args.batched_steps,
+            "gradients": "d/d(200 x (cx, cy, cz, a)), d/d(Tx), d/d(f); FP64 dual numbers",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -421,6 +479,9 @@ def main():
             return (props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12,
                     "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived, FFMA)" % (props.multi_processor_count, sm_max))
         batched = batched_crowd(args, creep, dev, flush, peak_fn)
+    adj = None
+    if world == 1 and not args.no_adjoint:
+        adj = adjoint_room200(args, creep, dev, flush)
     clocks = sampler.stop() if sampler else None
 
     ms, e2e_s = max_over_ranks([np.mean(dev_ms), np.mean(e2e_t)], device=dev)
@@ -474,6 +535,8 @@ def main():
                             "work_per_evaluation_flops": flops}
     if batched is not None:
         line["batched"] = batched
+    if adj is not None:
+        line["adjoint"] = adj
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -1900,6 +1900,30 @@ __device__ __noinline__ void occ_masks(const Ctx &c, float t0x, float t0y, float
     }
 }
 
+// the occluder masks of a tile's receivers: their bounding box as a disk of
+// radius rr round the box's longer midline T0 T1; every lane of the warp
+// takes part (rok: this lane's receiver exists)
+__device__ __forceinline__ void tile_masks(const Ctx &c, const float *rx, int n_rx, int r, bool rok, uint32_t *out,
+                                           int wi, int nwarps) {
+    float x0 = rok ? rx[r] : INFINITY, y0 = rok ? rx[n_rx + r] : INFINITY;
+    float x1 = rok ? x0 : -INFINITY, y1 = rok ? y0 : -INFINITY;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
+        y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
+        x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
+        y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
+    }
+    if (x0 <= x1) {
+        const float xm = 0.5f * (x0 + x1), ym = 0.5f * (y0 + y1);
+        const bool along_x = (x1 - x0) >= (y1 - y0);
+        // (half the shorter side, rounded up by a relative 1e-6 for the midpoint's rounding)
+        const float rr = (along_x ? 0.5f * (y1 - y0) : 0.5f * (x1 - x0)) * 1.000001f;
+        occ_masks(c, along_x ? x0 : xm, along_x ? ym : y0, along_x ? x1 : xm, along_x ? ym : y1, rr, out, wi,
+                  nwarps);
+    }
+}
+
 // copy n bytes (a multiple of 4) from global to shared memory, all threads
 __device__ __forceinline__ void stage_words(void *dst, const void *src, int n) {
     for (int i = threadIdx.x; i < n / 4; i += blockDim.x)
@@ -1984,6 +2008,22 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         const float *rx = rx_base;
         const int n_rx = F1.n_rx;
         const unsigned long long ntiles = ((unsigned long long)n_rx + 31ull) >> 5;
+        // occluder masks (FP32 body kernels): the source side per block, the
+        // receiver side per warp (each warp takes whole tiles)
+        constexpr bool OCC = BODIES && sizeof(T) == 4;
+        const bool occ_on = OCC && S.n_body > 0 && S.n_body <= OCC_MAX_BODIES;
+        const int occ_w = occ_on ? (S.n_body + 31) >> 5 : 0;
+        uint32_t *s_occ_src = reinterpret_cast<uint32_t *>(s_rec);
+        uint32_t *s_occ_mine = s_occ_src + (1 + warp) * S.n_body * occ_w;
+        if (threadIdx.x == 0) {
+            s_ctx.occ_src = occ_on ? s_occ_src : nullptr;
+            s_ctx.occ_w = occ_w;
+        }
+        __syncthreads();
+        if (occ_on) {
+            occ_masks(c, c.S.x, c.S.y, c.S.x, c.S.y, 0.0f, s_occ_src, warp, NW);
+            __syncthreads();
+        }
         asm volatile("griddepcontrol.wait;" ::: "memory");   // the previous class kernel's lists are complete
         // path lists: each warp takes tiles of 32 consecutive receivers from
         // the launch's queue and lists every candidate itself (codes in the
@@ -1994,6 +2034,10 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t >= ntiles) break;
             int r = (int)(t * 32ull) + lane;
+            if (occ_on) {
+                tile_masks(c, rx, n_rx, r, r < n_rx, s_occ_mine, 0, 1);
+                __syncwarp();
+            }
             if (r < n_rx) {
                 AccS<T> acc{nullptr};                // no fields in this mode
                 uint32_t fl;
@@ -2001,8 +2045,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                 int npath = accumulate ? counts[r] : 0;
                 int nrec;
                 eval_receiver<T, PATHS, CLS>(c, s_fqs, 1, S.enable, S.max_order, rx, n_rx, r, codes, cap, F1.hl,
-                                             0, c.n_body, true, false, 0, nullptr, 0, 1, acc, nullptr, fl, nesc, npath,
-                                             nrec);
+                                             0, c.n_body, true, false, 0, occ_on ? s_occ_mine : nullptr, 0, 1, acc,
+                                             nullptr, fl, nesc, npath, nrec);
                 counts[r] = npath;
                 if (fl_base) fl_base[r] = accumulate ? (fl_base[r] | fl) : fl;
                 if (nesc) atomicAdd(esc_counter, (unsigned long long)nesc);
@@ -2107,27 +2151,9 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
             const int r = r0 < n_rx ? (int)r0 + lane : n_rx;
             const bool rok = r < n_rx;
             if (occ_on) {
-                // the tile's region: its receivers' bounding box, as a disk of
-                // radius rr round the box's longer midline T0 T1.  Each warp
-                // makes the masks of the bodies of its own share (b = part
-                // mod NWT), so no other warp waits for them.
-                float x0 = rok ? rx[r] : INFINITY, y0 = rok ? rx[n_rx + r] : INFINITY;
-                float x1 = rok ? x0 : -INFINITY, y1 = rok ? y0 : -INFINITY;
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    x0 = fminf(x0, __shfl_xor_sync(0xffffffffu, x0, o));
-                    y0 = fminf(y0, __shfl_xor_sync(0xffffffffu, y0, o));
-                    x1 = fmaxf(x1, __shfl_xor_sync(0xffffffffu, x1, o));
-                    y1 = fmaxf(y1, __shfl_xor_sync(0xffffffffu, y1, o));
-                }
-                if (x0 <= x1) {
-                    const float xm = 0.5f * (x0 + x1), ym = 0.5f * (y0 + y1);
-                    const bool along_x = (x1 - x0) >= (y1 - y0);
-                    // (half the shorter side, rounded up by a relative 1e-6 for the midpoint's rounding)
-                    const float rr = (along_x ? 0.5f * (y1 - y0) : 0.5f * (x1 - x0)) * 1.000001f;
-                    occ_masks(c, along_x ? x0 : xm, along_x ? ym : y0, along_x ? x1 : xm, along_x ? ym : y1, rr,
-                              s_occ_rx + grp * S.n_body * occ_w, part, NWT);
-                }
+                // each warp makes the masks of the bodies of its own share
+                // (b = part mod NWT), so no other warp waits for them
+                tile_masks(c, rx, n_rx, r, rok, s_occ_rx + grp * S.n_body * occ_w, part, NWT);
                 __syncwarp();
             }
             AccS<T> acc{s_part + warp * prow * 32 + lane};     // the warp's partial sums, summed in place
@@ -2200,16 +2226,16 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
 
 // dynamic shared memory of a launch: scene, tables, then the path records
 // (body classes) or the wide partial sums of wide_chunks chunks (planar)
-static size_t smem_bytes(const DevScene &S, bool bodies, bool records, int blk, int rcap, int wide_chunks) {
+static size_t smem_bytes(const DevScene &S, bool bodies, bool records, int blk, int rcap, int wide_chunks,
+                         int occ_sets) {
     size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + S.n_face;
     if (S.n_body <= SMEM_BODY_MAX) n += 4 * S.n_body;
     if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;
-    const int occ_w = (records && S.n_body > 0 && S.n_body <= OCC_MAX_BODIES) ? (S.n_body + 31) >> 5 : 0;
-    const int tpb = (blk / 32) / WARPS_PER_TILE;
+    const int occ_w = (occ_sets > 0 && S.n_body > 0 && S.n_body <= OCC_MAX_BODIES) ? (S.n_body + 31) >> 5 : 0;
     return n * sizeof(float4) + WEIDEMAN_N * sizeof(float) + 16 +
            (records ? sizeof(float) * (blk / 32) * rcap * REC_N * 32 : 0) +
            sizeof(float) * (blk / 32) * wide_chunks * NFC * 6 * 32 +
-           sizeof(uint32_t) * (size_t)S.n_body * occ_w * (1 + tpb);
+           sizeof(uint32_t) * (size_t)S.n_body * occ_w * (1 + occ_sets);
 }
 
 // Launch state of one evaluation: the counters (escalations, one work queue
@@ -2246,7 +2272,10 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     const int rcap = (nch > 1) ? 6 : 5;
     const bool wide = CLS == CLS_PLANAR && sizeof(T) == 4 && !PATHS;
     if (nch < 1 || nch > MAX_CHUNKS || (!wide && !bodies && nch != 1)) return cudaErrorInvalidValue;
-    size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk, rcap, wide ? nch : 0);
+    // occluder masks (FP32 body kernels): one source-side set, and one
+    // receiver-side set per tile in flight (fields) or per warp (path lists)
+    const int occ_sets = (bodies && sizeof(T) == 4) ? (PATHS ? blk / 32 : blk / 32 / WARPS_PER_TILE) : 0;
+    size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk, rcap, wide ? nch : 0, occ_sets);
     cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     // persistent grid: the blocks that fit on the device at once, at most
