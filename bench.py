@@ -43,6 +43,11 @@ WORKLOAD = "room 10x8x3 m, 12 PEC triangles + 20 PEC cylinders, 256x256 rx at z=
 # Fock evaluation and per-path phase/accumulation.
 UNIT_FLOPS = dict(seg_tri=30, seg_body=25, inside_tri=60, image_cand=60, body_refl=150, creep_geom=150,
                   fock_evals=60, path_freq=30)
+# special-function (SFU) operations per unit: creeping geometry (tangent
+# angles, sincos of the attachment angles, sqrt), Fock evaluation per
+# polarisation pair (exp, sincos), the phase of a path at one frequency
+# (sincos), reflection geometry (acos, atan2, sqrt), image normalisation.
+UNIT_MUFU = dict(creep_geom=6, fock_evals=3, path_freq=2, body_refl=4, image_cand=1)
 
 
 def parse():
@@ -243,9 +248,9 @@ def cpu_baseline_and_accuracy(sc, E_gpu, paths_fn, target_s):
     return base, st, ref.counters, n
 
 
-def algorithmic_flops(counters, n_sample, n_rx, n_f):
+def algorithmic_flops(counters, n_sample, n_rx, n_f, units=UNIT_FLOPS):
     w = 0.0
-    for k, c in UNIT_FLOPS.items():
+    for k, c in units.items():
         if k == "path_freq":
             w += c * counters["paths"] * n_f
         else:
@@ -306,6 +311,7 @@ def batched_crowd(args, creep, dev, flush, peak_fn):
         rng = np.random.default_rng(77)
         flat = out.detach().cpu().numpy().astype(np.float64)
         flops_frames = 0.0          # algorithmic work of the sampled frames (scaled to their receivers)
+        mufu_frames = 0.0
         rx_frames = 0
         n_s = 0
         worst = {}
@@ -326,16 +332,14 @@ def batched_crowd(args, creep, dev, flush, peak_fn):
                 elif isinstance(v, (int, float)):
                     worst[k] = max(worst.get(k, v), v)
             flops_frames += algorithmic_flops(ref.counters, len(idx), n, n_f)
+            mufu_frames += algorithmic_flops(ref.counters, len(idx), n, n_f, UNIT_MUFU)
             rx_frames += n
             n_s += len(idx)
         # the sampled frames stand for all 64, in proportion to receivers
         flops = flops_frames * B.total_rx / rx_frames
-        peak, basis = peak_fn()
-        achieved = flops / (ms / 1e3) / 1e12
-        res["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                           "frac": achieved / peak, "traffic": None, "peak_basis": basis,
-                           "kernel": "evaluation: k_eval<float, false, 1|2|4> over all frames",
-                           "work_per_evaluation_flops": flops}
+        mufu = mufu_frames * B.total_rx / rx_frames
+        res["roofline"] = peak_fn(flops, mufu, ms, None)
+        res["roofline"]["kernel"] = "evaluation: k_eval<float, false, 1|2|4> over all frames"
         res["accuracy_vs_fp64_oracle"] = dict(worst, sample_receivers=n_s,
                                               sample="256 random receivers of each of 8 random frames")
         res["cpu_baseline"] = {"value": n_s * n_f / t_cpu, "unit": UNIT, "cores": os.cpu_count() or 1,
@@ -346,8 +350,9 @@ def batched_crowd(args, creep, dev, flush, peak_fn):
 # ---------------------------------------------------------------- adjoint
 def adjoint_room200(args, creep, dev, flush):
     """The adjoint form: the room with 200 PEC cylinders, 28 GHz, 64 x 64
-    receivers; one gradient step = forward fields (rt_evaluate), the path
-    list (rt_paths) and the adjoint (rt_backward) with a dB-power loss seed."""
+    receivers; one gradient step = the fields with their path list
+    (rt_evaluate_with_paths) and the adjoint (rt_backward) with a dB-power
+    loss seed.  The fields alone (rt_evaluate) are timed beside it."""
     import torch
     from paper_2310_10578_gb300 import scenes
     sc = scenes.room(n_cyl=200, nx=64, ny=64, freqs=(28e9,))
@@ -359,8 +364,7 @@ def adjoint_room200(args, creep, dev, flush):
     st = torch.cuda.current_stream()
 
     def step():
-        S.evaluate(rx, out=E, opts=opts)
-        codes, counts, _ = S.paths(rx, cap=64, opts=opts)
+        _, codes, counts, _ = S.evaluate_with_paths(rx, cap=64, out=E, opts=opts)
         p = (E.double() ** 2).sum(dim=(0, 1, 3))
         g = torch.where(p > 0, 20.0 / np.log(10.0) / torch.clamp(p, min=1e-300), torch.zeros_like(p))
         gE = (E.double() * g[None, None, :, None]).float()
@@ -376,7 +380,7 @@ def adjoint_room200(args, creep, dev, flush):
         ev[0].record(st)
         S.evaluate(rx, out=E, opts=opts)
         ev[1].record(st)
-        codes, counts, _ = S.paths(rx, cap=64, opts=opts)
+        _, codes, counts, _ = S.evaluate_with_paths(rx, cap=64, out=E, opts=opts)
         ev[2].record(st)
         p = (E.double() ** 2).sum(dim=(0, 1, 3))
         g = torch.where(p > 0, 20.0 / np.log(10.0) / torch.clamp(p, min=1e-300), torch.zeros_like(p))
@@ -387,12 +391,12 @@ def adjoint_room200(args, creep, dev, flush):
     torch.cuda.synchronize()
     t = np.array([[m[k].elapsed_time(m[k + 1]) for k in range(3)] for m in marks])
     fwd, paths, bwd = (float(np.mean(t[:, k])) for k in range(3))
-    total = float(np.mean([m[0].elapsed_time(m[3]) for m in marks]))
     n_paths = int(counts.sum())
     return {"workload": "room 10x8x3 m, 12 PEC triangles + 200 PEC cylinders, 64x64 rx at z=1.2 m, 28 GHz, refl<=2",
             "loss": "sum over receivers of received power in dB (seed dLoss/dE = 20/ln10 E/|E|^2)",
-            "ms_forward": fwd, "ms_path_list": paths, "ms_backward_incl_seed": bwd, "ms_step": total,
-            "value": n / (total / 1e3), "unit": "receiver gradients/s (forward + path list + adjoint)",
+            "ms_fields_only": fwd, "ms_fields_with_path_list": paths, "ms_backward_incl_seed": bwd,
+            "ms_step": paths + bwd,
+            "value": n / ((paths + bwd) / 1e3), "unit": "receiver gradients/s (fields with path list + adjoint)",
             "paths": n_paths, "steps": args.batched_steps,
             "gradients": "d/d(200 x (cx, cy, cz, a)), d/d(Tx), d/d(f); FP64 dual numbers",
             "l2": "flushed between timed steps (256 MiB write)"}
@@ -471,13 +475,29 @@ def main():
         e2e_t.append(time.perf_counter() - t0)
     barrier()
     props = torch.cuda.get_device_properties(dev)
+    # measured FP32 FFMA and SFU rates (microbenchmarks of the library), the
+    # roofline's denominators; the peak derived from unit counts and clock
+    # is kept beside them
+    ffma_meas, mufu_meas = creep.alu_peaks()
+
+    def peak_fn(flops, mufu, ms_eval, traffic):
+        c = (sampler.clocks_now() if sampler else None) or {}
+        sm_max = c.get("sm_max_mhz") or 2070.0
+        derived = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12
+        achieved = flops / (ms_eval / 1e3) / 1e12
+        mufu_rate = mufu / (ms_eval / 1e3) / 1e9
+        return {"bound": "alu", "achieved": achieved, "peak": ffma_meas, "unit": "TFLOP/s",
+                "frac": achieved / ffma_meas, "traffic": traffic,
+                "peak_basis": "measured: FFMA microbenchmark rt_alu_peaks in this run",
+                "peak_derived": derived,
+                "peak_derived_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz" % (props.multi_processor_count, sm_max),
+                "work_per_evaluation_flops": flops,
+                "sfu": {"achieved": mufu_rate, "peak": mufu_meas, "unit": "Gop/s", "frac": mufu_rate / mufu_meas,
+                        "peak_basis": "measured: ex2.approx microbenchmark rt_alu_peaks in this run",
+                        "work_per_evaluation_ops": mufu}}
+
     batched = None
     if world == 1 and not args.no_batched:
-        def peak_fn():
-            c = (sampler.clocks_now() if sampler else None) or {}
-            sm_max = c.get("sm_max_mhz") or 2070.0
-            return (props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12,
-                    "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived, FFMA)" % (props.multi_processor_count, sm_max))
         batched = batched_crowd(args, creep, dev, flush, peak_fn)
     adj = None
     if world == 1 and not args.no_adjoint:
@@ -520,19 +540,13 @@ def main():
         line["cpu_baseline"] = base
         line["accuracy_vs_fp64_oracle"] = dict(acc, sample_receivers=n_s)
         flops = algorithmic_flops(counters, n_s, n_rx, n_f)
-        sm_max = (clocks or {}).get("sm_max_mhz") or 2070.0
-        peak = props.multi_processor_count * 128 * 2 * sm_max * 1e6 / 1e12      # FP32 FFMA lanes x 2 x clock
-        achieved = flops / (ms / 1e3) / 1e12
+        mufu = algorithmic_flops(counters, n_s, n_rx, n_f, UNIT_MUFU)
         # the unit timed is one evaluation: the three class kernels, which
         # overlap through programmatic dependent launch (their durations are
         # not separable with events); per-kernel shares are in the ncu launch
         # list under profiles/
-        line["roofline"] = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                            "frac": achieved / peak, "traffic": _profiled_traffic(),
-                            "peak_basis": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived, FFMA)" %
-                                          (props.multi_processor_count, sm_max),
-                            "kernel": "evaluation: k_eval<float, false, 1|2|4> (planar, body reflection, creeping)",
-                            "work_per_evaluation_flops": flops}
+        line["roofline"] = peak_fn(flops, mufu, ms, _profiled_traffic())
+        line["roofline"]["kernel"] = "evaluation: k_eval<float, false, 1|2|4> (planar, body reflection, creeping)"
     if batched is not None:
         line["batched"] = batched
     if adj is not None:

@@ -275,6 +275,17 @@ int rt_batch_replay(rt_batch *batch, void *stream);
 int rt_batch_get_stats(rt_batch *batch, rt_stats *out);
 
 /*
+ * The evaluation of rt_evaluate and, in the same kernels, each receiver's
+ * path list (the visibility decisions of Eqs. 1-2): codes, counts, cap and
+ * flags as for rt_paths, except that a receiver's codes come in no
+ * particular order (the same set as rt_paths lists; sort to compare).  The
+ * list rt_backward needs, at the cost of one evaluation.
+ */
+int rt_evaluate_with_paths(rt_scene *scene, const float *rx_soa, int n_rx, float *e_out,
+                           uint64_t *codes, int32_t *counts, int cap, uint32_t *flags,
+                           const rt_options *opt, void *stream);
+
+/*
  * rt_backward -- gradient of a real loss through the fields (the adjoint of
  * rt_evaluate: its vector-Jacobian product) with respect to every body's
  * centre and radius, the transmitter position and every frequency, with
@@ -282,8 +293,9 @@ int rt_batch_get_stats(rt_batch *batch, rt_stats *out);
  * receivers and options, and each one's geometry and field (Eqs. 1-4) are
  * recomputed in FP64 dual numbers, nothing per path being stored.
  *   rx_soa, n_rx          device, as rt_evaluate.
- *   codes, counts, cap    device, as rt_paths wrote them (a receiver with more
- *                         than cap paths contributes its first cap).
+ *   codes, counts, cap    device, as rt_paths or rt_evaluate_with_paths wrote
+ *                         them (a receiver with more than cap paths
+ *                         contributes the cap listed).
  *   grad_e                device float [n_f][3][n_rx][2]: dLoss/dRe E and
  *                         dLoss/dIm E, the layout of rt_evaluate's e_out.
  *   grad_bodies           device double [n_body][4]: dLoss/d(cx, cy, cz, a)
@@ -297,6 +309,16 @@ int rt_batch_get_stats(rt_batch *batch, rt_stats *out);
 int rt_backward(rt_scene *scene, const float *rx_soa, int n_rx, const uint64_t *codes,
                 const int32_t *counts, int cap, const float *grad_e, double *grad_bodies,
                 double *grad_tx, double *grad_freqs, const rt_options *opt, void *stream);
+
+/*
+ * rt_alu_peaks -- measured FP32 throughput of the current device, the
+ * denominators of the evaluation's ALU roofline (an engineering addition: the
+ * paper has no counterpart).  Runs two short microbenchmarks on `stream` and
+ * synchronises: *ffma_tflops = FFMA rate (2 flops each) in TFLOP/s,
+ * *mufu_gops = special-function-unit rate (ex2.approx) in Gop/s.  Allocates
+ * and frees a small device buffer.  Errors: RT_ERR_ARG, RT_ERR_CUDA.
+ */
+int rt_alu_peaks(double *ffma_tflops, double *mufu_gops, void *stream);
 
 /* Counters of the last rt_evaluate / rt_paths on this scene (synchronises its stream). */
 int rt_get_stats(rt_scene *scene, rt_stats *out);

@@ -1,8 +1,8 @@
 """Differentiable field evaluation: a torch.autograd.Function over the C ABI.
 
-forward  -- rt_evaluate (FP32 fields) and rt_paths (the path list) at fixed
-            receivers for the given body centres/radii, transmitter position
-            and frequencies;
+forward  -- rt_evaluate_with_paths: the FP32 fields and, from the same
+            kernels, the path list at fixed receivers for the given body
+            centres/radii, transmitter position and frequencies;
 backward -- rt_backward: the adjoint of the evaluation with the path list of
             the forward pass held fixed (visibility frozen), each path's
             geometry and field recomputed in FP64 dual numbers.
@@ -54,8 +54,7 @@ class CreepField(torch.autograd.Function):
     @staticmethod
     def forward(ctx, body_params, tx, freqs, static):
         S = static.scene(body_params, tx, freqs)
-        E = S.evaluate(static.rx, opts=static.opts)
-        codes, counts, _ = S.paths(static.rx, cap=static.cap, opts=static.opts)
+        E, codes, counts, _ = S.evaluate_with_paths(static.rx, cap=static.cap, opts=static.opts)
         ctx.S, ctx.static = S, static
         ctx.save_for_backward(codes, counts)
         ctx.dtypes = (body_params.dtype, tx.dtype, freqs.dtype)
@@ -81,3 +80,25 @@ def power_db(E, zone=None):
     if zone is not None:
         p = p[zone]
     return 10.0 * torch.log10(p)
+
+
+# ---- several GPUs: receivers are independent, so each rank evaluates a
+# contiguous share of them and the parameter gradients (body centres and
+# radii, transmitter, frequencies) are summed over the ranks: the one
+# collective of the adjoint.
+
+def shard(n_rx, rank, world):
+    """The contiguous receiver range [lo, hi) of `rank` of `world` ranks."""
+    base, extra = divmod(int(n_rx), int(world))
+    lo = rank * base + min(rank, extra)
+    return lo, lo + base + (1 if rank < extra else 0)
+
+
+def allreduce_gradients(tensors, group=None):
+    """Sum each tensor over the ranks in place (no-op on one process)."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
+        return tensors
+    for t in tensors:
+        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    return tensors

@@ -24,7 +24,8 @@ FOCK_NRES = 8
 EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "rt_evaluate",
            "rt_evaluate_host", "rt_evaluate_host_noalloc", "rt_paths", "rt_get_stats", "rt_fock_table",
            "rt_last_error", "rt_batch_create", "rt_batch_destroy", "rt_batch_set_frame", "rt_batch_evaluate",
-           "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats", "rt_backward")
+           "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats", "rt_backward", "rt_alu_peaks",
+           "rt_evaluate_with_paths")
 RT_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -82,6 +83,8 @@ def load(build_if_missing=True):
     lib.rt_batch_replay.argtypes = [P, P]
     lib.rt_batch_get_stats.argtypes = [P, P]
     lib.rt_backward.argtypes = [P, P, I, P, P, I, P, P, P, P, P, P]
+    lib.rt_alu_peaks.argtypes = [P, P, P]
+    lib.rt_evaluate_with_paths.argtypes = [P, P, I, P, P, P, I, P, P, P]
     _lib = lib
     return lib
 
@@ -211,6 +214,23 @@ class Scene:
                              ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
         return codes, counts, fl
 
+    def evaluate_with_paths(self, rx_soa, cap=256, out=None, opts=None, stream=None):
+        """Fields and, from the same kernels, the path lists (codes unordered
+        per receiver): (E [n_f, 3, n, 2], codes [n, cap] int64, counts [n]
+        int32, flags [n] int32)."""
+        import torch
+        n = rx_soa.shape[1]
+        dev = rx_soa.device
+        if out is None:
+            out = torch.empty((self.n_f, 3, n, 2), dtype=torch.float32, device=dev)
+        codes = torch.zeros((n, cap), dtype=torch.int64, device=dev)
+        counts = torch.zeros(n, dtype=torch.int32, device=dev)
+        fl = torch.zeros(n, dtype=torch.int32, device=dev)
+        _check(_lib.rt_evaluate_with_paths(self._h, _ptr(rx_soa), n, _ptr(out), _ptr(codes), _ptr(counts), cap,
+                                           _ptr(fl), ctypes.byref(opts) if opts is not None else None,
+                                           _stream_handle(stream)))
+        return out, codes, counts, fl
+
     def backward(self, rx_soa, codes, counts, grad_e, opts=None, stream=None):
         """Adjoint of evaluate (rt_backward): dLoss/d(body centres and radii
         [n_body, 4], transmitter [3], frequencies [n_f]) as float64 CUDA
@@ -308,6 +328,14 @@ class Batch:
         st = rt_stats()
         _check(_lib.rt_batch_get_stats(self._h, ctypes.byref(st)))
         return {"escalated_candidates": int(st.escalated_candidates), "kernel_launches": int(st.kernel_launches)}
+
+
+def alu_peaks(stream=None):
+    """Measured FP32 FFMA (TFLOP/s) and SFU (Gop/s) rates of the current device."""
+    lib = load()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(lib.rt_alu_peaks(ctypes.byref(a), ctypes.byref(b), _stream_handle(stream)))
+    return a.value, b.value
 
 
 def fock_table():

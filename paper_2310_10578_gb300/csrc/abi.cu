@@ -544,6 +544,23 @@ int rt_paths(rt_scene *s, const float *rx_soa, int n_rx, uint64_t *codes, int32_
     return launch_eval(D, rx_soa, n_rx, nullptr, flags, codes, counts, cap, prec, s->d_esc, st, &s->last_launches);
 }
 
+int rt_evaluate_with_paths(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint64_t *codes, int32_t *counts,
+                           int cap, uint32_t *flags, const rt_options *opt, void *stream) {
+    if (!s) return fail(RT_ERR_ARG, "rt_evaluate_with_paths: NULL scene");
+    if (n_rx < 0 || cap < 1) return fail(RT_ERR_ARG, "rt_evaluate_with_paths: n_rx < 0 or cap < 1");
+    DevScene D;
+    int prec;
+    int rc = make_dev(s, opt, D, &prec);
+    if (rc != RT_OK) return rc;
+    if (n_rx > 0 && (!rx_soa || !e_out || !codes || !counts))
+        return fail(RT_ERR_ARG, "rt_evaluate_with_paths: NULL buffer");
+    if (n_rx == 0) return RT_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(cudaMemsetAsync(s->d_esc, 0, sizeof(unsigned long long) * CTR_N, st));
+    s->last_stream = st;
+    return launch_eval(D, rx_soa, n_rx, e_out, flags, codes, counts, cap, prec, s->d_esc, st, &s->last_launches);
+}
+
 int rt_backward(rt_scene *s, const float *rx_soa, int n_rx, const uint64_t *codes, const int32_t *counts, int cap,
                 const float *grad_e, double *grad_bodies, double *grad_tx, double *grad_freqs, const rt_options *opt,
                 void *stream) {

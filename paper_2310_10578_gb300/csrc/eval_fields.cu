@@ -1610,10 +1610,22 @@ __device__ __forceinline__ void apply_records(const Ctx &c, AccS<float> &acc, co
 // share (1 + i n_face + j) mod nparts, the paths of body b to share
 // b mod nparts -- summed into acc; the receiver's flags, the count of FP64
 // re-decisions and (PATHS) the path codes from slot npath on.
-template <typename T, bool PATHS, int CLS>
+// fields with the path list: the warps sharing a receiver take slots by
+// atomics (the list is in no particular order); returns the overflow flag
+__device__ __noinline__ uint32_t list_path(uint64_t *codes, int32_t *counts, int cap, int r, uint64_t code) {
+    const int slot = atomicAdd(&counts[r], 1);
+    if (slot < cap) {
+        codes[(size_t)r * cap + slot] = code;
+        return 0u;
+    }
+    return RT_FLAG_OVERFLOW;
+}
+
+template <typename T, bool PATHS, int CLS, bool LIST = false>
 __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, int nfq, unsigned enable, int max_order,
                                               const float *__restrict__ rx, int n_rx, int r,
-                                              uint64_t *__restrict__ codes, int cap, double half_lambda_max,
+                                              uint64_t *__restrict__ codes, int32_t *__restrict__ counts, int cap,
+                                              double half_lambda_max,
                                               int b_begin, int b_end, bool first_chunk, bool may_flush, int rcap,
                                               const uint32_t *occ_rx, int part, int nparts,
                                               AccS<T> acc, float *rec, uint32_t &fl, unsigned &nesc, int &npath,
@@ -1638,6 +1650,8 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
         if (PATHS) {
             if (npath < cap) codes[(size_t)r * cap + npath] = pcode(type, a, b);
             else fl |= RT_FLAG_OVERFLOW;
+        } else if constexpr (LIST) {
+            fl |= list_path(codes, counts, cap, r, pcode(type, a, b));
         }
         ++npath;
     };
@@ -1930,7 +1944,7 @@ __device__ __forceinline__ void stage_words(void *dst, const void *src, int n) {
         static_cast<uint32_t *>(dst)[i] = static_cast<const uint32_t *>(src)[i];
 }
 
-template <typename T, bool PATHS, int CLS>
+template <typename T, bool PATHS, int CLS, bool LIST = false>
 __global__ void __launch_bounds__(blk_of(CLS, sizeof(T) == 4), min_blocks(CLS, sizeof(T) == 4))
 k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frames, unsigned long long n_tiles,
        const float *__restrict__ rx_base, const int32_t *__restrict__ perm, float *__restrict__ e_base,
@@ -2044,7 +2058,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                 unsigned nesc;
                 int npath = accumulate ? counts[r] : 0;
                 int nrec;
-                eval_receiver<T, PATHS, CLS>(c, s_fqs, 1, S.enable, S.max_order, rx, n_rx, r, codes, cap, F1.hl,
+                eval_receiver<T, PATHS, CLS, LIST>(c, s_fqs, 1, S.enable, S.max_order, rx, n_rx, r, codes, counts, cap,
+                                                   F1.hl,
                                              0, c.n_body, true, false, 0, occ_on ? s_occ_mine : nullptr, 0, 1, acc,
                                              nullptr, fl, nesc, npath, nrec);
                 counts[r] = npath;
@@ -2164,7 +2179,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                 unsigned nesc = 0;
                 int npath = 0, nrec = 0;
                 if (rok)
-                    eval_receiver<T, PATHS, CLS>(c, s_fqs, WIDE ? nch : 1, S.enable, S.max_order, rx, n_rx, r, codes, cap,
+                    eval_receiver<T, PATHS, CLS, LIST>(c, s_fqs, WIDE ? nch : 1, S.enable, S.max_order, rx, n_rx, r,
+                                                       codes, counts, cap,
                                                  Fr.hl, b0, min(b0 + bc, n_b), b0 == 0, nch == 1, rcap,
                                                  occ_on ? s_occ_rx + grp * S.n_body * occ_w : nullptr, part,
                                                  NWT, acc, rec, fl, nesc, npath, nrec);
@@ -2262,7 +2278,7 @@ struct Work {
     int cap;
 };
 
-template <typename T, bool PATHS, int CLS>
+template <typename T, bool PATHS, int CLS, bool LIST = false>
 static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch, int accumulate, LaunchCtx &L) {
     if (L.n >= CTR_QUEUES) return cudaErrorInvalidValue;
     constexpr bool bodies = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
@@ -2276,15 +2292,17 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     // receiver-side set per tile in flight (fields) or per warp (path lists)
     const int occ_sets = (bodies && sizeof(T) == 4) ? (PATHS ? blk / 32 : blk / 32 / WARPS_PER_TILE) : 0;
     size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk, rcap, wide ? nch : 0, occ_sets);
-    cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     // persistent grid: the blocks that fit on the device at once, at most
     // one per work unit
     int dev = 0, nsm = 0, occ = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<T, PATHS, CLS>, blk, sm)) != cudaSuccess) return e;
-    constexpr int tiles_per_unit = PATHS ? blk / 32 : (bodies ? blk / 32 / WARPS_PER_TILE : 1);
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<T, PATHS, CLS, LIST>, blk, sm)) != cudaSuccess) return e;
+    // (path lists: each warp takes whole tiles; up to one block per tile, so
+    // that a few tiles spread over as many SMs)
+    constexpr int tiles_per_unit = PATHS ? 1 : (bodies ? blk / 32 / WARPS_PER_TILE : 1);
     long long need = (long long)((W.n_tiles + tiles_per_unit - 1) / tiles_per_unit);
     long long cap_blocks = (long long)nsm * (occ > 0 ? occ : 1);
     int grid = (int)(need < cap_blocks ? need : cap_blocks);
@@ -2301,7 +2319,7 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = L.n > 0 ? 1 : 0;
-    e = cudaLaunchKernelEx(&cfg, k_eval<T, PATHS, CLS>, S, W.F1, W.frames, W.n_frames, W.n_tiles, W.rx, W.perm, W.e, W.fl,
+    e = cudaLaunchKernelEx(&cfg, k_eval<T, PATHS, CLS, LIST>, S, W.F1, W.frames, W.n_frames, W.n_tiles, W.rx, W.perm, W.e, W.fl,
                            W.codes, W.counts, W.cap, ch0, nch, rcap, accumulate, L.ctr, L.ctr + 1 + L.n);
     ++L.n;
     return e != cudaSuccess ? e : cudaGetLastError();
@@ -2312,7 +2330,7 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
 // PLANAR_CHUNKS chunks, then each body kernel once for all chunks (the
 // geometry of a pass serves every chunk it covers).
 // The first launch writes the outputs, the later ones add to them.
-template <typename T, bool PATHS>
+template <typename T, bool PATHS, bool LIST = false>
 static cudaError_t launch_all(const DevScene &S, const Work &W, int nchunks, LaunchCtx &L) {
     cudaError_t e = cudaSuccess;
     const bool chunked_bodies = PATHS || sizeof(T) != 4;
@@ -2321,24 +2339,30 @@ static cudaError_t launch_all(const DevScene &S, const Work &W, int nchunks, Lau
     const int pstep = chunked_bodies ? 1 : PLANAR_CHUNKS;
     for (int ch = 0; ch < nchunks && e == cudaSuccess; ch += pstep) {
         const int n = nchunks - ch < pstep ? nchunks - ch : pstep;
-        e = launch_one<T, PATHS, CLS_PLANAR>(S, W, ch, n, 0, L);
-        if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL>(S, W, ch, 1, 1, L);
-        if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_CREEP>(S, W, ch, 1, 1, L);
+        e = launch_one<T, PATHS, CLS_PLANAR, LIST>(S, W, ch, n, 0, L);
+        if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL, LIST>(S, W, ch, 1, 1, L);
+        if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_CREEP, LIST>(S, W, ch, 1, 1, L);
     }
-    if (!chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL>(S, W, 0, nchunks, 1, L);
-    if (!chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_CREEP>(S, W, 0, nchunks, 1, L);
+    if (!chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL, LIST>(S, W, 0, nchunks, 1, L);
+    if (!chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_CREEP, LIST>(S, W, 0, nchunks, 1, L);
     return e;
 }
 
-static int run(const DevScene &S, const Work &W, int precision, bool paths, unsigned long long *ctr,
+// paths: path lists only; list: fields and the path list (FP32: from the
+// same kernels, unordered; FP64: the fields, then the path-list kernels)
+static int run(const DevScene &S, const Work &W, int precision, bool paths, bool list, unsigned long long *ctr,
                cudaStream_t stream, int *n_launches) {
     LaunchCtx L{ctr, 0, stream};
     const int nchunks = paths ? 1 : (S.n_f + NFC - 1) / NFC;
     cudaError_t e;
-    if (precision == RT_PREC_FP64)
+    if (precision == RT_PREC_FP64) {
         e = paths ? launch_all<dx, true>(S, W, nchunks, L) : launch_all<dx, false>(S, W, nchunks, L);
-    else
-        e = paths ? launch_all<float, true>(S, W, nchunks, L) : launch_all<float, false>(S, W, nchunks, L);
+        if (list && e == cudaSuccess) e = launch_all<dx, true>(S, W, 1, L);
+    } else if (paths) {
+        e = launch_all<float, true>(S, W, nchunks, L);
+    } else {
+        e = list ? launch_all<float, false, true>(S, W, nchunks, L) : launch_all<float, false>(S, W, nchunks, L);
+    }
     *n_launches = L.n;
     if (e != cudaSuccess) {
         set_error(std::string("k_eval launch: ") + cudaGetErrorString(e));
@@ -2351,6 +2375,8 @@ int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, 
                 uint64_t *codes, int32_t *counts, int cap, int precision, unsigned long long *ctr,
                 cudaStream_t stream, int *n_launches) {
     *n_launches = 0;
+    // fields and a path list (unordered): counts zeroed first
+    const bool paths = codes != nullptr && e_out == nullptr;
     if (n_rx <= 0) return RT_OK;
     Work W = {};
     W.F1.body = S.body;
@@ -2368,7 +2394,14 @@ int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, 
     W.n_tiles = ((unsigned long long)n_rx + 31ull) >> 5;
     W.rx = rx_soa; W.e = e_out; W.fl = flags;
     W.codes = codes; W.counts = counts; W.cap = cap;
-    return run(S, W, precision, codes != nullptr, ctr, stream, n_launches);
+    if (codes && e_out) {
+        cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_rx, stream);
+        if (e != cudaSuccess) {
+            set_error(std::string("launch_eval: ") + cudaGetErrorString(e));
+            return RT_ERR_CUDA;
+        }
+    }
+    return run(S, W, precision, paths, codes && e_out, ctr, stream, n_launches);
 }
 
 int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const FrameDev *frames_host, int n_frames,
@@ -2382,7 +2415,7 @@ int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const Frame
     W.n_frames = n_frames;
     W.n_tiles = n_tiles;
     W.rx = rx_soa; W.perm = perm; W.e = e_out; W.fl = flags;
-    return run(S, W, precision, false, ctr, stream, n_launches);
+    return run(S, W, precision, false, false, ctr, stream, n_launches);
 }
 
 // ============================================================== adjoint

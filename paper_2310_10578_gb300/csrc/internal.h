@@ -105,8 +105,9 @@ struct FrameDev {
 constexpr int CTR_QUEUES = 64;
 constexpr int CTR_N = 1 + CTR_QUEUES;
 
-// Evaluate (codes == nullptr) or list paths; *n_launches receives the number
-// of kernel launches queued.
+// Evaluate (codes == nullptr), list paths (e_out == nullptr: canonical
+// order), or both (the path list in no particular order); *n_launches
+// receives the number of kernel launches queued.
 int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
                 uint64_t *codes, int32_t *counts, int cap, int precision, unsigned long long *ctr,
                 cudaStream_t stream, int *n_launches);

@@ -1,0 +1,102 @@
+// peaks.cu -- measured FP32 FFMA and SFU (MUFU) throughput of the current
+// device: the denominators of the evaluation's ALU roofline.
+//
+// Each thread runs independent dependency chains (enough of them to hide the
+// pipeline latency) for a fixed number of iterations on registers; the grid
+// fills every SM with 8 resident blocks; the time is taken with CUDA events
+// around one launch after a warm-up launch.  FFMA: 2 flops per instruction.
+// SFU: one ex2.approx.f32 per operation (the special-function unit's
+// exponential), written as inline PTX.
+#include "internal.h"
+
+namespace creep {
+
+namespace {
+
+constexpr int PK_CHAINS = 8;
+constexpr int PK_THREADS = 256;
+
+__global__ void __launch_bounds__(PK_THREADS) k_ffma(float *out, int iters, float a, float b) {
+    float x[PK_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PK_CHAINS; ++k) x[k] = threadIdx.x * 1e-3f + k;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < PK_CHAINS; ++k) x[k] = fmaf(x[k], a, b);
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < PK_CHAINS; ++k) s += x[k];
+    if (s == 12345.678f) out[blockIdx.x] = s;         // keeps the chains live; never true in practice
+}
+
+__device__ __forceinline__ float ex2_approx(float v) {
+    float r;
+    asm volatile("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__global__ void __launch_bounds__(PK_THREADS) k_mufu(float *out, int iters, float a) {
+    float x[PK_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PK_CHAINS; ++k) x[k] = threadIdx.x * 1e-6f + k * 1e-3f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < PK_CHAINS; ++k) x[k] = ex2_approx(x[k]) * a;   // stays near 1: 2^x * a, x ~ 0
+    }
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < PK_CHAINS; ++k) s += x[k];
+    if (s == 12345.678f) out[blockIdx.x] = s;
+}
+
+}  // namespace
+
+}  // namespace creep
+
+using namespace creep;
+
+extern "C" int rt_alu_peaks(double *ffma_tflops, double *mufu_gops, void *stream) {
+    if (!ffma_tflops || !mufu_gops) {
+        set_error("rt_alu_peaks: NULL argument");
+        return RT_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    float *out = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&out, sizeof(float) * 8 * (size_t)nsm);
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    const int grid = 8 * nsm, iters_f = 1 << 16, iters_m = 1 << 13;
+    float ms_f = 0.0f, ms_m = 0.0f;
+    if (e == cudaSuccess) {
+        k_ffma<<<grid, PK_THREADS, 0, st>>>(out, iters_f / 16, 0.999999f, 1e-7f);      // warm-up
+        cudaEventRecord(t0, st);
+        k_ffma<<<grid, PK_THREADS, 0, st>>>(out, iters_f, 0.999999f, 1e-7f);
+        cudaEventRecord(t1, st);
+        e = cudaEventSynchronize(t1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_f, t0, t1);
+    }
+    if (e == cudaSuccess) {
+        k_mufu<<<grid, PK_THREADS, 0, st>>>(out, iters_m / 16, 0.5f);
+        cudaEventRecord(t0, st);
+        k_mufu<<<grid, PK_THREADS, 0, st>>>(out, iters_m, 0.5f);
+        cudaEventRecord(t1, st);
+        e = cudaEventSynchronize(t1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms_m, t0, t1);
+    }
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    cudaFree(out);
+    if (e != cudaSuccess) {
+        set_error(std::string("rt_alu_peaks: ") + cudaGetErrorString(e));
+        return RT_ERR_CUDA;
+    }
+    const double threads = (double)grid * PK_THREADS;
+    *ffma_tflops = 2.0 * PK_CHAINS * (double)iters_f * threads / (ms_f * 1e-3) / 1e12;
+    *mufu_gops = (double)PK_CHAINS * (double)iters_m * threads / (ms_m * 1e-3) / 1e9;
+    return RT_OK;
+}

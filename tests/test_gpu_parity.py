@@ -215,3 +215,32 @@ def test_host_entry_point_matches_device(creep):
     E = S.evaluate(rx).cpu().numpy()
     Eh, flh = S.evaluate_host(sc.rx_soa(), flags=True)
     assert np.array_equal(E, Eh)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_evaluate_with_paths(creep, precision):
+    """Fields and path lists in one call (FP32: from the same kernels): the
+    fields of rt_evaluate bit for bit, the path sets of rt_paths (in no
+    particular order), the same counts and flags; with a small capacity the
+    overflow flag and a subset of the list."""
+    sc = scenes.room(n_cyl=20, nx=40, ny=31, freqs=(2.4e9, 28e9), seed=5)
+    S = creep.Scene.from_scene(sc)
+    rx = torch.tensor(sc.rx_soa(), device="cuda")
+    opts = creep.options(max_order=2, precision=creep.RT_PREC_FP64 if precision == "fp64" else creep.RT_PREC_FP32)
+    fl0 = torch.zeros(sc.n_rx, dtype=torch.int32, device="cuda")
+    E0 = S.evaluate(rx, flags=fl0, opts=opts)
+    c0, n0, _ = S.paths(rx, opts=opts)
+    E1, c1, n1, fl1 = S.evaluate_with_paths(rx, opts=opts)
+    torch.cuda.synchronize()
+    assert torch.equal(E0, E1) and torch.equal(n0, n1) and torch.equal(fl0, fl1)
+    c0, c1, n = c0.cpu().numpy(), c1.cpu().numpy(), n0.cpu().numpy()
+    for r in range(sc.n_rx):
+        assert np.array_equal(np.sort(c0[r, :n[r]]), np.sort(c1[r, :n[r]])), r
+    E2, c2, n2, fl2 = S.evaluate_with_paths(rx, cap=4, opts=opts)
+    torch.cuda.synchronize()
+    assert torch.equal(E0, E2) and torch.equal(n0, n2)
+    c2, fl2 = c2.cpu().numpy(), fl2.cpu().numpy().astype(np.uint32)
+    over = n > 4
+    assert over.any() and np.array_equal((fl2 & creep.RT_FLAG_OVERFLOW) != 0, over)
+    for r in np.nonzero(over)[0][:200]:
+        assert set(c2[r].tolist()) <= set(c0[r, :n[r]].tolist())

@@ -69,3 +69,49 @@ def test_single_process_reduction_and_throughput():
     import bench
     assert bench.max_over_ranks([3.0, 4.5]) == [3.0, 4.5]
     assert bench.job_throughput(196608, 4, 0.5) == pytest.approx(4 * 196608 / 0.5)
+
+
+def _adjoint_worker(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        from paper_2310_10578_gb300 import adjoint
+        # stand-in for each receiver's contribution to the parameter gradient
+        # (the adjoint is a sum over receivers): the rank's share, then the sum
+        contrib = np.random.default_rng(0).standard_normal((4097, 9))
+        lo, hi = adjoint.shard(len(contrib), rank, world)
+        g = torch.tensor(contrib[lo:hi].sum(axis=0))
+        adjoint.allreduce_gradients([g])
+        q.put((rank, lo, hi, g.numpy()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_adjoint_gradient_sum_over_two_gloo_ranks():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_adjoint_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=240) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    full = np.random.default_rng(0).standard_normal((4097, 9)).sum(axis=0)
+    assert [(lo, hi) for _, lo, hi, _ in res] == [(0, 2049), (2049, 4097)]
+    for _, _, _, g in res:
+        assert np.allclose(g, full, rtol=1e-12, atol=1e-12)
+
+
+def test_shards_cover_every_receiver_once():
+    from paper_2310_10578_gb300 import adjoint
+    for n in (0, 1, 7, 4096, 4097):
+        for world in (1, 2, 3, 8):
+            ranges = [adjoint.shard(n, r, world) for r in range(world)]
+            assert ranges[0][0] == 0 and ranges[-1][1] == n
+            assert all(ranges[i][1] == ranges[i + 1][0] for i in range(world - 1))
+            sizes = [hi - lo for lo, hi in ranges]
+            assert max(sizes) - min(sizes) <= 1
