@@ -277,6 +277,7 @@ def batched_crowd(args, creep, dev, flush, peak_fn):
     opts = creep.options(max_order=2)
     side = torch.cuda.Stream(device=dev)
     side.wait_stream(torch.cuda.current_stream())
+    shape = B.tune(rx, out, opts=opts, stream=side)          # the batch's autotuner (tile shape)
     B.capture(rx, out, opts=opts, stream=side)
     for _ in range(3):
         B.replay(stream=side)
@@ -301,6 +302,8 @@ def batched_crowd(args, creep, dev, flush, peak_fn):
            "launch": "captured CUDA graph: counter resets + %d kernels (receiver spatial order: 3; planar, body "
                      "reflection, creeping)" % stats["kernel_launches"],
            "gpu_launches_per_step": stats["kernel_launches"],
+           "tile_shape": {"planar_warps_per_tile": shape[0], "body_warps_per_tile": shape[1],
+                          "planar_chunks_per_launch": shape[2], "chosen_by": "rt_batch_tune"},
            "fp64_escalated_candidates": stats["escalated_candidates"],
            "l2": "flushed between timed steps (256 MiB write)"}
     if not args.no_cpu_baseline:
@@ -428,6 +431,7 @@ def main():
     out = torch.empty((n_f, 3, n_rx, 2), dtype=torch.float32, device=dev)
     opts = creep.options(max_order=2)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    shape = S.tune(rx, out=out, opts=opts)          # the scene's autotuner (tile shape), before any timing
 
     def barrier():
         if world > 1:
@@ -518,7 +522,9 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_rx": n_rx, "n_freq": n_f, "n_cylinders": int(sc.bodies.shape[0]),
                        "n_triangles": int(sc.tri.shape[0]), "max_refl_order": 2, "precision": "fp32",
-                       "l2": "flushed between timed steps (256 MiB write)"},
+                       "l2": "flushed between timed steps (256 MiB write)",
+                       "tile_shape": {"planar_warps_per_tile": shape[0], "body_warps_per_tile": shape[1],
+                                      "planar_chunks_per_launch": shape[2], "chosen_by": "rt_tune"}},
             "clocks": clocks,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 3 * 4 * n_rx,
                     "d2h_bytes_per_step": n_f * 3 * n_rx * 8},

@@ -271,6 +271,29 @@ int rt_batch_capture(rt_batch *batch, const float *rx_soa, float *e_out, uint32_
 /* Launch the captured graph on `stream` (RT_ERR_STATE if none). */
 int rt_batch_replay(rt_batch *batch, void *stream);
 
+/*
+ * The batch's tile shape: shape[0] warps per 32-receiver tile in the planar
+ * kernel (1, 2 or 4), shape[1] in the body kernels (1, 2, 3, 4, 6 or 12),
+ * shape[2] frequency chunks of 4 per planar launch (1-4); default {4, 4, 4}.
+ * Fields differ between shapes only in the rounding of the sums over a
+ * tile's warps.  rt_batch_set_shape: RT_ERR_ARG outside those sets.
+ */
+int rt_batch_set_shape(rt_batch *batch, const int shape[3]);
+int rt_batch_get_shape(rt_batch *batch, int shape[3]);
+
+/*
+ * rt_batch_tune -- the batch's autotuner: times rt_batch_evaluate(batch,
+ * rx_soa, e_out, flags, opt, stream) over tile shapes (a coordinate search
+ * from the default: body warps per tile, then planar warps per tile, then
+ * planar chunks per launch; the faster of two runs after a warm-up each),
+ * keeps the fastest in the batch and writes it to shape_out (or NULL).  The
+ * choice is remembered per device, batch size and options: a later batch of
+ * the same size takes it without timing.  Synchronises; the outputs hold the
+ * last evaluation.  Call before rt_batch_capture.
+ */
+int rt_batch_tune(rt_batch *batch, const float *rx_soa, float *e_out, uint32_t *flags,
+                  const rt_options *opt, void *stream, int shape_out[3]);
+
 /* Counters of the batch's last evaluation or replay (synchronises its stream). */
 int rt_batch_get_stats(rt_batch *batch, rt_stats *out);
 
@@ -284,6 +307,20 @@ int rt_batch_get_stats(rt_batch *batch, rt_stats *out);
 int rt_evaluate_with_paths(rt_scene *scene, const float *rx_soa, int n_rx, float *e_out,
                            uint64_t *codes, int32_t *counts, int cap, uint32_t *flags,
                            const rt_options *opt, void *stream);
+
+/*
+ * The tile shape of rt_evaluate and rt_evaluate_with_paths on this scene
+ * (FP32), as for rt_batch_set_shape: warps per tile of the planar kernel
+ * and of the body kernels, planar frequency chunks per launch.
+ * rt_tune times rt_evaluate(scene, rx_soa, n_rx, e_out, flags, opt, stream)
+ * over shapes as rt_batch_tune does, keeps the fastest for the scene and
+ * writes it to shape_out (or NULL); remembered per device, receiver count,
+ * scene size and options.  Synchronises; e_out holds the last evaluation.
+ */
+int rt_set_shape(rt_scene *scene, const int shape[3]);
+int rt_get_shape(rt_scene *scene, int shape[3]);
+int rt_tune(rt_scene *scene, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
+            const rt_options *opt, void *stream, int shape_out[3]);
 
 /*
  * rt_backward -- gradient of a real loss through the fields (the adjoint of

@@ -25,7 +25,8 @@ EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "
            "rt_evaluate_host", "rt_evaluate_host_noalloc", "rt_paths", "rt_get_stats", "rt_fock_table",
            "rt_last_error", "rt_batch_create", "rt_batch_destroy", "rt_batch_set_frame", "rt_batch_evaluate",
            "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats", "rt_backward", "rt_alu_peaks",
-           "rt_evaluate_with_paths")
+           "rt_evaluate_with_paths", "rt_batch_set_shape", "rt_batch_get_shape", "rt_batch_tune",
+           "rt_set_shape", "rt_get_shape", "rt_tune")
 RT_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -85,6 +86,12 @@ def load(build_if_missing=True):
     lib.rt_backward.argtypes = [P, P, I, P, P, I, P, P, P, P, P, P]
     lib.rt_alu_peaks.argtypes = [P, P, P]
     lib.rt_evaluate_with_paths.argtypes = [P, P, I, P, P, P, I, P, P, P]
+    lib.rt_batch_set_shape.argtypes = [P, P]
+    lib.rt_batch_get_shape.argtypes = [P, P]
+    lib.rt_batch_tune.argtypes = [P, P, P, P, P, P, P]
+    lib.rt_set_shape.argtypes = [P, P]
+    lib.rt_get_shape.argtypes = [P, P]
+    lib.rt_tune.argtypes = [P, P, I, P, P, P, P, P]
     _lib = lib
     return lib
 
@@ -214,6 +221,26 @@ class Scene:
                              ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
         return codes, counts, fl
 
+    def set_shape(self, planar_warps, body_warps, planar_chunks):
+        sh = (ctypes.c_int * 3)(planar_warps, body_warps, planar_chunks)
+        _check(_lib.rt_set_shape(self._h, sh))
+
+    def shape(self):
+        sh = (ctypes.c_int * 3)()
+        _check(_lib.rt_get_shape(self._h, sh))
+        return tuple(sh)
+
+    def tune(self, rx_soa, out=None, opts=None, stream=None):
+        """Autotune the tile shape of evaluate on these receivers (rt_tune)."""
+        import torch
+        n = rx_soa.shape[1]
+        if out is None:
+            out = torch.empty((self.n_f, 3, n, 2), dtype=torch.float32, device=rx_soa.device)
+        sh = (ctypes.c_int * 3)()
+        _check(_lib.rt_tune(self._h, _ptr(rx_soa), n, _ptr(out), None,
+                            ctypes.byref(opts) if opts is not None else None, _stream_handle(stream), sh))
+        return tuple(sh)
+
     def evaluate_with_paths(self, rx_soa, cap=256, out=None, opts=None, stream=None):
         """Fields and, from the same kernels, the path lists (codes unordered
         per receiver): (E [n_f, 3, n, 2], codes [n, cap] int64, counts [n]
@@ -320,6 +347,22 @@ class Batch:
     def capture(self, rx_flat, out, flags=None, opts=None, stream=None):
         _check(_lib.rt_batch_capture(self._h, _ptr(rx_flat), _ptr(out), _ptr(flags),
                                      ctypes.byref(opts) if opts is not None else None, _stream_handle(stream)))
+
+    def set_shape(self, planar_warps, body_warps, planar_chunks):
+        sh = (ctypes.c_int * 3)(planar_warps, body_warps, planar_chunks)
+        _check(_lib.rt_batch_set_shape(self._h, sh))
+
+    def shape(self):
+        sh = (ctypes.c_int * 3)()
+        _check(_lib.rt_batch_get_shape(self._h, sh))
+        return tuple(sh)
+
+    def tune(self, rx_flat, out, flags=None, opts=None, stream=None):
+        """Autotune the tile shape on this batch (rt_batch_tune); returns it."""
+        sh = (ctypes.c_int * 3)()
+        _check(_lib.rt_batch_tune(self._h, _ptr(rx_flat), _ptr(out), _ptr(flags),
+                                  ctypes.byref(opts) if opts is not None else None, _stream_handle(stream), sh))
+        return tuple(sh)
 
     def replay(self, stream=None):
         _check(_lib.rt_batch_replay(self._h, _stream_handle(stream)))

@@ -141,6 +141,7 @@ struct rt_scene {
     size_t io_cap = 0;
     cudaStream_t last_stream = nullptr;
     int last_launches = 0;
+    int shape[3] = {4, 4, 4};           // tile shape of rt_evaluate (rt_set_shape / rt_tune)
 };
 
 #define CK(x)                                                                              \
@@ -525,7 +526,8 @@ int rt_evaluate(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint32
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemsetAsync(s->d_esc, 0, sizeof(unsigned long long) * CTR_N, st));
     s->last_stream = st;
-    return launch_eval(D, rx_soa, n_rx, e_out, flags, nullptr, nullptr, 0, prec, s->d_esc, st, &s->last_launches);
+    return launch_eval(D, rx_soa, n_rx, e_out, flags, nullptr, nullptr, 0, prec, s->shape, s->d_esc, st,
+                       &s->last_launches);
 }
 
 int rt_paths(rt_scene *s, const float *rx_soa, int n_rx, uint64_t *codes, int32_t *counts, int cap, uint32_t *flags,
@@ -541,7 +543,8 @@ int rt_paths(rt_scene *s, const float *rx_soa, int n_rx, uint64_t *codes, int32_
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemsetAsync(s->d_esc, 0, sizeof(unsigned long long) * CTR_N, st));
     s->last_stream = st;
-    return launch_eval(D, rx_soa, n_rx, nullptr, flags, codes, counts, cap, prec, s->d_esc, st, &s->last_launches);
+    return launch_eval(D, rx_soa, n_rx, nullptr, flags, codes, counts, cap, prec, nullptr, s->d_esc, st,
+                       &s->last_launches);
 }
 
 int rt_evaluate_with_paths(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint64_t *codes, int32_t *counts,
@@ -558,7 +561,8 @@ int rt_evaluate_with_paths(rt_scene *s, const float *rx_soa, int n_rx, float *e_
     cudaStream_t st = (cudaStream_t)stream;
     CK(cudaMemsetAsync(s->d_esc, 0, sizeof(unsigned long long) * CTR_N, st));
     s->last_stream = st;
-    return launch_eval(D, rx_soa, n_rx, e_out, flags, codes, counts, cap, prec, s->d_esc, st, &s->last_launches);
+    return launch_eval(D, rx_soa, n_rx, e_out, flags, codes, counts, cap, prec, s->shape, s->d_esc, st,
+                       &s->last_launches);
 }
 
 int rt_backward(rt_scene *s, const float *rx_soa, int n_rx, const uint64_t *codes, const int32_t *counts, int cap,
@@ -658,6 +662,9 @@ struct rt_batch {
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t last_stream = nullptr;
     int last_launches = 0;
+    // tile shape: warps per tile of the planar and of the body kernels,
+    // planar frequency chunks per launch (rt_batch_set_shape / rt_batch_tune)
+    int shape[3] = {4, 4, 4};
 };
 
 static void free_batch(rt_batch *b) {
@@ -696,7 +703,7 @@ static int batch_queue(rt_batch *b, const float *rx_soa, float *e_out, uint32_t 
                          b->d_perm, st);
     if (rc != RT_OK) return rc;
     rc = launch_eval_batch(D, b->d_frames, b->fr.data(), b->n_frames, b->n_tiles, b->d_rxs, b->d_perm, e_out, flags,
-                           prec, b->d_ctr, st, &b->last_launches);
+                           prec, b->shape, b->d_ctr, st, &b->last_launches);
     if (rc == RT_OK) b->last_launches += 3;          // the ordering kernels
     return rc;
 }
@@ -850,6 +857,151 @@ int rt_batch_replay(rt_batch *b, void *stream) {
     b->last_stream = st;
     return RT_OK;
 }
+
+static bool shape_ok(const int sh[3]) {
+    const bool p = sh[0] == 1 || sh[0] == 2 || sh[0] == 4;
+    const bool q = sh[1] >= 1 && sh[1] <= 12 && 12 % sh[1] == 0;
+    return p && q && sh[2] >= 1 && sh[2] <= 4;
+}
+
+int rt_batch_set_shape(rt_batch *b, const int shape[3]) {
+    if (!b || !shape) return fail(RT_ERR_ARG, "rt_batch_set_shape: NULL argument");
+    if (!shape_ok(shape))
+        return fail(RT_ERR_ARG, "rt_batch_set_shape: shape (%d, %d, %d) not in {1,2,4} x {1,2,3,4,6,12} x [1,4]",
+                    shape[0], shape[1], shape[2]);
+    memcpy(b->shape, shape, sizeof(b->shape));
+    return RT_OK;
+}
+
+int rt_batch_get_shape(rt_batch *b, int shape[3]) {
+    if (!b || !shape) return fail(RT_ERR_ARG, "rt_batch_get_shape: NULL argument");
+    memcpy(shape, b->shape, sizeof(b->shape));
+    return RT_OK;
+}
+
+}  // extern "C"
+
+// Tile shapes chosen by the autotuner, per device, workload size and
+// options: a later workload of the same size takes them without timing.
+static std::mutex g_tune_mu;
+static std::map<std::vector<long long>, std::vector<int>> g_tuned;
+
+// Coordinate search over tile shapes from the default {4, 4, 4}: body warps
+// per tile, then planar warps per tile, then planar chunks per launch (up to
+// nch), each timed as the faster of two evaluations after a warm-up.
+// run(shape) queues one evaluation on st.  A shape that cannot launch is
+// skipped; the default must run.
+template <typename RUN>
+static int tune_shape(RUN run, cudaStream_t st, int nch, const std::vector<long long> &key, int best[3]) {
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            for (int k = 0; k < 3; ++k) best[k] = it->second[k];
+            return RT_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    auto time_shape = [&](const int sh[3], float *ms) -> int {
+        int rc = run(sh);
+        float tb = 1e30f;
+        for (int rep = 0; rep < 2 && rc == RT_OK; ++rep) {
+            cudaEventRecord(e0, st);
+            rc = run(sh);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) return fail(RT_ERR_CUDA, "autotuner: evaluation failed");
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (t < tb) tb = t;
+        }
+        *ms = tb;
+        return rc;
+    };
+    best[0] = 4; best[1] = 4; best[2] = 4;
+    float t_best = 0.f;
+    int rc = time_shape(best, &t_best);
+    const int cand_body[] = {2, 3, 4, 6, 12}, cand_planar[] = {1, 2, 4}, cand_chunks[] = {1, 2, 3, 4};
+    auto trial = [&](int p, int q, int r) {
+        const int sh[3] = {p, q, r};
+        if (rc != RT_OK || !shape_ok(sh) || (sh[0] == best[0] && sh[1] == best[1] && sh[2] == best[2])) return;
+        float t;
+        if (time_shape(sh, &t) == RT_OK && t < t_best) { t_best = t; memcpy(best, sh, 3 * sizeof(int)); }
+        cudaGetLastError();                  // a shape the device cannot launch is skipped
+    };
+    for (int q : cand_body) trial(best[0], q, best[2]);
+    for (int p : cand_planar) trial(p, best[1], best[2]);
+    for (int r : cand_chunks)
+        if (r <= nch) trial(best[0], best[1], r);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != RT_OK) return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[key] = std::vector<int>(best, best + 3);
+    return RT_OK;
+}
+
+extern "C" int rt_batch_tune(rt_batch *b, const float *rx_soa, float *e_out, uint32_t *flags, const rt_options *opt,
+                             void *stream, int shape_out[3]) {
+    if (!b) return fail(RT_ERR_ARG, "rt_batch_tune: NULL batch");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::vector<long long> key = {0, dev, b->n_frames, b->n_f, b->max_body, b->total_rx, b->max_rx,
+                                  opt ? opt->max_order : 2, opt ? (long long)opt->enable : RT_EN_ALL,
+                                  opt ? opt->precision : RT_PREC_FP32};
+    int best[3];
+    int rc = tune_shape([&](const int *sh) {
+        memcpy(b->shape, sh, sizeof(b->shape));
+        return batch_queue(b, rx_soa, e_out, flags, opt, st);
+    }, st, (b->n_f + NFC - 1) / NFC, key, best);
+    static const int kDefault[3] = {4, 4, 4};
+    memcpy(b->shape, rc == RT_OK ? best : kDefault, sizeof(b->shape));
+    if (rc == RT_OK && shape_out) memcpy(shape_out, best, sizeof(best));
+    return rc;
+}
+
+extern "C" int rt_tune(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
+                       const rt_options *opt, void *stream, int shape_out[3]) {
+    if (!s) return fail(RT_ERR_ARG, "rt_tune: NULL scene");
+    if (n_rx <= 0) {
+        if (shape_out) memcpy(shape_out, s->shape, sizeof(s->shape));
+        return RT_OK;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    std::vector<long long> key = {1, dev, n_rx, (long long)s->freqs.size(), s->n_body, s->n_tri,
+                                  opt ? opt->max_order : 2, opt ? (long long)opt->enable : RT_EN_ALL,
+                                  opt ? opt->precision : RT_PREC_FP32};
+    int best[3];
+    int rc = tune_shape([&](const int *sh) {
+        memcpy(s->shape, sh, sizeof(s->shape));
+        return rt_evaluate(s, rx_soa, n_rx, e_out, flags, opt, stream);
+    }, st, ((int)s->freqs.size() + NFC - 1) / NFC, key, best);
+    static const int kDefault[3] = {4, 4, 4};
+    memcpy(s->shape, rc == RT_OK ? best : kDefault, sizeof(s->shape));
+    if (rc == RT_OK && shape_out) memcpy(shape_out, best, sizeof(best));
+    return rc;
+}
+
+extern "C" int rt_set_shape(rt_scene *s, const int shape[3]) {
+    if (!s || !shape) return fail(RT_ERR_ARG, "rt_set_shape: NULL argument");
+    if (!shape_ok(shape))
+        return fail(RT_ERR_ARG, "rt_set_shape: shape (%d, %d, %d) not in {1,2,4} x {1,2,3,4,6,12} x [1,4]",
+                    shape[0], shape[1], shape[2]);
+    memcpy(s->shape, shape, sizeof(s->shape));
+    return RT_OK;
+}
+
+extern "C" int rt_get_shape(rt_scene *s, int shape[3]) {
+    if (!s || !shape) return fail(RT_ERR_ARG, "rt_get_shape: NULL argument");
+    memcpy(shape, s->shape, sizeof(s->shape));
+    return RT_OK;
+}
+
+extern "C" {
 
 int rt_batch_get_stats(rt_batch *b, rt_stats *out) {
     if (!b || !out) return fail(RT_ERR_ARG, "rt_batch_get_stats: NULL argument");

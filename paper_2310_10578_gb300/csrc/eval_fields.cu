@@ -1950,7 +1950,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
        const float *__restrict__ rx_base, const int32_t *__restrict__ perm, float *__restrict__ e_base,
        uint32_t *__restrict__ fl_base,
        uint64_t *__restrict__ codes, int32_t *__restrict__ counts, int cap, int ch0, int nch, int rcap,
-       int accumulate, unsigned long long *esc_counter, unsigned long long *queue) {
+       int nwt, int accumulate, unsigned long long *esc_counter, unsigned long long *queue) {
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     extern __shared__ float4 smem[];
     __shared__ Ctx s_ctx;
@@ -2078,13 +2078,14 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         // record buffer; per chunk all warps finish the geometry pass before
         // any starts the field pass, which runs once per frequency chunk on
         // the same records and adds its rows to the outputs.
-        //   A work unit is TPB tiles of one frame; a batch's frames start at
-        // tile indices that are multiples of TILE_ALIGN (every class's TPB
-        // divides it), so unit u covers tiles u TPB .. u TPB + TPB - 1.  A
+        //   The tile shape: NWT = nwt warps share a tile (the launcher checks
+        // that it divides the block's warps), TPB tiles per block.  A work
+        // unit is TPB tiles of one frame; a batch's frames start at tile
+        // indices that are multiples of TILE_ALIGN (the launcher checks that
+        // TPB divides it), so unit u covers tiles u TPB .. u TPB + TPB - 1.  A
         // block's units come in increasing order, so its frame only moves on.
-        constexpr int NWT = BODIES ? WARPS_PER_TILE : NW;
-        constexpr int TPB = NW / NWT;
-        static_assert(TILE_ALIGN % TPB == 0, "frame alignment");
+        const int NWT = nwt;
+        const int TPB = NW / NWT;
         constexpr bool RECS = BODIES && sizeof(T) == 4;
         constexpr int PER = ((CLS & CLS_CREEP) ? 2 : 0) + ((CLS & CLS_BODYREFL) ? 1 : 0);
         const unsigned long long n_units = (n_tiles + TPB - 1) / TPB;
@@ -2276,6 +2277,7 @@ struct Work {
     uint64_t *codes;
     int32_t *counts;
     int cap;
+    int nwt_planar, nwt_body, planar_chunks;   // tile shape and planar chunks per launch (FP32 fields)
 };
 
 template <typename T, bool PATHS, int CLS, bool LIST = false>
@@ -2283,6 +2285,12 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     if (L.n >= CTR_QUEUES) return cudaErrorInvalidValue;
     constexpr bool bodies = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     constexpr int blk = blk_of(CLS, sizeof(T) == 4);
+    constexpr int NW = blk / 32;
+    // warps per tile (fields): the configured shape where it divides the
+    // block (FP32), else the default (body kernels 4, planar the whole block)
+    int nwt = bodies ? (sizeof(T) == 4 ? W.nwt_body : WARPS_PER_TILE) : (sizeof(T) == 4 ? W.nwt_planar : NW);
+    if (nwt < 1 || NW % nwt != 0) nwt = bodies ? WARPS_PER_TILE : NW;
+    if (W.frames && TILE_ALIGN % (NW / nwt) != 0) return cudaErrorInvalidValue;
     // records per lane: one frequency chunk flushes full buffers on the way
     // (5 is enough); several chunks size the body range by the capacity
     const int rcap = (nch > 1) ? 6 : 5;
@@ -2290,7 +2298,7 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     if (nch < 1 || nch > MAX_CHUNKS || (!wide && !bodies && nch != 1)) return cudaErrorInvalidValue;
     // occluder masks (FP32 body kernels): one source-side set, and one
     // receiver-side set per tile in flight (fields) or per warp (path lists)
-    const int occ_sets = (bodies && sizeof(T) == 4) ? (PATHS ? blk / 32 : blk / 32 / WARPS_PER_TILE) : 0;
+    const int occ_sets = (bodies && sizeof(T) == 4) ? (PATHS ? NW : NW / nwt) : 0;
     size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk, rcap, wide ? nch : 0, occ_sets);
     cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -2302,7 +2310,7 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<T, PATHS, CLS, LIST>, blk, sm)) != cudaSuccess) return e;
     // (path lists: each warp takes whole tiles; up to one block per tile, so
     // that a few tiles spread over as many SMs)
-    constexpr int tiles_per_unit = PATHS ? 1 : (bodies ? blk / 32 / WARPS_PER_TILE : 1);
+    const int tiles_per_unit = PATHS ? 1 : NW / nwt;
     long long need = (long long)((W.n_tiles + tiles_per_unit - 1) / tiles_per_unit);
     long long cap_blocks = (long long)nsm * (occ > 0 ? occ : 1);
     int grid = (int)(need < cap_blocks ? need : cap_blocks);
@@ -2320,7 +2328,7 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     cfg.attrs = attr;
     cfg.numAttrs = L.n > 0 ? 1 : 0;
     e = cudaLaunchKernelEx(&cfg, k_eval<T, PATHS, CLS, LIST>, S, W.F1, W.frames, W.n_frames, W.n_tiles, W.rx, W.perm, W.e, W.fl,
-                           W.codes, W.counts, W.cap, ch0, nch, rcap, accumulate, L.ctr, L.ctr + 1 + L.n);
+                           W.codes, W.counts, W.cap, ch0, nch, rcap, nwt, accumulate, L.ctr, L.ctr + 1 + L.n);
     ++L.n;
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -2336,7 +2344,8 @@ static cudaError_t launch_all(const DevScene &S, const Work &W, int nchunks, Lau
     const bool chunked_bodies = PATHS || sizeof(T) != 4;
     // FP32 fields: each planar launch takes up to PLANAR_CHUNKS chunks in one
     // geometry pass
-    const int pstep = chunked_bodies ? 1 : PLANAR_CHUNKS;
+    const int pstep = chunked_bodies ? 1 : (W.planar_chunks >= 1 && W.planar_chunks <= MAX_CHUNKS ? W.planar_chunks
+                                                                                                  : PLANAR_CHUNKS);
     for (int ch = 0; ch < nchunks && e == cudaSuccess; ch += pstep) {
         const int n = nchunks - ch < pstep ? nchunks - ch : pstep;
         e = launch_one<T, PATHS, CLS_PLANAR, LIST>(S, W, ch, n, 0, L);
@@ -2372,7 +2381,7 @@ static int run(const DevScene &S, const Work &W, int precision, bool paths, bool
 }
 
 int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
-                uint64_t *codes, int32_t *counts, int cap, int precision, unsigned long long *ctr,
+                uint64_t *codes, int32_t *counts, int cap, int precision, const int *shape, unsigned long long *ctr,
                 cudaStream_t stream, int *n_launches) {
     *n_launches = 0;
     // fields and a path list (unordered): counts zeroed first
@@ -2394,6 +2403,9 @@ int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, 
     W.n_tiles = ((unsigned long long)n_rx + 31ull) >> 5;
     W.rx = rx_soa; W.e = e_out; W.fl = flags;
     W.codes = codes; W.counts = counts; W.cap = cap;
+    W.nwt_planar = shape ? shape[0] : 4;
+    W.nwt_body = shape ? shape[1] : WARPS_PER_TILE;
+    W.planar_chunks = shape ? shape[2] : PLANAR_CHUNKS;
     if (codes && e_out) {
         cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int32_t) * (size_t)n_rx, stream);
         if (e != cudaSuccess) {
@@ -2406,7 +2418,8 @@ int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, 
 
 int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const FrameDev *frames_host, int n_frames,
                       unsigned long long n_tiles, const float *rx_soa, const int32_t *perm, float *e_out,
-                      uint32_t *flags, int precision, unsigned long long *ctr, cudaStream_t stream, int *n_launches) {
+                      uint32_t *flags, int precision, const int shape[3], unsigned long long *ctr,
+                      cudaStream_t stream, int *n_launches) {
     *n_launches = 0;
     if (n_frames <= 0 || n_tiles == 0) return RT_OK;
     Work W = {};
@@ -2415,6 +2428,7 @@ int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const Frame
     W.n_frames = n_frames;
     W.n_tiles = n_tiles;
     W.rx = rx_soa; W.perm = perm; W.e = e_out; W.fl = flags;
+    W.nwt_planar = shape[0]; W.nwt_body = shape[1]; W.planar_chunks = shape[2];
     return run(S, W, precision, false, false, ctr, stream, n_launches);
 }
 

@@ -87,7 +87,7 @@ struct DevScene {
 // evaluation is one frame passed by value; a batch is a device array of them.
 // Each frame's first tile index (32 receivers a tile) is a multiple of
 // TILE_ALIGN, so that a work unit of any class kernel lies in one frame.
-constexpr int TILE_ALIGN = 3;
+constexpr int TILE_ALIGN = 12;
 struct FrameDev {
     const float4 *body;        // [n_body][2], as DevScene::body
     const float4 *txb;         // [n_body][2], as DevScene::txb
@@ -108,8 +108,9 @@ constexpr int CTR_N = 1 + CTR_QUEUES;
 // Evaluate (codes == nullptr), list paths (e_out == nullptr: canonical
 // order), or both (the path list in no particular order); *n_launches
 // receives the number of kernel launches queued.
+// shape: the tile shape (see launch_eval_batch), or nullptr for the default.
 int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
-                uint64_t *codes, int32_t *counts, int cap, int precision, unsigned long long *ctr,
+                uint64_t *codes, int32_t *counts, int cap, int precision, const int *shape, unsigned long long *ctr,
                 cudaStream_t stream, int *n_launches);
 
 // Evaluate the n_frames frames of frames_dev (device copy of frames_host):
@@ -117,9 +118,12 @@ int launch_eval(const DevScene &S, const float *rx_soa, int n_rx, float *e_out, 
 // the end of the last frame's tile range.  perm (or nullptr): the receivers
 // in rx_soa are in a reordered sequence; sorted position rx_off + p of a
 // frame holds its receiver perm[rx_off + p], where that receiver's outputs go.
+// shape = {warps per tile of the planar kernel (1, 2, 4), of the body
+// kernels (1, 2, 3, 4, 6, 12), planar frequency chunks per launch (1-4)}.
 int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const FrameDev *frames_host, int n_frames,
                       unsigned long long n_tiles, const float *rx_soa, const int32_t *perm, float *e_out,
-                      uint32_t *flags, int precision, unsigned long long *ctr, cudaStream_t stream, int *n_launches);
+                      uint32_t *flags, int precision, const int shape[3], unsigned long long *ctr,
+                      cudaStream_t stream, int *n_launches);
 
 // Gradient of a loss through the fields (adjoint pass, eval_fields.cu): for
 // the n_rx receivers' listed paths (codes/counts/cap as rt_paths wrote

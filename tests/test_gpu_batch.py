@@ -193,3 +193,60 @@ def test_batch_errors(creep):
         E.set_frame(i, cw.bodies[i], cw.freqs[i])
     out = E.evaluate(torch.zeros(0, dtype=torch.float32, device="cuda"))
     assert out.numel() == 0
+
+
+def test_batch_tile_shapes(creep, oracle_mod):
+    """Every tile shape gives the oracle's fields within the bound, the same
+    flags, and the default shape's fields up to the rounding of the sums
+    over a tile's warps."""
+    cw = _small_crowd()
+    S, B, rx = _batch(creep, cw)
+    opts = creep.options(max_order=2)
+    fl0 = torch.zeros(max(B.total_rx, 1), dtype=torch.int32, device="cuda")
+    ref = B.evaluate(rx, flags=fl0, opts=opts).clone()
+    assert B.shape() == (4, 4, 4)
+    for shape in [(1, 1, 1), (2, 2, 2), (1, 3, 1), (4, 6, 2), (2, 12, 1), (4, 12, 4)]:
+        B.set_shape(*shape)
+        fl = torch.zeros_like(fl0)
+        out = B.evaluate(rx, flags=fl, opts=opts)
+        torch.cuda.synchronize()
+        assert torch.equal(fl, fl0), shape
+        scale = torch.max(torch.abs(ref)).item()
+        assert torch.max(torch.abs(out - ref)).item() <= 1e-5 * scale, shape
+        if shape == (1, 3, 1):
+            for i in (0, 3, 4):
+                oref = oracle_mod.evaluate(cw.frame(i))
+                compare_fields(gpu_fields(B.frame_fields(out, i)), oref, flags=oref.flags, freqs=cw.freqs[i])
+    with pytest.raises(creep.CreepError) as e:
+        B.set_shape(3, 4, 4)
+    assert e.value.code == creep.RT_ERR_ARG
+    with pytest.raises(creep.CreepError) as e:
+        B.set_shape(4, 5, 4)
+    assert e.value.code == creep.RT_ERR_ARG
+
+
+def test_batch_tune(creep):
+    """The autotuner keeps a valid shape whose evaluation is that of the
+    shape set by hand, and a batch of the same size takes it from its cache."""
+    cw = scenes.crowd(n_frames=6, n_cyl=30, n_freq=8, rx_range=(2000, 8000), seed=41)
+    S, B, rx = _batch(creep, cw)
+    opts = creep.options(max_order=2)
+    out = torch.empty(6 * 8 * B.total_rx, device="cuda")
+    shape = B.tune(rx, out, opts=opts)
+    assert shape[0] in (1, 2, 4) and 12 % shape[1] == 0 and 1 <= shape[2] <= 2
+    assert B.shape() == shape
+    a = B.evaluate(rx, opts=opts).clone()
+    B2 = creep.Batch(S, cw.n_rx, 8, max(len(b) for b in cw.bodies))
+    for i in range(cw.n_frames):
+        B2.set_frame(i, cw.bodies[i], cw.freqs[i])
+    B2.set_shape(*shape)
+    b = B2.evaluate(rx, opts=opts)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    import time
+    B3 = creep.Batch(S, cw.n_rx, 8, max(len(b) for b in cw.bodies))
+    for i in range(cw.n_frames):
+        B3.set_frame(i, cw.bodies[i], cw.freqs[i])
+    t0 = time.perf_counter()
+    assert B3.tune(rx, out, opts=opts) == shape
+    assert time.perf_counter() - t0 < 0.05          # cached: no timing runs

@@ -244,3 +244,26 @@ def test_evaluate_with_paths(creep, precision):
     assert over.any() and np.array_equal((fl2 & creep.RT_FLAG_OVERFLOW) != 0, over)
     for r in np.nonzero(over)[0][:200]:
         assert set(c2[r].tolist()) <= set(c0[r, :n[r]].tolist())
+
+
+def test_scene_tile_shapes_and_tune(creep, oracle_mod):
+    """Every tile shape of rt_evaluate gives the oracle's fields within the
+    bound; the autotuner keeps a valid shape and evaluates with it."""
+    sc = scenes.room(n_cyl=20, nx=61, ny=47, seed=3)
+    S = creep.Scene.from_scene(sc)
+    rx = torch.tensor(sc.rx_soa(), device="cuda")
+    opts = creep.options(max_order=2)
+    ref = oracle_mod.evaluate(sc)
+    base = S.evaluate(rx, opts=opts).clone()
+    for shape in [(1, 3, 1), (2, 6, 4), (4, 12, 2), (1, 1, 1)]:
+        S.set_shape(*shape)
+        E = S.evaluate(rx, opts=opts)
+        torch.cuda.synchronize()
+        assert torch.max(torch.abs(E - base)).item() <= 1e-5 * torch.max(torch.abs(base)).item(), shape
+        compare_fields(gpu_fields(E), ref, flags=ref.flags, freqs=sc.freqs)
+    shape = S.tune(rx, opts=opts)
+    assert S.shape() == shape and shape[0] in (1, 2, 4) and 12 % shape[1] == 0
+    compare_fields(gpu_fields(S.evaluate(rx, opts=opts)), ref, flags=ref.flags, freqs=sc.freqs)
+    with pytest.raises(creep.CreepError) as e:
+        S.set_shape(4, 4, 5)
+    assert e.value.code == creep.RT_ERR_ARG
