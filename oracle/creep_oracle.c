@@ -159,7 +159,10 @@ static void fock_bracket(const fock_rule *R, double xi, double K, cplx *Bs, cplx
 
 /* ------------------------------------------------------------ scene */
 typedef struct { int type; v3 c; double a, h; } body;   /* type 0 sphere, 1 cylinder (axis +z, base c.z) */
-typedef struct { v3 n; double d; int first, count; } face; /* plane n.x = d; triangles [first, first+count) in order list */
+typedef struct {
+    v3 n; double d; int first, count;   /* plane n.x = d; triangles [first, first+count) in order list */
+    int dielectric; cplx eps;           /* PEC, or a dielectric half-space of relative permittivity eps */
+} face;
 
 typedef struct {
     int n_tri; const double *tri; const int *tri_face; int *order; /* triangle ids grouped by face */
@@ -296,6 +299,32 @@ static c3 pec_mirror(c3 E, v3 n) {
     return CV(-E.x + 2.0 * en * n.x, -E.y + 2.0 * en * n.y, -E.z + 2.0 * en * n.z);
 }
 
+/* Reflection of a field vector E at face F, the ray arriving along si and
+ * leaving along sr.  PEC: the image mirror above.  Dielectric half-space of
+ * relative permittivity eps (e^{+jwt}: eps = eps' - j eps''): the Fresnel
+ * coefficients at the incidence angle (cos = |si.n|)
+ *   G_perp = (cos - r) / (cos + r),  G_par = (eps cos - r) / (eps cos + r),
+ *   r = sqrt(eps - sin^2) (principal branch),
+ * applied in the basis e_perp = unit(n x si), e_par = e_perp x si before and
+ * e_perp x sr after the bounce (the basis in which the PEC mirror is
+ * G_perp = -1, G_par = +1, the limit eps -> infinity).  At normal incidence
+ * G_par = -G_perp and the reflection is G_perp E for any e_perp. */
+static c3 reflect_at(const face *F, c3 E, v3 si, v3 sr) {
+    if (!F->dielectric) return pec_mirror(E, F->n);
+    double cth = fabs(dot(si, F->n));
+    double s2 = 1.0 - cth * cth;
+    cplx r = csqrt(F->eps - s2);
+    cplx gs = (cth - r) / (cth + r);
+    cplx gp = (F->eps * cth - r) / (F->eps * cth + r);
+    v3 ep = cross(F->n, si);
+    double ne = norm(ep);
+    if (ne == 0.0) return c3_scl(E, gs);
+    ep = scl(ep, 1.0 / ne);
+    v3 epi = cross(ep, si), epr = cross(ep, sr);
+    cplx a = c3_dotr(E, ep), b = c3_dotr(E, epi);
+    return c3_add(rscl(ep, gs * a), rscl(epr, gp * b));
+}
+
 static v3 mirror_point(v3 X, const face *F) {
     double dist = dot(F->n, X) - F->d;
     return sub(X, scl(F->n, 2.0 * dist));
@@ -342,7 +371,7 @@ static inline void accum(rx_state *st, int f, c3 v) {
     }
 }
 
-/* LOS and planar image paths (order 1 and 2); PEC faces. */
+/* LOS and planar image paths (order 1 and 2); PEC or dielectric faces. */
 static void planar_paths(const scene *s, v3 P, rx_state *st) {
     v3 S = s->tx;
     if (s->enable & EN_LOS) {
@@ -372,7 +401,7 @@ static void planar_paths(const scene *s, v3 P, rx_state *st) {
             if (!visible(s, Q, P, i, -1, -1, &st->ct)) continue;
             add_path(st, pcode(PT_R1, i, 0));
             double L = norm(sub(Q, S)) + norm(sub(P, Q));
-            c3 e = pec_mirror(c3_from(source_pol(s, unit(sub(Q, S)))), Fi->n);
+            c3 e = reflect_at(Fi, c3_from(source_pol(s, unit(sub(Q, S)))), unit(sub(Q, S)), unit(sub(P, Q)));
             for (int f = 0; f < s->n_f; ++f) {
                 double k = kwave(s->freq[f]);
                 accum(st, f, c3_scl(e, cexp(-I * k * L) / L));
@@ -403,7 +432,8 @@ static void planar_paths(const scene *s, v3 P, rx_state *st) {
                 if (!visible(s, Q2, P, j, -1, -1, &st->ct)) continue;
                 add_path(st, pcode(PT_R2, i, j));
                 double L = norm(sub(Q1, S)) + norm(sub(Q2, Q1)) + norm(sub(P, Q2));
-                c3 e = pec_mirror(pec_mirror(c3_from(source_pol(s, unit(sub(Q1, S)))), Fi->n), Fj->n);
+                c3 e = reflect_at(Fi, c3_from(source_pol(s, unit(sub(Q1, S)))), unit(sub(Q1, S)), unit(sub(Q2, Q1)));
+                e = reflect_at(Fj, e, unit(sub(Q2, Q1)), unit(sub(P, Q2)));
                 for (int f = 0; f < s->n_f; ++f) {
                     double k = kwave(s->freq[f]);
                     accum(st, f, c3_scl(e, cexp(-I * k * L) / L));
@@ -751,13 +781,18 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
                 int max_order, int enable,
                 double *E_out, uint64_t *path_codes, int *path_count, int cap,
                 unsigned *flags_out, long long *counters_out, int n_threads, double *sabs_out,
-                double *path_E_out) {
+                double *path_E_out, const double *face_eps) {
     fock_rule R = {tau_re, tau_im, ws_re, ws_im, wh_re, wh_im, offsets, n_buckets,
                    res_alpha, res_cs, res_beta, res_ch, n_res, xi_lo, xi_hi};
     scene s;
     memset(&s, 0, sizeof(s));
     s.n_tri = n_tri; s.tri = tri; s.tri_face = tri_face;
     build_faces(&s);
+    /* face materials: [n_face][3] = (dielectric flag, eps', eps'') or NULL (all PEC) */
+    for (int f = 0; f < s.n_face; ++f) {
+        s.faces[f].dielectric = face_eps ? face_eps[3 * f] != 0.0 : 0;
+        s.faces[f].eps = face_eps ? face_eps[3 * f + 1] - I * face_eps[3 * f + 2] : 0.0;
+    }
     s.n_body = n_body;
     s.bodies = (body *)malloc(sizeof(body) * (n_body > 0 ? n_body : 1));
     for (int b = 0; b < n_body; ++b) {
@@ -882,6 +917,21 @@ int oracle_body_creeping(const double *body6, const double *S, const double *P, 
     return 1;
 }
 /* Segment visibility probe against one body (1 = obstructed). */
+/* One reflection (reflect_at) of the complex field E[3] (re, im pairs) at a
+ * face of unit normal n: dielectric != 0 with eps = eps_re - j eps_im. */
+void oracle_reflect(const double *n, const double *si, const double *sr, const double *E, int dielectric,
+                    double eps_re, double eps_im, double *out) {
+    face F;
+    memset(&F, 0, sizeof(F));
+    F.n = V(n[0], n[1], n[2]);
+    F.dielectric = dielectric;
+    F.eps = eps_re - I * eps_im;
+    c3 e = CV(E[0] + I * E[1], E[2] + I * E[3], E[4] + I * E[5]);
+    c3 r = reflect_at(&F, e, V(si[0], si[1], si[2]), V(sr[0], sr[1], sr[2]));
+    out[0] = creal(r.x); out[1] = cimag(r.x); out[2] = creal(r.y); out[3] = cimag(r.y);
+    out[4] = creal(r.z); out[5] = cimag(r.z);
+}
+
 int oracle_seg_hits_body(const double *body6, const double *A, const double *Bp) {
     body B = body_from(body6);
     return seg_hits_body(V(A[0], A[1], A[2]), V(Bp[0], Bp[1], Bp[2]), &B);

@@ -54,13 +54,15 @@ def _load():
         d = ctypes.c_double
         _lib.oracle_eval.argtypes = [P, P, i, P, i, P, P, P, i, P, i,
                                      P, P, P, P, P, P, P, i, P, P, P, P, i, d, d,
-                                     i, i, P, P, P, i, P, P, i, P, P]
+                                     i, i, P, P, P, i, P, P, i, P, P, P]
         _lib.oracle_eval.restype = i
         _lib.oracle_transition_F.argtypes = [P, i, P]
         _lib.oracle_fock_bracket.argtypes = [P, P, P, P, P, P, P, i, P, P, P, P, i, d, d, P, P, i, P]
         _lib.oracle_body_reflection.argtypes = [P, P, P, P]
         _lib.oracle_body_creeping.argtypes = [P, P, P, i, P]
         _lib.oracle_seg_hits_body.argtypes = [P, P, P]
+        _lib.oracle_reflect.argtypes = [P, P, P, P, i, d, d, P]
+        _lib.oracle_reflect.restype = None
     return _lib
 
 
@@ -120,12 +122,16 @@ def evaluate(scene, rx=None, enable=EN_ALL, cap=256, threads=0, want_paths=True,
     ctr = np.zeros(8, dtype=np.int64)
     sabs = np.zeros((n_f, n_rx), dtype=np.float64)
     pE = np.zeros((n_rx, cap, n_f, 3, 2), dtype=np.float64) if (path_fields and want_paths) else None
+    # face materials: [n_face][3] (dielectric flag, eps', eps''), eps_r = eps' - j eps''; None: PEC
+    fe = getattr(scene, "face_eps", None)
+    fe = None if fe is None else np.ascontiguousarray(np.asarray(fe, dtype=np.float64).reshape(-1, 3))
     t0 = time.perf_counter()
     lib.oracle_eval(_p(tri), _p(tf), scene.tri.shape[0], _p(bodies), scene.bodies.shape[0],
                     _p(tx), _p(pol), _p(fr), n_f, _p(rx64), n_rx, *_fock_args(),
                     scene.max_order, enable, _p(E),
                     _p(codes) if want_paths else None, _p(counts), cap if want_paths else 0,
-                    _p(flags), _p(ctr), threads, _p(sabs), _p(pE) if pE is not None else None)
+                    _p(flags), _p(ctr), threads, _p(sabs), _p(pE) if pE is not None else None,
+                    _p(fe) if fe is not None else None)
     res = Result()
     res.seconds = time.perf_counter() - t0
     res.E = E[..., 0] + 1j * E[..., 1]
@@ -193,3 +199,15 @@ def seg_hits_body(body6, A, B):
     lib = _load()
     b, a_, bb = _d3(body6), _d3(A), _d3(B)
     return bool(lib.oracle_seg_hits_body(_p(b), _p(a_), _p(bb)))
+
+
+def reflect(n, si, sr, E, eps=None):
+    """One reflection of the complex field vector E at a face of unit normal
+    n (ray along si in, sr out): PEC (eps None) or a dielectric half-space
+    eps = (eps', eps''), eps_r = eps' - j eps''."""
+    lib = _load()
+    e = np.ascontiguousarray(np.stack([np.real(E), np.imag(E)], axis=1).reshape(-1).astype(np.float64))
+    out = np.zeros(6)
+    lib.oracle_reflect(_p(_d3(n)), _p(_d3(si)), _p(_d3(sr)), _p(e), 0 if eps is None else 1,
+                       0.0 if eps is None else float(eps[0]), 0.0 if eps is None else float(eps[1]), _p(out))
+    return out[0::2] + 1j * out[1::2]

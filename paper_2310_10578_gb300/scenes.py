@@ -33,7 +33,7 @@ BODY_CYLINDER = 1
 class Scene:
     """Plain container: float32 arrays, no behaviour."""
 
-    def __init__(self, tri, tri_face, bodies, tx, pol, freqs, rx, name, max_order=2):
+    def __init__(self, tri, tri_face, bodies, tx, pol, freqs, rx, name, max_order=2, face_eps=None):
         self.tri = np.ascontiguousarray(tri, dtype=np.float32).reshape(-1, 3, 3)
         self.tri_face = np.ascontiguousarray(tri_face, dtype=np.int32)
         self.bodies = np.ascontiguousarray(bodies, dtype=np.float32).reshape(-1, 6)
@@ -43,6 +43,8 @@ class Scene:
         self.rx = np.ascontiguousarray(rx, dtype=np.float32).reshape(-1, 3)
         self.name = name
         self.max_order = int(max_order)
+        # per face (dielectric flag, eps', eps''), eps_r = eps' - j eps''; None: every face PEC
+        self.face_eps = None if face_eps is None else np.asarray(face_eps, dtype=np.float32).reshape(-1, 3)
 
     @property
     def n_rx(self):
@@ -54,7 +56,7 @@ class Scene:
 
     def subset(self, idx, name=None):
         return Scene(self.tri, self.tri_face, self.bodies, self.tx, self.pol, self.freqs,
-                     self.rx[idx], name or self.name + "[sub]", self.max_order)
+                     self.rx[idx], name or self.name + "[sub]", self.max_order, self.face_eps)
 
 
 def box_triangles(lx, ly, lz):
@@ -119,15 +121,21 @@ def grid_receivers(nx, ny, lx, ly, z):
 
 
 def room(n_cyl=20, nx=256, ny=256, freqs=(2.4e9, 5.8e9, 28e9), seed=SEED_BASE + 1,
-         size=(10.0, 8.0, 3.0), tx=(1.0, 1.0, 2.0), pol=(0.0, 0.0, 1.0), rx_z=1.2, max_order=2):
+         size=(10.0, 8.0, 3.0), tx=(1.0, 1.0, 2.0), pol=(0.0, 0.0, 1.0), rx_z=1.2, max_order=2, face_eps=None):
+    """face_eps: None (PEC faces) or, per face id (floor, ceiling, x=0, x=lx,
+    y=0, y=ly), None for PEC or (eps', eps'') of a dielectric half-space."""
     lx, ly, lz = size
     rng = np.random.default_rng(seed)
     tri, face = box_triangles(lx, ly, lz)
     bodies = place_cylinders(n_cyl, lx, ly, rng, avoid=[(tx[0], tx[1], 0.3)])
     rx = grid_receivers(nx, ny, lx, ly, rx_z)
-    name = "room(%gx%gx%g m, %d PEC cylinders, %dx%d rx, f=%s GHz, refl<=%d)" % (
-        lx, ly, lz, n_cyl, nx, ny, ",".join("%g" % (f / 1e9) for f in freqs), max_order)
-    return Scene(tri, face, bodies, tx, pol, freqs, rx, name, max_order=max_order)
+    name = "room(%gx%gx%g m, %d PEC cylinders, %dx%d rx, f=%s GHz, refl<=%d%s)" % (
+        lx, ly, lz, n_cyl, nx, ny, ",".join("%g" % (f / 1e9) for f in freqs), max_order,
+        "" if face_eps is None else ", dielectric faces")
+    fe = None
+    if face_eps is not None:
+        fe = [(0.0, 0.0, 0.0) if e is None else (1.0, float(e[0]), float(e[1])) for e in face_eps]
+    return Scene(tri, face, bodies, tx, pol, freqs, rx, name, max_order=max_order, face_eps=fe)
 
 
 class Crowd:
