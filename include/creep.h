@@ -132,6 +132,16 @@ void rt_scene_destroy(rt_scene *scene);
  */
 int rt_set_tx(rt_scene *scene, const float tx[3], const float pol[3]);
 
+/*
+ * Face materials for the planar reflections (Eq. 3): mat host float
+ * [n_face][3] = (kind, eps', eps''), kind 0 PEC (R = -1 / +1) or 1 a
+ * dielectric half-space of relative permittivity eps' - j eps'' (eps' > 0,
+ * eps'' >= 0; e^{+jwt}), reflecting with the Fresnel coefficients at the
+ * incidence angle; NULL makes every face PEC (the default).  n_face must be
+ * the scene's face count.  Curved bodies stay PEC.
+ */
+int rt_set_face_materials(rt_scene *scene, const float *mat, int n_face);
+
 /* Frequencies (host double[n_f], Hz, > 0), 1 <= n_f <= RT_MAX_FREQS. */
 int rt_set_freqs(rt_scene *scene, const double *f_hz, int n_f);
 

@@ -22,7 +22,7 @@ class Static:
     every body's type and height, the polarisation, the receivers (CUDA
     float32 tensor [3, n]), the options and the path-list capacity."""
 
-    def __init__(self, tri, tri_face, body_type, body_h, pol, rx_soa, opts=None, cap=256):
+    def __init__(self, tri, tri_face, body_type, body_h, pol, rx_soa, opts=None, cap=256, face_mat=None):
         self.tri = np.asarray(tri, dtype=np.float32)
         self.tri_face = None if tri_face is None else np.asarray(tri_face, dtype=np.int32)
         self.body_type = np.asarray(body_type, dtype=np.float64).reshape(-1)
@@ -31,11 +31,13 @@ class Static:
         self.rx = rx_soa
         self.opts = opts if opts is not None else creep.options(max_order=2)
         self.cap = int(cap)
+        self.face_mat = face_mat              # per face (kind, eps', eps'') or None (PEC)
 
     @classmethod
     def from_scene(cls, sc, rx_soa, opts=None, cap=256):
         return cls(sc.tri, sc.tri_face, sc.bodies[:, 0], sc.bodies[:, 5], sc.pol, rx_soa,
-                   opts if opts is not None else creep.options(max_order=sc.max_order), cap)
+                   opts if opts is not None else creep.options(max_order=sc.max_order), cap,
+                   getattr(sc, "face_eps", None))
 
     def scene(self, body_params, tx, freqs):
         """An rt_scene for parameters body_params [n, 4] (cx, cy, cz, a), tx [3], freqs [n_f]."""
@@ -44,6 +46,8 @@ class Static:
         S = creep.Scene(self.tri, self.tri_face, bodies)
         S.set_tx(tx.detach().cpu().numpy(), self.pol)
         S.set_freqs(freqs.detach().cpu().numpy().astype(np.float64))
+        if self.face_mat is not None:
+            S.set_face_materials(self.face_mat)
         return S
 
 

@@ -26,7 +26,7 @@ EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "
            "rt_last_error", "rt_batch_create", "rt_batch_destroy", "rt_batch_set_frame", "rt_batch_evaluate",
            "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats", "rt_backward", "rt_alu_peaks",
            "rt_evaluate_with_paths", "rt_batch_set_shape", "rt_batch_get_shape", "rt_batch_tune",
-           "rt_set_shape", "rt_get_shape", "rt_tune")
+           "rt_set_shape", "rt_get_shape", "rt_tune", "rt_set_face_materials")
 RT_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -92,6 +92,7 @@ def load(build_if_missing=True):
     lib.rt_set_shape.argtypes = [P, P]
     lib.rt_get_shape.argtypes = [P, P]
     lib.rt_tune.argtypes = [P, P, I, P, P, P, P, P]
+    lib.rt_set_face_materials.argtypes = [P, P, I]
     _lib = lib
     return lib
 
@@ -153,7 +154,17 @@ class Scene:
         s = cls(sc.tri, sc.tri_face, sc.bodies)
         s.set_tx(sc.tx, sc.pol)
         s.set_freqs(sc.freqs)
+        if getattr(sc, "face_eps", None) is not None:
+            s.set_face_materials(sc.face_eps)
         return s
+
+    def set_face_materials(self, mat):
+        """Per face (kind, eps', eps''): kind 0 PEC, 1 dielectric (eps' - j eps''); None: all PEC."""
+        if mat is None:
+            _check(_lib.rt_set_face_materials(self._h, None, 0))
+            return
+        m = np.ascontiguousarray(np.asarray(mat, dtype=np.float32).reshape(-1, 3))
+        _check(_lib.rt_set_face_materials(self._h, _ptr(m), m.shape[0]))
 
     def close(self):
         if self._h:

@@ -125,6 +125,8 @@ struct rt_scene {
     FreqC *d_fqc = nullptr;            // [RT_MAX_FREQS / NFC] per-chunk frequency constants
     float4 *d_img = nullptr;            // source images, see DevScene::img
     float4 *d_txb = nullptr;            // source-side body frames, see DevScene::txb
+    float4 *d_face_mat = nullptr;       // face materials, see DevScene::face_mat
+    bool any_dielectric = false;
     unsigned long long *d_esc = nullptr;   // [CTR_N]: FP64-decided candidates, then one work queue per launch
     DevTable *table = nullptr;
     // state
@@ -169,6 +171,7 @@ static void free_scene(rt_scene *s) {
     cudaFree(s->d_tri); cudaFree(s->d_aux); cudaFree(s->d_face32); cudaFree(s->d_body);
     cudaFree(s->d_face64); cudaFree(s->d_face_rng); cudaFree(s->d_face_tris); cudaFree(s->d_freq); cudaFree(s->d_fqc);
     cudaFree(s->d_esc); cudaFree(s->io_rx); cudaFree(s->io_e); cudaFree(s->io_fl); cudaFree(s->d_img); cudaFree(s->d_txb);
+    cudaFree(s->d_face_mat);
 }
 
 // distance from point p to the solid of body b (0 if inside)
@@ -471,6 +474,29 @@ int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
     return RT_OK;
 }
 
+int rt_set_face_materials(rt_scene *s, const float *mat, int n_face) {
+    if (!s) return fail(RT_ERR_ARG, "rt_set_face_materials: NULL scene");
+    if (!mat) {
+        s->any_dielectric = false;
+        return RT_OK;
+    }
+    if (n_face != s->n_face) return fail(RT_ERR_ARG, "rt_set_face_materials: %d faces, the scene has %d", n_face, s->n_face);
+    std::vector<float4> m(n_face > 0 ? n_face : 1, make_float4(0.f, 0.f, 0.f, 0.f));
+    bool any = false;
+    for (int f = 0; f < n_face; ++f) {
+        const float kind = mat[3 * f], er = mat[3 * f + 1], ei = mat[3 * f + 2];
+        if (kind != 0.0f && kind != 1.0f) return fail(RT_ERR_ARG, "rt_set_face_materials: face %d: kind not 0 or 1", f);
+        if (kind == 1.0f && (!fin32(er) || !fin32(ei) || !(er > 0.0f) || ei < 0.0f))
+            return fail(RT_ERR_ARG, "rt_set_face_materials: face %d: eps' must be > 0 and eps'' >= 0", f);
+        m[f] = make_float4(kind, kind == 1.0f ? er : 0.f, kind == 1.0f ? ei : 0.f, 0.f);
+        any = any || kind == 1.0f;
+    }
+    if (!s->d_face_mat) CK(cudaMalloc(&s->d_face_mat, sizeof(float4) * (n_face > 0 ? n_face : 1)));
+    if (n_face > 0) CK(cudaMemcpy(s->d_face_mat, m.data(), sizeof(float4) * n_face, cudaMemcpyHostToDevice));
+    s->any_dielectric = any;
+    return RT_OK;
+}
+
 int rt_set_freqs(rt_scene *s, const double *f_hz, int n_f) {
     if (!s || !f_hz) return fail(RT_ERR_ARG, "rt_set_freqs: NULL argument");
     std::vector<FreqC> fq((RT_MAX_FREQS + NFC - 1) / NFC);
@@ -504,6 +530,7 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, 
     D.fqc = s->d_fqc;
     D.img = s->d_img;
     D.txb = s->d_txb;
+    D.face_mat = s->any_dielectric ? s->d_face_mat : nullptr;
     memcpy(D.tx, s->tx, sizeof(D.tx));
     memcpy(D.pol, s->pol, sizeof(D.pol));
     D.band_len = s->band_len;

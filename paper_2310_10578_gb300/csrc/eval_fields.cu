@@ -66,6 +66,7 @@ struct Ctx {
     const double *weid64;
     const float4 *img;           // source images (double-float), see DevScene
     const float4 *txb;           // [n_body][2] source-side body frame, see DevScene
+    const float4 *face_mat;      // face materials, see DevScene (nullptr: all PEC)
     // occluder masks (FP32 body kernels): occ_w words per body; word w of
     // body b's source-side mask has bit j set if body j may block a segment
     // from the source to a point of body b (occ_w = 0: no masks)
@@ -1239,6 +1240,85 @@ __device__ __forceinline__ void add_ray_chunks(AccS<T> &acc, const FreqC *fqs, i
         add_ray(a, fqs[k], e, amp, len);
     }
 }
+// ---- dielectric faces (planar reflections): Fresnel coefficients of a
+// half-space of relative permittivity eps = eps' - j eps'' (e^{+jwt}),
+//   G_perp = (cos - r) / (cos + r),  G_par = (eps cos - r) / (eps cos + r),
+//   r = sqrt(eps - sin^2) (principal branch), cos = |s_i . n|,
+// in the basis e_perp = unit(n x s_i), e_par = e_perp x s_i before and
+// e_perp x s_r after the bounce, the basis in which the PEC image mirror is
+// G_perp = -1, G_par = +1.  At normal incidence the reflection is G_perp E.
+template <typename T>
+__device__ __forceinline__ cpx<T> csqrt_t(cpx<T> z) {     // principal branch, without cancellation
+    T r = Sqrt(z.re * z.re + z.im * z.im);
+    if (z.re >= T(0)) {
+        T a = Sqrt((r + z.re) * T(0.5));
+        return mkc<T>(a, a > T(0) ? z.im / (a * T(2)) : T(0));
+    }
+    T b = Sqrt((r - z.re) * T(0.5));
+    return mkc<T>(Fabs(z.im) / (b * T(2)), z.im < T(0) ? -b : b);
+}
+template <typename T>
+__device__ __forceinline__ cpx<T> c3dot(const cpx<T> E[3], v3t<T> u) { return E[0] * u.x + E[1] * u.y + E[2] * u.z; }
+template <typename T>
+__device__ void reflect_face(const Ctx &c, int f, cpx<T> E[3], v3t<T> si, v3t<T> sr) {
+    v3t<T> n;
+    T d;
+    face_plane<T>(c, f, &n, &d);
+    const float4 m = c.face_mat ? c.face_mat[f] : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (m.x == 0.0f) {                                   // PEC: E -> -E + 2 (n.E) n
+        cpx<T> en = c3dot(E, n) * T(2);
+        E[0] = en * n.x - E[0]; E[1] = en * n.y - E[1]; E[2] = en * n.z - E[2];
+        return;
+    }
+    const T cth = Fabs(dot3(si, n));
+    const cpx<T> eps = mkc<T>(T((double)m.y), T(-(double)m.z));
+    const cpx<T> r = csqrt_t(mkc<T>(eps.re - (T(1) - cth * cth), eps.im));
+    const cpx<T> gs = cdiv(mkc<T>(cth - r.re, -r.im), mkc<T>(cth + r.re, r.im));
+    const cpx<T> ec = eps * cth;
+    const cpx<T> gp = cdiv(ec - r, ec + r);
+    v3t<T> ep = cross3(n, si);
+    const T ne = norm3(ep);
+    if (ne == T(0)) {
+        E[0] = E[0] * gs; E[1] = E[1] * gs; E[2] = E[2] * gs;
+        return;
+    }
+    ep = ep * (T(1) / ne);
+    const v3t<T> epi = cross3(ep, si), epr = cross3(ep, sr);
+    const cpx<T> a = gs * c3dot(E, ep), b = gp * c3dot(E, epi);
+    E[0] = a * ep.x + b * epr.x; E[1] = a * ep.y + b * epr.y; E[2] = a * ep.z + b * epr.z;
+}
+// a ray of complex polarisation e (amplitude amp, length len) at every frequency of fq
+template <typename T, typename L, typename ACC>
+__device__ __forceinline__ void add_ray_cx(ACC &acc, const FreqC &fq, const cpx<T> e[3], T amp, L len) {
+#pragma unroll 1
+    for (int f = 0; f < fq.nf; ++f) {
+        cpx<T> ph = phasor(fq, f, len) * amp;
+        acc_put(acc, f, ph * e[0], ph * e[1], ph * e[2]);
+    }
+}
+// planar image path S -> Q1 (face i) [-> Q2 (face j)] -> P with at least one
+// dielectric face: its complex polarisation, then the ray at every chunk
+template <typename T, typename L>
+__device__ __noinline__ void add_planar_dielectric(const Ctx &c, AccS<T> &acc, const FreqC *fqs, int nfq, v3t<T> S,
+                                                   v3t<T> Q1, v3t<T> Q2, v3t<T> P, int i, int j, T amp, L len) {
+    const v3t<T> s1 = unit3(Q1 - S);
+    const v3t<T> e0 = src_pol(c, s1);
+    cpx<T> E[3] = {mkc<T>(e0.x, T(0)), mkc<T>(e0.y, T(0)), mkc<T>(e0.z, T(0))};
+    if (j < 0) {
+        reflect_face(c, i, E, s1, unit3(P - Q1));
+    } else {
+        const v3t<T> s2 = unit3(Q2 - Q1);
+        reflect_face(c, i, E, s1, s2);
+        reflect_face(c, j, E, s2, unit3(P - Q2));
+    }
+#pragma unroll 1
+    for (int k = 0; k < nfq; ++k) {
+        AccS<T> a{acc.p + k * (NFC * 6 * 32)};
+        add_ray_cx(a, fqs[k], E, amp, len);
+    }
+}
+__device__ __forceinline__ bool dielectric(const Ctx &c, int f) { return c.face_mat && f >= 0 && c.face_mat[f].x != 0.0f; }
+
 template <typename T>
 __device__ __forceinline__ void acc_zero_rows(AccS<T> &acc, int rows) {
 #pragma unroll 4
@@ -1717,8 +1797,12 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                             LT L;
                             if constexpr (sizeof(T) == 4) L = df_dist_df(c.img[2 * i], c.img[2 * i + 1], Pf);
                             else L = ladd(seglen(Sx, g.Q1), seglen(g.Q1, P));
-                            add_ray_chunks(acc, fqs, nfq, pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni),
-                                           T(1) / (T)len_val(L), L);
+                            if (dielectric(c, i))
+                                add_planar_dielectric(c, acc, fqs, nfq, Sx, g.Q1, g.Q1, P, i, -1,
+                                                      T(1) / (T)len_val(L), L);
+                            else
+                                add_ray_chunks(acc, fqs, nfq, pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni),
+                                               T(1) / (T)len_val(L), L);
                         }
                     }
                 }
@@ -1748,8 +1832,13 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                                 } else {
                                     L = ladd(ladd(seglen(Sx, g.Q1), seglen(g.Q1, g.Q2)), seglen(g.Q2, P));
                                 }
-                                v3t<T> e = pec_mirror(pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni), nj);
-                                add_ray_chunks(acc, fqs, nfq, e, T(1) / (T)len_val(L), L);
+                                if (dielectric(c, i) || dielectric(c, j)) {
+                                    add_planar_dielectric(c, acc, fqs, nfq, Sx, g.Q1, g.Q2, P, i, j,
+                                                          T(1) / (T)len_val(L), L);
+                                } else {
+                                    v3t<T> e = pec_mirror(pec_mirror(src_pol(c, unit3(g.Q1 - Sx)), ni), nj);
+                                    add_ray_chunks(acc, fqs, nfq, e, T(1) / (T)len_val(L), L);
+                                }
                             }
                         }
                     }
@@ -2003,6 +2092,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         c.fock = s_fock; c.res = s_res; c.weid = s_weid; c.weid_L = S.weid_L;
         c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
         c.img = S.img;
+        c.face_mat = S.face_mat;
         c.txb = body_sm ? s_txb : F1.txb;
         c.occ_src = nullptr;
         c.occ_w = 0;
@@ -2693,7 +2783,14 @@ __device__ __noinline__ void adj_planar(const Ctx &c, int order, int i, int j, v
         D8 d1 = dot3(ni, S1) - di, dP = dot3(ni, P) - di;
         v3t<D8> Q = S1 + (P - S1) * (d1 / (d1 - dP));
         D8 L = norm3(Q - S) + norm3(P - Q);
-        add_ray(acc, fq, pec_mirror(src_pol(c, unit3(Q - S)), ni), D8(1.0) / L, L);
+        if (dielectric(c, i)) {
+            const v3t<D8> s1 = unit3(Q - S), e0 = src_pol(c, s1);
+            cpx<D8> E[3] = {mkc<D8>(e0.x, D8(0.0)), mkc<D8>(e0.y, D8(0.0)), mkc<D8>(e0.z, D8(0.0))};
+            reflect_face(c, i, E, s1, unit3(P - Q));
+            add_ray_cx(acc, fq, E, D8(1.0) / L, L);
+        } else {
+            add_ray(acc, fq, pec_mirror(src_pol(c, unit3(Q - S)), ni), D8(1.0) / L, L);
+        }
         return;
     }
     face_plane<D8>(c, j, &nj, &dj);
@@ -2703,7 +2800,15 @@ __device__ __noinline__ void adj_planar(const Ctx &c, int order, int i, int j, v
     D8 e1 = dot3(ni, S1) - di, eq = dot3(ni, Q2) - di;
     v3t<D8> Q1 = S1 + (Q2 - S1) * (e1 / (e1 - eq));
     D8 L = norm3(Q1 - S) + norm3(Q2 - Q1) + norm3(P - Q2);
-    add_ray(acc, fq, pec_mirror(pec_mirror(src_pol(c, unit3(Q1 - S)), ni), nj), D8(1.0) / L, L);
+    if (dielectric(c, i) || dielectric(c, j)) {
+        const v3t<D8> s1 = unit3(Q1 - S), s2 = unit3(Q2 - Q1), e0 = src_pol(c, s1);
+        cpx<D8> E[3] = {mkc<D8>(e0.x, D8(0.0)), mkc<D8>(e0.y, D8(0.0)), mkc<D8>(e0.z, D8(0.0))};
+        reflect_face(c, i, E, s1, s2);
+        reflect_face(c, j, E, s2, unit3(P - Q2));
+        add_ray_cx(acc, fq, E, D8(1.0) / L, L);
+    } else {
+        add_ray(acc, fq, pec_mirror(pec_mirror(src_pol(c, unit3(Q1 - S)), ni), nj), D8(1.0) / L, L);
+    }
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -2729,7 +2834,7 @@ __global__ void __launch_bounds__(128) k_adjoint(DevScene S, const float *__rest
     c.pol = mk3(S.pol[0], S.pol[1], S.pol[2]);
     c.fock = nullptr; c.res = nullptr; c.weid = nullptr; c.weid_L = S.weid_L;
     c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
-    c.img = S.img; c.txb = S.txb; c.occ_src = nullptr; c.occ_w = 0;
+    c.img = S.img; c.txb = S.txb; c.occ_src = nullptr; c.occ_w = 0; c.face_mat = S.face_mat;
     const int lane = threadIdx.x & 31;
     const int nch = (S.n_f + NFC - 1) / NFC;
     const v3t<D8> Sd = mk3<D8>(dvar(c.S.x, DS_SX), dvar(c.S.y, DS_SY), dvar(c.S.z, DS_SZ));

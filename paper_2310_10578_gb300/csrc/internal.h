@@ -72,6 +72,8 @@ struct DevScene {
     float weid_L;
     const float4 *img;         // [n_face + n_face^2][2]: source images (hi, lo) as double-float:
                                // [f] mirror of Tx in face f; [n_face + i n_face + j] in i then j
+    const float4 *face_mat;    // [n_face]: (dielectric ? 1 : 0, eps', eps'', 0), eps_r = eps' - j eps''; or
+                               // nullptr when every face is PEC
     const float4 *txb;         // [n_body][2] per transmitter, FP64-computed: (u, |S - c|), (beta_s, sqrt(|S-c|^2 - a^2) hi, lo,
                                // lateral paths possible ? 1 : 0); cylinders use horizontal distances
     const double *freq;        // [n_f] Hz (host copy, read by the launcher)

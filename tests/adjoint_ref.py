@@ -30,7 +30,8 @@ def _scene64(sc, bodies=None, tx=None, freqs=None, rx=None):
                            tx=np.asarray(sc.tx if tx is None else tx, dtype=np.float64),
                            pol=np.asarray(sc.pol, dtype=np.float64),
                            freqs=np.asarray(sc.freqs if freqs is None else freqs, dtype=np.float64),
-                           rx=sc.rx if rx is None else rx, max_order=sc.max_order)
+                           rx=sc.rx if rx is None else rx, max_order=sc.max_order,
+                           face_eps=getattr(sc, "face_eps", None))
 
 
 def _path_fields(scene, enable, cap):

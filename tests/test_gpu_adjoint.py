@@ -145,3 +145,12 @@ def test_autograd_power_db_over_a_zone(creep, oracle_mod):
     for k in range(3):
         _close(float(tx.grad[k]), ref["tx"][k], ref["tx_abs"][k], "tx %d" % k)
     _close(float(fr.grad[0]), ref["f"][0], ref["f_abs"][0], "freq")
+
+
+def test_adjoint_dielectric_faces(creep, oracle_mod):
+    # the planar paths' Fresnel reflections move with the transmitter and the frequency
+    walls = (5.31, 0.48)
+    sc = _jitter(scenes.room(n_cyl=8, nx=20, ny=16, freqs=(2.4e9, 5.8e9), seed=17,
+                             face_eps=[(4.0, 0.2), None, walls, walls, walls, walls]), 19)
+    n_checked, _ = _check(creep, sc, bodies=range(3), seed=5)
+    assert n_checked >= 6

@@ -267,3 +267,23 @@ def test_scene_tile_shapes_and_tune(creep, oracle_mod):
     with pytest.raises(creep.CreepError) as e:
         S.set_shape(4, 4, 5)
     assert e.value.code == creep.RT_ERR_ARG
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_dielectric_faces(creep, oracle_mod, precision):
+    """Dielectric (Fresnel) walls and floor, PEC ceiling: the oracle's fields
+    within the bound, its path lists bit for bit (materials change no
+    visibility)."""
+    walls = (5.31, 0.48)
+    sc = scenes.room(n_cyl=20, nx=61, ny=47, seed=8, face_eps=[(4.0, 0.2), None, walls, walls, walls, walls])
+    opts = creep.options(max_order=2, precision=creep.RT_PREC_FP64 if precision == "fp64" else creep.RT_PREC_FP32)
+    S, Eg, codes, counts, fl, _ = _run(creep, sc, opts=opts)
+    ref = oracle_mod.evaluate(sc)
+    compare_paths(codes, counts, ref)
+    _flags_equal(fl, ref)
+    compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs)
+    pec = oracle_mod.evaluate(scenes.room(n_cyl=20, nx=61, ny=47, seed=8))
+    assert np.max(np.abs(ref.E - pec.E)) > 0.1 * np.max(np.abs(pec.E))     # the materials matter
+    with pytest.raises(creep.CreepError) as e:
+        S.set_face_materials([(1, -2.0, 0.0)] * 6)
+    assert e.value.code == creep.RT_ERR_ARG
