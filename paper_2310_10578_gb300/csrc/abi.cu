@@ -913,7 +913,7 @@ int rt_batch_get_shape(rt_batch *b, int shape[3]) {
 static std::mutex g_tune_mu;
 static std::map<std::vector<long long>, std::vector<int>> g_tuned;
 
-// Coordinate search over tile shapes from the default {4, 4, 4}: body warps
+// Coordinate search over tile shapes from the default {4, 4, min(4, nch)}: body warps
 // per tile, then planar warps per tile, then planar chunks per launch (up to
 // nch), each timed as the faster of two evaluations after a warm-up.
 // run(shape) queues one evaluation on st.  A shape that cannot launch is
@@ -946,7 +946,7 @@ static int tune_shape(RUN run, cudaStream_t st, int nch, const std::vector<long 
         *ms = tb;
         return rc;
     };
-    best[0] = 4; best[1] = 4; best[2] = 4;
+    best[0] = 4; best[1] = 4; best[2] = nch < 4 ? (nch > 0 ? nch : 1) : 4;
     float t_best = 0.f;
     int rc = time_shape(best, &t_best);
     const int cand_body[] = {2, 3, 4, 6, 12}, cand_planar[] = {1, 2, 4}, cand_chunks[] = {1, 2, 3, 4};

@@ -2302,9 +2302,11 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                         for (int j = part; j < fqc.nf * 3; j += NWT) {
                             T re = pp[(w0 * prow + 2 * j) * 32], im = pp[(w0 * prow + 2 * j + 1) * 32];
 #pragma unroll
-                            for (int w = 1; w < NWT; ++w) {
-                                re = re + pp[((w0 + w) * prow + 2 * j) * 32];
-                                im = im + pp[((w0 + w) * prow + 2 * j + 1) * 32];
+                            for (int w = 1; w < NW; ++w) {      // (unrolled to the block's warps, in order)
+                                if (w < NWT) {
+                                    re = re + pp[((w0 + w) * prow + 2 * j) * 32];
+                                    im = im + pp[((w0 + w) * prow + 2 * j + 1) * 32];
+                                }
                             }
                             size_t idx = ((size_t)(f0 + j / 3) * 3 + (j % 3)) * n_rx + ro;
                             float2 v;
@@ -2320,7 +2322,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                         if (ch == 0 && part == 0 && flags_out) {
                             uint32_t f_all = 0;
 #pragma unroll
-                            for (int w = 0; w < NWT; ++w) f_all |= s_fl[w0 + w][lane];
+                            for (int w = 0; w < NW; ++w)
+                                if (w < NWT) f_all |= s_fl[w0 + w][lane];
                             flags_out[ro] = add ? (flags_out[ro] | f_all) : f_all;
                         }
                     }
