@@ -287,3 +287,15 @@ def test_dielectric_faces(creep, oracle_mod, precision):
     with pytest.raises(creep.CreepError) as e:
         S.set_face_materials([(1, -2.0, 0.0)] * 6)
     assert e.value.code == creep.RT_ERR_ARG
+
+
+def test_alu_peaks(creep):
+    """The measured FFMA and SFU rates are near the device's unit counts x
+    clock: FFMA within [0.5, 1.2] of SMs x 128 lanes x 2 x the maximum clock,
+    SFU at least 8 per SM per clock."""
+    ffma, mufu = creep.alu_peaks()
+    p = torch.cuda.get_device_properties(0)
+    clock_ghz = 2.1           # GB300 maximum SM clock, about
+    derived = p.multi_processor_count * 128 * 2 * clock_ghz / 1e3          # TFLOP/s
+    assert 0.5 * derived <= ffma <= 1.2 * derived, (ffma, derived)
+    assert mufu >= p.multi_processor_count * 8 * clock_ghz * 0.5, mufu      # Gop/s
