@@ -75,8 +75,8 @@ extern "C" {
 #define RT_PATH_R1 1       /* id1 = face */
 #define RT_PATH_R2 2       /* id1 = first face, id2 = second face */
 #define RT_PATH_RB 3       /* id1 = body: GO reflection off the body */
-#define RT_PATH_CP 4       /* id1 = body: creeping ray, short way round */
-#define RT_PATH_CM 5       /* id1 = body: creeping ray, long way round */
+#define RT_PATH_CP 4       /* id1 = body, id2 = extra turns: creeping ray, short way round */
+#define RT_PATH_CM 5       /* id1 = body, id2 = extra turns: creeping ray, long way round */
 
 /* library limits */
 #define RT_MAX_FACES 64
@@ -97,6 +97,10 @@ typedef struct {
     int max_order;      /* planar reflection order 0, 1 or 2 */
     unsigned enable;    /* RT_EN_* mask */
     int precision;      /* RT_PREC_* */
+    int max_encirclements;  /* creeping rays: extra full turns round a body, 0-4 (0: the first ray
+                               each way only).  Turn n's ray is the first one's with its arc
+                               lengthened by 2 pi a n, listed as (CP or CM, body, n); it exists where
+                               the first one does and its heights on a cylinder are in range */
 } rt_options;
 
 typedef struct {

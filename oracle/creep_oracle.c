@@ -172,6 +172,7 @@ typedef struct {
     int n_f; const double *freq;
     const fock_rule *fock;
     int max_order, enable;
+    int max_enc;                        /* extra encirclements of the creeping rays (0: the first ray only) */
 } scene;
 
 static inline v3 tri_v(const scene *s, int t, int k) {
@@ -481,6 +482,7 @@ typedef struct {
     double rho_g;          /* geodesic radius of curvature (constant along the ray) */
     int caustic_j;         /* 1: the ray crossed the source axis (factor +j) */
     double dperp_P;        /* receiver distance from the source axis (sphere; 0 for cylinder) */
+    int turns;             /* extra full encirclements */
 } creep_geom;
 
 /* Frame of a sphere/cylinder problem: u towards S, v in the (S, c, P) plane towards P. */
@@ -574,12 +576,16 @@ static int cylinder_reflection(const body *B, v3 S, v3 P, refl_geom *G) {
  * geodesic in the (S, c, P) plane; t = a (angle travelled); exists iff t > 0.
  * Divergence x spreading = sqrt(d_perp(Q1)/d_perp(P)) / sqrt(s), d_perp the
  * distance from the S-c axis; the long-way ray crosses that axis once. */
-static int sphere_creeping(const body *B, v3 S, v3 P, int dir, creep_geom *G) {
+/* turns: extra full encirclements (the ray of the first one with its arc
+ * lengthened by 2 pi a turns; it exists where the first one does). */
+static int sphere_creeping(const body *B, v3 S, v3 P, int dir, int turns, creep_geom *G) {
     body_frame F;
     sphere_frame(B, S, P, &F);
     double a = B->a;
     double dpsi = (dir == 0) ? (F.gam - F.bs - F.bp) : (TWO_PI - F.gam - F.bs - F.bp);
     if (!(dpsi > 0.0)) return 0;
+    dpsi += TWO_PI * turns;
+    G->turns = turns;
     double psi1 = (dir == 0) ? F.bs : -F.bs;
     double psi2 = (dir == 0) ? F.gam - F.bp : F.gam + F.bp;
     G->n1 = add(scl(F.u, cos(psi1)), scl(F.v, sin(psi1)));
@@ -601,12 +607,14 @@ static int sphere_creeping(const body *B, v3 S, v3 P, int dir, creep_geom *G) {
  * line of horizontal length H = d_s + a dphi + d_p and rise dz.  Valid iff
  * dphi > 0 and both Q1, Q2 lie within cz <= z <= cz + h.
  * Amplitude (1/s') sqrt(s'/(s'+t)) sqrt((s'+t)/(s (s'+t+s))) = 1/sqrt(s' s (s'+t+s)). */
-static int cylinder_creeping(const body *B, v3 S, v3 P, int dir, creep_geom *G) {
+static int cylinder_creeping(const body *B, v3 S, v3 P, int dir, int turns, creep_geom *G) {
     body_frame F;
     if (!cylinder_frame(B, S, P, &F)) return 0;
     double a = B->a;
     double dphi = (dir == 0) ? (F.gam - F.bs - F.bp) : (TWO_PI - F.gam - F.bs - F.bp);
     if (!(dphi > 0.0)) return 0;
+    dphi += TWO_PI * turns;
+    G->turns = turns;
     double ds_ = sqrt(F.ds * F.ds - a * a), dp_ = sqrt(F.dp * F.dp - a * a);
     double dz = P.z - S.z;
     double H = ds_ + a * dphi + dp_;
@@ -682,6 +690,10 @@ static void add_creeping(const scene *s, const creep_geom *G, v3 P, rx_state *st
     double Es = dot(e0, b1), Eh = dot(e0, G->n1);
     double L = G->sp * G->sq / (G->sp + G->sq);
     cplx caus = G->caustic_j ? I : 1.0;
+    /* a sphere's ray crosses the source axis twice per extra encirclement:
+     * +j per crossing, -1 per turn */
+    int sphere_turns = (G->dperp_P > 0.0) ? G->turns : 0;
+    if (sphere_turns & 1) caus = -caus;
     for (int f = 0; f < s->n_f; ++f) {
         double k = kwave(s->freq[f]);
         double m = cbrt(k * G->rho_g / 2.0);
@@ -711,14 +723,16 @@ static void body_paths(const scene *s, int b, v3 P, rx_state *st) {
         }
     }
     if (!(s->enable & (EN_CREEP_SOFT | EN_CREEP_HARD))) return;
+    for (int turns = 0; turns <= s->max_enc; ++turns)
     for (int dir = 0; dir < 2; ++dir) {
         creep_geom G;
         st->ct.creep_geom++;
-        int ok = (B->type == 0) ? sphere_creeping(B, S, P, dir, &G) : cylinder_creeping(B, S, P, dir, &G);
+        int ok = (B->type == 0) ? sphere_creeping(B, S, P, dir, turns, &G)
+                                : cylinder_creeping(B, S, P, dir, turns, &G);
         if (!ok) continue;
         if (!visible(s, S, G.Q1, -1, -1, b, &st->ct)) continue;
         if (!visible(s, G.Q2, P, -1, -1, b, &st->ct)) continue;
-        add_path(st, pcode(dir == 0 ? PT_CP : PT_CM, b, 0));
+        add_path(st, pcode(dir == 0 ? PT_CP : PT_CM, b, turns));
         if (B->type == 0) {
             /* axial caustic of the sphere's creeping rays: flag k d_perp < pi */
             for (int f = 0; f < s->n_f; ++f)
@@ -781,7 +795,7 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
                 int max_order, int enable,
                 double *E_out, uint64_t *path_codes, int *path_count, int cap,
                 unsigned *flags_out, long long *counters_out, int n_threads, double *sabs_out,
-                double *path_E_out, const double *face_eps) {
+                double *path_E_out, const double *face_eps, int max_enc) {
     fock_rule R = {tau_re, tau_im, ws_re, ws_im, wh_re, wh_im, offsets, n_buckets,
                    res_alpha, res_cs, res_beta, res_ch, n_res, xi_lo, xi_hi};
     scene s;
@@ -806,6 +820,7 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
     s.pol = V(pol[0], pol[1], pol[2]);
     s.n_f = n_f; s.freq = freq; s.fock = &R;
     s.max_order = max_order; s.enable = enable;
+    s.max_enc = max_enc;
     counters tot;
     memset(&tot, 0, sizeof(tot));
 #ifdef _OPENMP
@@ -905,11 +920,11 @@ int oracle_body_reflection(const double *body6, const double *S, const double *P
     memcpy(out, v, sizeof(v));
     return 1;
 }
-int oracle_body_creeping(const double *body6, const double *S, const double *P, int dir, double *out) {
+int oracle_body_creeping(const double *body6, const double *S, const double *P, int dir, int turns, double *out) {
     body B = body_from(body6);
     creep_geom G;
     v3 s_ = V(S[0], S[1], S[2]), p_ = V(P[0], P[1], P[2]);
-    int ok = (B.type == 0) ? sphere_creeping(&B, s_, p_, dir, &G) : cylinder_creeping(&B, s_, p_, dir, &G);
+    int ok = (B.type == 0) ? sphere_creeping(&B, s_, p_, dir, turns, &G) : cylinder_creeping(&B, s_, p_, dir, turns, &G);
     if (!ok) return 0;
     double v[19] = {G.Q1.x, G.Q1.y, G.Q1.z, G.Q2.x, G.Q2.y, G.Q2.z, G.n1.x, G.n1.y, G.n1.z,
                     G.n2.x, G.n2.y, G.n2.z, G.sp, G.t, G.sq, G.amp, G.rho_g, (double)G.caustic_j, G.dperp_P};

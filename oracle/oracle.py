@@ -54,12 +54,12 @@ def _load():
         d = ctypes.c_double
         _lib.oracle_eval.argtypes = [P, P, i, P, i, P, P, P, i, P, i,
                                      P, P, P, P, P, P, P, i, P, P, P, P, i, d, d,
-                                     i, i, P, P, P, i, P, P, i, P, P, P]
+                                     i, i, P, P, P, i, P, P, i, P, P, P, i]
         _lib.oracle_eval.restype = i
         _lib.oracle_transition_F.argtypes = [P, i, P]
         _lib.oracle_fock_bracket.argtypes = [P, P, P, P, P, P, P, i, P, P, P, P, i, d, d, P, P, i, P]
         _lib.oracle_body_reflection.argtypes = [P, P, P, P]
-        _lib.oracle_body_creeping.argtypes = [P, P, P, i, P]
+        _lib.oracle_body_creeping.argtypes = [P, P, P, i, i, P]
         _lib.oracle_seg_hits_body.argtypes = [P, P, P]
         _lib.oracle_reflect.argtypes = [P, P, P, P, i, d, d, P]
         _lib.oracle_reflect.restype = None
@@ -131,7 +131,7 @@ def evaluate(scene, rx=None, enable=EN_ALL, cap=256, threads=0, want_paths=True,
                     scene.max_order, enable, _p(E),
                     _p(codes) if want_paths else None, _p(counts), cap if want_paths else 0,
                     _p(flags), _p(ctr), threads, _p(sabs), _p(pE) if pE is not None else None,
-                    _p(fe) if fe is not None else None)
+                    _p(fe) if fe is not None else None, int(getattr(scene, "max_enc", 0)))
     res = Result()
     res.seconds = time.perf_counter() - t0
     res.E = E[..., 0] + 1j * E[..., 1]
@@ -184,12 +184,13 @@ def body_reflection(body6, S, P):
     return dict(Q=out[0:3], n=out[3:6], inv_f1=out[6], inv_f2=out[7], rho_g=out[8])
 
 
-def body_creeping(body6, S, P, direction):
-    """Creeping-ray geometry (direction 0 short way, 1 long way) or None."""
+def body_creeping(body6, S, P, direction, turns=0):
+    """Creeping-ray geometry (direction 0 short way, 1 long way; `turns` extra
+    full turns round the body) or None."""
     lib = _load()
     out = np.zeros(19)
     b, s, p = _d3(body6), _d3(S), _d3(P)
-    if not lib.oracle_body_creeping(_p(b), _p(s), _p(p), int(direction), _p(out)):
+    if not lib.oracle_body_creeping(_p(b), _p(s), _p(p), int(direction), int(turns), _p(out)):
         return None
     return dict(Q1=out[0:3], Q2=out[3:6], n1=out[6:9], n2=out[9:12], sp=out[12], t=out[13], sq=out[14],
                 amp=out[15], rho_g=out[16], caustic_j=bool(out[17]), dperp_P=out[18])

@@ -41,7 +41,8 @@ class rt_body(ctypes.Structure):
 
 
 class rt_options(ctypes.Structure):
-    _fields_ = [("max_order", ctypes.c_int), ("enable", ctypes.c_uint), ("precision", ctypes.c_int)]
+    _fields_ = [("max_order", ctypes.c_int), ("enable", ctypes.c_uint), ("precision", ctypes.c_int),
+                ("max_encirclements", ctypes.c_int)]
 
 
 class rt_stats(ctypes.Structure):
@@ -110,8 +111,8 @@ def _ptr(a):
     return ctypes.c_void_p(a.data_ptr())
 
 
-def options(max_order=2, enable=RT_EN_ALL, precision=RT_PREC_FP32):
-    return rt_options(max_order, enable, precision)
+def options(max_order=2, enable=RT_EN_ALL, precision=RT_PREC_FP32, max_encirclements=0):
+    return rt_options(max_order, enable, precision, max_encirclements)
 
 
 def _stream_handle(stream):

@@ -512,8 +512,10 @@ int rt_set_freqs(rt_scene *s, const double *f_hz, int n_f) {
 }
 
 static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, bool need_freqs = true) {
-    rt_options o = {2, RT_EN_ALL, RT_PREC_FP32};
+    rt_options o = {2, RT_EN_ALL, RT_PREC_FP32, 0};
     if (opt) o = *opt;
+    if (o.max_encirclements < 0 || o.max_encirclements > 4)
+        return fail(RT_ERR_ARG, "max_encirclements %d not in [0, 4]", o.max_encirclements);
     if (o.max_order < 0 || o.max_order > 2) return fail(RT_ERR_ARG, "max_order %d not in [0, 2]", o.max_order);
     if (o.precision != RT_PREC_FP32 && o.precision != RT_PREC_FP64) return fail(RT_ERR_ARG, "bad precision %d", o.precision);
     if (o.enable & ~RT_EN_ALL) return fail(RT_ERR_ARG, "bad enable mask 0x%x", o.enable);
@@ -535,6 +537,7 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, 
     memcpy(D.pol, s->pol, sizeof(D.pol));
     D.band_len = s->band_len;
     D.max_order = o.max_order;
+    D.max_enc = o.max_encirclements;
     D.enable = o.enable;
     *prec = o.precision;
     return RT_OK;

@@ -67,6 +67,7 @@ struct Ctx {
     const float4 *img;           // source images (double-float), see DevScene
     const float4 *txb;           // [n_body][2] source-side body frame, see DevScene
     const float4 *face_mat;      // face materials, see DevScene (nullptr: all PEC)
+    int enc;                     // this launch's creeping rays: extra full turns round the body
     // occluder masks (FP32 body kernels): occ_w words per body; word w of
     // body b's source-side mask has bit j set if body j may block a segment
     // from the source to a point of body b (occ_w = 0: no masks)
@@ -889,6 +890,10 @@ __device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T ba
     const T TWO_PI_T = T(6.283185307179586476925286766559);
     T dpsi = (dir == 0) ? (F.gam - F.bs - F.bp) : (TWO_PI_T - F.gam - F.bs - F.bp);
     if (!conj(acc, decide(dpsi * a, band, D_NO))) return D_NO;
+    // extra encirclements: the same attachment and shedding points, the arc
+    // 2 pi a longer per turn; on a sphere the ray crosses the source axis
+    // twice per turn (+j each: -1 per turn)
+    if (c.enc > 0) dpsi = dpsi + TWO_PI_T * T(c.enc);
     T psi1 = (dir == 0) ? F.bs : -F.bs;
     T psi2 = (dir == 0) ? F.gam - F.bp : F.gam + F.bp;
     T s1, c1, s2, c2;
@@ -914,6 +919,7 @@ __device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T ba
         T dq1 = a * Sqrt(Fmax(T(0), T(1) - (a / F.ds) * (a / F.ds)));   // a sin(beta_s)
         if (band == T(0)) { T sb, cb; SinCos(F.bs, &sb, &cb); dq1 = a * sb; }
         g.amp = (g.dperp > T(0)) ? Sqrt(dq1 / g.dperp) / Sqrt(g.sq) / g.sp : T(0);
+        if (c.enc & 1) g.amp = -g.amp;           // the (-1) of an odd number of extra turns
     } else {
         T ds_ = F.sps, dp_ = F.sqp;
         T dz = P.z - S.z;
@@ -1484,7 +1490,8 @@ __device__ __forceinline__ void creep_prep(const Ctx &c, float *r, v3t<float> S,
     v3t<float> e0 = src_pol(c, t1);
     float Es = (enable & RT_EN_CREEP_SOFT) ? dot3(e0, b1) : 0.0f;
     float Eh = (enable & RT_EN_CREEP_HARD) ? dot3(e0, g.n1) : 0.0f;
-    rec_put(r, Es, Eh, b2, g.n2, g.caus ? -g.amp : g.amp, -(g.sp * g.sq / (g.sp + g.sq)), cbrtf(g.rho_g),
+    if (signbit(g.amp)) { Es = -Es; Eh = -Eh; }  // (the record's amplitude sign is the caustic flag)
+    rec_put(r, Es, Eh, b2, g.n2, g.caus ? -fabsf(g.amp) : fabsf(g.amp), -(g.sp * g.sq / (g.sp + g.sq)), cbrtf(g.rho_g),
             g.t / g.rho_g, len);
 }
 __device__ __forceinline__ void creep_apply(const Ctx &c, AccS<float> &acc, const FreqC &fq, const float *r) {
@@ -1924,7 +1931,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                                     d = esc_creep(c, b, dir, Pf, fq, !PATHS && !defer, half_lambda_max, enable, &ct,
                                                   &caus, defer ? rec + nrec * REC_N * 32 : nullptr, &added);
                                     if (d == D_YES) {
-                                        emit(dir == 0 ? PT_CP : PT_CM, b, 0);
+                                        emit(dir == 0 ? PT_CP : PT_CM, b, c.enc);
                                         if (caus) fl |= RT_FLAG_CAUSTIC;
                                         if (defer) nrec += added;
                                         else if (!PATHS) acc_add(acc, ct, nf);
@@ -1933,7 +1940,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                                 }
                             }
                             if (d != D_YES) continue;
-                            emit(dir == 0 ? PT_CP : PT_CM, b, 0);
+                            emit(dir == 0 ? PT_CP : PT_CM, b, c.enc);
                             if (sphere) {
                                 if (cd == D_YES) fl |= RT_FLAG_CAUSTIC;
                                 if (!(g.dperp > T(0.0))) continue;        // exactly on the axis: no finite ray field
@@ -2039,7 +2046,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
        const float *__restrict__ rx_base, const int32_t *__restrict__ perm, float *__restrict__ e_base,
        uint32_t *__restrict__ fl_base,
        uint64_t *__restrict__ codes, int32_t *__restrict__ counts, int cap, int ch0, int nch, int rcap,
-       int nwt, int accumulate, unsigned long long *esc_counter, unsigned long long *queue) {
+       int nwt, int accumulate, int enc, unsigned long long *esc_counter, unsigned long long *queue) {
     constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     extern __shared__ float4 smem[];
     __shared__ Ctx s_ctx;
@@ -2096,6 +2103,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         c.txb = body_sm ? s_txb : F1.txb;
         c.occ_src = nullptr;
         c.occ_w = 0;
+        c.enc = enc;
 
     }
     __syncthreads();
@@ -2374,7 +2382,8 @@ struct Work {
 };
 
 template <typename T, bool PATHS, int CLS, bool LIST = false>
-static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch, int accumulate, LaunchCtx &L) {
+static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch, int accumulate, LaunchCtx &L,
+                              int enc = 0) {
     if (L.n >= CTR_QUEUES) return cudaErrorInvalidValue;
     constexpr bool bodies = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
     constexpr int blk = blk_of(CLS, sizeof(T) == 4);
@@ -2421,7 +2430,7 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     cfg.attrs = attr;
     cfg.numAttrs = L.n > 0 ? 1 : 0;
     e = cudaLaunchKernelEx(&cfg, k_eval<T, PATHS, CLS, LIST>, S, W.F1, W.frames, W.n_frames, W.n_tiles, W.rx, W.perm, W.e, W.fl,
-                           W.codes, W.counts, W.cap, ch0, nch, rcap, nwt, accumulate, L.ctr, L.ctr + 1 + L.n);
+                           W.codes, W.counts, W.cap, ch0, nch, rcap, nwt, accumulate, enc, L.ctr, L.ctr + 1 + L.n);
     ++L.n;
     return e != cudaSuccess ? e : cudaGetLastError();
 }
@@ -2430,7 +2439,9 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
 // three classes per frequency chunk.  FP32 fields: the planar kernel per
 // PLANAR_CHUNKS chunks, then each body kernel once for all chunks (the
 // geometry of a pass serves every chunk it covers).
-// The first launch writes the outputs, the later ones add to them.
+// The first launch writes the outputs, the later ones add to them.  Creeping
+// rays with extra turns round the body: one more creeping launch per turn
+// count (the geometry differs only in the arc length).
 template <typename T, bool PATHS, bool LIST = false>
 static cudaError_t launch_all(const DevScene &S, const Work &W, int nchunks, LaunchCtx &L) {
     cudaError_t e = cudaSuccess;
@@ -2443,10 +2454,12 @@ static cudaError_t launch_all(const DevScene &S, const Work &W, int nchunks, Lau
         const int n = nchunks - ch < pstep ? nchunks - ch : pstep;
         e = launch_one<T, PATHS, CLS_PLANAR, LIST>(S, W, ch, n, 0, L);
         if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL, LIST>(S, W, ch, 1, 1, L);
-        if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_CREEP, LIST>(S, W, ch, 1, 1, L);
+        for (int enc = 0; chunked_bodies && enc <= S.max_enc && e == cudaSuccess; ++enc)
+            e = launch_one<T, PATHS, CLS_CREEP, LIST>(S, W, ch, 1, 1, L, enc);
     }
     if (!chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL, LIST>(S, W, 0, nchunks, 1, L);
-    if (!chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_CREEP, LIST>(S, W, 0, nchunks, 1, L);
+    for (int enc = 0; !chunked_bodies && enc <= S.max_enc && e == cudaSuccess; ++enc)
+        e = launch_one<T, PATHS, CLS_CREEP, LIST>(S, W, 0, nchunks, 1, L, enc);
     return e;
 }
 
@@ -2713,8 +2726,9 @@ __device__ __noinline__ void adj_rb(const Ctx &c, int b, v3t<D8> S, v3t<D8> P, c
     field_body_refl<D8, D8, false, AccAdj>(c, acc, fq, S, P, g, norm3(Q - S) + norm3(P - Q));
 }
 
-// creeping ray round body b, dir 0 short way, 1 long way; false: no finite field
-__device__ __noinline__ bool adj_creep(const Ctx &c, int b, int dir, v3t<D8> S, v3t<D8> P, const FreqC &fq,
+// creeping ray round body b, dir 0 short way, 1 long way, with enc extra
+// turns; false: no finite field
+__device__ __noinline__ bool adj_creep(const Ctx &c, int b, int dir, int enc, v3t<D8> S, v3t<D8> P, const FreqC &fq,
                                        unsigned enable, AccAdj &acc) {
     v3t<D8> cc;
     D8 a;
@@ -2725,12 +2739,13 @@ __device__ __noinline__ bool adj_creep(const Ctx &c, int b, int dir, v3t<D8> S, 
     else cyl_frame(S, P, cc.x, cc.y, a, F, D8(0.0));
     const D8 TWO_PI(6.283185307179586476925286766559);
     D8 dpsi = (dir == 0) ? (F.gam - F.bs - F.bp) : (TWO_PI - F.gam - F.bs - F.bp);
+    dpsi = dpsi + TWO_PI * D8((double)enc);
+    Geo<D8> g;
     D8 psi1 = (dir == 0) ? F.bs : -F.bs;
     D8 psi2 = (dir == 0) ? F.gam - F.bp : F.gam + F.bp;
     D8 s1, c1, s2, c2;
     SinCos(psi1, &s1, &c1);
     SinCos(psi2, &s2, &c2);
-    Geo<D8> g;
     g.n1 = F.u * c1 + F.v * s1;
     g.n2 = F.u * c2 + F.v * s2;
     if (sphere) {
@@ -2748,6 +2763,7 @@ __device__ __noinline__ bool adj_creep(const Ctx &c, int b, int dir, v3t<D8> S, 
         D8 sb, cb;
         SinCos(F.bs, &sb, &cb);
         g.amp = Sqrt(a * sb / g.dperp) / Sqrt(g.sq) / g.sp;
+        if (enc & 1) g.amp = -g.amp;             // the (-1) of an odd number of extra turns
     } else {
         D8 ds_ = F.sps, dp_ = F.sqp;
         D8 dz = P.z - S.z;
@@ -2868,7 +2884,7 @@ __global__ void __launch_bounds__(128) k_adjoint(DevScene S, const float *__rest
                     else if (type == PT_R2) adj_planar(c, 2, id1, id2, Sd, Pd, fq, acc);
                     else if (type == PT_RB) { adj_rb(c, id1, Sd, Pd, fq, acc); body = id1; }
                     else if (type == PT_CP || type == PT_CM) {
-                        if (adj_creep(c, id1, type == PT_CM, Sd, Pd, fq, S.enable, acc)) body = id1;
+                        if (adj_creep(c, id1, type == PT_CM, id2, Sd, Pd, fq, S.enable, acc)) body = id1;
                     }
                 }
                 if (body >= 0)

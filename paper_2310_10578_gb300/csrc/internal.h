@@ -82,6 +82,7 @@ struct DevScene {
     float band_len;            // FP32 decision band (m)
     int max_order;
     unsigned enable;
+    int max_enc;               // extra encirclements of the creeping rays
 };
 
 // One frame of an evaluation: its curved bodies, frequencies and receivers
@@ -104,7 +105,7 @@ struct FrameDev {
 
 // Device counters of one evaluation: [0] candidates decided in FP64, [1 + i]
 // the work queue of launch i.  Zeroed by the caller before launch_eval.
-constexpr int CTR_QUEUES = 64;
+constexpr int CTR_QUEUES = 128;
 constexpr int CTR_N = 1 + CTR_QUEUES;
 
 // Evaluate (codes == nullptr), list paths (e_out == nullptr: canonical

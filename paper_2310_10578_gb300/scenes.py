@@ -45,6 +45,7 @@ class Scene:
         self.max_order = int(max_order)
         # per face (dielectric flag, eps', eps''), eps_r = eps' - j eps''; None: every face PEC
         self.face_eps = None if face_eps is None else np.asarray(face_eps, dtype=np.float32).reshape(-1, 3)
+        self.max_enc = 0          # extra encirclements of the creeping rays
 
     @property
     def n_rx(self):
@@ -55,8 +56,10 @@ class Scene:
         return np.ascontiguousarray(self.rx.T)
 
     def subset(self, idx, name=None):
-        return Scene(self.tri, self.tri_face, self.bodies, self.tx, self.pol, self.freqs,
-                     self.rx[idx], name or self.name + "[sub]", self.max_order, self.face_eps)
+        sub = Scene(self.tri, self.tri_face, self.bodies, self.tx, self.pol, self.freqs,
+                    self.rx[idx], name or self.name + "[sub]", self.max_order, self.face_eps)
+        sub.max_enc = self.max_enc
+        return sub
 
 
 def box_triangles(lx, ly, lz):

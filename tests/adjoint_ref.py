@@ -25,7 +25,8 @@ def pcode(t, a, b):
 
 
 def _scene64(sc, bodies=None, tx=None, freqs=None, rx=None):
-    return SimpleNamespace(tri=np.asarray(sc.tri, dtype=np.float64), tri_face=sc.tri_face,
+    return SimpleNamespace(max_enc=getattr(sc, "max_enc", 0), tri=np.asarray(sc.tri, dtype=np.float64),
+                           tri_face=sc.tri_face,
                            bodies=np.asarray(sc.bodies if bodies is None else bodies, dtype=np.float64).reshape(-1, 6),
                            tx=np.asarray(sc.tx if tx is None else tx, dtype=np.float64),
                            pol=np.asarray(sc.pol, dtype=np.float64),
@@ -73,7 +74,7 @@ def vjp(sc, codes, g, bodies=(), h=1e-5, df=1e3, cap=256, tx=True, freqs=True):
                     for c in codes[r]:
                         if (c >> 56) not in BODY_TYPES or ((c >> 28) & 0xFFFFFFF) != b:
                             continue
-                        key = pcode(c >> 56, 0, 0)
+                        key = pcode(c >> 56, 0, c & 0xFFFFFFF)     # body 0 of the one-body scene; turns kept
                         if key not in fs[0][i] or key not in fs[1][i]:
                             out["skipped"] += 1
                             out["skipped_paths"].append(("body %d param %d" % (b, k), r, c))

@@ -48,7 +48,7 @@ def _close(got, ref, absum, what):
 def _forward(creep, sc, cap=256):
     S = creep.Scene.from_scene(sc)
     rx = torch.tensor(sc.rx_soa(), device="cuda")
-    opts = creep.options(max_order=sc.max_order)
+    opts = creep.options(max_order=sc.max_order, max_encirclements=getattr(sc, "max_enc", 0))
     E = S.evaluate(rx, opts=opts)
     codes, counts, _ = S.paths(rx, cap=cap, opts=opts)
     torch.cuda.synchronize()
@@ -58,8 +58,16 @@ def _forward(creep, sc, cap=256):
     return S, rx, opts, E, codes, counts, lists
 
 
-def _check(creep, sc, bodies, seed, cap=256, tx=True, freqs=True):
+def _check(creep, sc, bodies, seed, cap=256, tx=True, freqs=True, keep=None):
     S, rx, opts, E, codes, counts, lists = _forward(creep, sc, cap)
+    if keep is not None:
+        # the gradient through the listed paths that pass keep(code) only
+        lists = [[c for c in cs if keep(c)] for cs in lists]
+        cd = np.zeros((sc.n_rx, cap), dtype=np.uint64)
+        for r, cs in enumerate(lists):
+            cd[r, :len(cs)] = cs
+        codes = torch.tensor(cd.view(np.int64), device="cuda").view(codes.dtype)
+        counts = torch.tensor([len(cs) for cs in lists], dtype=counts.dtype, device="cuda")
     rng = np.random.default_rng(seed)
     g = rng.standard_normal((len(sc.freqs), 3, sc.n_rx, 2)).astype(np.float32)
     gb, gt, gf = S.backward(rx, codes, counts, torch.tensor(g, device="cuda"), opts=opts)
@@ -95,6 +103,22 @@ def test_adjoint_sphere(creep, oracle_mod):
     sc.rx[:, 2] = 0.3                                       # off the plane of the source: a 3-D frame
     n_checked, gb = _check(creep, sc, bodies=[0], seed=2)
     assert n_checked == 4                                   # x, y, z and radius all move the field
+
+
+def test_adjoint_extra_turns(creep, oracle_mod):
+    """Creeping rays with one or two extra turns round a sphere (off the
+    source's plane) and round the room's cylinders: the gradient through
+    those paths alone."""
+    sc = scenes.sphere_ring(n_rx=96, freq=2.4e9)
+    sc.rx[:, 2] = 0.3
+    sc.max_enc = 2
+    extra = lambda c: (c >> 56) in (4, 5) and (c & 0xFFFFFFF) > 0
+    n_checked, _ = _check(creep, sc, bodies=[0], seed=5, keep=extra)
+    assert n_checked == 4
+    sc = _jitter(scenes.room(n_cyl=12, nx=24, ny=20, freqs=(2.4e9,), seed=7), 11)
+    sc.max_enc = 1
+    n_checked, _ = _check(creep, sc, bodies=range(12), seed=6, keep=extra)
+    assert n_checked >= 8
 
 
 def test_adjoint_200_cylinders(creep, oracle_mod):

@@ -299,3 +299,26 @@ def test_alu_peaks(creep):
     derived = p.multi_processor_count * 128 * 2 * clock_ghz / 1e3          # TFLOP/s
     assert 0.5 * derived <= ffma <= 1.2 * derived, (ffma, derived)
     assert mufu >= p.multi_processor_count * 8 * clock_ghz * 0.5, mufu      # Gop/s
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_extra_turns(creep, oracle_mod, precision):
+    """Creeping rays with up to two extra turns round each body: the path
+    lists bit for bit (CP / CM, body, turns), the fields within the bound;
+    a sphere (both polarisations' shadow fields) and the room's cylinders,
+    where the heights decide which turns stay on the body."""
+    prec = creep.RT_PREC_FP64 if precision == "fp64" else creep.RT_PREC_FP32
+    for sc in (scenes.sphere_ring(n_rx=1024, pol=(0, 1.0, 0)), scenes.room(n_cyl=20, nx=61, ny=47, seed=8)):
+        sc.max_enc = 2
+        opts = creep.options(max_order=sc.max_order, precision=prec, max_encirclements=2)
+        S, Eg, codes, counts, fl, _ = _run(creep, sc, opts=opts)
+        ref = oracle_mod.evaluate(sc)
+        compare_paths(codes, counts, ref)
+        _flags_equal(fl, ref)
+        compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs)
+        turns = {int(c) & 0xFFFFFFF for cs in ref.paths for c in cs if (int(c) >> 56) in (4, 5)}
+        assert turns == {0, 1, 2}
+    with pytest.raises(creep.CreepError) as e:
+        S.evaluate(torch.zeros((3, 4), dtype=torch.float32, device="cuda"),
+                   opts=creep.options(max_encirclements=5))
+    assert e.value.code == creep.RT_ERR_ARG
