@@ -17,7 +17,10 @@
  *         (Eq. 3 with the Fock-uniform R and the curved-surface caustic
  *         distances),
  *   E^d   the first creeping ray in each direction around each body (Eq. 4),
- *         with T from the off-surface UTD of the references the paper cites.
+ *         with T from the off-surface UTD of the references the paper cites,
+ *         optionally with extra full turns round the body, and optionally
+ *         fed by one planar reflection (the creeping rays of the source's
+ *         image in a face, the wall->creeping paths).
  * The U's are the visibility bits of the straight sub-segments (Eqs. 1-2).
  *
  * Everything is plain double arithmetic in the order the formulas are written;
@@ -39,11 +42,11 @@ typedef double complex cplx;
 #define TWO_PI (2.0 * M_PI)
 
 /* path type codes; a path is (type << 56) | (id1 << 28) | id2 */
-enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5 };
+enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5, PT_WCP = 6, PT_WCM = 7 };
 /* receiver flags */
 enum { FL_INSIDE = 1u, FL_CAUSTIC = 2u, FL_OVERFLOW = 8u };
 /* enable mask */
-enum { EN_LOS = 1, EN_PLANAR = 2, EN_BODYREFL = 4, EN_CREEP_SOFT = 8, EN_CREEP_HARD = 16 };
+enum { EN_LOS = 1, EN_PLANAR = 2, EN_BODYREFL = 4, EN_CREEP_SOFT = 8, EN_CREEP_HARD = 16, EN_WALL_CREEP = 32 };
 
 /* -------------------------------------------------------------- vectors */
 typedef struct { double x, y, z; } v3;
@@ -682,12 +685,10 @@ static void add_body_reflection(const scene *s, const refl_geom *G, v3 P, rx_sta
  *   E^d = E^i(Q1) . [b1 b2 T_s + n1 n2 T_h] sqrt(deta1/deta2) sqrt(rho_d/(s(rho_d+s))) e^{-jks}
  *   T_{s,h} = -sqrt(m1 m2) sqrt(2/k) [P_{s,h}(xi) + (c/xi)(1 - F(X))] e^{-jkt},
  *   xi = m t / rho_g, X = k L xi^2/(2 m1 m2), L = s' s/(s'+s). */
-static void add_creeping(const scene *s, const creep_geom *G, v3 P, rx_state *st) {
-    v3 S = s->tx;
+static void add_creeping_from(const scene *s, const creep_geom *G, v3 S, c3 e0, v3 P, rx_state *st) {
     v3 t1 = unit(sub(G->Q1, S)), t2 = unit(sub(P, G->Q2));
     v3 b1 = cross(t1, G->n1), b2 = cross(t2, G->n2);
-    v3 e0 = source_pol(s, t1);
-    double Es = dot(e0, b1), Eh = dot(e0, G->n1);
+    cplx Es = c3_dotr(e0, b1), Eh = c3_dotr(e0, G->n1);
     double L = G->sp * G->sq / (G->sp + G->sq);
     cplx caus = G->caustic_j ? I : 1.0;
     /* a sphere's ray crosses the source axis twice per extra encirclement:
@@ -708,6 +709,11 @@ static void add_creeping(const scene *s, const creep_geom *G, v3 P, rx_state *st
         c3 Ed = c3_add(rscl(b2, Ts * Es * ph), rscl(G->n2, Th * Eh * ph));
         accum(st, f, Ed);
     }
+}
+/* the creeping ray of the source itself: its polarisation along t1 */
+static void add_creeping(const scene *s, const creep_geom *G, v3 P, rx_state *st) {
+    v3 e0 = source_pol(s, unit(sub(G->Q1, s->tx)));
+    add_creeping_from(s, G, s->tx, CV(e0.x, e0.y, e0.z), P, st);
 }
 
 static void body_paths(const scene *s, int b, v3 P, rx_state *st) {
@@ -740,6 +746,56 @@ static void body_paths(const scene *s, int b, v3 P, rx_state *st) {
             if (!(G.dperp_P > 0.0)) continue;   /* exactly on the axis: no finite ray field */
         }
         add_creeping(s, &G, P, st);
+    }
+}
+
+/* Wall -> creeping paths: S -> Qw (face f) -> Q1 -> surface ray -> Q2 -> P.
+ * By the image method the reflected wave is the wave of the source's mirror
+ * image Sf in the plane of face f, so the creeping ray is the one of Sf
+ * (same geometry, spreading and length |Sf - Q1| = |S - Qw| + |Qw - Q1|)
+ * with, at Q1, the source's polarisation reflected at Qw (reflect_at).
+ * Valid iff Sf lies outside the body (a cylinder: its axis distance > a),
+ * Q1 lies strictly on the source's side of the plane, Qw (where Sf -> Q1
+ * crosses the plane) lies in face f, S -> Qw is visible (face f's triangles
+ * not tested), Qw -> Q1 is visible (face f and body b not tested), and
+ * Q2 -> P is visible (body b not tested).  Listed as (WCP or WCM, b,
+ * 16 f + turns). */
+static void wall_creep_paths(const scene *s, int b, v3 P, rx_state *st) {
+    const body *B = &s->bodies[b];
+    v3 S = s->tx;
+    for (int f = 0; f < s->n_face; ++f) {
+        const face *F = &s->faces[f];
+        double dS = dot(F->n, S) - F->d;
+        v3 Sf = mirror_point(S, F);
+        v3 w = sub(Sf, B->c);
+        if (B->type != 0) w.z = 0.0;
+        if (!(norm(w) > B->a)) continue;
+        for (int turns = 0; turns <= s->max_enc; ++turns)
+        for (int dir = 0; dir < 2; ++dir) {
+            creep_geom G;
+            st->ct.creep_geom++;
+            int ok = (B->type == 0) ? sphere_creeping(B, Sf, P, dir, turns, &G)
+                                    : cylinder_creeping(B, Sf, P, dir, turns, &G);
+            if (!ok) continue;
+            double dQ = dot(F->n, G.Q1) - F->d;
+            if (!(dS * dQ > 0.0)) continue;
+            double dI = dot(F->n, Sf) - F->d;
+            v3 Qw = add(Sf, scl(sub(G.Q1, Sf), dI / (dI - dQ)));
+            if (!point_in_face(s, f, Qw, &st->ct)) continue;
+            if (!visible(s, S, Qw, f, -1, -1, &st->ct)) continue;
+            if (!visible(s, Qw, G.Q1, f, -1, b, &st->ct)) continue;
+            if (!visible(s, G.Q2, P, -1, -1, b, &st->ct)) continue;
+            add_path(st, pcode(dir == 0 ? PT_WCP : PT_WCM, b, 16 * f + turns));
+            if (B->type == 0) {
+                for (int k = 0; k < s->n_f; ++k)
+                    if (kwave(s->freq[k]) * G.dperp_P < M_PI) st->flags |= FL_CAUSTIC;
+                if (!(G.dperp_P > 0.0)) continue;
+            }
+            v3 si = unit(sub(Qw, S)), sr = unit(sub(G.Q1, Qw));
+            v3 e0 = source_pol(s, si);
+            c3 Er = reflect_at(F, CV(e0.x, e0.y, e0.z), si, sr);
+            add_creeping_from(s, &G, Sf, Er, P, st);
+        }
     }
 }
 
@@ -852,6 +908,8 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
         } else {
             planar_paths(&s, P, &st);
             for (int b = 0; b < n_body; ++b) body_paths(&s, b, P, &st);
+            if (s.enable & EN_WALL_CREEP)
+                for (int b = 0; b < n_body; ++b) wall_creep_paths(&s, b, P, &st);
         }
         for (int f = 0; f < n_f; ++f) {
             size_t base = ((size_t)f * 3) * n_rx + r;

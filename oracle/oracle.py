@@ -21,10 +21,11 @@ LIB = os.path.join(BUILD, "liboracle.so")
 # enable mask (same meaning as the C enum)
 EN_LOS, EN_PLANAR, EN_BODYREFL, EN_CREEP_SOFT, EN_CREEP_HARD = 1, 2, 4, 8, 16
 EN_ALL = 31
+EN_WALL_CREEP = 32          # wall -> creeping paths (also switched on by scene.wall_creep)
 # receiver flags
 FL_INSIDE, FL_CAUSTIC, FL_OVERFLOW = 1, 2, 8
 # path types
-PT_LOS, PT_R1, PT_R2, PT_RB, PT_CP, PT_CM = range(6)
+PT_LOS, PT_R1, PT_R2, PT_RB, PT_CP, PT_CM, PT_WCP, PT_WCM = range(8)
 COUNTER_NAMES = ("seg_tri", "seg_body", "inside_tri", "image_cand", "body_refl", "creep_geom",
                  "paths", "fock_evals")
 
@@ -128,7 +129,7 @@ def evaluate(scene, rx=None, enable=EN_ALL, cap=256, threads=0, want_paths=True,
     t0 = time.perf_counter()
     lib.oracle_eval(_p(tri), _p(tf), scene.tri.shape[0], _p(bodies), scene.bodies.shape[0],
                     _p(tx), _p(pol), _p(fr), n_f, _p(rx64), n_rx, *_fock_args(),
-                    scene.max_order, enable, _p(E),
+                    scene.max_order, enable | (EN_WALL_CREEP if getattr(scene, "wall_creep", False) else 0), _p(E),
                     _p(codes) if want_paths else None, _p(counts), cap if want_paths else 0,
                     _p(flags), _p(ctr), threads, _p(sabs), _p(pE) if pE is not None else None,
                     _p(fe) if fe is not None else None, int(getattr(scene, "max_enc", 0)))

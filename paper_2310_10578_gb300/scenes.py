@@ -46,6 +46,7 @@ class Scene:
         # per face (dielectric flag, eps', eps''), eps_r = eps' - j eps''; None: every face PEC
         self.face_eps = None if face_eps is None else np.asarray(face_eps, dtype=np.float32).reshape(-1, 3)
         self.max_enc = 0          # extra encirclements of the creeping rays
+        self.wall_creep = False   # creeping rays fed by one planar reflection
 
     @property
     def n_rx(self):
@@ -59,6 +60,7 @@ class Scene:
         sub = Scene(self.tri, self.tri_face, self.bodies, self.tx, self.pol, self.freqs,
                     self.rx[idx], name or self.name + "[sub]", self.max_order, self.face_eps)
         sub.max_enc = self.max_enc
+        sub.wall_creep = self.wall_creep
         return sub
 
 

@@ -17,7 +17,7 @@ import numpy as np
 from oracle import oracle
 
 EN_BODIES = oracle.EN_BODYREFL | oracle.EN_CREEP_SOFT | oracle.EN_CREEP_HARD
-BODY_TYPES = (oracle.PT_RB, oracle.PT_CP, oracle.PT_CM)
+BODY_TYPES = (oracle.PT_RB, oracle.PT_CP, oracle.PT_CM, oracle.PT_WCP, oracle.PT_WCM)
 
 
 def pcode(t, a, b):
@@ -25,7 +25,7 @@ def pcode(t, a, b):
 
 
 def _scene64(sc, bodies=None, tx=None, freqs=None, rx=None):
-    return SimpleNamespace(max_enc=getattr(sc, "max_enc", 0), tri=np.asarray(sc.tri, dtype=np.float64),
+    return SimpleNamespace(max_enc=getattr(sc, "max_enc", 0), wall_creep=getattr(sc, "wall_creep", False), tri=np.asarray(sc.tri, dtype=np.float64),
                            tri_face=sc.tri_face,
                            bodies=np.asarray(sc.bodies if bodies is None else bodies, dtype=np.float64).reshape(-1, 6),
                            tx=np.asarray(sc.tx if tx is None else tx, dtype=np.float64),
