@@ -59,6 +59,17 @@ extern "C" {
 #define RT_EN_CREEP_SOFT 8u
 #define RT_EN_CREEP_HARD 16u
 #define RT_EN_ALL 31u
+/* Creeping rays fed by one planar reflection: S -> Qw (face f) -> Q1 ->
+ * surface ray -> Q2 -> P, the creeping rays of the source's mirror image in
+ * face f with the source's polarisation reflected at Qw (PEC image mirror or
+ * the face's Fresnel coefficients).  Not in RT_EN_ALL; single scenes only
+ * (rt_batch_* reject it with RT_ERR_ARG).  A path exists iff the image lies
+ * outside the body (a cylinder: off its footprint), the image's creeping ray
+ * exists (with any extra turns), Q1 lies strictly on the source's side of
+ * face f's plane, Qw (where image -> Q1 crosses the plane) lies in face f,
+ * and S -> Qw (face f not tested), Qw -> Q1 (face f and the body not
+ * tested) and Q2 -> P (the body not tested) are unobstructed. */
+#define RT_EN_WALL_CREEP 32u
 
 /* arithmetic of the geometry and field math (rt_options.precision) */
 #define RT_PREC_FP32 0     /* FP32 bulk, double-float path lengths, FP64 re-evaluation of uncertain decisions */
@@ -77,6 +88,8 @@ extern "C" {
 #define RT_PATH_RB 3       /* id1 = body: GO reflection off the body */
 #define RT_PATH_CP 4       /* id1 = body, id2 = extra turns: creeping ray, short way round */
 #define RT_PATH_CM 5       /* id1 = body, id2 = extra turns: creeping ray, long way round */
+#define RT_PATH_WCP 6      /* id1 = body, id2 = 16 face + extra turns: reflection at face, then CP */
+#define RT_PATH_WCM 7      /* id1 = body, id2 = 16 face + extra turns: reflection at face, then CM */
 
 /* library limits */
 #define RT_MAX_FACES 64

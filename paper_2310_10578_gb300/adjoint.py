@@ -36,8 +36,10 @@ class Static:
     @classmethod
     def from_scene(cls, sc, rx_soa, opts=None, cap=256):
         return cls(sc.tri, sc.tri_face, sc.bodies[:, 0], sc.bodies[:, 5], sc.pol, rx_soa,
-                   opts if opts is not None else creep.options(max_order=sc.max_order,
-                                                                 max_encirclements=getattr(sc, "max_enc", 0)), cap,
+                   opts if opts is not None else creep.options(
+                       max_order=sc.max_order, max_encirclements=getattr(sc, "max_enc", 0),
+                       enable=creep.RT_EN_ALL | (creep.RT_EN_WALL_CREEP if getattr(sc, "wall_creep", False) else 0)),
+                   cap,
                    getattr(sc, "face_eps", None))
 
     def scene(self, body_params, tx, freqs):

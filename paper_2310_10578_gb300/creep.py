@@ -16,9 +16,10 @@ RT_OK, RT_ERR_ARG, RT_ERR_GEOM, RT_ERR_CUDA, RT_ERR_TIMEOUT, RT_ERR_OVERFLOW, RT
 RT_BODY_SPHERE, RT_BODY_CYLINDER = 0, 1
 RT_EN_LOS, RT_EN_PLANAR, RT_EN_BODYREFL, RT_EN_CREEP_SOFT, RT_EN_CREEP_HARD = 1, 2, 4, 8, 16
 RT_EN_ALL = 31
+RT_EN_WALL_CREEP = 32        # creeping rays fed by one planar reflection (not in RT_EN_ALL)
 RT_PREC_FP32, RT_PREC_FP64 = 0, 1
 RT_FLAG_INSIDE, RT_FLAG_CAUSTIC, RT_FLAG_ESCALATED, RT_FLAG_OVERFLOW = 1, 2, 4, 8
-RT_PATH_LOS, RT_PATH_R1, RT_PATH_R2, RT_PATH_RB, RT_PATH_CP, RT_PATH_CM = range(6)
+RT_PATH_LOS, RT_PATH_R1, RT_PATH_R2, RT_PATH_RB, RT_PATH_CP, RT_PATH_CM, RT_PATH_WCP, RT_PATH_WCM = range(8)
 FOCK_NRES = 8
 
 EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "rt_evaluate",

@@ -125,6 +125,7 @@ struct rt_scene {
     FreqC *d_fqc = nullptr;            // [RT_MAX_FREQS / NFC] per-chunk frequency constants
     float4 *d_img = nullptr;            // source images, see DevScene::img
     float4 *d_txb = nullptr;            // source-side body frames, see DevScene::txb
+    float4 *d_txw = nullptr;            // the same for each face's source image, see DevScene::txw
     float4 *d_face_mat = nullptr;       // face materials, see DevScene::face_mat
     bool any_dielectric = false;
     unsigned long long *d_esc = nullptr;   // [CTR_N]: FP64-decided candidates, then one work queue per launch
@@ -171,6 +172,7 @@ static void free_scene(rt_scene *s) {
     cudaFree(s->d_tri); cudaFree(s->d_aux); cudaFree(s->d_face32); cudaFree(s->d_body);
     cudaFree(s->d_face64); cudaFree(s->d_face_rng); cudaFree(s->d_face_tris); cudaFree(s->d_freq); cudaFree(s->d_fqc);
     cudaFree(s->d_esc); cudaFree(s->io_rx); cudaFree(s->io_e); cudaFree(s->io_fl); cudaFree(s->d_img); cudaFree(s->d_txb);
+    cudaFree(s->d_txw);
     cudaFree(s->d_face_mat);
 }
 
@@ -401,6 +403,7 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
     CKS(cudaMalloc(&s->d_esc, sizeof(unsigned long long) * CTR_N));
     CKS(cudaMalloc(&s->d_img, sizeof(float4) * 2 * (nfc + nfc * nfc)));
     CKS(cudaMalloc(&s->d_txb, sizeof(float4) * 2 * nbd));
+    CKS(cudaMalloc(&s->d_txw, sizeof(float4) * 2 * nbd * nfc));
     if (n_tri > 0) {
         CKS(cudaMemcpy(s->d_tri, htri.data(), sizeof(float4) * 3 * n_tri, cudaMemcpyHostToDevice));
         CKS(cudaMemcpy(s->d_aux, haux.data(), sizeof(float4) * 3 * n_tri, cudaMemcpyHostToDevice));
@@ -469,6 +472,16 @@ int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
     std::vector<float4> txb(2 * (size_t)(s->n_body > 0 ? s->n_body : 1));
     prep_txb(p, s->bodies.data(), s->n_body, txb.data());
     if (s->n_body > 0) CK(cudaMemcpy(s->d_txb, txb.data(), sizeof(float4) * 2 * s->n_body, cudaMemcpyHostToDevice));
+    // and per face, the same for the source's mirror image (wall -> creeping)
+    if (s->n_body > 0 && nf > 0) {
+        std::vector<float4> txw(2 * (size_t)s->n_body * nf);
+        for (int f = 0; f < nf; ++f) {
+            double S1[3];
+            mirror(p, f, S1);
+            prep_txb(S1, s->bodies.data(), s->n_body, txw.data() + 2 * (size_t)f * s->n_body);
+        }
+        CK(cudaMemcpy(s->d_txw, txw.data(), sizeof(float4) * txw.size(), cudaMemcpyHostToDevice));
+    }
     s->tx_set = true;
     ++s->tx_version;
     return RT_OK;
@@ -518,7 +531,7 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, 
         return fail(RT_ERR_ARG, "max_encirclements %d not in [0, 4]", o.max_encirclements);
     if (o.max_order < 0 || o.max_order > 2) return fail(RT_ERR_ARG, "max_order %d not in [0, 2]", o.max_order);
     if (o.precision != RT_PREC_FP32 && o.precision != RT_PREC_FP64) return fail(RT_ERR_ARG, "bad precision %d", o.precision);
-    if (o.enable & ~RT_EN_ALL) return fail(RT_ERR_ARG, "bad enable mask 0x%x", o.enable);
+    if (o.enable & ~(RT_EN_ALL | RT_EN_WALL_CREEP)) return fail(RT_ERR_ARG, "bad enable mask 0x%x", o.enable);
     if (!s->tx_set || (need_freqs && !s->f_set)) return fail(RT_ERR_STATE, "transmitter or frequencies not set");
     memset(&D, 0, sizeof(D));
     D.n_tri = s->n_tri; D.n_face = s->n_face; D.n_body = s->n_body; D.n_f = (int)s->freqs.size();
@@ -532,6 +545,7 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, 
     D.fqc = s->d_fqc;
     D.img = s->d_img;
     D.txb = s->d_txb;
+    D.txw = s->d_txw;
     D.face_mat = s->any_dielectric ? s->d_face_mat : nullptr;
     memcpy(D.tx, s->tx, sizeof(D.tx));
     memcpy(D.pol, s->pol, sizeof(D.pol));
@@ -716,7 +730,9 @@ static int batch_queue(rt_batch *b, const float *rx_soa, float *e_out, uint32_t 
     int rc = make_dev(s, opt, D, &prec, false);
     if (rc != RT_OK) return rc;
     if (b->n_tiles > 0 && (!rx_soa || !e_out)) return fail(RT_ERR_ARG, "rt_batch: NULL buffer");
+    if (D.enable & RT_EN_WALL_CREEP) return fail(RT_ERR_ARG, "rt_batch: wall -> creeping paths are for single scenes");
     D.n_body = b->max_body;
+    D.txw = nullptr;
     D.n_f = b->n_f;
     D.body = b->d_body; D.txb = b->d_txb; D.fqc = b->d_fqc;
     D.freq = nullptr;

@@ -28,7 +28,7 @@ namespace creep {
 
 #define EPS_TRIM 1e-6
 enum { D_NO = 0, D_YES = 1, D_UNSURE = 2 };
-enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5 };
+enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5, PT_WCP = 6, PT_WCM = 7 };
 
 constexpr int BLOCK = 128;
 constexpr int SMEM_TRI_MAX = 256;
@@ -66,6 +66,7 @@ struct Ctx {
     const double *weid64;
     const float4 *img;           // source images (double-float), see DevScene
     const float4 *txb;           // [n_body][2] source-side body frame, see DevScene
+    const float4 *txw;           // [n_face][n_body][2] the same for each face's source image (or nullptr)
     const float4 *face_mat;      // face materials, see DevScene (nullptr: all PEC)
     int enc;                     // this launch's creeping rays: extra full turns round the body
     // occluder masks (FP32 body kernels): occ_w words per body; word w of
@@ -546,8 +547,9 @@ __device__ void cyl_frame(v3t<T> S, v3t<T> P, T cx, T cy, T a, Frame<T> &F, T ba
 // rays.  FP32: the source-only quantities (u, |S - c|, beta_s, s' or d_s, and
 // whether the source is over a cylinder's footprint) come precomputed in FP64
 // per transmitter (Ctx::txb); FP64: computed here as the definition does.
-__device__ void body_frame(const Ctx &c, int b, v3t<float> S, v3t<float> P, float band, Frame<float> &F) {
-    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1], t0 = c.txb[2 * b], t1 = c.txb[2 * b + 1];
+__device__ __forceinline__ void body_frame_tb(const Ctx &c, const float4 *tb, int b, v3t<float> S, v3t<float> P,
+                                              float band, Frame<float> &F) {
+    float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1], t0 = tb[2 * b], t1 = tb[2 * b + 1];
     float a = q0.w;
     F.dec = D_YES;
     F.axis_ok = true;
@@ -594,6 +596,9 @@ __device__ void body_frame(const Ctx &c, int b, v3t<float> S, v3t<float> P, floa
     F.sqp = F.dpq.hi;
     F.sps = F.dsq.hi;
     F.bp = atan2f(F.sqp, a);
+}
+__device__ void body_frame(const Ctx &c, int b, v3t<float> S, v3t<float> P, float band, Frame<float> &F) {
+    body_frame_tb(c, c.txb, b, S, P, band, F);
 }
 __device__ void body_frame(const Ctx &c, int b, v3t<dx> S, v3t<dx> P, dx band, Frame<dx> &F) {
     float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
@@ -877,8 +882,9 @@ __device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Fr
     return acc;
 }
 
-// creeping candidate, dir 0 short way, 1 long way
-template <typename T>
+// creeping candidate, dir 0 short way, 1 long way (SRC_LEG false: the leg
+// from the source S to Q1 is the caller's, e.g. S is a source image)
+template <typename T, bool SRC_LEG = true>
 __device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T band, const Frame<T> &F, Geo<T> &g,
                           const uint32_t *occ_rx = nullptr) {
     float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
@@ -940,8 +946,37 @@ __device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T ba
         g.dperp = T(0);
         g.amp = T(1) / Sqrt(g.sp * g.sq * (g.sp + g.t + g.sq));
     }
-    if (!conj(acc, vis_to_dec(blocked_leg(c, S, g.Q1, b, band, occ_of(c, c.occ_src, b))))) return D_NO;
+    if constexpr (SRC_LEG) {
+        if (!conj(acc, vis_to_dec(blocked_leg(c, S, g.Q1, b, band, occ_of(c, c.occ_src, b))))) return D_NO;
+    }
     if (!conj(acc, vis_to_dec(blocked_leg(c, g.Q2, P, b, band, occ_of(c, occ_rx, b))))) return D_NO;
+    return acc;
+}
+
+// The planar leg of a wall -> creeping path: the source S reflects at face f
+// towards Q1, the attachment point of the creeping ray of S's image Sw.
+// Q1 strictly on S's side of the plane; Qw (where Sw -> Q1 crosses it) in
+// the face; S -> Qw clear (face f not tested), Qw -> Q1 clear (face f and
+// body b not tested).
+template <typename T>
+__device__ __forceinline__ v3t<T> wall_point(const Ctx &c, int f, v3t<T> Sw, v3t<T> Q1, T *dQ) {
+    v3t<T> n; T d;
+    face_plane<T>(c, f, &n, &d);
+    T dI = dot3(n, Sw) - d;
+    *dQ = dot3(n, Q1) - d;
+    return Sw + (Q1 - Sw) * (dI / (dI - *dQ));
+}
+template <typename T>
+__device__ int wall_legs(const Ctx &c, int f, int b, v3t<T> S, v3t<T> Sw, v3t<T> Q1, T band) {
+    v3t<T> n; T d;
+    face_plane<T>(c, f, &n, &d);
+    T dQ;
+    const v3t<T> Qw = wall_point(c, f, Sw, Q1, &dQ);
+    int acc = D_YES;
+    if (!conj(acc, side_dec(dot3(n, S) - d, dQ, band, true))) return D_NO;
+    if (!conj(acc, in_face(c, f, Qw, band))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, S, Qw, f, -1, -1, band)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, Qw, Q1, f, -1, b, band)))) return D_NO;
     return acc;
 }
 
@@ -1412,6 +1447,40 @@ __device__ void field_creep(const Ctx &c, ACC &acc, const FreqC &fq, v3t<T> S, v
     }
 }
 
+// wall -> creeping path: the creeping ray of the source's image Sw in face f,
+// with the source's polarisation reflected at Qw (complex for a dielectric
+// face) as the incident field at Q1
+template <typename T, typename L, bool F32FOCK = false, typename ACC = Acc<T>>
+__device__ void field_wcreep(const Ctx &c, ACC &acc, const FreqC &fq, int wf, v3t<T> S, v3t<T> Sw, v3t<T> P,
+                             const Geo<T> &g, L len, unsigned enable) {
+    T dQ;
+    const v3t<T> Qw = wall_point(c, wf, Sw, g.Q1, &dQ);
+    const v3t<T> si = unit3(Qw - S), t1 = unit3(g.Q1 - Sw), t2 = unit3(P - g.Q2);
+    const v3t<T> e0 = src_pol(c, si);
+    cpx<T> E[3] = {mkc<T>(e0.x, T(0)), mkc<T>(e0.y, T(0)), mkc<T>(e0.z, T(0))};
+    reflect_face(c, wf, E, si, t1);
+    const v3t<T> b1 = cross3(t1, g.n1), b2 = cross3(t2, g.n2);
+    cpx<T> Es = c3dot(E, b1), Eh = c3dot(E, g.n1);
+    if (!(enable & RT_EN_CREEP_SOFT)) Es = mkc<T>(T(0), T(0));
+    if (!(enable & RT_EN_CREEP_HARD)) Eh = mkc<T>(T(0), T(0));
+    T Lp = g.sp * g.sq / (g.sp + g.sq);
+    T rcb = Cbrt(g.rho_g);
+    T tr = g.t / g.rho_g;
+#pragma unroll 1
+    for (int f = 0; f < fq.nf; ++f) {
+        T k = kof(fq, f, T(0));
+        T m = khof(fq, f, T(0)) * rcb;
+        T xi = m * tr;
+        cpx<T> Bs, Bh;
+        fock_bracket<T, F32FOCK>(c, xi, Sqrt(k * Lp / (T(2) * m * m)), Bs, Bh);
+        T pre = -m * Sqrt(T(2) / k) * g.amp;
+        cpx<T> ph = phasor(fq, f, len) * pre;
+        if (g.caus) ph = mkc<T>(-ph.im, ph.re);          // x (+j)
+        cpx<T> as = Bs * ph * Es, ah = Bh * ph * Eh;
+        acc_put(acc, f, as * b2.x + ah * g.n2.x, as * b2.y + ah * g.n2.y, as * b2.z + ah * g.n2.z);
+    }
+}
+
 // ---- path records (FP32): the frequency-independent factors of one path's
 // field, written by the geometry pass and turned into fields, frequency by
 // frequency, by the field pass; the two passes are separate loops so that
@@ -1493,6 +1562,29 @@ __device__ __forceinline__ void creep_prep(const Ctx &c, float *r, v3t<float> S,
     if (signbit(g.amp)) { Es = -Es; Eh = -Eh; }  // (the record's amplitude sign is the caustic flag)
     rec_put(r, Es, Eh, b2, g.n2, g.caus ? -fabsf(g.amp) : fabsf(g.amp), -(g.sp * g.sq / (g.sp + g.sq)), cbrtf(g.rho_g),
             g.t / g.rho_g, len);
+}
+// wall -> creeping path (see field_wcreep): the real part of the reflected
+// polarisation in one record; an imaginary part (a dielectric face) in a
+// second one, its factor j taken by the record's caustic flag (j j = -1
+// where the ray already has one).  Returns the number of records written.
+__device__ __forceinline__ int wcreep_prep(const Ctx &c, float *r, int wf, v3t<float> S, v3t<float> Sw,
+                                           v3t<float> P, const Geo<float> &g, dfl len, unsigned enable) {
+    float dQ;
+    const v3t<float> Qw = wall_point(c, wf, Sw, g.Q1, &dQ);
+    const v3t<float> si = unit3(Qw - S), t1 = unit3(g.Q1 - Sw), t2 = unit3(P - g.Q2);
+    const v3t<float> e0 = src_pol(c, si);
+    cpx<float> E[3] = {mkc(e0.x, 0.0f), mkc(e0.y, 0.0f), mkc(e0.z, 0.0f)};
+    reflect_face(c, wf, E, si, t1);
+    const v3t<float> b1 = cross3(t1, g.n1), b2 = cross3(t2, g.n2);
+    const cpx<float> Es = (enable & RT_EN_CREEP_SOFT) ? c3dot(E, b1) : mkc(0.0f, 0.0f);
+    const cpx<float> Eh = (enable & RT_EN_CREEP_HARD) ? c3dot(E, g.n1) : mkc(0.0f, 0.0f);
+    const float sg = signbit(g.amp) ? -1.0f : 1.0f, A = fabsf(g.amp);
+    const float Lp = -(g.sp * g.sq / (g.sp + g.sq)), rcb = cbrtf(g.rho_g), tr = g.t / g.rho_g;
+    rec_put(r, sg * Es.re, sg * Eh.re, b2, g.n2, g.caus ? -A : A, Lp, rcb, tr, len);
+    if (!dielectric(c, wf)) return 1;
+    const float si2 = g.caus ? -sg : sg;
+    rec_put(r + REC_N * 32, si2 * Es.im, si2 * Eh.im, b2, g.n2, g.caus ? A : -A, Lp, rcb, tr, len);
+    return 2;
 }
 __device__ __forceinline__ void creep_apply(const Ctx &c, AccS<float> &acc, const FreqC &fq, const float *r) {
     const float Es = r[0], Eh = r[32], Lp = -r[288], rcb = r[320], tr = r[352];
@@ -1657,21 +1749,79 @@ __device__ __noinline__ int esc_creep(const Ctx &c, int b, int dir, v3t<float> P
     }
     return d;
 }
+// a source image outside body b (a cylinder: off its footprint), FP64
+__device__ __forceinline__ bool img_outside(const Ctx &c, int b, v3t<dx> X) {
+    const float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
+    const dx ex = X.x - dx((double)q0.x), ey = X.y - dx((double)q0.y);
+    const dx ez = (q1.y == 0.0f) ? X.z - dx((double)q0.z) : dx(0.0);
+    return Sqrt(ex * ex + ey * ey + ez * ez) > dx((double)q0.w);
+}
+// the source's image in face wf: FP32 (hi) and FP64 (hi + lo)
+__device__ __forceinline__ v3t<float> wall_img_f(const Ctx &c, int wf) {
+    const float4 h = c.img[2 * wf];
+    return mk3(h.x, h.y, h.z);
+}
+__device__ __forceinline__ v3t<dx> wall_img_d(const Ctx &c, int wf) {
+    const float4 h = c.img[2 * wf], l = c.img[2 * wf + 1];
+    return mk3<dx>(dx((double)h.x + (double)l.x), dx((double)h.y + (double)l.y), dx((double)h.z + (double)l.z));
+}
+// wall -> creeping candidate decided, its caustic flag taken, and (field)
+// evaluated in FP64, or its records written (rec)
+__device__ __noinline__ int esc_wcreep(const Ctx &c, int wf, int b, int dir, v3t<float> Pf, const FreqC &fq,
+                                       bool field, double half_lambda_max, unsigned enable, Contrib *out,
+                                       int *caustic, float *rec, int *n_rec) {
+    Geo<dx> g;
+    const v3t<dx> Sd = dxv(c.S), Pd = dxv(Pf), Sw = wall_img_d(c, wf);
+    *caustic = 0;
+    *n_rec = 0;
+    if (!img_outside(c, b, Sw)) return D_NO;
+    Frame<dx> F;
+    body_frame(c, b, Sw, Pd, dx(0.0), F);
+    int d = (F.dec == D_NO) ? D_NO : cand_creep<dx, false>(c, b, dir, Sw, Pd, dx(0.0), F, g);
+    if (d == D_YES) d = wall_legs<dx>(c, wf, b, Sd, Sw, g.Q1, dx(0.0));
+    if (d != D_YES) return d;
+    if (c.body[2 * b + 1].y == 0.0f) {
+        *caustic = half_lambda_max > g.dperp.v;
+        if (!(g.dperp > dx(0.0))) {                  // exactly on the axis: no finite ray field
+            if (field) {
+                for (int f = 0; f < NFC; ++f)
+                    for (int q = 0; q < 3; ++q) out->E[f][q] = mkc(0.0f, 0.0f);
+            }
+            return d;
+        }
+    }
+    if (rec) {
+        *n_rec = wcreep_prep(c, rec, wf, c.S, wall_img_f(c, wf), Pf, to_f(g), to_df(to_double(g.sp + g.t + g.sq)),
+                             enable);
+    } else if (field) {
+        Acc<dx> a;
+        acc_zero(a);
+        field_wcreep<dx, dx, true>(c, a, fq, wf, Sd, Sw, Pd, g, g.sp + g.t + g.sq, enable);
+        contrib_from(out, a);
+    }
+    return d;
+}
 
 // ------------------------------------------------------------------ kernel
 // Path classes; one launch evaluates the classes of its CLS mask, so that each
 // kernel carries only the code (and the live registers) of its classes.
 enum { CLS_PLANAR = 1,        // direct ray and planar image reflections
        CLS_BODYREFL = 2,      // GO reflection off each curved body
-       CLS_CREEP = 4 };       // creeping rays round each curved body
+       CLS_CREEP = 4,         // creeping rays round each curved body
+       CLS_WCREEP = 8 };      // creeping rays fed by a planar reflection (a work unit: face x body)
+constexpr int CLS_BODIES = CLS_BODYREFL | CLS_CREEP | CLS_WCREEP;
 // Block shape.  The body classes run one block of 12 warps per SM: three
 // tiles at a time, four warps per tile; a block barrier between the geometry
 // pass and the field pass keeps all warps of the SM in the same pass, so the
 // instruction cache holds one pass's code at a time.  The planar class, and
 // the FP64 path, run 4-warp blocks, several per SM.
-constexpr int blk_of(int cls, bool fp32) { return ((cls & (CLS_BODYREFL | CLS_CREEP)) && fp32) ? 384 : BLOCK; }
+constexpr int blk_of(int cls, bool fp32) { return ((cls & CLS_BODIES) && fp32) ? 384 : BLOCK; }
 constexpr int min_blocks(int cls, bool fp32) {
-    return ((cls & (CLS_BODYREFL | CLS_CREEP)) && fp32) ? 1 : (cls == CLS_PLANAR ? 4 : 3);
+    return ((cls & CLS_BODIES) && fp32) ? 1 : (cls == CLS_PLANAR ? 4 : 3);
+}
+// records per work unit of a body class (FP32 fields)
+constexpr int recs_per_unit(int cls) {
+    return ((cls & CLS_CREEP) ? 2 : 0) + ((cls & CLS_BODYREFL) ? 1 : 0) + ((cls & CLS_WCREEP) ? 4 : 0);
 }
 constexpr int WARPS_PER_TILE = 4;
 constexpr int MAX_CHUNKS = (RT_MAX_FREQS + NFC - 1) / NFC;
@@ -1682,7 +1832,7 @@ constexpr int OCC_MAX_BODIES = 256;    // occluder masks up to this many bodies 
 template <int CLS>
 __device__ __forceinline__ void apply_records(const Ctx &c, AccS<float> &acc, const FreqC &fq, const float *rec,
                                               int nrec) {
-    constexpr bool RB = (CLS & CLS_BODYREFL) != 0, CP = (CLS & CLS_CREEP) != 0;
+    constexpr bool RB = (CLS & CLS_BODYREFL) != 0, CP = (CLS & (CLS_CREEP | CLS_WCREEP)) != 0;
 #pragma unroll 1
     for (int j = 0; j < nrec; ++j) {
         const float *r = rec + j * REC_N * 32;
@@ -1717,7 +1867,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                                               const uint32_t *occ_rx, int part, int nparts,
                                               AccS<T> acc, float *rec, uint32_t &fl, unsigned &nesc, int &npath,
                                               int &nrec_out) {
-    constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
+    constexpr bool BODIES = (CLS & CLS_BODIES) != 0;
     const bool fp32 = sizeof(T) == 4;
     const T band = fp32 ? T(c.band) : T(0);
     // fqs[0]: the frequency chunk of the body classes' fields; the planar
@@ -1859,7 +2009,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
             // turns them into fields, frequency chunk by frequency chunk, after
             // a block barrier.  The body range is sized so that the records fit.
             constexpr bool RECS = (sizeof(T) == 4) && !PATHS;
-            constexpr int PER = ((CLS & CLS_CREEP) ? 2 : 0) + ((CLS & CLS_BODYREFL) ? 1 : 0);
+            constexpr int PER = recs_per_unit(CLS);
             int nrec = 0;
 #pragma unroll 1
             for (int b = b_begin + part; b < b_end; b += nparts) {
@@ -1871,6 +2021,64 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                         apply_records<CLS>(c, acc, fq, rec, nrec);
                         nrec = 0;
                     }
+                }
+                if constexpr (CLS == CLS_WCREEP) {
+                    // unit b: face wf, body bb; the creeping rays of the
+                    // source's image in face wf, fed by the reflection there
+                    if (!(enable & (RT_EN_CREEP_SOFT | RT_EN_CREEP_HARD))) continue;
+                    const int wf = b / c.n_body, bb = b - wf * c.n_body;
+                    const bool sphere = c.body[2 * bb + 1].y == 0.0f;
+                    Frame<T> F;
+                    v3t<T> Sw;
+                    if constexpr (sizeof(T) == 4) {
+                        Sw = wall_img_f(c, wf);
+                        body_frame_tb(c, c.txw + 2 * (size_t)wf * c.n_body, bb, Sw, P, band, F);
+                    } else {
+                        Sw = wall_img_d(c, wf);
+                        if (!img_outside(c, bb, Sw)) continue;
+                        body_frame(c, bb, Sw, P, band, F);
+                    }
+#pragma unroll 1
+                    for (int dir = 0; dir < 2; ++dir) {
+                        Geo<T> g;
+                        int d = cand_creep<T, false>(c, bb, dir, Sw, P, band, F, g);
+                        if (d == D_YES) d = wall_legs<T>(c, wf, bb, Sx, Sw, g.Q1, band);
+                        int cd = D_NO;
+                        if (d == D_YES && sphere) {
+                            if constexpr (sizeof(T) == 8) cd = (half_lambda_max > to_double(g.dperp)) ? D_YES : D_NO;
+                            else cd = decide((T)half_lambda_max - g.dperp, band, D_NO);
+                        }
+                        if constexpr (sizeof(T) == 4) {
+                            if (d == D_UNSURE || cd == D_UNSURE) {
+                                escalated();
+                                Contrib ct;
+                                int caus = 0, added = 0;
+                                const bool defer = RECS && !may_flush;
+                                d = esc_wcreep(c, wf, bb, dir, Pf, fq, !PATHS && !defer, half_lambda_max, enable, &ct,
+                                               &caus, defer ? rec + nrec * REC_N * 32 : nullptr, &added);
+                                if (d == D_YES) {
+                                    emit(dir == 0 ? PT_WCP : PT_WCM, bb, 16 * wf + c.enc);
+                                    if (caus) fl |= RT_FLAG_CAUSTIC;
+                                    if (defer) nrec += added;
+                                    else if (!PATHS) acc_add(acc, ct, nf);
+                                }
+                                continue;
+                            }
+                        }
+                        if (d != D_YES) continue;
+                        emit(dir == 0 ? PT_WCP : PT_WCM, bb, 16 * wf + c.enc);
+                        if (sphere) {
+                            if (cd == D_YES) fl |= RT_FLAG_CAUSTIC;
+                            if (!(g.dperp > T(0.0))) continue;        // exactly on the axis: no finite ray field
+                        }
+                        if constexpr (RECS) {
+                            nrec += wcreep_prep(c, rec + nrec * REC_N * 32, wf, Sx, Sw, P, g,
+                                                creep_len(c, bb, Sw, P, g, F), enable);
+                        } else if constexpr (!PATHS) {
+                            field_wcreep<T>(c, acc, fq, wf, Sx, Sw, P, g, creep_len(c, bb, Sw, P, g, F), enable);
+                        }
+                    }
+                    continue;
                 }
                 Frame<T> F;
                 body_frame(c, b, Sx, P, band, F);
@@ -2047,7 +2255,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
        uint32_t *__restrict__ fl_base,
        uint64_t *__restrict__ codes, int32_t *__restrict__ counts, int cap, int ch0, int nch, int rcap,
        int nwt, int accumulate, int enc, unsigned long long *esc_counter, unsigned long long *queue) {
-    constexpr bool BODIES = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
+    constexpr bool BODIES = (CLS & CLS_BODIES) != 0;
     extern __shared__ float4 smem[];
     __shared__ Ctx s_ctx;
     __shared__ FreqC s_fqs[MAX_CHUNKS];        // frequency chunks ch0 .. ch0 + nch - 1
@@ -2104,6 +2312,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         c.occ_src = nullptr;
         c.occ_w = 0;
         c.enc = enc;
+        c.txw = frames ? nullptr : S.txw;
 
     }
     __syncthreads();
@@ -2122,7 +2331,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         const unsigned long long ntiles = ((unsigned long long)n_rx + 31ull) >> 5;
         // occluder masks (FP32 body kernels): the source side per block, the
         // receiver side per warp (each warp takes whole tiles)
-        constexpr bool OCC = BODIES && sizeof(T) == 4;
+        constexpr bool OCC = BODIES && sizeof(T) == 4 && CLS != CLS_WCREEP;
         const bool occ_on = OCC && S.n_body > 0 && S.n_body <= OCC_MAX_BODIES;
         const int occ_w = occ_on ? (S.n_body + 31) >> 5 : 0;
         uint32_t *s_occ_src = reinterpret_cast<uint32_t *>(s_rec);
@@ -2158,7 +2367,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                 int nrec;
                 eval_receiver<T, PATHS, CLS, LIST>(c, s_fqs, 1, S.enable, S.max_order, rx, n_rx, r, codes, counts, cap,
                                                    F1.hl,
-                                             0, c.n_body, true, false, 0, occ_on ? s_occ_mine : nullptr, 0, 1, acc,
+                                             0, CLS == CLS_WCREEP ? c.n_face * c.n_body : c.n_body, true, false, 0,
+                                             occ_on ? s_occ_mine : nullptr, 0, 1, acc,
                                              nullptr, fl, nesc, npath, nrec);
                 counts[r] = npath;
                 if (fl_base) fl_base[r] = accumulate ? (fl_base[r] | fl) : fl;
@@ -2185,7 +2395,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         const int NWT = nwt;
         const int TPB = NW / NWT;
         constexpr bool RECS = BODIES && sizeof(T) == 4;
-        constexpr int PER = ((CLS & CLS_CREEP) ? 2 : 0) + ((CLS & CLS_BODYREFL) ? 1 : 0);
+        constexpr int PER = recs_per_unit(CLS);
         const unsigned long long n_units = (n_tiles + TPB - 1) / TPB;
         const int grp = warp / NWT, part = warp % NWT;
         // partial sums of each warp: NFC * 6 rows of 32 lanes; the FP32
@@ -2202,7 +2412,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         __shared__ FrameDev s_fr;
         // occluder masks (FP32 body kernels): the source side per frame, the
         // receiver side per tile, after the path records
-        constexpr bool OCC = BODIES && sizeof(T) == 4;
+        constexpr bool OCC = BODIES && sizeof(T) == 4 && CLS != CLS_WCREEP;
         const bool occ_on = OCC && S.n_body > 0 && S.n_body <= OCC_MAX_BODIES;
         const int occ_w = occ_on ? (S.n_body + 31) >> 5 : 0;
         uint32_t *s_occ_src = reinterpret_cast<uint32_t *>(s_rec + (RECS ? NW * rcap * REC_N * 32 : 0));
@@ -2256,7 +2466,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
             const float *rx = rx_base + 3 * Fr.rx_off;
             float *e_out = e_base + Fr.e_off;
             uint32_t *flags_out = fl_base ? fl_base + Fr.rx_off : nullptr;
-            const int n_b = BODIES ? c.n_body : 0;
+            const int n_b = BODIES ? (CLS == CLS_WCREEP ? c.n_face * c.n_body : c.n_body) : 0;
             // bodies per geometry pass: all of them with one frequency chunk (full
             // record buffers are flushed on the way), else as many as the buffer holds
             const int bc = (RECS && nch > 1) ? NWT * (rcap / PER) : (n_b > 0 ? n_b : 1);
@@ -2385,7 +2595,7 @@ template <typename T, bool PATHS, int CLS, bool LIST = false>
 static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch, int accumulate, LaunchCtx &L,
                               int enc = 0) {
     if (L.n >= CTR_QUEUES) return cudaErrorInvalidValue;
-    constexpr bool bodies = (CLS & (CLS_BODYREFL | CLS_CREEP)) != 0;
+    constexpr bool bodies = (CLS & CLS_BODIES) != 0;
     constexpr int blk = blk_of(CLS, sizeof(T) == 4);
     constexpr int NW = blk / 32;
     // warps per tile (fields): the configured shape where it divides the
@@ -2400,7 +2610,7 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     if (nch < 1 || nch > MAX_CHUNKS || (!wide && !bodies && nch != 1)) return cudaErrorInvalidValue;
     // occluder masks (FP32 body kernels): one source-side set, and one
     // receiver-side set per tile in flight (fields) or per warp (path lists)
-    const int occ_sets = (bodies && sizeof(T) == 4) ? (PATHS ? NW : NW / nwt) : 0;
+    const int occ_sets = (bodies && sizeof(T) == 4 && CLS != CLS_WCREEP) ? (PATHS ? NW : NW / nwt) : 0;
     size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk, rcap, wide ? nch : 0, occ_sets);
     cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
@@ -2446,6 +2656,8 @@ template <typename T, bool PATHS, bool LIST = false>
 static cudaError_t launch_all(const DevScene &S, const Work &W, int nchunks, LaunchCtx &L) {
     cudaError_t e = cudaSuccess;
     const bool chunked_bodies = PATHS || sizeof(T) != 4;
+    // wall -> creeping paths: single scenes with faces and bodies
+    const bool wall = (S.enable & RT_EN_WALL_CREEP) && S.txw && !W.frames && S.n_face > 0 && S.n_body > 0;
     // FP32 fields: each planar launch takes up to PLANAR_CHUNKS chunks in one
     // geometry pass
     const int pstep = chunked_bodies ? 1 : (W.planar_chunks >= 1 && W.planar_chunks <= MAX_CHUNKS ? W.planar_chunks
@@ -2456,10 +2668,14 @@ static cudaError_t launch_all(const DevScene &S, const Work &W, int nchunks, Lau
         if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL, LIST>(S, W, ch, 1, 1, L);
         for (int enc = 0; chunked_bodies && enc <= S.max_enc && e == cudaSuccess; ++enc)
             e = launch_one<T, PATHS, CLS_CREEP, LIST>(S, W, ch, 1, 1, L, enc);
+        for (int enc = 0; chunked_bodies && wall && enc <= S.max_enc && e == cudaSuccess; ++enc)
+            e = launch_one<T, PATHS, CLS_WCREEP, LIST>(S, W, ch, 1, 1, L, enc);
     }
     if (!chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL, LIST>(S, W, 0, nchunks, 1, L);
     for (int enc = 0; !chunked_bodies && enc <= S.max_enc && e == cudaSuccess; ++enc)
         e = launch_one<T, PATHS, CLS_CREEP, LIST>(S, W, 0, nchunks, 1, L, enc);
+    for (int enc = 0; !chunked_bodies && wall && enc <= S.max_enc && e == cudaSuccess; ++enc)
+        e = launch_one<T, PATHS, CLS_WCREEP, LIST>(S, W, 0, nchunks, 1, L, enc);
     return e;
 }
 
@@ -2727,13 +2943,21 @@ __device__ __noinline__ void adj_rb(const Ctx &c, int b, v3t<D8> S, v3t<D8> P, c
 }
 
 // creeping ray round body b, dir 0 short way, 1 long way, with enc extra
-// turns; false: no finite field
-__device__ __noinline__ bool adj_creep(const Ctx &c, int b, int dir, int enc, v3t<D8> S, v3t<D8> P, const FreqC &fq,
-                                       unsigned enable, AccAdj &acc) {
+// turns; wall >= 0: fed by the reflection at face wall (the creeping ray of
+// the source's image there); false: no finite field
+__device__ __noinline__ bool adj_creep(const Ctx &c, int b, int dir, int enc, v3t<D8> S0, v3t<D8> P, const FreqC &fq,
+                                       unsigned enable, AccAdj &acc, int wall = -1) {
     v3t<D8> cc;
     D8 a;
     bool sphere;
     adj_body(c, b, cc, a, sphere);
+    v3t<D8> S = S0;
+    if (wall >= 0) {
+        v3t<D8> n;
+        D8 d;
+        face_plane<D8>(c, wall, &n, &d);
+        S = mirror_pt(S0, n, d);
+    }
     Frame<D8> F;
     if (sphere) sphere_frame(S, P, cc, a, F, D8(0.0));
     else cyl_frame(S, P, cc.x, cc.y, a, F, D8(0.0));
@@ -2781,7 +3005,8 @@ __device__ __noinline__ bool adj_creep(const Ctx &c, int b, int dir, int enc, v3
         g.dperp = D8(0.0);
         g.amp = D8(1.0) / Sqrt(g.sp * g.sq * (g.sp + g.t + g.sq));
     }
-    field_creep<D8, D8, false, AccAdj>(c, acc, fq, S, P, g, g.sp + g.t + g.sq, enable);
+    if (wall >= 0) field_wcreep<D8, D8, false, AccAdj>(c, acc, fq, wall, S0, S, P, g, g.sp + g.t + g.sq, enable);
+    else field_creep<D8, D8, false, AccAdj>(c, acc, fq, S, P, g, g.sp + g.t + g.sq, enable);
     return true;
 }
 
@@ -2885,6 +3110,8 @@ __global__ void __launch_bounds__(128) k_adjoint(DevScene S, const float *__rest
                     else if (type == PT_RB) { adj_rb(c, id1, Sd, Pd, fq, acc); body = id1; }
                     else if (type == PT_CP || type == PT_CM) {
                         if (adj_creep(c, id1, type == PT_CM, id2, Sd, Pd, fq, S.enable, acc)) body = id1;
+                    } else if (type == PT_WCP || type == PT_WCM) {
+                        if (adj_creep(c, id1, type == PT_WCM, id2 & 15, Sd, Pd, fq, S.enable, acc, id2 >> 4)) body = id1;
                     }
                 }
                 if (body >= 0)

@@ -76,6 +76,8 @@ struct DevScene {
                                // nullptr when every face is PEC
     const float4 *txb;         // [n_body][2] per transmitter, FP64-computed: (u, |S - c|), (beta_s, sqrt(|S-c|^2 - a^2) hi, lo,
                                // lateral paths possible ? 1 : 0); cylinders use horizontal distances
+    const float4 *txw;         // [n_face][n_body][2]: as txb, for the source's mirror image in each face
+                               // (wall -> creeping paths); nullptr in batches
     const double *freq;        // [n_f] Hz (host copy, read by the launcher)
     const FreqC *fqc;          // [ceil(n_f / NFC)] per-chunk frequency constants (device)
     float tx[3], pol[3];
@@ -105,7 +107,7 @@ struct FrameDev {
 
 // Device counters of one evaluation: [0] candidates decided in FP64, [1 + i]
 // the work queue of launch i.  Zeroed by the caller before launch_eval.
-constexpr int CTR_QUEUES = 128;
+constexpr int CTR_QUEUES = 256;
 constexpr int CTR_N = 1 + CTR_QUEUES;
 
 // Evaluate (codes == nullptr), list paths (e_out == nullptr: canonical

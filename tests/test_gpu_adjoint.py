@@ -48,7 +48,8 @@ def _close(got, ref, absum, what):
 def _forward(creep, sc, cap=256):
     S = creep.Scene.from_scene(sc)
     rx = torch.tensor(sc.rx_soa(), device="cuda")
-    opts = creep.options(max_order=sc.max_order, max_encirclements=getattr(sc, "max_enc", 0))
+    opts = creep.options(max_order=sc.max_order, max_encirclements=getattr(sc, "max_enc", 0),
+                         enable=creep.RT_EN_ALL | (creep.RT_EN_WALL_CREEP if getattr(sc, "wall_creep", False) else 0))
     E = S.evaluate(rx, opts=opts)
     codes, counts, _ = S.paths(rx, cap=cap, opts=opts)
     torch.cuda.synchronize()
@@ -119,6 +120,32 @@ def test_adjoint_extra_turns(creep, oracle_mod):
     sc.max_enc = 1
     n_checked, _ = _check(creep, sc, bodies=range(12), seed=6, keep=extra)
     assert n_checked >= 8
+
+
+def _room_with_spheres(n_cyl, nx, ny, freqs, seed):
+    """The room with every other cylinder replaced by a sphere of its radius
+    centred 0.9 m above its foot."""
+    sc = scenes.room(n_cyl=n_cyl, nx=nx, ny=ny, freqs=freqs, seed=seed)
+    for k in range(0, n_cyl, 2):
+        x, y, a = sc.bodies[k, 1], sc.bodies[k, 2], sc.bodies[k, 4]
+        sc.bodies[k] = [scenes.BODY_SPHERE, x, y, 0.9, a, 0.0]
+    return sc
+
+
+def test_adjoint_wall_creep(creep, oracle_mod):
+    """Creeping rays fed by a planar reflection (PEC faces, then a dielectric
+    floor and walls): the gradient through those paths alone, with respect to
+    the spheres' and cylinders' centres and radii, the transmitter and the
+    frequencies."""
+    walls = (5.31, 0.48)
+    for fe in (None, [(4.0, 0.2), None, walls, walls, walls, walls]):
+        sc = _jitter(_room_with_spheres(8, 20, 16, (2.4e9, 5.8e9), 17), 18)
+        sc.face_eps = None if fe is None else np.asarray(
+            [(0.0, 0.0, 0.0) if e is None else (1.0, e[0], e[1]) for e in fe], dtype=np.float32)
+        sc.wall_creep = True
+        wall = lambda c: (c >> 56) in (6, 7)
+        n_checked, _ = _check(creep, sc, bodies=range(8), seed=7, keep=wall)
+        assert n_checked >= 20
 
 
 def test_adjoint_200_cylinders(creep, oracle_mod):

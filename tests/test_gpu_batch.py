@@ -171,6 +171,9 @@ def test_batch_errors(creep):
     assert e.value.code == creep.RT_ERR_ARG
     B.set_frame(2, cw.bodies[2], cw.freqs[2])
     B.evaluate(rx)
+    with pytest.raises(creep.CreepError) as e:       # wall -> creeping paths: single scenes only
+        B.evaluate(rx, opts=creep.options(enable=creep.RT_EN_ALL | creep.RT_EN_WALL_CREEP))
+    assert e.value.code == creep.RT_ERR_ARG
     S.set_tx(cw.tx + np.float32(0.01), cw.pol)       # every frame must be set again
     with pytest.raises(creep.CreepError) as e:
         B.evaluate(rx)

@@ -322,3 +322,40 @@ def test_extra_turns(creep, oracle_mod, precision):
         S.evaluate(torch.zeros((3, 4), dtype=torch.float32, device="cuda"),
                    opts=creep.options(max_encirclements=5))
     assert e.value.code == creep.RT_ERR_ARG
+
+
+def _room_with_spheres(n_cyl, nx, ny, seed):
+    """The room with every other cylinder replaced by a sphere of its radius
+    centred 0.9 m above its foot."""
+    sc = scenes.room(n_cyl=n_cyl, nx=nx, ny=ny, seed=seed)
+    for k in range(0, n_cyl, 2):
+        x, y, a = sc.bodies[k, 1], sc.bodies[k, 2], sc.bodies[k, 4]
+        sc.bodies[k] = [scenes.BODY_SPHERE, x, y, 0.9, a, 0.0]
+    return sc
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_wall_creep(creep, oracle_mod, precision):
+    """Creeping rays fed by a planar reflection (RT_EN_WALL_CREEP): the
+    20-cylinder room with PEC faces, the same with a dielectric floor and
+    walls and one extra turn, and a room of spheres and cylinders; path lists
+    bit for bit (WCP / WCM, body, 16 face + turns), flags, fields within the
+    bound."""
+    prec = creep.RT_PREC_FP64 if precision == "fp64" else creep.RT_PREC_FP32
+    walls = (5.31, 0.48)
+    cases = [(scenes.room(n_cyl=20, nx=61, ny=47, seed=8), 0),
+             (scenes.room(n_cyl=20, nx=61, ny=47, seed=8, face_eps=[(4.0, 0.2), None, walls, walls, walls, walls]), 1),
+             (_room_with_spheres(12, 40, 32, 9), 0)]
+    for sc, enc in cases:
+        sc.wall_creep = True
+        sc.max_enc = enc
+        opts = creep.options(max_order=2, precision=prec, enable=creep.RT_EN_ALL | creep.RT_EN_WALL_CREEP,
+                             max_encirclements=enc)
+        S, Eg, codes, counts, fl, fl2 = _run(creep, sc, opts=opts)
+        ref = oracle_mod.evaluate(sc)
+        compare_paths(codes, counts, ref)
+        _flags_equal(fl, ref)
+        _flags_equal(fl2, ref)
+        compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs)
+        n_wall = sum(1 for cs in ref.paths for c in cs if (int(c) >> 56) in (6, 7))
+        assert n_wall > 20000, n_wall
