@@ -12,8 +12,11 @@ At N = 1 the line also carries "batched": the batched form on 64 crowd frames
 (50 walking PEC cylinders, 16 frequencies in 24-30 GHz per frame, 1k-64k
 receivers per frame, 1.12 M receivers in all) replayed from a captured CUDA
 graph, with its own roofline and oracle comparison (--no-batched skips it),
-and "adjoint": one gradient step (fields, path list, rt_backward) on the room
-with 200 PEC cylinders at 28 GHz, 64 x 64 receivers (--no-adjoint skips it).
+"adjoint": one gradient step (fields, path list, rt_backward) on the room
+with 200 PEC cylinders at 28 GHz, 64 x 64 receivers (--no-adjoint skips it),
+and "extended_paths": the room workload with dielectric floor and walls,
+creeping rays with up to two extra turns and wall-reflection -> creeping
+paths, against the oracle on 512 sampled receivers (--no-extended skips it).
 
 N > 1 runs under torch.distributed (one process per GPU): each rank evaluates
 its own receiver grid (shifted by a fraction of a cell) with no data-path
@@ -60,6 +63,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched crowd-frames measurement")
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) measurement")
+    ap.add_argument("--no-extended", action="store_true",
+                    help="skip the extended path set (dielectric faces, extra turns, wall->creeping)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
@@ -405,6 +410,74 @@ def adjoint_room200(args, creep, dev, flush):
             "l2": "flushed between timed steps (256 MiB write)"}
 
 
+def extended_room(args, creep, dev, flush, peak_fn, base_ms):
+    """The room workload (20 cylinders, 256 x 256 receivers, 3 frequencies)
+    with the extended path set: a dielectric floor and walls (PEC ceiling),
+    creeping rays with up to two extra turns, and wall-reflection -> creeping
+    paths.  Its time per evaluation beside the first-order set's, and the
+    fields and path lists of 512 sampled receivers against the oracle."""
+    import torch
+    from paper_2310_10578_gb300 import scenes
+    walls = (5.31, 0.48)
+    sc = scenes.room(face_eps=[(4.0, 0.2), None, walls, walls, walls, walls])
+    sc.max_enc = 2
+    sc.wall_creep = True
+    S = creep.Scene.from_scene(sc)
+    rx = torch.tensor(sc.rx_soa(), device=dev)
+    n, n_f = sc.n_rx, len(sc.freqs)
+    opts = creep.options(max_order=2, enable=creep.RT_EN_ALL | creep.RT_EN_WALL_CREEP, max_encirclements=2)
+    out = torch.empty((n_f, 3, n, 2), dtype=torch.float32, device=dev)
+    shape = S.tune(rx, out=out, opts=opts)
+    for _ in range(3):
+        S.evaluate(rx, out=out, opts=opts)
+    st = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(args.batched_steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        S.evaluate(rx, out=out, opts=opts)
+        e1.record(st)
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ms]))
+    stats = S.stats()
+    res = {"workload": "room 10x8x3 m, dielectric floor (eps 4.0-0.2j) and walls (5.31-0.48j), PEC ceiling, "
+                       "20 PEC cylinders, 256x256 rx, 2.4/5.8/28 GHz, refl<=2, creeping with <=2 extra turns, "
+                       "wall->creeping paths",
+           "value": n * n_f / (ms / 1e3), "unit": UNIT, "ms_per_step": ms, "steps": args.batched_steps,
+           "vs_first_order_set": ms / base_ms, "gpu_launches_per_step": stats["kernel_launches"],
+           "tile_shape": {"planar_warps_per_tile": shape[0], "body_warps_per_tile": shape[1],
+                          "planar_chunks_per_launch": shape[2], "chosen_by": "rt_tune"},
+           "fp64_escalated_candidates": stats["escalated_candidates"],
+           "l2": "flushed between timed steps (256 MiB write)"}
+    if not args.no_cpu_baseline:
+        from oracle import oracle
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from parity import compare_fields, path_mismatches
+        oracle.build()
+        idx = np.sort(np.random.default_rng(91).choice(n, 512, replace=False))
+        t0 = time.perf_counter()
+        ref = oracle.evaluate(sc.subset(idx))
+        t_cpu = time.perf_counter() - t0
+        Eg = out.detach().cpu().numpy().astype(np.float64)
+        Eg = (Eg[..., 0] + 1j * Eg[..., 1])[:, :, idx]
+        acc = compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs, check=False)
+        codes, counts, _ = S.paths(torch.tensor(sc.subset(idx).rx_soa(), device=dev), opts=opts)
+        torch.cuda.synchronize()
+        acc["path_list_mismatches"] = len(path_mismatches(codes.cpu().numpy(), counts.cpu().numpy(), ref))
+        res["accuracy_vs_fp64_oracle"] = dict(acc, sample_receivers=len(idx))
+        flops = algorithmic_flops(ref.counters, len(idx), n, n_f)
+        mufu = algorithmic_flops(ref.counters, len(idx), n, n_f, UNIT_MUFU)
+        res["roofline"] = peak_fn(flops, mufu, ms, None)
+        res["roofline"]["kernel"] = "evaluation: k_eval<float, false, 1|2|4|8> (planar, body reflection, creeping x3, " \
+                                    "wall->creeping x3)"
+        res["cpu_baseline"] = {"value": len(idx) * n_f / t_cpu, "unit": UNIT, "cores": os.cpu_count() or 1,
+                               "kind": "oracle", "sample": "the accuracy sample (%.1f s)" % t_cpu}
+    return res
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -506,6 +579,9 @@ def main():
     adj = None
     if world == 1 and not args.no_adjoint:
         adj = adjoint_room200(args, creep, dev, flush)
+    ext = None
+    if world == 1 and not args.no_extended:
+        ext = extended_room(args, creep, dev, flush, peak_fn, float(np.mean(dev_ms)))
     clocks = sampler.stop() if sampler else None
 
     ms, e2e_s = max_over_ranks([np.mean(dev_ms), np.mean(e2e_t)], device=dev)
@@ -557,6 +633,8 @@ def main():
         line["batched"] = batched
     if adj is not None:
         line["adjoint"] = adj
+    if ext is not None:
+        line["extended_paths"] = ext
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
