@@ -42,7 +42,7 @@ typedef double complex cplx;
 #define TWO_PI (2.0 * M_PI)
 
 /* path type codes; a path is (type << 56) | (id1 << 28) | id2 */
-enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5, PT_WCP = 6, PT_WCM = 7 };
+enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5, PT_WCP = 6, PT_WCM = 7, PT_R3 = 8 };
 /* receiver flags */
 enum { FL_INSIDE = 1u, FL_CAUSTIC = 2u, FL_OVERFLOW = 8u };
 /* enable mask */
@@ -170,6 +170,7 @@ typedef struct {
 typedef struct {
     int n_tri; const double *tri; const int *tri_face; int *order; /* triangle ids grouped by face */
     int n_face; face *faces;
+    const int *cand; int n_cand;        /* candidate face sequences [n_cand][3] (-1 padded), or none */
     int n_body; body *bodies;
     v3 tx, pol;
     int n_f; const double *freq;
@@ -375,7 +376,50 @@ static inline void accum(rx_state *st, int f, c3 v) {
     }
 }
 
-/* LOS and planar image paths (order 1 and 2); PEC or dielectric faces. */
+/* Planar image path through the faces fs[0..k-1] in that order (k <= 3):
+ * images S_m of the source in faces fs[0..m-1]; backwards from P, Q_m is
+ * where S_{m+1} -> Q_{m+1} (Q_k = P) crosses face fs[m]'s plane (the two
+ * strictly on opposite sides) and must lie in that face; then every leg
+ * S -> Q_0 -> ... -> P clear of all triangles but those of the faces at its
+ * ends.  Field: the source's polarisation reflected at each point in turn. */
+static void seq_path(const scene *s, const int *fs, int k, v3 P, rx_state *st, uint64_t code) {
+    v3 S = s->tx;
+    v3 img[4];
+    img[0] = S;
+    for (int m = 0; m < k; ++m) img[m + 1] = mirror_point(img[m], &s->faces[fs[m]]);
+    st->ct.image_cand++;
+    v3 Q[3], X = P;
+    for (int m = k - 1; m >= 0; --m) {
+        const face *F = &s->faces[fs[m]];
+        double di = dot(F->n, img[m + 1]) - F->d, dx = dot(F->n, X) - F->d;
+        if (!(di * dx < 0.0)) return;
+        Q[m] = add(img[m + 1], scl(sub(X, img[m + 1]), di / (di - dx)));
+        if (!point_in_face(s, fs[m], Q[m], &st->ct)) return;
+        X = Q[m];
+    }
+    if (!visible(s, S, Q[0], fs[0], -1, -1, &st->ct)) return;
+    for (int m = 0; m + 1 < k; ++m)
+        if (!visible(s, Q[m], Q[m + 1], fs[m], fs[m + 1], -1, &st->ct)) return;
+    if (!visible(s, Q[k - 1], P, fs[k - 1], -1, -1, &st->ct)) return;
+    add_path(st, code);
+    double L = norm(sub(Q[0], S)) + norm(sub(P, Q[k - 1]));
+    for (int m = 0; m + 1 < k; ++m) L += norm(sub(Q[m + 1], Q[m]));
+    v3 din = unit(sub(Q[0], S));
+    c3 e = c3_from(source_pol(s, din));
+    for (int m = 0; m < k; ++m) {
+        v3 dout = unit(sub(m + 1 < k ? Q[m + 1] : P, Q[m]));
+        e = reflect_at(&s->faces[fs[m]], e, din, dout);
+        din = dout;
+    }
+    for (int f = 0; f < s->n_f; ++f) {
+        double kw = kwave(s->freq[f]);
+        accum(st, f, c3_scl(e, cexp(-I * kw * L) / L));
+    }
+}
+
+/* LOS and planar image paths (order 1 and 2 over all faces and face pairs,
+ * or, with a candidate list, orders 1-3 over its sequences); PEC or
+ * dielectric faces. */
 static void planar_paths(const scene *s, v3 P, rx_state *st) {
     v3 S = s->tx;
     if (s->enable & EN_LOS) {
@@ -390,6 +434,18 @@ static void planar_paths(const scene *s, v3 P, rx_state *st) {
         }
     }
     if (!(s->enable & EN_PLANAR)) return;
+    if (s->cand) {
+        /* candidate mode: orders 1 and 2 listed by their faces, order 3 by
+         * the sequence's index in the list */
+        for (int q = 0; q < s->n_cand; ++q) {
+            const int *fs = s->cand + 3 * q;
+            int k = (fs[0] >= 0) + (fs[1] >= 0) + (fs[2] >= 0);
+            if (k < 1 || k > s->max_order) continue;
+            uint64_t code = (k == 1) ? pcode(PT_R1, fs[0], 0) : (k == 2) ? pcode(PT_R2, fs[0], fs[1]) : pcode(PT_R3, q, 0);
+            seq_path(s, fs, k, P, st, code);
+        }
+        return;
+    }
     if (s->max_order >= 1) {
         for (int i = 0; i < s->n_face; ++i) {
             const face *Fi = &s->faces[i];
@@ -851,7 +907,7 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
                 int max_order, int enable,
                 double *E_out, uint64_t *path_codes, int *path_count, int cap,
                 unsigned *flags_out, long long *counters_out, int n_threads, double *sabs_out,
-                double *path_E_out, const double *face_eps, int max_enc) {
+                double *path_E_out, const double *face_eps, int max_enc, const int *cand, int n_cand) {
     fock_rule R = {tau_re, tau_im, ws_re, ws_im, wh_re, wh_im, offsets, n_buckets,
                    res_alpha, res_cs, res_beta, res_ch, n_res, xi_lo, xi_hi};
     scene s;
@@ -877,6 +933,7 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
     s.n_f = n_f; s.freq = freq; s.fock = &R;
     s.max_order = max_order; s.enable = enable;
     s.max_enc = max_enc;
+    s.cand = cand; s.n_cand = cand ? n_cand : 0;
     counters tot;
     memset(&tot, 0, sizeof(tot));
 #ifdef _OPENMP
@@ -933,6 +990,87 @@ int oracle_eval(const double *tri, const int *tri_face, int n_tri,
     }
     free(s.faces); free(s.order); free(s.bodies);
     return 0;
+}
+
+/* ------------------------------------------------------------ candidates */
+/* Ray hit with the closed triangle (v0, v1, v2) (Moller-Trumbore); returns
+ * the ray parameter or -1. */
+static double ray_tri(v3 o, v3 d, v3 v0, v3 v1, v3 v2) {
+    v3 e1 = sub(v1, v0), e2 = sub(v2, v0);
+    v3 p = cross(d, e2);
+    double det = dot(e1, p);
+    if (fabs(det) < 1e-14) return -1.0;
+    double inv = 1.0 / det;
+    v3 sv = sub(o, v0);
+    double u = dot(sv, p) * inv;
+    if (u < 0.0 || u > 1.0) return -1.0;
+    v3 q = cross(sv, e1);
+    double v = dot(d, q) * inv;
+    if (v < 0.0 || u + v > 1.0) return -1.0;
+    return dot(e2, q) * inv;
+}
+
+static int seq_cmp(const void *pa, const void *pb) {
+    const int *x = (const int *)pa, *y = (const int *)pb;
+    int kx = (x[0] >= 0) + (x[1] >= 0) + (x[2] >= 0), ky = (y[0] >= 0) + (y[1] >= 0) + (y[2] >= 0);
+    if (kx != ky) return kx < ky ? -1 : 1;
+    for (int m = 0; m < 3; ++m)
+        if (x[m] != y[m]) return x[m] < y[m] ? -1 : 1;
+    return 0;
+}
+
+/* Candidate face sequences of the large-scene mode, by a ray launch from the
+ * transmitter: n_rays directions of the spherical Fibonacci lattice
+ * (z_i = 1 - (2i + 1)/n, phi_i = i pi (3 - sqrt 5)), each ray reflected
+ * specularly at the nearest triangle hit (parameter > 1e-9, the face it
+ * leaves excluded; ties to the lower triangle index; bodies ignored) up to
+ * max_order times; every prefix of its face sequence is a candidate.  The
+ * distinct sequences, sorted (order, then faces), go to seq [cap][3] (-1
+ * padded).  Returns their number (capped at cap). */
+int oracle_candidates(const double *tri, const int *tri_face, int n_tri, const double *tx, int n_rays, int max_order,
+                      int *seq, int cap) {
+    scene s;
+    memset(&s, 0, sizeof(s));
+    s.n_tri = n_tri; s.tri = tri; s.tri_face = tri_face;
+    build_faces(&s);
+    int n_all = 0;
+    int *all = (int *)malloc(sizeof(int) * 3 * (size_t)(n_rays > 0 ? n_rays : 1) * (max_order > 0 ? max_order : 1));
+    const double golden = M_PI * (3.0 - sqrt(5.0));
+    for (int i = 0; i < n_rays; ++i) {
+        double z = 1.0 - (2.0 * i + 1.0) / n_rays;
+        double r = sqrt(fmax(0.0, 1.0 - z * z));
+        double ph = golden * i;
+        v3 o = V(tx[0], tx[1], tx[2]), d = V(r * cos(ph), r * sin(ph), z);
+        int fs[3] = {-1, -1, -1}, last = -1;
+        for (int k = 0; k < max_order; ++k) {
+            double best = INFINITY;
+            int bt = -1;
+            for (int t = 0; t < n_tri; ++t) {
+                if (tri_face[t] == last) continue;
+                double h = ray_tri(o, d, tri_v(&s, t, 0), tri_v(&s, t, 1), tri_v(&s, t, 2));
+                if (h > 1e-9 && h < best) { best = h; bt = t; }
+            }
+            if (bt < 0) break;
+            int f = tri_face[bt];
+            fs[k] = f;
+            for (int m = 0; m < 3; ++m) all[3 * n_all + m] = (m <= k) ? fs[m] : -1;
+            ++n_all;
+            v3 n = s.faces[f].n;
+            o = add(o, scl(d, best));
+            d = sub(d, scl(n, 2.0 * dot(d, n)));
+            last = f;
+        }
+    }
+    /* sort by (order, faces) and keep the distinct ones */
+    qsort(all, (size_t)n_all, 3 * sizeof(int), seq_cmp);
+    int n = 0;
+    for (int a = 0; a < n_all; ++a) {
+        if (a > 0 && !memcmp(all + 3 * a, all + 3 * (a - 1), 3 * sizeof(int))) continue;
+        if (n < cap) memcpy(seq + 3 * n, all + 3 * a, 3 * sizeof(int));
+        ++n;
+    }
+    free(all); free(s.faces); free(s.order);
+    return n < cap ? n : cap;
 }
 
 /* Exposed for the oracle's own tests. */

@@ -25,7 +25,7 @@ EN_WALL_CREEP = 32          # wall -> creeping paths (also switched on by scene.
 # receiver flags
 FL_INSIDE, FL_CAUSTIC, FL_OVERFLOW = 1, 2, 8
 # path types
-PT_LOS, PT_R1, PT_R2, PT_RB, PT_CP, PT_CM, PT_WCP, PT_WCM = range(8)
+PT_LOS, PT_R1, PT_R2, PT_RB, PT_CP, PT_CM, PT_WCP, PT_WCM, PT_R3 = range(9)
 COUNTER_NAMES = ("seg_tri", "seg_body", "inside_tri", "image_cand", "body_refl", "creep_geom",
                  "paths", "fock_evals")
 
@@ -55,7 +55,7 @@ def _load():
         d = ctypes.c_double
         _lib.oracle_eval.argtypes = [P, P, i, P, i, P, P, P, i, P, i,
                                      P, P, P, P, P, P, P, i, P, P, P, P, i, d, d,
-                                     i, i, P, P, P, i, P, P, i, P, P, P, i]
+                                     i, i, P, P, P, i, P, P, i, P, P, P, i, P, i]
         _lib.oracle_eval.restype = i
         _lib.oracle_transition_F.argtypes = [P, i, P]
         _lib.oracle_fock_bracket.argtypes = [P, P, P, P, P, P, P, i, P, P, P, P, i, d, d, P, P, i, P]
@@ -64,6 +64,8 @@ def _load():
         _lib.oracle_seg_hits_body.argtypes = [P, P, P]
         _lib.oracle_reflect.argtypes = [P, P, P, P, i, d, d, P]
         _lib.oracle_reflect.restype = None
+        _lib.oracle_candidates.argtypes = [P, P, i, P, i, i, P, i]
+        _lib.oracle_candidates.restype = i
     return _lib
 
 
@@ -126,13 +128,17 @@ def evaluate(scene, rx=None, enable=EN_ALL, cap=256, threads=0, want_paths=True,
     # face materials: [n_face][3] (dielectric flag, eps', eps''), eps_r = eps' - j eps''; None: PEC
     fe = getattr(scene, "face_eps", None)
     fe = None if fe is None else np.ascontiguousarray(np.asarray(fe, dtype=np.float64).reshape(-1, 3))
+    # candidate face sequences [n][3] (-1 padded): planar paths of orders 1-3 from them only
+    cand = getattr(scene, "candidates", None)
+    cand = None if cand is None else np.ascontiguousarray(np.asarray(cand, dtype=np.int32).reshape(-1, 3))
     t0 = time.perf_counter()
     lib.oracle_eval(_p(tri), _p(tf), scene.tri.shape[0], _p(bodies), scene.bodies.shape[0],
                     _p(tx), _p(pol), _p(fr), n_f, _p(rx64), n_rx, *_fock_args(),
                     scene.max_order, enable | (EN_WALL_CREEP if getattr(scene, "wall_creep", False) else 0), _p(E),
                     _p(codes) if want_paths else None, _p(counts), cap if want_paths else 0,
                     _p(flags), _p(ctr), threads, _p(sabs), _p(pE) if pE is not None else None,
-                    _p(fe) if fe is not None else None, int(getattr(scene, "max_enc", 0)))
+                    _p(fe) if fe is not None else None, int(getattr(scene, "max_enc", 0)),
+                    _p(cand) if cand is not None else None, 0 if cand is None else cand.shape[0])
     res = Result()
     res.seconds = time.perf_counter() - t0
     res.E = E[..., 0] + 1j * E[..., 1]
@@ -146,6 +152,18 @@ def evaluate(scene, rx=None, enable=EN_ALL, cap=256, threads=0, want_paths=True,
         res.path_E = pE[..., 0] + 1j * pE[..., 1]
     res.counters = dict(zip(COUNTER_NAMES, (int(c) for c in ctr)))
     return res
+
+
+def candidates(scene, n_rays, max_order=3, cap=1 << 20):
+    """Candidate face sequences [n][3] int32 (-1 padded) of the ray launch from
+    the scene's transmitter (see oracle_candidates in creep_oracle.c)."""
+    lib = _load()
+    tri = np.ascontiguousarray(scene.tri.astype(np.float64).reshape(-1))
+    tf = np.ascontiguousarray(scene.tri_face.astype(np.int32))
+    tx = np.ascontiguousarray(np.asarray(scene.tx, dtype=np.float64))
+    out = np.zeros((cap, 3), dtype=np.int32)
+    n = lib.oracle_candidates(_p(tri), _p(tf), scene.tri.shape[0], _p(tx), int(n_rays), int(max_order), _p(out), cap)
+    return out[:n].copy()
 
 
 def transition_F(X):
