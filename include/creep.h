@@ -90,9 +90,15 @@ extern "C" {
 #define RT_PATH_CM 5       /* id1 = body, id2 = extra turns: creeping ray, long way round */
 #define RT_PATH_WCP 6      /* id1 = body, id2 = 16 face + extra turns: reflection at face, then CP */
 #define RT_PATH_WCM 7      /* id1 = body, id2 = 16 face + extra turns: reflection at face, then CM */
+#define RT_PATH_R3 8       /* id1 = index in the candidate list: planar reflection of order 3 */
 
-/* library limits */
-#define RT_MAX_FACES 64
+/* library limits.  Scenes of more than RT_MAX_ENUM_FACES faces take their
+ * planar paths from a candidate list (rt_set_candidates) and have no
+ * wall -> creeping paths; scenes of more than 64 triangles test visibility
+ * through a triangle BVH. */
+#define RT_MAX_FACES (1 << 20)
+#define RT_MAX_ENUM_FACES 64
+#define RT_MAX_CANDIDATES (1 << 20)
 #define RT_MAX_BODIES 1024
 #define RT_MAX_TRIS 4096
 #define RT_MAX_FREQS 64
@@ -158,6 +164,33 @@ int rt_set_tx(rt_scene *scene, const float tx[3], const float pol[3]);
  * the scene's face count.  Curved bodies stay PEC.
  */
 int rt_set_face_materials(rt_scene *scene, const float *mat, int n_face);
+
+/*
+ * Candidate face sequences of a ray launch from the transmitter (the planar
+ * paths of large scenes).  The rule: n_rays
+ * directions of the spherical Fibonacci lattice z_i = 1 - (2i + 1)/n_rays,
+ * phi_i = i pi (3 - sqrt 5); each ray reflected specularly at the nearest
+ * triangle hit -- parameter > 1e-9, the face it leaves excluded, ties to the
+ * lower triangle index, curved bodies ignored -- up to max_order (1-3)
+ * times; every prefix of its face sequence is a candidate; the distinct
+ * ones sorted by order, then faces).  Host computation, FP64.
+ *   seq    host int32 [cap][3]: face ids, -1 padded; NULL to count only.
+ *   n_out  number of distinct sequences (those beyond cap are not written).
+ * Errors: RT_ERR_STATE without a transmitter, RT_ERR_ARG for bad sizes.
+ */
+int rt_candidates(rt_scene *scene, int n_rays, int max_order, int32_t *seq, int cap, int *n_out);
+
+/*
+ * The candidate list of the planar paths (orders 1-3): host int32
+ * [n][3], face ids with -1 padding at the end, no face twice in a row;
+ * copied.  With a list the planar class evaluates its sequences (up to the
+ * options' max_order) instead of every face and ordered face pair: the path
+ * list is exact for the candidate set.  Orders 1 and 2 are listed as
+ * RT_PATH_R1 / RT_PATH_R2 with their faces, order 3 as RT_PATH_R3 with the
+ * sequence's index.  The images are recomputed by every rt_set_tx.  n = 0
+ * clears the list.  Errors: RT_ERR_ARG (bad face id, repeat, n > RT_MAX_CANDIDATES).
+ */
+int rt_set_candidates(rt_scene *scene, const int32_t *seq, int n);
 
 /* Frequencies (host double[n_f], Hz, > 0), 1 <= n_f <= RT_MAX_FREQS. */
 int rt_set_freqs(rt_scene *scene, const double *f_hz, int n_f);

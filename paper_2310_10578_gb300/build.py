@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcreep.so")
-SOURCES = ["abi.cu", "eval_fields.cu", "fock_table.cu", "rx_order.cu", "peaks.cu"]
+SOURCES = ["abi.cu", "eval_fields.cu", "fock_table.cu", "rx_order.cu", "peaks.cu", "bvh.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: -ffp-contract=off so that host-side FP64 decisions (per-transmitter
 # precomputation) round as written on every host ISA

@@ -27,7 +27,8 @@ EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "
            "rt_last_error", "rt_batch_create", "rt_batch_destroy", "rt_batch_set_frame", "rt_batch_evaluate",
            "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats", "rt_backward", "rt_alu_peaks",
            "rt_evaluate_with_paths", "rt_batch_set_shape", "rt_batch_get_shape", "rt_batch_tune",
-           "rt_set_shape", "rt_get_shape", "rt_tune", "rt_set_face_materials")
+           "rt_set_shape", "rt_get_shape", "rt_tune", "rt_set_face_materials", "rt_candidates",
+           "rt_set_candidates")
 RT_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -95,6 +96,8 @@ def load(build_if_missing=True):
     lib.rt_get_shape.argtypes = [P, P]
     lib.rt_tune.argtypes = [P, P, I, P, P, P, P, P]
     lib.rt_set_face_materials.argtypes = [P, P, I]
+    lib.rt_candidates.argtypes = [P, I, I, P, I, ctypes.POINTER(I)]
+    lib.rt_set_candidates.argtypes = [P, P, I]
     _lib = lib
     return lib
 
@@ -158,7 +161,26 @@ class Scene:
         s.set_freqs(sc.freqs)
         if getattr(sc, "face_eps", None) is not None:
             s.set_face_materials(sc.face_eps)
+        if getattr(sc, "candidates", None) is not None:
+            s.set_candidates(sc.candidates)
         return s
+
+    def candidates(self, n_rays, max_order=3):
+        """Candidate face sequences [n, 3] int32 (-1 padded) of the ray launch
+        from the transmitter (rt_candidates; host computation)."""
+        n = ctypes.c_int(0)
+        _check(_lib.rt_candidates(self._h, int(n_rays), int(max_order), None, 0, ctypes.byref(n)))
+        out = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+        _check(_lib.rt_candidates(self._h, int(n_rays), int(max_order), _ptr(out), n.value, ctypes.byref(n)))
+        return out[:n.value]
+
+    def set_candidates(self, seq):
+        """The planar paths' candidate list (rt_set_candidates); None clears it."""
+        if seq is None:
+            _check(_lib.rt_set_candidates(self._h, None, 0))
+            return
+        a = np.ascontiguousarray(np.asarray(seq, dtype=np.int32).reshape(-1, 3))
+        _check(_lib.rt_set_candidates(self._h, _ptr(a), a.shape[0]))
 
     def set_face_materials(self, mat):
         """Per face (kind, eps', eps''): kind 0 PEC, 1 dielectric (eps' - j eps''); None: all PEC."""

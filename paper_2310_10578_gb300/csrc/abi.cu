@@ -128,6 +128,16 @@ struct rt_scene {
     float4 *d_txw = nullptr;            // the same for each face's source image, see DevScene::txw
     float4 *d_face_mat = nullptr;       // face materials, see DevScene::face_mat
     bool any_dielectric = false;
+    // large-scene mode: the triangle BVH (host copy for the ray launch; on the
+    // device above BVH_MIN_TRI triangles) and the candidate face sequences
+    std::vector<float4> h_bvh;
+    std::vector<int> h_bvh_tri;
+    float4 *d_bvh = nullptr;
+    int *d_bvh_tri = nullptr;
+    std::vector<int> cand;              // [n_cand][3]
+    int4 *d_cand = nullptr;
+    float4 *d_cimg = nullptr;           // [n_cand][3][2]
+    int n_cand = 0;
     unsigned long long *d_esc = nullptr;   // [CTR_N]: FP64-decided candidates, then one work queue per launch
     DevTable *table = nullptr;
     // state
@@ -172,7 +182,7 @@ static void free_scene(rt_scene *s) {
     cudaFree(s->d_tri); cudaFree(s->d_aux); cudaFree(s->d_face32); cudaFree(s->d_body);
     cudaFree(s->d_face64); cudaFree(s->d_face_rng); cudaFree(s->d_face_tris); cudaFree(s->d_freq); cudaFree(s->d_fqc);
     cudaFree(s->d_esc); cudaFree(s->io_rx); cudaFree(s->io_e); cudaFree(s->io_fl); cudaFree(s->d_img); cudaFree(s->d_txb);
-    cudaFree(s->d_txw);
+    cudaFree(s->d_txw); cudaFree(s->d_bvh); cudaFree(s->d_bvh_tri); cudaFree(s->d_cand); cudaFree(s->d_cimg);
     cudaFree(s->d_face_mat);
 }
 
@@ -401,9 +411,19 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
     CKS(cudaMalloc(&s->d_freq, sizeof(double) * RT_MAX_FREQS));
     CKS(cudaMalloc(&s->d_fqc, sizeof(FreqC) * ((RT_MAX_FREQS + NFC - 1) / NFC)));
     CKS(cudaMalloc(&s->d_esc, sizeof(unsigned long long) * CTR_N));
-    CKS(cudaMalloc(&s->d_img, sizeof(float4) * 2 * (nfc + nfc * nfc)));
+    // images of the source in every face and, for scenes the planar class
+    // enumerates, in every ordered face pair
+    const bool enum_faces = nf <= RT_MAX_ENUM_FACES;
+    CKS(cudaMalloc(&s->d_img, sizeof(float4) * 2 * (nfc + (enum_faces ? nfc * nfc : 0))));
     CKS(cudaMalloc(&s->d_txb, sizeof(float4) * 2 * nbd));
-    CKS(cudaMalloc(&s->d_txw, sizeof(float4) * 2 * nbd * nfc));
+    if (enum_faces) CKS(cudaMalloc(&s->d_txw, sizeof(float4) * 2 * nbd * nfc));
+    bvh_build(s->tri.data(), n_tri, s->h_bvh, s->h_bvh_tri);
+    if (n_tri > BVH_MIN_TRI) {
+        CKS(cudaMalloc(&s->d_bvh, sizeof(float4) * s->h_bvh.size()));
+        CKS(cudaMalloc(&s->d_bvh_tri, sizeof(int) * s->h_bvh_tri.size()));
+        CKS(cudaMemcpy(s->d_bvh, s->h_bvh.data(), sizeof(float4) * s->h_bvh.size(), cudaMemcpyHostToDevice));
+        CKS(cudaMemcpy(s->d_bvh_tri, s->h_bvh_tri.data(), sizeof(int) * s->h_bvh_tri.size(), cudaMemcpyHostToDevice));
+    }
     if (n_tri > 0) {
         CKS(cudaMemcpy(s->d_tri, htri.data(), sizeof(float4) * 3 * n_tri, cudaMemcpyHostToDevice));
         CKS(cudaMemcpy(s->d_aux, haux.data(), sizeof(float4) * 3 * n_tri, cudaMemcpyHostToDevice));
@@ -426,6 +446,8 @@ void rt_scene_destroy(rt_scene *s) {
     delete s;
 }
 
+static int upload_candidates(rt_scene *s);
+
 int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
     if (!s || !tx || !pol) return fail(RT_ERR_ARG, "rt_set_tx: NULL argument");
     for (int k = 0; k < 3; ++k)
@@ -445,7 +467,8 @@ int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
     // into float hi + lo: the planar path length is |P - image| (Eq. 3, image
     // method), exact to ~1e-14 for any receiver
     int nf = s->n_face;
-    std::vector<float4> img(2 * (size_t)(nf + nf * nf));
+    const bool enum_faces = nf <= RT_MAX_ENUM_FACES;
+    std::vector<float4> img(2 * (size_t)(nf + (enum_faces ? nf * nf : 0)));
     auto mirror = [&](const double X[3], int f, double Y[3]) {
         const FaceHost &F = s->faces[f];
         double dist = F.n[0] * X[0] + F.n[1] * X[1] + F.n[2] * X[2] - F.d;
@@ -461,7 +484,7 @@ int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
         double S1[3];
         mirror(p, i, S1);
         put(i, S1);
-        for (int j = 0; j < nf; ++j) {
+        for (int j = 0; j < nf && enum_faces; ++j) {
             double S2[3];
             mirror(S1, j, S2);
             put(nf + (size_t)i * nf + j, S2);
@@ -473,7 +496,7 @@ int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
     prep_txb(p, s->bodies.data(), s->n_body, txb.data());
     if (s->n_body > 0) CK(cudaMemcpy(s->d_txb, txb.data(), sizeof(float4) * 2 * s->n_body, cudaMemcpyHostToDevice));
     // and per face, the same for the source's mirror image (wall -> creeping)
-    if (s->n_body > 0 && nf > 0) {
+    if (s->n_body > 0 && nf > 0 && s->d_txw) {
         std::vector<float4> txw(2 * (size_t)s->n_body * nf);
         for (int f = 0; f < nf; ++f) {
             double S1[3];
@@ -484,6 +507,75 @@ int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
     }
     s->tx_set = true;
     ++s->tx_version;
+    if (s->n_cand > 0) return upload_candidates(s);
+    return RT_OK;
+}
+
+// The candidate list's device copy: the sequences and, per sequence, the
+// source's images after each of its reflections (FP64, as hi + lo floats).
+static int upload_candidates(rt_scene *s) {
+    const int n = s->n_cand;
+    cudaFree(s->d_cand); cudaFree(s->d_cimg);
+    s->d_cand = nullptr; s->d_cimg = nullptr;
+    if (n == 0) return RT_OK;
+    std::vector<int4> hc(n);
+    std::vector<float4> hi(6 * (size_t)n, make_float4(0.f, 0.f, 0.f, 0.f));
+    const double p[3] = {s->tx[0], s->tx[1], s->tx[2]};
+    for (int q = 0; q < n; ++q) {
+        const int *f = &s->cand[3 * (size_t)q];
+        const int k = (f[0] >= 0) + (f[1] >= 0) + (f[2] >= 0);
+        hc[q] = make_int4(f[0], f[1], f[2], k);
+        double X[3] = {p[0], p[1], p[2]};
+        for (int m = 0; m < k; ++m) {
+            const FaceHost &F = s->faces[f[m]];
+            double dist = F.n[0] * X[0] + F.n[1] * X[1] + F.n[2] * X[2] - F.d;
+            for (int c = 0; c < 3; ++c) X[c] = X[c] - F.n[c] * (2.0 * dist);
+            float h[3], l[3];
+            for (int c = 0; c < 3; ++c) { h[c] = (float)X[c]; l[c] = (float)(X[c] - (double)h[c]); }
+            hi[6 * (size_t)q + 2 * m] = make_float4(h[0], h[1], h[2], 0.f);
+            hi[6 * (size_t)q + 2 * m + 1] = make_float4(l[0], l[1], l[2], 0.f);
+        }
+    }
+    CK(cudaMalloc(&s->d_cand, sizeof(int4) * n));
+    CK(cudaMalloc(&s->d_cimg, sizeof(float4) * hi.size()));
+    CK(cudaMemcpy(s->d_cand, hc.data(), sizeof(int4) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(s->d_cimg, hi.data(), sizeof(float4) * hi.size(), cudaMemcpyHostToDevice));
+    return RT_OK;
+}
+
+int rt_set_candidates(rt_scene *s, const int32_t *seq, int n) {
+    if (!s || (n > 0 && !seq)) return fail(RT_ERR_ARG, "rt_set_candidates: NULL argument");
+    if (n < 0 || n > RT_MAX_CANDIDATES) return fail(RT_ERR_ARG, "rt_set_candidates: n = %d out of range", n);
+    for (int q = 0; q < n; ++q) {
+        const int32_t *f = seq + 3 * (size_t)q;
+        int k = 0;
+        while (k < 3 && f[k] >= 0) ++k;
+        if (k == 0) return fail(RT_ERR_ARG, "rt_set_candidates: sequence %d is empty", q);
+        for (int m = 0; m < 3; ++m) {
+            if (m < k && f[m] >= s->n_face) return fail(RT_ERR_ARG, "rt_set_candidates: bad face in sequence %d", q);
+            if (m >= k && f[m] != -1) return fail(RT_ERR_ARG, "rt_set_candidates: sequence %d not -1 padded", q);
+            if (m > 0 && m < k && f[m] == f[m - 1])
+                return fail(RT_ERR_ARG, "rt_set_candidates: face twice in a row in sequence %d", q);
+        }
+    }
+    s->cand.assign(seq, seq + 3 * (size_t)n);
+    s->n_cand = n;
+    if (!s->tx_set) return RT_OK;            // the images follow with the transmitter
+    return upload_candidates(s);
+}
+
+int rt_candidates(rt_scene *s, int n_rays, int max_order, int32_t *seq, int cap, int *n_out) {
+    if (!s || !n_out) return fail(RT_ERR_ARG, "rt_candidates: NULL argument");
+    if (n_rays < 1 || max_order < 1 || max_order > 3 || cap < 0 || (cap > 0 && !seq))
+        return fail(RT_ERR_ARG, "rt_candidates: bad n_rays, max_order or cap");
+    if (!s->tx_set) return fail(RT_ERR_STATE, "rt_candidates: transmitter not set");
+    const double p[3] = {s->tx[0], s->tx[1], s->tx[2]};
+    std::vector<int> out;
+    int n = ray_launch(s->tri.data(), s->tri_face.data(), s->n_tri, s->n_face, s->h_bvh, s->h_bvh_tri, p, n_rays,
+                       max_order, out);
+    for (int q = 0; q < n && q < cap; ++q)
+        for (int m = 0; m < 3; ++m) seq[3 * (size_t)q + m] = out[3 * (size_t)q + m];
+    *n_out = n;
     return RT_OK;
 }
 
@@ -532,6 +624,12 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, 
     if (o.max_order < 0 || o.max_order > 2) return fail(RT_ERR_ARG, "max_order %d not in [0, 2]", o.max_order);
     if (o.precision != RT_PREC_FP32 && o.precision != RT_PREC_FP64) return fail(RT_ERR_ARG, "bad precision %d", o.precision);
     if (o.enable & ~(RT_EN_ALL | RT_EN_WALL_CREEP)) return fail(RT_ERR_ARG, "bad enable mask 0x%x", o.enable);
+    if (s->n_face > RT_MAX_ENUM_FACES) {
+        if ((o.enable & RT_EN_PLANAR) && o.max_order >= 1 && s->n_cand == 0)
+            return fail(RT_ERR_STATE, "%d faces: planar paths need a candidate list (rt_set_candidates)", s->n_face);
+        if (o.enable & RT_EN_WALL_CREEP)
+            return fail(RT_ERR_ARG, "wall -> creeping paths: at most %d faces", RT_MAX_ENUM_FACES);
+    }
     if (!s->tx_set || (need_freqs && !s->f_set)) return fail(RT_ERR_STATE, "transmitter or frequencies not set");
     memset(&D, 0, sizeof(D));
     D.n_tri = s->n_tri; D.n_face = s->n_face; D.n_body = s->n_body; D.n_f = (int)s->freqs.size();
@@ -546,6 +644,11 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, 
     D.img = s->d_img;
     D.txb = s->d_txb;
     D.txw = s->d_txw;
+    D.bvh = s->d_bvh;
+    D.bvh_tri = s->d_bvh_tri;
+    D.cand = s->n_cand > 0 ? s->d_cand : nullptr;
+    D.cimg = s->d_cimg;
+    D.n_cand = s->n_cand;
     D.face_mat = s->any_dielectric ? s->d_face_mat : nullptr;
     memcpy(D.tx, s->tx, sizeof(D.tx));
     memcpy(D.pol, s->pol, sizeof(D.pol));

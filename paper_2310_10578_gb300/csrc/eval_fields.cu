@@ -28,10 +28,11 @@ namespace creep {
 
 #define EPS_TRIM 1e-6
 enum { D_NO = 0, D_YES = 1, D_UNSURE = 2 };
-enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5, PT_WCP = 6, PT_WCM = 7 };
+enum { PT_LOS = 0, PT_R1 = 1, PT_R2 = 2, PT_RB = 3, PT_CP = 4, PT_CM = 5, PT_WCP = 6, PT_WCM = 7, PT_R3 = 8 };
 
 constexpr int BLOCK = 128;
 constexpr int SMEM_TRI_MAX = 256;
+constexpr int SMEM_FACE_MAX = 512;
 constexpr int SMEM_BODY_MAX = 256;
 
 __device__ __forceinline__ uint64_t pcode(int type, int a, int b) {
@@ -67,6 +68,11 @@ struct Ctx {
     const float4 *img;           // source images (double-float), see DevScene
     const float4 *txb;           // [n_body][2] source-side body frame, see DevScene
     const float4 *txw;           // [n_face][n_body][2] the same for each face's source image (or nullptr)
+    const float4 *bvh;           // triangle BVH, see DevScene (nullptr: every triangle is tested)
+    const int *bvh_tri;
+    const int4 *cand;            // candidate face sequences, see DevScene (n_cand = 0: every face and pair)
+    const float4 *cimg;
+    int n_cand;
     const float4 *face_mat;      // face materials, see DevScene (nullptr: all PEC)
     int enc;                     // this launch's creeping rays: extra full turns round the body
     // occluder masks (FP32 body kernels): occ_w words per body; word w of
@@ -199,6 +205,73 @@ __device__ int seg_body(const Ctx &c, int b, v3t<dx> A, v3t<dx> B, dx) {
     return (olo < hi && ohi > lo) ? D_YES : D_NO;
 }
 
+// The segment A + t D, t in [0, 1], meets the box [lo, hi] grown by m?
+// (the host grows every box by more than the rounding of this test)
+template <typename T>
+__device__ __forceinline__ bool seg_box(v3t<T> A, v3t<T> D, const float4 &lo, const float4 &hi, T m) {
+    T t0 = T(0), t1 = T(1);
+    const T a[3] = {A.x, A.y, A.z}, d[3] = {D.x, D.y, D.z};
+    const T l[3] = {T((double)lo.x) - m, T((double)lo.y) - m, T((double)lo.z) - m};
+    const T h[3] = {T((double)hi.x) + m, T((double)hi.y) + m, T((double)hi.z) + m};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        if (d[k] == T(0)) {
+            if (a[k] < l[k] || a[k] > h[k]) return false;
+            continue;
+        }
+        T u = (l[k] - a[k]) / d[k], v = (h[k] - a[k]) / d[k];
+        if (u > v) { T w = u; u = v; v = w; }
+        t0 = Fmax(t0, u);
+        t1 = Fmin(t1, v);
+        if (t0 > t1) return false;
+    }
+    return true;
+}
+// Triangles (those of faces sf1/sf2 skipped) through the BVH: 0 none hit, 1
+// hit, 2 unsure.  FP64: each triangle is tested in FP32 on the rounded
+// endpoints first, in FP64 only where that is uncertain.
+template <typename T>
+__device__ __forceinline__ int tris_bvh(const Ctx &c, v3t<T> A, v3t<T> B, int sf1, int sf2, T band) {
+    const v3t<T> D = B - A;
+    v3t<float> Af, Bf;
+    if constexpr (sizeof(T) == 4) {
+        Af = A; Bf = B;
+    } else {
+        Af = mk3<float>(to_float(A.x), to_float(A.y), to_float(A.z));
+        Bf = mk3<float>(to_float(B.x), to_float(B.y), to_float(B.z));
+    }
+    int stk[32];
+    int sp = 0, uns = 0;
+    stk[sp++] = 0;
+    while (sp > 0) {
+        const int nd = stk[--sp];
+        const float4 lo = c.bvh[2 * nd], hi = c.bvh[2 * nd + 1];
+        if (!seg_box<T>(A, D, lo, hi, band)) continue;
+        const int first = __float_as_int(lo.w), count = __float_as_int(hi.w);
+        if (count == 0) {
+            if (sp + 2 > 32) { uns = 1; continue; }    // (the host build is at most 32 deep)
+            stk[sp++] = first + 1;
+            stk[sp++] = first;
+            continue;
+        }
+        for (int j = first; j < first + count; ++j) {
+            const int t = c.bvh_tri[j];
+            const int f = __float_as_int(c.tri[3 * t].w);
+            if (f == sf1 || f == sf2) continue;
+            int r;
+            if constexpr (sizeof(T) == 4) {
+                r = seg_tri(c, t, Af, Bf, c.band);
+            } else {
+                r = seg_tri(c, t, Af, Bf, c.band);
+                if (r == D_UNSURE) r = seg_tri(c, t, A, B, band);
+            }
+            if (r == D_YES) return D_YES;
+            uns |= (r == D_UNSURE);
+        }
+    }
+    return uns ? D_UNSURE : D_NO;
+}
+
 // 0 visible, 1 blocked, 2 unsure.  Faces sf1/sf2 and body sb are skipped.
 template <typename T>
 __device__ __forceinline__ int blocked_impl(const Ctx &c, v3t<T> A, v3t<T> B, int sf1, int sf2, int sb, T band) {
@@ -206,8 +279,14 @@ __device__ __forceinline__ int blocked_impl(const Ctx &c, v3t<T> A, v3t<T> B, in
     if constexpr (sizeof(T) == 4) {
         // faces first: both ends clearly on one side of a face's plane => none of
         // its triangles can be hit (the plane tests of all faces are made
-        // branch-free; only the faces left over are looked at)
-        for (int f0 = 0; f0 < c.n_face; f0 += 32) {
+        // branch-free; only the faces left over are looked at); large scenes
+        // through the BVH
+        if (c.bvh) {
+            const int r = tris_bvh(c, A, B, sf1, sf2, band);
+            if (r == D_YES) return D_YES;
+            uns = (r == D_UNSURE);
+        }
+        for (int f0 = 0; f0 < (c.bvh ? 0 : c.n_face); f0 += 32) {
             unsigned keep = 0;
             const int nfc = min(32, c.n_face - f0);
 #pragma unroll 4
@@ -234,7 +313,10 @@ __device__ __forceinline__ int blocked_impl(const Ctx &c, v3t<T> A, v3t<T> B, in
         // the rounding of the endpoints); only an uncertain one is tested in FP64
         v3t<float> Af = mk3<float>(to_float(A.x), to_float(A.y), to_float(A.z));
         v3t<float> Bf = mk3<float>(to_float(B.x), to_float(B.y), to_float(B.z));
-        for (int t = 0; t < c.n_tri; ++t) {
+        if (c.bvh) {
+            if (tris_bvh(c, A, B, sf1, sf2, band) == D_YES) return D_YES;
+        }
+        for (int t = 0; t < (c.bvh ? 0 : c.n_tri); ++t) {
             int f = __float_as_int(c.tri[3 * t].w);
             if (f == sf1 || f == sf2) continue;
             int r = seg_tri(c, t, Af, Bf, c.band);
@@ -489,6 +571,47 @@ __device__ int cand_r2(const Ctx &c, int i, int j, v3t<T> S, v3t<T> P, T band, G
     if (!conj(acc, vis_to_dec(blocked(c, Q1, Q2, i, j, -1, band)))) return D_NO;
     if (!conj(acc, vis_to_dec(blocked(c, Q2, P, j, -1, -1, band)))) return D_NO;
     g.Q1 = Q1; g.Q2 = Q2;
+    return acc;
+}
+
+// candidate face sequence q of order k = sq.w (large-scene mode): the
+// source's images after each reflection from the candidate table (FP32: hi;
+// FP64: hi + lo); backwards from P, Q_m is where image m -> Q_{m+1} crosses
+// face sq[m]'s plane (the two strictly on opposite sides) and lies in the
+// face; then every leg clear but of the faces at its ends
+template <typename T>
+__device__ __forceinline__ v3t<T> cand_image(const Ctx &c, int q, int m) {
+    const float4 h = c.cimg[6 * q + 2 * m];
+    if constexpr (sizeof(T) == 4) {
+        return mk3(h.x, h.y, h.z);
+    } else {
+        const float4 l = c.cimg[6 * q + 2 * m + 1];
+        return mk3<T>(T((double)h.x + (double)l.x), T((double)h.y + (double)l.y), T((double)h.z + (double)l.z));
+    }
+}
+template <typename T>
+__device__ int cand_seq(const Ctx &c, int q, int4 sq, v3t<T> S, v3t<T> P, T band, v3t<T> Q[3]) {
+    const int k = sq.w;
+    const int fs[3] = {sq.x, sq.y, sq.z};
+    int acc = D_YES;
+    v3t<T> X = P;
+#pragma unroll
+    for (int m = 2; m >= 0; --m) {
+        if (m >= k) continue;
+        v3t<T> n; T d;
+        face_plane<T>(c, fs[m], &n, &d);
+        const v3t<T> I = cand_image<T>(c, q, m);
+        const T di = dot3(n, I) - d, dX = dot3(n, X) - d;
+        if (!conj(acc, side_dec(di, dX, band, false))) return D_NO;
+        Q[m] = I + (X - I) * (di / (di - dX));
+        if (!conj(acc, in_face(c, fs[m], Q[m], band))) return D_NO;
+        X = Q[m];
+    }
+    if (!conj(acc, vis_to_dec(blocked(c, S, Q[0], fs[0], -1, -1, band)))) return D_NO;
+    if (k >= 2 && !conj(acc, vis_to_dec(blocked(c, Q[0], Q[1], fs[0], fs[1], -1, band)))) return D_NO;
+    if (k >= 3 && !conj(acc, vis_to_dec(blocked(c, Q[1], Q[2], fs[1], fs[2], -1, band)))) return D_NO;
+    const v3t<T> E = (k == 1) ? Q[0] : ((k == 2) ? Q[1] : Q[2]);
+    if (!conj(acc, vis_to_dec(blocked(c, E, P, fs[k - 1], -1, -1, band)))) return D_NO;
     return acc;
 }
 
@@ -1359,6 +1482,38 @@ __device__ __noinline__ void add_planar_dielectric(const Ctx &c, AccS<T> &acc, c
     }
 }
 __device__ __forceinline__ bool dielectric(const Ctx &c, int f) { return c.face_mat && f >= 0 && c.face_mat[f].x != 0.0f; }
+// candidate sequence path S -> Q[0] .. Q[k-1] -> P (faces fs): the source's
+// polarisation reflected at each point (PEC mirror or Fresnel), the ray at
+// every chunk
+template <typename T, typename L>
+__device__ __noinline__ void add_seq_field(const Ctx &c, AccS<T> &acc, const FreqC *fqs, int nfq, v3t<T> S,
+                                           const v3t<T> Q[3], v3t<T> P, int4 sq, T amp, L len) {
+    const int k = sq.w;
+    const int fs[3] = {sq.x, sq.y, sq.z};
+    v3t<T> din = unit3(Q[0] - S);
+    const v3t<T> e0 = src_pol(c, din);
+    if (!dielectric(c, fs[0]) && !(k >= 2 && dielectric(c, fs[1])) && !(k >= 3 && dielectric(c, fs[2]))) {
+        v3t<T> e = e0;
+        for (int m = 0; m < k; ++m) {
+            v3t<T> n; T d;
+            face_plane<T>(c, fs[m], &n, &d);
+            e = pec_mirror(e, n);
+        }
+        add_ray_chunks(acc, fqs, nfq, e, amp, len);
+        return;
+    }
+    cpx<T> E[3] = {mkc<T>(e0.x, T(0)), mkc<T>(e0.y, T(0)), mkc<T>(e0.z, T(0))};
+    for (int m = 0; m < k; ++m) {
+        const v3t<T> dout = unit3((m + 1 < k ? Q[m + 1] : P) - Q[m]);
+        reflect_face(c, fs[m], E, din, dout);
+        din = dout;
+    }
+#pragma unroll 1
+    for (int ch = 0; ch < nfq; ++ch) {
+        AccS<T> a{acc.p + ch * (NFC * 6 * 32)};
+        add_ray_cx(a, fqs[ch], E, amp, len);
+    }
+}
 
 template <typename T>
 __device__ __forceinline__ void acc_zero_rows(AccS<T> &acc, int rows) {
@@ -1696,6 +1851,13 @@ __device__ __noinline__ int esc_r2(const Ctx &c, int i, int j, v3t<float> Pf, v3
     if (d == D_YES) { *Q1 = to_f3(g.Q1); *Q2 = to_f3(g.Q2); }
     return d;
 }
+__device__ __noinline__ int esc_seq(const Ctx &c, int q, int4 sq, v3t<float> Pf, v3t<float> Q[3]) {
+    v3t<dx> Qd[3];
+    int d = cand_seq<dx>(c, q, sq, dxv(c.S), dxv(Pf), dx(0.0), Qd);
+    if (d == D_YES)
+        for (int m = 0; m < sq.w; ++m) Q[m] = to_f3(Qd[m]);
+    return d;
+}
 // body reflection decided and (field = true) evaluated in FP64
 __device__ __noinline__ int esc_rb(const Ctx &c, int b, v3t<float> Pf, const FreqC &fq, bool field, Contrib *out,
                                    float *rec) {
@@ -1808,7 +1970,9 @@ __device__ __noinline__ int esc_wcreep(const Ctx &c, int wf, int b, int dir, v3t
 enum { CLS_PLANAR = 1,        // direct ray and planar image reflections
        CLS_BODYREFL = 2,      // GO reflection off each curved body
        CLS_CREEP = 4,         // creeping rays round each curved body
-       CLS_WCREEP = 8 };      // creeping rays fed by a planar reflection (a work unit: face x body)
+       CLS_WCREEP = 8,        // creeping rays fed by a planar reflection (a work unit: face x body)
+       CLS_SEQ = 16 };        // direct ray and the planar paths of the candidate list (large scenes)
+constexpr bool is_planar(int cls) { return cls == CLS_PLANAR || cls == CLS_SEQ; }
 constexpr int CLS_BODIES = CLS_BODYREFL | CLS_CREEP | CLS_WCREEP;
 // Block shape.  The body classes run one block of 12 warps per SM: three
 // tiles at a time, four warps per tile; a block barrier between the geometry
@@ -1817,7 +1981,7 @@ constexpr int CLS_BODIES = CLS_BODYREFL | CLS_CREEP | CLS_WCREEP;
 // the FP64 path, run 4-warp blocks, several per SM.
 constexpr int blk_of(int cls, bool fp32) { return ((cls & CLS_BODIES) && fp32) ? 384 : BLOCK; }
 constexpr int min_blocks(int cls, bool fp32) {
-    return ((cls & CLS_BODIES) && fp32) ? 1 : (cls == CLS_PLANAR ? 4 : 3);
+    return ((cls & CLS_BODIES) && fp32) ? 1 : (is_planar(cls) ? 4 : 3);
 }
 // records per work unit of a body class (FP32 fields)
 constexpr int recs_per_unit(int cls) {
@@ -1923,7 +2087,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
     if (inside) {
         fl |= RT_FLAG_INSIDE;
     } else {
-        if constexpr ((CLS & CLS_PLANAR) != 0) {
+        if constexpr ((CLS & (CLS_PLANAR | CLS_SEQ)) != 0) {
             // ---- direct ray (candidate 0)
             if ((enable & RT_EN_LOS) && part == 0) {
                 int d = cand_los<T>(c, Sx, P, band);
@@ -1936,7 +2100,38 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                     }
                 }
             }
-            // ---- planar image reflections
+            // ---- planar image reflections: the candidate sequences (large
+            // scenes), else every face and ordered face pair
+            if constexpr (CLS == CLS_SEQ) {
+              if ((enable & RT_EN_PLANAR) && max_order >= 1) {
+#pragma unroll 1
+                for (int q = 0; q < c.n_cand; ++q) {
+                    if ((1 + q) % nparts != part) continue;
+                    const int4 sq = c.cand[q];
+                    if (sq.w > max_order) continue;
+                    v3t<T> Q[3];
+                    int d = cand_seq<T>(c, q, sq, Sx, P, band, Q);
+                    if constexpr (sizeof(T) == 4) {
+                        if (d == D_UNSURE) { escalated(); d = esc_seq(c, q, sq, Pf, Q); }
+                    }
+                    if (d != D_YES) continue;
+                    if (sq.w == 1) emit(PT_R1, sq.x, 0);
+                    else if (sq.w == 2) emit(PT_R2, sq.x, sq.y);
+                    else emit(PT_R3, q, 0);
+                    if (!PATHS) {
+                        LT L;
+                        if constexpr (sizeof(T) == 4) {
+                            L = df_dist_df(c.cimg[6 * q + 2 * (sq.w - 1)], c.cimg[6 * q + 2 * (sq.w - 1) + 1], Pf);
+                        } else {
+                            L = seglen(Sx, Q[0]);
+                            for (int m = 0; m + 1 < sq.w; ++m) L = ladd(L, seglen(Q[m], Q[m + 1]));
+                            L = ladd(L, seglen(Q[sq.w - 1], P));
+                        }
+                        add_seq_field(c, acc, fqs, nfq, Sx, Q, P, sq, T(1) / (T)len_val(L), L);
+                    }
+                }
+              }
+            } else {
             if ((enable & RT_EN_PLANAR) && max_order >= 1) {
 #pragma unroll 1
                 for (int i = 0; i < c.n_face; ++i) {
@@ -2001,6 +2196,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                     }
                 }
             }
+            }   // enumeration
         }
         // ---- curved bodies b_begin .. b_end - 1 (this share: every nparts-th)
         if constexpr (BODIES) {
@@ -2265,7 +2461,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
     float4 *s_res = s_fock + n_fock;                         // n_res
     float4 *s_face = s_res + n_res;                          // n_face
     bool body_sm = S.n_body <= SMEM_BODY_MAX;
-    float4 *s_body = s_face + S.n_face;                      // n_body * 2 (if staged)
+    const bool face_sm = S.n_face <= SMEM_FACE_MAX;
+    float4 *s_body = s_face + (face_sm ? S.n_face : 0);      // n_body * 2 (if staged)
     bool tri_sm = S.n_tri <= SMEM_TRI_MAX;
     float4 *s_tri = s_body + (body_sm ? 2 * S.n_body : 0);   // n_tri * 3 (if staged)
     float4 *s_aux = s_tri + (tri_sm ? 3 * S.n_tri : 0);      // n_tri * 3 (if staged)
@@ -2274,7 +2471,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
     float *s_rec = s_weid + WEIDEMAN_N;                      // path records (FP32 fields of the body classes)
     for (int i = threadIdx.x; i < n_fock; i += blockDim.x) s_fock[i] = S.fock32[i];
     for (int i = threadIdx.x; i < n_res; i += blockDim.x) s_res[i] = S.res32[i];
-    for (int i = threadIdx.x; i < S.n_face; i += blockDim.x) s_face[i] = S.face32[i];
+    if (face_sm)
+        for (int i = threadIdx.x; i < S.n_face; i += blockDim.x) s_face[i] = S.face32[i];
     // the frame's bodies, source-side body frames and frequency chunks (one
     // frame: F1; a batch: staged again whenever the block's next work unit is
     // in another frame)
@@ -2295,7 +2493,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         Ctx &c = s_ctx;
         c.tri = tri_sm ? s_tri : S.tri;
         c.tri_aux = tri_sm ? s_aux : S.tri_alt;
-        c.face32 = s_face;
+        c.face32 = face_sm ? s_face : S.face32;
         c.face64 = S.face64;
         c.face_rng = S.face_rng;
         c.face_tris = S.face_tris;
@@ -2313,6 +2511,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         c.occ_w = 0;
         c.enc = enc;
         c.txw = frames ? nullptr : S.txw;
+        c.bvh = S.bvh; c.bvh_tri = S.bvh_tri;
+        c.cand = S.cand; c.cimg = S.cimg; c.n_cand = S.cand ? S.n_cand : 0;
 
     }
     __syncthreads();
@@ -2402,7 +2602,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         // planar kernel ("wide") keeps the rows of all nch chunks at once in
         // the dynamic region (it has no path records), so one geometry pass
         // serves every chunk
-        constexpr bool WIDE = (CLS == CLS_PLANAR) && sizeof(T) == 4;
+        constexpr bool WIDE = is_planar(CLS) && sizeof(T) == 4;
         __shared__ T s_part_st[NW][WIDE ? 1 : NFC * 6][32];
         const int prow = WIDE ? nch * NFC * 6 : NFC * 6;
         T *s_part = WIDE ? reinterpret_cast<T *>(s_rec) : &s_part_st[0][0][0];
@@ -2556,7 +2756,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
 // (body classes) or the wide partial sums of wide_chunks chunks (planar)
 static size_t smem_bytes(const DevScene &S, bool bodies, bool records, int blk, int rcap, int wide_chunks,
                          int occ_sets) {
-    size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + S.n_face;
+    size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + (S.n_face <= SMEM_FACE_MAX ? S.n_face : 0);
     if (S.n_body <= SMEM_BODY_MAX) n += 4 * S.n_body;
     if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;
     const int occ_w = (occ_sets > 0 && S.n_body > 0 && S.n_body <= OCC_MAX_BODIES) ? (S.n_body + 31) >> 5 : 0;
@@ -2606,7 +2806,7 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     // records per lane: one frequency chunk flushes full buffers on the way
     // (5 is enough); several chunks size the body range by the capacity
     const int rcap = (nch > 1) ? 6 : 5;
-    const bool wide = CLS == CLS_PLANAR && sizeof(T) == 4 && !PATHS;
+    const bool wide = is_planar(CLS) && sizeof(T) == 4 && !PATHS;
     if (nch < 1 || nch > MAX_CHUNKS || (!wide && !bodies && nch != 1)) return cudaErrorInvalidValue;
     // occluder masks (FP32 body kernels): one source-side set, and one
     // receiver-side set per tile in flight (fields) or per warp (path lists)
@@ -2664,7 +2864,8 @@ static cudaError_t launch_all(const DevScene &S, const Work &W, int nchunks, Lau
                                                                                                   : PLANAR_CHUNKS);
     for (int ch = 0; ch < nchunks && e == cudaSuccess; ch += pstep) {
         const int n = nchunks - ch < pstep ? nchunks - ch : pstep;
-        e = launch_one<T, PATHS, CLS_PLANAR, LIST>(S, W, ch, n, 0, L);
+        e = (S.cand && S.n_cand > 0) ? launch_one<T, PATHS, CLS_SEQ, LIST>(S, W, ch, n, 0, L)
+                                     : launch_one<T, PATHS, CLS_PLANAR, LIST>(S, W, ch, n, 0, L);
         if (chunked_bodies && e == cudaSuccess) e = launch_one<T, PATHS, CLS_BODYREFL, LIST>(S, W, ch, 1, 1, L);
         for (int enc = 0; chunked_bodies && enc <= S.max_enc && e == cudaSuccess; ++enc)
             e = launch_one<T, PATHS, CLS_CREEP, LIST>(S, W, ch, 1, 1, L, enc);
@@ -3055,6 +3256,36 @@ __device__ __noinline__ void adj_planar(const Ctx &c, int order, int i, int j, v
     }
 }
 
+// order-3 candidate path (faces fs, the candidate list's sequence): the
+// images by mirroring the dual-number source, the points backwards from P
+__device__ __noinline__ void adj_seq3(const Ctx &c, int4 sq, v3t<D8> S, v3t<D8> P, const FreqC &fq, AccAdj &acc) {
+    const int fs[3] = {sq.x, sq.y, sq.z};
+    v3t<D8> n[3], I[3], Q[3];
+    D8 d[3];
+    v3t<D8> X = S;
+    for (int m = 0; m < 3; ++m) {
+        face_plane<D8>(c, fs[m], &n[m], &d[m]);
+        X = mirror_pt(X, n[m], d[m]);
+        I[m] = X;
+    }
+    X = P;
+    for (int m = 2; m >= 0; --m) {
+        const D8 di = dot3(n[m], I[m]) - d[m], dX = dot3(n[m], X) - d[m];
+        Q[m] = I[m] + (X - I[m]) * (di / (di - dX));
+        X = Q[m];
+    }
+    const D8 L = norm3(Q[0] - S) + norm3(Q[1] - Q[0]) + norm3(Q[2] - Q[1]) + norm3(P - Q[2]);
+    v3t<D8> din = unit3(Q[0] - S);
+    const v3t<D8> e0 = src_pol(c, din);
+    cpx<D8> E[3] = {mkc<D8>(e0.x, D8(0.0)), mkc<D8>(e0.y, D8(0.0)), mkc<D8>(e0.z, D8(0.0))};
+    for (int m = 0; m < 3; ++m) {
+        const v3t<D8> dout = unit3((m < 2 ? Q[m + 1] : P) - Q[m]);
+        reflect_face(c, fs[m], E, din, dout);
+        din = dout;
+    }
+    add_ray_cx(acc, fq, E, D8(1.0) / L, L);
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -3079,6 +3310,8 @@ __global__ void __launch_bounds__(128) k_adjoint(DevScene S, const float *__rest
     c.fock = nullptr; c.res = nullptr; c.weid = nullptr; c.weid_L = S.weid_L;
     c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
     c.img = S.img; c.txb = S.txb; c.occ_src = nullptr; c.occ_w = 0; c.face_mat = S.face_mat;
+    c.txw = S.txw; c.bvh = S.bvh; c.bvh_tri = S.bvh_tri;
+    c.cand = S.cand; c.cimg = S.cimg; c.n_cand = S.cand ? S.n_cand : 0;
     const int lane = threadIdx.x & 31;
     const int nch = (S.n_f + NFC - 1) / NFC;
     const v3t<D8> Sd = mk3<D8>(dvar(c.S.x, DS_SX), dvar(c.S.y, DS_SY), dvar(c.S.z, DS_SZ));
@@ -3107,6 +3340,7 @@ __global__ void __launch_bounds__(128) k_adjoint(DevScene S, const float *__rest
                     if (type == PT_LOS) adj_planar(c, 0, -1, -1, Sd, Pd, fq, acc);
                     else if (type == PT_R1) adj_planar(c, 1, id1, -1, Sd, Pd, fq, acc);
                     else if (type == PT_R2) adj_planar(c, 2, id1, id2, Sd, Pd, fq, acc);
+                    else if (type == PT_R3 && c.cand && id1 < c.n_cand) adj_seq3(c, c.cand[id1], Sd, Pd, fq, acc);
                     else if (type == PT_RB) { adj_rb(c, id1, Sd, Pd, fq, acc); body = id1; }
                     else if (type == PT_CP || type == PT_CM) {
                         if (adj_creep(c, id1, type == PT_CM, id2, Sd, Pd, fq, S.enable, acc)) body = id1;

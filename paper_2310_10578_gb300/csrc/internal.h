@@ -76,6 +76,13 @@ struct DevScene {
                                // nullptr when every face is PEC
     const float4 *txb;         // [n_body][2] per transmitter, FP64-computed: (u, |S - c|), (beta_s, sqrt(|S-c|^2 - a^2) hi, lo,
                                // lateral paths possible ? 1 : 0); cylinders use horizontal distances
+    const float4 *bvh;         // triangle BVH (nullptr: small scene, every triangle is tested); node i:
+                               // (box min, first), (box max, count); count > 0 leaf over bvh_tri[first ..
+                               // first + count), else children first, first + 1 (ints as float bits)
+    const int *bvh_tri;        // triangle ids in leaf order
+    const int4 *cand;          // [n_cand] candidate face sequences (f0, f1, f2, order), -1 padded, or nullptr
+    const float4 *cimg;        // [n_cand][3][2]: the source's image after 1, 2, 3 reflections (hi, lo)
+    int n_cand;
     const float4 *txw;         // [n_face][n_body][2]: as txb, for the source's mirror image in each face
                                // (wall -> creeping paths); nullptr in batches
     const double *freq;        // [n_f] Hz (host copy, read by the launcher)
@@ -107,6 +114,13 @@ struct FrameDev {
 
 // Device counters of one evaluation: [0] candidates decided in FP64, [1 + i]
 // the work queue of launch i.  Zeroed by the caller before launch_eval.
+// Host side of the large-scene mode (bvh.cu): the triangle BVH (layout of
+// DevScene::bvh) and the candidate face sequences of a ray launch.
+void bvh_build(const float *tri, int n_tri, std::vector<float4> &nodes, std::vector<int> &order);
+int ray_launch(const float *tri, const int *tri_face, int n_tri, int n_face, const std::vector<float4> &nodes,
+               const std::vector<int> &order, const double tx[3], int n_rays, int max_order, std::vector<int> &seq);
+constexpr int BVH_MIN_TRI = 64;        // scenes with more triangles traverse the BVH on the device
+
 constexpr int CTR_QUEUES = 256;
 constexpr int CTR_N = 1 + CTR_QUEUES;
 

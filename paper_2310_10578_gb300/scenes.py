@@ -47,6 +47,7 @@ class Scene:
         self.face_eps = None if face_eps is None else np.asarray(face_eps, dtype=np.float32).reshape(-1, 3)
         self.max_enc = 0          # extra encirclements of the creeping rays
         self.wall_creep = False   # creeping rays fed by one planar reflection
+        self.candidates = None    # candidate face sequences [n, 3] of the planar paths (large scenes)
 
     @property
     def n_rx(self):
@@ -61,6 +62,7 @@ class Scene:
                     self.rx[idx], name or self.name + "[sub]", self.max_order, self.face_eps)
         sub.max_enc = self.max_enc
         sub.wall_creep = self.wall_creep
+        sub.candidates = self.candidates
         return sub
 
 
@@ -141,6 +143,92 @@ def room(n_cyl=20, nx=256, ny=256, freqs=(2.4e9, 5.8e9, 28e9), seed=SEED_BASE + 
     if face_eps is not None:
         fe = [(0.0, 0.0, 0.0) if e is None else (1.0, float(e[0]), float(e[1])) for e in face_eps]
     return Scene(tri, face, bodies, tx, pol, freqs, rx, name, max_order=max_order, face_eps=fe)
+
+
+def box_mesh(x0, x1, y0, y1, z0, z1, face0):
+    """An axis-aligned box as 12 triangles, 2 per side, face ids face0 ..
+    face0 + 5 (bottom, top, x0, x1, y0, y1)."""
+    quads = [
+        [(x0, y0, z0), (x1, y0, z0), (x1, y1, z0), (x0, y1, z0)],
+        [(x0, y0, z1), (x0, y1, z1), (x1, y1, z1), (x1, y0, z1)],
+        [(x0, y0, z0), (x0, y1, z0), (x0, y1, z1), (x0, y0, z1)],
+        [(x1, y0, z0), (x1, y0, z1), (x1, y1, z1), (x1, y1, z0)],
+        [(x0, y0, z0), (x0, y0, z1), (x1, y0, z1), (x1, y0, z0)],
+        [(x0, y1, z0), (x1, y1, z0), (x1, y1, z1), (x0, y1, z1)],
+    ]
+    tri, face = [], []
+    for f, q in enumerate(quads):
+        tri.append([q[0], q[1], q[2]]); face.append(face0 + f)
+        tri.append([q[0], q[2], q[3]]); face.append(face0 + f)
+    return tri, face
+
+
+def office(n_rooms=(20, 15), room=(5.0, 4.0), height=3.0, n_furn=15000, n_cyl=100, n_sph=10, n_tx=4,
+           nx=1250, ny=800, freqs=(5.8e9,), seed=SEED_BASE + 5, wall=0.12, door=1.0, rx_z=1.2, max_order=3):
+    """Large office: a building of n_rooms[0] x n_rooms[1] rooms of room[0] x
+    room[1] m, as axis-aligned boxes -- the outer shell, interior wall panels
+    (thickness `wall`, a door gap of `door` m in every wall between two
+    rooms) and furniture boxes on the floor with sides and height uniform in
+    0.3-2 m -- each box 12 triangles and 6 faces; n_cyl PEC cylinders
+    (radius 0.15-0.25 m, 1.7 m high) and n_sph PEC spheres (radius 0.1-0.4
+    m, centre 0.5-2 m high); n_tx transmitters at 2.5 m in distinct room
+    centres (scene.txs; scene.tx is the first); receivers on an nx x ny grid
+    at rx_z.  Default: about 195k triangles, 1M receivers, 5.8 GHz."""
+    rng = np.random.default_rng(seed)
+    nrx, nry = n_rooms
+    lx, ly = nrx * room[0], nry * room[1]
+    tri, face = box_mesh(0.0, lx, 0.0, ly, 0.0, height, 0)
+    nf = 6
+
+    def add(x0, x1, y0, y1, z0, z1):
+        nonlocal nf
+        t, f = box_mesh(x0, x1, y0, y1, z0, z1, nf)
+        tri.extend(t); face.extend(f)
+        nf += 6
+
+    h = wall / 2
+    for j in range(1, nry):                      # walls along x between room rows
+        y = j * room[1]
+        for i in range(nrx):
+            xa, xb = i * room[0], (i + 1) * room[0]
+            g = rng.uniform(xa + 0.5, xb - 0.5 - door)
+            add(xa, g, y - h, y + h, 0.0, height)
+            add(g + door, xb, y - h, y + h, 0.0, height)
+    for i in range(1, nrx):                      # walls along y between room columns
+        x = i * room[0]
+        for j in range(nry):
+            ya, yb = j * room[1], (j + 1) * room[1]
+            g = rng.uniform(ya + 0.5, yb - 0.5 - door)
+            add(x - h, x + h, ya, g, 0.0, height)
+            add(x - h, x + h, g + door, yb, 0.0, height)
+    rooms = rng.choice(nrx * nry, n_tx, replace=False)
+    txs = [((r % nrx + 0.5) * room[0] + 0.0123, (r // nrx + 0.5) * room[1] + 0.0171, 2.5) for r in rooms]
+    for _ in range(n_furn):
+        sx, sy, sz = rng.uniform(0.3, 2.0, 3)
+        x0 = rng.uniform(0.2, lx - 0.2 - sx)
+        y0 = rng.uniform(0.2, ly - 0.2 - sy)
+        add(x0, x0 + sx, y0, y0 + sy, 0.0, sz)
+    tri = np.asarray(tri, dtype=np.float32)
+    face = np.asarray(face, dtype=np.int32)
+    cyl = place_cylinders(n_cyl, lx, ly, rng, avoid=[(t[0], t[1], 0.3) for t in txs], max_tries=1000000)
+    sph = []
+    while len(sph) < n_sph:
+        a = rng.uniform(0.1, 0.4)
+        c = np.array([rng.uniform(a + 0.1, lx - a - 0.1), rng.uniform(a + 0.1, ly - a - 0.1), rng.uniform(0.5, 2.0)])
+        if any(np.linalg.norm(c - np.asarray(t)) < a + 0.3 for t in txs):
+            continue
+        if any(np.hypot(*(c[:2] - b[1:3])) < a + b[4] + 0.05 for b in cyl):
+            continue
+        if any(np.linalg.norm(c - s_[1:4]) < a + s_[4] + 0.05 for s_ in sph):
+            continue
+        sph.append(np.array([BODY_SPHERE, *c, a, 0.0], dtype=np.float32))
+    bodies = np.concatenate([cyl, np.asarray(sph, dtype=np.float32).reshape(-1, 6)], axis=0)
+    rx = grid_receivers(nx, ny, lx, ly, rx_z)
+    name = "office(%dx%d rooms, %d triangles, %d PEC cylinders + %d spheres, %dx%d rx, %d Tx, f=%s GHz, refl<=%d)" % (
+        nrx, nry, tri.shape[0], n_cyl, n_sph, nx, ny, n_tx, ",".join("%g" % (f / 1e9) for f in freqs), max_order)
+    sc = Scene(tri, face, bodies, txs[0], (0.0, 0.0, 1.0), freqs, rx, name, max_order=max_order)
+    sc.txs = np.asarray(txs, dtype=np.float32)
+    return sc
 
 
 class Crowd:

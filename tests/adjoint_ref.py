@@ -25,7 +25,8 @@ def pcode(t, a, b):
 
 
 def _scene64(sc, bodies=None, tx=None, freqs=None, rx=None):
-    return SimpleNamespace(max_enc=getattr(sc, "max_enc", 0), wall_creep=getattr(sc, "wall_creep", False), tri=np.asarray(sc.tri, dtype=np.float64),
+    return SimpleNamespace(max_enc=getattr(sc, "max_enc", 0), wall_creep=getattr(sc, "wall_creep", False),
+                           candidates=getattr(sc, "candidates", None), tri=np.asarray(sc.tri, dtype=np.float64),
                            tri_face=sc.tri_face,
                            bodies=np.asarray(sc.bodies if bodies is None else bodies, dtype=np.float64).reshape(-1, 6),
                            tx=np.asarray(sc.tx if tx is None else tx, dtype=np.float64),
