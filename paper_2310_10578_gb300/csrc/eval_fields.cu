@@ -383,7 +383,12 @@ __device__ __noinline__ int blocked_occ(const Ctx &c, v3t<float> A, v3t<float> B
                                         const uint32_t *occ) {
     if (!occ) return blocked_impl(c, A, B, -1, -1, sb, band);
     int uns = 0;
-    for (int f0 = 0; f0 < c.n_face; f0 += 32) {
+    if (c.bvh) {
+        const int r = tris_bvh(c, A, B, -1, -1, band);
+        if (r == D_YES) return D_YES;
+        uns = (r == D_UNSURE);
+    }
+    for (int f0 = 0; f0 < (c.bvh ? 0 : c.n_face); f0 += 32) {
         unsigned keep = 0;
         const int nfc = min(32, c.n_face - f0);
 #pragma unroll 4
