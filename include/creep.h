@@ -100,7 +100,7 @@ extern "C" {
 #define RT_MAX_ENUM_FACES 64
 #define RT_MAX_CANDIDATES (1 << 20)
 #define RT_MAX_BODIES 1024
-#define RT_MAX_TRIS 4096
+#define RT_MAX_TRIS (1 << 22)
 #define RT_MAX_FREQS 64
 
 typedef struct rt_scene rt_scene;
@@ -113,7 +113,7 @@ typedef struct {
 } rt_body;
 
 typedef struct {
-    int max_order;      /* planar reflection order 0, 1 or 2 */
+    int max_order;      /* planar reflection order 0, 1 or 2 (3 with a candidate list) */
     unsigned enable;    /* RT_EN_* mask */
     int precision;      /* RT_PREC_* */
     int max_encirclements;  /* creeping rays: extra full turns round a body, 0-4 (0: the first ray

@@ -621,7 +621,9 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, 
     if (opt) o = *opt;
     if (o.max_encirclements < 0 || o.max_encirclements > 4)
         return fail(RT_ERR_ARG, "max_encirclements %d not in [0, 4]", o.max_encirclements);
-    if (o.max_order < 0 || o.max_order > 2) return fail(RT_ERR_ARG, "max_order %d not in [0, 2]", o.max_order);
+    // order 3 only through a candidate list
+    const int top = s->n_cand > 0 ? 3 : 2;
+    if (o.max_order < 0 || o.max_order > top) return fail(RT_ERR_ARG, "max_order %d not in [0, %d]", o.max_order, top);
     if (o.precision != RT_PREC_FP32 && o.precision != RT_PREC_FP64) return fail(RT_ERR_ARG, "bad precision %d", o.precision);
     if (o.enable & ~(RT_EN_ALL | RT_EN_WALL_CREEP)) return fail(RT_ERR_ARG, "bad enable mask 0x%x", o.enable);
     if (s->n_face > RT_MAX_ENUM_FACES) {
