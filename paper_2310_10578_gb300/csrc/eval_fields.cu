@@ -3264,30 +3264,27 @@ __device__ __noinline__ void adj_planar(const Ctx &c, int order, int i, int j, v
 // order-3 candidate path (faces fs, the candidate list's sequence): the
 // images by mirroring the dual-number source, the points backwards from P
 __device__ __noinline__ void adj_seq3(const Ctx &c, int4 sq, v3t<D8> S, v3t<D8> P, const FreqC &fq, AccAdj &acc) {
-    const int fs[3] = {sq.x, sq.y, sq.z};
-    v3t<D8> n[3], I[3], Q[3];
-    D8 d[3];
-    v3t<D8> X = S;
-    for (int m = 0; m < 3; ++m) {
-        face_plane<D8>(c, fs[m], &n[m], &d[m]);
-        X = mirror_pt(X, n[m], d[m]);
-        I[m] = X;
-    }
-    X = P;
-    for (int m = 2; m >= 0; --m) {
-        const D8 di = dot3(n[m], I[m]) - d[m], dX = dot3(n[m], X) - d[m];
-        Q[m] = I[m] + (X - I[m]) * (di / (di - dX));
-        X = Q[m];
-    }
-    const D8 L = norm3(Q[0] - S) + norm3(Q[1] - Q[0]) + norm3(Q[2] - Q[1]) + norm3(P - Q[2]);
-    v3t<D8> din = unit3(Q[0] - S);
-    const v3t<D8> e0 = src_pol(c, din);
+    v3t<D8> ni, nj, nk;
+    D8 di, dj, dk;
+    face_plane<D8>(c, sq.x, &ni, &di);
+    face_plane<D8>(c, sq.y, &nj, &dj);
+    face_plane<D8>(c, sq.z, &nk, &dk);
+    const v3t<D8> S1 = mirror_pt(S, ni, di);
+    const v3t<D8> S2 = mirror_pt(S1, nj, dj);
+    const v3t<D8> S3 = mirror_pt(S2, nk, dk);
+    const D8 e3 = dot3(nk, S3) - dk, p3 = dot3(nk, P) - dk;
+    const v3t<D8> Q3 = S3 + (P - S3) * (e3 / (e3 - p3));
+    const D8 e2 = dot3(nj, S2) - dj, p2 = dot3(nj, Q3) - dj;
+    const v3t<D8> Q2 = S2 + (Q3 - S2) * (e2 / (e2 - p2));
+    const D8 e1 = dot3(ni, S1) - di, p1 = dot3(ni, Q2) - di;
+    const v3t<D8> Q1 = S1 + (Q2 - S1) * (e1 / (e1 - p1));
+    const D8 L = norm3(Q1 - S) + norm3(Q2 - Q1) + norm3(Q3 - Q2) + norm3(P - Q3);
+    const v3t<D8> s1 = unit3(Q1 - S), s2 = unit3(Q2 - Q1), s3 = unit3(Q3 - Q2), s4 = unit3(P - Q3);
+    const v3t<D8> e0 = src_pol(c, s1);
     cpx<D8> E[3] = {mkc<D8>(e0.x, D8(0.0)), mkc<D8>(e0.y, D8(0.0)), mkc<D8>(e0.z, D8(0.0))};
-    for (int m = 0; m < 3; ++m) {
-        const v3t<D8> dout = unit3((m < 2 ? Q[m + 1] : P) - Q[m]);
-        reflect_face(c, fs[m], E, din, dout);
-        din = dout;
-    }
+    reflect_face(c, sq.x, E, s1, s2);
+    reflect_face(c, sq.y, E, s2, s3);
+    reflect_face(c, sq.z, E, s3, s4);
     add_ray_cx(acc, fq, E, D8(1.0) / L, L);
 }
 
