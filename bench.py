@@ -16,7 +16,10 @@ graph, with its own roofline and oracle comparison (--no-batched skips it),
 with 200 PEC cylinders at 28 GHz, 64 x 64 receivers (--no-adjoint skips it),
 and "extended_paths": the room workload with dielectric floor and walls,
 creeping rays with up to two extra turns and wall-reflection -> creeping
-paths, against the oracle on 512 sampled receivers (--no-extended skips it).
+paths, against the oracle on 512 sampled receivers (--no-extended skips it),
+and "office": the large office (about 194k triangles, 110 bodies, 1M
+receivers, reflections up to order 3 from a ray-launch candidate list, four
+transmitters) (--no-office skips it).
 
 N > 1 runs under torch.distributed (one process per GPU): each rank evaluates
 its own receiver grid (shifted by a fraction of a cell) with no data-path
@@ -63,6 +66,7 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched crowd-frames measurement")
     ap.add_argument("--batched-steps", type=int, default=10)
     ap.add_argument("--no-adjoint", action="store_true", help="skip the adjoint (gradient) measurement")
+    ap.add_argument("--no-office", action="store_true", help="skip the large-office measurement")
     ap.add_argument("--no-extended", action="store_true",
                     help="skip the extended path set (dielectric faces, extra turns, wall->creeping)")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
@@ -478,6 +482,91 @@ def extended_room(args, creep, dev, flush, peak_fn, base_ms):
     return res
 
 
+def office_large(args, creep, dev, flush):
+    """The large office: about 194k triangles (rooms, wall panels with doors,
+    furniture boxes), 100 PEC cylinders and 10 PEC spheres, 1M receivers at
+    1.2 m, 5.8 GHz, reflections up to order 3 from the candidate list of a
+    4096-ray launch per transmitter, first-order creeping; four transmitters
+    in turn.  Each transmitter's evaluation is timed (the candidate list is
+    host work, reported beside it); 32 sampled receivers of the first
+    transmitter (within 10 m of it; half of them among those with a path)
+    against the oracle with the same candidate list."""
+    import torch
+    from paper_2310_10578_gb300 import scenes
+    sc = scenes.office()
+    S = creep.Scene.from_scene(sc)
+    n, n_f = sc.n_rx, len(sc.freqs)
+    rx = torch.tensor(sc.rx_soa(), device=dev)
+    out = torch.empty((n_f, 3, n, 2), dtype=torch.float32, device=dev)
+    opts = creep.options(max_order=3)
+    st = torch.cuda.current_stream()
+    per_tx, host_s, n_cand = [], [], []
+    for i, t in enumerate(sc.txs):
+        S.set_tx(t, sc.pol)
+        t0 = time.perf_counter()
+        cand = S.candidates(4096, 3)
+        host_s.append(time.perf_counter() - t0)
+        n_cand.append(int(len(cand)))
+        S.set_candidates(cand)
+        if i == 0:
+            cand0 = cand
+        S.evaluate(rx, out=out, opts=opts)
+        torch.cuda.synchronize()
+        ms = []
+        for k in range(2):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            S.evaluate(rx, out=out, opts=opts)
+            e1.record(st)
+            ms.append((e0, e1))
+        torch.cuda.synchronize()
+        per_tx.append(float(np.mean([a.elapsed_time(b) for a, b in ms])))
+        if i == 0:
+            E0 = out.detach().cpu().numpy().astype(np.float64)
+    total_ms = float(np.sum(per_tx))
+    res = {"workload": sc.name, "value": len(sc.txs) * n * n_f / (total_ms / 1e3), "unit": UNIT,
+           "ms_per_step": total_ms, "ms_per_tx": per_tx, "candidates_per_tx": n_cand,
+           "candidate_host_ms_per_tx": [1e3 * x for x in host_s], "n_triangles": int(sc.tri.shape[0]),
+           "gpu_launches_per_step": 3 * len(sc.txs), "roofline": None,
+           "roofline_note": "visibility goes through a BVH; the oracle's work counters count brute-force "
+                            "segment-triangle tests, which are not this kernel's work",
+           "l2": "flushed between timed evaluations (256 MiB write)"}
+    if not args.no_cpu_baseline:
+        from oracle import oracle
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from parity import compare_fields, path_mismatches
+        oracle.build()
+        sc.tx = np.asarray(sc.txs[0], dtype=np.float32)
+        sc.candidates = cand0
+        # (receivers within 10 m of the transmitter: most of the building is
+        # walled off from it and has no path at all)
+        near = np.nonzero(np.hypot(sc.rx[:, 0] - sc.txs[0][0], sc.rx[:, 1] - sc.txs[0][1]) < 10.0)[0]
+        # and, as the furniture hides most of them, half of the sample among
+        # those with at least one path
+        S.set_tx(sc.txs[0], sc.pol)
+        S.set_candidates(cand0)
+        _, cnt_near, _ = S.paths(torch.tensor(sc.subset(near).rx_soa(), device=dev), opts=opts)
+        torch.cuda.synchronize()
+        lit = near[cnt_near.cpu().numpy() > 0]
+        rng = np.random.default_rng(93)
+        idx = np.unique(np.concatenate([rng.choice(near, 16, replace=False),
+                                        rng.choice(lit, min(16, len(lit)), replace=False)]))
+        t0 = time.perf_counter()
+        ref = oracle.evaluate(sc.subset(idx))
+        t_cpu = time.perf_counter() - t0
+        Eg = (E0[..., 0] + 1j * E0[..., 1])[:, :, idx]
+        acc = compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs, check=False)
+        codes, counts, _ = S.paths(torch.tensor(sc.subset(idx).rx_soa(), device=dev), opts=opts)
+        torch.cuda.synchronize()
+        acc["path_list_mismatches"] = len(path_mismatches(codes.cpu().numpy(), counts.cpu().numpy(), ref))
+        res["accuracy_vs_fp64_oracle"] = dict(acc, sample_receivers=len(idx), transmitter=0)
+        res["cpu_baseline"] = {"value": len(idx) * n_f / t_cpu, "unit": UNIT, "cores": os.cpu_count() or 1,
+                               "kind": "oracle (brute-force visibility)",
+                               "sample": "the accuracy sample (%.1f s)" % t_cpu}
+    return res
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -579,6 +668,9 @@ def main():
     adj = None
     if world == 1 and not args.no_adjoint:
         adj = adjoint_room200(args, creep, dev, flush)
+    office = None
+    if world == 1 and not args.no_office:
+        office = office_large(args, creep, dev, flush)
     ext = None
     if world == 1 and not args.no_extended:
         ext = extended_room(args, creep, dev, flush, peak_fn, float(np.mean(dev_ms)))
@@ -635,6 +727,8 @@ def main():
         line["adjoint"] = adj
     if ext is not None:
         line["extended_paths"] = ext
+    if office is not None:
+        line["office"] = office
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
