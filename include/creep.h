@@ -180,6 +180,12 @@ int rt_set_face_materials(rt_scene *scene, const float *mat, int n_face);
  */
 int rt_candidates(rt_scene *scene, int n_rays, int max_order, int32_t *seq, int cap, int *n_out);
 
+/* The same ray launch for a mesh and a transmitter without a scene: host
+ * only (no device, no CUDA call).  tri_xyz, tri_face as in
+ * rt_scene_create; tx host float[3].  Errors: RT_ERR_ARG. */
+int rt_candidates_mesh(const float *tri_xyz, const int *tri_face, int n_tri, const float tx[3], int n_rays,
+                       int max_order, int32_t *seq, int cap, int *n_out);
+
 /*
  * The candidate list of the planar paths (orders 1-3): host int32
  * [n][3], face ids with -1 padding at the end, no face twice in a row;

@@ -28,7 +28,7 @@ EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "
            "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats", "rt_backward", "rt_alu_peaks",
            "rt_evaluate_with_paths", "rt_batch_set_shape", "rt_batch_get_shape", "rt_batch_tune",
            "rt_set_shape", "rt_get_shape", "rt_tune", "rt_set_face_materials", "rt_candidates",
-           "rt_set_candidates")
+           "rt_set_candidates", "rt_candidates_mesh")
 RT_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -98,6 +98,7 @@ def load(build_if_missing=True):
     lib.rt_set_face_materials.argtypes = [P, P, I]
     lib.rt_candidates.argtypes = [P, I, I, P, I, ctypes.POINTER(I)]
     lib.rt_set_candidates.argtypes = [P, P, I]
+    lib.rt_candidates_mesh.argtypes = [P, P, I, P, I, I, P, I, ctypes.POINTER(I)]
     _lib = lib
     return lib
 
@@ -314,6 +315,22 @@ class Scene:
         st = rt_stats()
         _check(_lib.rt_get_stats(self._h, ctypes.byref(st)))
         return {"escalated_candidates": int(st.escalated_candidates), "kernel_launches": int(st.kernel_launches)}
+
+
+def candidates_mesh(tri, tri_face, tx, n_rays, max_order=3):
+    """The ray launch of rt_candidates for a mesh and a transmitter, host
+    only (rt_candidates_mesh): [n, 3] int32 face sequences, -1 padded."""
+    lib = load()
+    tri = np.ascontiguousarray(np.asarray(tri, dtype=np.float32).reshape(-1, 9))
+    tf = None if tri_face is None else np.ascontiguousarray(np.asarray(tri_face, dtype=np.int32))
+    t = np.ascontiguousarray(np.asarray(tx, dtype=np.float32).reshape(3))
+    n = ctypes.c_int(0)
+    _check(lib.rt_candidates_mesh(_ptr(tri), _ptr(tf), tri.shape[0], _ptr(t), int(n_rays), int(max_order), None, 0,
+                                  ctypes.byref(n)))
+    out = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+    _check(lib.rt_candidates_mesh(_ptr(tri), _ptr(tf), tri.shape[0], _ptr(t), int(n_rays), int(max_order),
+                                  _ptr(out), n.value, ctypes.byref(n)))
+    return out[:n.value]
 
 
 class Batch:

@@ -564,6 +564,29 @@ int rt_set_candidates(rt_scene *s, const int32_t *seq, int n) {
     return upload_candidates(s);
 }
 
+int rt_candidates_mesh(const float *tri_xyz, const int *tri_face, int n_tri, const float tx[3], int n_rays,
+                       int max_order, int32_t *seq, int cap, int *n_out) {
+    if (!tri_xyz || !tx || !n_out || n_tri < 1) return fail(RT_ERR_ARG, "rt_candidates_mesh: NULL argument or no triangle");
+    if (n_rays < 1 || max_order < 1 || max_order > 3 || cap < 0 || (cap > 0 && !seq))
+        return fail(RT_ERR_ARG, "rt_candidates_mesh: bad n_rays, max_order or cap");
+    std::vector<int> tf(n_tri);
+    int nf = 0;
+    for (int t = 0; t < n_tri; ++t) {
+        tf[t] = tri_face ? tri_face[t] : t;
+        if (tf[t] < 0) return fail(RT_ERR_ARG, "rt_candidates_mesh: negative face id");
+        if (tf[t] + 1 > nf) nf = tf[t] + 1;
+    }
+    std::vector<float4> nodes;
+    std::vector<int> order, out;
+    bvh_build(tri_xyz, n_tri, nodes, order);
+    const double p[3] = {tx[0], tx[1], tx[2]};
+    int n = ray_launch(tri_xyz, tf.data(), n_tri, nf, nodes, order, p, n_rays, max_order, out);
+    for (int q = 0; q < n && q < cap; ++q)
+        for (int m = 0; m < 3; ++m) seq[3 * (size_t)q + m] = out[3 * (size_t)q + m];
+    *n_out = n;
+    return RT_OK;
+}
+
 int rt_candidates(rt_scene *s, int n_rays, int max_order, int32_t *seq, int cap, int *n_out) {
     if (!s || !n_out) return fail(RT_ERR_ARG, "rt_candidates: NULL argument");
     if (n_rays < 1 || max_order < 1 || max_order > 3 || cap < 0 || (cap > 0 && !seq))
