@@ -16,6 +16,13 @@
  * visibility bits U are straight-segment tests against every triangle and
  * body (Eqs. 1-2, "path validation", Sec. III.B).
  *
+ * Optional extensions of the path set (each off by default): dielectric
+ * faces (rt_set_face_materials), creeping rays with extra turns round the
+ * body (rt_options.max_encirclements), creeping rays fed by one planar
+ * reflection (RT_EN_WALL_CREEP), and for large scenes planar reflections up
+ * to order 3 over a candidate list of face sequences (rt_candidates,
+ * rt_set_candidates) with BVH visibility.
+ *
  * Conventions
  *   - Units: metres, Hz.  Time convention e^{+j w t}: fields go as e^{-jks}.
  *   - Source: isotropic, polarisation vector pol; on a ray leaving in
@@ -46,7 +53,7 @@ extern "C" {
 #define RT_ERR_CUDA 3      /* a CUDA runtime call failed; message in rt_last_error() */
 #define RT_ERR_TIMEOUT 4   /* a bounded device wait gave up */
 #define RT_ERR_OVERFLOW 5  /* a size exceeds a library limit (faces, bodies, path cap) */
-#define RT_ERR_STATE 6     /* transmitter or frequencies not set */
+#define RT_ERR_STATE 6     /* transmitter or frequencies not set; a large scene without a candidate list */
 
 /* body types */
 #define RT_BODY_SPHERE 0   /* centre c, radius a */
