@@ -20,9 +20,11 @@ from . import creep
 class Static:
     """What stays fixed across evaluations: the triangles (and their faces),
     every body's type and height, the polarisation, the receivers (CUDA
-    float32 tensor [3, n]), the options and the path-list capacity."""
+    float32 tensor [3, n]), the options, the path-list capacity, the face
+    materials and (large scenes) the candidate face sequences."""
 
-    def __init__(self, tri, tri_face, body_type, body_h, pol, rx_soa, opts=None, cap=256, face_mat=None):
+    def __init__(self, tri, tri_face, body_type, body_h, pol, rx_soa, opts=None, cap=256, face_mat=None,
+                 candidates=None):
         self.tri = np.asarray(tri, dtype=np.float32)
         self.tri_face = None if tri_face is None else np.asarray(tri_face, dtype=np.int32)
         self.body_type = np.asarray(body_type, dtype=np.float64).reshape(-1)
@@ -32,6 +34,7 @@ class Static:
         self.opts = opts if opts is not None else creep.options(max_order=2)
         self.cap = int(cap)
         self.face_mat = face_mat              # per face (kind, eps', eps'') or None (PEC)
+        self.candidates = candidates          # candidate face sequences [n, 3] (large scenes) or None
 
     @classmethod
     def from_scene(cls, sc, rx_soa, opts=None, cap=256):
@@ -40,7 +43,7 @@ class Static:
                        max_order=sc.max_order, max_encirclements=getattr(sc, "max_enc", 0),
                        enable=creep.RT_EN_ALL | (creep.RT_EN_WALL_CREEP if getattr(sc, "wall_creep", False) else 0)),
                    cap,
-                   getattr(sc, "face_eps", None))
+                   getattr(sc, "face_eps", None), getattr(sc, "candidates", None))
 
     def scene(self, body_params, tx, freqs):
         """An rt_scene for parameters body_params [n, 4] (cx, cy, cz, a), tx [3], freqs [n_f]."""
@@ -51,6 +54,8 @@ class Static:
         S.set_freqs(freqs.detach().cpu().numpy().astype(np.float64))
         if self.face_mat is not None:
             S.set_face_materials(self.face_mat)
+        if self.candidates is not None:
+            S.set_candidates(self.candidates)
         return S
 
 
