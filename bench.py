@@ -404,14 +404,66 @@ def adjoint_room200(args, creep, dev, flush):
     t = np.array([[m[k].elapsed_time(m[k + 1]) for k in range(3)] for m in marks])
     fwd, paths, bwd = (float(np.mean(t[:, k])) for k in range(3))
     n_paths = int(counts.sum())
-    return {"workload": "room 10x8x3 m, 12 PEC triangles + 200 PEC cylinders, 64x64 rx at z=1.2 m, 28 GHz, refl<=2",
-            "loss": "sum over receivers of received power in dB (seed dLoss/dE = 20/ln10 E/|E|^2)",
-            "ms_fields_only": fwd, "ms_fields_with_path_list": paths, "ms_backward_incl_seed": bwd,
-            "ms_step": paths + bwd,
-            "value": n / ((paths + bwd) / 1e3), "unit": "receiver gradients/s (fields with path list + adjoint)",
-            "paths": n_paths, "steps": args.batched_steps,
-            "gradients": "d/d(200 x (cx, cy, cz, a)), d/d(Tx), d/d(f); FP64 dual numbers",
-            "l2": "flushed between timed steps (256 MiB write)"}
+    res = {"workload": "room 10x8x3 m, 12 PEC triangles + 200 PEC cylinders, 64x64 rx at z=1.2 m, 28 GHz, refl<=2",
+           "loss": "sum over receivers of received power in dB (seed dLoss/dE = 20/ln10 E/|E|^2)",
+           "ms_fields_only": fwd, "ms_fields_with_path_list": paths, "ms_backward_incl_seed": bwd,
+           "ms_step": paths + bwd,
+           "value": n / ((paths + bwd) / 1e3), "unit": "receiver gradients/s (fields with path list + adjoint)",
+           "paths": n_paths, "steps": args.batched_steps,
+           "gradients": "d/d(200 x (cx, cy, cz, a)), d/d(Tx), d/d(f); FP64 dual numbers",
+           "l2": "flushed between timed steps (256 MiB write)"}
+    if not args.no_cpu_baseline:
+        try:
+            res.update(adjoint_oracle_sample(creep, S, sc, dev, opts))
+        except Exception as e:                      # the measurement above stands without it
+            res["cpu_baseline"] = {"error": "%s: %s" % (type(e).__name__, e)}
+    return res
+
+
+def _seed_db(E):
+    """dLoss/dE of the received power in dB summed over receivers, as bench's
+    adjoint step seeds it: 20/ln10 E/|E|^2 (zero where no field)."""
+    import torch
+    p = (E.double() ** 2).sum(dim=(0, 1, 3))
+    g = torch.where(p > 0, 20.0 / np.log(10.0) / torch.clamp(p, min=1e-300), torch.zeros_like(p))
+    return (E.double() * g[None, None, :, None]).float()
+
+
+def adjoint_oracle_sample(creep, S, sc, dev, opts, n_sample=48):
+    """The oracle beside the adjoint: on n_sample receivers with paths, the
+    transmitter gradient of the dB loss by rt_backward and by the oracle's
+    central differences of its per-path fields (visibility held fixed), the
+    relative difference, and the oracle's rate."""
+    import torch
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    import adjoint_ref
+    from oracle import oracle
+    oracle.build()
+    rng = np.random.default_rng(31)
+    rx_all = torch.tensor(sc.rx_soa(), device=dev)
+    _, _, cnt_all, _ = S.evaluate_with_paths(rx_all, cap=64, opts=opts)
+    with_paths = np.nonzero(cnt_all.cpu().numpy() > 0)[0]
+    idx = np.sort(rng.choice(with_paths, min(n_sample, len(with_paths)), replace=False))
+    sub = sc.subset(idx)
+    rx = torch.tensor(sub.rx_soa(), device=dev)
+    E, codes, counts, _ = S.evaluate_with_paths(rx, cap=64, opts=opts)
+    gE = _seed_db(E)
+    _, gt, _ = S.backward(rx, codes, counts, gE, opts=opts)
+    torch.cuda.synchronize()
+    c = codes.cpu().numpy().astype(np.uint64)
+    k = counts.cpu().numpy()
+    lists = [[int(x) for x in c[r, :min(int(k[r]), 64)]] for r in range(len(idx))]
+    g = gE.cpu().numpy().astype(np.float64)
+    t0 = time.perf_counter()
+    ref = adjoint_ref.vjp(sub, lists, g[..., 0] + 1j * g[..., 1], bodies=(), freqs=False, cap=64)
+    t_cpu = time.perf_counter() - t0
+    gt = gt.cpu().numpy()
+    err = [abs(gt[i] - ref["tx"][i]) / max(abs(ref["tx"][i]), 1e-3 * ref["tx_abs"][i], 1e-300) for i in range(3)]
+    return {"accuracy_vs_fp64_oracle": {"tx_gradient_rel_err_max": float(max(err)), "sample_receivers": len(idx),
+                                        "paths_skipped_by_reference": int(ref["skipped"])},
+            "cpu_baseline": {"value": len(idx) / t_cpu, "unit": "receiver gradients/s (transmitter only)",
+                             "cores": os.cpu_count() or 1, "kind": "oracle central differences (h = 1e-5 m)",
+                             "sample": "%d receivers with paths (%.1f s)" % (len(idx), t_cpu)}}
 
 
 def extended_room(args, creep, dev, flush, peak_fn, base_ms):
