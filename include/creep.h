@@ -106,6 +106,7 @@ extern "C" {
 #define RT_MAX_FACES (1 << 20)
 #define RT_MAX_ENUM_FACES 64
 #define RT_MAX_CANDIDATES (1 << 20)
+#define RT_MAX_RAYS (1 << 24)      /* rays of one candidate launch */
 #define RT_MAX_BODIES 1024
 #define RT_MAX_TRIS (1 << 22)
 #define RT_MAX_FREQS 64
@@ -186,6 +187,7 @@ int rt_set_face_materials(rt_scene *scene, const float *mat, int n_face);
  * Errors: RT_ERR_STATE without a transmitter, RT_ERR_ARG for bad sizes.
  */
 int rt_candidates(rt_scene *scene, int n_rays, int max_order, int32_t *seq, int cap, int *n_out);
+/* (1 <= n_rays <= RT_MAX_RAYS) */
 
 /* The same ray launch for a mesh and a transmitter without a scene: host
  * only (no device, no CUDA call).  tri_xyz, tri_face as in

@@ -567,7 +567,7 @@ int rt_set_candidates(rt_scene *s, const int32_t *seq, int n) {
 int rt_candidates_mesh(const float *tri_xyz, const int *tri_face, int n_tri, const float tx[3], int n_rays,
                        int max_order, int32_t *seq, int cap, int *n_out) {
     if (!tri_xyz || !tx || !n_out || n_tri < 1) return fail(RT_ERR_ARG, "rt_candidates_mesh: NULL argument or no triangle");
-    if (n_rays < 1 || max_order < 1 || max_order > 3 || cap < 0 || (cap > 0 && !seq))
+    if (n_rays < 1 || n_rays > RT_MAX_RAYS || max_order < 1 || max_order > 3 || cap < 0 || (cap > 0 && !seq))
         return fail(RT_ERR_ARG, "rt_candidates_mesh: bad n_rays, max_order or cap");
     std::vector<int> tf(n_tri);
     int nf = 0;
@@ -589,7 +589,7 @@ int rt_candidates_mesh(const float *tri_xyz, const int *tri_face, int n_tri, con
 
 int rt_candidates(rt_scene *s, int n_rays, int max_order, int32_t *seq, int cap, int *n_out) {
     if (!s || !n_out) return fail(RT_ERR_ARG, "rt_candidates: NULL argument");
-    if (n_rays < 1 || max_order < 1 || max_order > 3 || cap < 0 || (cap > 0 && !seq))
+    if (n_rays < 1 || n_rays > RT_MAX_RAYS || max_order < 1 || max_order > 3 || cap < 0 || (cap > 0 && !seq))
         return fail(RT_ERR_ARG, "rt_candidates: bad n_rays, max_order or cap");
     if (!s->tx_set) return fail(RT_ERR_STATE, "rt_candidates: transmitter not set");
     const double p[3] = {s->tx[0], s->tx[1], s->tx[2]};

@@ -30,7 +30,8 @@ def test_host_ray_launch_equals_oracle(creep, oracle_mod, n_rays, order):
 
 def test_host_ray_launch_errors(creep):
     tri, face = scenes.box_triangles(10.0, 8.0, 3.0)
-    for args in ((tri, face, (1.0, 1.0, 2.0), 0, 3), (tri, face, (1.0, 1.0, 2.0), 100, 4)):
+    for args in ((tri, face, (1.0, 1.0, 2.0), 0, 3), (tri, face, (1.0, 1.0, 2.0), 100, 4),
+                 (tri, face, (1.0, 1.0, 2.0), (1 << 24) + 1, 3)):
         with pytest.raises(creep.CreepError) as e:
             creep.candidates_mesh(*args)
         assert e.value.code == creep.RT_ERR_ARG
