@@ -21,9 +21,10 @@ and "office": the large office (about 194k triangles, 110 bodies, 1M
 receivers, reflections up to order 3 from a ray-launch candidate list, four
 transmitters) (--no-office skips it).
 
-N > 1 runs under torch.distributed (one process per GPU): each rank evaluates
-its own receiver grid (shifted by a fraction of a cell) with no data-path
-collective; value = all ranks' samples / max-over-ranks time ("weak").
+N > 1 runs under torch.distributed (one process per GPU): one job of
+256 x 256 N receivers, each rank evaluating its contiguous range of 65 536
+with no data-path collective, the slices gathered on rank 0 after the timed
+region; value = all ranks' samples / max-over-ranks time ("weak").
 --impl reference times the FP64 oracle (oracle/) on the host cores instead.
 """
 import argparse
@@ -69,21 +70,23 @@ def parse():
     ap.add_argument("--no-office", action="store_true", help="skip the large-office measurement")
     ap.add_argument("--no-extended", action="store_true",
                     help="skip the extended path set (dielectric faces, extra turns, wall->creeping)")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 form of the room workload")
+    ap.add_argument("--no-ring", action="store_true", help="skip the sphere-ring workload")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
 
 
 def make_scene(rank=0, world=1):
-    """The workload of one rank: the room with its own 256 x 256 receiver grid
-    (rank r shifts the grid by r / world of a cell in x, so ranks evaluate
-    distinct receivers of the same size: weak scaling, no exchange)."""
-    from paper_2310_10578_gb300 import scenes
-    sc = scenes.room()
+    """The workload of one rank.  One job: the room with a 256 x (256 world)
+    receiver grid at z = 1.2 m (cell centres; at one GPU the 256 x 256 grid).
+    Rank r evaluates the contiguous receiver range shard(n, r, world) of it,
+    65 536 receivers each (weak scaling), with no data-path exchange; the
+    ranks' output slices gather into the single-rank layout."""
+    from paper_2310_10578_gb300 import scenes, shard
+    sc = scenes.room(nx=256, ny=256 * world)
     if world > 1:
-        dx = (10.0 / 256) * rank / world
-        rx = sc.rx.copy()
-        rx[:, 0] = rx[:, 0] + dx
-        sc.rx = rx.astype(np.float32)
+        lo, hi = shard.shard(sc.n_rx, rank, world)
+        sc.rx = np.ascontiguousarray(sc.rx[lo:hi])
     return sc
 
 
@@ -170,8 +173,9 @@ def _profiled_traffic():
         return None
     kv = {}
     for line in open(p):
-        if ":" in line:
-            k, v = line.split(":", 1)
+        # "key: value" -- split at the first ": " (keys may hold a colon, e.g. sha256[:16])
+        if ": " in line:
+            k, v = line.split(": ", 1)
             kv[k.strip()] = v.strip()
     if kv.get("eval_fields.cu sha256[:16]") != _kernel_source_hash():
         return None
@@ -360,11 +364,30 @@ def batched_crowd(args, creep, dev, flush, peak_fn):
 
 
 # ---------------------------------------------------------------- adjoint
+ZONE = ((6.0, 8.0), (4.0, 6.0))     # the adjoint workload's target zone: x in [6, 8] m, y in [4, 6] m
+
+
+def zone_of(sc):
+    (x0, x1), (y0, y1) = ZONE
+    return np.nonzero((sc.rx[:, 0] >= x0) & (sc.rx[:, 0] <= x1) & (sc.rx[:, 1] >= y0) & (sc.rx[:, 1] <= y1))[0]
+
+
+def _seed_zone_db(E, zone_mask):
+    """dLoss/dE of the loss = sum over the zone's receivers of the received
+    power in dB, 10 log10 sum|E|^2: 20/ln10 E/|E|^2 on the zone (zero where
+    a zone receiver has no field), zero elsewhere."""
+    import torch
+    p = (E.double() ** 2).sum(dim=(0, 1, 3))
+    g = torch.where((p > 0) & zone_mask, 20.0 / np.log(10.0) / torch.clamp(p, min=1e-300), torch.zeros_like(p))
+    return (E.double() * g[None, None, :, None]).float()
+
+
 def adjoint_room200(args, creep, dev, flush):
     """The adjoint form: the room with 200 PEC cylinders, 28 GHz, 64 x 64
-    receivers; one gradient step = the fields with their path list
-    (rt_evaluate_with_paths) and the adjoint (rt_backward) with a dB-power
-    loss seed.  The fields alone (rt_evaluate) are timed beside it."""
+    receivers; loss = sum over the target zone (x in [6, 8] m, y in [4, 6] m)
+    of the received power in dB.  One gradient step = the fields with their
+    path list (rt_evaluate_with_paths), the loss seed, and the adjoint
+    (rt_backward).  The fields alone (rt_evaluate) are timed beside it."""
     import torch
     from paper_2310_10578_gb300 import scenes
     sc = scenes.room(n_cyl=200, nx=64, ny=64, freqs=(28e9,))
@@ -372,15 +395,15 @@ def adjoint_room200(args, creep, dev, flush):
     rx = torch.tensor(sc.rx_soa(), device=dev)
     opts = creep.options(max_order=2)
     n = sc.n_rx
+    zone = zone_of(sc)
+    zmask = torch.zeros(n, dtype=torch.bool, device=dev)
+    zmask[torch.tensor(zone, device=dev)] = True
     E = torch.empty((1, 3, n, 2), dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
 
     def step():
         _, codes, counts, _ = S.evaluate_with_paths(rx, cap=64, out=E, opts=opts)
-        p = (E.double() ** 2).sum(dim=(0, 1, 3))
-        g = torch.where(p > 0, 20.0 / np.log(10.0) / torch.clamp(p, min=1e-300), torch.zeros_like(p))
-        gE = (E.double() * g[None, None, :, None]).float()
-        return S.backward(rx, codes, counts, gE, opts=opts)
+        return S.backward(rx, codes, counts, _seed_zone_db(E, zmask), opts=opts)
 
     for _ in range(3):
         step()
@@ -394,10 +417,7 @@ def adjoint_room200(args, creep, dev, flush):
         ev[1].record(st)
         _, codes, counts, _ = S.evaluate_with_paths(rx, cap=64, out=E, opts=opts)
         ev[2].record(st)
-        p = (E.double() ** 2).sum(dim=(0, 1, 3))
-        g = torch.where(p > 0, 20.0 / np.log(10.0) / torch.clamp(p, min=1e-300), torch.zeros_like(p))
-        gE = (E.double() * g[None, None, :, None]).float()
-        gb, gt, gf = S.backward(rx, codes, counts, gE, opts=opts)
+        gb, gt, gf = S.backward(rx, codes, counts, _seed_zone_db(E, zmask), opts=opts)
         ev[3].record(st)
         marks.append(ev)
     torch.cuda.synchronize()
@@ -405,65 +425,168 @@ def adjoint_room200(args, creep, dev, flush):
     fwd, paths, bwd = (float(np.mean(t[:, k])) for k in range(3))
     n_paths = int(counts.sum())
     res = {"workload": "room 10x8x3 m, 12 PEC triangles + 200 PEC cylinders, 64x64 rx at z=1.2 m, 28 GHz, refl<=2",
-           "loss": "sum over receivers of received power in dB (seed dLoss/dE = 20/ln10 E/|E|^2)",
+           "loss": "sum over the target zone x in [6, 8] m, y in [4, 6] m (%d receivers) of received power in dB "
+                   "(seed dLoss/dE = 20/ln10 E/|E|^2 on the zone)" % len(zone),
            "ms_fields_only": fwd, "ms_fields_with_path_list": paths, "ms_backward_incl_seed": bwd,
            "ms_step": paths + bwd,
            "value": n / ((paths + bwd) / 1e3), "unit": "receiver gradients/s (fields with path list + adjoint)",
            "paths": n_paths, "steps": args.batched_steps,
-           "gradients": "d/d(200 x (cx, cy, cz, a)), d/d(Tx), d/d(f); FP64 dual numbers",
+           "gradients": "d/d(200 x (cx, cy, cz, a)), d/d(Tx), d/d(f)",
            "l2": "flushed between timed steps (256 MiB write)"}
     if not args.no_cpu_baseline:
         try:
-            res.update(adjoint_oracle_sample(creep, S, sc, dev, opts))
+            res.update(adjoint_oracle_sample(creep, S, sc, dev, opts, zone, gb, gt))
         except Exception as e:                      # the measurement above stands without it
             res["cpu_baseline"] = {"error": "%s: %s" % (type(e).__name__, e)}
     return res
 
 
-def _seed_db(E):
-    """dLoss/dE of the received power in dB summed over receivers, as bench's
-    adjoint step seeds it: 20/ln10 E/|E|^2 (zero where no field)."""
-    import torch
-    p = (E.double() ** 2).sum(dim=(0, 1, 3))
-    g = torch.where(p > 0, 20.0 / np.log(10.0) / torch.clamp(p, min=1e-300), torch.zeros_like(p))
-    return (E.double() * g[None, None, :, None]).float()
-
-
-def adjoint_oracle_sample(creep, S, sc, dev, opts, n_sample=48):
-    """The oracle beside the adjoint: on n_sample receivers with paths, the
-    transmitter gradient of the dB loss by rt_backward and by the oracle's
-    central differences of its per-path fields (visibility held fixed), the
-    relative difference, and the oracle's rate."""
+def adjoint_oracle_sample(creep, S, sc, dev, opts, zone, gb, gt):
+    """The oracle beside the adjoint: the zone loss's gradient with respect
+    to every body's centre and radius and the transmitter, by rt_backward
+    (the timed step's result, gb and gt) and by the oracle's central
+    differences of its per-path fields with the same path lists (visibility
+    held fixed); the worst relative difference and the oracle's rate."""
     import torch
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     import adjoint_ref
     from oracle import oracle
     oracle.build()
-    rng = np.random.default_rng(31)
-    rx_all = torch.tensor(sc.rx_soa(), device=dev)
-    _, _, cnt_all, _ = S.evaluate_with_paths(rx_all, cap=64, opts=opts)
-    with_paths = np.nonzero(cnt_all.cpu().numpy() > 0)[0]
-    idx = np.sort(rng.choice(with_paths, min(n_sample, len(with_paths)), replace=False))
-    sub = sc.subset(idx)
-    rx = torch.tensor(sub.rx_soa(), device=dev)
+    rx = torch.tensor(sc.rx_soa(), device=dev)
     E, codes, counts, _ = S.evaluate_with_paths(rx, cap=64, opts=opts)
-    gE = _seed_db(E)
-    _, gt, _ = S.backward(rx, codes, counts, gE, opts=opts)
+    zmask = torch.zeros(sc.n_rx, dtype=torch.bool, device=dev)
+    zmask[torch.tensor(zone, device=dev)] = True
+    gE = _seed_zone_db(E, zmask)
     torch.cuda.synchronize()
     c = codes.cpu().numpy().astype(np.uint64)
     k = counts.cpu().numpy()
-    lists = [[int(x) for x in c[r, :min(int(k[r]), 64)]] for r in range(len(idx))]
+    zset = set(int(r) for r in zone)
+    # paths of the zone's receivers only (the seed is zero elsewhere)
+    lists = [[int(x) for x in c[r, :min(int(k[r]), 64)]] if r in zset else [] for r in range(sc.n_rx)]
     g = gE.cpu().numpy().astype(np.float64)
+    bodies = sorted({(cc >> 28) & 0xFFFFFFF for cs in lists for cc in cs if (cc >> 56) >= 3})
     t0 = time.perf_counter()
-    ref = adjoint_ref.vjp(sub, lists, g[..., 0] + 1j * g[..., 1], bodies=(), freqs=False, cap=64)
+    ref = adjoint_ref.vjp(sc, lists, g[..., 0] + 1j * g[..., 1], bodies=bodies, freqs=False, cap=64)
     t_cpu = time.perf_counter() - t0
-    gt = gt.cpu().numpy()
-    err = [abs(gt[i] - ref["tx"][i]) / max(abs(ref["tx"][i]), 1e-3 * ref["tx_abs"][i], 1e-300) for i in range(3)]
-    return {"accuracy_vs_fp64_oracle": {"tx_gradient_rel_err_max": float(max(err)), "sample_receivers": len(idx),
-                                        "paths_skipped_by_reference": int(ref["skipped"])},
-            "cpu_baseline": {"value": len(idx) / t_cpu, "unit": "receiver gradients/s (transmitter only)",
+    gb, gt = gb.cpu().numpy(), gt.cpu().numpy()
+
+    def rel(got, want, absum):
+        return abs(got - want) / max(abs(want), 1e-3 * absum, 1e-300)
+
+    err_tx = max(rel(gt[i], ref["tx"][i], ref["tx_abs"][i]) for i in range(3))
+    err_b = max([rel(gb[b, j], ref["body"][b][j], ref["body_abs"][b][j]) for b in bodies for j in range(4)] or [0.0])
+    # bodies without a path to the zone must get exactly zero
+    idle = [b for b in range(sc.bodies.shape[0]) if b not in set(bodies)]
+    return {"accuracy_vs_fp64_oracle": {"tx_gradient_rel_err_max": float(err_tx),
+                                        "body_gradient_rel_err_max": float(err_b),
+                                        "bodies_checked": len(bodies), "bodies_without_zone_paths": len(idle),
+                                        "bodies_without_zone_paths_nonzero_gradient":
+                                            int(np.count_nonzero(np.any(gb[idle] != 0.0, axis=1))) if idle else 0,
+                                        "zone_receivers": len(zone),
+                                        "paths_skipped_by_reference": int(ref["skipped"]),
+                                        "tolerance": "1e-3 relative (against max(|ref|, 1e-3 sum|contributions|))"},
+            "cpu_baseline": {"value": len(zone) / t_cpu,
+                             "unit": "receiver gradients/s (every body with zone paths + transmitter)",
                              "cores": os.cpu_count() or 1, "kind": "oracle central differences (h = 1e-5 m)",
-                             "sample": "%d receivers with paths (%.1f s)" % (len(idx), t_cpu)}}
+                             "sample": "the zone's %d receivers (%.1f s)" % (len(zone), t_cpu)}}
+
+
+def _time_eval(S, rx, out, opts, flush, steps, flags=None):
+    """Mean CUDA-event time (ms) of S.evaluate over `steps` evaluations, the
+    L2 flushed before each, after three untimed ones."""
+    import torch
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        S.evaluate(rx, out=out, flags=flags, opts=opts)
+    torch.cuda.synchronize()
+    ev = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        S.evaluate(rx, out=out, flags=flags, opts=opts)
+        e1.record(st)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    return float(np.mean([a.elapsed_time(b) for a, b in ev]))
+
+
+def room_fp64(args, creep, dev, flush, base_ms):
+    """The bench workload computed entirely in FP64 (RT_PREC_FP64: geometry,
+    decisions, Fock evaluation, fields): its time beside the FP32 form's, and
+    its fields and path lists against the oracle on sampled receivers."""
+    import torch
+    sc = make_scene()
+    S = creep.Scene.from_scene(sc)
+    rx = torch.tensor(sc.rx_soa(), device=dev)
+    n, n_f = sc.n_rx, len(sc.freqs)
+    opts = creep.options(max_order=2, precision=creep.RT_PREC_FP64)
+    out = torch.empty((n_f, 3, n, 2), dtype=torch.float32, device=dev)
+    ms = _time_eval(S, rx, out, opts, flush, max(3, args.batched_steps // 2))
+    res = {"workload": WORKLOAD + ", FP64", "value": n * n_f / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+           "dtype": "f64", "fp64_over_fp32_time": ms / base_ms,
+           "gpu_launches_per_step": S.stats()["kernel_launches"],
+           "l2": "flushed between timed steps (256 MiB write)"}
+    if not args.no_cpu_baseline:
+        from oracle import oracle
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from parity import compare_fields, path_mismatches
+        oracle.build()
+        idx = np.sort(np.random.default_rng(97).choice(n, 2048, replace=False))
+        ref = oracle.evaluate(sc.subset(idx))
+        Eg = out.detach().cpu().numpy().astype(np.float64)
+        Eg = (Eg[..., 0] + 1j * Eg[..., 1])[:, :, idx]
+        acc = compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs, tol_rel=2e-6, dl=0.0, check=False)
+        codes, counts, _ = S.paths(torch.tensor(sc.subset(idx).rx_soa(), device=dev), opts=opts)
+        torch.cuda.synchronize()
+        acc["path_list_mismatches"] = len(path_mismatches(codes.cpu().numpy(), counts.cpu().numpy(), ref))
+        res["accuracy_vs_fp64_oracle"] = dict(acc, sample_receivers=len(idx),
+                                              tolerance="|dE| <= 2e-6 sum|E_path| per receiver (FP64 mode)")
+    return res
+
+
+def sphere_ring_bench(args, creep, dev, flush):
+    """The analytical-sphere workload (Sec. IV.A's validation case): PEC
+    sphere a = 0.5 m, source at (3, 0, 0) m, 4096 receivers on the r = 2 m
+    ring, 2.4 GHz, direct ray + GO reflection + first creeping ray each way;
+    z-polarised (soft) and y-polarised (hard) source; FP64 (the
+    configuration's precision) and FP32.  Every receiver against the oracle."""
+    import torch
+    from paper_2310_10578_gb300 import scenes
+    res = {"workload": "PEC sphere a=0.5 m, Tx (3,0,0) m, 4096 rx on the r=2 m ring, 2.4 GHz, z- and y-polarised",
+           "unit": UNIT, "l2": "flushed between timed steps (256 MiB write)", "cases": {}}
+    for pol in ((0.0, 0.0, 1.0), (0.0, 1.0, 0.0)):
+        sc = scenes.sphere_ring(pol=pol)
+        S = creep.Scene.from_scene(sc)
+        rx = torch.tensor(sc.rx_soa(), device=dev)
+        n = sc.n_rx
+        for prec, name in ((creep.RT_PREC_FP64, "fp64"), (creep.RT_PREC_FP32, "fp32")):
+            opts = creep.options(max_order=0, precision=prec)
+            out = torch.empty((1, 3, n, 2), dtype=torch.float32, device=dev)
+            fl = torch.zeros(n, dtype=torch.int32, device=dev)
+            ms = _time_eval(S, rx, out, opts, flush, args.batched_steps, flags=fl)
+            case = {"value": n / (ms / 1e3), "ms_per_step": ms}
+            if not args.no_cpu_baseline:
+                from oracle import oracle
+                sys.path.insert(0, os.path.join(ROOT, "tests"))
+                from parity import compare_fields, path_mismatches
+                oracle.build()
+                t0 = time.perf_counter()
+                ref = oracle.evaluate(sc)
+                t_cpu = time.perf_counter() - t0
+                Eg = out.detach().cpu().numpy().astype(np.float64)
+                kw = dict(tol_rel=2e-6, dl=0.0) if name == "fp64" else {}
+                acc = compare_fields(Eg[..., 0] + 1j * Eg[..., 1], ref, flags=ref.flags, freqs=sc.freqs,
+                                     check=False, **kw)
+                codes, counts, _ = S.paths(rx, opts=opts)
+                torch.cuda.synchronize()
+                acc["path_list_mismatches"] = len(path_mismatches(codes.cpu().numpy(), counts.cpu().numpy(), ref))
+                acc["flags_equal"] = bool(np.array_equal(fl.cpu().numpy().astype(np.uint32) & 3, ref.flags & 3))
+                case["accuracy_vs_fp64_oracle"] = acc
+                case["cpu_baseline"] = {"value": n / t_cpu, "unit": UNIT, "cores": os.cpu_count() or 1,
+                                        "kind": "oracle", "sample": "all 4096 receivers (%.2f s)" % t_cpu}
+            res["cases"]["%s_%s" % ("zpol" if pol[2] else "ypol", name)] = case
+    return res
 
 
 def extended_room(args, creep, dev, flush, peak_fn, base_ms):
@@ -539,10 +662,13 @@ def office_large(args, creep, dev, flush):
     furniture boxes), 100 PEC cylinders and 10 PEC spheres, 1M receivers at
     1.2 m, 5.8 GHz, reflections up to order 3 from the candidate list of a
     4096-ray launch per transmitter, first-order creeping; four transmitters
-    in turn.  Each transmitter's evaluation is timed (the candidate list is
-    host work, reported beside it); 32 sampled receivers of the first
-    transmitter (within 10 m of it; half of them among those with a path)
-    against the oracle with the same candidate list."""
+    in turn.  A transmitter's step = its ray launch (candidate list), the
+    list's upload, and the evaluation of every receiver, timed end to end
+    on the host clock around a synchronised step (the evaluation alone with
+    CUDA events beside it).  Against the oracle: the first transmitter's
+    candidate list (the oracle's own launch, whole office), then 256 sampled
+    receivers within 10 m of it (half among those with a path) evaluated by
+    the oracle with ITS list."""
     import torch
     from paper_2310_10578_gb300 import scenes
     sc = scenes.office()
@@ -552,67 +678,84 @@ def office_large(args, creep, dev, flush):
     out = torch.empty((n_f, 3, n, 2), dtype=torch.float32, device=dev)
     opts = creep.options(max_order=3)
     st = torch.cuda.current_stream()
-    per_tx, host_s, n_cand = [], [], []
+    step_ms, eval_ms, cand_ms, n_cand, cands = [], [], [], [], []
     for i, t in enumerate(sc.txs):
         S.set_tx(t, sc.pol)
-        t0 = time.perf_counter()
-        cand = S.candidates(4096, 3)
-        host_s.append(time.perf_counter() - t0)
-        n_cand.append(int(len(cand)))
-        S.set_candidates(cand)
-        if i == 0:
-            cand0 = cand
+        S.set_candidates(S.candidates(4096, 3))          # warm-up of this transmitter
         S.evaluate(rx, out=out, opts=opts)
         torch.cuda.synchronize()
-        ms = []
+        stp, evm, cdm = [], [], []
         for k in range(2):
             flush.fill_(float(k))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            cand = S.candidates(4096, 3)
+            S.set_candidates(cand)
+            t1 = time.perf_counter()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(st)
             S.evaluate(rx, out=out, opts=opts)
             e1.record(st)
-            ms.append((e0, e1))
-        torch.cuda.synchronize()
-        per_tx.append(float(np.mean([a.elapsed_time(b) for a, b in ms])))
+            torch.cuda.synchronize()
+            t2 = time.perf_counter()
+            stp.append(1e3 * (t2 - t0))
+            cdm.append(1e3 * (t1 - t0))
+            evm.append(e0.elapsed_time(e1))
+        step_ms.append(float(np.mean(stp)))
+        eval_ms.append(float(np.mean(evm)))
+        cand_ms.append(float(np.mean(cdm)))
+        n_cand.append(int(len(cand)))
+        cands.append(cand)
         if i == 0:
             E0 = out.detach().cpu().numpy().astype(np.float64)
-    total_ms = float(np.sum(per_tx))
+    total_ms = float(np.sum(step_ms))
     res = {"workload": sc.name, "value": len(sc.txs) * n * n_f / (total_ms / 1e3), "unit": UNIT,
-           "ms_per_step": total_ms, "ms_per_tx": per_tx, "candidates_per_tx": n_cand,
-           "candidate_host_ms_per_tx": [1e3 * x for x in host_s], "n_triangles": int(sc.tri.shape[0]),
-           "gpu_launches_per_step": 3 * len(sc.txs), "roofline": None,
-           "roofline_note": "visibility goes through a BVH; the oracle's work counters count brute-force "
-                            "segment-triangle tests, which are not this kernel's work",
-           "l2": "flushed between timed evaluations (256 MiB write)"}
+           "ms_per_step": total_ms, "step": "per transmitter: ray launch (candidate list) + upload + evaluation",
+           "ms_per_tx": step_ms, "ms_evaluation_per_tx": eval_ms, "ms_candidates_per_tx": cand_ms,
+           "value_evaluation_only": len(sc.txs) * n * n_f / (float(np.sum(eval_ms)) / 1e3),
+           "candidates_per_tx": n_cand, "n_triangles": int(sc.tri.shape[0]),
+           "gpu_launches_per_step": S.stats()["kernel_launches"] * len(sc.txs), "roofline": None,
+           "l2": "flushed between timed steps (256 MiB write)"}
     if not args.no_cpu_baseline:
         from oracle import oracle
         sys.path.insert(0, os.path.join(ROOT, "tests"))
         from parity import compare_fields, path_mismatches
         oracle.build()
         sc.tx = np.asarray(sc.txs[0], dtype=np.float32)
-        sc.candidates = cand0
+        t0 = time.perf_counter()
+        ocand = oracle.candidates(sc, 4096, 3)
+        t_cand = time.perf_counter() - t0
+        res["candidate_list_equals_oracle"] = bool(np.array_equal(ocand, cands[0]))
+        res["oracle_candidates_s"] = t_cand
+        sc.candidates = ocand
         # (receivers within 10 m of the transmitter: most of the building is
         # walled off from it and has no path at all)
         near = np.nonzero(np.hypot(sc.rx[:, 0] - sc.txs[0][0], sc.rx[:, 1] - sc.txs[0][1]) < 10.0)[0]
         # and, as the furniture hides most of them, half of the sample among
         # those with at least one path
         S.set_tx(sc.txs[0], sc.pol)
-        S.set_candidates(cand0)
+        S.set_candidates(ocand)
         _, cnt_near, _ = S.paths(torch.tensor(sc.subset(near).rx_soa(), device=dev), opts=opts)
         torch.cuda.synchronize()
         lit = near[cnt_near.cpu().numpy() > 0]
         rng = np.random.default_rng(93)
-        idx = np.unique(np.concatenate([rng.choice(near, 16, replace=False),
-                                        rng.choice(lit, min(16, len(lit)), replace=False)]))
+        idx = np.unique(np.concatenate([rng.choice(near, 128, replace=False),
+                                        rng.choice(lit, min(128, len(lit)), replace=False)]))
+        sub = sc.subset(idx)
         t0 = time.perf_counter()
-        ref = oracle.evaluate(sc.subset(idx))
+        ref = oracle.evaluate(sub)
         t_cpu = time.perf_counter() - t0
-        Eg = (E0[..., 0] + 1j * E0[..., 1])[:, :, idx]
-        acc = compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs, check=False)
-        codes, counts, _ = S.paths(torch.tensor(sc.subset(idx).rx_soa(), device=dev), opts=opts)
+        Eg = S.evaluate(torch.tensor(sub.rx_soa(), device=dev), opts=opts).cpu().numpy().astype(np.float64)
+        acc = compare_fields(Eg[..., 0] + 1j * Eg[..., 1], ref, flags=ref.flags, freqs=sc.freqs, check=False)
+        if res["candidate_list_equals_oracle"]:
+            # the timed evaluation's own output at those receivers
+            Et = (E0[..., 0] + 1j * E0[..., 1])[:, :, idx]
+            acc["timed_output_equals_sample_evaluation"] = bool(np.array_equal(Et, Eg[..., 0] + 1j * Eg[..., 1]))
+        codes, counts, _ = S.paths(torch.tensor(sub.rx_soa(), device=dev), opts=opts)
         torch.cuda.synchronize()
         acc["path_list_mismatches"] = len(path_mismatches(codes.cpu().numpy(), counts.cpu().numpy(), ref))
-        res["accuracy_vs_fp64_oracle"] = dict(acc, sample_receivers=len(idx), transmitter=0)
+        res["accuracy_vs_fp64_oracle"] = dict(acc, sample_receivers=len(idx), transmitter=0,
+                                              candidate_list="the oracle's own ray launch")
         res["cpu_baseline"] = {"value": len(idx) * n_f / t_cpu, "unit": UNIT, "cores": os.cpu_count() or 1,
                                "kind": "oracle (brute-force visibility)",
                                "sample": "the accuracy sample (%.1f s)" % t_cpu}
@@ -692,6 +835,14 @@ def main():
         e2e_once()
         e2e_t.append(time.perf_counter() - t0)
     barrier()
+    gathered = None
+    if world > 1:
+        # the optional gather of the ranks' slices into the job's layout
+        # (after the timed regions; the evaluation itself exchanges nothing)
+        from paper_2310_10578_gb300 import shard
+        full = shard.gather_fields(out, 256 * 256 * world)
+        if rank == 0:
+            gathered = {"shape": list(full.shape), "finite": bool(torch.isfinite(full).all())}
     props = torch.cuda.get_device_properties(dev)
     # measured FP32 FFMA and SFU rates (microbenchmarks of the library), the
     # roofline's denominators; the peak derived from unit counts and clock
@@ -726,6 +877,11 @@ def main():
     ext = None
     if world == 1 and not args.no_extended:
         ext = extended_room(args, creep, dev, flush, peak_fn, float(np.mean(dev_ms)))
+    fp64 = ring = None
+    if world == 1 and not args.no_fp64:
+        fp64 = room_fp64(args, creep, dev, flush, float(np.mean(dev_ms)))
+    if world == 1 and not args.no_ring:
+        ring = sphere_ring_bench(args, creep, dev, flush)
     clocks = sampler.stop() if sampler else None
 
     ms, e2e_s = max_over_ranks([np.mean(dev_ms), np.mean(e2e_t)], device=dev)
@@ -752,6 +908,10 @@ def main():
             "roofline": None, "cpu_baseline": None}
     stats = S.stats()
     line["config"]["fp64_escalated_candidates"] = stats["escalated_candidates"]
+    if world > 1:
+        line["config"]["sharding"] = {"job_receivers": 256 * 256 * world, "per_rank": n_rx,
+                                      "partition": "contiguous receiver ranges, no data-path collective",
+                                      "gathered_on_rank0": gathered}
     if world == 1 and not args.no_cpu_baseline:
         E_gpu = out.detach().cpu().numpy().astype(np.float64)
         E_gpu = E_gpu[..., 0] + 1j * E_gpu[..., 1]
@@ -781,6 +941,10 @@ def main():
         line["extended_paths"] = ext
     if office is not None:
         line["office"] = office
+    if fp64 is not None:
+        line["fp64"] = fp64
+    if ring is not None:
+        line["sphere_ring"] = ring
     print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -256,9 +256,11 @@ int rt_evaluate_host(rt_scene *scene, const float *rx_soa, int n_rx, float *e_ou
  *     768 + n_rx * (16 + 24 * n_f) bytes (rounded up to 256-byte sections);
  *     larger requests fail with RT_ERR_OVERFLOW before any work is queued.
  *     With 3 frequencies that is up to about 95 000 receivers per call.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *   - rt_scene_create looks up the array's device address
+ *     (cudaGetSymbolAddress) on the device current at creation, which also
+ *     loads the module holding it; the entry point itself only reads the
+ *     stored address.  Call it with the scene's device current
+ *     (RT_ERR_STATE otherwise).
  *   - All calls on a device share the one array and leave their data in it;
  *     nothing in it needs clearing, since each call overwrites what it reads.
  *     Calls whose GPU work overlaps (other threads, other streams) race on

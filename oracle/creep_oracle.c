@@ -1033,9 +1033,14 @@ int oracle_candidates(const double *tri, const int *tri_face, int n_tri, const d
     memset(&s, 0, sizeof(s));
     s.n_tri = n_tri; s.tri = tri; s.tri_face = tri_face;
     build_faces(&s);
-    int n_all = 0;
-    int *all = (int *)malloc(sizeof(int) * 3 * (size_t)(n_rays > 0 ? n_rays : 1) * (max_order > 0 ? max_order : 1));
+    /* ray i records its prefixes in slots i * max_order + k (unused slots
+     * keep face -2 and are dropped), so the rays are independent */
+    const int mo = max_order > 0 ? max_order : 1;
+    const size_t n_slot = (size_t)(n_rays > 0 ? n_rays : 1) * mo;
+    int *slot = (int *)malloc(sizeof(int) * 3 * n_slot);
+    for (size_t q = 0; q < 3 * n_slot; ++q) slot[q] = -2;
     const double golden = M_PI * (3.0 - sqrt(5.0));
+#pragma omp parallel for schedule(dynamic, 8)
     for (int i = 0; i < n_rays; ++i) {
         double z = 1.0 - (2.0 * i + 1.0) / n_rays;
         double r = sqrt(fmax(0.0, 1.0 - z * z));
@@ -1053,14 +1058,19 @@ int oracle_candidates(const double *tri, const int *tri_face, int n_tri, const d
             if (bt < 0) break;
             int f = tri_face[bt];
             fs[k] = f;
-            for (int m = 0; m < 3; ++m) all[3 * n_all + m] = (m <= k) ? fs[m] : -1;
-            ++n_all;
+            int *q = slot + 3 * ((size_t)i * mo + k);
+            for (int m = 0; m < 3; ++m) q[m] = (m <= k) ? fs[m] : -1;
             v3 n = s.faces[f].n;
             o = add(o, scl(d, best));
             d = sub(d, scl(n, 2.0 * dot(d, n)));
             last = f;
         }
     }
+    int n_all = 0;
+    int *all = (int *)malloc(sizeof(int) * 3 * n_slot);
+    for (size_t q = 0; q < n_slot; ++q)
+        if (slot[3 * q] != -2) { memcpy(all + 3 * n_all, slot + 3 * q, 3 * sizeof(int)); ++n_all; }
+    free(slot);
     /* sort by (order, faces) and keep the distinct ones */
     qsort(all, (size_t)n_all, 3 * sizeof(int), seq_cmp);
     int n = 0;

@@ -97,20 +97,5 @@ def power_db(E, zone=None):
 # ---- several GPUs: receivers are independent, so each rank evaluates a
 # contiguous share of them and the parameter gradients (body centres and
 # radii, transmitter, frequencies) are summed over the ranks: the one
-# collective of the adjoint.
-
-def shard(n_rx, rank, world):
-    """The contiguous receiver range [lo, hi) of `rank` of `world` ranks."""
-    base, extra = divmod(int(n_rx), int(world))
-    lo = rank * base + min(rank, extra)
-    return lo, lo + base + (1 if rank < extra else 0)
-
-
-def allreduce_gradients(tensors, group=None):
-    """Sum each tensor over the ranks in place (no-op on one process)."""
-    import torch.distributed as dist
-    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size(group) == 1:
-        return tensors
-    for t in tensors:
-        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
-    return tensors
+# collective of the adjoint (shard.py holds both).
+from .shard import allreduce_gradients, shard  # noqa: E402,F401

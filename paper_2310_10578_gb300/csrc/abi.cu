@@ -293,6 +293,8 @@ static int prep_freqs(const double *f_hz, int n_f, FreqC *fq, double *hl, const 
     return RT_OK;
 }
 
+static int noalloc_lookup(int dev);
+
 extern "C" {
 
 const char *rt_last_error(void) { return g_err.c_str(); }
@@ -307,6 +309,13 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
     if (n_body > RT_MAX_BODIES) return fail(RT_ERR_OVERFLOW, "rt_scene_create: %d bodies > %d", n_body, RT_MAX_BODIES);
     rt_scene *s = new rt_scene();
     cudaGetDevice(&s->device);
+    // the no-allocation entry point's fixed device array: its address is
+    // looked up here, with the scene's device current, so that the module
+    // holding it is loaded now and not by a later rt_evaluate_host_noalloc
+    {
+        int rcn = noalloc_lookup(s->device);
+        if (rcn != RT_OK) { delete s; return rcn; }
+    }
     s->n_tri = n_tri;
     s->n_body = n_body;
     s->tri.assign(tri_xyz, tri_xyz + 9 * (size_t)n_tri);
@@ -1203,6 +1212,23 @@ void *g_noalloc_ptr[NOALLOC_MAX_DEVICES];   // device address per device (nullpt
 size_t round256(size_t n) { return (n + 255) & ~(size_t)255; }
 }  // namespace
 
+// The array's device address on device dev (current), looked up once.  Called
+// by rt_scene_create, so the lookup (and the lazy load of this file's module,
+// which holds the array) happens when a scene is made, not inside an
+// evaluation.
+static int noalloc_lookup(int dev) {
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(RT_ERR_ARG, "device %d beyond the library's limit", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(RT_ERR_CUDA, "cudaGetSymbolAddress of the no-allocation array: %s", cudaGetErrorString(e));
+        g_noalloc_ptr[dev] = p;
+    }
+    return RT_OK;
+}
+
 extern "C" int rt_evaluate_host_noalloc(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags,
                                         const rt_options *opt, void *stream) {
     if (!s) return fail(RT_ERR_ARG, "rt_evaluate_host_noalloc: NULL scene");
@@ -1222,17 +1248,16 @@ extern "C" int rt_evaluate_host_noalloc(rt_scene *s, const float *rx_soa, int n_
                     n_rx, (int)nf, need, RT_NOALLOC_SCRATCH_BYTES);
     int dev = 0;
     CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(RT_ERR_ARG, "rt_evaluate_host_noalloc: device %d", dev);
+    // the scene's buffers live on s->device: pairing them with another
+    // device's array would be a cross-device access
+    if (dev != s->device)
+        return fail(RT_ERR_STATE, "rt_evaluate_host_noalloc: device %d is current, the scene lives on device %d", dev,
+                    s->device);
     void *base = nullptr;
     {
+        int rcn = noalloc_lookup(dev);      // done by rt_scene_create; a no-op here
+        if (rcn != RT_OK) return rcn;
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_ptr[dev]) {
-            void *p = nullptr;
-            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-            if (e != cudaSuccess || !p)
-                return fail(RT_ERR_CUDA, "rt_evaluate_host_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-            g_noalloc_ptr[dev] = p;
-        }
         base = g_noalloc_ptr[dev];
     }
     float *d_rx = (float *)base;

@@ -1,12 +1,26 @@
-// eval_fields.cu -- the per-receiver field kernel (sm_103a).
+// eval_fields.cu -- the per-receiver field kernels (sm_103a).
 //
-// One thread evaluates one receiver P: it enumerates the candidate ray paths
-// (direct; planar image reflections of order 1 and 2; per convex body the
-// GO reflection and the creeping ray each way round), decides each path's
-// existence and visibility, and sums the coherent field of the valid ones
-// over the frequencies of the launch (Eqs. 1-4 of the paper; the surface-ray
-// geometry of Fig. 1).  Scene geometry and the Fock--Pekeris table are
-// staged in shared memory per block.
+// For every receiver P the method enumerates the candidate ray paths (direct;
+// planar image reflections of order 1 and 2, or the candidate face sequences
+// of a large scene; per convex body the GO reflection and the creeping ray
+// each way round, optionally with extra turns and fed by a wall reflection),
+// decides each path's existence and visibility, and sums the coherent field
+// of the valid ones over the frequencies (Eqs. 1-4 of the paper; the
+// surface-ray geometry of Fig. 1).
+//
+// Work split.  One evaluation is a few class kernels k_eval<T, PATHS, CLS>
+// on the caller's stream, one per path class (planar, body reflection,
+// creeping, wall -> creeping), launched as programmatic dependents so that
+// each one's geometry work overlaps the previous one's tail.  Blocks are
+// persistent: they take work units of tiles of 32 consecutive receivers from
+// an atomic queue; the warps of a tile split its candidates (warp p takes
+// body b = p mod the tile's warps, planar candidate k = p mod ...) and their
+// partial fields are summed in shared memory in warp order, so a result does
+// not depend on timing.  The body classes (FP32 fields) run two passes per
+// tile: a geometry pass that writes one record per valid path to shared
+// memory, then, after a block barrier, a field pass over the records per
+// frequency chunk.  Scene geometry, source images, body frames and the
+// Fock--Pekeris table are staged in shared memory per block.
 //
 // Precision (RT_PREC_FP32): geometry and field math in FP32; every
 // existence/visibility decision is computed with a margin in metres and is
@@ -314,7 +328,11 @@ __device__ __forceinline__ int blocked_impl(const Ctx &c, v3t<T> A, v3t<T> B, in
         v3t<float> Af = mk3<float>(to_float(A.x), to_float(A.y), to_float(A.z));
         v3t<float> Bf = mk3<float>(to_float(B.x), to_float(B.y), to_float(B.z));
         if (c.bvh) {
-            if (tris_bvh(c, A, B, sf1, sf2, band) == D_YES) return D_YES;
+            // D_UNSURE here is a traversal-stack overflow (the FP64 triangle
+            // tests are exact): the segment is then never reported visible.
+            // The host build bounds the depth so that it cannot happen.
+            const int rb = tris_bvh(c, A, B, sf1, sf2, band);
+            if (rb != D_NO) return rb;
         }
         for (int t = 0; t < (c.bvh ? 0 : c.n_tri); ++t) {
             int f = __float_as_int(c.tri[3 * t].w);

@@ -67,7 +67,50 @@ def compare_fields(Eg, ref, flags=None, freqs=None, tol_rel=TOL_REL, dl=DL_FP32,
         if check:
             assert db.max() <= db_tol, stats
             assert ph.max() <= ph_tol, stats
+    stats.update(all_samples(Eg, Eo, sabs, flags, db_tol, ph_tol))
     return stats
+
+
+KAPPA_BINS = (1.0, 2.0, 5.0, 10.0, 100.0, 1e3, np.inf)
+
+
+def all_samples(Eg, Eo, sabs, flags=None, db_tol=0.05, ph_tol=1e-3):
+    """|dB| and phase errors over EVERY compared sample (each frequency and
+    receiver with a field and no semantic flag), whatever its conditioning,
+    with the histogram of kappa = sum|E_path| / |E| and the worst errors per
+    kappa bin.  Reported beside the kappa <= KAPPA_MAX statistics; nothing is
+    asserted here (the per-sample bound of compare_fields is the assertion)."""
+    amp_o = np.linalg.norm(Eo, axis=1)
+    amp_g = np.linalg.norm(Eg, axis=1)
+    ok = amp_o > 0
+    if flags is not None:
+        ok &= (np.asarray(flags)[None, :] & FLAG_SEMANTIC) == 0
+    out = {"n_all": int(ok.sum())}
+    if not ok.any():
+        return out
+    kap = sabs[ok] / amp_o[ok]
+    with np.errstate(divide="ignore"):
+        db = np.abs(20 * np.log10(np.maximum(amp_g[ok], 1e-300) / amp_o[ok]))
+    idx = np.argmax(np.abs(Eo), axis=1)
+    Eo_d = np.take_along_axis(Eo, idx[:, None, :], 1)[:, 0, :]
+    Eg_d = np.take_along_axis(Eg, idx[:, None, :], 1)[:, 0, :]
+    ph = np.abs(np.angle(Eg_d[ok] / Eo_d[ok]))
+    # the same error measured against the scale of the paths: |dE| / sum|E_path|
+    rel = np.linalg.norm(Eg - Eo, axis=1)[ok] / sabs[ok]
+    out.update(db_max_all=float(db.max()), db_p99_all=float(np.percentile(db, 99)),
+               ph_max_all=float(ph.max()), ph_p99_all=float(np.percentile(ph, 99)),
+               n_all_over_db_ph=int(np.sum((db > db_tol) | (ph > ph_tol))),
+               rel_to_path_sum_max_all=float(rel.max()))
+    hist = []
+    lo = 0.0
+    for hi in KAPPA_BINS:
+        m = (kap > lo) & (kap <= hi) if lo > 0 else (kap <= hi)
+        if m.any():
+            hist.append({"kappa": [lo, None if np.isinf(hi) else hi], "n": int(m.sum()),
+                         "db_max": float(db[m].max()), "ph_max": float(ph[m].max())})
+        lo = hi
+    out["kappa_hist"] = hist
+    return out
 
 
 def path_mismatches(codes, counts, ref):

@@ -45,7 +45,9 @@ def test_candidates_match_oracle(creep, oracle_mod):
 def test_office_parity(creep, oracle_mod, precision):
     sc = _small_office()
     S = creep.Scene.from_scene(sc)
-    sc.candidates = S.candidates(4096, 3)
+    # the oracle's own candidate list (the library's launch is compared with
+    # it in test_candidates_match_oracle); the GPU takes the same list
+    sc.candidates = oracle_mod.candidates(sc, 4096, 3)
     S.set_candidates(sc.candidates)
     prec = creep.RT_PREC_FP64 if precision == "fp64" else creep.RT_PREC_FP32
     opts = creep.options(max_order=3, precision=prec)
@@ -71,7 +73,7 @@ def test_office_adjoint_order3(creep, oracle_mod):
     sc.rx[:, :2] += np.random.default_rng(3).uniform(-0.02, 0.02, (sc.n_rx, 2)).astype(np.float32)
     sc.rx = sc.rx[::4].copy()
     S = creep.Scene.from_scene(sc)
-    sc.candidates = S.candidates(4096, 3)
+    sc.candidates = oracle_mod.candidates(sc, 4096, 3)
     S.set_candidates(sc.candidates)
     opts = creep.options(max_order=3)
     rx = torch.tensor(sc.rx_soa(), device="cuda")

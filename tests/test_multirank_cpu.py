@@ -1,9 +1,11 @@
 """The N > 1 host logic of bench.py on CPU, two gloo ranks.
 
 Receivers are independent (Eqs. 1-4 per receiver), so the evaluation shards
-across ranks with no data-path exchange: each rank owns a distinct receiver
-grid of the same size, the job's time is the slowest rank's, and the job's
-throughput is all ranks' samples over that time.  No GPU is used here.
+across ranks with no data-path exchange: one job's receivers split into
+contiguous ranges of the same size, each rank writes its own output slice
+(gathered into the single-rank layout afterwards), the job's time is the
+slowest rank's, and the job's throughput is all ranks' samples over that
+time.  No GPU is used here.
 """
 import os
 import socket
@@ -31,19 +33,32 @@ def _worker(rank, world, port, q):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
         import bench
+        from paper_2310_10578_gb300 import shard
         sc = bench.make_scene(rank, world)
         # a rank-dependent "time": the reduction must return the slowest rank's
         ms, e2e = bench.max_over_ranks([1.0 + rank, 10.0 - rank])
-        grids = [None] * world
-        dist.all_gather_object(grids, sc.rx[:64].copy())
+        # stand-in for the rank's field slice: a function of each receiver's
+        # coordinates in the evaluation's layout [n_f][3][n][2]
+        E = torch.tensor(_fake_fields(sc.rx, len(sc.freqs)))
+        full = shard.gather_fields(E, 256 * 256 * world)
         # the reference arm runs on rank 0 only; other ranks return without work
         rc = bench.run_reference(None) if rank != 0 else 0
-        q.put((rank, ms, e2e, sc.n_rx, len(sc.freqs), [g.tolist() for g in grids], rc))
+        q.put((rank, ms, e2e, sc.n_rx, len(sc.freqs), sc.rx.copy(), None if full is None else full.numpy(), rc))
     finally:
         dist.destroy_process_group()
 
 
-def test_two_gloo_ranks_shard_without_exchange():
+def _fake_fields(rx, n_f):
+    x, y, z = (rx[:, k].astype(np.float64) for k in range(3))
+    E = np.empty((n_f, 3, len(rx), 2), dtype=np.float32)
+    for f in range(n_f):
+        for c in range(3):
+            E[f, c, :, 0] = x * (1 + f) + c * y
+            E[f, c, :, 1] = y * (2 + c) - z * f
+    return E
+
+
+def test_two_gloo_ranks_shard_one_job_without_exchange():
     world = 2
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
@@ -51,17 +66,21 @@ def test_two_gloo_ranks_shard_without_exchange():
     procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
     for p in procs:
         p.start()
-    res = sorted(q.get(timeout=240) for _ in range(world))
+    res = sorted((q.get(timeout=240) for _ in range(world)), key=lambda t: t[0])
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
-    for rank, ms, e2e, n_rx, n_f, grids, rc in res:
+    for rank, ms, e2e, n_rx, n_f, rx, full, rc in res:
         assert ms == 2.0 and e2e == 10.0          # max over ranks, on every rank
         assert n_rx == 65536 and n_f == 3          # same per-rank work (weak scaling)
         assert rc == 0
-    g0, g1 = (np.asarray(g) for g in res[0][5])
-    assert not np.any(np.all(np.isclose(g0[:, None, :], g1[None, :, :], atol=1e-6), axis=2))   # distinct receivers
-    assert np.allclose(g1[:, 1:], g0[:, 1:]) and np.allclose(g1[:, 0] - g0[:, 0], 10.0 / 256 / 2, atol=1e-5)
+        assert (full is None) == (rank != 0)       # gathered on rank 0 only
+    # one job: the ranks' receivers are the contiguous halves of the job's grid
+    from paper_2310_10578_gb300 import scenes
+    job = scenes.room(nx=256, ny=512)
+    assert np.array_equal(np.concatenate([res[0][5], res[1][5]]), job.rx)
+    # the gather gives the single-rank layout of the whole job
+    assert np.array_equal(res[0][6], _fake_fields(job.rx, 3))
 
 
 def test_single_process_reduction_and_throughput():

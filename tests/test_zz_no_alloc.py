@@ -9,6 +9,10 @@ ABI twice in a row -- two different workloads, so a call that read stale data
 from the shared array would show -- and checks each result against the
 ordinary host entry point rt_evaluate_host (same kernel; the same parity
 tolerance as the other GPU tests applies, and the two agree exactly).
+A second test checks the promise itself: on a scene that has never seen
+rt_evaluate_host (whose staging buffers are allocated per scene), the free
+device memory the driver reports does not move across no-allocation calls,
+the later ones with more receivers than the first.
 It lives in its own file, collected last, and passes alone or after the rest.
 """
 import ctypes
@@ -58,3 +62,26 @@ def test_noalloc_entry_point_matches_host_entry_point_twice():
     with pytest.raises(creep.CreepError) as e:
         S.evaluate_host_noalloc(big)
     assert e.value.code == creep.RT_ERR_OVERFLOW and "scratch" in str(e.value)
+
+
+def test_noalloc_entry_point_allocates_nothing():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2310_10578_gb300 import creep
+    creep.load()
+    torch.cuda.synchronize()
+    sc = scenes.room(n_cyl=12, nx=160, ny=128, freqs=(2.4e9, 5.8e9, 28e9), seed=5)   # 20 480 receivers
+    S = creep.Scene.from_scene(sc)          # never given to rt_evaluate_host
+    opts = creep.options(max_order=sc.max_order)
+    rx = np.ascontiguousarray(sc.rx_soa())
+    small = np.ascontiguousarray(rx[:, :1000])
+    _host_call(creep, "rt_evaluate_host_noalloc", S, small, len(sc.freqs), opts)    # warm-up: kernels loaded
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    outs = []
+    for _ in range(2):
+        outs.append(_host_call(creep, "rt_evaluate_host_noalloc", S, rx, len(sc.freqs), opts))
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    assert np.any(outs[0][0] != 0.0)
