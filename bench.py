@@ -71,6 +71,10 @@ def parse():
     ap.add_argument("--no-extended", action="store_true",
                     help="skip the extended path set (dielectric faces, extra turns, wall->creeping)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 form of the room workload")
+    ap.add_argument("--office-rooms", type=int, nargs=2, default=(20, 15), metavar=("NX", "NY"),
+                    help="rooms of the office building (a smaller building keeps an ncu capture small)")
+    ap.add_argument("--only-office", action="store_true",
+                    help="time the office alone (no room line extras); for profiling captures")
     ap.add_argument("--no-ring", action="store_true", help="skip the sphere-ring workload")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="target CPU time of the oracle sample")
     return ap.parse_args()
@@ -671,7 +675,15 @@ def office_large(args, creep, dev, flush):
     the oracle with ITS list."""
     import torch
     from paper_2310_10578_gb300 import scenes
-    sc = scenes.office()
+    nrx, nry = args.office_rooms
+    if (nrx, nry) == (20, 15):
+        sc = scenes.office()
+    else:
+        # the same building recipe at a smaller size: furniture, bodies and
+        # receivers in proportion to the floor area
+        frac = nrx * nry / 300.0
+        sc = scenes.office(n_rooms=(nrx, nry), n_furn=int(15000 * frac), n_cyl=max(4, int(100 * frac)),
+                           n_sph=max(2, int(10 * frac)), nx=int(62.5 * nrx), ny=int(53.34 * nry))
     S = creep.Scene.from_scene(sc)
     n, n_f = sc.n_rx, len(sc.freqs)
     rx = torch.tensor(sc.rx_soa(), device=dev)
@@ -779,6 +791,11 @@ def main():
         torch.cuda.set_device(0)
     from paper_2310_10578_gb300 import build, creep
     build.build()
+    if args.only_office:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        print(json.dumps({"office": office_large(args, creep, dev, flush)}), flush=True)
+        return 0
     sc = make_scene(rank, world)
     S = creep.Scene.from_scene(sc)
     dev = torch.device("cuda", torch.cuda.current_device())
