@@ -690,43 +690,49 @@ def office_large(args, creep, dev, flush):
     out = torch.empty((n_f, 3, n, 2), dtype=torch.float32, device=dev)
     opts = creep.options(max_order=3)
     st = torch.cuda.current_stream()
-    step_ms, eval_ms, cand_ms, n_cand, cands = [], [], [], [], []
+    step_ms, cand_ms, host_ms, n_cand, cands, esc = [], [], [], [], [], []
     for i, t in enumerate(sc.txs):
         S.set_tx(t, sc.pol)
-        S.set_candidates(S.candidates(4096, 3))          # warm-up of this transmitter
+        # the host launch of the same rule, for reference (not in the step)
+        t0 = time.perf_counter()
+        host_list = S.candidates(4096, 3)
+        host_ms.append(1e3 * (time.perf_counter() - t0))
+        S.candidates_device(4096, 3)                     # warm-up of this transmitter
         S.evaluate(rx, out=out, opts=opts)
         torch.cuda.synchronize()
-        stp, evm, cdm = [], [], []
+        stp, cdm = [], []
         for k in range(2):
             flush.fill_(float(k))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            cand = S.candidates(4096, 3)
-            S.set_candidates(cand)
-            t1 = time.perf_counter()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
             e0.record(st)
-            S.evaluate(rx, out=out, opts=opts)
+            S.candidates_device(4096, 3)                 # the ray launch, on the device
             e1.record(st)
+            S.evaluate(rx, out=out, opts=opts)
+            e2.record(st)
             torch.cuda.synchronize()
-            t2 = time.perf_counter()
-            stp.append(1e3 * (t2 - t0))
-            cdm.append(1e3 * (t1 - t0))
-            evm.append(e0.elapsed_time(e1))
+            stp.append(e0.elapsed_time(e2))
+            cdm.append(e0.elapsed_time(e1))
         step_ms.append(float(np.mean(stp)))
-        eval_ms.append(float(np.mean(evm)))
         cand_ms.append(float(np.mean(cdm)))
+        esc.append(int(S.stats()["escalated_candidates"]))
+        cand = S.get_candidates()
         n_cand.append(int(len(cand)))
         cands.append(cand)
+        res_equal = bool(np.array_equal(cand, host_list))
         if i == 0:
             E0 = out.detach().cpu().numpy().astype(np.float64)
+            dev_equals_host = [res_equal]
+        else:
+            dev_equals_host.append(res_equal)
     total_ms = float(np.sum(step_ms))
     res = {"workload": sc.name, "value": len(sc.txs) * n * n_f / (total_ms / 1e3), "unit": UNIT,
-           "ms_per_step": total_ms, "step": "per transmitter: ray launch (candidate list) + upload + evaluation",
-           "ms_per_tx": step_ms, "ms_evaluation_per_tx": eval_ms, "ms_candidates_per_tx": cand_ms,
-           "value_evaluation_only": len(sc.txs) * n * n_f / (float(np.sum(eval_ms)) / 1e3),
+           "ms_per_step": total_ms,
+           "step": "per transmitter: the device ray launch (4096 rays, candidate list) + the evaluation, one stream",
+           "ms_per_tx": step_ms, "ms_candidates_per_tx": cand_ms, "ms_host_launch_per_tx_reference": host_ms,
+           "device_list_equals_host_launch": dev_equals_host,
            "candidates_per_tx": n_cand, "n_triangles": int(sc.tri.shape[0]),
-           "gpu_launches_per_step": S.stats()["kernel_launches"] * len(sc.txs), "roofline": None,
+           "fp64_escalated_candidates_per_tx": esc,
+           "gpu_launches_per_step": (S.stats()["kernel_launches"] + 2) * len(sc.txs), "roofline": None,
            "l2": "flushed between timed steps (256 MiB write)"}
     if not args.no_cpu_baseline:
         from oracle import oracle

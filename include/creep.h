@@ -207,6 +207,36 @@ int rt_candidates_mesh(const float *tri_xyz, const int *tri_face, int n_tri, con
  */
 int rt_set_candidates(rt_scene *scene, const int32_t *seq, int n);
 
+/*
+ * The ray launch of rt_candidates run on the device and installed as the
+ * scene's candidate list, as rt_set_candidates would install the list
+ * rt_candidates returns (the same sequences in the same order, so the same
+ * path codes; the same FP64 arithmetic, rounded operation by operation as
+ * the host launch rounds it), with no host round trip: the class kernels of
+ * a later evaluation on `stream` read the list and its length from device
+ * memory.  Sec. III's path search, in the form of the candidate rule above.
+ *   n_rays x max_order <= RT_DEV_CAND_SLOTS; max_order 1-3; fewer than
+ *   2^20 - 1 faces.
+ * Asynchronous on `stream` (CUDA stream or NULL), except on the first call
+ * and whenever n_rays changes, which upload the launch's directions and
+ * face normals synchronously (library-owned device buffers, freed with the
+ * scene).  The list belongs to the current transmitter: rt_set_tx and
+ * rt_set_candidates drop it.  Errors: RT_ERR_ARG (sizes), RT_ERR_STATE (no
+ * transmitter, no triangles, another device current), RT_ERR_OVERFLOW
+ * (faces), RT_ERR_CUDA.
+ */
+#define RT_DEV_CAND_SLOTS 16384
+int rt_candidates_device(rt_scene *scene, int n_rays, int max_order, void *stream);
+
+/*
+ * The scene's current candidate list into host int32 seq [cap][3] (-1
+ * padded); *n_out receives its length (sequences beyond cap are not
+ * written).  A device-built list is copied back after its stream
+ * synchronises.  Errors: RT_ERR_ARG, RT_ERR_OVERFLOW (a traversal stack of
+ * the device launch overflowed: no list), RT_ERR_CUDA.
+ */
+int rt_get_candidates(rt_scene *scene, int32_t *seq, int cap, int *n_out);
+
 /* Frequencies (host double[n_f], Hz, > 0), 1 <= n_f <= RT_MAX_FREQS. */
 int rt_set_freqs(rt_scene *scene, const double *f_hz, int n_f);
 

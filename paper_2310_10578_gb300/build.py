@@ -15,7 +15,10 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcreep.so")
-SOURCES = ["abi.cu", "eval_fields.cu", "fock_table.cu", "rx_order.cu", "peaks.cu", "bvh.cu"]
+SOURCES = ["abi.cu", "eval_fields.cu", "fock_table.cu", "rx_order.cu", "peaks.cu", "bvh.cu", "candidates.cu"]
+# per-file flags: the device ray launch rounds every FP64 operation as the
+# host launch does (no fused multiply-add), so both trace identical rays
+FILE_FLAGS = {"candidates.cu": ["-fmad=false"]}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # host code: -ffp-contract=off so that host-side FP64 decisions (per-transmitter
 # precomputation) round as written on every host ISA
@@ -46,7 +49,7 @@ def build(force=False, verbose=False, extra=()):
 
     def compile_one(src):
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
-        cmd = [exe, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj]
+        cmd = [exe, *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), *extra, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("nvcc failed for %s:\n%s\n%s" % (src, " ".join(cmd), r.stderr))

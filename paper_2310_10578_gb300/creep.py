@@ -28,7 +28,8 @@ EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "
            "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats", "rt_backward", "rt_alu_peaks",
            "rt_evaluate_with_paths", "rt_batch_set_shape", "rt_batch_get_shape", "rt_batch_tune",
            "rt_set_shape", "rt_get_shape", "rt_tune", "rt_set_face_materials", "rt_candidates",
-           "rt_set_candidates", "rt_candidates_mesh")
+           "rt_set_candidates", "rt_candidates_mesh", "rt_candidates_device", "rt_get_candidates")
+RT_DEV_CAND_SLOTS = 16384
 RT_NOALLOC_SCRATCH_BYTES = 8 << 20
 
 
@@ -99,6 +100,8 @@ def load(build_if_missing=True):
     lib.rt_candidates.argtypes = [P, I, I, P, I, ctypes.POINTER(I)]
     lib.rt_set_candidates.argtypes = [P, P, I]
     lib.rt_candidates_mesh.argtypes = [P, P, I, P, I, I, P, I, ctypes.POINTER(I)]
+    lib.rt_candidates_device.argtypes = [P, I, I, P]
+    lib.rt_get_candidates.argtypes = [P, P, I, ctypes.POINTER(I)]
     _lib = lib
     return lib
 
@@ -173,6 +176,19 @@ class Scene:
         _check(_lib.rt_candidates(self._h, int(n_rays), int(max_order), None, 0, ctypes.byref(n)))
         out = np.zeros((max(n.value, 1), 3), dtype=np.int32)
         _check(_lib.rt_candidates(self._h, int(n_rays), int(max_order), _ptr(out), n.value, ctypes.byref(n)))
+        return out[:n.value]
+
+    def candidates_device(self, n_rays, max_order=3, stream=None):
+        """The same ray launch on the device, installed as the candidate list
+        (rt_candidates_device; asynchronous on the stream)."""
+        _check(_lib.rt_candidates_device(self._h, int(n_rays), int(max_order), _stream_handle(stream)))
+
+    def get_candidates(self):
+        """The current candidate list [n, 3] int32 (rt_get_candidates)."""
+        n = ctypes.c_int(0)
+        _check(_lib.rt_get_candidates(self._h, None, 0, ctypes.byref(n)))
+        out = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+        _check(_lib.rt_get_candidates(self._h, _ptr(out), n.value, ctypes.byref(n)))
         return out[:n.value]
 
     def set_candidates(self, seq):

@@ -138,6 +138,15 @@ struct rt_scene {
     int4 *d_cand = nullptr;
     float4 *d_cimg = nullptr;           // [n_cand][3][2]
     int n_cand = 0;
+    // a candidate list built on the device (rt_candidates_device): in use
+    // while cand_dev is set (rt_set_tx and rt_set_candidates clear it); its
+    // length lives in device memory (dcb.n_cand[0])
+    bool cand_dev = false;
+    DevCandBufs dcb = {};
+    int dcb_rays = 0;                   // rays whose directions dcb.dir holds
+    float4 *d_lbvh = nullptr;           // the BVH for the launch when the scene has too few triangles for d_bvh
+    int *d_lbvh_tri = nullptr;
+    cudaStream_t cand_stream = nullptr;
     unsigned long long *d_esc = nullptr;   // [CTR_N]: FP64-decided candidates, then one work queue per launch
     DevTable *table = nullptr;
     // state
@@ -184,6 +193,8 @@ static void free_scene(rt_scene *s) {
     cudaFree(s->d_esc); cudaFree(s->io_rx); cudaFree(s->io_e); cudaFree(s->io_fl); cudaFree(s->d_img); cudaFree(s->d_txb);
     cudaFree(s->d_txw); cudaFree(s->d_bvh); cudaFree(s->d_bvh_tri); cudaFree(s->d_cand); cudaFree(s->d_cimg);
     cudaFree(s->d_face_mat);
+    cudaFree(s->dcb.dir); cudaFree(s->dcb.fn); cudaFree(s->dcb.keys); cudaFree(s->dcb.cand); cudaFree(s->dcb.cimg);
+    cudaFree(s->dcb.n_cand); cudaFree(s->d_lbvh); cudaFree(s->d_lbvh_tri);
 }
 
 // distance from point p to the solid of body b (0 if inside)
@@ -516,6 +527,7 @@ int rt_set_tx(rt_scene *s, const float tx[3], const float pol[3]) {
     }
     s->tx_set = true;
     ++s->tx_version;
+    s->cand_dev = false;                 // a device-built list belongs to the previous transmitter
     if (s->n_cand > 0) return upload_candidates(s);
     return RT_OK;
 }
@@ -569,6 +581,7 @@ int rt_set_candidates(rt_scene *s, const int32_t *seq, int n) {
     }
     s->cand.assign(seq, seq + 3 * (size_t)n);
     s->n_cand = n;
+    s->cand_dev = false;
     if (!s->tx_set) return RT_OK;            // the images follow with the transmitter
     return upload_candidates(s);
 }
@@ -608,6 +621,80 @@ int rt_candidates(rt_scene *s, int n_rays, int max_order, int32_t *seq, int cap,
     for (int q = 0; q < n && q < cap; ++q)
         for (int m = 0; m < 3; ++m) seq[3 * (size_t)q + m] = out[3 * (size_t)q + m];
     *n_out = n;
+    return RT_OK;
+}
+
+int rt_candidates_device(rt_scene *s, int n_rays, int max_order, void *stream) {
+    if (!s) return fail(RT_ERR_ARG, "rt_candidates_device: NULL scene");
+    if (n_rays < 1 || max_order < 1 || max_order > 3 || (long long)n_rays * max_order > RT_DEV_CAND_SLOTS)
+        return fail(RT_ERR_ARG, "rt_candidates_device: n_rays x max_order = %lld not in [1, %d] (max_order 1-3)",
+                    (long long)n_rays * max_order, RT_DEV_CAND_SLOTS);
+    if (!s->tx_set) return fail(RT_ERR_STATE, "rt_candidates_device: transmitter not set");
+    if (s->n_tri < 1) return fail(RT_ERR_STATE, "rt_candidates_device: no triangles");
+    if (s->n_face >= (1 << 20) - 1) return fail(RT_ERR_OVERFLOW, "rt_candidates_device: %d faces", s->n_face);
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    if (dev != s->device) return fail(RT_ERR_STATE, "rt_candidates_device: the scene lives on device %d", s->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    // set-up on first use (or for a new ray count): synchronous uploads of
+    // the launch's inputs; later calls with the same ray count only queue
+    // the two kernels
+    if (!s->dcb.keys) {
+        std::vector<double> fn;
+        ray_face_normals(s->tri.data(), s->tri_face.data(), s->n_tri, s->n_face, fn);
+        CK(cudaMalloc(&s->dcb.fn, sizeof(double) * fn.size()));
+        CK(cudaMemcpy(s->dcb.fn, fn.data(), sizeof(double) * fn.size(), cudaMemcpyHostToDevice));
+        CK(cudaMalloc(&s->dcb.keys, sizeof(unsigned long long) * RT_DEV_CAND_SLOTS));
+        CK(cudaMalloc(&s->dcb.cand, sizeof(int4) * RT_DEV_CAND_SLOTS));
+        CK(cudaMalloc(&s->dcb.cimg, sizeof(float4) * 6 * (size_t)RT_DEV_CAND_SLOTS));
+        CK(cudaMalloc(&s->dcb.n_cand, sizeof(int) * 2));
+        CK(cudaMemset(s->dcb.n_cand, 0, sizeof(int) * 2));
+        if (!s->d_bvh) {
+            CK(cudaMalloc(&s->d_lbvh, sizeof(float4) * s->h_bvh.size()));
+            CK(cudaMalloc(&s->d_lbvh_tri, sizeof(int) * s->h_bvh_tri.size()));
+            CK(cudaMemcpy(s->d_lbvh, s->h_bvh.data(), sizeof(float4) * s->h_bvh.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(s->d_lbvh_tri, s->h_bvh_tri.data(), sizeof(int) * s->h_bvh_tri.size(), cudaMemcpyHostToDevice));
+        }
+    }
+    if (s->dcb_rays != n_rays) {
+        std::vector<double> dir;
+        ray_directions(n_rays, dir);
+        cudaFree(s->dcb.dir);
+        s->dcb.dir = nullptr;
+        s->dcb_rays = 0;
+        CK(cudaMalloc(&s->dcb.dir, sizeof(double) * dir.size()));
+        CK(cudaMemcpy(s->dcb.dir, dir.data(), sizeof(double) * dir.size(), cudaMemcpyHostToDevice));
+        s->dcb_rays = n_rays;
+    }
+    const double p[3] = {s->tx[0], s->tx[1], s->tx[2]};
+    int rc = launch_ray_candidates(s->d_tri, s->d_bvh ? s->d_bvh : s->d_lbvh, s->d_bvh ? s->d_bvh_tri : s->d_lbvh_tri,
+                                   s->d_face64, p, n_rays, max_order, s->dcb, st);
+    if (rc != RT_OK) return rc;
+    s->cand_dev = true;
+    s->cand_stream = st;
+    return RT_OK;
+}
+
+int rt_get_candidates(rt_scene *s, int32_t *seq, int cap, int *n_out) {
+    if (!s || !n_out || cap < 0 || (cap > 0 && !seq)) return fail(RT_ERR_ARG, "rt_get_candidates: bad argument");
+    if (!s->cand_dev) {
+        for (int q = 0; q < s->n_cand && q < cap; ++q)
+            for (int m = 0; m < 3; ++m) seq[3 * (size_t)q + m] = s->cand[3 * (size_t)q + m];
+        *n_out = s->n_cand;
+        return RT_OK;
+    }
+    CK(cudaStreamSynchronize(s->cand_stream));
+    int h[2] = {0, 0};
+    CK(cudaMemcpy(h, s->dcb.n_cand, sizeof(h), cudaMemcpyDeviceToHost));
+    if (h[1]) return fail(RT_ERR_OVERFLOW, "rt_get_candidates: a traversal stack of the device launch overflowed");
+    std::vector<int4> c(h[0] > 0 ? h[0] : 1);
+    if (h[0] > 0) CK(cudaMemcpy(c.data(), s->dcb.cand, sizeof(int4) * h[0], cudaMemcpyDeviceToHost));
+    for (int q = 0; q < h[0] && q < cap; ++q) {
+        seq[3 * (size_t)q] = c[q].x;
+        seq[3 * (size_t)q + 1] = c[q].y;
+        seq[3 * (size_t)q + 2] = c[q].z;
+    }
+    *n_out = h[0];
     return RT_OK;
 }
 
@@ -654,12 +741,13 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, 
     if (o.max_encirclements < 0 || o.max_encirclements > 4)
         return fail(RT_ERR_ARG, "max_encirclements %d not in [0, 4]", o.max_encirclements);
     // order 3 only through a candidate list
-    const int top = s->n_cand > 0 ? 3 : 2;
+    const bool has_list = s->n_cand > 0 || s->cand_dev;
+    const int top = has_list ? 3 : 2;
     if (o.max_order < 0 || o.max_order > top) return fail(RT_ERR_ARG, "max_order %d not in [0, %d]", o.max_order, top);
     if (o.precision != RT_PREC_FP32 && o.precision != RT_PREC_FP64) return fail(RT_ERR_ARG, "bad precision %d", o.precision);
     if (o.enable & ~(RT_EN_ALL | RT_EN_WALL_CREEP)) return fail(RT_ERR_ARG, "bad enable mask 0x%x", o.enable);
     if (s->n_face > RT_MAX_ENUM_FACES) {
-        if ((o.enable & RT_EN_PLANAR) && o.max_order >= 1 && s->n_cand == 0)
+        if ((o.enable & RT_EN_PLANAR) && o.max_order >= 1 && !has_list)
             return fail(RT_ERR_STATE, "%d faces: planar paths need a candidate list (rt_set_candidates)", s->n_face);
         if (o.enable & RT_EN_WALL_CREEP)
             return fail(RT_ERR_ARG, "wall -> creeping paths: at most %d faces", RT_MAX_ENUM_FACES);
@@ -680,9 +768,18 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, 
     D.txw = s->d_txw;
     D.bvh = s->d_bvh;
     D.bvh_tri = s->d_bvh_tri;
-    D.cand = s->n_cand > 0 ? s->d_cand : nullptr;
-    D.cimg = s->d_cimg;
-    D.n_cand = s->n_cand;
+    D.bvh_nodes = s->d_bvh ? (int)(s->h_bvh.size() / 2) : 0;
+    if (s->cand_dev) {
+        D.cand = s->dcb.cand;
+        D.cimg = s->dcb.cimg;
+        D.n_cand = RT_DEV_CAND_SLOTS;           // an upper bound; the kernels read the length
+        D.n_cand_dev = s->dcb.n_cand;
+    } else {
+        D.cand = s->n_cand > 0 ? s->d_cand : nullptr;
+        D.cimg = s->d_cimg;
+        D.n_cand = s->n_cand;
+        D.n_cand_dev = nullptr;
+    }
     D.face_mat = s->any_dielectric ? s->d_face_mat : nullptr;
     memcpy(D.tx, s->tx, sizeof(D.tx));
     memcpy(D.pol, s->pol, sizeof(D.pol));

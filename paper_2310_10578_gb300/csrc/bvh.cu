@@ -5,10 +5,11 @@
 //
 // BVH: binary, median split of the triangle centroids along the longest
 // axis of their bounds, leaves of at most BVH_LEAF triangles (depth <=
-// ceil(log2(n / BVH_LEAF)) + 1 <= 32 for any n < 2^31).  Node i is two
-// float4: (box min, first) and (box max, count); count > 0: a leaf over
-// bvh_tri[first .. first + count); count == 0: an inner node with children
-// first and first + 1.  The boxes are the triangles' float bounds widened
+// ceil(log2(n / BVH_LEAF)) + 1 <= 32 for any n < 2^31), nodes numbered
+// breadth first (the top levels first).  Node i is two float4: (box min,
+// first) and (box max, count); count > 0: a leaf over bvh_tri[first ..
+// first + count); count == 0: an inner node with children first and
+// first + 1.  The boxes are the triangles' float bounds widened
 // outwards by 1e-4 m + 1e-6 of the coordinate, so an FP32 or FP64 slab test
 // with its own rounding never drops a triangle that the exact test would hit.
 //
@@ -155,17 +156,37 @@ void bvh_build(const float *tri, int n_tri, std::vector<float4> &nodes, std::vec
     }
     B.nodes.resize(2);
     B.build(0, 0, n_tri);
-    nodes.swap(B.nodes);
+    // renumber the nodes breadth first (children pairs stay adjacent), so
+    // that the top levels are the array's first nodes: the class kernels
+    // stage that prefix (the top treelet) in shared memory
+    const size_t n_nodes = B.nodes.size() / 2;
+    std::vector<int> bfs;                   // bfs[new id] = old id
+    bfs.reserve(n_nodes);
+    std::vector<int> new_id(n_nodes, -1);
+    bfs.push_back(0);
+    new_id[0] = 0;
+    for (size_t h = 0; h < bfs.size(); ++h) {
+        const int old = bfs[h];
+        if (float_bits(B.nodes[2 * (size_t)old + 1].w) == 0) {       // inner node: children first, first + 1
+            const int c = float_bits(B.nodes[2 * (size_t)old].w);
+            new_id[c] = (int)bfs.size();
+            bfs.push_back(c);
+            new_id[c + 1] = (int)bfs.size();
+            bfs.push_back(c + 1);
+        }
+    }
+    nodes.assign(2 * n_nodes, make_float4(0.f, 0.f, 0.f, 0.f));
+    for (size_t k = 0; k < n_nodes; ++k) {
+        float4 lo = B.nodes[2 * (size_t)bfs[k]], hi = B.nodes[2 * (size_t)bfs[k] + 1];
+        if (float_bits(hi.w) == 0) lo.w = int_bits(new_id[float_bits(lo.w)]);
+        nodes[2 * k] = lo;
+        nodes[2 * k + 1] = hi;
+    }
     order.swap(B.idx);
 }
 
-int ray_launch(const float *tri, const int *tri_face, int n_tri, int n_face, const std::vector<float4> &nodes,
-               const std::vector<int> &order, const double tx[3], int n_rays, int max_order,
-               std::vector<int> &seq) {
-    seq.clear();
-    if (n_tri <= 0 || n_rays <= 0 || max_order < 1) return 0;
-    // face normals from each face's first triangle
-    std::vector<V3> fn(n_face, v3(0, 0, 0));
+void ray_face_normals(const float *tri, const int *tri_face, int n_tri, int n_face, std::vector<double> &fn) {
+    fn.assign(3 * (size_t)n_face, 0.0);
     std::vector<char> has(n_face, 0);
     for (int t = 0; t < n_tri; ++t) {
         int f = tri_face[t];
@@ -174,21 +195,46 @@ int ray_launch(const float *tri, const int *tri_face, int n_tri, int n_face, con
         const float *v = tri + 9 * (size_t)t;
         V3 c = crossv(v3(v[3], v[4], v[5]) - v3(v[0], v[1], v[2]), v3(v[6], v[7], v[8]) - v3(v[0], v[1], v[2]));
         double inv = 1.0 / sqrt(dotv(c, c));
-        fn[f] = v3(c.x * inv, c.y * inv, c.z * inv);
+        fn[3 * (size_t)f] = c.x * inv;
+        fn[3 * (size_t)f + 1] = c.y * inv;
+        fn[3 * (size_t)f + 2] = c.z * inv;
     }
+}
+
+void ray_directions(int n_rays, std::vector<double> &dir) {
+    dir.resize(3 * (size_t)n_rays);
+    const double golden = M_PI * (3.0 - sqrt(5.0));
+    for (int i = 0; i < n_rays; ++i) {
+        double z = 1.0 - (2.0 * i + 1.0) / n_rays;
+        double r = sqrt(std::max(0.0, 1.0 - z * z));
+        double ph = golden * i;
+        dir[3 * (size_t)i] = r * cos(ph);
+        dir[3 * (size_t)i + 1] = r * sin(ph);
+        dir[3 * (size_t)i + 2] = z;
+    }
+}
+
+int ray_launch(const float *tri, const int *tri_face, int n_tri, int n_face, const std::vector<float4> &nodes,
+               const std::vector<int> &order, const double tx[3], int n_rays, int max_order,
+               std::vector<int> &seq) {
+    seq.clear();
+    if (n_tri <= 0 || n_rays <= 0 || max_order < 1) return 0;
+    // face normals from each face's first triangle
+    std::vector<double> fnv;
+    ray_face_normals(tri, tri_face, n_tri, n_face, fnv);
+    std::vector<V3> fn(n_face);
+    for (int f = 0; f < n_face; ++f) fn[f] = v3(fnv[3 * (size_t)f], fnv[3 * (size_t)f + 1], fnv[3 * (size_t)f + 2]);
+    std::vector<double> dirs;
+    ray_directions(n_rays, dirs);
     auto vert = [&](int t, int k) {
         const float *v = tri + 9 * (size_t)t + 3 * k;
         return v3(v[0], v[1], v[2]);
     };
     std::vector<int> all;
     all.reserve(3 * (size_t)n_rays * max_order);
-    const double golden = M_PI * (3.0 - sqrt(5.0));
     int stack[64];
     for (int i = 0; i < n_rays; ++i) {
-        double z = 1.0 - (2.0 * i + 1.0) / n_rays;
-        double r = sqrt(std::max(0.0, 1.0 - z * z));
-        double ph = golden * i;
-        V3 o = v3(tx[0], tx[1], tx[2]), d = v3(r * cos(ph), r * sin(ph), z);
+        V3 o = v3(tx[0], tx[1], tx[2]), d = v3(dirs[3 * (size_t)i], dirs[3 * (size_t)i + 1], dirs[3 * (size_t)i + 2]);
         int fs[3] = {-1, -1, -1}, last = -1;
         for (int k = 0; k < max_order && k < 3; ++k) {
             double best = INFINITY;

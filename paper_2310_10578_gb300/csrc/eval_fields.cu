@@ -48,6 +48,7 @@ constexpr int BLOCK = 128;
 constexpr int SMEM_TRI_MAX = 256;
 constexpr int SMEM_FACE_MAX = 512;
 constexpr int SMEM_BODY_MAX = 256;
+constexpr int BVH_TOP_NODES = 511;     // BVH nodes (the top 9 levels) staged in shared memory per block
 
 __device__ __forceinline__ uint64_t pcode(int type, int a, int b) {
     return ((uint64_t)type << 56) | ((uint64_t)a << 28) | (uint64_t)b;
@@ -84,6 +85,8 @@ struct Ctx {
     const float4 *txw;           // [n_face][n_body][2] the same for each face's source image (or nullptr)
     const float4 *bvh;           // triangle BVH, see DevScene (nullptr: every triangle is tested)
     const int *bvh_tri;
+    const float4 *bvh_top;       // its first bvh_top_n nodes (the top levels) staged in shared memory
+    int bvh_top_n;
     const int4 *cand;            // candidate face sequences, see DevScene (n_cand = 0: every face and pair)
     const float4 *cimg;
     int n_cand;
@@ -246,21 +249,28 @@ __device__ __forceinline__ bool seg_box(v3t<T> A, v3t<T> D, const float4 &lo, co
 // endpoints first, in FP64 only where that is uncertain.
 template <typename T>
 __device__ __forceinline__ int tris_bvh(const Ctx &c, v3t<T> A, v3t<T> B, int sf1, int sf2, T band) {
-    const v3t<T> D = B - A;
     v3t<float> Af, Bf;
+    float box_m = 0.0f;
     if constexpr (sizeof(T) == 4) {
         Af = A; Bf = B;
+        box_m = band;
     } else {
         Af = mk3<float>(to_float(A.x), to_float(A.y), to_float(A.z));
         Bf = mk3<float>(to_float(B.x), to_float(B.y), to_float(B.z));
     }
+    const v3t<float> Df = Bf - Af;
     int stk[32];
     int sp = 0, uns = 0;
     stk[sp++] = 0;
     while (sp > 0) {
         const int nd = stk[--sp];
-        const float4 lo = c.bvh[2 * nd], hi = c.bvh[2 * nd + 1];
-        if (!seg_box<T>(A, D, lo, hi, band)) continue;
+        // the top levels from shared memory, the rest through L1/L2
+        const float4 *nb = (nd < c.bvh_top_n) ? c.bvh_top : c.bvh;
+        const float4 lo = nb[2 * nd], hi = nb[2 * nd + 1];
+        // box test in FP32 in both precisions: on the rounded endpoints it
+        // stays conservative (the boxes are padded by 1e-4 m plus 1e-6 of the
+        // coordinate, far beyond the rounding of the endpoints and the test)
+        if (!seg_box<float>(Af, Df, lo, hi, box_m)) continue;
         const int first = __float_as_int(lo.w), count = __float_as_int(hi.w);
         if (count == 0) {
             if (sp + 2 > 32) { uns = 1; continue; }    // (the host build is at most 32 deep)
@@ -612,8 +622,9 @@ __device__ __forceinline__ v3t<T> cand_image(const Ctx &c, int q, int m) {
         return mk3<T>(T((double)h.x + (double)l.x), T((double)h.y + (double)l.y), T((double)h.z + (double)l.z));
     }
 }
+// the geometric part: each reflection point on its face (no visibility)
 template <typename T>
-__device__ int cand_seq(const Ctx &c, int q, int4 sq, v3t<T> S, v3t<T> P, T band, v3t<T> Q[3]) {
+__device__ __forceinline__ int cand_seq_geom(const Ctx &c, int q, int4 sq, v3t<T> P, T band, v3t<T> Q[3]) {
     const int k = sq.w;
     const int fs[3] = {sq.x, sq.y, sq.z};
     int acc = D_YES;
@@ -630,6 +641,14 @@ __device__ int cand_seq(const Ctx &c, int q, int4 sq, v3t<T> S, v3t<T> P, T band
         if (!conj(acc, in_face(c, fs[m], Q[m], band))) return D_NO;
         X = Q[m];
     }
+    return acc;
+}
+template <typename T>
+__device__ int cand_seq(const Ctx &c, int q, int4 sq, v3t<T> S, v3t<T> P, T band, v3t<T> Q[3]) {
+    const int k = sq.w;
+    const int fs[3] = {sq.x, sq.y, sq.z};
+    int acc = cand_seq_geom<T>(c, q, sq, P, band, Q);
+    if (acc == D_NO) return D_NO;
     if (!conj(acc, vis_to_dec(blocked(c, S, Q[0], fs[0], -1, -1, band)))) return D_NO;
     if (k >= 2 && !conj(acc, vis_to_dec(blocked(c, Q[0], Q[1], fs[0], fs[1], -1, band)))) return D_NO;
     if (k >= 3 && !conj(acc, vis_to_dec(blocked(c, Q[1], Q[2], fs[1], fs[2], -1, band)))) return D_NO;
@@ -2490,8 +2509,11 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
     float4 *s_tri = s_body + (body_sm ? 2 * S.n_body : 0);   // n_tri * 3 (if staged)
     float4 *s_aux = s_tri + (tri_sm ? 3 * S.n_tri : 0);      // n_tri * 3 (if staged)
     float4 *s_txb = s_aux + (tri_sm ? 3 * S.n_tri : 0);      // n_body * 2 (if staged)
-    float *s_weid = (float *)(s_txb + (body_sm ? 2 * S.n_body : 0));
+    const int n_top = S.bvh ? min(S.bvh_nodes, BVH_TOP_NODES) : 0;
+    float4 *s_bvh = s_txb + (body_sm ? 2 * S.n_body : 0);    // n_top * 2: the BVH's top treelet
+    float *s_weid = (float *)(s_bvh + 2 * n_top);
     float *s_rec = s_weid + WEIDEMAN_N;                      // path records (FP32 fields of the body classes)
+    for (int i = threadIdx.x; i < 2 * n_top; i += blockDim.x) s_bvh[i] = S.bvh[i];
     for (int i = threadIdx.x; i < n_fock; i += blockDim.x) s_fock[i] = S.fock32[i];
     for (int i = threadIdx.x; i < n_res; i += blockDim.x) s_res[i] = S.res32[i];
     if (face_sm)
@@ -2535,8 +2557,9 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         c.enc = enc;
         c.txw = frames ? nullptr : S.txw;
         c.bvh = S.bvh; c.bvh_tri = S.bvh_tri;
-        c.cand = S.cand; c.cimg = S.cimg; c.n_cand = S.cand ? S.n_cand : 0;
-
+        c.bvh_top = s_bvh; c.bvh_top_n = n_top;
+        c.cand = S.cand; c.cimg = S.cimg;
+        c.n_cand = S.cand ? (S.n_cand_dev ? *S.n_cand_dev : S.n_cand) : 0;
     }
     __syncthreads();
     // the next class kernel (launched as a programmatic dependent) may start
@@ -2779,7 +2802,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
 // (body classes) or the wide partial sums of wide_chunks chunks (planar)
 static size_t smem_bytes(const DevScene &S, bool bodies, bool records, int blk, int rcap, int wide_chunks,
                          int occ_sets) {
-    size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + (S.n_face <= SMEM_FACE_MAX ? S.n_face : 0);
+    size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + (S.n_face <= SMEM_FACE_MAX ? S.n_face : 0) +
+               (S.bvh ? 2 * (size_t)min(S.bvh_nodes, BVH_TOP_NODES) : 0);
     if (S.n_body <= SMEM_BODY_MAX) n += 4 * S.n_body;
     if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;
     const int occ_w = (occ_sets > 0 && S.n_body > 0 && S.n_body <= OCC_MAX_BODIES) ? (S.n_body + 31) >> 5 : 0;
@@ -3330,8 +3354,9 @@ __global__ void __launch_bounds__(128) k_adjoint(DevScene S, const float *__rest
     c.fock = nullptr; c.res = nullptr; c.weid = nullptr; c.weid_L = S.weid_L;
     c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
     c.img = S.img; c.txb = S.txb; c.occ_src = nullptr; c.occ_w = 0; c.face_mat = S.face_mat;
-    c.txw = S.txw; c.bvh = S.bvh; c.bvh_tri = S.bvh_tri;
-    c.cand = S.cand; c.cimg = S.cimg; c.n_cand = S.cand ? S.n_cand : 0;
+    c.txw = S.txw; c.bvh = S.bvh; c.bvh_tri = S.bvh_tri; c.bvh_top = nullptr; c.bvh_top_n = 0;
+    c.cand = S.cand; c.cimg = S.cimg;
+    c.n_cand = S.cand ? (S.n_cand_dev ? *S.n_cand_dev : S.n_cand) : 0;
     const int lane = threadIdx.x & 31;
     const int nch = (S.n_f + NFC - 1) / NFC;
     const v3t<D8> Sd = mk3<D8>(dvar(c.S.x, DS_SX), dvar(c.S.y, DS_SY), dvar(c.S.z, DS_SZ));

@@ -80,9 +80,11 @@ struct DevScene {
                                // (box min, first), (box max, count); count > 0 leaf over bvh_tri[first ..
                                // first + count), else children first, first + 1 (ints as float bits)
     const int *bvh_tri;        // triangle ids in leaf order
+    int bvh_nodes;             // nodes of the BVH (numbered breadth first: the top levels first)
     const int4 *cand;          // [n_cand] candidate face sequences (f0, f1, f2, order), -1 padded, or nullptr
     const float4 *cimg;        // [n_cand][3][2]: the source's image after 1, 2, 3 reflections (hi, lo)
-    int n_cand;
+    int n_cand;                // the list's length, or (n_cand_dev set) an upper bound of it
+    const int *n_cand_dev;     // device-built list: its length in device memory (else nullptr)
     const float4 *txw;         // [n_face][n_body][2]: as txb, for the source's mirror image in each face
                                // (wall -> creeping paths); nullptr in batches
     const double *freq;        // [n_f] Hz (host copy, read by the launcher)
@@ -119,7 +121,27 @@ struct FrameDev {
 void bvh_build(const float *tri, int n_tri, std::vector<float4> &nodes, std::vector<int> &order);
 int ray_launch(const float *tri, const int *tri_face, int n_tri, int n_face, const std::vector<float4> &nodes,
                const std::vector<int> &order, const double tx[3], int n_rays, int max_order, std::vector<int> &seq);
+// The launch's inputs, shared by the host launch and the device one
+// (candidates.cu), so that both trace bit-identical rays: per face the unit
+// normal of its first triangle, (v1 - v0) x (v2 - v0) / |.|, [n_face][3];
+// the n_rays directions of the spherical Fibonacci lattice, [n_rays][3].
+void ray_face_normals(const float *tri, const int *tri_face, int n_tri, int n_face, std::vector<double> &fn);
+void ray_directions(int n_rays, std::vector<double> &dir);
 constexpr int BVH_MIN_TRI = 64;        // scenes with more triangles traverse the BVH on the device
+
+// Device ray launch (candidates.cu): at most RT_DEV_CAND_SLOTS ray prefixes
+// (n_rays x max_order); the finished list is sorted and made unique in one
+// block's shared memory.
+struct DevCandBufs {
+    double *dir;               // [n_rays][3]
+    double *fn;                // [n_face][3]
+    unsigned long long *keys;  // [RT_DEV_CAND_SLOTS]
+    int4 *cand;                // [RT_DEV_CAND_SLOTS]
+    float4 *cimg;              // [RT_DEV_CAND_SLOTS][3][2]
+    int *n_cand;               // [1]
+};
+int launch_ray_candidates(const float4 *tri, const float4 *bvh, const int *bvh_tri, const dq4 *face64,
+                          const double tx[3], int n_rays, int max_order, const DevCandBufs &B, cudaStream_t st);
 
 constexpr int CTR_QUEUES = 256;
 constexpr int CTR_N = 1 + CTR_QUEUES;

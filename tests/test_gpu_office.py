@@ -41,6 +41,47 @@ def test_candidates_match_oracle(creep, oracle_mod):
     assert len(got) > 100
 
 
+def test_device_candidates_match_oracle(creep, oracle_mod):
+    """The ray launch on the device (rt_candidates_device) gives the
+    oracle's list, sequence for sequence, in a BVH scene and in the room
+    (12 triangles), for several ray counts and orders."""
+    sc = _small_office()
+    S = creep.Scene.from_scene(sc)
+    for n_rays, order in ((4096, 3), (1000, 2), (5461, 3), (333, 1)):
+        S.candidates_device(n_rays, order)
+        got = S.get_candidates()
+        ref = oracle_mod.candidates(sc, n_rays, order)
+        assert np.array_equal(got, ref), (n_rays, order, len(got), len(ref))
+    room = scenes.room(n_cyl=4, nx=8, ny=8)
+    R = creep.Scene.from_scene(room)
+    R.candidates_device(2000, 3)
+    assert np.array_equal(R.get_candidates(), oracle_mod.candidates(room, 2000, 3))
+    with pytest.raises(creep.CreepError):
+        S.candidates_device(8000, 3)                 # beyond RT_DEV_CAND_SLOTS prefixes
+
+
+def test_device_candidates_evaluate_like_a_host_list(creep, oracle_mod):
+    """Fields and path lists with the device-built list equal those with the
+    same list set from the host (bit for bit); rt_set_tx drops the device
+    list and the host list serves again."""
+    sc = _small_office()
+    S = creep.Scene.from_scene(sc)
+    rx = torch.tensor(sc.rx_soa(), device="cuda")
+    opts = creep.options(max_order=3)
+    S.set_candidates(oracle_mod.candidates(sc, 4096, 3))
+    E1 = S.evaluate(rx, opts=opts).clone()
+    c1, n1, _ = S.paths(rx, opts=opts)
+    S.candidates_device(4096, 3)
+    E2 = S.evaluate(rx, opts=opts).clone()
+    c2, n2, _ = S.paths(rx, opts=opts)
+    torch.cuda.synchronize()
+    assert torch.equal(E1, E2) and torch.equal(n1, n2) and torch.equal(c1, c2)
+    S.set_tx(sc.tx, sc.pol)
+    E3 = S.evaluate(rx, opts=opts)
+    torch.cuda.synchronize()
+    assert torch.equal(E1, E3)
+
+
 @pytest.mark.parametrize("precision", ["fp32", "fp64"])
 def test_office_parity(creep, oracle_mod, precision):
     sc = _small_office()
