@@ -127,6 +127,7 @@ struct rt_scene {
     float4 *d_txb = nullptr;            // source-side body frames, see DevScene::txb
     float4 *d_txw = nullptr;            // the same for each face's source image, see DevScene::txw
     float4 *d_face_mat = nullptr;       // face materials, see DevScene::face_mat
+    float4 *d_face_box = nullptr;       // per face its culling box, see DevScene::face_box
     bool any_dielectric = false;
     // large-scene mode: the triangle BVH (host copy for the ray launch; on the
     // device above BVH_MIN_TRI triangles) and the candidate face sequences
@@ -192,7 +193,7 @@ static void free_scene(rt_scene *s) {
     cudaFree(s->d_face64); cudaFree(s->d_face_rng); cudaFree(s->d_face_tris); cudaFree(s->d_freq); cudaFree(s->d_fqc);
     cudaFree(s->d_esc); cudaFree(s->io_rx); cudaFree(s->io_e); cudaFree(s->io_fl); cudaFree(s->d_img); cudaFree(s->d_txb);
     cudaFree(s->d_txw); cudaFree(s->d_bvh); cudaFree(s->d_bvh_tri); cudaFree(s->d_cand); cudaFree(s->d_cimg);
-    cudaFree(s->d_face_mat);
+    cudaFree(s->d_face_mat); cudaFree(s->d_face_box);
     cudaFree(s->dcb.dir); cudaFree(s->dcb.fn); cudaFree(s->dcb.keys); cudaFree(s->dcb.cand); cudaFree(s->dcb.cimg);
     cudaFree(s->dcb.n_cand); cudaFree(s->d_lbvh); cudaFree(s->d_lbvh_tri);
 }
@@ -404,6 +405,42 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
     std::vector<float4> hf32(nf > 0 ? nf : 1);
     std::vector<dq4> hf64(nf > 0 ? nf : 1);
     std::vector<int2> hr(nf > 0 ? nf : 1);
+    // per face the box of its triangles, grown by a margin that bounds the
+    // FP32 face-membership decision: a point this far outside the box is
+    // outside every triangle of the face by more than the decision band in
+    // edge distance (the band over sin of half the smallest triangle angle),
+    // plus the rounding of the culling test (1 mm)
+    std::vector<float4> hbox(2 * (size_t)(nf > 0 ? nf : 1));
+    {
+        std::vector<double> bmin(3 * (size_t)nf, INFINITY), bmax(3 * (size_t)nf, -INFINITY), smin(nf, 1.0);
+        for (int t = 0; t < n_tri; ++t) {
+            const int f = s->tri_face[t];
+            const float *v = &s->tri[9 * (size_t)t];
+            for (int c = 0; c < 3; ++c)
+                for (int k = 0; k < 3; ++k) {
+                    bmin[3 * (size_t)f + k] = fmin(bmin[3 * (size_t)f + k], (double)v[3 * c + k]);
+                    bmax[3 * (size_t)f + k] = fmax(bmax[3 * (size_t)f + k], (double)v[3 * c + k]);
+                }
+            for (int c = 0; c < 3; ++c) {        // the triangle's angle at vertex c
+                const float *a = v + 3 * c, *b = v + 3 * ((c + 1) % 3), *e = v + 3 * ((c + 2) % 3);
+                double u[3], w[3];
+                for (int k = 0; k < 3; ++k) { u[k] = (double)b[k] - a[k]; w[k] = (double)e[k] - a[k]; }
+                const double uu = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+                const double ww = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+                const double cs = (u[0] * w[0] + u[1] * w[1] + u[2] * w[2]) / (uu * ww);
+                const double half = 0.5 * acos(fmax(-1.0, fmin(1.0, cs)));
+                smin[f] = fmin(smin[f], sin(half));
+            }
+        }
+        const double band = band_of(scale);
+        for (int f = 0; f < nf; ++f) {
+            const double m = 4.0 * band / fmax(smin[f], 1e-6) + 1e-3;
+            hbox[2 * f] = make_float4((float)(bmin[3 * (size_t)f] - m), (float)(bmin[3 * (size_t)f + 1] - m),
+                                      (float)(bmin[3 * (size_t)f + 2] - m), 0.f);
+            hbox[2 * f + 1] = make_float4((float)(bmax[3 * (size_t)f] + m), (float)(bmax[3 * (size_t)f + 1] + m),
+                                          (float)(bmax[3 * (size_t)f + 2] + m), 0.f);
+        }
+    }
     for (int f = 0; f < nf; ++f) {
         const FaceHost &F = s->faces[f];
         hf32[f] = make_float4((float)F.n[0], (float)F.n[1], (float)F.n[2], (float)F.d);
@@ -426,6 +463,7 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
     CKS(cudaMalloc(&s->d_face32, sizeof(float4) * nfc));
     CKS(cudaMalloc(&s->d_face64, sizeof(dq4) * nfc));
     CKS(cudaMalloc(&s->d_face_rng, sizeof(int2) * nfc));
+    CKS(cudaMalloc(&s->d_face_box, sizeof(float4) * 2 * nfc));
     CKS(cudaMalloc(&s->d_face_tris, sizeof(int) * ntr));
     CKS(cudaMalloc(&s->d_body, sizeof(float4) * 2 * nbd));
     CKS(cudaMalloc(&s->d_freq, sizeof(double) * RT_MAX_FREQS));
@@ -453,6 +491,7 @@ int rt_scene_create(const float *tri_xyz, const int *tri_face, int n_tri, const 
         CKS(cudaMemcpy(s->d_face32, hf32.data(), sizeof(float4) * nf, cudaMemcpyHostToDevice));
         CKS(cudaMemcpy(s->d_face64, hf64.data(), sizeof(dq4) * nf, cudaMemcpyHostToDevice));
         CKS(cudaMemcpy(s->d_face_rng, hr.data(), sizeof(int2) * nf, cudaMemcpyHostToDevice));
+        CKS(cudaMemcpy(s->d_face_box, hbox.data(), sizeof(float4) * 2 * nf, cudaMemcpyHostToDevice));
     }
     if (n_body > 0) CKS(cudaMemcpy(s->d_body, hb.data(), sizeof(float4) * 2 * n_body, cudaMemcpyHostToDevice));
     CKS(cudaMemset(s->d_esc, 0, sizeof(unsigned long long) * CTR_N));
@@ -781,6 +820,7 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, 
         D.n_cand_dev = nullptr;
     }
     D.face_mat = s->any_dielectric ? s->d_face_mat : nullptr;
+    D.face_box = s->d_face_box;
     memcpy(D.tx, s->tx, sizeof(D.tx));
     memcpy(D.pol, s->pol, sizeof(D.pol));
     D.band_len = s->band_len;

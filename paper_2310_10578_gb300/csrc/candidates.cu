@@ -11,8 +11,8 @@
 // index) up to max_order times; every prefix of its face sequence is a
 // candidate; the distinct sequences sorted by (order, faces).
 //
-// Here: k_ray_launch, one thread per ray, walks the scene's triangle BVH in
-// FP64 (the node boxes are padded outwards, so no slab test drops a hit);
+// Here: k_ray_launch, one thread per ray, walks the scene's triangle BVH
+// (FP32 box tests, conservative on the padded boxes; FP64 triangle tests);
 // this file is compiled without FMA contraction, so every FP64 operation
 // rounds as in the host code (-ffp-contract=off) and both launches trace
 // bit-identical rays from the same host-made directions and face normals.
@@ -58,21 +58,26 @@ __device__ double ray_tri_d(D3 o, D3 d, D3 v0, D3 v1, D3 v2) {
     return dotd(e2, q) * inv;
 }
 
-// the ray's parameter interval [0, tmax] meets the box?
-__device__ bool ray_box_d(D3 o, D3 d, float4 lo, float4 hi, double tmax) {
-    double t0 = 0.0, t1 = tmax;
-    const double os[3] = {o.x, o.y, o.z}, ds[3] = {d.x, d.y, d.z};
-    const double bl[3] = {lo.x, lo.y, lo.z}, bh[3] = {hi.x, hi.y, hi.z};
+// the ray's parameter interval [0, tmax] meets the box?  In FP32 on the
+// rounded ray: conservative, since the node
+// boxes are padded outwards by 1e-4 m + 1e-6 of the coordinate, far beyond
+// the rounding of the ray and of this test over the scene's extent; tmax is
+// rounded up.  It only prunes the walk: every box holding a triangle whose
+// FP64 hit parameter is <= tmax is kept, so the nearest hit is the FP64 one.
+__device__ __forceinline__ bool ray_box_f(const float o[3], const float d[3], float4 lo, float4 hi, float tmax) {
+    float t0 = 0.0f, t1 = tmax;
+    const float bl[3] = {lo.x, lo.y, lo.z}, bh[3] = {hi.x, hi.y, hi.z};
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-        if (ds[k] == 0.0) {
-            if (os[k] < bl[k] || os[k] > bh[k]) return false;
+        if (d[k] == 0.0f) {
+            if (o[k] < bl[k] || o[k] > bh[k]) return false;
             continue;
         }
-        double a = (bl[k] - os[k]) / ds[k], b = (bh[k] - os[k]) / ds[k];
-        if (a > b) { double w = a; a = b; b = w; }
-        t0 = fmax(t0, a);
-        t1 = fmin(t1, b);
+        const float inv = 1.0f / d[k];
+        float a = (bl[k] - o[k]) * inv, b = (bh[k] - o[k]) * inv;
+        if (a > b) { const float w = a; a = b; b = w; }
+        t0 = fmaxf(t0, a);
+        t1 = fminf(t1, b);
         if (t0 > t1) return false;
     }
     return true;
@@ -103,11 +108,12 @@ __global__ void __launch_bounds__(32) k_ray_launch(const float4 *__restrict__ tr
     for (int k = 0; k < max_order; ++k) {
         double best = INFINITY;
         int bt = -1, sp = 0;
+        const float of[3] = {(float)o.x, (float)o.y, (float)o.z}, df[3] = {(float)d.x, (float)d.y, (float)d.z};
         stack[sp++] = 0;
         while (sp > 0) {
             const int nd = stack[--sp];
             const float4 lo = bvh[2 * nd], hi = bvh[2 * nd + 1];
-            if (!ray_box_d(o, d, lo, hi, best)) continue;
+            if (!ray_box_f(of, df, lo, hi, __double2float_ru(best))) continue;
             const int first = __float_as_int(lo.w), count = __float_as_int(hi.w);
             if (count == 0) {
                 if (sp + 2 > 64) { atomicExch(overflow, 1); continue; }    // (the build is far shallower)

@@ -70,6 +70,7 @@ struct Ctx {
     const dq4 *face64;
     const int2 *face_rng;
     const int *face_tris;
+    const float4 *face_box;      // see DevScene
     int n_tri, n_face, n_body;
     float band;
     v3t<float> S, pol;
@@ -2053,6 +2054,84 @@ __device__ __forceinline__ void apply_records(const Ctx &c, AccS<float> &acc, co
 // share (1 + i n_face + j) mod nparts, the paths of body b to share
 // b mod nparts -- summed into acc; the receiver's flags, the count of FP64
 // re-decisions and (PATHS) the path codes from slot npath on.
+// ---- candidate-list culling per tile.  A candidate (face sequence) can give
+// a path to receiver P only if P and the source's last image lie strictly on
+// opposite sides of the last face's plane and the last reflection point --
+// where the segment image -> P crosses the plane -- lies on that face.  For a
+// box holding the tile's receivers, both fail for every receiver at once if
+// all eight corners lie on the image's side by more than twice the decision
+// band, or, with all corners on the far side, if the box of the corners'
+// crossing points misses the face's box (DevScene::face_box): the crossing
+// points of the whole box lie in the hull of the corners' (the central
+// projection keeps convexity on that half-space), and the face box is grown
+// so that a point outside it is outside every triangle of the face by more
+// than the band.  Such candidates are decided "no" for every receiver of the
+// tile by the per-receiver test too (FP32 with its band, or FP64), so
+// leaving them out changes no decision and no field.
+constexpr int SEQ_MASK_WORDS = 512;      // culling up to 16384 candidates (a larger list is not culled)
+__device__ __forceinline__ bool seq_may_hit(const Ctx &c, int q, int4 sq, const float lo[3], const float hi[3]) {
+    const int k = sq.w;
+    const int f = (k == 1) ? sq.x : ((k == 2) ? sq.y : sq.z);
+    const float4 I = c.cimg[6 * q + 2 * (k - 1)];
+    const float4 pl = c.face32[f];
+    const float di = pl.x * I.x + pl.y * I.y + pl.z * I.z - pl.w;
+    const float m = 2.0f * c.band;
+    if (!(fabsf(di) > m)) return true;
+    const float sg = di > 0.0f ? 1.0f : -1.0f;
+    bool same = true, opp = true;
+    float qlo[3] = {INFINITY, INFINITY, INFINITY}, qhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+        const float px = (cc & 1) ? hi[0] : lo[0], py = (cc & 2) ? hi[1] : lo[1], pz = (cc & 4) ? hi[2] : lo[2];
+        const float dp = pl.x * px + pl.y * py + pl.z * pz - pl.w;
+        same = same && (dp * sg > m);
+        opp = opp && (-dp * sg > m);
+        const float t = di / (di - dp);
+        const float x = I.x + (px - I.x) * t, y = I.y + (py - I.y) * t, z = I.z + (pz - I.z) * t;
+        qlo[0] = fminf(qlo[0], x); qhi[0] = fmaxf(qhi[0], x);
+        qlo[1] = fminf(qlo[1], y); qhi[1] = fmaxf(qhi[1], y);
+        qlo[2] = fminf(qlo[2], z); qhi[2] = fmaxf(qhi[2], z);
+    }
+    if (same) return false;
+    if (!opp) return true;
+    const float4 b0 = c.face_box[2 * f], b1 = c.face_box[2 * f + 1];
+    return qlo[0] <= b1.x && qhi[0] >= b0.x && qlo[1] <= b1.y && qhi[1] >= b0.y && qlo[2] <= b1.z && qhi[2] >= b0.z;
+}
+// All 32 lanes of a warp: the box of the tile's receivers (lanes with ok),
+// then bit lane of word w set iff candidate 32 w + lane is in share part of
+// nparts, within max_order, and not culled.  Returns false (no mask) when
+// the list is too long to be culled.
+__device__ __noinline__ bool seq_tile_mask(const Ctx &c, const float *rx, int n_rx, int r, bool ok, int part,
+                                           int nparts, int max_order, uint32_t *mask) {
+    if (c.n_cand > 32 * SEQ_MASK_WORDS) return false;
+    const int lane = threadIdx.x & 31;
+    float lo[3], hi[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float v = ok ? rx[k * n_rx + r] : 0.0f;
+        lo[k] = ok ? v : INFINITY;
+        hi[k] = ok ? v : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], o));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], o));
+        }
+    }
+    const int nw = (c.n_cand + 31) >> 5;
+    for (int w = 0; w < nw; ++w) {
+        const int q = 32 * w + lane;
+        bool keep = false;
+        if (q < c.n_cand && (1 + q) % nparts == part && lo[0] <= hi[0]) {
+            const int4 sq = c.cand[q];
+            if (sq.w <= max_order) keep = seq_may_hit(c, q, sq, lo, hi);
+        }
+        const unsigned word = __ballot_sync(0xffffffffu, keep);
+        if (lane == 0) mask[w] = word;
+    }
+    __syncwarp();
+    return true;
+}
+
 // fields with the path list: the warps sharing a receiver take slots by
 // atomics (the list is in no particular order); returns the overflow flag
 __device__ __noinline__ uint32_t list_path(uint64_t *codes, int32_t *counts, int cap, int r, uint64_t code) {
@@ -2072,7 +2151,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                                               int b_begin, int b_end, bool first_chunk, bool may_flush, int rcap,
                                               const uint32_t *occ_rx, int part, int nparts,
                                               AccS<T> acc, float *rec, uint32_t &fl, unsigned &nesc, int &npath,
-                                              int &nrec_out) {
+                                              int &nrec_out, const uint32_t *qmask = nullptr) {
     constexpr bool BODIES = (CLS & CLS_BODIES) != 0;
     const bool fp32 = sizeof(T) == 4;
     const T band = fp32 ? T(c.band) : T(0);
@@ -2146,9 +2225,22 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
             // scenes), else every face and ordered face pair
             if constexpr (CLS == CLS_SEQ) {
               if ((enable & RT_EN_PLANAR) && max_order >= 1) {
+                // the tile's mask (seq_tile_mask) lists this share's candidates
+                // that survive culling; without one, every candidate of the share
+                int w = 0, q = -1;
+                uint32_t word = qmask ? qmask[0] : 0u;
+                const int nw = (c.n_cand + 31) >> 5;
 #pragma unroll 1
-                for (int q = 0; q < c.n_cand; ++q) {
-                    if ((1 + q) % nparts != part) continue;
+                for (;;) {
+                    if (qmask) {
+                        while (word == 0u && ++w < nw) word = qmask[w];
+                        if (word == 0u) break;
+                        q = 32 * w + __ffs(word) - 1;
+                        word &= word - 1u;
+                    } else {
+                        if (++q >= c.n_cand) break;
+                        if ((1 + q) % nparts != part) continue;
+                    }
                     const int4 sq = c.cand[q];
                     if (sq.w > max_order) continue;
                     v3t<T> Q[3];
@@ -2542,6 +2634,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         c.face64 = S.face64;
         c.face_rng = S.face_rng;
         c.face_tris = S.face_tris;
+        c.face_box = S.face_box;
         c.body = body_sm ? s_body : F1.body;
         c.n_tri = S.n_tri; c.n_face = S.n_face; c.n_body = frames ? 0 : F1.n_body;
         c.band = S.band_len;
@@ -2595,6 +2688,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         // path lists: each warp takes tiles of 32 consecutive receivers from
         // the launch's queue and lists every candidate itself (codes in the
         // canonical order)
+        __shared__ uint32_t s_qmask_p[CLS == CLS_SEQ ? NW : 1][CLS == CLS_SEQ ? SEQ_MASK_WORDS : 1];
         for (;;) {
             unsigned long long t = 0;
             if (lane == 0) t = atomicAdd(queue, 1ull);
@@ -2604,6 +2698,11 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
             if (occ_on) {
                 tile_masks(c, rx, n_rx, r, r < n_rx, s_occ_mine, 0, 1);
                 __syncwarp();
+            }
+            bool qm_on = false;
+            if constexpr (CLS == CLS_SEQ) {
+                qm_on = seq_tile_mask(c, rx, n_rx, r < n_rx ? r : n_rx - 1, r < n_rx, 0, 1, S.max_order,
+                                      &s_qmask_p[warp][0]);
             }
             if (r < n_rx) {
                 AccS<T> acc{nullptr};                // no fields in this mode
@@ -2615,7 +2714,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                                                    F1.hl,
                                              0, CLS == CLS_WCREEP ? c.n_face * c.n_body : c.n_body, true, false, 0,
                                              occ_on ? s_occ_mine : nullptr, 0, 1, acc,
-                                             nullptr, fl, nesc, npath, nrec);
+                                             nullptr, fl, nesc, npath, nrec, qm_on ? &s_qmask_p[warp][0] : nullptr);
                 counts[r] = npath;
                 if (fl_base) fl_base[r] = accumulate ? (fl_base[r] | fl) : fl;
                 if (nesc) atomicAdd(esc_counter, (unsigned long long)nesc);
@@ -2653,6 +2752,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         const int prow = WIDE ? nch * NFC * 6 : NFC * 6;
         T *s_part = WIDE ? reinterpret_cast<T *>(s_rec) : &s_part_st[0][0][0];
         __shared__ uint32_t s_fl[NW][32];
+        __shared__ uint32_t s_qmask[CLS == CLS_SEQ ? NW : 1][CLS == CLS_SEQ ? SEQ_MASK_WORDS : 1];
         __shared__ unsigned long long s_unit;
         __shared__ int s_fi, s_new;
         __shared__ FrameDev s_fr;
@@ -2726,6 +2826,12 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                 tile_masks(c, rx, n_rx, r, rok, s_occ_rx + grp * S.n_body * occ_w, part, NWT);
                 __syncwarp();
             }
+            // candidate-list class: this warp's surviving candidates for the tile
+            bool qm_on = false;
+            if constexpr (CLS == CLS_SEQ) {
+                if (n_rx > 0)
+                    qm_on = seq_tile_mask(c, rx, n_rx, rok ? r : n_rx - 1, rok, part, NWT, S.max_order, &s_qmask[warp][0]);
+            }
             AccS<T> acc{s_part + warp * prow * 32 + lane};     // the warp's partial sums, summed in place
             float *rec = s_rec + warp * (rcap * REC_N * 32) + lane;
 #pragma unroll 1
@@ -2738,7 +2844,8 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                                                        codes, counts, cap,
                                                  Fr.hl, b0, min(b0 + bc, n_b), b0 == 0, nch == 1, rcap,
                                                  occ_on ? s_occ_rx + grp * S.n_body * occ_w : nullptr, part,
-                                                 NWT, acc, rec, fl, nesc, npath, nrec);
+                                                 NWT, acc, rec, fl, nesc, npath, nrec,
+                                                 qm_on ? &s_qmask[warp][0] : nullptr);
                 s_fl[warp][lane] = fl;
                 if (nesc && ch0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
 #pragma unroll 1

@@ -61,6 +61,8 @@ struct DevScene {
     const float4 *face32;      // [n_face]: unit normal, offset (FP32)
     const dq4 *face64;     // [n_face]: unit normal, offset (FP64)
     const int2 *face_rng;      // [n_face]: first, count in face_tris
+    const float4 *face_box;    // [n_face][2]: box of the face's triangles (min, max), grown by the margin
+                               // beyond which the FP32 face-membership test is a certain no
     const int *face_tris;      // [n_tri]
     const float4 *body;        // [n_body][2]: (cx, cy, cz, a), (h, type, 0, 0)
     const float4 *fock32;      // [FOCK_N][2]: (G.re, G.im, h G'.re, h G'.im) soft, hard
