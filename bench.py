@@ -391,66 +391,76 @@ def adjoint_room200(args, creep, dev, flush):
     receivers; loss = sum over the target zone (x in [6, 8] m, y in [4, 6] m)
     of the received power in dB.  One gradient step = the fields with their
     path list (rt_evaluate_with_paths), the loss seed, and the adjoint
-    (rt_backward).  The fields alone (rt_evaluate) are timed beside it."""
+    (rt_backward), timed with FP64 dual numbers (the line's value) and with
+    FP32 ones (beside it); the fields alone (rt_evaluate) beside both."""
     import torch
     from paper_2310_10578_gb300 import scenes
     sc = scenes.room(n_cyl=200, nx=64, ny=64, freqs=(28e9,))
     S = creep.Scene.from_scene(sc)
     rx = torch.tensor(sc.rx_soa(), device=dev)
     opts = creep.options(max_order=2)
+    bopts = {"fp64": creep.options(max_order=2, precision=creep.RT_PREC_FP64),
+             "fp32": creep.options(max_order=2, precision=creep.RT_PREC_FP32)}
     n = sc.n_rx
     zone = zone_of(sc)
     zmask = torch.zeros(n, dtype=torch.bool, device=dev)
     zmask[torch.tensor(zone, device=dev)] = True
     E = torch.empty((1, 3, n, 2), dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream()
-
-    def step():
-        _, codes, counts, _ = S.evaluate_with_paths(rx, cap=64, out=E, opts=opts)
-        return S.backward(rx, codes, counts, _seed_zone_db(E, zmask), opts=opts)
-
-    for _ in range(3):
-        step()
-    torch.cuda.synchronize()
-    marks = []
-    for i in range(args.batched_steps):
-        flush.fill_(float(i))
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ev[0].record(st)
-        S.evaluate(rx, out=E, opts=opts)
-        ev[1].record(st)
-        _, codes, counts, _ = S.evaluate_with_paths(rx, cap=64, out=E, opts=opts)
-        ev[2].record(st)
-        gb, gt, gf = S.backward(rx, codes, counts, _seed_zone_db(E, zmask), opts=opts)
-        ev[3].record(st)
-        marks.append(ev)
-    torch.cuda.synchronize()
-    t = np.array([[m[k].elapsed_time(m[k + 1]) for k in range(3)] for m in marks])
-    fwd, paths, bwd = (float(np.mean(t[:, k])) for k in range(3))
-    n_paths = int(counts.sum())
+    out = {}
+    for name, bo in bopts.items():
+        for _ in range(3):
+            _, codes, counts, _ = S.evaluate_with_paths(rx, cap=64, out=E, opts=opts)
+            S.backward(rx, codes, counts, _seed_zone_db(E, zmask), opts=bo)
+        torch.cuda.synchronize()
+        marks = []
+        for i in range(args.batched_steps):
+            flush.fill_(float(i))
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(st)
+            S.evaluate(rx, out=E, opts=opts)
+            ev[1].record(st)
+            _, codes, counts, _ = S.evaluate_with_paths(rx, cap=64, out=E, opts=opts)
+            ev[2].record(st)
+            gb, gt, gf = S.backward(rx, codes, counts, _seed_zone_db(E, zmask), opts=bo)
+            ev[3].record(st)
+            marks.append(ev)
+        torch.cuda.synchronize()
+        t = np.array([[m[k].elapsed_time(m[k + 1]) for k in range(3)] for m in marks])
+        fwd, paths, bwd = (float(np.mean(t[:, k])) for k in range(3))
+        out[name] = dict(fwd=fwd, paths=paths, bwd=bwd, gb=gb, gt=gt, n_paths=int(counts.sum()))
+    o = out["fp64"]
     res = {"workload": "room 10x8x3 m, 12 PEC triangles + 200 PEC cylinders, 64x64 rx at z=1.2 m, 28 GHz, refl<=2",
            "loss": "sum over the target zone x in [6, 8] m, y in [4, 6] m (%d receivers) of received power in dB "
                    "(seed dLoss/dE = 20/ln10 E/|E|^2 on the zone)" % len(zone),
-           "ms_fields_only": fwd, "ms_fields_with_path_list": paths, "ms_backward_incl_seed": bwd,
-           "ms_step": paths + bwd,
-           "value": n / ((paths + bwd) / 1e3), "unit": "receiver gradients/s (fields with path list + adjoint)",
-           "paths": n_paths, "steps": args.batched_steps,
+           "ms_fields_only": o["fwd"], "ms_fields_with_path_list": o["paths"], "ms_backward_incl_seed": o["bwd"],
+           "ms_step": o["paths"] + o["bwd"],
+           "value": n / ((o["paths"] + o["bwd"]) / 1e3), "unit": "receiver gradients/s (fields with path list + adjoint)",
+           "duals": "FP64 (RT_PREC_FP64)",
+           "paths": o["n_paths"], "steps": args.batched_steps,
            "gradients": "d/d(200 x (cx, cy, cz, a)), d/d(Tx), d/d(f)",
+           "fp32_duals": {"ms_backward_incl_seed": out["fp32"]["bwd"],
+                          "ms_step": out["fp32"]["paths"] + out["fp32"]["bwd"],
+                          "value": n / ((out["fp32"]["paths"] + out["fp32"]["bwd"]) / 1e3),
+                          "note": "RT_PREC_FP32: FP32 dual numbers on direct, planar and creeping paths, FP64 on "
+                                  "reflections off bodies"},
            "l2": "flushed between timed steps (256 MiB write)"}
     if not args.no_cpu_baseline:
         try:
-            res.update(adjoint_oracle_sample(creep, S, sc, dev, opts, zone, gb, gt))
+            acc = adjoint_oracle_sample(creep, S, sc, dev, opts, zone, {k: (v["gb"], v["gt"]) for k, v in out.items()})
+            res.update(acc)
         except Exception as e:                      # the measurement above stands without it
             res["cpu_baseline"] = {"error": "%s: %s" % (type(e).__name__, e)}
     return res
 
 
-def adjoint_oracle_sample(creep, S, sc, dev, opts, zone, gb, gt):
+def adjoint_oracle_sample(creep, S, sc, dev, opts, zone, grads):
     """The oracle beside the adjoint: the zone loss's gradient with respect
     to every body's centre and radius and the transmitter, by rt_backward
-    (the timed step's result, gb and gt) and by the oracle's central
-    differences of its per-path fields with the same path lists (visibility
-    held fixed); the worst relative difference and the oracle's rate."""
+    (the timed steps' results, grads = {duals: (g_body, g_tx)}) and by the
+    oracle's central differences of its per-path fields with the same path
+    lists (visibility held fixed); the worst relative difference of each
+    and the oracle's rate."""
     import torch
     sys.path.insert(0, os.path.join(ROOT, "tests"))
     import adjoint_ref
@@ -472,23 +482,23 @@ def adjoint_oracle_sample(creep, S, sc, dev, opts, zone, gb, gt):
     t0 = time.perf_counter()
     ref = adjoint_ref.vjp(sc, lists, g[..., 0] + 1j * g[..., 1], bodies=bodies, freqs=False, cap=64)
     t_cpu = time.perf_counter() - t0
-    gb, gt = gb.cpu().numpy(), gt.cpu().numpy()
 
     def rel(got, want, absum):
         return abs(got - want) / max(abs(want), 1e-3 * absum, 1e-300)
 
-    err_tx = max(rel(gt[i], ref["tx"][i], ref["tx_abs"][i]) for i in range(3))
-    err_b = max([rel(gb[b, j], ref["body"][b][j], ref["body_abs"][b][j]) for b in bodies for j in range(4)] or [0.0])
-    # bodies without a path to the zone must get exactly zero
+    acc = {"bodies_checked": len(bodies), "zone_receivers": len(zone),
+           "paths_skipped_by_reference": int(ref["skipped"]),
+           "tolerance": "1e-3 relative (against max(|ref|, 1e-3 sum|contributions|))"}
     idle = [b for b in range(sc.bodies.shape[0]) if b not in set(bodies)]
-    return {"accuracy_vs_fp64_oracle": {"tx_gradient_rel_err_max": float(err_tx),
-                                        "body_gradient_rel_err_max": float(err_b),
-                                        "bodies_checked": len(bodies), "bodies_without_zone_paths": len(idle),
-                                        "bodies_without_zone_paths_nonzero_gradient":
-                                            int(np.count_nonzero(np.any(gb[idle] != 0.0, axis=1))) if idle else 0,
-                                        "zone_receivers": len(zone),
-                                        "paths_skipped_by_reference": int(ref["skipped"]),
-                                        "tolerance": "1e-3 relative (against max(|ref|, 1e-3 sum|contributions|))"},
+    for name, (gb, gt) in grads.items():
+        gb, gt = gb.cpu().numpy(), gt.cpu().numpy()
+        acc[name] = {"tx_gradient_rel_err_max": float(max(rel(gt[i], ref["tx"][i], ref["tx_abs"][i]) for i in range(3))),
+                     "body_gradient_rel_err_max": float(max([rel(gb[b, j], ref["body"][b][j], ref["body_abs"][b][j])
+                                                             for b in bodies for j in range(4)] or [0.0])),
+                     # bodies without a path to the zone must get exactly zero
+                     "bodies_without_zone_paths_nonzero_gradient":
+                         int(np.count_nonzero(np.any(gb[idle] != 0.0, axis=1))) if idle else 0}
+    return {"accuracy_vs_fp64_oracle": acc,
             "cpu_baseline": {"value": len(zone) / t_cpu,
                              "unit": "receiver gradients/s (every body with zone paths + transmitter)",
                              "cores": os.cpu_count() or 1, "kind": "oracle central differences (h = 1e-5 m)",

@@ -435,7 +435,13 @@ int rt_tune(rt_scene *scene, const float *rx_soa, int n_rx, float *e_out, uint32
  * centre and radius, the transmitter position and every frequency, with
  * visibility held fixed: the paths are those listed by rt_paths for the same
  * receivers and options, and each one's geometry and field (Eqs. 1-4) are
- * recomputed in FP64 dual numbers, nothing per path being stored.
+ * recomputed in dual numbers (value and eight tangents), nothing per path
+ * being stored.  opt->precision RT_PREC_FP64: FP64 dual numbers throughout;
+ * RT_PREC_FP32: FP32 ones on direct, planar and creeping paths (each path's
+ * length for the phase kept in double-float, as the FP32 fields keep it) and
+ * FP64 ones on reflections off bodies.  The FP32 form is about 2.4x faster;
+ * its field derivatives carry FP32 rounding, which a loss seeded by
+ * E / |E|^2 (power in dB) amplifies near interference nulls.
  *   rx_soa, n_rx          device, as rt_evaluate.
  *   codes, counts, cap    device, as rt_paths or rt_evaluate_with_paths wrote
  *                         them (a receiver with more than cap paths
@@ -447,7 +453,8 @@ int rt_tune(rt_scene *scene, const float *rx_soa, int n_rx, float *e_out, uint32
  *   grad_tx               device double [3]; grad_freqs device double [n_f]
  *                         (per Hz).  All three are overwritten.
  *   opt                   as for rt_evaluate (its enable mask weighs the soft
- *                         and hard creeping fields; precision is ignored).
+ *                         and hard creeping fields; precision picks the dual
+ *                         numbers, above).
  * Asynchronous on `stream`.  Errors: RT_ERR_ARG, RT_ERR_STATE, RT_ERR_CUDA.
  */
 int rt_backward(rt_scene *scene, const float *rx_soa, int n_rx, const uint64_t *codes,

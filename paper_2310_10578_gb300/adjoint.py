@@ -5,7 +5,8 @@ forward  -- rt_evaluate_with_paths: the FP32 fields and, from the same
             centres/radii, transmitter position and frequencies;
 backward -- rt_backward: the adjoint of the evaluation with the path list of
             the forward pass held fixed (visibility frozen), each path's
-            geometry and field recomputed in FP64 dual numbers.
+            geometry and field recomputed in dual numbers: FP64 ones by
+            default (Static.grad_precision), FP32 ones on request.
 
 Argument marshalling only: every step runs in libcreep.so.  The loss is the
 caller's (PyTorch) function of the fields, e.g. received power in dB over a
@@ -24,7 +25,7 @@ class Static:
     materials and (large scenes) the candidate face sequences."""
 
     def __init__(self, tri, tri_face, body_type, body_h, pol, rx_soa, opts=None, cap=256, face_mat=None,
-                 candidates=None):
+                 candidates=None, grad_precision=None):
         self.tri = np.asarray(tri, dtype=np.float32)
         self.tri_face = None if tri_face is None else np.asarray(tri_face, dtype=np.int32)
         self.body_type = np.asarray(body_type, dtype=np.float64).reshape(-1)
@@ -35,6 +36,14 @@ class Static:
         self.cap = int(cap)
         self.face_mat = face_mat              # per face (kind, eps', eps'') or None (PEC)
         self.candidates = candidates          # candidate face sequences [n, 3] (large scenes) or None
+        # the adjoint's dual numbers: FP64 by default -- a loss like received
+        # power in dB seeds dLoss/dE = E/|E|^2, which multiplies the field
+        # derivatives' FP32 error by the sum's conditioning near interference
+        # nulls; creep.RT_PREC_FP32 for the faster FP32 form
+        o = self.opts
+        self.grad_opts = creep.options(o.max_order, o.enable,
+                                       creep.RT_PREC_FP64 if grad_precision is None else grad_precision,
+                                       o.max_encirclements)
 
     @classmethod
     def from_scene(cls, sc, rx_soa, opts=None, cap=256):
@@ -76,7 +85,7 @@ class CreepField(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_E):
         codes, counts = ctx.saved_tensors
-        gb, gt, gf = ctx.S.backward(ctx.static.rx, codes, counts, grad_E, opts=ctx.static.opts)
+        gb, gt, gf = ctx.S.backward(ctx.static.rx, codes, counts, grad_E, opts=ctx.static.grad_opts)
         (db, dt, df), (vb, vt, vf) = ctx.dtypes, ctx.devs
         return gb.to(device=vb, dtype=db), gt.to(device=vt, dtype=dt), gf.to(device=vf, dtype=df), None
 

@@ -803,6 +803,7 @@ static int make_dev(rt_scene *s, const rt_options *opt, DevScene &D, int *prec, 
     D.freq = s->freqs.data();   // host pointer: read by the launcher only
     D.fqc = s->d_fqc;
     D.img = s->d_img;
+    D.img_pairs = s->n_face <= RT_MAX_ENUM_FACES ? 1 : 0;
     D.txb = s->d_txb;
     D.txw = s->d_txw;
     D.bvh = s->d_bvh;
@@ -899,7 +900,7 @@ int rt_backward(rt_scene *s, const float *rx_soa, int n_rx, const uint64_t *code
     s->last_stream = st;
     s->last_launches = n_rx > 0 ? 1 : 0;
     return launch_adjoint(D, rx_soa, n_rx, codes, counts, cap, grad_e, grad_bodies, grad_tx, grad_freqs, s->d_esc + 1,
-                          st);
+                          prec, st);
 }
 
 int rt_evaluate_host(rt_scene *s, const float *rx_soa, int n_rx, float *e_out, uint32_t *flags, const rt_options *opt,

@@ -1,12 +1,14 @@
-// dual.cuh -- FP64 dual numbers for the adjoint (reverse) pass.
+// dual.cuh -- dual numbers for the adjoint (reverse) pass.
 //
-// D8 carries a value and its derivatives with respect to eight parameters of
-// one path: slots 0-3 the centre (x, y, z) and radius of the path's body,
-// 4-6 the transmitter position, 7 the frequency (Hz).  Each path's field
-// depends on no other parameter once its visibility is fixed, so eight
-// tangents give the whole Jacobian of one path's field; the adjoint kernel
-// contracts it with the incoming gradient of the fields.  Every operation
-// below applies the first-order chain rule to the exact FP64 operation.
+// DualT<S> carries a value and its derivatives with respect to eight
+// parameters of one path: slots 0-3 the centre (x, y, z) and radius of the
+// path's body, 4-6 the transmitter position, 7 the frequency (Hz).  Each
+// path's field depends on no other parameter once its visibility is fixed, so
+// eight tangents give the whole Jacobian of one path's field; the adjoint
+// kernel contracts it with the incoming gradient of the fields.  Every
+// operation below applies the first-order chain rule to the operation in the
+// value's own precision: F8 (float) is the adjoint's default, D8 (double)
+// its FP64 form.
 #pragma once
 #include "devmath.cuh"
 
@@ -15,113 +17,143 @@ namespace creep {
 constexpr int ND = 8;
 enum { DS_CX = 0, DS_CY = 1, DS_CZ = 2, DS_A = 3, DS_SX = 4, DS_SY = 5, DS_SZ = 6, DS_F = 7 };
 
-struct D8 {
-    double v;
-    double d[ND];
-    D8() = default;
-    __device__ __forceinline__ D8(double a) : v(a) {
+template <typename S>
+struct DualT {
+    S v;
+    S d[ND];
+    DualT() = default;
+    __device__ __forceinline__ DualT(S a) : v(a) {
 #pragma unroll
-        for (int k = 0; k < ND; ++k) d[k] = 0.0;
+        for (int k = 0; k < ND; ++k) d[k] = S(0);
     }
 };
+typedef DualT<double> D8;
+typedef DualT<float> F8;
+
+// the value-precision math of a dual's scalar type
+__device__ __forceinline__ void dsincos(double x, double *s, double *c) { sincos(x, s, c); }
+__device__ __forceinline__ void dsincos(float x, float *s, float *c) { sincosf(x, s, c); }
+__device__ __forceinline__ void dsincospi(double x, double *s, double *c) { sincospi(x, s, c); }
+__device__ __forceinline__ void dsincospi(float x, float *s, float *c) { sincospif(x, s, c); }
+
 // a parameter: value a, derivative 1 in slot k
-__device__ __forceinline__ D8 dvar(double a, int k) {
-    D8 r(a);
-    r.d[k] = 1.0;
+template <typename S>
+__device__ __forceinline__ DualT<S> dvar_t(S a, int k) {
+    DualT<S> r(a);
+    r.d[k] = S(1);
     return r;
 }
+__device__ __forceinline__ D8 dvar(double a, int k) { return dvar_t<double>(a, k); }
 // y = f(x) with f'(x) = df: y.d = df x.d
-__device__ __forceinline__ D8 dchain(double y, double df, const D8 &x) {
-    D8 r;
+template <typename S>
+__device__ __forceinline__ DualT<S> dchain(S y, S df, const DualT<S> &x) {
+    DualT<S> r;
     r.v = y;
 #pragma unroll
     for (int k = 0; k < ND; ++k) r.d[k] = df * x.d[k];
     return r;
 }
-__device__ __forceinline__ D8 operator+(const D8 &a, const D8 &b) {
-    D8 r;
+template <typename S>
+__device__ __forceinline__ DualT<S> operator+(const DualT<S> &a, const DualT<S> &b) {
+    DualT<S> r;
     r.v = a.v + b.v;
 #pragma unroll
     for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] + b.d[k];
     return r;
 }
-__device__ __forceinline__ D8 operator-(const D8 &a, const D8 &b) {
-    D8 r;
+template <typename S>
+__device__ __forceinline__ DualT<S> operator-(const DualT<S> &a, const DualT<S> &b) {
+    DualT<S> r;
     r.v = a.v - b.v;
 #pragma unroll
     for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] - b.d[k];
     return r;
 }
-__device__ __forceinline__ D8 operator-(const D8 &a) {
-    D8 r;
+template <typename S>
+__device__ __forceinline__ DualT<S> operator-(const DualT<S> &a) {
+    DualT<S> r;
     r.v = -a.v;
 #pragma unroll
     for (int k = 0; k < ND; ++k) r.d[k] = -a.d[k];
     return r;
 }
-__device__ __forceinline__ D8 operator*(const D8 &a, const D8 &b) {
-    D8 r;
+template <typename S>
+__device__ __forceinline__ DualT<S> operator*(const DualT<S> &a, const DualT<S> &b) {
+    DualT<S> r;
     r.v = a.v * b.v;
 #pragma unroll
     for (int k = 0; k < ND; ++k) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
     return r;
 }
-__device__ __forceinline__ D8 operator/(const D8 &a, const D8 &b) {
-    D8 r;
-    const double ib = 1.0 / b.v;
+template <typename S>
+__device__ __forceinline__ DualT<S> operator/(const DualT<S> &a, const DualT<S> &b) {
+    DualT<S> r;
+    const S ib = S(1) / b.v;
     r.v = a.v * ib;
 #pragma unroll
     for (int k = 0; k < ND; ++k) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
     return r;
 }
-__device__ __forceinline__ bool operator<(const D8 &a, const D8 &b) { return a.v < b.v; }
-__device__ __forceinline__ bool operator>(const D8 &a, const D8 &b) { return a.v > b.v; }
-__device__ __forceinline__ bool operator<=(const D8 &a, const D8 &b) { return a.v <= b.v; }
-__device__ __forceinline__ bool operator>=(const D8 &a, const D8 &b) { return a.v >= b.v; }
-__device__ __forceinline__ bool operator==(const D8 &a, const D8 &b) { return a.v == b.v; }
-__device__ __forceinline__ bool operator!=(const D8 &a, const D8 &b) { return a.v != b.v; }
+template <typename S> __device__ __forceinline__ bool operator<(const DualT<S> &a, const DualT<S> &b) { return a.v < b.v; }
+template <typename S> __device__ __forceinline__ bool operator>(const DualT<S> &a, const DualT<S> &b) { return a.v > b.v; }
+template <typename S> __device__ __forceinline__ bool operator<=(const DualT<S> &a, const DualT<S> &b) { return a.v <= b.v; }
+template <typename S> __device__ __forceinline__ bool operator>=(const DualT<S> &a, const DualT<S> &b) { return a.v >= b.v; }
+template <typename S> __device__ __forceinline__ bool operator==(const DualT<S> &a, const DualT<S> &b) { return a.v == b.v; }
+template <typename S> __device__ __forceinline__ bool operator!=(const DualT<S> &a, const DualT<S> &b) { return a.v != b.v; }
 
-__device__ __forceinline__ D8 Sqrt(const D8 &x) {
-    const double s = sqrt(x.v);
-    return dchain(s, s > 0.0 ? 0.5 / s : 0.0, x);
+template <typename S>
+__device__ __forceinline__ DualT<S> Sqrt(const DualT<S> &x) {
+    const S s = sqrt(x.v);
+    return dchain<S>(s, s > S(0) ? S(0.5) / s : S(0), x);
 }
-__device__ __forceinline__ D8 Cbrt(const D8 &x) {
-    const double c = cbrt(x.v);
-    return dchain(c, c != 0.0 ? 1.0 / (3.0 * c * c) : 0.0, x);
+template <typename S>
+__device__ __forceinline__ DualT<S> Cbrt(const DualT<S> &x) {
+    const S c = cbrt(x.v);
+    return dchain<S>(c, c != S(0) ? S(1) / (S(3) * c * c) : S(0), x);
 }
-__device__ __forceinline__ D8 Acos(const D8 &x) {
-    const double s = sqrt(fmax(0.0, 1.0 - x.v * x.v));
-    return dchain(acos(x.v), s > 0.0 ? -1.0 / s : 0.0, x);
+template <typename S>
+__device__ __forceinline__ DualT<S> Acos(const DualT<S> &x) {
+    const S s = sqrt(fmax(S(0), S(1) - x.v * x.v));
+    return dchain<S>(acos(x.v), s > S(0) ? S(-1) / s : S(0), x);
 }
-__device__ __forceinline__ D8 Atan2(const D8 &y, const D8 &x) {
-    D8 r;
+template <typename S>
+__device__ __forceinline__ DualT<S> Atan2(const DualT<S> &y, const DualT<S> &x) {
+    DualT<S> r;
     r.v = atan2(y.v, x.v);
-    const double q = x.v * x.v + y.v * y.v;
-    const double iq = q > 0.0 ? 1.0 / q : 0.0;
+    const S q = x.v * x.v + y.v * y.v;
+    const S iq = q > S(0) ? S(1) / q : S(0);
 #pragma unroll
     for (int k = 0; k < ND; ++k) r.d[k] = (x.v * y.d[k] - y.v * x.d[k]) * iq;
     return r;
 }
-__device__ __forceinline__ D8 Exp(const D8 &x) {
-    const double e = exp(x.v);
-    return dchain(e, e, x);
+template <typename S>
+__device__ __forceinline__ DualT<S> Exp(const DualT<S> &x) {
+    const S e = exp(x.v);
+    return dchain<S>(e, e, x);
 }
-__device__ __forceinline__ D8 Fabs(const D8 &x) { return dchain(fabs(x.v), x.v < 0.0 ? -1.0 : 1.0, x); }
-__device__ __forceinline__ D8 Fmin(const D8 &a, const D8 &b) { return (b.v < a.v) ? b : a; }
-__device__ __forceinline__ D8 Fmax(const D8 &a, const D8 &b) { return (b.v > a.v) ? b : a; }
-__device__ __forceinline__ void SinCos(const D8 &x, D8 *s, D8 *c) {
-    double sv, cv;
-    sincos(x.v, &sv, &cv);
-    *s = dchain(sv, cv, x);
-    *c = dchain(cv, -sv, x);
+template <typename S>
+__device__ __forceinline__ DualT<S> Fabs(const DualT<S> &x) { return dchain<S>(fabs(x.v), x.v < S(0) ? S(-1) : S(1), x); }
+template <typename S>
+__device__ __forceinline__ DualT<S> Fmin(const DualT<S> &a, const DualT<S> &b) { return (b.v < a.v) ? b : a; }
+template <typename S>
+__device__ __forceinline__ DualT<S> Fmax(const DualT<S> &a, const DualT<S> &b) { return (b.v > a.v) ? b : a; }
+template <typename S>
+__device__ __forceinline__ void SinCos(const DualT<S> &x, DualT<S> *s, DualT<S> *c) {
+    S sv, cv;
+    dsincos(x.v, &sv, &cv);
+    *s = dchain<S>(sv, cv, x);
+    *c = dchain<S>(cv, -sv, x);
 }
-__device__ __forceinline__ void SinCosPi(const D8 &x, D8 *s, D8 *c) {
-    double sv, cv;
-    sincospi(x.v, &sv, &cv);
-    *s = dchain(sv, M_PI * cv, x);
-    *c = dchain(cv, -M_PI * sv, x);
+template <typename S>
+__device__ __forceinline__ void SinCosPi(const DualT<S> &x, DualT<S> *s, DualT<S> *c) {
+    S sv, cv;
+    dsincospi(x.v, &sv, &cv);
+    *s = dchain<S>(sv, S(M_PI) * cv, x);
+    *c = dchain<S>(cv, -S(M_PI) * sv, x);
 }
-__device__ __forceinline__ double to_double(const D8 &x) { return x.v; }
-__device__ __forceinline__ float to_float(const D8 &x) { return (float)x.v; }
+template <typename S>
+__device__ __forceinline__ double to_double(const DualT<S> &x) { return (double)x.v; }
+template <typename S>
+__device__ __forceinline__ float to_float(const DualT<S> &x) { return (float)x.v; }
 
 }  // namespace creep

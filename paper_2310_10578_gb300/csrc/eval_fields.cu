@@ -82,6 +82,7 @@ struct Ctx {
     const dq4 *res64;
     const double *weid64;
     const float4 *img;           // source images (double-float), see DevScene
+    int img_pairs;               // img holds the ordered face pairs too
     const float4 *txb;           // [n_body][2] source-side body frame, see DevScene
     const float4 *txw;           // [n_face][n_body][2] the same for each face's source image (or nullptr)
     const float4 *bvh;           // triangle BVH, see DevScene (nullptr: every triangle is tested)
@@ -2643,6 +2644,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         c.fock = s_fock; c.res = s_res; c.weid = s_weid; c.weid_L = S.weid_L;
         c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
         c.img = S.img;
+        c.img_pairs = S.img_pairs;
         c.face_mat = S.face_mat;
         c.txb = body_sm ? s_txb : F1.txb;
         c.occ_src = nullptr;
@@ -3116,19 +3118,32 @@ int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const Frame
 // field derivative with respect to its body's centre and radius, the
 // transmitter position and the frequency.  Visibility is held fixed: the
 // paths are those of the forward path list (rt_paths), and each one's
-// geometry and field are recomputed here in FP64 dual numbers (D8), by the
-// same construction as the forward FP64 path: image points for planar
+// geometry and field are recomputed here in dual numbers (dual.cuh), by the
+// same construction as the forward path: image points for planar
 // reflections (Eq. 3), the specular point on the body (its derivative from
-// one Newton step in dual arithmetic at the FP64 root, which is the
+// one Newton step in dual arithmetic at the root, which is the
 // implicit-function derivative), the tangent points and geodesic of the
 // creeping ray (Eq. 4, Fig. 1), the Fock--Pekeris functions (table
 // derivative from the cubic Hermite interpolant, residue series term by
 // term), the transition function through w'(z) = -2 z w(z) + 2j/sqrt(pi).
+//
+// F8 (FP32 duals, the default): the forward FP32 construction -- FP32
+// geometry, table and Faddeeva coefficients -- with each path's length for
+// the phase as double-float from the same exact pieces the forward FP32
+// kernel uses (the source's FP64 images, the tangent lengths from exact
+// squares), so its phase keeps the forward's accuracy.  Direct, planar and
+// creeping paths take F8; reflections off a body take D8 in both modes.
+// D8 (FP64 duals, RT_PREC_FP64): the forward FP64 construction.
 
 template <> __device__ __forceinline__ void face_plane<D8>(const Ctx &c, int f, v3t<D8> *n, D8 *d) {
     dq4 q = c.face64[f]; *n = mk3<D8>(q.x, q.y, q.z); *d = D8(q.w);
 }
+template <> __device__ __forceinline__ void face_plane<F8>(const Ctx &c, int f, v3t<F8> *n, F8 *d) {
+    float4 q = c.face32[f]; *n = mk3<F8>(q.x, q.y, q.z); *d = F8(q.w);
+}
 
+// Fock--Pekeris functions of a dual xi: the residue series term by term
+// above XI_HI, else the table's cubic Hermite interpolant and its slope
 __device__ void pekeris(const Ctx &c, const D8 &xi, cpx<D8> &ps, cpx<D8> &ph, bool regular) {
     const double cc = (0.5 / sqrt(M_PI)) * cos(M_PI / 4.0);
     const D8 ci = D8(cc) / xi;
@@ -3167,25 +3182,64 @@ __device__ void pekeris(const Ctx &c, const D8 &xi, cpx<D8> &ps, cpx<D8> &ph, bo
         const double gi = h00 * g0.y + h10 * q0.y + h01 * g1.y + h11 * q1.y;
         const double dr = d00 * g0.x + d10 * q0.x + d01 * g1.x + d11 * q1.x;
         const double di = d00 * g0.y + d10 * q0.y + d01 * g1.y + d11 * q1.y;
-        G[k] = mkc<D8>(dchain(gr, dr, xi), dchain(gi, di, xi));
+        G[k] = mkc<D8>(dchain<double>(gr, dr, xi), dchain<double>(gi, di, xi));
     }
     const cpx<D8> rot = cexpi(xi * xi * xi / D8(12.0));
     ps = G[0] * rot;
     ph = G[1] * rot;
     if (!regular) { ps = ps - mkc<D8>(ci, -ci); ph = ph - mkc<D8>(ci, -ci); }
 }
+__device__ void pekeris(const Ctx &c, const F8 &xi, cpx<F8> &ps, cpx<F8> &ph, bool regular) {
+    const F8 ci = F8(0.19947114f) / xi;               // c/xi = (ci, -ci)
+    if (xi.v > (float)XI_HI) {
+        // (the FP32 table's residue constants: alpha sqrt3/2, alpha/2, coefficient)
+        cpx<F8> ss = mkc<F8>(0.0f, 0.0f), sh = mkc<F8>(0.0f, 0.0f);
+        for (int n = 0; n < FOCK_NRES; ++n) {
+            const float4 rs = c.res[2 * n], rh = c.res[2 * n + 1];
+            F8 sn, cs;
+            SinCos(xi * F8(rs.y), &sn, &cs);
+            F8 e = Exp(-(xi * F8(rs.x))) * F8(rs.z);
+            ss = ss + mkc<F8>(e * cs, -(e * sn));
+            SinCos(xi * F8(rh.y), &sn, &cs);
+            e = Exp(-(xi * F8(rh.x))) * F8(rh.z);
+            sh = sh + mkc<F8>(e * cs, -(e * sn));
+        }
+        const cpx<F8> pre = mkc<F8>(-0.27248264483602590f, 0.07301150463530957f);   // -e^{-j pi/12}/(2 sqrt(pi))
+        ps = pre * ss;
+        ph = pre * sh;
+        if (regular) { ps = ps + mkc<F8>(ci, -ci); ph = ph + mkc<F8>(ci, -ci); }
+        return;
+    }
+    // the FP32 table holds G and XI_STEP G' per node
+    const float u = (xi.v - (float)XI_LO) * (float)(1.0 / XI_STEP);
+    const int j = min(max((int)u, 0), FOCK_N - 2);
+    const float t = u - (float)j, t2 = t * t, omt = 1.0f - t;
+    const float h00 = (1.0f + 2.0f * t) * omt * omt, h10 = t * omt * omt, h01 = t2 * (3.0f - 2.0f * t),
+                h11 = t2 * (t - 1.0f);
+    const float ih = (float)(1.0 / XI_STEP);
+    const float d00 = (6.0f * t2 - 6.0f * t) * ih, d10 = (1.0f - 4.0f * t + 3.0f * t2) * ih,
+                d01 = (6.0f * t - 6.0f * t2) * ih, d11 = (3.0f * t2 - 2.0f * t) * ih;
+    cpx<F8> G[2];
+    for (int k = 0; k < 2; ++k) {
+        const float4 a0 = c.fock[2 * j + k], a1 = c.fock[2 * j + 2 + k];
+        const float gr = h00 * a0.x + h10 * a0.z + h01 * a1.x + h11 * a1.z;
+        const float gi = h00 * a0.y + h10 * a0.w + h01 * a1.y + h11 * a1.w;
+        const float dr = d00 * a0.x + d10 * a0.z + d01 * a1.x + d11 * a1.z;
+        const float di = d00 * a0.y + d10 * a0.w + d01 * a1.y + d11 * a1.w;
+        G[k] = mkc<F8>(dchain<float>(gr, dr, xi), dchain<float>(gi, di, xi));
+    }
+    const cpx<F8> rot = cexpi(xi * xi * xi / F8(12.0f));
+    ps = G[0] * rot;
+    ph = G[1] * rot;
+    if (!regular) { ps = ps - mkc<F8>(ci, -ci); ph = ph - mkc<F8>(ci, -ci); }
+}
 
-__device__ cpx<D8> faddeeva_t(const Ctx &c, const cpx<D8> &zd) {
-    cpx<double> z = mkc(zd.re.v, zd.im.v);
-    const double L = c.weid_L;
-    cpx<double> lm = mkc(L + z.im, -z.re), lp = mkc(L - z.im, z.re);
-    cpx<double> Z = cdiv(lp, lm);
-    cpx<double> p = mkc(c.weid64[WEIDEMAN_N - 1], 0.0);
-    for (int n = WEIDEMAN_N - 2; n >= 0; --n) p = p * Z + mkc(c.weid64[n], 0.0);
-    cpx<double> w = cdiv(p * 2.0, lm * lm) + cdiv(mkc(0.56418958354775628, 0.0), lm);
-    // w'(z) = -2 z w + 2j / sqrt(pi)
-    cpx<double> wp = z * w * -2.0 + mkc(0.0, 1.1283791670955126);
-    cpx<D8> r;
+// w(z) of a dual z, with w'(z) = -2 z w + 2j / sqrt(pi)
+template <typename S>
+__device__ __forceinline__ cpx<DualT<S>> faddeeva_dual(const cpx<DualT<S>> &zd, cpx<S> w) {
+    const cpx<S> z = mkc(zd.re.v, zd.im.v);
+    const cpx<S> wp = z * w * S(-2) + mkc(S(0), S(1.1283791670955126));
+    cpx<DualT<S>> r;
     r.re.v = w.re; r.im.v = w.im;
 #pragma unroll
     for (int k = 0; k < ND; ++k) {
@@ -3194,14 +3248,35 @@ __device__ cpx<D8> faddeeva_t(const Ctx &c, const cpx<D8> &zd) {
     }
     return r;
 }
+__device__ cpx<D8> faddeeva_t(const Ctx &c, const cpx<D8> &zd) {
+    cpx<double> z = mkc(zd.re.v, zd.im.v);
+    const double L = c.weid_L;
+    cpx<double> lm = mkc(L + z.im, -z.re), lp = mkc(L - z.im, z.re);
+    cpx<double> Z = cdiv(lp, lm);
+    cpx<double> p = mkc(c.weid64[WEIDEMAN_N - 1], 0.0);
+    for (int n = WEIDEMAN_N - 2; n >= 0; --n) p = p * Z + mkc(c.weid64[n], 0.0);
+    cpx<double> w = cdiv(p * 2.0, lm * lm) + cdiv(mkc(0.56418958354775628, 0.0), lm);
+    return faddeeva_dual<double>(zd, w);
+}
+__device__ cpx<F8> faddeeva_t(const Ctx &c, const cpx<F8> &zd) {
+    return faddeeva_dual<float>(zd, faddeeva<float>(c, mkc(zd.re.v, zd.im.v)));
+}
 
-// wavenumber, (k/2)^{1/3} and the path phasor with the frequency as slot DS_F
+// wavenumber, (k/2)^{1/3} with the frequency as slot DS_F
 __device__ __forceinline__ D8 kof(const FreqC &fq, int f, const D8 &) {
     D8 k(fq.kd[f]);
     k.d[DS_F] = 2.0 * M_PI / 299792458.0;
     return k;
 }
+__device__ __forceinline__ F8 kof(const FreqC &fq, int f, const F8 &) {
+    F8 k(fq.k[f]);
+    k.d[DS_F] = (float)(2.0 * M_PI / 299792458.0);
+    return k;
+}
 __device__ __forceinline__ D8 khof(const FreqC &fq, int f, const D8 &x) { return Cbrt(kof(fq, f, x) * D8(0.5)); }
+__device__ __forceinline__ F8 khof(const FreqC &fq, int f, const F8 &x) { return Cbrt(kof(fq, f, x) * F8(0.5f)); }
+
+// the path phasor e^{-j k L}; FP64 duals: from the dual length itself
 __device__ __forceinline__ cpx<D8> phasor(const FreqC &fq, int f, const D8 &L) {
     D8 fc(fq.fc[f]);
     fc.d[DS_F] = 1.0 / 299792458.0;
@@ -3212,6 +3287,34 @@ __device__ __forceinline__ cpx<D8> phasor(const FreqC &fq, int f, const D8 &L) {
     return mkc<D8>(co, -s);
 }
 __device__ __forceinline__ D8 len_val(const D8 &L) { return L; }
+// FP32 duals: the length's tangents from the dual, its value as double-float
+// (the phase as the FP32 fraction of L / lambda, integer cycles dropped)
+struct LenF8 {
+    F8 l;           // tangents (and an FP32 value for amplitudes)
+    dfl h;          // the value, for the phase
+};
+__device__ __forceinline__ cpx<F8> phasor(const FreqC &fq, int f, const LenF8 &L) {
+    dfl il; il.hi = fq.il_hi[f]; il.lo = fq.il_lo[f];
+    const dfl cyc = df_mul(L.h, il);
+    float fr = (cyc.hi - floorf(cyc.hi)) + cyc.lo;
+    fr -= floorf(fr);
+    const float ilf = il.hi;
+    F8 c;
+    c.v = fr;
+#pragma unroll
+    for (int k = 0; k < ND; ++k) c.d[k] = L.l.d[k] * ilf;
+    c.d[DS_F] += (L.h.hi + L.h.lo) * (float)(1.0 / 299792458.0);    // d(L f / c)/df
+    F8 s, co;
+    SinCosPi(c * F8(2.0f), &s, &co);
+    return mkc<F8>(co, -s);
+}
+__device__ __forceinline__ F8 len_val(const LenF8 &L) { return L.l; }
+
+template <typename DT> struct AdjLen;
+template <> struct AdjLen<D8> { typedef D8 type; };
+template <> struct AdjLen<F8> { typedef LenF8 type; };
+__device__ __forceinline__ D8 mk_len(const D8 &l, dfl) { return l; }
+__device__ __forceinline__ LenF8 mk_len(const F8 &l, dfl h) { return LenF8{l, h}; }
 
 // contracts each path field's tangents with dLoss/dE of its receiver
 struct AccAdj {
@@ -3220,113 +3323,193 @@ struct AccAdj {
     double g[ND - 1];       // body and transmitter slots
     double gf[NFC];         // frequency slot, per frequency of the chunk
 };
-__device__ __forceinline__ void acc_put(AccAdj &a, int f, const cpx<D8> &x, const cpx<D8> &y, const cpx<D8> &z) {
-    const cpx<D8> *e[3] = {&x, &y, &z};
+template <typename S>
+__device__ __forceinline__ void acc_put(AccAdj &a, int f, const cpx<DualT<S>> &x, const cpx<DualT<S>> &y,
+                                        const cpx<DualT<S>> &z) {
+    const cpx<DualT<S>> *e[3] = {&x, &y, &z};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
         const size_t idx = ((size_t)(a.f0 + f) * 3 + q) * a.n_rx + a.r;
-        const float gr = a.gE[2 * idx], gi = a.gE[2 * idx + 1];
+        const S gr = a.gE[2 * idx], gi = a.gE[2 * idx + 1];
 #pragma unroll
-        for (int k = 0; k < ND - 1; ++k) a.g[k] += gr * e[q]->re.d[k] + gi * e[q]->im.d[k];
-        a.gf[f] += gr * e[q]->re.d[DS_F] + gi * e[q]->im.d[DS_F];
+        for (int k = 0; k < ND - 1; ++k) a.g[k] += (double)(gr * e[q]->re.d[k] + gi * e[q]->im.d[k]);
+        a.gf[f] += (double)(gr * e[q]->re.d[DS_F] + gi * e[q]->im.d[DS_F]);
     }
 }
 
 // body b's centre and radius as parameters (slots 0-3)
-__device__ __forceinline__ void adj_body(const Ctx &c, int b, v3t<D8> &cc, D8 &a, bool &sphere) {
+template <typename S>
+__device__ __forceinline__ void adj_body(const Ctx &c, int b, v3t<DualT<S>> &cc, DualT<S> &a, bool &sphere) {
     float4 q0 = c.body[2 * b], q1 = c.body[2 * b + 1];
-    cc = mk3<D8>(dvar(q0.x, DS_CX), dvar(q0.y, DS_CY), dvar(q0.z, DS_CZ));
-    a = dvar(q0.w, DS_A);
+    cc = mk3<DualT<S>>(dvar_t<S>(q0.x, DS_CX), dvar_t<S>(q0.y, DS_CY), dvar_t<S>(q0.z, DS_CZ));
+    a = dvar_t<S>(q0.w, DS_A);
     sphere = q1.y == 0.0f;
 }
 
-__device__ __noinline__ void adj_refl_root(const D8 &a, const D8 &ds, const D8 &pu, const D8 &pv, const D8 &gam,
-                                           D8 *cs, D8 *sn) {
-    dx c0, s0;
-    refl_root(dx(a.v), dx(ds.v), dx(pu.v), dx(pv.v), dx(gam.v), &c0, &s0);
-    // one Newton step on dL/dpsi = 0 in dual arithmetic at the root
-    const D8 psi(atan2(s0.v, c0.v));
-    D8 s, c;
+// the reflection point's angle as a dual: the root in the dual's precision
+// (FP64: refined to the bisection root; FP32: the forward FP32 root, refined
+// in double-float or FP64 near grazing), then one Newton step on dL/dpsi = 0
+// in dual arithmetic (the implicit-function derivative)
+__device__ __forceinline__ void refl_root_val(double a, double ds, double pu, double pv, double gam, double *c0,
+                                              double *s0) {
+    dx cc, ss;
+    refl_root(dx(a), dx(ds), dx(pu), dx(pv), dx(gam), &cc, &ss);
+    *c0 = cc.v; *s0 = ss.v;
+}
+__device__ __forceinline__ void refl_root_val(float a, float ds, float pu, float pv, float gam, float *c0, float *s0) {
+    float err = 0.0f;
+    const float psi = refl_psi(a, ds, pu, pv, gam, &err);
+    float sn, cs;
+    sincosf(psi, &sn, &cs);
+    const float c2 = (ds * cs - a) / sqrtf((a * cs - ds) * (a * cs - ds) + a * a * sn * sn);
+    if (err > 1e-5f * fmaxf(c2, 0.0f)) {
+        if (!refl_polish_df(a, ds, pu, pv, psi, &cs, &sn)) refl_polish(a, ds, pu, pv, gam, psi, &cs, &sn);
+    }
+    *c0 = cs; *s0 = sn;
+}
+template <typename S>
+__device__ __noinline__ void adj_refl_root(const DualT<S> &a, const DualT<S> &ds, const DualT<S> &pu,
+                                           const DualT<S> &pv, const DualT<S> &gam, DualT<S> *cs, DualT<S> *sn) {
+    typedef DualT<S> DT;
+    S c0, s0;
+    refl_root_val(a.v, ds.v, pu.v, pv.v, gam.v, &c0, &s0);
+    const DT psi(atan2(s0, c0));
+    DT s, c;
     SinCos(psi, &s, &c);
-    const D8 qx = a * c, qy = a * s;
-    const D8 lS = Sqrt((qx - ds) * (qx - ds) + qy * qy);
-    const D8 lP = Sqrt((qx - pu) * (qx - pu) + (qy - pv) * (qy - pv));
-    const D8 gS = a * ds * s / lS, gP = a * (pu * s - pv * c) / lP;
-    const D8 h = (ds * qx - gS * gS) / lS + (pu * qx + pv * qy - gP * gP) / lP;
+    const DT qx = a * c, qy = a * s;
+    const DT lS = Sqrt((qx - ds) * (qx - ds) + qy * qy);
+    const DT lP = Sqrt((qx - pu) * (qx - pu) + (qy - pv) * (qy - pv));
+    const DT gS = a * ds * s / lS, gP = a * (pu * s - pv * c) / lP;
+    DT h;
+    if constexpr (sizeof(S) == 8) {
+        h = (ds * qx - gS * gS) / lS + (pu * qx + pv * qy - gP * gP) / lP;
+    } else {
+        // d2L/dpsi2 in the product form a sum_X (u - a)(|X|^2 - a u) / |Q - X|^3,
+        // u = X.n: the difference form above cancels near grazing incidence
+        const DT uS = ds * c, uP = pu * c + pv * s;
+        h = a * ((uS - a) * (ds * ds - a * uS) / (lS * lS * lS) +
+                 (uP - a) * (pu * pu + pv * pv - a * uP) / (lP * lP * lP));
+    }
     SinCos(psi - (gS + gP) / h, sn, cs);
 }
 
-// reflection off body b (the forward FP64 construction, without decisions)
-__device__ __noinline__ void adj_rb(const Ctx &c, int b, v3t<D8> S, v3t<D8> P, const FreqC &fq, AccAdj &acc) {
-    v3t<D8> cc;
-    D8 a;
+// double-float lengths of the FP32 path pieces (no use for FP64 duals)
+__device__ __forceinline__ v3t<float> vals(const v3t<F8> &a) { return mk3(a.x.v, a.y.v, a.z.v); }
+__device__ __forceinline__ v3t<float> vals(const v3t<D8> &a) {
+    return mk3((float)a.x.v, (float)a.y.v, (float)a.z.v);
+}
+// sqrt(|X - c|^2 - a^2) from the exact squares (horiz: horizontal distance)
+__device__ __forceinline__ dfl df_tangent_len(v3t<float> X, float4 q0, bool horiz) {
+    dfl q2 = df_add(df_sq_diff(X.x, q0.x), df_sq_diff(X.y, q0.y));
+    if (!horiz) q2 = df_add(q2, df_sq_diff(X.z, q0.z));
+    dfl a2 = two_prod(q0.w, q0.w);
+    a2.hi = -a2.hi; a2.lo = -a2.lo;
+    q2 = df_add(q2, a2);
+    if (!(q2.hi > 0.0f)) { q2.hi = 0.0f; q2.lo = 0.0f; return q2; }
+    return df_sqrt(q2);
+}
+
+// reflection off body b (the forward construction, without decisions)
+template <typename DT>
+__device__ __noinline__ void adj_rb(const Ctx &c, int b, v3t<DT> S, v3t<DT> P, const FreqC &fq, AccAdj &acc) {
+    typedef decltype(DT().v) SC;
+    v3t<DT> cc;
+    DT a;
     bool sphere;
-    adj_body(c, b, cc, a, sphere);
-    Frame<D8> F;
-    if (sphere) sphere_frame(S, P, cc, a, F, D8(0.0));
-    else cyl_frame(S, P, cc.x, cc.y, a, F, D8(0.0));
-    D8 cs, sn;
-    adj_refl_root(a, F.ds, F.pu, F.pv, F.gam, &cs, &sn);
-    v3t<D8> n = F.u * cs + F.v * sn;
-    v3t<D8> Q;
+    adj_body<SC>(c, b, cc, a, sphere);
+    Frame<DT> F;
+    if (sphere) sphere_frame(S, P, cc, a, F, DT(0.0f));
+    else cyl_frame(S, P, cc.x, cc.y, a, F, DT(0.0f));
+    DT cs, sn;
+    adj_refl_root<SC>(a, F.ds, F.pu, F.pv, F.gam, &cs, &sn);
+    v3t<DT> n = F.u * cs + F.v * sn;
+    v3t<DT> Q;
     if (sphere) {
         Q = cc + n * a;
     } else {
-        D8 qx = a * cs, qy = a * sn;
-        D8 l1 = Sqrt((qx - F.ds) * (qx - F.ds) + qy * qy);
-        D8 l2 = Sqrt((qx - F.pu) * (qx - F.pu) + (qy - F.pv) * (qy - F.pv));
-        D8 zq = S.z + (P.z - S.z) * l1 / (l1 + l2);
-        Q = mk3<D8>(cc.x + a * n.x, cc.y + a * n.y, zq);
+        DT qx = a * cs, qy = a * sn;
+        DT l1 = Sqrt((qx - F.ds) * (qx - F.ds) + qy * qy);
+        DT l2 = Sqrt((qx - F.pu) * (qx - F.pu) + (qy - F.pv) * (qy - F.pv));
+        DT zq = S.z + (P.z - S.z) * l1 / (l1 + l2);
+        Q = mk3<DT>(cc.x + a * n.x, cc.y + a * n.y, zq);
     }
-    Geo<D8> g;
-    v3t<D8> shi = unit3(Q - S);
-    D8 cth = -dot3(shi, n);
+    Geo<DT> g;
+    v3t<DT> shi = unit3(Q - S);
+    DT cth = -dot3(shi, n);
     g.dr = P - Q;
     g.Q1 = Q;
     g.n1 = n;
     if (sphere) {
-        g.inv_f1 = D8(2.0) / (a * cth);
-        g.inv_f2 = D8(2.0) * cth / a;
+        g.inv_f1 = DT(2.0f) / (a * cth);
+        g.inv_f2 = DT(2.0f) * cth / a;
         g.rho_g = a;
     } else {
-        g.inv_f1 = D8(2.0) * (D8(1.0) - shi.z * shi.z) / (a * cth);
-        g.inv_f2 = D8(0.0);
-        D8 sphi = -(shi.x * n.y) + shi.y * n.x;
-        g.rho_g = (sphi == D8(0.0)) ? D8(INFINITY) : a * (D8(1.0) - cth * cth) / (sphi * sphi);
+        g.inv_f1 = DT(2.0f) * (DT(1.0f) - shi.z * shi.z) / (a * cth);
+        g.inv_f2 = DT(0.0f);
+        DT sphi = -(shi.x * n.y) + shi.y * n.x;
+        g.rho_g = (sphi == DT(0.0f)) ? DT(INFINITY) : a * (DT(1.0f) - cth * cth) / (sphi * sphi);
     }
-    field_body_refl<D8, D8, false, AccAdj>(c, acc, fq, S, P, g, norm3(Q - S) + norm3(P - Q));
+    dfl Lh = {0.0f, 0.0f};
+    if constexpr (sizeof(SC) == 4) {
+        // the forward's length: both legs to the FP32 surface point c + a n, in double-float
+        const float4 q0 = c.body[2 * b];
+        dfl ws[3], wp[3];
+        df_to_surface(vals(S), q0, q0.w, vals(n), !sphere, ws);
+        df_to_surface(vals(P), q0, q0.w, vals(n), !sphere, wp);
+        const dfl si = df_norm3(ws), sr = df_norm3(wp);
+        if (sphere) {
+            Lh = df_add(si, sr);
+        } else {
+            const dfl H = df_add(si, sr);
+            Lh = df_sqrt(df_add(df_mul(H, H), df_sq_diff(P.z.v, S.z.v)));
+        }
+    }
+    field_body_refl<DT, typename AdjLen<DT>::type, false, AccAdj>(c, acc, fq, S, P, g,
+                                                                  mk_len(norm3(Q - S) + norm3(P - Q), Lh));
 }
 
 // creeping ray round body b, dir 0 short way, 1 long way, with enc extra
 // turns; wall >= 0: fed by the reflection at face wall (the creeping ray of
 // the source's image there); false: no finite field
-__device__ __noinline__ bool adj_creep(const Ctx &c, int b, int dir, int enc, v3t<D8> S0, v3t<D8> P, const FreqC &fq,
+template <typename DT>
+__device__ __noinline__ bool adj_creep(const Ctx &c, int b, int dir, int enc, v3t<DT> S0, v3t<DT> P, const FreqC &fq,
                                        unsigned enable, AccAdj &acc, int wall = -1) {
-    v3t<D8> cc;
-    D8 a;
+    typedef decltype(DT().v) SC;
+    v3t<DT> cc;
+    DT a;
     bool sphere;
-    adj_body(c, b, cc, a, sphere);
-    v3t<D8> S = S0;
+    adj_body<SC>(c, b, cc, a, sphere);
+    v3t<DT> S = S0;
+    v3t<float> Sval = vals(S0);            // (FP32 duals: the source point of the tangent length)
     if (wall >= 0) {
-        v3t<D8> n;
-        D8 d;
-        face_plane<D8>(c, wall, &n, &d);
+        v3t<DT> n;
+        DT d;
+        face_plane<DT>(c, wall, &n, &d);
         S = mirror_pt(S0, n, d);
+        if constexpr (sizeof(SC) == 4) {
+            // the image's value from the FP64 plane, as the forward's per-transmitter table has it
+            const dq4 q = c.face64[wall];
+            const double X[3] = {c.S.x, c.S.y, c.S.z};
+            const double dist = q.x * X[0] + q.y * X[1] + q.z * X[2] - q.w;
+            Sval = mk3((float)(X[0] - q.x * (2.0 * dist)), (float)(X[1] - q.y * (2.0 * dist)),
+                       (float)(X[2] - q.z * (2.0 * dist)));
+        }
     }
-    Frame<D8> F;
-    if (sphere) sphere_frame(S, P, cc, a, F, D8(0.0));
-    else cyl_frame(S, P, cc.x, cc.y, a, F, D8(0.0));
-    const D8 TWO_PI(6.283185307179586476925286766559);
-    D8 dpsi = (dir == 0) ? (F.gam - F.bs - F.bp) : (TWO_PI - F.gam - F.bs - F.bp);
-    dpsi = dpsi + TWO_PI * D8((double)enc);
-    Geo<D8> g;
-    D8 psi1 = (dir == 0) ? F.bs : -F.bs;
-    D8 psi2 = (dir == 0) ? F.gam - F.bp : F.gam + F.bp;
-    D8 s1, c1, s2, c2;
+    Frame<DT> F;
+    if (sphere) sphere_frame(S, P, cc, a, F, DT(0.0f));
+    else cyl_frame(S, P, cc.x, cc.y, a, F, DT(0.0f));
+    const DT TWO_PI(SC(6.283185307179586476925286766559));
+    DT dpsi = (dir == 0) ? (F.gam - F.bs - F.bp) : (TWO_PI - F.gam - F.bs - F.bp);
+    dpsi = dpsi + TWO_PI * DT(SC(enc));
+    Geo<DT> g;
+    DT psi1 = (dir == 0) ? F.bs : -F.bs;
+    DT psi2 = (dir == 0) ? F.gam - F.bp : F.gam + F.bp;
+    DT s1, c1, s2, c2;
     SinCos(psi1, &s1, &c1);
     SinCos(psi2, &s2, &c2);
     g.n1 = F.u * c1 + F.v * s1;
     g.n2 = F.u * c2 + F.v * s2;
+    dfl Lh = {0.0f, 0.0f};
     if (sphere) {
         g.Q1 = cc + g.n1 * a;
         g.Q2 = cc + g.n2 * a;
@@ -3335,106 +3518,150 @@ __device__ __noinline__ bool adj_creep(const Ctx &c, int b, int dir, int enc, v3
         g.t = a * dpsi;
         g.rho_g = a;
         g.caus = (dir == 1);
-        D8 sg, cg;
+        DT sg, cg;
         SinCos(F.gam, &sg, &cg);
         g.dperp = F.dp * sg;
-        if (!(g.dperp > D8(0.0))) return false;
-        D8 sb, cb;
+        if (!(g.dperp > DT(0.0f))) return false;
+        DT sb, cb;
         SinCos(F.bs, &sb, &cb);
         g.amp = Sqrt(a * sb / g.dperp) / Sqrt(g.sq) / g.sp;
         if (enc & 1) g.amp = -g.amp;             // the (-1) of an odd number of extra turns
+        if constexpr (sizeof(SC) == 4) {
+            const float4 q0 = c.body[2 * b];
+            Lh = df_addf(df_add(df_tangent_len(Sval, q0, false), df_tangent_len(vals(P), q0, false)), g.t.v);
+        }
     } else {
-        D8 ds_ = F.sps, dp_ = F.sqp;
-        D8 dz = P.z - S.z;
-        D8 H = ds_ + a * dpsi + dp_;
-        D8 ell = Sqrt(H * H + dz * dz);
-        D8 sin0 = H / ell;
-        D8 z1 = S.z + dz * ds_ / H, z2 = S.z + dz * (ds_ + a * dpsi) / H;
-        g.Q1 = mk3<D8>(cc.x + a * g.n1.x, cc.y + a * g.n1.y, z1);
-        g.Q2 = mk3<D8>(cc.x + a * g.n2.x, cc.y + a * g.n2.y, z2);
+        DT ds_ = F.sps, dp_ = F.sqp;
+        DT dz = P.z - S.z;
+        DT H = ds_ + a * dpsi + dp_;
+        DT ell = Sqrt(H * H + dz * dz);
+        DT sin0 = H / ell;
+        DT z1 = S.z + dz * ds_ / H, z2 = S.z + dz * (ds_ + a * dpsi) / H;
+        g.Q1 = mk3<DT>(cc.x + a * g.n1.x, cc.y + a * g.n1.y, z1);
+        g.Q2 = mk3<DT>(cc.x + a * g.n2.x, cc.y + a * g.n2.y, z2);
         g.sp = ds_ / sin0;
         g.t = a * dpsi / sin0;
         g.sq = dp_ / sin0;
         g.rho_g = a / (sin0 * sin0);
         g.caus = 0;
-        g.dperp = D8(0.0);
-        g.amp = D8(1.0) / Sqrt(g.sp * g.sq * (g.sp + g.t + g.sq));
+        g.dperp = DT(0.0f);
+        g.amp = DT(1.0f) / Sqrt(g.sp * g.sq * (g.sp + g.t + g.sq));
+        if constexpr (sizeof(SC) == 4) {
+            const float4 q0 = c.body[2 * b];
+            const dfl Hh = df_addf(df_add(df_tangent_len(Sval, q0, true), df_tangent_len(vals(P), q0, true)),
+                                   (a * dpsi).v);
+            Lh = df_sqrt(df_add(df_mul(Hh, Hh), df_sq_diff(P.z.v, Sval.z)));
+        }
     }
-    if (wall >= 0) field_wcreep<D8, D8, false, AccAdj>(c, acc, fq, wall, S0, S, P, g, g.sp + g.t + g.sq, enable);
-    else field_creep<D8, D8, false, AccAdj>(c, acc, fq, S, P, g, g.sp + g.t + g.sq, enable);
+    typedef typename AdjLen<DT>::type LT;
+    if (wall >= 0)
+        field_wcreep<DT, LT, false, AccAdj>(c, acc, fq, wall, S0, S, P, g, mk_len(g.sp + g.t + g.sq, Lh), enable);
+    else
+        field_creep<DT, LT, false, AccAdj>(c, acc, fq, S, P, g, mk_len(g.sp + g.t + g.sq, Lh), enable);
     return true;
 }
 
+// the precise value of a planar path's length for FP32 duals: |P - image|,
+// the image the source's FP64 mirror (double-float tables where they exist)
+__device__ __forceinline__ dfl planar_len(const Ctx &c, int order, int i, int j, v3t<float> P) {
+    if (order == 0) return df_dist(c.S, P);
+    if (order == 1) return df_dist_df(c.img[2 * i], c.img[2 * i + 1], P);
+    if (c.img_pairs) {
+        const int slot = c.n_face + i * c.n_face + j;
+        return df_dist_df(c.img[2 * slot], c.img[2 * slot + 1], P);
+    }
+    // (large scenes keep no pair table: the second mirror from the first image in FP64)
+    const float4 h = c.img[2 * i], l = c.img[2 * i + 1];
+    const double X[3] = {(double)h.x + (double)l.x, (double)h.y + (double)l.y, (double)h.z + (double)l.z};
+    const dq4 q = c.face64[j];
+    const double dist = q.x * X[0] + q.y * X[1] + q.z * X[2] - q.w;
+    const double Y[3] = {X[0] - q.x * (2.0 * dist), X[1] - q.y * (2.0 * dist), X[2] - q.z * (2.0 * dist)};
+    float4 yh, yl;
+    yh.x = (float)Y[0]; yh.y = (float)Y[1]; yh.z = (float)Y[2]; yh.w = 0.0f;
+    yl.x = (float)(Y[0] - (double)yh.x); yl.y = (float)(Y[1] - (double)yh.y); yl.z = (float)(Y[2] - (double)yh.z);
+    yl.w = 0.0f;
+    return df_dist_df(yh, yl, P);
+}
+
 // direct ray and planar image paths (faces i, j; -1: none)
-__device__ __noinline__ void adj_planar(const Ctx &c, int order, int i, int j, v3t<D8> S, v3t<D8> P,
+template <typename DT>
+__device__ __noinline__ void adj_planar(const Ctx &c, int order, int i, int j, v3t<DT> S, v3t<DT> P,
                                         const FreqC &fq, AccAdj &acc) {
+    typedef decltype(DT().v) SC;
+    dfl Lh = {0.0f, 0.0f};
+    if constexpr (sizeof(SC) == 4) Lh = planar_len(c, order, i, j, vals(P));
     if (order == 0) {
-        v3t<D8> d = P - S;
-        D8 L = norm3(d);
-        add_ray(acc, fq, src_pol(c, d * (D8(1.0) / L)), D8(1.0) / L, L);
+        v3t<DT> d = P - S;
+        DT L = norm3(d);
+        add_ray(acc, fq, src_pol(c, d * (DT(1.0f) / L)), DT(1.0f) / L, mk_len(L, Lh));
         return;
     }
-    v3t<D8> ni, nj;
-    D8 di, dj;
-    face_plane<D8>(c, i, &ni, &di);
-    v3t<D8> S1 = mirror_pt(S, ni, di);
+    v3t<DT> ni, nj;
+    DT di, dj;
+    face_plane<DT>(c, i, &ni, &di);
+    v3t<DT> S1 = mirror_pt(S, ni, di);
     if (order == 1) {
-        D8 d1 = dot3(ni, S1) - di, dP = dot3(ni, P) - di;
-        v3t<D8> Q = S1 + (P - S1) * (d1 / (d1 - dP));
-        D8 L = norm3(Q - S) + norm3(P - Q);
+        DT d1 = dot3(ni, S1) - di, dP = dot3(ni, P) - di;
+        v3t<DT> Q = S1 + (P - S1) * (d1 / (d1 - dP));
+        DT L = norm3(Q - S) + norm3(P - Q);
         if (dielectric(c, i)) {
-            const v3t<D8> s1 = unit3(Q - S), e0 = src_pol(c, s1);
-            cpx<D8> E[3] = {mkc<D8>(e0.x, D8(0.0)), mkc<D8>(e0.y, D8(0.0)), mkc<D8>(e0.z, D8(0.0))};
+            const v3t<DT> s1 = unit3(Q - S), e0 = src_pol(c, s1);
+            cpx<DT> E[3] = {mkc<DT>(e0.x, DT(0.0f)), mkc<DT>(e0.y, DT(0.0f)), mkc<DT>(e0.z, DT(0.0f))};
             reflect_face(c, i, E, s1, unit3(P - Q));
-            add_ray_cx(acc, fq, E, D8(1.0) / L, L);
+            add_ray_cx(acc, fq, E, DT(1.0f) / L, mk_len(L, Lh));
         } else {
-            add_ray(acc, fq, pec_mirror(src_pol(c, unit3(Q - S)), ni), D8(1.0) / L, L);
+            add_ray(acc, fq, pec_mirror(src_pol(c, unit3(Q - S)), ni), DT(1.0f) / L, mk_len(L, Lh));
         }
         return;
     }
-    face_plane<D8>(c, j, &nj, &dj);
-    v3t<D8> S2 = mirror_pt(S1, nj, dj);
-    D8 d2 = dot3(nj, S2) - dj, dP = dot3(nj, P) - dj;
-    v3t<D8> Q2 = S2 + (P - S2) * (d2 / (d2 - dP));
-    D8 e1 = dot3(ni, S1) - di, eq = dot3(ni, Q2) - di;
-    v3t<D8> Q1 = S1 + (Q2 - S1) * (e1 / (e1 - eq));
-    D8 L = norm3(Q1 - S) + norm3(Q2 - Q1) + norm3(P - Q2);
+    face_plane<DT>(c, j, &nj, &dj);
+    v3t<DT> S2 = mirror_pt(S1, nj, dj);
+    DT d2 = dot3(nj, S2) - dj, dP = dot3(nj, P) - dj;
+    v3t<DT> Q2 = S2 + (P - S2) * (d2 / (d2 - dP));
+    DT e1 = dot3(ni, S1) - di, eq = dot3(ni, Q2) - di;
+    v3t<DT> Q1 = S1 + (Q2 - S1) * (e1 / (e1 - eq));
+    DT L = norm3(Q1 - S) + norm3(Q2 - Q1) + norm3(P - Q2);
     if (dielectric(c, i) || dielectric(c, j)) {
-        const v3t<D8> s1 = unit3(Q1 - S), s2 = unit3(Q2 - Q1), e0 = src_pol(c, s1);
-        cpx<D8> E[3] = {mkc<D8>(e0.x, D8(0.0)), mkc<D8>(e0.y, D8(0.0)), mkc<D8>(e0.z, D8(0.0))};
+        const v3t<DT> s1 = unit3(Q1 - S), s2 = unit3(Q2 - Q1), e0 = src_pol(c, s1);
+        cpx<DT> E[3] = {mkc<DT>(e0.x, DT(0.0f)), mkc<DT>(e0.y, DT(0.0f)), mkc<DT>(e0.z, DT(0.0f))};
         reflect_face(c, i, E, s1, s2);
         reflect_face(c, j, E, s2, unit3(P - Q2));
-        add_ray_cx(acc, fq, E, D8(1.0) / L, L);
+        add_ray_cx(acc, fq, E, DT(1.0f) / L, mk_len(L, Lh));
     } else {
-        add_ray(acc, fq, pec_mirror(pec_mirror(src_pol(c, unit3(Q1 - S)), ni), nj), D8(1.0) / L, L);
+        add_ray(acc, fq, pec_mirror(pec_mirror(src_pol(c, unit3(Q1 - S)), ni), nj), DT(1.0f) / L, mk_len(L, Lh));
     }
 }
 
-// order-3 candidate path (faces fs, the candidate list's sequence): the
+// order-3 candidate path (faces fs, the candidate list's sequence q): the
 // images by mirroring the dual-number source, the points backwards from P
-__device__ __noinline__ void adj_seq3(const Ctx &c, int4 sq, v3t<D8> S, v3t<D8> P, const FreqC &fq, AccAdj &acc) {
-    v3t<D8> ni, nj, nk;
-    D8 di, dj, dk;
-    face_plane<D8>(c, sq.x, &ni, &di);
-    face_plane<D8>(c, sq.y, &nj, &dj);
-    face_plane<D8>(c, sq.z, &nk, &dk);
-    const v3t<D8> S1 = mirror_pt(S, ni, di);
-    const v3t<D8> S2 = mirror_pt(S1, nj, dj);
-    const v3t<D8> S3 = mirror_pt(S2, nk, dk);
-    const D8 e3 = dot3(nk, S3) - dk, p3 = dot3(nk, P) - dk;
-    const v3t<D8> Q3 = S3 + (P - S3) * (e3 / (e3 - p3));
-    const D8 e2 = dot3(nj, S2) - dj, p2 = dot3(nj, Q3) - dj;
-    const v3t<D8> Q2 = S2 + (Q3 - S2) * (e2 / (e2 - p2));
-    const D8 e1 = dot3(ni, S1) - di, p1 = dot3(ni, Q2) - di;
-    const v3t<D8> Q1 = S1 + (Q2 - S1) * (e1 / (e1 - p1));
-    const D8 L = norm3(Q1 - S) + norm3(Q2 - Q1) + norm3(Q3 - Q2) + norm3(P - Q3);
-    const v3t<D8> s1 = unit3(Q1 - S), s2 = unit3(Q2 - Q1), s3 = unit3(Q3 - Q2), s4 = unit3(P - Q3);
-    const v3t<D8> e0 = src_pol(c, s1);
-    cpx<D8> E[3] = {mkc<D8>(e0.x, D8(0.0)), mkc<D8>(e0.y, D8(0.0)), mkc<D8>(e0.z, D8(0.0))};
+template <typename DT>
+__device__ __noinline__ void adj_seq3(const Ctx &c, int q, int4 sq, v3t<DT> S, v3t<DT> P, const FreqC &fq,
+                                      AccAdj &acc) {
+    typedef decltype(DT().v) SC;
+    v3t<DT> ni, nj, nk;
+    DT di, dj, dk;
+    face_plane<DT>(c, sq.x, &ni, &di);
+    face_plane<DT>(c, sq.y, &nj, &dj);
+    face_plane<DT>(c, sq.z, &nk, &dk);
+    const v3t<DT> S1 = mirror_pt(S, ni, di);
+    const v3t<DT> S2 = mirror_pt(S1, nj, dj);
+    const v3t<DT> S3 = mirror_pt(S2, nk, dk);
+    const DT e3 = dot3(nk, S3) - dk, p3 = dot3(nk, P) - dk;
+    const v3t<DT> Q3 = S3 + (P - S3) * (e3 / (e3 - p3));
+    const DT e2 = dot3(nj, S2) - dj, p2 = dot3(nj, Q3) - dj;
+    const v3t<DT> Q2 = S2 + (Q3 - S2) * (e2 / (e2 - p2));
+    const DT e1 = dot3(ni, S1) - di, p1 = dot3(ni, Q2) - di;
+    const v3t<DT> Q1 = S1 + (Q2 - S1) * (e1 / (e1 - p1));
+    const DT L = norm3(Q1 - S) + norm3(Q2 - Q1) + norm3(Q3 - Q2) + norm3(P - Q3);
+    const v3t<DT> s1 = unit3(Q1 - S), s2 = unit3(Q2 - Q1), s3 = unit3(Q3 - Q2), s4 = unit3(P - Q3);
+    const v3t<DT> e0 = src_pol(c, s1);
+    cpx<DT> E[3] = {mkc<DT>(e0.x, DT(0.0f)), mkc<DT>(e0.y, DT(0.0f)), mkc<DT>(e0.z, DT(0.0f))};
     reflect_face(c, sq.x, E, s1, s2);
     reflect_face(c, sq.y, E, s2, s3);
     reflect_face(c, sq.z, E, s3, s4);
-    add_ray_cx(acc, fq, E, D8(1.0) / L, L);
+    dfl Lh = {0.0f, 0.0f};
+    if constexpr (sizeof(SC) == 4) Lh = df_dist_df(c.cimg[6 * q + 4], c.cimg[6 * q + 5], vals(P));
+    add_ray_cx(acc, fq, E, DT(1.0f) / L, mk_len(L, Lh));
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -3446,27 +3673,30 @@ __device__ __forceinline__ double warp_sum(double v) {
 // One warp per receiver (persistent, from a queue), its lanes over the
 // receiver's listed paths.  Body gradients by atomics per path; transmitter
 // and frequency gradients summed over the warp first.
+template <typename DT>
 __global__ void __launch_bounds__(128) k_adjoint(DevScene S, const float *__restrict__ rx, int n_rx,
                                                  const uint64_t *__restrict__ codes,
                                                  const int32_t *__restrict__ counts, int cap,
                                                  const float *__restrict__ gE, double *g_body, double *g_tx,
                                                  double *g_f, unsigned long long *queue) {
+    typedef decltype(DT().v) SC;
     Ctx c;
     c.tri = S.tri; c.tri_aux = S.tri_alt; c.face32 = S.face32; c.face64 = S.face64;
-    c.face_rng = S.face_rng; c.face_tris = S.face_tris; c.body = S.body;
+    c.face_rng = S.face_rng; c.face_tris = S.face_tris; c.face_box = S.face_box; c.body = S.body;
     c.n_tri = S.n_tri; c.n_face = S.n_face; c.n_body = S.n_body;
     c.band = 0.0f;
     c.S = mk3(S.tx[0], S.tx[1], S.tx[2]);
     c.pol = mk3(S.pol[0], S.pol[1], S.pol[2]);
-    c.fock = nullptr; c.res = nullptr; c.weid = nullptr; c.weid_L = S.weid_L;
+    c.fock = S.fock32; c.res = S.res32; c.weid = S.weid; c.weid_L = S.weid_L;
     c.fock64 = S.fock64; c.res64 = S.res64; c.weid64 = S.weid64;
-    c.img = S.img; c.txb = S.txb; c.occ_src = nullptr; c.occ_w = 0; c.face_mat = S.face_mat;
+    c.img = S.img; c.img_pairs = S.img_pairs; c.txb = S.txb; c.occ_src = nullptr; c.occ_w = 0;
+    c.face_mat = S.face_mat;
     c.txw = S.txw; c.bvh = S.bvh; c.bvh_tri = S.bvh_tri; c.bvh_top = nullptr; c.bvh_top_n = 0;
     c.cand = S.cand; c.cimg = S.cimg;
     c.n_cand = S.cand ? (S.n_cand_dev ? *S.n_cand_dev : S.n_cand) : 0;
     const int lane = threadIdx.x & 31;
     const int nch = (S.n_f + NFC - 1) / NFC;
-    const v3t<D8> Sd = mk3<D8>(dvar(c.S.x, DS_SX), dvar(c.S.y, DS_SY), dvar(c.S.z, DS_SZ));
+    const v3t<DT> Sd = mk3<DT>(dvar_t<SC>(c.S.x, DS_SX), dvar_t<SC>(c.S.y, DS_SY), dvar_t<SC>(c.S.z, DS_SZ));
     double gtx[3] = {0.0, 0.0, 0.0};
     for (;;) {
         unsigned long long q = 0;
@@ -3475,7 +3705,7 @@ __global__ void __launch_bounds__(128) k_adjoint(DevScene S, const float *__rest
         if (q >= (unsigned long long)n_rx) break;
         const int r = (int)q;
         const int np = min(counts[r], cap);
-        const v3t<D8> Pd = mk3<D8>(rx[r], rx[n_rx + r], rx[2 * n_rx + r]);
+        const v3t<DT> Pd = mk3<DT>(DT(SC(rx[r])), DT(SC(rx[n_rx + r])), DT(SC(rx[2 * n_rx + r])));
         for (int j0 = 0; j0 < np; j0 += 32) {
             const int jj = j0 + lane;
             for (int ch = 0; ch < nch; ++ch) {
@@ -3489,15 +3719,26 @@ __global__ void __launch_bounds__(128) k_adjoint(DevScene S, const float *__rest
                     const uint64_t code = codes[(size_t)r * cap + jj];
                     const int type = (int)(code >> 56), id1 = (int)((code >> 28) & 0xFFFFFFFu),
                               id2 = (int)(code & 0xFFFFFFFu);
-                    if (type == PT_LOS) adj_planar(c, 0, -1, -1, Sd, Pd, fq, acc);
-                    else if (type == PT_R1) adj_planar(c, 1, id1, -1, Sd, Pd, fq, acc);
-                    else if (type == PT_R2) adj_planar(c, 2, id1, id2, Sd, Pd, fq, acc);
-                    else if (type == PT_R3 && c.cand && id1 < c.n_cand) adj_seq3(c, c.cand[id1], Sd, Pd, fq, acc);
-                    else if (type == PT_RB) { adj_rb(c, id1, Sd, Pd, fq, acc); body = id1; }
+                    if (type == PT_LOS) adj_planar<DT>(c, 0, -1, -1, Sd, Pd, fq, acc);
+                    else if (type == PT_R1) adj_planar<DT>(c, 1, id1, -1, Sd, Pd, fq, acc);
+                    else if (type == PT_R2) adj_planar<DT>(c, 2, id1, id2, Sd, Pd, fq, acc);
+                    else if (type == PT_R3 && c.cand && id1 < c.n_cand)
+                        adj_seq3<DT>(c, id1, c.cand[id1], Sd, Pd, fq, acc);
+                    else if (type == PT_RB) {
+                        // reflection off a body: FP64 duals in both precisions (the
+                        // FP32 chain through the specular point left errors of ~1e-3
+                        // of the gradient on the test scenes)
+                        const v3t<D8> S64 = mk3<D8>(dvar(c.S.x, DS_SX), dvar(c.S.y, DS_SY), dvar(c.S.z, DS_SZ));
+                        const v3t<D8> P64 = mk3<D8>(D8((double)rx[r]), D8((double)rx[n_rx + r]),
+                                                    D8((double)rx[2 * n_rx + r]));
+                        adj_rb<D8>(c, id1, S64, P64, fq, acc);
+                        body = id1;
+                    }
                     else if (type == PT_CP || type == PT_CM) {
-                        if (adj_creep(c, id1, type == PT_CM, id2, Sd, Pd, fq, S.enable, acc)) body = id1;
+                        if (adj_creep<DT>(c, id1, type == PT_CM, id2, Sd, Pd, fq, S.enable, acc)) body = id1;
                     } else if (type == PT_WCP || type == PT_WCM) {
-                        if (adj_creep(c, id1, type == PT_WCM, id2 & 15, Sd, Pd, fq, S.enable, acc, id2 >> 4)) body = id1;
+                        if (adj_creep<DT>(c, id1, type == PT_WCM, id2 & 15, Sd, Pd, fq, S.enable, acc, id2 >> 4))
+                            body = id1;
                     }
                 }
                 if (body >= 0)
@@ -3519,7 +3760,7 @@ __global__ void __launch_bounds__(128) k_adjoint(DevScene S, const float *__rest
 
 int launch_adjoint(const DevScene &S, const float *rx_soa, int n_rx, const uint64_t *codes, const int32_t *counts,
                    int cap, const float *grad_e, double *g_body, double *g_tx, double *g_f,
-                   unsigned long long *queue, cudaStream_t st) {
+                   unsigned long long *queue, int precision, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess && S.n_body > 0) e = cudaMemsetAsync(g_body, 0, sizeof(double) * 4 * S.n_body, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(g_tx, 0, sizeof(double) * 3, st);
@@ -3530,7 +3771,10 @@ int launch_adjoint(const DevScene &S, const float *rx_soa, int n_rx, const uint6
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         long long need = ((long long)n_rx + 3) / 4;
         int grid = (int)(need < 4LL * nsm ? need : 4LL * nsm);
-        k_adjoint<<<grid, 128, 0, st>>>(S, rx_soa, n_rx, codes, counts, cap, grad_e, g_body, g_tx, g_f, queue);
+        if (precision == RT_PREC_FP64)
+            k_adjoint<D8><<<grid, 128, 0, st>>>(S, rx_soa, n_rx, codes, counts, cap, grad_e, g_body, g_tx, g_f, queue);
+        else
+            k_adjoint<F8><<<grid, 128, 0, st>>>(S, rx_soa, n_rx, codes, counts, cap, grad_e, g_body, g_tx, g_f, queue);
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) {

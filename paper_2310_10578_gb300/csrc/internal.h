@@ -74,6 +74,7 @@ struct DevScene {
     float weid_L;
     const float4 *img;         // [n_face + n_face^2][2]: source images (hi, lo) as double-float:
                                // [f] mirror of Tx in face f; [n_face + i n_face + j] in i then j
+    int img_pairs;             // img holds the pair slots (faces <= RT_MAX_ENUM_FACES)
     const float4 *face_mat;    // [n_face]: (dielectric ? 1 : 0, eps', eps'', 0), eps_r = eps' - j eps''; or
                                // nullptr when every face is PEC
     const float4 *txb;         // [n_body][2] per transmitter, FP64-computed: (u, |S - c|), (beta_s, sqrt(|S-c|^2 - a^2) hi, lo,
@@ -172,10 +173,11 @@ int launch_eval_batch(const DevScene &S, const FrameDev *frames_dev, const Frame
 // the n_rx receivers' listed paths (codes/counts/cap as rt_paths wrote
 // them), the sums of dLoss/dE (grad_e, as the fields) times each path's
 // field derivative: g_body [n_body][4] (centre x, y, z, radius), g_tx [3],
-// g_f [n_f]; all zeroed first.  queue: one device counter.
+// g_f [n_f]; all zeroed first.  queue: one device counter.  precision:
+// RT_PREC_FP32 (FP32 dual numbers) or RT_PREC_FP64.
 int launch_adjoint(const DevScene &S, const float *rx_soa, int n_rx, const uint64_t *codes, const int32_t *counts,
                    int cap, const float *grad_e, double *g_body, double *g_tx, double *g_f,
-                   unsigned long long *queue, cudaStream_t st);
+                   unsigned long long *queue, int precision, cudaStream_t st);
 
 // Spatial ordering of a batch's receivers (rx_order.cu): a counting sort per
 // frame on the RX_GRID x RX_GRID cells (Morton order) of the rectangle grid

@@ -1,7 +1,8 @@
 """The adjoint (rt_backward and the autograd.Function over it) against the
 FP64 oracle: gradients of a loss through the fields with respect to body
-centres and radii, the transmitter position and the frequencies, with the
-visibility of the forward path list held fixed (tests/adjoint_ref.py:
+centres and radii, the transmitter position and the frequencies (FP32 dual
+numbers by default; FP64 ones where a test says so), with the visibility of
+the forward path list held fixed (tests/adjoint_ref.py:
 central differences of the oracle's per-path fields, h = 1e-5 m).
 
 Tolerance: 1e-3 relative, where the relative error of a gradient that is a
@@ -45,11 +46,12 @@ def _close(got, ref, absum, what):
     assert abs(got - ref) <= tol, "%s: gpu %.9e ref %.9e (|contributions| %.3e)" % (what, got, ref, absum)
 
 
-def _forward(creep, sc, cap=256):
+def _forward(creep, sc, cap=256, precision=None):
     S = creep.Scene.from_scene(sc)
     rx = torch.tensor(sc.rx_soa(), device="cuda")
     opts = creep.options(max_order=sc.max_order, max_encirclements=getattr(sc, "max_enc", 0),
-                         enable=creep.RT_EN_ALL | (creep.RT_EN_WALL_CREEP if getattr(sc, "wall_creep", False) else 0))
+                         enable=creep.RT_EN_ALL | (creep.RT_EN_WALL_CREEP if getattr(sc, "wall_creep", False) else 0),
+                         precision=creep.RT_PREC_FP32 if precision is None else precision)
     E = S.evaluate(rx, opts=opts)
     codes, counts, _ = S.paths(rx, cap=cap, opts=opts)
     torch.cuda.synchronize()
@@ -59,8 +61,8 @@ def _forward(creep, sc, cap=256):
     return S, rx, opts, E, codes, counts, lists
 
 
-def _check(creep, sc, bodies, seed, cap=256, tx=True, freqs=True, keep=None):
-    S, rx, opts, E, codes, counts, lists = _forward(creep, sc, cap)
+def _check(creep, sc, bodies, seed, cap=256, tx=True, freqs=True, keep=None, precision=None):
+    S, rx, opts, E, codes, counts, lists = _forward(creep, sc, cap, precision)
     if keep is not None:
         # the gradient through the listed paths that pass keep(code) only
         lists = [[c for c in cs if keep(c)] for cs in lists]
@@ -91,10 +93,13 @@ def _check(creep, sc, bodies, seed, cap=256, tx=True, freqs=True, keep=None):
     return n_checked, gb
 
 
-def test_adjoint_room_small(creep, oracle_mod):
-    # 12 cylinders, 24 x 20 receivers, two frequencies; every body's gradient
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_adjoint_room_small(creep, oracle_mod, precision):
+    # 12 cylinders, 24 x 20 receivers, two frequencies; every body's gradient,
+    # with FP32 dual numbers (the default) and with FP64 ones
     sc = _jitter(scenes.room(n_cyl=12, nx=24, ny=20, freqs=(2.4e9, 28e9), seed=7), 11)
-    n_checked, _ = _check(creep, sc, bodies=range(12), seed=1)
+    prec = creep.RT_PREC_FP64 if precision == "fp64" else creep.RT_PREC_FP32
+    n_checked, _ = _check(creep, sc, bodies=range(12), seed=1, precision=prec)
     assert n_checked >= 30
 
 
