@@ -237,6 +237,24 @@ int rt_candidates_device(rt_scene *scene, int n_rays, int max_order, void *strea
  */
 int rt_get_candidates(rt_scene *scene, int32_t *seq, int cap, int *n_out);
 
+/*
+ * Received power (the paper's maps and cuts are received power in dBm for
+ * a 40 dBm omnidirectional transmitter, Sec. IV).
+ * rt_set_tx_power: the transmitter's power in dBm (default 0 dBm).
+ * rt_power_dbm: from a field e_out of rt_evaluate (device float
+ *   [n_f][3][n_rx][2], normalised to |E| = 1/R in free space) the received
+ *   power of an isotropic antenna, device float p_out [n_f][n_rx]:
+ *     P_r = P_t + 20 log10(lambda / (4 pi)) + 20 log10 |E . p|
+ *   (Friis), p = rx_pol (host float[3], normalised here) or, with rx_pol
+ *   NULL, |E| (the power summed over polarisations); -inf where the field
+ *   is zero.  Asynchronous on `stream`.  Errors: RT_ERR_ARG (NULL buffer,
+ *   zero or non-finite polarisation), RT_ERR_STATE (no frequencies),
+ *   RT_ERR_CUDA.
+ */
+int rt_set_tx_power(rt_scene *scene, float power_dbm);
+int rt_power_dbm(rt_scene *scene, const float *e_out, int n_rx, const float rx_pol[3], float *p_out,
+                 void *stream);
+
 /* Frequencies (host double[n_f], Hz, > 0), 1 <= n_f <= RT_MAX_FREQS. */
 int rt_set_freqs(rt_scene *scene, const double *f_hz, int n_f);
 

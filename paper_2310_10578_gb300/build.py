@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libcreep.so")
-SOURCES = ["abi.cu", "eval_fields.cu", "fock_table.cu", "rx_order.cu", "peaks.cu", "bvh.cu", "candidates.cu"]
+SOURCES = ["abi.cu", "eval_fields.cu", "fock_table.cu", "rx_order.cu", "peaks.cu", "bvh.cu", "candidates.cu", "power.cu"]
 # per-file flags: the device ray launch rounds every FP64 operation as the
 # host launch does (no fused multiply-add), so both trace identical rays
 FILE_FLAGS = {"candidates.cu": ["-fmad=false"]}

@@ -28,7 +28,8 @@ EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "
            "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats", "rt_backward", "rt_alu_peaks",
            "rt_evaluate_with_paths", "rt_batch_set_shape", "rt_batch_get_shape", "rt_batch_tune",
            "rt_set_shape", "rt_get_shape", "rt_tune", "rt_set_face_materials", "rt_candidates",
-           "rt_set_candidates", "rt_candidates_mesh", "rt_candidates_device", "rt_get_candidates")
+           "rt_set_candidates", "rt_candidates_mesh", "rt_candidates_device", "rt_get_candidates",
+           "rt_set_tx_power", "rt_power_dbm")
 RT_DEV_CAND_SLOTS = 16384
 RT_NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -102,6 +103,8 @@ def load(build_if_missing=True):
     lib.rt_candidates_mesh.argtypes = [P, P, I, P, I, I, P, I, ctypes.POINTER(I)]
     lib.rt_candidates_device.argtypes = [P, I, I, P]
     lib.rt_get_candidates.argtypes = [P, P, I, ctypes.POINTER(I)]
+    lib.rt_set_tx_power.argtypes = [P, ctypes.c_float]
+    lib.rt_power_dbm.argtypes = [P, P, I, P, P, P]
     _lib = lib
     return lib
 
@@ -222,6 +225,22 @@ class Scene:
         tx = np.ascontiguousarray(np.asarray(tx, dtype=np.float32).reshape(3))
         pol = np.ascontiguousarray(np.asarray(pol, dtype=np.float32).reshape(3))
         _check(_lib.rt_set_tx(self._h, _ptr(tx), _ptr(pol)))
+
+    def set_tx_power(self, power_dbm):
+        """The transmitter's power in dBm (rt_set_tx_power)."""
+        _check(_lib.rt_set_tx_power(self._h, float(power_dbm)))
+
+    def power_dbm(self, E, rx_pol=None, out=None, stream=None):
+        """Received power in dBm [n_f, n] from fields E [n_f, 3, n, 2]
+        (rt_power_dbm); rx_pol: the receiving antenna's polarisation, or
+        None for the power over all polarisations."""
+        import torch
+        n = E.shape[2]
+        if out is None:
+            out = torch.empty((E.shape[0], n), dtype=torch.float32, device=E.device)
+        pol = None if rx_pol is None else np.ascontiguousarray(np.asarray(rx_pol, dtype=np.float32).reshape(3))
+        _check(_lib.rt_power_dbm(self._h, _ptr(E.contiguous()), n, _ptr(pol), _ptr(out), _stream_handle(stream)))
+        return out
 
     def set_freqs(self, freqs):
         f = np.ascontiguousarray(np.asarray(freqs, dtype=np.float64).reshape(-1))

@@ -148,6 +148,10 @@ struct rt_scene {
     float4 *d_lbvh = nullptr;           // the BVH for the launch when the scene has too few triangles for d_bvh
     int *d_lbvh_tri = nullptr;
     cudaStream_t cand_stream = nullptr;
+    // received power (rt_set_tx_power, rt_power_dbm): the transmitter's power
+    // and per frequency P_t + 20 log10(lambda / 4 pi) on the device
+    float power_dbm = 0.0f;
+    float *d_pc0 = nullptr;             // [RT_MAX_FREQS]
     unsigned long long *d_esc = nullptr;   // [CTR_N]: FP64-decided candidates, then one work queue per launch
     DevTable *table = nullptr;
     // state
@@ -195,7 +199,7 @@ static void free_scene(rt_scene *s) {
     cudaFree(s->d_txw); cudaFree(s->d_bvh); cudaFree(s->d_bvh_tri); cudaFree(s->d_cand); cudaFree(s->d_cimg);
     cudaFree(s->d_face_mat); cudaFree(s->d_face_box);
     cudaFree(s->dcb.dir); cudaFree(s->dcb.fn); cudaFree(s->dcb.keys); cudaFree(s->dcb.cand); cudaFree(s->dcb.cimg);
-    cudaFree(s->dcb.n_cand); cudaFree(s->d_lbvh); cudaFree(s->d_lbvh_tri);
+    cudaFree(s->dcb.n_cand); cudaFree(s->d_lbvh); cudaFree(s->d_lbvh_tri); cudaFree(s->d_pc0);
 }
 
 // distance from point p to the solid of body b (0 if inside)
@@ -737,6 +741,42 @@ int rt_get_candidates(rt_scene *s, int32_t *seq, int cap, int *n_out) {
     return RT_OK;
 }
 
+// P_t + 20 log10(lambda / 4 pi) per frequency, to the device
+static int upload_power(rt_scene *s) {
+    if (!s->f_set) return RT_OK;
+    std::vector<float> c0(s->freqs.size());
+    for (size_t f = 0; f < c0.size(); ++f)
+        c0[f] = (float)((double)s->power_dbm + 20.0 * log10(299792458.0 / s->freqs[f] / (4.0 * M_PI)));
+    if (!s->d_pc0) CK(cudaMalloc(&s->d_pc0, sizeof(float) * RT_MAX_FREQS));
+    CK(cudaMemcpy(s->d_pc0, c0.data(), sizeof(float) * c0.size(), cudaMemcpyHostToDevice));
+    return RT_OK;
+}
+
+int rt_set_tx_power(rt_scene *s, float power_dbm) {
+    if (!s) return fail(RT_ERR_ARG, "rt_set_tx_power: NULL scene");
+    if (!fin32(power_dbm)) return fail(RT_ERR_ARG, "rt_set_tx_power: non-finite power");
+    s->power_dbm = power_dbm;
+    return upload_power(s);
+}
+
+int rt_power_dbm(rt_scene *s, const float *e_out, int n_rx, const float rx_pol[3], float *p_out, void *stream) {
+    if (!s) return fail(RT_ERR_ARG, "rt_power_dbm: NULL scene");
+    if (n_rx < 0) return fail(RT_ERR_ARG, "rt_power_dbm: n_rx < 0");
+    if (!s->f_set) return fail(RT_ERR_STATE, "rt_power_dbm: frequencies not set");
+    if (n_rx > 0 && (!e_out || !p_out)) return fail(RT_ERR_ARG, "rt_power_dbm: NULL buffer");
+    if (rx_pol) {
+        for (int k = 0; k < 3; ++k)
+            if (!fin32(rx_pol[k])) return fail(RT_ERR_ARG, "rt_power_dbm: non-finite polarisation");
+        if (rx_pol[0] == 0.f && rx_pol[1] == 0.f && rx_pol[2] == 0.f)
+            return fail(RT_ERR_ARG, "rt_power_dbm: zero polarisation");
+    }
+    if (!s->d_pc0) {
+        int rc = upload_power(s);
+        if (rc != RT_OK) return rc;
+    }
+    return launch_power_dbm(e_out, (int)s->freqs.size(), n_rx, s->d_pc0, rx_pol, p_out, (cudaStream_t)stream);
+}
+
 int rt_set_face_materials(rt_scene *s, const float *mat, int n_face) {
     if (!s) return fail(RT_ERR_ARG, "rt_set_face_materials: NULL scene");
     if (!mat) {
@@ -771,6 +811,7 @@ int rt_set_freqs(rt_scene *s, const double *f_hz, int n_f) {
     int nch = (n_f + NFC - 1) / NFC;
     CK(cudaMemcpy(s->d_fqc, fq.data(), sizeof(FreqC) * nch, cudaMemcpyHostToDevice));
     s->f_set = true;
+    if (s->d_pc0) return upload_power(s);
     return RT_OK;
 }
 

@@ -179,6 +179,12 @@ int launch_adjoint(const DevScene &S, const float *rx_soa, int n_rx, const uint6
                    int cap, const float *grad_e, double *g_body, double *g_tx, double *g_f,
                    unsigned long long *queue, int precision, cudaStream_t st);
 
+// Received power in dBm (power.cu): p_out [n_f][n_rx] from the field
+// e_out [n_f][3][n_rx][2]; c0_dev [n_f] device floats P_t + 20 log10(lambda /
+// 4 pi); pol host float[3] (normalised here) or nullptr for |E|.
+int launch_power_dbm(const float *e_out, int n_f, int n_rx, const float *c0_dev, const float pol[3], float *p_out,
+                     cudaStream_t st);
+
 // Spatial ordering of a batch's receivers (rx_order.cu): a counting sort per
 // frame on the RX_GRID x RX_GRID cells (Morton order) of the rectangle grid
 // = (x0, y0, cells per metre in x, in y).  Scratch: cnt [n_frames][RX_CELLS],
