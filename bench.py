@@ -168,11 +168,10 @@ def _kernel_source_hash():
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-def _profiled_traffic():
-    """DRAM bytes of one evaluation (the three class kernels) from the
-    committed ncu summary, if it was taken on the current kernel source; else
-    None."""
-    p = os.path.join(ROOT, "profiles", "k_eval_room20_traffic.txt")
+def _profiled(name="k_eval_room20_traffic.txt", key="dram_bytes_per_evaluation_full_workload"):
+    """A per-evaluation counter from a committed ncu summary under profiles/,
+    if it was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(p):
         return None
     kv = {}
@@ -184,9 +183,24 @@ def _profiled_traffic():
     if kv.get("eval_fields.cu sha256[:16]") != _kernel_source_hash():
         return None
     try:
-        return float(kv["dram_bytes_per_evaluation_full_workload"])
+        return float(kv[key])
     except (KeyError, ValueError):
         return None
+
+
+def _profiled_traffic():
+    """DRAM bytes of one evaluation of the room (the three class kernels)."""
+    return _profiled()
+
+
+def hbm_peak():
+    """The measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json),
+    else the stated fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"]), "measured: MEASURED_PEAKS.json hbm_gbs (copy bandwidth)"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback: 6.8 TB/s (no MEASURED_PEAKS.json)"
 
 
 # ---------------------------------------------------------------- reference arm
@@ -744,6 +758,24 @@ def office_large(args, creep, dev, flush):
            "fp64_escalated_candidates_per_tx": esc,
            "gpu_launches_per_step": (S.stats()["kernel_launches"] + 2) * len(sc.txs), "roofline": None,
            "l2": "flushed between timed steps (256 MiB write)"}
+    # roofline of the traversal-bound evaluation (transmitter 0): DRAM and L2
+    # bytes of one evaluation from the committed ncu summary of the same
+    # kernel source, over the evaluation's time in this run
+    dram = _profiled("k_eval_office_traffic.txt")
+    l2b = _profiled("k_eval_office_traffic.txt", "l2_bytes_per_evaluation_full_workload")
+    if dram is not None and (nrx, nry) == (20, 15):
+        t_eval = (step_ms[0] - cand_ms[0]) / 1e3
+        peak, basis = hbm_peak()
+        l2peak = creep.l2_peak()
+        res["roofline"] = {
+            "bound": "hbm", "achieved": dram / t_eval / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": dram / t_eval / 1e9 / peak, "traffic": dram, "peak_basis": basis,
+            "kernel": "evaluation of transmitter 0: k_eval<float, false, 16|2|4> (candidate list, body "
+                      "reflection, creeping), BVH visibility",
+            "l2": {"achieved": l2b / t_eval / 1e9, "peak": l2peak, "unit": "GB/s", "frac": l2b / t_eval / 1e9 / l2peak,
+                   "bytes": l2b, "peak_basis": "measured: L2 read microbenchmark rt_l2_peak in this run"},
+            "note": "the BVH (194k triangles) and the scene stay in the 129 MB L2: DRAM carries the receivers and "
+                    "fields only, the traversal reads the L2"}
     if not args.no_cpu_baseline:
         from oracle import oracle
         sys.path.insert(0, os.path.join(ROOT, "tests"))

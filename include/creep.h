@@ -489,6 +489,16 @@ int rt_backward(rt_scene *scene, const float *rx_soa, int n_rx, const uint64_t *
  */
 int rt_alu_peaks(double *ffma_tflops, double *mufu_gops, void *stream);
 
+/*
+ * rt_l2_peak -- measured L2 read bandwidth of the current device (GB/s), the
+ * denominator of the large-scene traversal's roofline, whose BVH and
+ * triangles stay in the L2 (an engineering addition: the paper has no
+ * counterpart).  Reads a 32 MiB buffer through L2 only, 16 passes, on
+ * `stream`, and synchronises; allocates and frees the buffer.  Errors:
+ * RT_ERR_ARG, RT_ERR_CUDA.
+ */
+int rt_l2_peak(double *l2_gbs, void *stream);
+
 /* Counters of the last rt_evaluate / rt_paths on this scene (synchronises its stream). */
 int rt_get_stats(rt_scene *scene, rt_stats *out);
 

@@ -29,7 +29,7 @@ EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "
            "rt_evaluate_with_paths", "rt_batch_set_shape", "rt_batch_get_shape", "rt_batch_tune",
            "rt_set_shape", "rt_get_shape", "rt_tune", "rt_set_face_materials", "rt_candidates",
            "rt_set_candidates", "rt_candidates_mesh", "rt_candidates_device", "rt_get_candidates",
-           "rt_set_tx_power", "rt_power_dbm")
+           "rt_set_tx_power", "rt_power_dbm", "rt_l2_peak")
 RT_DEV_CAND_SLOTS = 16384
 RT_NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -104,6 +104,7 @@ def load(build_if_missing=True):
     lib.rt_candidates_device.argtypes = [P, I, I, P]
     lib.rt_get_candidates.argtypes = [P, P, I, ctypes.POINTER(I)]
     lib.rt_set_tx_power.argtypes = [P, ctypes.c_float]
+    lib.rt_l2_peak.argtypes = [P, P]
     lib.rt_power_dbm.argtypes = [P, P, I, P, P, P]
     _lib = lib
     return lib
@@ -466,6 +467,14 @@ def alu_peaks(stream=None):
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(lib.rt_alu_peaks(ctypes.byref(a), ctypes.byref(b), _stream_handle(stream)))
     return a.value, b.value
+
+
+def l2_peak(stream=None):
+    """Measured L2 read bandwidth (GB/s) of the current device."""
+    lib = load()
+    a = ctypes.c_double()
+    _check(lib.rt_l2_peak(ctypes.byref(a), _stream_handle(stream)))
+    return a.value
 
 
 def fock_table():
