@@ -781,36 +781,65 @@ __device__ void body_frame(const Ctx &c, int b, v3t<dx> S, v3t<dx> P, dx band, F
     cyl_frame(S, P, dx((double)q0.x), dx((double)q0.y), a, F, band);
 }
 
-// 2-D reflection point psi on the circle of radius a, S = (ds, 0), P = (pu, pv):
-// root of dL/dpsi in (0, gam).  FP32: safeguarded Newton; FP64: bisection to
+// 2-D reflection point on the circle of radius a, S = (ds, 0), P = (pu, pv)
+// with pv >= 0 and gam = the angle of P in [0, pi]: the root psi of dL/dpsi
+// in (0, gam), returned as n = (cos psi, sin psi) with psi.
+//   FP32: safeguarded Newton in x = psi / pi (sincospi needs no argument
+// reduction), with the bracket (lo, hi) for bisection.  For Q = a n, t = a
+// (-sin psi, cos psi):
+//   dL/dpsi   = (Q - S).t / |Q - S| + (Q - P).t / |Q - P|,
+//   d2L/dpsi2 = sum over X = S, P of (X.Q - ((Q - X).t / |Q - X|)^2) / |Q - X|,
+// each term formed from the difference vector Q - X itself (well conditioned
+// for X within microns of the surface).  The start is the bisector of the
+// directions to S and P, psi = gam / 2, moved by the first-order shift of the
+// reflection point towards the nearer end, delta = (a / 2) sin(gam / 2) (1/d_p
+// - 1/d_s) (from expanding dL/dpsi = 0 to first order in a / d).  The
+// iteration stops at a step below 2e-7 psi, or at a Newton step below the
+// rounding noise of dL/dpsi over its slope -- the root's own error estimate
+// *err_est, which no further step could improve on.  FP64: bisection to
 // double resolution.
-__device__ float refl_psi(float a, float ds, float pu, float pv, float gam, float *err_est) {
-    float lo = 0.0f, hi = gam;
+__device__ __forceinline__ float rsqrt1(float x) {      // 1/sqrt(x) with one Newton step on rsqrtf
+    const float y = rsqrtf(x);
+    return y * fmaf(-0.5f * x * y, y, 1.5f);
+}
+__device__ float refl_n32(float a, float ds, float pu, float pv, float gam, float *cs_out, float *sn_out,
+                          float *err_est) {
+    constexpr float EPS8 = 8.0f * 1.2e-7f;       // 8 ulp: the rounding noise of dL/dpsi, relative to gmag
+    constexpr float PI_F = 3.14159265358979f, IPI_F = 0.318309886183791f;
     float gmag = 0.0f, curv = 1.0f;
-    // start at the direction of u_S + u_P
-    float dpn = sqrtf(pu * pu + pv * pv);
-    float psi = atan2f(pv / dpn, 1.0f + pu / dpn);
+    const float ip = rsqrt1(pu * pu + pv * pv);
+    const float bx = 1.0f + pu * ip, by = pv * ip;          // u_S + u_P (bx >= 0)
+    const float s_half = by * rsqrt1(bx * bx + by * by);    // sin(gam / 2)
+    float dl = 0.5f * a * s_half * (ip - 1.0f / ds);
+    dl = fminf(fmaxf(dl, -0.4f * gam), 0.4f * gam);
+    const float xg = gam * IPI_F;
+    float lo = 0.0f, hi = xg;
+    float x = 0.5f * xg + dl * IPI_F;
+    float s, c;
+    sincospif(x, &s, &c);
     for (int it = 0; it < 24; ++it) {
-        float sn, cs;
-        sincosf(psi, &sn, &cs);
-        float qx = a * cs, qy = a * sn, tx = -a * sn, ty = a * cs;
-        float sx = qx - ds, sy = qy, rx = qx - pu, ry = qy - pv;
-        float fs = sqrtf(sx * sx + sy * sy), fr = sqrtf(rx * rx + ry * ry);
-        float gs = (sx * tx + sy * ty) / fs, gr = (rx * tx + ry * ty) / fr;
-        float g = gs + gr;
-        // d2L/dpsi2 = sum (X.Q - f'^2)/f
-        float g2 = (ds * qx - gs * gs) / fs + (pu * qx + pv * qy - gr * gr) / fr;
+        const float qx = a * c, qy = a * s;
+        const float sx = qx - ds, sy = qy, rx = qx - pu, ry = qy - pv;
+        const float ifs = rsqrt1(sx * sx + sy * sy), ifr = rsqrt1(rx * rx + ry * ry);
+        const float gs = (sy * qx - sx * qy) * ifs, gr = (ry * qx - rx * qy) * ifr;    // (Q - X).t / |Q - X|
+        const float g = gs + gr;
+        const float g2 = (ds * qx - gs * gs) * ifs + (pu * qx + pv * qy - gr * gr) * ifr;
         gmag = fabsf(gs) + fabsf(gr) + a;
         curv = g2;
         if (g == 0.0f) break;
-        if (g < 0.0f) lo = psi; else hi = psi;
-        float nx = psi - g / g2;
-        if (!(g2 > 0.0f) || nx < lo || nx > hi) nx = 0.5f * (lo + hi);
-        if (fabsf(nx - psi) <= 2e-7f * fmaxf(fabsf(psi), 1e-3f)) { psi = nx; break; }
-        psi = nx;
+        if (g < 0.0f) lo = x; else hi = x;
+        float nx = x - g / (PI_F * g2);
+        const bool newton = g2 > 0.0f && nx >= lo && nx <= hi;   // (false for a NaN step)
+        if (!newton) nx = 0.5f * (lo + hi);
+        const float step = PI_F * fabsf(nx - x);
+        x = nx;
+        sincospif(x, &s, &c);
+        if (step <= 2e-7f * fmaxf(PI_F * x, 1e-3f) || (newton && step <= EPS8 * gmag / g2)) break;
     }
-    // FP32 root error: rounding noise of dL/dpsi over its slope
-    *err_est = (curv > 0.0f) ? 8.0f * 1.2e-7f * gmag / curv + 2e-7f * fabsf(psi) : 1.0f;
+    const float psi = PI_F * x;
+    *err_est = (curv > 0.0f) ? EPS8 * gmag / curv + 2e-7f * psi : 1.0f;
+    *cs_out = c;
+    *sn_out = s;
     return psi;
 }
 __device__ dx refl_psi(dx a, dx ds, dx pu, dx pv, dx gam) {
@@ -864,15 +893,14 @@ __device__ bool refl_newton64(double A, double Ds, double Pu, double Pv, double 
 
 // Double-float refinement of an FP32 reflection point (near-grazing
 // incidence, where the FP32 root of dL/dpsi is too coarse for cos(theta_i)).
-// At n0 = (c0, s0) = sincos(psi0) normalised exactly (1/|n0| = 1 - delta/2,
+// At n0 = (c0, s0), the FP32 root, normalised exactly (1/|n0| = 1 - delta/2,
 // delta = |n0|^2 - 1 formed exactly), dL/dpsi of the closed form above is
 // evaluated in double-float -- its two terms cancel at the root, which is
 // what limits the FP32 root -- and Newton steps rotate n; the FP32 slope is
 // enough for the step.  Returns false if a step exceeds 1e-4 or the slope is
 // not positive.
-__device__ bool refl_polish_df(float a, float ds, float pu, float pv, float psi0, float *cs_out, float *sn_out) {
-    float c0, s0;
-    sincosf(psi0, &s0, &c0);
+__device__ bool refl_polish_df(float a, float ds, float pu, float pv, float c0, float s0, float *cs_out,
+                               float *sn_out) {
     for (int it = 0; it < 3; ++it) {
         dfl r2 = df_add(two_prod(c0, c0), two_prod(s0, s0));
         float delta = (r2.hi - 1.0f) + r2.lo;
@@ -910,10 +938,8 @@ __device__ bool refl_polish_df(float a, float ds, float pu, float pv, float psi0
 // FP64 refinement of an FP32 reflection point, for the cases the
 // double-float step does not take; FP64 bisection when Newton does not
 // converge.  Returns (cos psi, sin psi) in FP32.
-__device__ __noinline__ void refl_polish(float a, float ds, float pu, float pv, float gam, float psi0,
+__device__ __noinline__ void refl_polish(float a, float ds, float pu, float pv, float gam, float c0f, float s0f,
                                          float *cs_out, float *sn_out) {
-    float c0f, s0f;
-    sincosf(psi0, &s0f, &c0f);
     double c = c0f, s = s0f;
     double r = 1.0 / sqrt(c * c + s * s);
     c *= r; s *= r;
@@ -929,10 +955,8 @@ __device__ __noinline__ void refl_polish(float a, float ds, float pu, float pv, 
 // ~1e-15 of the bisection root of the definition); bisection when Newton
 // does not converge.
 __device__ __noinline__ void refl_root(dx a, dx ds, dx pu, dx pv, dx gam, dx *cs_out, dx *sn_out) {
-    float err;
-    float psi0 = refl_psi(to_float(a), to_float(ds), to_float(pu), to_float(pv), to_float(gam), &err);
-    float c0f, s0f;
-    sincosf(psi0, &s0f, &c0f);
+    float err, c0f, s0f;
+    refl_n32(to_float(a), to_float(ds), to_float(pu), to_float(pv), to_float(gam), &c0f, &s0f, &err);
     double c = c0f, s = s0f;
     double r = 1.0 / sqrt(c * c + s * s);
     c *= r; s *= r;
@@ -983,15 +1007,14 @@ __device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Fr
     T sn, cs;
     if constexpr (sizeof(T) == 4) {
         float psi_err = 0.0f;
-        float psi = refl_psi(a, F.ds, F.pu, F.pv, F.gam, &psi_err);
-        SinCos(psi, &sn, &cs);
+        refl_n32(a, F.ds, F.pu, F.pv, F.gam, &cs, &sn, &psi_err);
         // incidence cosine (2-D, horizontal for cylinders): refine the root in FP64
         // when its FP32 error would exceed 1e-5 of cos(theta_i) (near grazing),
         // the amplitude budget of the FP32 path
         float c2 = (F.ds * cs - a) / sqrtf((a * cs - F.ds) * (a * cs - F.ds) + a * a * sn * sn);
         if (psi_err > 1e-5f * fmaxf(c2, 0.0f)) {
-            if (!refl_polish_df(a, F.ds, F.pu, F.pv, psi, &cs, &sn))
-                refl_polish(a, F.ds, F.pu, F.pv, F.gam, psi, &cs, &sn);
+            if (!refl_polish_df(a, F.ds, F.pu, F.pv, cs, sn, &cs, &sn))
+                refl_polish(a, F.ds, F.pu, F.pv, F.gam, cs, sn, &cs, &sn);
         }
     } else {
         refl_root(a, F.ds, F.pu, F.pv, F.gam, &cs, &sn);
@@ -1067,11 +1090,24 @@ __device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T ba
     // 2 pi a longer per turn; on a sphere the ray crosses the source axis
     // twice per turn (+j each: -1 per turn)
     if (c.enc > 0) dpsi = dpsi + TWO_PI_T * T(c.enc);
-    T psi1 = (dir == 0) ? F.bs : -F.bs;
-    T psi2 = (dir == 0) ? F.gam - F.bp : F.gam + F.bp;
     T s1, c1, s2, c2;
-    SinCos(psi1, &s1, &c1);
-    SinCos(psi2, &s2, &c2);
+    if constexpr (sizeof(T) == 4) {
+        // the attachment and shedding directions psi1 = +-beta_s and psi2 =
+        // gam -+ beta_p in closed form: cos beta_s = a / d_s, sin beta_s =
+        // s' / d_s, (cos gam, sin gam) = (p_u, p_v) / d_p, cos beta_p = a / d_p,
+        // sin beta_p = s'' / d_p (tangent lengths s', s'' from the frame)
+        const float ids = 1.0f / F.ds, idp2 = 1.0f / (F.dp * F.dp);
+        c1 = a * ids;
+        s1 = (dir == 0) ? F.sps * ids : -F.sps * ids;
+        const float pa_u = F.pu * a, pa_v = F.pv * a, qs_u = F.pu * F.sqp, qs_v = F.pv * F.sqp;
+        c2 = ((dir == 0) ? pa_u + qs_v : pa_u - qs_v) * idp2;
+        s2 = ((dir == 0) ? pa_v - qs_u : pa_v + qs_u) * idp2;
+    } else {
+        T psi1 = (dir == 0) ? F.bs : -F.bs;
+        T psi2 = (dir == 0) ? F.gam - F.bp : F.gam + F.bp;
+        SinCos(psi1, &s1, &c1);
+        SinCos(psi2, &s2, &c2);
+    }
     g.n1 = F.u * c1 + F.v * s1;
     g.n2 = F.u * c2 + F.v * s2;
     if (sphere) {
@@ -3357,13 +3393,11 @@ __device__ __forceinline__ void refl_root_val(double a, double ds, double pu, do
     *c0 = cc.v; *s0 = ss.v;
 }
 __device__ __forceinline__ void refl_root_val(float a, float ds, float pu, float pv, float gam, float *c0, float *s0) {
-    float err = 0.0f;
-    const float psi = refl_psi(a, ds, pu, pv, gam, &err);
-    float sn, cs;
-    sincosf(psi, &sn, &cs);
+    float err = 0.0f, sn, cs;
+    refl_n32(a, ds, pu, pv, gam, &cs, &sn, &err);
     const float c2 = (ds * cs - a) / sqrtf((a * cs - ds) * (a * cs - ds) + a * a * sn * sn);
     if (err > 1e-5f * fmaxf(c2, 0.0f)) {
-        if (!refl_polish_df(a, ds, pu, pv, psi, &cs, &sn)) refl_polish(a, ds, pu, pv, gam, psi, &cs, &sn);
+        if (!refl_polish_df(a, ds, pu, pv, cs, sn, &cs, &sn)) refl_polish(a, ds, pu, pv, gam, cs, sn, &cs, &sn);
     }
     *c0 = cs; *s0 = sn;
 }
