@@ -406,15 +406,15 @@ __device__ __forceinline__ int blocked_impl(const Ctx &c, v3t<T> A, v3t<T> B, in
 __device__ __noinline__ int blocked(const Ctx &c, v3t<float> A, v3t<float> B, int sf1, int sf2, int sb, float band) {
     return blocked_impl(c, A, B, sf1, sf2, sb, band);
 }
-// A leg between a point of body sb and the source or a receiver (FP32): the
-// faces as in blocked; the bodies are those of the occluder mask occ (a
-// superset of the bodies that can pass the distance test), or all.
-__device__ __noinline__ int blocked_occ(const Ctx &c, v3t<float> A, v3t<float> B, int sb, float band,
-                                        const uint32_t *occ) {
-    if (!occ) return blocked_impl(c, A, B, -1, -1, sb, band);
+// A leg with an occluder mask (FP32): the faces (but sf1, sf2) as in blocked;
+// the bodies (but sb) are those of the mask occ, nw words (a superset of the
+// bodies that can pass the distance test), or all of them without a mask.
+__device__ __noinline__ int blocked_mask(const Ctx &c, v3t<float> A, v3t<float> B, int sf1, int sf2, int sb,
+                                         float band, const uint32_t *occ, int nw) {
+    if (!occ) return blocked_impl(c, A, B, sf1, sf2, sb, band);
     int uns = 0;
     if (c.bvh) {
-        const int r = tris_bvh(c, A, B, -1, -1, band);
+        const int r = tris_bvh(c, A, B, sf1, sf2, band);
         if (r == D_YES) return D_YES;
         uns = (r == D_UNSURE);
     }
@@ -425,7 +425,7 @@ __device__ __noinline__ int blocked_occ(const Ctx &c, v3t<float> A, v3t<float> B
         for (int k = 0; k < nfc; ++k) {
             float4 q = c.face32[f0 + k];
             float sA = q.x * A.x + q.y * A.y + q.z * A.z - q.w, sB = q.x * B.x + q.y * B.y + q.z * B.z - q.w;
-            bool cull = (sA > band && sB > band) || (sA < -band && sB < -band);
+            bool cull = (sA > band && sB > band) || (sA < -band && sB < -band) || f0 + k == sf1 || f0 + k == sf2;
             keep |= cull ? 0u : (1u << k);
         }
         while (keep) {
@@ -445,9 +445,9 @@ __device__ __noinline__ int blocked_occ(const Ctx &c, v3t<float> A, v3t<float> B
     const float idd = 1.0f / (qa + D.z * D.z);
     const float tlo = (float)EPS_TRIM, thi = 1.0f - (float)EPS_TRIM;
 #pragma unroll 1
-    for (int w = 0; w < c.occ_w; ++w) {
+    for (int w = 0; w < nw; ++w) {
         unsigned cand = occ[w];
-        if (sb >> 5 == w) cand &= ~(1u << (sb & 31));
+        if (sb >= 0 && sb >> 5 == w) cand &= ~(1u << (sb & 31));
         while (cand) {
             const int b = 32 * w + __ffs(cand) - 1;
             cand &= cand - 1;
@@ -474,11 +474,97 @@ __device__ __noinline__ int blocked(const Ctx &c, v3t<dx> A, v3t<dx> B, int sf1,
 // (nullptr: every body)
 template <typename T>
 __device__ __forceinline__ int blocked_leg(const Ctx &c, v3t<T> A, v3t<T> B, int b, T band, const uint32_t *occ) {
-    if constexpr (sizeof(T) == 4) return blocked_occ(c, A, B, b, band, occ);
+    if constexpr (sizeof(T) == 4) return blocked_mask(c, A, B, -1, -1, b, band, occ, c.occ_w);
     else return blocked(c, A, B, -1, -1, b, band);
 }
 __device__ __forceinline__ const uint32_t *occ_of(const Ctx &c, const uint32_t *masks, int b) {
     return (masks && c.occ_w) ? masks + b * c.occ_w : nullptr;
+}
+
+// squared distance in the floor plane from p to the segment a b
+__device__ __forceinline__ float seg_d2(float px, float py, float ax, float ay, float bx, float by) {
+    const float dx = bx - ax, dy = by - ay, wx = px - ax, wy = py - ay;
+    const float dd = dx * dx + dy * dy;
+    const float t = dd > 0.0f ? fminf(fmaxf((wx * dx + wy * dy) / dd, 0.0f), 1.0f) : 0.0f;
+    const float hx = wx - t * dx, hy = wy - t * dy;
+    return hx * hx + hy * hy;
+}
+
+// ---- occluder masks of the planar legs (FP32 fields).  The lanes of a warp
+// take the same planar candidate for the warp's receivers.  Its legs run
+// between consecutive regions: the source point, the box of the lanes'
+// reflection points on each face, the box of the lanes' receivers.  In
+// projection on the floor every leg between two regions lies in the capsule
+// of the segment joining the regions' centres, of radius the larger region's
+// half-diagonal (a point of a leg is a convex combination of points of the
+// two regions); a body whose disk, grown by the band and a margin for the
+// FP32 arithmetic of this test, misses the capsule cannot pass the distance
+// test of the visibility loop (projection shortens distances), and is left
+// out of that leg's mask.
+
+// a float's bits mapped to an unsigned integer of the same order
+__device__ __forceinline__ unsigned ord_of(float f) {
+    const unsigned u = __float_as_uint(f);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float of_ord(unsigned u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+// the box in the floor plane of the points (x, y) of the lanes with v among
+// the lanes `lanes` (all of which call this), as centre and half-diagonal;
+// rad < 0 when no lane has v
+__device__ __forceinline__ void lanes_box(unsigned lanes, bool v, float x, float y, float &cx, float &cy,
+                                          float &rad) {
+    const unsigned x0 = __reduce_min_sync(lanes, v ? ord_of(x) : 0xffffffffu);
+    const unsigned x1 = __reduce_max_sync(lanes, v ? ord_of(x) : 0u);
+    const unsigned y0 = __reduce_min_sync(lanes, v ? ord_of(y) : 0xffffffffu);
+    const unsigned y1 = __reduce_max_sync(lanes, v ? ord_of(y) : 0u);
+    if (x0 > x1) {
+        cx = cy = 0.0f;
+        rad = -1.0f;
+        return;
+    }
+    const float fx0 = of_ord(x0), fx1 = of_ord(x1), fy0 = of_ord(y0), fy1 = of_ord(y1);
+    cx = 0.5f * (fx0 + fx1);
+    cy = 0.5f * (fy0 + fy1);
+    // (rounded up by a relative 1e-6 for the centre's rounding)
+    rad = 0.5f * sqrtf((fx1 - fx0) * (fx1 - fx0) + (fy1 - fy0) * (fy1 - fy0)) * 1.000001f;
+}
+// masks wm[l][nw] of the legs l = 0 .. LEGS - 1 between the disks (cx[l],
+// cy[l], cr[l]) and (cx[l + 1], ...); the lanes `lanes` (all of which call
+// this) share the bodies and set the bits by shared-memory atomics
+template <int LEGS>
+__device__ __forceinline__ void leg_masks(const Ctx &c, unsigned lanes, const float *cx, const float *cy,
+                                          const float *cr, uint32_t *wm, int nw) {
+    const int lane = threadIdx.x & 31;
+    const int rank = __popc(lanes & ((1u << lane) - 1u)), nact = __popc(lanes);
+    __syncwarp(lanes);                        // every lane is done with the previous masks
+    for (int i = rank; i < LEGS * nw; i += nact) wm[i] = 0u;
+    __syncwarp(lanes);
+    const float margin = 1e-3f + 8.0f * c.band;
+    float dx[LEGS], dy[LEGS], idd[LEGS], rl[LEGS];
+#pragma unroll
+    for (int l = 0; l < LEGS; ++l) {
+        dx[l] = cx[l + 1] - cx[l];
+        dy[l] = cy[l + 1] - cy[l];
+        const float dd = dx[l] * dx[l] + dy[l] * dy[l];
+        idd[l] = dd > 0.0f ? 1.0f / dd : 0.0f;
+        rl[l] = fmaxf(cr[l], cr[l + 1]) + c.band + margin;
+    }
+#pragma unroll 1
+    for (int b = rank; b < c.n_body; b += nact) {
+        const float4 q = c.body[2 * b];
+#pragma unroll
+        for (int l = 0; l < LEGS; ++l) {
+            // squared distance from the body's centre to the segment of centres
+            const float wx = q.x - cx[l], wy = q.y - cy[l];
+            const float t = fminf(fmaxf((wx * dx[l] + wy * dy[l]) * idd[l], 0.0f), 1.0f);
+            const float hx = wx - t * dx[l], hy = wy - t * dy[l];
+            const float lim = rl[l] + q.w;
+            if (hx * hx + hy * hy <= lim * lim) atomicOr(&wm[l * nw + (b >> 5)], 1u << (b & 31));
+        }
+    }
+    __syncwarp(lanes);
 }
 
 // point (on the triangle's plane) inside the closed triangle
@@ -566,8 +652,11 @@ __device__ int cand_los(const Ctx &c, v3t<T> S, v3t<T> P, T band) {
     return vis_to_dec(blocked(c, S, P, -1, -1, -1, band));
 }
 
+// planar candidates: the geometric part (sides, reflection points in their
+// faces; the points in g), then the visibility of the legs (FP32: with the
+// legs' occluder masks wm, or none)
 template <typename T>
-__device__ int cand_r1(const Ctx &c, int i, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
+__device__ __forceinline__ int cand_r1_geo(const Ctx &c, int i, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
     v3t<T> n; T d;
     face_plane<T>(c, i, &n, &d);
     T dS = dot3(n, S) - d, dP = dot3(n, P) - d;
@@ -576,16 +665,27 @@ __device__ int cand_r1(const Ctx &c, int i, v3t<T> S, v3t<T> P, T band, Geo<T> &
     v3t<T> S1 = mirror_pt(S, n, d);
     T d1 = dot3(n, S1) - d;
     T t = d1 / (d1 - dP);
-    v3t<T> Q = S1 + (P - S1) * t;
-    if (!conj(acc, in_face(c, i, Q, band))) return D_NO;
-    if (!conj(acc, vis_to_dec(blocked(c, S, Q, i, -1, -1, band)))) return D_NO;
-    if (!conj(acc, vis_to_dec(blocked(c, Q, P, i, -1, -1, band)))) return D_NO;
-    g.Q1 = Q;
+    g.Q1 = S1 + (P - S1) * t;
+    if (!conj(acc, in_face(c, i, g.Q1, band))) return D_NO;
+    return acc;
+}
+__device__ __forceinline__ int cand_r1_vis(const Ctx &c, int i, v3t<float> S, v3t<float> P, float band,
+                                           const Geo<float> &g, int acc, const uint32_t *wm, int nw) {
+    if (!conj(acc, vis_to_dec(blocked_mask(c, S, g.Q1, i, -1, -1, band, wm, nw)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked_mask(c, g.Q1, P, i, -1, -1, band, wm ? wm + nw : nullptr, nw)))) return D_NO;
+    return acc;
+}
+template <typename T>
+__device__ int cand_r1(const Ctx &c, int i, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
+    int acc = cand_r1_geo<T>(c, i, S, P, band, g);
+    if (acc == D_NO) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, S, g.Q1, i, -1, -1, band)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, g.Q1, P, i, -1, -1, band)))) return D_NO;
     return acc;
 }
 
 template <typename T>
-__device__ int cand_r2(const Ctx &c, int i, int j, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
+__device__ __forceinline__ int cand_r2_geo(const Ctx &c, int i, int j, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
     v3t<T> ni, nj; T di, dj;
     face_plane<T>(c, i, &ni, &di);
     face_plane<T>(c, j, &nj, &dj);
@@ -601,11 +701,24 @@ __device__ int cand_r2(const Ctx &c, int i, int j, v3t<T> S, v3t<T> P, T band, G
     if (!conj(acc, side_dec(e1, eq, band, false))) return D_NO;
     T t1 = e1 / (e1 - eq);
     v3t<T> Q1 = S1 + (Q2 - S1) * t1;
-    if (!conj(acc, in_face(c, i, Q1, band))) return D_NO;
-    if (!conj(acc, vis_to_dec(blocked(c, S, Q1, i, -1, -1, band)))) return D_NO;
-    if (!conj(acc, vis_to_dec(blocked(c, Q1, Q2, i, j, -1, band)))) return D_NO;
-    if (!conj(acc, vis_to_dec(blocked(c, Q2, P, j, -1, -1, band)))) return D_NO;
     g.Q1 = Q1; g.Q2 = Q2;
+    if (!conj(acc, in_face(c, i, Q1, band))) return D_NO;
+    return acc;
+}
+__device__ __forceinline__ int cand_r2_vis(const Ctx &c, int i, int j, v3t<float> S, v3t<float> P, float band,
+                                           const Geo<float> &g, int acc, const uint32_t *wm, int nw) {
+    if (!conj(acc, vis_to_dec(blocked_mask(c, S, g.Q1, i, -1, -1, band, wm, nw)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked_mask(c, g.Q1, g.Q2, i, j, -1, band, wm ? wm + nw : nullptr, nw)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked_mask(c, g.Q2, P, j, -1, -1, band, wm ? wm + 2 * nw : nullptr, nw)))) return D_NO;
+    return acc;
+}
+template <typename T>
+__device__ int cand_r2(const Ctx &c, int i, int j, v3t<T> S, v3t<T> P, T band, Geo<T> &g) {
+    int acc = cand_r2_geo<T>(c, i, j, S, P, band, g);
+    if (acc == D_NO) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, S, g.Q1, i, -1, -1, band)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, g.Q1, g.Q2, i, j, -1, band)))) return D_NO;
+    if (!conj(acc, vis_to_dec(blocked(c, g.Q2, P, j, -1, -1, band)))) return D_NO;
     return acc;
 }
 
@@ -796,8 +909,7 @@ __device__ void body_frame(const Ctx &c, int b, v3t<dx> S, v3t<dx> P, dx band, F
 // - 1/d_s) (from expanding dL/dpsi = 0 to first order in a / d).  The
 // iteration stops at a step below 2e-7 psi, or at a Newton step below the
 // rounding noise of dL/dpsi over its slope -- the root's own error estimate
-// *err_est, which no further step could improve on.  FP64: bisection to
-// double resolution.
+// *err_est, which no further step could improve on.
 __device__ __forceinline__ float rsqrt1(float x) {      // 1/sqrt(x) with one Newton step on rsqrtf
     const float y = rsqrtf(x);
     return y * fmaf(-0.5f * x * y, y, 1.5f);
@@ -842,66 +954,78 @@ __device__ float refl_n32(float a, float ds, float pu, float pv, float gam, floa
     *sn_out = s;
     return psi;
 }
-__device__ dx refl_psi(dx a, dx ds, dx pu, dx pv, dx gam) {
-    dx lo = dx(0.0), hi = gam;
-    for (int it = 0; it < 200; ++it) {
-        dx mid = dx(0.5) * (lo + hi);
-        if (!(mid > lo && mid < hi)) break;
-        dx sn, cs;
-        SinCos(mid, &sn, &cs);
-        dx qx = a * cs, qy = a * sn, tx = -(a * sn), ty = a * cs;
-        dx sx = qx - ds, sy = qy, rx = qx - pu, ry = qy - pv;
-        dx g = (sx * tx + sy * ty) / Sqrt(sx * sx + sy * sy) + (rx * tx + ry * ty) / Sqrt(rx * rx + ry * ry);
-        if (g < dx(0.0)) lo = mid; else hi = mid;
-    }
-    return dx(0.5) * (lo + hi);
-}
-// FP64 Newton steps for the reflection point, on the unit vector
-// n = (cos psi, sin psi) itself and without trigonometric calls: for Q = a n
-// on the circle, (Q - S).t = a ds sin(psi) and (Q - P).t = a (pu sin(psi) -
-// pv cos(psi)), t the unit tangent, so
-//   dL/dpsi   = a [ds s / |Q - S| + (pu s - pv c) / |Q - P|],
-//   d2L/dpsi2 = (X.Q - (dL/dpsi)_X^2) / |Q - X| summed over X = S, P,
-// and n is rotated by each step d with cos d, sin d from their Taylor series
-// (|d| <= 1e-3), until a step is below tol (quadratic convergence: the next
-// one would be of order tol^2).  Returns false (no result) if a step is too
-// large or the curvature not positive; the caller then brackets.
-__device__ bool refl_newton64(double A, double Ds, double Pu, double Pv, double *c_io, double *s_io, double tol) {
+// FP64 reflection point from a start n0 = (c, s): safeguarded Newton on the
+// unit vector n itself, without trigonometric calls.  The bracket is kept as
+// two unit vectors, n_lo (dL/dpsi < 0; initially psi = 0, the direction of S)
+// and n_hi (dL/dpsi >= 0; initially psi = gam, the direction of P).  For Q =
+// a n and t = a (-s, c),
+//   dL/dpsi   = (Q - S).t / |Q - S| + (Q - P).t / |Q - P|,
+//   d2L/dpsi2 = sum over X = S, P of (X.Q - ((Q - X).t / |Q - X|)^2) / |Q - X|,
+// each from the difference vector Q - X.  A Newton step d turns n by the
+// angle 2 atan(d / 2) (the rational rotation ((1 - u^2), 2u) / (1 + u^2), u =
+// d / 2: a unit vector by construction, equal to the turn by d up to d^3/12,
+// which only changes the step length); a step that leaves the bracket is
+// replaced by its bisector normalise(n_lo + n_hi) (the bracket spans less than
+// pi).  Stops at a Newton step below tol or a bracket narrower than tol
+// (near grazing, where the slope vanishes, the Newton steps bounce within the
+// rounding noise of dL/dpsi over its slope and the bracket closes on it); the
+// result is the last n.
+__device__ void refl_root64(double A, double Ds, double Pu, double Pv, double *c_io, double *s_io, double tol) {
+    const double ip = rsqrt(Pu * Pu + Pv * Pv);
+    double lc = 1.0, ls = 0.0, hc = Pu * ip, hs = Pv * ip;
     double c = *c_io, s = *s_io;
-    const double dp2 = Pu * Pu + Pv * Pv;
-    for (int it = 0; it < 6; ++it) {
-        double ifs = rsqrt(A * A + Ds * Ds - 2.0 * A * Ds * c);
-        double ifr = rsqrt(A * A + dp2 - 2.0 * A * (Pu * c + Pv * s));
-        double gs = A * Ds * s * ifs, gr = A * (Pu * s - Pv * c) * ifr;
-        double g = gs + gr;
-        double g2 = (Ds * A * c - gs * gs) * ifs + (A * (Pu * c + Pv * s) - gr * gr) * ifr;
-        if (!(g2 > 0.0)) return false;
-        double d = -g / g2;
-        if (!(fabs(d) <= 1e-3)) return false;
-        double d2 = d * d;
-        double cd = 1.0 - d2 * (0.5 - d2 * (1.0 / 24.0));
-        double sd = d * (1.0 - d2 * ((1.0 / 6.0) - d2 * (1.0 / 120.0)));
-        double cn = c * cd - s * sd, sn = s * cd + c * sd;
-        c = cn; s = sn;
-        if (fabs(d) <= tol) {
-            *c_io = c; *s_io = s;
-            return true;
-        }
+    {
+        const double r = rsqrt(c * c + s * s);
+        c *= r; s *= r;
     }
-    return false;
+    // a start outside the bracket: its bisector
+    if (!(ls * c - lc * s < 0.0 && c * hs - s * hc > 0.0)) {
+        const double bc = lc + hc, bs = ls + hs, r = rsqrt(bc * bc + bs * bs);
+        c = bc * r; s = bs * r;
+    }
+    for (int it = 0; it < 80; ++it) {
+        const double qx = A * c, qy = A * s;
+        const double sx = qx - Ds, sy = qy, rx = qx - Pu, ry = qy - Pv;
+        const double ifs = rsqrt(sx * sx + sy * sy), ifr = rsqrt(rx * rx + ry * ry);
+        const double gs = (sy * qx - sx * qy) * ifs, gr = (ry * qx - rx * qy) * ifr;
+        const double g = gs + gr;
+        const double g2 = (Ds * qx - gs * gs) * ifs + (Pu * qx + Pv * qy - gr * gr) * ifr;
+        if (g == 0.0) break;
+        if (g < 0.0) { lc = c; ls = s; } else { hc = c; hs = s; }
+        const double d = -g / g2;
+        bool ok = g2 > 0.0 && fabs(d) <= 0.5;
+        double nc = c, ns = s;
+        if (ok) {
+            const double u = 0.5 * d, iu = 1.0 / (1.0 + u * u);
+            const double cd = (1.0 - u * u) * iu, sd = 2.0 * u * iu;
+            nc = c * cd - s * sd;
+            ns = s * cd + c * sd;
+            ok = (ls * nc - lc * ns < 0.0) && (nc * hs - ns * hc > 0.0);     // strictly inside the bracket
+        }
+        if (!ok) {
+            const double bc = lc + hc, bs = ls + hs, r = rsqrt(bc * bc + bs * bs);
+            nc = bc * r; ns = bs * r;
+        }
+        c = nc; s = ns;
+        if ((ok && fabs(d) <= tol) || fabs(lc * hs - ls * hc) <= tol) break;
+    }
+    *c_io = c;
+    *s_io = s;
 }
 
 // Double-float refinement of an FP32 reflection point (near-grazing
 // incidence, where the FP32 root of dL/dpsi is too coarse for cos(theta_i)).
 // At n0 = (c0, s0), the FP32 root, normalised exactly (1/|n0| = 1 - delta/2,
-// delta = |n0|^2 - 1 formed exactly), dL/dpsi of the closed form above is
-// evaluated in double-float -- its two terms cancel at the root, which is
-// what limits the FP32 root -- and Newton steps rotate n; the FP32 slope is
-// enough for the step.  Returns false if a step exceeds 1e-4 or the slope is
-// not positive.
+// delta = |n0|^2 - 1 formed exactly), dL/dpsi in the closed form
+//   dL/dpsi = a [ds s / |Q - S| + (pu s - pv c) / |Q - P|]
+// (for Q = a n on the circle, (Q - S).t = a ds s and (Q - P).t = a (pu s -
+// pv c), t the unit tangent) is evaluated in double-float -- its two terms
+// cancel at the root, which is what limits the FP32 root -- and Newton steps
+// rotate n; the FP32 slope is enough for the step.  Returns false if a step
+// exceeds 1e-3 or the slope is not positive.
 __device__ bool refl_polish_df(float a, float ds, float pu, float pv, float c0, float s0, float *cs_out,
                                float *sn_out) {
-    for (int it = 0; it < 3; ++it) {
+    for (int it = 0; it < 4; ++it) {
         dfl r2 = df_add(two_prod(c0, c0), two_prod(s0, s0));
         float delta = (r2.hi - 1.0f) + r2.lo;
         dfl c, s;
@@ -923,10 +1047,12 @@ __device__ bool refl_polish_df(float a, float ds, float pu, float pv, float c0, 
                         (uP - a) * (pu * pu + pv * pv - a * uP) / (fr.hi * fr.hi * fr.hi));
         if (!(g2 > 0.0f)) return false;
         float d = -(a * (g.hi + g.lo)) / g2;
-        if (!(fabsf(d) <= 1e-4f)) return false;
-        // rotate by d (cos d = 1 - d^2/2, sin d = d at this size), one rounding
-        float cn = c0 + (c.lo - s0 * d - 0.5f * c0 * d * d);
-        float sn = s0 + (s.lo + c0 * d - 0.5f * s0 * d * d);
+        if (!(fabsf(d) <= 1e-3f)) return false;
+        // rotate by d (cos d = 1 - d^2/2, sin d = d - d^3/6 to FP32 resolution
+        // at this size), one rounding
+        const float d2 = d * d, d3 = d2 * d * (1.0f / 6.0f);
+        float cn = c0 + (c.lo - s0 * d - 0.5f * c0 * d2 + s0 * d3);
+        float sn = s0 + (s.lo + c0 * d - 0.5f * s0 * d2 - c0 * d3);
         c0 = cn; s0 = sn;
         if (fabsf(d) <= 1e-9f) break;
     }
@@ -936,36 +1062,22 @@ __device__ bool refl_polish_df(float a, float ds, float pu, float pv, float c0, 
 }
 
 // FP64 refinement of an FP32 reflection point, for the cases the
-// double-float step does not take; FP64 bisection when Newton does not
-// converge.  Returns (cos psi, sin psi) in FP32.
+// double-float step does not take.  Returns (cos psi, sin psi) in FP32.
 __device__ __noinline__ void refl_polish(float a, float ds, float pu, float pv, float gam, float c0f, float s0f,
                                          float *cs_out, float *sn_out) {
     double c = c0f, s = s0f;
-    double r = 1.0 / sqrt(c * c + s * s);
-    c *= r; s *= r;
-    if (!refl_newton64(a, ds, pu, pv, &c, &s, 1e-9)) {        // the result is rounded to FP32
-        dx psi = refl_psi(dx((double)a), dx((double)ds), dx((double)pu), dx((double)pv), dx((double)gam));
-        sincos(psi.v, &s, &c);
-    }
+    refl_root64(a, ds, pu, pv, &c, &s, 1e-9);                 // (the result is rounded to FP32)
     *cs_out = (float)c;
     *sn_out = (float)s;
 }
 
-// FP64 reflection point: the FP32 root refined by FP64 Newton steps (to
-// ~1e-15 of the bisection root of the definition); bisection when Newton
-// does not converge.
+// FP64 reflection point: the FP32 root refined by the safeguarded FP64 Newton
+// iteration to a step below 1e-14 (or its rounding noise).
 __device__ __noinline__ void refl_root(dx a, dx ds, dx pu, dx pv, dx gam, dx *cs_out, dx *sn_out) {
     float err, c0f, s0f;
     refl_n32(to_float(a), to_float(ds), to_float(pu), to_float(pv), to_float(gam), &c0f, &s0f, &err);
     double c = c0f, s = s0f;
-    double r = 1.0 / sqrt(c * c + s * s);
-    c *= r; s *= r;
-    if (!refl_newton64(a.v, ds.v, pu.v, pv.v, &c, &s, 1e-13)) {
-        dx psi = refl_psi(a, ds, pu, pv, gam);
-        dx sn, cs;
-        SinCos(psi, &sn, &cs);
-        c = cs.v; s = sn.v;
-    }
+    refl_root64(a.v, ds.v, pu.v, pv.v, &c, &s, 1e-14);
     *cs_out = dx(c);
     *sn_out = dx(s);
 }
@@ -991,6 +1103,9 @@ __device__ __forceinline__ void df_to_surface(v3t<float> X, float4 c, float a, v
 __device__ __forceinline__ dfl df_norm3(const dfl w[3]) {
     return df_sqrt(df_add(df_add(df_sq(w[0]), df_sq(w[1])), df_sq(w[2])));
 }
+
+// smallest incidence cosine of a reflection off a body (see cand_rb)
+constexpr double COS_MIN = 1e-30;
 
 // body reflection candidate (sphere or vertical cylinder)
 template <typename T>
@@ -1033,7 +1148,11 @@ __device__ int cand_rb(const Ctx &c, int b, v3t<T> S, v3t<T> P, T band, const Fr
         Q = mk3<T>(T((double)q0.x) + a * n.x, T((double)q0.y) + a * n.y, zq);
     }
     v3t<T> shi = unit3(Q - S);
-    T cth = -dot3(shi, n);
+    // incidence cosine, positive on the lit side; at grazing its rounding may
+    // reach zero, where the divergence factor's zero and the Fock-uniform
+    // coefficient's pole (both of order cos^(1/2)) would meet as 0 * inf: the
+    // smallest positive value keeps their finite product
+    const T cth = Fmax(-dot3(shi, n), T(COS_MIN));
     if (!conj(acc, vis_to_dec(blocked_leg(c, S, Q, b, band, occ_of(c, c.occ_src, b))))) return D_NO;
     if (!conj(acc, vis_to_dec(blocked_leg(c, Q, P, b, band, occ_of(c, occ_rx, b))))) return D_NO;
     if constexpr (sizeof(T) == 4) {
@@ -1607,7 +1726,7 @@ __device__ void field_body_refl(const Ctx &c, ACC &acc, const FreqC &fq, v3t<T> 
     v3t<T> di = Q - S;
     T si = norm3(di), sr = norm3(g.dr);
     v3t<T> shi = di * (T(1) / si);
-    T cth = -dot3(shi, n);
+    const T cth = Fmax(-dot3(shi, n), T(COS_MIN));       // (as in cand_rb)
     // reflected direction by the law of reflection: unlike (P - Q) / |P - Q|
     // it does not turn with a rounding-size shift of Q along the surface,
     // which matters when the receiver is within a wavelength of the body
@@ -1738,27 +1857,33 @@ __device__ __forceinline__ void rec_put(float *r, float Es, float Eh, v3t<float>
     r[256] = A; r[288] = Lp; r[320] = rcb; r[352] = x; r[384] = len.hi; r[416] = len.lo;
 }
 
-// reflection off a body: as field_body_refl, up to the frequency loop
-__device__ __forceinline__ void rb_prep(const Ctx &c, float *r, v3t<float> S, const Geo<float> &g, dfl len) {
-    v3t<float> Q = g.Q1, n = g.n1;
-    v3t<float> di = Q - S;
-    float si = norm3(di), sr = norm3(g.dr);
-    v3t<float> shi = di * (1.0f / si);
-    float cth = -dot3(shi, n);
-    v3t<float> shr = unit3(shi + n * (2.0f * cth));
-    v3t<float> ep = cross3(n, shi);
-    float ne = norm3(ep);
-    if (ne == 0.0f) {
-        v3t<float> tmp = (fabsf(n.x) < 0.9f) ? mk3<float>(1, 0, 0) : mk3<float>(0, 1, 0);
+// reflection off a body: as field_body_refl, up to the frequency loop, in
+// the geometry's own precision (FP64 for a candidate decided in FP64: near
+// grazing its incidence cosine and divergence factor must come from the same
+// FP64 geometry, as their product is what stays finite)
+template <typename T>
+__device__ __forceinline__ void rb_prep(const Ctx &c, float *r, v3t<T> S, const Geo<T> &g, dfl len) {
+    auto f3 = [](v3t<T> v) { return mk3<float>(to_float(v.x), to_float(v.y), to_float(v.z)); };
+    v3t<T> Q = g.Q1, n = g.n1;
+    v3t<T> di = Q - S;
+    T si = norm3(di), sr = norm3(g.dr);
+    v3t<T> shi = di * (T(1) / si);
+    const T cth = Fmax(-dot3(shi, n), T(COS_MIN));    // (as in cand_rb)
+    v3t<T> shr = unit3(shi + n * (T(2) * cth));
+    v3t<T> ep = cross3(n, shi);
+    T ne = norm3(ep);
+    if (ne == T(0)) {
+        v3t<T> tmp = (Fabs(n.x) < T(0.9)) ? mk3<T>(1, 0, 0) : mk3<T>(0, 1, 0);
         ep = unit3(cross3(n, tmp));
     } else {
-        ep = ep * (1.0f / ne);
+        ep = ep * (T(1) / ne);
     }
-    v3t<float> epi = cross3(ep, shi), epr = cross3(ep, shr);
-    v3t<float> e0 = src_pol(c, shi);
-    float rho1 = 1.0f / (1.0f / si + g.inv_f1), rho2 = 1.0f / (1.0f / si + g.inv_f2);
-    float A = sqrtf(rho1 * rho2 / ((rho1 + sr) * (rho2 + sr))) / si;
-    rec_put(r, dot3(e0, ep), dot3(e0, epi), ep, epr, A, si * sr / (si + sr), cbrtf(g.rho_g), cth, len);
+    v3t<T> epi = cross3(ep, shi), epr = cross3(ep, shr);
+    v3t<T> e0 = src_pol(c, shi);
+    T rho1 = T(1) / (T(1) / si + g.inv_f1), rho2 = T(1) / (T(1) / si + g.inv_f2);
+    T A = Sqrt(rho1 * rho2 / ((rho1 + sr) * (rho2 + sr))) / si;
+    rec_put(r, to_float(dot3(e0, ep)), to_float(dot3(e0, epi)), f3(ep), f3(epr), to_float(A),
+            to_float(si * sr / (si + sr)), to_float(Cbrt(g.rho_g)), to_float(cth), len);
 }
 __device__ __forceinline__ void rb_apply(const Ctx &c, AccS<float> &acc, const FreqC &fq, const float *r) {
     const float Es = r[0], Eh = r[32], A = r[256], Lp = r[288], rcb = r[320], cth = r[352];
@@ -1949,7 +2074,7 @@ __device__ __noinline__ int esc_rb(const Ctx &c, int b, v3t<float> Pf, const Fre
     if (d == D_YES && rec) {
         // the path record of the FP64 geometry (its field is summed with the
         // FP32 records, frequency chunk by frequency chunk)
-        rb_prep(c, rec, c.S, to_f(g), to_df(to_double(seglen(Sd, g.Q1) + seglen(g.Q1, Pd))));
+        rb_prep<dx>(c, rec, Sd, g, to_df(to_double(seglen(Sd, g.Q1) + seglen(g.Q1, Pd))));
     } else if (d == D_YES && field) {
         Acc<dx> a;
         acc_zero(a);
@@ -2188,7 +2313,8 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                                               int b_begin, int b_end, bool first_chunk, bool may_flush, int rcap,
                                               const uint32_t *occ_rx, int part, int nparts,
                                               AccS<T> acc, float *rec, uint32_t &fl, unsigned &nesc, int &npath,
-                                              int &nrec_out, const uint32_t *qmask = nullptr) {
+                                              int &nrec_out, const uint32_t *qmask = nullptr, unsigned lanes = 0u,
+                                              uint32_t *pwm = nullptr) {
     constexpr bool BODIES = (CLS & CLS_BODIES) != 0;
     const bool fp32 = sizeof(T) == 4;
     const T band = fp32 ? T(c.band) : T(0);
@@ -2242,6 +2368,22 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
         inside = (d == D_YES);
     }
 
+    // planar occluder masks (FP32 fields, enumeration): the lanes `lanes`
+    // (every lane of the warp that evaluates a receiver) share them; pnw mask
+    // words per leg, 0 without masks
+    constexpr bool PM = sizeof(T) == 4 && !PATHS && CLS == CLS_PLANAR;
+    unsigned pl = 0u;
+    int pnw = 0;
+    float tcx = 0.0f, tcy = 0.0f, tcr = 0.0f;
+    if constexpr (PM) {
+        if (pwm && lanes && c.n_body > 0 && c.n_body <= OCC_MAX_BODIES) {
+            pl = __ballot_sync(lanes, !inside);
+            if (pl) {
+                pnw = (c.n_body + 31) >> 5;
+                if (!inside) lanes_box(pl, true, Pf.x, Pf.y, tcx, tcy, tcr);
+            }
+        }
+    }
     if (inside) {
         fl |= RT_FLAG_INSIDE;
     } else {
@@ -2308,7 +2450,23 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                 for (int i = 0; i < c.n_face; ++i) {
                     if ((1 + i) % nparts != part) continue;      // candidates 1 .. n_face
                     Geo<T> g;
-                    int d = cand_r1<T>(c, i, Sx, P, band, g);
+                    int d;
+                    if constexpr (PM) {
+                        if (pnw) {
+                            d = cand_r1_geo<T>(c, i, Sx, P, band, g);
+                            const bool v = d != D_NO;
+                            float qx, qy, qr;
+                            lanes_box(pl, v, g.Q1.x, g.Q1.y, qx, qy, qr);
+                            if (qr < 0.0f) continue;                 // (no lane: the whole warp)
+                            const float cx[3] = {c.S.x, qx, tcx}, cy[3] = {c.S.y, qy, tcy}, cr[3] = {0.0f, qr, tcr};
+                            leg_masks<2>(c, pl, cx, cy, cr, pwm, pnw);
+                            if (v) d = cand_r1_vis(c, i, Sx, P, band, g, d, pwm, pnw);
+                        } else {
+                            d = cand_r1<T>(c, i, Sx, P, band, g);
+                        }
+                    } else {
+                        d = cand_r1<T>(c, i, Sx, P, band, g);
+                    }
                     if constexpr (sizeof(T) == 4) {
                         if (d == D_UNSURE) { escalated(); d = esc_r1(c, i, Pf, &g.Q1); }
                     }
@@ -2338,7 +2496,25 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                         if (j == i) continue;
                         if ((1 + i * c.n_face + j) % nparts != part) continue;   // then the ordered pairs
                         Geo<T> g;
-                        int d = cand_r2<T>(c, i, j, Sx, P, band, g);
+                        int d;
+                        if constexpr (PM) {
+                            if (pnw) {
+                                d = cand_r2_geo<T>(c, i, j, Sx, P, band, g);
+                                const bool v = d != D_NO;
+                                float ax, ay, ar, bx, by, br;
+                                lanes_box(pl, v, g.Q1.x, g.Q1.y, ax, ay, ar);
+                                lanes_box(pl, v, g.Q2.x, g.Q2.y, bx, by, br);
+                                if (ar < 0.0f) continue;             // (no lane: the whole warp)
+                                const float cx[4] = {c.S.x, ax, bx, tcx}, cy[4] = {c.S.y, ay, by, tcy},
+                                            cr[4] = {0.0f, ar, br, tcr};
+                                leg_masks<3>(c, pl, cx, cy, cr, pwm, pnw);
+                                if (v) d = cand_r2_vis(c, i, j, Sx, P, band, g, d, pwm, pnw);
+                            } else {
+                                d = cand_r2<T>(c, i, j, Sx, P, band, g);
+                            }
+                        } else {
+                            d = cand_r2<T>(c, i, j, Sx, P, band, g);
+                        }
                         if constexpr (sizeof(T) == 4) {
                             if (d == D_UNSURE) { escalated(); d = esc_r2(c, i, j, Pf, &g.Q1, &g.Q2); }
                         }
@@ -2542,13 +2718,6 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
 // disk (grown by the band and a margin for the FP32 arithmetic of this test)
 // misses it cannot pass the distance test of the visibility loop for any
 // such leg (projection shortens distances), and is left out of the mask.
-__device__ __forceinline__ float seg_d2(float px, float py, float ax, float ay, float bx, float by) {
-    const float dx = bx - ax, dy = by - ay, wx = px - ax, wy = py - ay;
-    const float dd = dx * dx + dy * dy;
-    const float t = dd > 0.0f ? fminf(fmaxf((wx * dx + wy * dy) / dd, 0.0f), 1.0f) : 0.0f;
-    const float hx = wx - t * dx, hy = wy - t * dy;
-    return hx * hx + hy * hy;
-}
 // squared distance from p to the triangle (a, b, c); 0 inside or degenerate
 __device__ __forceinline__ float tri_d2(float px, float py, float ax, float ay, float bx, float by, float cx,
                                         float cy) {
@@ -2791,6 +2960,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
         T *s_part = WIDE ? reinterpret_cast<T *>(s_rec) : &s_part_st[0][0][0];
         __shared__ uint32_t s_fl[NW][32];
         __shared__ uint32_t s_qmask[CLS == CLS_SEQ ? NW : 1][CLS == CLS_SEQ ? SEQ_MASK_WORDS : 1];
+        __shared__ uint32_t s_pwm[CLS == CLS_PLANAR ? NW : 1][CLS == CLS_PLANAR ? 3 * (OCC_MAX_BODIES / 32) : 1];
         __shared__ unsigned long long s_unit;
         __shared__ int s_fi, s_new;
         __shared__ FrameDev s_fr;
@@ -2872,6 +3042,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
             }
             AccS<T> acc{s_part + warp * prow * 32 + lane};     // the warp's partial sums, summed in place
             float *rec = s_rec + warp * (rcap * REC_N * 32) + lane;
+            const unsigned lanes = __ballot_sync(0xffffffffu, rok);      // the lanes that evaluate a receiver
 #pragma unroll 1
             for (int b0 = 0; b0 < (n_b > 0 ? n_b : 1); b0 += bc) {
                 uint32_t fl = 0;
@@ -2883,7 +3054,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
                                                  Fr.hl, b0, min(b0 + bc, n_b), b0 == 0, nch == 1, rcap,
                                                  occ_on ? s_occ_rx + grp * S.n_body * occ_w : nullptr, part,
                                                  NWT, acc, rec, fl, nesc, npath, nrec,
-                                                 qm_on ? &s_qmask[warp][0] : nullptr);
+                                                 qm_on ? &s_qmask[warp][0] : nullptr, lanes, &s_pwm[warp][0]);
                 s_fl[warp][lane] = fl;
                 if (nesc && ch0 == 0) atomicAdd(esc_counter, (unsigned long long)nesc);
 #pragma unroll 1

@@ -155,6 +155,24 @@ def test_receivers_near_body_surfaces(creep, oracle_mod, kind):
     compare_fields(Eg, ref, flags=ref.flags, freqs=sc2.freqs)
 
 
+def test_grazing_reflection_at_the_shadow_boundary(creep, oracle_mod):
+    """Crowd frame 63, receiver 33615: 1.3e-8 rad inside the lit side of a
+    cylinder's shadow boundary, so the reflection off it (Eq. 3) has an
+    incidence cosine of about 6e-9 and is decided in FP64.  Its divergence
+    factor (zero) and Fock-uniform coefficient (pole) must come from the same
+    geometry, whose product stays finite; the neighbouring receivers too, in
+    FP32 and FP64."""
+    cw = scenes.crowd()
+    sc = cw.frame(63).subset(np.arange(33600, 33632))
+    for prec in (creep.RT_PREC_FP32, creep.RT_PREC_FP64):
+        opts = creep.options(max_order=2, precision=prec)
+        S, Eg, codes, counts, fl, _ = _run(creep, sc, opts=opts)
+        ref = oracle_mod.evaluate(sc)
+        compare_paths(codes, counts, ref)
+        assert np.all(np.isfinite(Eg))
+        compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs)
+
+
 def test_fp64_mode(creep, oracle_mod):
     sc = scenes.room(n_cyl=12, nx=23, ny=19, seed=77)
     opts = creep.options(precision=creep.RT_PREC_FP64)
