@@ -1209,24 +1209,16 @@ __device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T ba
     // 2 pi a longer per turn; on a sphere the ray crosses the source axis
     // twice per turn (+j each: -1 per turn)
     if (c.enc > 0) dpsi = dpsi + TWO_PI_T * T(c.enc);
-    T s1, c1, s2, c2;
-    if constexpr (sizeof(T) == 4) {
-        // the attachment and shedding directions psi1 = +-beta_s and psi2 =
-        // gam -+ beta_p in closed form: cos beta_s = a / d_s, sin beta_s =
-        // s' / d_s, (cos gam, sin gam) = (p_u, p_v) / d_p, cos beta_p = a / d_p,
-        // sin beta_p = s'' / d_p (tangent lengths s', s'' from the frame)
-        const float ids = 1.0f / F.ds, idp2 = 1.0f / (F.dp * F.dp);
-        c1 = a * ids;
-        s1 = (dir == 0) ? F.sps * ids : -F.sps * ids;
-        const float pa_u = F.pu * a, pa_v = F.pv * a, qs_u = F.pu * F.sqp, qs_v = F.pv * F.sqp;
-        c2 = ((dir == 0) ? pa_u + qs_v : pa_u - qs_v) * idp2;
-        s2 = ((dir == 0) ? pa_v - qs_u : pa_v + qs_u) * idp2;
-    } else {
-        T psi1 = (dir == 0) ? F.bs : -F.bs;
-        T psi2 = (dir == 0) ? F.gam - F.bp : F.gam + F.bp;
-        SinCos(psi1, &s1, &c1);
-        SinCos(psi2, &s2, &c2);
-    }
+    // the attachment and shedding directions psi1 = +-beta_s and psi2 = gam
+    // -+ beta_p in closed form: cos beta_s = a / d_s, sin beta_s = s' / d_s,
+    // (cos gam, sin gam) = (p_u, p_v) / d_p, cos beta_p = a / d_p, sin beta_p =
+    // s'' / d_p (tangent lengths s', s'' from the frame)
+    const T ids = T(1) / F.ds, idp2 = T(1) / (F.dp * F.dp);
+    const T c1 = a * ids;
+    const T s1 = (dir == 0) ? F.sps * ids : -(F.sps * ids);
+    const T pa_u = F.pu * a, pa_v = F.pv * a, qs_u = F.pu * F.sqp, qs_v = F.pv * F.sqp;
+    const T c2 = ((dir == 0) ? pa_u + qs_v : pa_u - qs_v) * idp2;
+    const T s2 = ((dir == 0) ? pa_v - qs_u : pa_v + qs_u) * idp2;
     g.n1 = F.u * c1 + F.v * s1;
     g.n2 = F.u * c2 + F.v * s2;
     if (sphere) {
@@ -1238,14 +1230,8 @@ __device__ int cand_creep(const Ctx &c, int b, int dir, v3t<T> S, v3t<T> P, T ba
         g.t = a * dpsi;
         g.rho_g = a;
         g.caus = (dir == 1);
-        if (band > T(0)) {
-            g.dperp = F.pv;                      // distance of P from the S-c axis
-        } else {
-            T sg, cg; SinCos(F.gam, &sg, &cg);
-            g.dperp = F.dp * sg;
-        }
-        T dq1 = a * Sqrt(Fmax(T(0), T(1) - (a / F.ds) * (a / F.ds)));   // a sin(beta_s)
-        if (band == T(0)) { T sb, cb; SinCos(F.bs, &sb, &cb); dq1 = a * sb; }
+        g.dperp = F.pv;                          // distance of P from the S-c axis, d_p sin(gam)
+        const T dq1 = a * (F.sps * ids);         // a sin(beta_s)
         g.amp = (g.dperp > T(0)) ? Sqrt(dq1 / g.dperp) / Sqrt(g.sq) / g.sp : T(0);
         if (c.enc & 1) g.amp = -g.amp;           // the (-1) of an odd number of extra turns
     } else {
@@ -1912,16 +1898,20 @@ __device__ __forceinline__ void rb_apply(const Ctx &c, AccS<float> &acc, const F
 }
 
 // creeping ray: as field_creep, up to the frequency loop
-__device__ __forceinline__ void creep_prep(const Ctx &c, float *r, v3t<float> S, v3t<float> P, const Geo<float> &g,
-                                           dfl len, unsigned enable) {
-    v3t<float> t1 = unit3(g.Q1 - S), t2 = unit3(P - g.Q2);
-    v3t<float> b1 = cross3(t1, g.n1), b2 = cross3(t2, g.n2);
-    v3t<float> e0 = src_pol(c, t1);
-    float Es = (enable & RT_EN_CREEP_SOFT) ? dot3(e0, b1) : 0.0f;
-    float Eh = (enable & RT_EN_CREEP_HARD) ? dot3(e0, g.n1) : 0.0f;
-    if (signbit(g.amp)) { Es = -Es; Eh = -Eh; }  // (the record's amplitude sign is the caustic flag)
-    rec_put(r, Es, Eh, b2, g.n2, g.caus ? -fabsf(g.amp) : fabsf(g.amp), -(g.sp * g.sq / (g.sp + g.sq)), cbrtf(g.rho_g),
-            g.t / g.rho_g, len);
+// (in the geometry's own precision: FP64 for a candidate decided in FP64)
+template <typename T>
+__device__ __forceinline__ void creep_prep(const Ctx &c, float *r, v3t<T> S, v3t<T> P, const Geo<T> &g, dfl len,
+                                           unsigned enable) {
+    auto f3 = [](v3t<T> v) { return mk3<float>(to_float(v.x), to_float(v.y), to_float(v.z)); };
+    v3t<T> t1 = unit3(g.Q1 - S), t2 = unit3(P - g.Q2);
+    v3t<T> b1 = cross3(t1, g.n1), b2 = cross3(t2, g.n2);
+    v3t<T> e0 = src_pol(c, t1);
+    float Es = (enable & RT_EN_CREEP_SOFT) ? to_float(dot3(e0, b1)) : 0.0f;
+    float Eh = (enable & RT_EN_CREEP_HARD) ? to_float(dot3(e0, g.n1)) : 0.0f;
+    const float amp = to_float(g.amp);
+    if (signbit(amp)) { Es = -Es; Eh = -Eh; }    // (the record's amplitude sign is the caustic flag)
+    rec_put(r, Es, Eh, f3(b2), f3(g.n2), g.caus ? -fabsf(amp) : fabsf(amp), to_float(-(g.sp * g.sq / (g.sp + g.sq))),
+            to_float(Cbrt(g.rho_g)), to_float(g.t / g.rho_g), len);
 }
 // wall -> creeping path (see field_wcreep): the real part of the reflected
 // polarisation in one record; an imaginary part (a dielectric face) in a
@@ -2106,7 +2096,7 @@ __device__ __noinline__ int esc_creep(const Ctx &c, int b, int dir, v3t<float> P
         }
     }
     if (rec) {
-        creep_prep(c, rec, c.S, Pf, to_f(g), to_df(to_double(g.sp + g.t + g.sq)), enable);
+        creep_prep<dx>(c, rec, Sd, Pd, g, to_df(to_double(g.sp + g.t + g.sq)), enable);
         *n_rec = 1;
     } else if (field) {
         Acc<dx> a;
@@ -2596,7 +2586,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                                 escalated();
                                 Contrib ct;
                                 int caus = 0, added = 0;
-                                const bool defer = RECS && !may_flush;
+                                const bool defer = RECS;
                                 d = esc_wcreep(c, wf, bb, dir, Pf, fq, !PATHS && !defer, half_lambda_max, enable, &ct,
                                                &caus, defer ? rec + nrec * REC_N * 32 : nullptr, &added);
                                 if (d == D_YES) {
@@ -2633,12 +2623,11 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                             if (d == D_UNSURE) {
                                 // decided in FP64, and its geometry, length and amplitude
                                 // too (they may be ill-conditioned in FP32, e.g. for a
-                                // receiver at a surface); the Fock bracket stays FP32
+                                // receiver at a surface); its record holds them, and the
+                                // FP32 field pass evaluates it with the others
                                 escalated();
                                 Contrib ct;
-                                // (with several frequency chunks its field goes through a
-                                // record, as the FP32 candidates' do)
-                                const bool defer = RECS && !may_flush;
+                                const bool defer = RECS;
                                 d = esc_rb(c, b, Pf, fq, !PATHS && !defer, &ct,
                                            defer ? rec + nrec * REC_N * 32 : nullptr);
                                 if (d == D_YES) {
@@ -2677,7 +2666,7 @@ __device__ __forceinline__ void eval_receiver(const Ctx &c, const FreqC *fqs, in
                                     escalated();
                                     Contrib ct;
                                     int caus = 0;
-                                    const bool defer = RECS && !may_flush;
+                                    const bool defer = RECS;
                                     int added = 0;
                                     d = esc_creep(c, b, dir, Pf, fq, !PATHS && !defer, half_lambda_max, enable, &ct,
                                                   &caus, defer ? rec + nrec * REC_N * 32 : nullptr, &added);
