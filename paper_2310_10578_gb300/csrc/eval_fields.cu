@@ -966,10 +966,10 @@ __device__ float refl_n32(float a, float ds, float pu, float pv, float gam, floa
 // d / 2: a unit vector by construction, equal to the turn by d up to d^3/12,
 // which only changes the step length); a step that leaves the bracket is
 // replaced by its bisector normalise(n_lo + n_hi) (the bracket spans less than
-// pi).  Stops at a Newton step below tol or a bracket narrower than tol
-// (near grazing, where the slope vanishes, the Newton steps bounce within the
-// rounding noise of dL/dpsi over its slope and the bracket closes on it); the
-// result is the last n.
+// pi).  Stops at a Newton step below tol, or below the rounding of dL/dpsi
+// over its slope (4 ulp of its two terms: near grazing, where the slope
+// vanishes, no step can improve on it), or at a bracket narrower than tol;
+// the result is the last n.
 __device__ void refl_root64(double A, double Ds, double Pu, double Pv, double *c_io, double *s_io, double tol) {
     const double ip = rsqrt(Pu * Pu + Pv * Pv);
     double lc = 1.0, ls = 0.0, hc = Pu * ip, hs = Pv * ip;
@@ -1007,7 +1007,8 @@ __device__ void refl_root64(double A, double Ds, double Pu, double Pv, double *c
             nc = bc * r; ns = bs * r;
         }
         c = nc; s = ns;
-        if ((ok && fabs(d) <= tol) || fabs(lc * hs - ls * hc) <= tol) break;
+        const double noise = 4.0 * 1.1102230246251565e-16 * (fabs(gs) + fabs(gr)) / g2;
+        if ((ok && (fabs(d) <= tol || fabs(d) <= noise)) || fabs(lc * hs - ls * hc) <= tol) break;
     }
     *c_io = c;
     *s_io = s;
@@ -1072,12 +1073,13 @@ __device__ __noinline__ void refl_polish(float a, float ds, float pu, float pv, 
 }
 
 // FP64 reflection point: the FP32 root refined by the safeguarded FP64 Newton
-// iteration to a step below 1e-14 (or its rounding noise).
+// iteration to a step below 1e-13 (the next one would be of order 1e-26) or
+// its rounding noise.
 __device__ __noinline__ void refl_root(dx a, dx ds, dx pu, dx pv, dx gam, dx *cs_out, dx *sn_out) {
     float err, c0f, s0f;
     refl_n32(to_float(a), to_float(ds), to_float(pu), to_float(pv), to_float(gam), &c0f, &s0f, &err);
     double c = c0f, s = s0f;
-    refl_root64(a.v, ds.v, pu.v, pv.v, &c, &s, 1e-14);
+    refl_root64(a.v, ds.v, pu.v, pv.v, &c, &s, 1e-13);
     *cs_out = dx(c);
     *sn_out = dx(s);
 }
