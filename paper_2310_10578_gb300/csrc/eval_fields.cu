@@ -954,6 +954,45 @@ __device__ float refl_n32(float a, float ds, float pu, float pv, float gam, floa
     *sn_out = s;
     return psi;
 }
+// FP64 Newton steps for the reflection point, on the unit vector
+// n = (cos psi, sin psi) itself and without trigonometric calls: for Q = a n
+// on the circle, (Q - S).t = a ds sin(psi) and (Q - P).t = a (pu sin(psi) -
+// pv cos(psi)), t the unit tangent, so
+//   dL/dpsi   = a [ds s / |Q - S| + (pu s - pv c) / |Q - P|],
+//   d2L/dpsi2 = (X.Q - (dL/dpsi)_X^2) / |Q - X| summed over X = S, P,
+// and n is rotated by each step d with cos d, sin d from their Taylor series
+// (|d| <= 1e-3), until a step is below tol (quadratic convergence: the next
+// one would be of order tol^2).  Returns false (no result) if a step is too
+// large, the curvature not positive or six steps do not converge; the caller
+// then takes the safeguarded iteration below.
+__device__ bool refl_newton64(double A, double Ds, double Pu, double Pv, double *c_io, double *s_io, double tol) {
+    double c = *c_io, s = *s_io;
+    const double dp2 = Pu * Pu + Pv * Pv;
+    for (int it = 0; it < 6; ++it) {
+        double ifs = rsqrt(A * A + Ds * Ds - 2.0 * A * Ds * c);
+        double ifr = rsqrt(A * A + dp2 - 2.0 * A * (Pu * c + Pv * s));
+        double gs = A * Ds * s * ifs, gr = A * (Pu * s - Pv * c) * ifr;
+        double g = gs + gr;
+        double g2 = (Ds * A * c - gs * gs) * ifs + (A * (Pu * c + Pv * s) - gr * gr) * ifr;
+        if (!(g2 > 0.0)) return false;
+        double d = -g / g2;
+        if (!(fabs(d) <= 1e-3)) return false;
+        double d2 = d * d;
+        double cd = 1.0 - d2 * (0.5 - d2 * (1.0 / 24.0));
+        double sd = d * (1.0 - d2 * ((1.0 / 6.0) - d2 * (1.0 / 120.0)));
+        double cn = c * cd - s * sd, sn = s * cd + c * sd;
+        c = cn; s = sn;
+        if (fabs(d) <= tol) {
+            *c_io = c; *s_io = s;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Double-float refinement of an FP32 reflection point (near-grazing
+// incidence, where the FP32 root of dL/dpsi is too coarse for cos(theta_i)).
+
 // FP64 reflection point from a start n0 = (c, s): safeguarded Newton on the
 // unit vector n itself, without trigonometric calls.  The bracket is kept as
 // two unit vectors, n_lo (dL/dpsi < 0; initially psi = 0, the direction of S)
@@ -1063,23 +1102,34 @@ __device__ bool refl_polish_df(float a, float ds, float pu, float pv, float c0, 
 }
 
 // FP64 refinement of an FP32 reflection point, for the cases the
-// double-float step does not take.  Returns (cos psi, sin psi) in FP32.
+// double-float step does not take: FP64 Newton steps, the safeguarded
+// iteration when they do not converge.  Returns (cos psi, sin psi) in FP32.
 __device__ __noinline__ void refl_polish(float a, float ds, float pu, float pv, float gam, float c0f, float s0f,
                                          float *cs_out, float *sn_out) {
     double c = c0f, s = s0f;
-    refl_root64(a, ds, pu, pv, &c, &s, 1e-9);                 // (the result is rounded to FP32)
+    double r = 1.0 / sqrt(c * c + s * s);
+    c *= r; s *= r;
+    if (!refl_newton64(a, ds, pu, pv, &c, &s, 1e-9)) {        // (the result is rounded to FP32)
+        c = c0f; s = s0f;
+        refl_root64(a, ds, pu, pv, &c, &s, 1e-9);
+    }
     *cs_out = (float)c;
     *sn_out = (float)s;
 }
 
-// FP64 reflection point: the FP32 root refined by the safeguarded FP64 Newton
-// iteration to a step below 1e-13 (the next one would be of order 1e-26) or
-// its rounding noise.
+// FP64 reflection point: the FP32 root refined by FP64 Newton steps to a step
+// below 1e-13 (the next one would be of order 1e-26); the safeguarded
+// iteration when they do not converge.
 __device__ __noinline__ void refl_root(dx a, dx ds, dx pu, dx pv, dx gam, dx *cs_out, dx *sn_out) {
     float err, c0f, s0f;
     refl_n32(to_float(a), to_float(ds), to_float(pu), to_float(pv), to_float(gam), &c0f, &s0f, &err);
     double c = c0f, s = s0f;
-    refl_root64(a.v, ds.v, pu.v, pv.v, &c, &s, 1e-13);
+    double r = 1.0 / sqrt(c * c + s * s);
+    c *= r; s *= r;
+    if (!refl_newton64(a.v, ds.v, pu.v, pv.v, &c, &s, 1e-13)) {
+        c = c0f; s = s0f;
+        refl_root64(a.v, ds.v, pu.v, pv.v, &c, &s, 1e-13);
+    }
     *cs_out = dx(c);
     *sn_out = dx(s);
 }
