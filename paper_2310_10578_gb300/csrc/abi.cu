@@ -298,6 +298,8 @@ static int prep_freqs(const double *f_hz, int n_f, FreqC *fq, double *hl, const 
             double il = fr / 299792458.0;
             q.k[f] = (float)k;
             q.kh[f] = (float)cbrt(k / 2.0);
+            q.sk[f] = (float)sqrt(k / (2.0 * cbrt(k / 2.0) * cbrt(k / 2.0)));
+            q.pk[f] = (float)(cbrt(k / 2.0) * sqrt(2.0 / k));
             q.il_hi[f] = (float)il;
             q.il_lo[f] = (float)(il - (double)q.il_hi[f]);
             q.kd[f] = k;

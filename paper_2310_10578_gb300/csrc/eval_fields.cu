@@ -1927,9 +1927,9 @@ __device__ __forceinline__ void rb_apply(const Ctx &c, AccS<float> &acc, const F
     const float Es = r[0], Eh = r[32], A = r[256], Lp = r[288], rcb = r[320], cth = r[352];
     dfl len;
     len.hi = r[384]; len.lo = r[416];
+    const float sLr = sqrtf(Lp) / rcb;            // (K = sk sqrt(L') / rcb, as in creep_apply)
 #pragma unroll 1
     for (int f = 0; f < fq.nf; ++f) {
-        float k = fq.k[f];
         float m = fq.kh[f] * rcb;
         float xi = -2.0f * m * cth;
         cpx<float> Rs, Rh;
@@ -1937,7 +1937,7 @@ __device__ __forceinline__ void rb_apply(const Ctx &c, AccS<float> &acc, const F
             Rs = mkc<float>(-1, 0); Rh = mkc<float>(1, 0);
         } else {
             cpx<float> Bs, Bh;
-            fock_bracket<float>(c, xi, sqrtf(k * Lp / (2.0f * m * m)), Bs, Bh);
+            fock_bracket<float>(c, xi, fq.sk[f] * sLr, Bs, Bh);
             float sn, cs;
             sincospif(-xi * xi * xi * (float)(1.0 / (12.0 * M_PI)), &sn, &cs);
             cpx<float> pre = mkc<float>(cs, sn) * (-sqrtf(-4.0f / xi));
@@ -1994,14 +1994,16 @@ __device__ __forceinline__ void creep_apply(const Ctx &c, AccS<float> &acc, cons
     const bool caus = r[256] < 0.0f;
     dfl len;
     len.hi = r[384]; len.lo = r[416];
+    // per frequency, K = sqrt(k L' / (2 m^2)) = sk sqrt(L') / rcb and the
+    // amplitude m sqrt(2 / k) = pk rcb (m = kh rcb)
+    const float sLr = sqrtf(Lp) / rcb, ra = rcb * amp;
 #pragma unroll 1
     for (int f = 0; f < fq.nf; ++f) {
-        float k = fq.k[f];
         float m = fq.kh[f] * rcb;
         float xi = m * tr;
         cpx<float> Bs, Bh;
-        fock_bracket<float>(c, xi, sqrtf(k * Lp / (2.0f * m * m)), Bs, Bh);
-        float pre = -m * sqrtf(2.0f / k) * amp;
+        fock_bracket<float>(c, xi, fq.sk[f] * sLr, Bs, Bh);
+        float pre = -fq.pk[f] * ra;
         cpx<float> ph = phasor(fq, f, len) * pre;
         if (caus) ph = mkc<float>(-ph.im, ph.re);          // x (+j)
         cpx<float> as = Bs * ph * Es, ah = Bh * ph * Eh;

@@ -47,6 +47,8 @@ constexpr int NFC = 4;
 // Per-chunk frequency constants (built on the host at rt_set_freqs).
 struct FreqC {
     float k[NFC], kh[NFC];       // wavenumber, (k/2)^{1/3}
+    float sk[NFC], pk[NFC];      // sqrt(k / (2 kh^2)), kh sqrt(2 / k): the per-frequency factors of the
+                                 // Fock distance parameter and of the creeping amplitude
     float il_hi[NFC], il_lo[NFC];// 1/lambda as double-float
     double kd[NFC], fc[NFC];     // FP64: wavenumber, f/c
     int nf;                      // frequencies in this chunk (0 for path lists)
