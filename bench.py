@@ -193,6 +193,12 @@ def _profiled_traffic():
     return _profiled()
 
 
+def _profiled_timed_step_read():
+    """DRAM bytes read by the three class kernels of a timed room step (L2 as
+    the bench leaves it after its flush), from the committed summary."""
+    return _profiled(key="dram_read_bytes_per_evaluation_timed_step")
+
+
 def hbm_peak():
     """The measured copy bandwidth of this machine's GPUs (MEASURED_PEAKS.json),
     else the stated fallback."""
@@ -869,10 +875,13 @@ def main():
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     barrier()
+    nvtx = torch.cuda.nvtx      # names the timed evaluations for a profiler's range filter
     for i in range(args.steps):
         flush.fill_(float(i))                        # evict L2 between timed steps
         starts[i].record(stream)
+        nvtx.range_push("room_step")
         S.evaluate(rx, out=out, opts=opts)
+        nvtx.range_pop()
         ends[i].record(stream)
     barrier()
     dev_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
@@ -997,6 +1006,10 @@ def main():
         # not separable with events); per-kernel shares are in the ncu launch
         # list under profiles/
         line["roofline"] = peak_fn(flops, mufu, ms, _profiled_traffic())
+        line["roofline"]["traffic_basis"] = ("ncu, caches flushed before each of the three class kernels: the "
+                                             "body kernels' read-modify-writes of the outputs read DRAM")
+        line["roofline"]["timed_step_dram_read"] = _profiled_timed_step_read()
+        line["roofline"]["algorithmic_bytes"] = n_rx * (12 + 24 * n_f)
         line["roofline"]["kernel"] = "evaluation: k_eval<float, false, 1|2|4> (planar, body reflection, creeping)"
     if batched is not None:
         line["batched"] = batched
