@@ -512,6 +512,17 @@ int rt_get_stats(rt_scene *scene, rt_stats *out);
  */
 int rt_fock_table(double *xi_lo, double *step, int *n, double *g, double *dg, double *res);
 
+/*
+ * The table's second segment, used by the FP32 fields above xi0 = 1.5 (the
+ * smooth-surface functions after Eq. 4): P(xi) itself, P = phat - c/xi
+ * (soft kind 0, hard kind 1), and dP/dxi at xi = xi0 + j step (the step of
+ * rt_fock_table), j = 0 .. n - 1, up to xi = 5, where the residue series
+ * takes over.  p, dp: host double [2][n][2] ((re, im) pairs), or NULL to
+ * query xi0 and n only.  Returns RT_OK, or RT_ERR_CUDA if the table could
+ * not be built.
+ */
+int rt_fock_table_p(double *xi0, int *n, double *p, double *dp);
+
 /* Thread-local description of the last error (never NULL). */
 const char *rt_last_error(void);
 

@@ -24,6 +24,7 @@ FOCK_NRES = 8
 
 EXPORTS = ("rt_scene_create", "rt_scene_destroy", "rt_set_tx", "rt_set_freqs", "rt_evaluate",
            "rt_evaluate_host", "rt_evaluate_host_noalloc", "rt_paths", "rt_get_stats", "rt_fock_table",
+           "rt_fock_table_p",
            "rt_last_error", "rt_batch_create", "rt_batch_destroy", "rt_batch_set_frame", "rt_batch_evaluate",
            "rt_batch_capture", "rt_batch_replay", "rt_batch_get_stats", "rt_backward", "rt_alu_peaks",
            "rt_evaluate_with_paths", "rt_batch_set_shape", "rt_batch_get_shape", "rt_batch_tune",
@@ -79,6 +80,7 @@ def load(build_if_missing=True):
     lib.rt_paths.argtypes = [P, P, I, P, P, I, P, P, P]
     lib.rt_get_stats.argtypes = [P, P]
     lib.rt_fock_table.argtypes = [P, P, P, P, P, P]
+    lib.rt_fock_table_p.argtypes = [P, P, P, P]
     lib.rt_last_error.restype = ctypes.c_char_p
     lib.rt_batch_create.argtypes = [P, I, P, I, I, ctypes.POINTER(P)]
     lib.rt_batch_destroy.argtypes = [P]
@@ -487,6 +489,17 @@ def fock_table():
     res = np.zeros((4, FOCK_NRES))
     _check(lib.rt_fock_table(None, None, None, _ptr(g), _ptr(dg), _ptr(res)))
     return xi_lo.value, step.value, g[..., 0] + 1j * g[..., 1], dg[..., 0] + 1j * dg[..., 1], res
+
+
+def fock_table_p():
+    """The table's P segment (FP32 fields above xi0): (xi0, P [2, n] complex, dP [2, n])."""
+    lib = load()
+    xi0, n = ctypes.c_double(), ctypes.c_int()
+    _check(lib.rt_fock_table_p(ctypes.byref(xi0), ctypes.byref(n), None, None))
+    p = np.zeros((2, n.value, 2))
+    dp = np.zeros((2, n.value, 2))
+    _check(lib.rt_fock_table_p(None, None, _ptr(p), _ptr(dp)))
+    return xi0.value, p[..., 0] + 1j * p[..., 1], dp[..., 0] + 1j * dp[..., 1]
 
 
 def decode(code):

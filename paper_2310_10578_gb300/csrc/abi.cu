@@ -58,7 +58,7 @@ static int get_table(DevTable **out) {
     DevTable T;
     int rc = build_fock_table(&T.host);
     if (rc != RT_OK) return rc;
-    std::vector<float4> f32(FOCK_N * 2);
+    std::vector<float4> f32((FOCK_N + FOCK_NP) * 2);
     std::vector<double2> f64(FOCK_N * 4);
     for (int j = 0; j < FOCK_N; ++j)
         for (int k = 0; k < 2; ++k) {
@@ -66,6 +66,12 @@ static int get_table(DevTable **out) {
             f32[j * 2 + k] = make_float4((float)q[0], (float)q[1], (float)(q[2] * XI_STEP), (float)(q[3] * XI_STEP));
             f64[(j * 2 + k) * 2] = make_double2(q[0], q[1]);
             f64[(j * 2 + k) * 2 + 1] = make_double2(q[2], q[3]);
+        }
+    for (int j = 0; j < FOCK_NP; ++j)              // the FP32 second segment: P, h P'
+        for (int k = 0; k < 2; ++k) {
+            const double *q = &T.host.tabp[(j * 2 + k) * 4];
+            f32[(FOCK_N + j) * 2 + k] =
+                make_float4((float)q[0], (float)q[1], (float)(q[2] * XI_STEP), (float)(q[3] * XI_STEP));
         }
     std::vector<float4> r32(FOCK_NRES * 2);
     std::vector<dq4> r64(FOCK_NRES * 2);
@@ -996,6 +1002,21 @@ int rt_fock_table(double *xi_lo, double *step, int *n, double *g, double *dg, do
             if (dg) { dg[(k * FOCK_N + j) * 2] = q[2]; dg[(k * FOCK_N + j) * 2 + 1] = q[3]; }
         }
     if (res) memcpy(res, T->host.res.data(), sizeof(double) * 4 * FOCK_NRES);
+    return RT_OK;
+}
+
+int rt_fock_table_p(double *xi0, int *n, double *p, double *dp) {
+    DevTable *T = nullptr;
+    int rc = get_table(&T);
+    if (rc != RT_OK) return rc;
+    if (xi0) *xi0 = XI_HI;
+    if (n) *n = FOCK_NP;
+    for (int j = 0; j < FOCK_NP; ++j)
+        for (int k = 0; k < 2; ++k) {
+            const double *q = &T->host.tabp[(j * 2 + k) * 4];
+            if (p) { p[(k * FOCK_NP + j) * 2] = q[0]; p[(k * FOCK_NP + j) * 2 + 1] = q[1]; }
+            if (dp) { dp[(k * FOCK_NP + j) * 2] = q[2]; dp[(k * FOCK_NP + j) * 2 + 1] = q[3]; }
+        }
     return RT_OK;
 }
 

@@ -74,7 +74,7 @@ struct Ctx {
     int n_tri, n_face, n_body;
     float band;
     v3t<float> S, pol;
-    const float4 *fock;          // [FOCK_N][2]
+    const float4 *fock;          // [FOCK_N][2], then the P segment [FOCK_NP][2] (see DevScene)
     const float4 *res;           // [FOCK_NRES][2]
     const float *weid;
     float weid_L;
@@ -1359,6 +1359,20 @@ __device__ cpx<float> faddeeva<float>(const Ctx &c, cpx<float> z) {
 // false returns P itself (each computed without cancellation in its domain).
 __device__ void pekeris(const Ctx &c, float xi, cpx<float> &ps, cpx<float> &ph, bool regular) {
     const float ci = 0.19947114f / xi;                 // c/xi = e^{-j pi/4}/(2 sqrt(pi) xi) = (ci, -ci)
+    if (xi > (float)XI_HI && xi < (float)XI_P) {
+        // the table's P segment: cubic Hermite in P itself
+        const float u = (xi - (float)XI_HI) * (float)(1.0 / XI_STEP);
+        const int j = min(max((int)u, 0), FOCK_NP - 2);
+        const float t = u - (float)j, t2 = t * t, omt = 1.0f - t;
+        const float h00 = (1.0f + 2.0f * t) * omt * omt, h10 = t * omt * omt, h01 = t2 * (3.0f - 2.0f * t),
+                    h11 = t2 * (t - 1.0f);
+        const float4 *tp = c.fock + 2 * FOCK_N;
+        const float4 a0 = tp[2 * j], a1 = tp[2 * j + 2], b0 = tp[2 * j + 1], b1 = tp[2 * j + 3];
+        ps = mkc(h00 * a0.x + h10 * a0.z + h01 * a1.x + h11 * a1.z, h00 * a0.y + h10 * a0.w + h01 * a1.y + h11 * a1.w);
+        ph = mkc(h00 * b0.x + h10 * b0.z + h01 * b1.x + h11 * b1.z, h00 * b0.y + h10 * b0.w + h01 * b1.y + h11 * b1.w);
+        if (regular) { ps = ps + mkc(ci, -ci); ph = ph + mkc(ci, -ci); }
+        return;
+    }
     if (xi > (float)XI_HI) {
         // residue series: term n decays as exp(-xi rs.x); the terms are summed
         // until one falls below 1e-8 of the first (exp2 and sincospi with the
@@ -2839,7 +2853,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
     __shared__ Ctx s_ctx;
     __shared__ FreqC s_fqs[MAX_CHUNKS];        // frequency chunks ch0 .. ch0 + nch - 1
     // stage scene (and, for the body classes, the Fock--Pekeris table)
-    const int n_fock = BODIES ? FOCK_N * 2 : 0, n_res = BODIES ? FOCK_NRES * 2 : 0;
+    const int n_fock = BODIES ? (FOCK_N + FOCK_NP) * 2 : 0, n_res = BODIES ? FOCK_NRES * 2 : 0;
     float4 *s_fock = smem;                                   // n_fock
     float4 *s_res = s_fock + n_fock;                         // n_res
     float4 *s_face = s_res + n_res;                          // n_face
@@ -3161,7 +3175,7 @@ k_eval(DevScene S, FrameDev F1, const FrameDev *__restrict__ frames, int n_frame
 // (body classes) or the wide partial sums of wide_chunks chunks (planar)
 static size_t smem_bytes(const DevScene &S, bool bodies, bool records, int blk, int rcap, int wide_chunks,
                          int occ_sets) {
-    size_t n = (bodies ? FOCK_N * 2 + FOCK_NRES * 2 : 0) + (S.n_face <= SMEM_FACE_MAX ? S.n_face : 0) +
+    size_t n = (bodies ? (FOCK_N + FOCK_NP) * 2 + FOCK_NRES * 2 : 0) + (S.n_face <= SMEM_FACE_MAX ? S.n_face : 0) +
                (S.bvh ? 2 * (size_t)min(S.bvh_nodes, BVH_TOP_NODES) : 0);
     if (S.n_body <= SMEM_BODY_MAX) n += 4 * S.n_body;
     if (S.n_tri <= SMEM_TRI_MAX) n += 6 * S.n_tri;

@@ -2,7 +2,9 @@
 // the residue-series constants used by the field kernel.
 //
 // Table: G_{s,h}(xi) = phat_{s,h}(xi) e^{-j xi^3/12} and dG/dxi at
-// xi_j = XI_LO + j * XI_STEP, j = 0 .. FOCK_N - 1, covering [XI_LO, XI_HI].
+// xi_j = XI_LO + j * XI_STEP, j = 0 .. FOCK_N - 1, covering [XI_LO, XI_HI];
+// and P_{s,h}(xi) = phat - c/xi with dP/dxi on [XI_HI, XI_P] (the FP32
+// fields' second segment).
 // The e^{-j xi^3/12} factor removes the geometrical-optics phase of the lit
 // side (phat ~ sqrt(-xi/4) e^{j xi^3/12} as xi -> -inf), leaving a slowly
 // varying function for cubic Hermite interpolation.
@@ -87,12 +89,15 @@ __global__ void k_fock_integrands(const cd *tau, const cd *wt, int n_pos, int n,
     Wh[i] = wt[i] * gh;
 }
 
-// One block per table node: phat, dphat/dxi by summing the bucket's nodes.
+// One block per table node xi = xi0 + j XI_STEP: phat, dphat/dxi by summing
+// the bucket's nodes; stored as G = phat e^{-j xi^3/12} and G' (p_form false)
+// or as P = phat - c/xi and P' = phat' + c/xi^2 (p_form true, xi > 0).
 __global__ void k_fock_table(const cd *tau, const cd *Ws, const cd *Wh, int n_pos, const int *neg_off,
-                             int n_tab, double *out /* [n_tab][2 kinds][4] = G.re, G.im, G'.re, G'.im */) {
+                             int n_tab, double xi0, bool p_form,
+                             double *out /* [n_tab][2 kinds][4] = G.re, G.im, G'.re, G'.im (or P, P') */) {
     int j = blockIdx.x;
     if (j >= n_tab) return;
-    double xi = XI_LO + j * XI_STEP;
+    double xi = xi0 + j * XI_STEP;
     int b = (xi >= 0.0) ? 0 : (int)ceil(-xi);
     int lo = neg_off[b], hi = neg_off[b + 1];
     int cnt = n_pos + (hi - lo);
@@ -121,6 +126,17 @@ __global__ void k_fock_table(const cd *tau, const cd *Ws, const cd *Wh, int n_po
         cd pre = cpolar(1.0 / sqrt(M_PI), -M_PI / 4.0);
         cd ph[2] = {pre * C(red[0][0], red[1][0]), pre * C(red[2][0], red[3][0])};
         cd dph[2] = {pre * C(red[4][0], red[5][0]), pre * C(red[6][0], red[7][0])};
+        if (p_form) {
+            const cd c = cpolar(0.5 / sqrt(M_PI), -M_PI / 4.0);   // e^{-j pi/4} / (2 sqrt(pi))
+            for (int k = 0; k < 2; ++k) {
+                cd P = ph[k] - c * (1.0 / xi), dP = dph[k] + c * (1.0 / (xi * xi));
+                out[(j * 2 + k) * 4 + 0] = P.x;
+                out[(j * 2 + k) * 4 + 1] = P.y;
+                out[(j * 2 + k) * 4 + 2] = dP.x;
+                out[(j * 2 + k) * 4 + 3] = dP.y;
+            }
+            return;
+        }
         cd rot = cpolar(1.0, -xi * xi * xi / 12.0);          // e^{-j xi^3/12}
         for (int k = 0; k < 2; ++k) {
             cd G = ph[k] * rot;
@@ -210,7 +226,7 @@ int build_fock_table(FockHost *T) {
     int n = (int)tau.size();
     cd *d_tau = nullptr, *d_wt = nullptr, *d_ws = nullptr, *d_wh = nullptr;
     int *d_off = nullptr;
-    double *d_out = nullptr, *d_res = nullptr;
+    double *d_out = nullptr, *d_outp = nullptr, *d_res = nullptr;
     int rc = RT_ERR_CUDA;
     CK(cudaMalloc(&d_tau, sizeof(cd) * n));
     CK(cudaMalloc(&d_wt, sizeof(cd) * n));
@@ -218,26 +234,31 @@ int build_fock_table(FockHost *T) {
     CK(cudaMalloc(&d_wh, sizeof(cd) * n));
     CK(cudaMalloc(&d_off, sizeof(int) * (FOCK_NBUCKET + 1)));
     CK(cudaMalloc(&d_out, sizeof(double) * FOCK_N * 8));
+    CK(cudaMalloc(&d_outp, sizeof(double) * FOCK_NP * 8));
     CK(cudaMalloc(&d_res, sizeof(double) * 4 * FOCK_NRES));
     CK(cudaMemcpy(d_tau, tau.data(), sizeof(cd) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_wt, wt.data(), sizeof(cd) * n, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(d_off, off.data(), sizeof(int) * (FOCK_NBUCKET + 1), cudaMemcpyHostToDevice));
     k_fock_integrands<<<(n + 127) / 128, 128>>>(d_tau, d_wt, n_pos, n, d_ws, d_wh);
     CK(cudaGetLastError());
-    k_fock_table<<<FOCK_N, 256>>>(d_tau, d_ws, d_wh, n_pos, d_off, FOCK_N, d_out);
+    k_fock_table<<<FOCK_N, 256>>>(d_tau, d_ws, d_wh, n_pos, d_off, FOCK_N, XI_LO, false, d_out);
+    CK(cudaGetLastError());
+    k_fock_table<<<FOCK_NP, 256>>>(d_tau, d_ws, d_wh, n_pos, d_off, FOCK_NP, XI_HI, true, d_outp);
     CK(cudaGetLastError());
     k_airy_zeros<<<1, 32>>>(d_res);
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());
     T->tab.resize(FOCK_N * 8);
+    T->tabp.resize(FOCK_NP * 8);
     T->res.resize(4 * FOCK_NRES);
     CK(cudaMemcpy(T->tab.data(), d_out, sizeof(double) * FOCK_N * 8, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(T->tabp.data(), d_outp, sizeof(double) * FOCK_NP * 8, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(T->res.data(), d_res, sizeof(double) * 4 * FOCK_NRES, cudaMemcpyDeviceToHost));
     T->n_nodes = n;
     rc = RT_OK;
 fail:
     cudaFree(d_tau); cudaFree(d_wt); cudaFree(d_ws); cudaFree(d_wh);
-    cudaFree(d_off); cudaFree(d_out); cudaFree(d_res);
+    cudaFree(d_off); cudaFree(d_out); cudaFree(d_outp); cudaFree(d_res);
     return rc;
 }
 

@@ -23,12 +23,19 @@ constexpr double XI_LO = -10.0;
 constexpr double XI_HI = 1.5;
 constexpr double XI_STEP = 1.0 / 64.0;
 constexpr int FOCK_N = 737;            // (XI_HI - XI_LO) / XI_STEP + 1
+// FP32 fields: a second segment of the table on [XI_HI, XI_P] holds P itself
+// (not phat, and without the e^{-j xi^3/12} factor), where the residue series
+// needs 8 to 16 terms (soft and hard) and phat = P + c/xi is mostly c/xi (so
+// that P = phat - c/xi would lose FP32 digits); the series runs above XI_P.
+constexpr double XI_P = 5.0;
+constexpr int FOCK_NP = 225;           // (XI_P - XI_HI) / XI_STEP + 1
 constexpr int FOCK_NBUCKET = 11;       // quadrature buckets: [0, XI_HI], [-1, 0), ..., [-10, -9)
 constexpr int FOCK_NRES = 8;           // residue-series terms
 constexpr int WEIDEMAN_N = 16;         // terms of the rational approximation of w(z)
 
 struct FockHost {
     std::vector<double> tab;   // [FOCK_N][2][4]: G.re, G.im, G'.re, G'.im (soft, hard)
+    std::vector<double> tabp;  // [FOCK_NP][2][4]: P.re, P.im, P'.re, P'.im (soft, hard) on [XI_HI, XI_P]
     std::vector<double> res;   // [4][FOCK_NRES]: alpha, 1/Ai'(-alpha)^2, beta, 1/(beta Ai(-beta)^2)
     int n_nodes = 0;
 };
@@ -67,7 +74,8 @@ struct DevScene {
                                // beyond which the FP32 face-membership test is a certain no
     const int *face_tris;      // [n_tri]
     const float4 *body;        // [n_body][2]: (cx, cy, cz, a), (h, type, 0, 0)
-    const float4 *fock32;      // [FOCK_N][2]: (G.re, G.im, h G'.re, h G'.im) soft, hard
+    const float4 *fock32;      // [FOCK_N][2]: (G.re, G.im, h G'.re, h G'.im) soft, hard; then
+                               // [FOCK_NP][2]: (P.re, P.im, h P'.re, h P'.im) on [XI_HI, XI_P]
     const double2 *fock64;     // [FOCK_N][2][2]: G, G' (soft, hard)
     const float4 *res32;       // [FOCK_NRES][2]: (alpha sqrt3/2, alpha/2, coef, 0) soft, hard
     const dq4 *res64;      // [FOCK_NRES][2]
