@@ -3225,19 +3225,32 @@ static cudaError_t launch_one(const DevScene &S, const Work &W, int ch0, int nch
     if (W.frames && TILE_ALIGN % (NW / nwt) != 0) return cudaErrorInvalidValue;
     // records per lane: one frequency chunk flushes full buffers on the way
     // (5 is enough); several chunks size the body range by the capacity
-    const int rcap = (nch > 1) ? 6 : 5;
+    int rcap = (nch > 1) ? 6 : 5;
     const bool wide = is_planar(CLS) && sizeof(T) == 4 && !PATHS;
     if (nch < 1 || nch > MAX_CHUNKS || (!wide && !bodies && nch != 1)) return cudaErrorInvalidValue;
     // occluder masks (FP32 body kernels): one source-side set, and one
     // receiver-side set per tile in flight (fields) or per warp (path lists)
     const int occ_sets = (bodies && sizeof(T) == 4 && CLS != CLS_WCREEP) ? (PATHS ? NW : NW / nwt) : 0;
-    size_t sm = smem_bytes(S, bodies, bodies && sizeof(T) == 4 && !PATHS, blk, rcap, wide ? nch : 0, occ_sets);
-    cudaError_t e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const bool recs = bodies && sizeof(T) == 4 && !PATHS;
+    size_t sm = smem_bytes(S, bodies, recs, blk, rcap, wide ? nch : 0, occ_sets);
+    int dev = 0, nsm = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (recs) {
+        // many bodies (their data and occluder masks in shared memory): fewer
+        // records per lane -- fewer bodies per geometry pass, or earlier
+        // flushes -- down to one work unit's, so that the block still fits
+        int smax = 0;
+        cudaFuncAttributes fa;
+        if ((e = cudaDeviceGetAttribute(&smax, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+        if ((e = cudaFuncGetAttributes(&fa, k_eval<T, PATHS, CLS, LIST>)) != cudaSuccess) return e;
+        while (rcap > recs_per_unit(CLS) && fa.sharedSizeBytes + sm > (size_t)smax)
+            sm = smem_bytes(S, bodies, recs, blk, --rcap, wide ? nch : 0, occ_sets);
+    }
+    e = cudaFuncSetAttribute(k_eval<T, PATHS, CLS, LIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     // persistent grid: the blocks that fit on the device at once, at most
     // one per work unit
-    int dev = 0, nsm = 0, occ = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_eval<T, PATHS, CLS, LIST>, blk, sm)) != cudaSuccess) return e;
     // (path lists: each warp takes whole tiles; up to one block per tile, so

@@ -219,6 +219,18 @@ def test_many_frequencies_and_masks(creep, oracle_mod):
         compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs)
 
 
+def test_many_bodies_many_frequencies(creep, oracle_mod):
+    # 256 cylinders and 8 frequencies (two chunks): the bodies' data and their
+    # occluder masks take so much shared memory that the body kernels keep
+    # fewer path records per lane (fewer bodies per geometry pass)
+    sc = scenes.room(n_cyl=256, nx=13, ny=11, freqs=tuple(np.linspace(2.4e9, 28e9, 8)), seed=23)
+    S, Eg, codes, counts, fl, _ = _run(creep, sc)
+    ref = oracle_mod.evaluate(sc)
+    compare_paths(codes, counts, ref)
+    _flags_equal(fl, ref)
+    compare_fields(Eg, ref, flags=ref.flags, freqs=sc.freqs)
+
+
 def test_receivers_inside_bodies_and_on_axes(creep, oracle_mod):
     sc = scenes.room(n_cyl=10, nx=4, ny=4, seed=9)
     b = sc.bodies
