@@ -4,7 +4,7 @@
 // Table: G_{s,h}(xi) = phat_{s,h}(xi) e^{-j xi^3/12} and dG/dxi at
 // xi_j = XI_LO + j * XI_STEP, j = 0 .. FOCK_N - 1, covering [XI_LO, XI_HI];
 // and P_{s,h}(xi) = phat - c/xi with dP/dxi on [XI_HI, XI_P] (the FP32
-// fields' second segment).
+// fields' second segment; from XI_PRES on by the residue series).
 // The e^{-j xi^3/12} factor removes the geometrical-optics phase of the lit
 // side (phat ~ sqrt(-xi/4) e^{j xi^3/12} as xi -> -inf), leaving a slowly
 // varying function for cubic Hermite interpolation.
@@ -91,13 +91,37 @@ __global__ void k_fock_integrands(const cd *tau, const cd *wt, int n_pos, int n,
 
 // One block per table node xi = xi0 + j XI_STEP: phat, dphat/dxi by summing
 // the bucket's nodes; stored as G = phat e^{-j xi^3/12} and G' (p_form false)
-// or as P = phat - c/xi and P' = phat' + c/xi^2 (p_form true, xi > 0).
+// or as P = phat - c/xi and P' = phat' + c/xi^2 (p_form true, xi > 0).  In
+// P form from XI_PRES on, P and P' come from the residue series instead:
+// P = -e^{-j pi/12}/(2 sqrt(pi)) sum_n coef_n e^{-xi z_n}, z_n = a_n e^{j pi/6}
+// (a_n the zeros alpha_n, beta_n; res as k_airy_zeros writes it).
 __global__ void k_fock_table(const cd *tau, const cd *Ws, const cd *Wh, int n_pos, const int *neg_off,
-                             int n_tab, double xi0, bool p_form,
+                             int n_tab, double xi0, bool p_form, const double *res,
                              double *out /* [n_tab][2 kinds][4] = G.re, G.im, G'.re, G'.im (or P, P') */) {
     int j = blockIdx.x;
     if (j >= n_tab) return;
     double xi = xi0 + j * XI_STEP;
+    if (p_form && xi >= XI_PRES) {
+        if (threadIdx.x == 0) {
+            const cd pre = -cpolar(0.5 / sqrt(M_PI), -M_PI / 12.0);
+            for (int k = 0; k < 2; ++k) {
+                cd s = C(0), ds = C(0);
+                for (int n = 0; n < FOCK_NRES; ++n) {
+                    const double a = res[(2 * k) * FOCK_NRES + n], coef = res[(2 * k + 1) * FOCK_NRES + n];
+                    const cd z = C(a * (0.5 * sqrt(3.0)), a * 0.5);
+                    const cd t = cexp_(-(z * xi)) * coef;
+                    s = s + t;
+                    ds = ds - z * t;
+                }
+                const cd P = pre * s, dP = pre * ds;
+                out[(j * 2 + k) * 4 + 0] = P.x;
+                out[(j * 2 + k) * 4 + 1] = P.y;
+                out[(j * 2 + k) * 4 + 2] = dP.x;
+                out[(j * 2 + k) * 4 + 3] = dP.y;
+            }
+        }
+        return;
+    }
     int b = (xi >= 0.0) ? 0 : (int)ceil(-xi);
     int lo = neg_off[b], hi = neg_off[b + 1];
     int cnt = n_pos + (hi - lo);
@@ -241,11 +265,11 @@ int build_fock_table(FockHost *T) {
     CK(cudaMemcpy(d_off, off.data(), sizeof(int) * (FOCK_NBUCKET + 1), cudaMemcpyHostToDevice));
     k_fock_integrands<<<(n + 127) / 128, 128>>>(d_tau, d_wt, n_pos, n, d_ws, d_wh);
     CK(cudaGetLastError());
-    k_fock_table<<<FOCK_N, 256>>>(d_tau, d_ws, d_wh, n_pos, d_off, FOCK_N, XI_LO, false, d_out);
-    CK(cudaGetLastError());
-    k_fock_table<<<FOCK_NP, 256>>>(d_tau, d_ws, d_wh, n_pos, d_off, FOCK_NP, XI_HI, true, d_outp);
-    CK(cudaGetLastError());
     k_airy_zeros<<<1, 32>>>(d_res);
+    CK(cudaGetLastError());
+    k_fock_table<<<FOCK_N, 256>>>(d_tau, d_ws, d_wh, n_pos, d_off, FOCK_N, XI_LO, false, d_res, d_out);
+    CK(cudaGetLastError());
+    k_fock_table<<<FOCK_NP, 256>>>(d_tau, d_ws, d_wh, n_pos, d_off, FOCK_NP, XI_HI, true, d_res, d_outp);
     CK(cudaGetLastError());
     CK(cudaDeviceSynchronize());
     T->tab.resize(FOCK_N * 8);

@@ -65,13 +65,13 @@ def test_fock_table_matches_oracle(creep):
 
 
 def test_fock_table_p_segment_matches_oracle(creep):
-    # the FP32 fields' second table segment, P itself on [1.5, 5], against the
+    # the FP32 fields' second table segment, P itself on [1.5, 8], against the
     # oracle's P: its quadrature at 1.5, its 40-term residue series above
     from oracle import fock
     _, step, _, _, _ = creep.fock_table()
     xi0, Pt, dPt = creep.fock_table_p()
     xi = xi0 + step * np.arange(Pt.shape[1])
-    assert abs(xi0 - fock.XI_HI) < 1e-12 and abs(xi[-1] - 5.0) < 1e-12
+    assert abs(xi0 - fock.XI_HI) < 1e-12 and abs(xi[-1] - 8.0) < 1e-12
     h = 1e-5
     for k, hard in ((0, False), (1, True)):
         ref = np.array([fock.P(x, hard) for x in xi])
