@@ -163,9 +163,18 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(self.samples)}
 
 
+# the class kernels' translation unit: its source and the headers it includes
+KERNEL_SOURCES = ("paper_2310_10578_gb300/csrc/eval_fields.cu", "paper_2310_10578_gb300/csrc/devmath.cuh",
+                  "paper_2310_10578_gb300/csrc/dual.cuh", "paper_2310_10578_gb300/csrc/internal.h",
+                  "include/creep.h")
+
+
 def _kernel_source_hash():
-    p = os.path.join(ROOT, "paper_2310_10578_gb300", "csrc", "eval_fields.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    """sha256[:16] of the concatenated kernel sources (the key of the ncu summaries)."""
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, rel), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def _profiled(name="k_eval_room20_traffic.txt", key="dram_bytes_per_evaluation_full_workload"):
@@ -180,7 +189,7 @@ def _profiled(name="k_eval_room20_traffic.txt", key="dram_bytes_per_evaluation_f
         if ": " in line:
             k, v = line.split(": ", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("eval_fields.cu sha256[:16]") != _kernel_source_hash():
+    if kv.get("kernel sources sha256[:16]") != _kernel_source_hash():
         return None
     try:
         return float(kv[key])
