@@ -516,7 +516,7 @@ int rt_fock_table(double *xi_lo, double *step, int *n, double *g, double *dg, do
  * The table's second segment, used by the FP32 fields above xi0 = 1.5 (the
  * smooth-surface functions after Eq. 4): P(xi) itself, P = phat - c/xi
  * (soft kind 0, hard kind 1), and dP/dxi at xi = xi0 + j step (the step of
- * rt_fock_table), j = 0 .. n - 1, up to xi = 8, where the residue series
+ * rt_fock_table), j = 0 .. n - 1, up to xi = 12, where the residue series
  * takes over (nodes below xi = 3 from the table's quadrature, from 3 on from
  * the 8-term residue series).  p, dp: host double [2][n][2] ((re, im) pairs), or NULL to
  * query xi0 and n only.  Returns RT_OK, or RT_ERR_CUDA if the table could

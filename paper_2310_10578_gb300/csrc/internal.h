@@ -29,9 +29,9 @@ constexpr int FOCK_N = 737;            // (XI_HI - XI_LO) / XI_STEP + 1
 // that P = phat - c/xi would lose FP32 digits); the series runs above XI_P.
 // Its nodes come from the quadrature below XI_PRES and from the 8-term
 // residue series (converged there to ~1e-11) from XI_PRES on.
-constexpr double XI_P = 8.0;
+constexpr double XI_P = 12.0;
 constexpr double XI_PRES = 3.0;
-constexpr int FOCK_NP = 417;           // (XI_P - XI_HI) / XI_STEP + 1
+constexpr int FOCK_NP = 673;           // (XI_P - XI_HI) / XI_STEP + 1
 constexpr int FOCK_NBUCKET = 11;       // quadrature buckets: [0, XI_HI], [-1, 0), ..., [-10, -9)
 constexpr int FOCK_NRES = 8;           // residue-series terms
 constexpr int WEIDEMAN_N = 16;         // terms of the rational approximation of w(z)

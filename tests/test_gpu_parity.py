@@ -65,20 +65,25 @@ def test_fock_table_matches_oracle(creep):
 
 
 def test_fock_table_p_segment_matches_oracle(creep):
-    # the FP32 fields' second table segment, P itself on [1.5, 8], against the
-    # oracle's P: its quadrature at 1.5, its 40-term residue series above
+    # the FP32 fields' second table segment, P itself on [1.5, 12], against the
+    # oracle's P: its quadrature at 1.5, its 40-term residue series above (taken
+    # directly: P = phat - c/xi would cancel to a few digits at xi = 12)
     from oracle import fock
     _, step, _, _, _ = creep.fock_table()
     xi0, Pt, dPt = creep.fock_table_p()
     xi = xi0 + step * np.arange(Pt.shape[1])
-    assert abs(xi0 - fock.XI_HI) < 1e-12 and abs(xi[-1] - 8.0) < 1e-12
+    assert abs(xi0 - fock.XI_HI) < 1e-12 and abs(xi[-1] - 12.0) < 1e-12
+
+    def P(x, hard):
+        return fock.P_residue(x, hard) if x > fock.XI_HI else fock.P(x, hard)
+
     h = 1e-5
     for k, hard in ((0, False), (1, True)):
-        ref = np.array([fock.P(x, hard) for x in xi])
+        ref = np.array([P(x, hard) for x in xi])
         assert np.max(np.abs(Pt[k] - ref)) < 1e-10
         assert np.max(np.abs(Pt[k] - ref) / np.abs(ref)) < 1e-6      # FP32 storage needs ~1e-7
         xs = xi[1:-1]
-        num = (np.array([fock.P(x + h, hard) for x in xs]) - np.array([fock.P(x - h, hard) for x in xs])) / (2 * h)
+        num = (np.array([P(x + h, hard) for x in xs]) - np.array([P(x - h, hard) for x in xs])) / (2 * h)
         assert np.max(np.abs(dPt[k][1:-1] - num) / np.abs(num)) < 1e-5
 
 
