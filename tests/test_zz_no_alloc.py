@@ -11,7 +11,7 @@ ordinary host entry point rt_evaluate_host (same kernel; the same parity
 tolerance as the other GPU tests applies, and the two agree exactly).
 A second test checks the promise itself: on a scene that has never seen
 rt_evaluate_host (whose staging buffers are allocated per scene), the free
-device memory the driver reports does not move across no-allocation calls,
+device memory that cudaMemGetInfo reports does not move across no-allocation calls,
 the later ones with more receivers than the first.
 It lives in its own file, collected last, and passes alone or after the rest.
 """
